@@ -1,0 +1,54 @@
+"""Static screening for SOSEX-stat (oracle, molecules).  Test infrastructure.
+
+Sec. II B: statically screened SOSEX replaces the first bare interaction by the
+screened interaction at zero bosonic frequency, W(i Omega = 0).  The RPA form
+used by the statically screened workload is
+
+    Pi_PQ(0) = sum_j w_j G^PQ(tau_j) G^QP(-tau_j)          (quadrature of int_0^beta)
+    W        = V^1/2 (1 - V^1/2 Pi(0) V^1/2)^-1 V^1/2
+
+with G^PQ = X G X^T.  The printed Pi(0) carries an extra minus sign; with the
+sign above Pi(0) is negative semidefinite and W <= V (screening).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import grid, thc
+
+
+def pi0_quadrature(X: np.ndarray, G_tau: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Pi_PQ(0) = sum_j w_j G^PQ(tau_j) G^QP(-tau_j) for one spin block G_tau [n_tau, n, n]."""
+    Gm_tau = grid.g_minus_tau(G_tau)
+    Pi = np.zeros((X.shape[0], X.shape[0]), dtype=np.result_type(X, G_tau))
+    for j in range(G_tau.shape[0]):
+        gp = thc.project_full(X, G_tau[j])
+        gm = thc.project_full(X, Gm_tau[j])
+        Pi += w[j] * gp * gm.T
+    return Pi
+
+
+def pi0_pole_sum(X: np.ndarray, eps: np.ndarray, U: np.ndarray, mu: float, beta: float) -> np.ndarray:
+    """Exact int_0^beta G^PQ(tau) G^QP(-tau) d tau for G = -U diag(e^{-xi tau}/(1+e^{-beta xi})) U^T.
+
+    With y = X U and occupations f_a = 1/(1 + e^{beta xi_a}) the integral is
+        Pi_PQ = -sum_ab y_Pa y_Qa y_Pb y_Qb (f_b - f_a)/(xi_a - xi_b),
+    whose diagonal limit (xi_a = xi_b) is beta f_a (1 - f_a).
+    """
+    xi = eps - mu
+    f = 0.5 * (1.0 - np.tanh(0.5 * beta * xi))
+    d = xi[:, None] - xi[None, :]
+    same = np.abs(d) < 1e-12
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = np.where(same, beta * f[:, None] * (1.0 - f[:, None]), (f[None, :] - f[:, None]) / np.where(same, 1.0, d))
+    y = X @ U
+    return -np.einsum("Pa,Qa,ab,Pb,Qb->PQ", y, y, c, y, y, optimize=True)
+
+
+def w_static(V: np.ndarray, Pi: np.ndarray) -> np.ndarray:
+    """W = V^1/2 (1 - V^1/2 Pi V^1/2)^-1 V^1/2 with V^1/2 from the eigendecomposition of V."""
+    lam, Q = np.linalg.eigh(V)
+    s = np.sqrt(np.clip(lam, 0.0, None))
+    Vh = (Q * s) @ Q.conj().T
+    K = np.eye(V.shape[0]) - Vh @ Pi @ Vh
+    return Vh @ np.linalg.solve(K, Vh)
