@@ -1,0 +1,205 @@
+/*
+ * thc_sox.h - C ABI of the GB300 (sm_103a) library for the imaginary-time
+ * second-order-exchange (SOX) self-energy in tensor-hypercontraction (THC)
+ * form and its screened variants (arXiv 2412.18829, Sec. II B-C).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (SOX_OK = 0 on success).  On failure
+ *   sox_last_error(h) returns a message; nothing is written to outputs that
+ *   failed validation.
+ * - Pointers are owned by the caller.  Tensor pointers may be DEVICE or HOST
+ *   memory (detected per pointer).  Host inputs are staged through the
+ *   handle's workspace; when any output is in host memory the call
+ *   synchronises `stream` before returning.  The library never keeps a caller
+ *   pointer past the call.
+ * - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *   is the legacy default stream) when all tensors are device pointers.
+ * - The handle owns a device workspace that grows on demand with cudaMalloc.
+ *   A call that needs more workspace than any earlier call allocates, so
+ *   capture calls into a CUDA graph only after one un-captured call of the
+ *   same (or larger) size, or after sox_reserve.
+ * - Layouts are row-major, contiguous, outermost index first:
+ *     G, Sigma  [n_spin][n_k][n_tau][n][n]
+ *     X         [n_k][N][n]         X[k][P][p] = X^k_{pP}
+ *     V, W0     [n_q][N][N]         U^q_{PQ}   (n_q = n_k)
+ *   Real data (SOX_REAL64) are doubles; complex data (SOX_COMPLEX128) are
+ *   interleaved (re, im) doubles.  Only SOX_REAL64 with n_k = 1 (molecules)
+ *   is implemented by the entry points below; other forms return
+ *   SOX_ERR_UNSUPPORTED.
+ * - The tau grid must be mirror-symmetric, tau_{n_tau-1-j} = beta - tau_j
+ *   (Chebyshev-Lobatto, see sox_tau_grid): G(-tau_j) is taken as
+ *   -G(tau_{n_tau-1-j}) (fermionic antiperiodicity of Eq. G_def).
+ * - Same-spin only (Sec. II C): spin blocks are independent.
+ */
+#ifndef THC_SOX_H
+#define THC_SOX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SOX_API __attribute__((visibility("default")))
+#else
+#define SOX_API
+#endif
+
+/* status codes */
+#define SOX_OK 0
+#define SOX_ERR_INVALID_ARG 1  /* null pointer, bad enum, bad handle          */
+#define SOX_ERR_SHAPE 2        /* sizes out of range or inconsistent           */
+#define SOX_ERR_UNSUPPORTED 3  /* valid request this build does not implement  */
+#define SOX_ERR_OOM 4          /* device or pinned allocation failed           */
+#define SOX_ERR_CUDA 5         /* a CUDA runtime/driver call failed            */
+#define SOX_ERR_TIMEOUT 6      /* a device-side wait hit its iteration cap     */
+
+/* arithmetic of the contractions (projections, back-projection, Phi: FP64) */
+#define SOX_PREC_FP64 0   /* every step in FP64 on CUDA cores (reference path)          */
+#define SOX_PREC_F16X2 1  /* B/C/A/U contractions as 2-piece FP16 splits with per-row
+                             power-of-two scaling on tcgen05 tensor cores, FP32 accumulate */
+
+#define SOX_REAL64 0
+#define SOX_COMPLEX128 1
+
+/* limits checked by every entry point */
+#define SOX_MAX_N_AO 1024
+#define SOX_MAX_N_THC 16384
+#define SOX_MAX_N_TAU 4096
+
+typedef struct sox_context *sox_handle;
+
+typedef struct {
+  int precision;        /* SOX_PREC_*                                           */
+  int device;           /* CUDA device ordinal the handle is bound to            */
+  long long spin_limit; /* iteration cap for device-side waits; 0 = default      */
+} sox_options;
+
+typedef struct {
+  int n;      /* orbitals per k-point (n_AO), 1..SOX_MAX_N_AO                    */
+  int N;      /* THC interpolation points, 1..SOX_MAX_N_THC                       */
+  int n_tau;  /* imaginary-time points, 2..SOX_MAX_N_TAU, mirror-symmetric grid   */
+  int n_spin; /* 1 (restricted) or 2 (unrestricted, independent blocks)           */
+  int nk[3];  /* k-mesh; {1,1,1} for molecules                                    */
+  int dtype;  /* SOX_REAL64 or SOX_COMPLEX128                                     */
+  double beta;/* inverse temperature (Ha^-1), > 0                                 */
+} sox_problem;
+
+/* Library version (major*10000 + minor*100 + patch). */
+SOX_API int sox_version(void);
+
+/* Create a handle bound to opt->device (NULL opt: FP64, device 0).
+ * Allocates nothing on the device until the first call needs workspace. */
+SOX_API int sox_create(sox_handle *out, const sox_options *opt);
+
+/* Destroy a handle and free its workspace (synchronises the device). */
+SOX_API int sox_destroy(sox_handle h);
+
+/* Message for the last failed call on this handle ("" if none).  Valid until
+ * the next call on the same handle. */
+SOX_API const char *sox_last_error(sox_handle h);
+
+/* Launch accounting for measurement.  While enabled, every kernel the
+ * handle launches is counted, and the launches of the named hot kernels are
+ * bracketed by CUDA events on their launch stream.  sox_profile_read
+ * synchronises the device, then returns for `kernel` (e.g. "sox_bcd") the
+ * number of timed launches and their summed device time in ms; kernel = NULL
+ * returns the total number of kernels launched since enabling (ms = 0).
+ * Enabling resets the counters. */
+SOX_API int sox_profile_enable(sox_handle h, int enable);
+SOX_API int sox_profile_read(sox_handle h, const char *kernel, long long *launches, double *ms);
+
+/* Grow the workspace for problem p now (outside any graph capture). */
+SOX_API int sox_reserve(sox_handle h, const sox_problem *p);
+
+/* Host helper: Chebyshev-Lobatto nodes tau_j = (beta/2)(1 - cos(pi j/(n_tau-1)))
+ * and Clenshaw-Curtis weights w_j (sum_j w_j f(tau_j) ~ int_0^beta f).  The
+ * paper uses sparse-ir grids (Sec. III A); any mirror-symmetric grid with
+ * symmetric weights may be passed instead.  tau, w: host arrays [n_tau]. */
+SOX_API int sox_tau_grid(int n_tau, double beta, double *tau, double *w);
+
+/* THC projections of G (Sec. II C, the G_Rq and G_wP steps after
+ * Eq. U_contraction; full projection G^PQ = X G X^T used by Pi and Phi):
+ *   G_Rq[s][k][t][R][q] = sum_u X_{uR} G_{uq}(tau_t)
+ *   G_wP[s][k][t][w][P] = sum_p G_{wp}(tau_t) X_{pP}
+ *   G_PQ[s][k][t][P][Q] = sum_pq X_{pP} G_{pq}(tau_t) X_{qQ}   (may be NULL)
+ * All FP64 regardless of precision. */
+SOX_API int thc_project_G(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                  double *G_Rq, double *G_wP, double *G_PQ, void *stream);
+
+/* Bare SOX self-energy, Eq. (sox) with U(1) = U(2) = v in THC form and the
+ * static time collapse (Sec. II C):
+ *   Sigma_tr(tau) = -sum U1_(pr|qs) U2_(tu|vw) G_wp(tau) G_uq(tau) G_sv(-tau).
+ * Computed by the THC chain U_Pqs -> A -> (B o C summed over v) -> D ->
+ * Sigma_RP = -D_PR -> Sigma_tr = sum_PR X_tR Sigma_RP X_rP.
+ * G, Sigma [n_spin][1][n_tau][n][n]; X [1][N][n]; V [1][N][N]. */
+SOX_API int sox_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+              const double *V, double *Sigma, void *stream);
+
+/* Statically screened SOSEX (Sec. II B): SOX with one interaction replaced by
+ * the screened W(i Omega = 0).  slot = 1: U(1) = W0, U(2) = V (the screened
+ * first interaction of Sec. II B and the dynamic algorithm); slot = 2:
+ * U(1) = V, U(2) = W0 (the form written in the G3W2 decomposition, Sec. III C).
+ * W0 [1][N][N]. */
+SOX_API int sosex_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                       const double *V, const double *W0, int slot, double *Sigma,
+                       void *stream);
+
+/* General static SOX(U1, U2) (Eq. sox with two static interactions). */
+SOX_API int sox_sigma_general(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                      const double *U1, const double *U2, double *Sigma, void *stream);
+
+/* Static polarisability in THC form for the statically screened interaction:
+ *   Pi0[s][P][Q] = sum_j w_j G^PQ(tau_j) G^QP(-tau_j)   (FP64)
+ * w: tau weights [n_tau] (host or device).  Pi0 [n_spin][N][N]. */
+SOX_API int sox_pi0(sox_handle h, const sox_problem *p, const double *G, const double *X,
+            const double *w, double *Pi0, void *stream);
+
+/* Screened interaction W0 = V^1/2 (1 - V^1/2 Pi V^1/2)^-1 V^1/2, computed as
+ * the equal (1 - V Pi)^-1 V by Gauss-Jordan elimination with partial
+ * pivoting in FP64.  Pi is the total polarisability [N][N] (sum the spin
+ * blocks of sox_pi0 first if desired).  Returns SOX_ERR_INVALID_ARG for a
+ * singular system. */
+SOX_API int sox_w_static(sox_handle h, const sox_problem *p, const double *V, const double *Pi,
+                 double *W0, void *stream);
+
+/* Luttinger-Ward functional of bare SOX per spin block:
+ *   phi[s] = 1/4 sum_j w_j Tr[Sigma(tau_j) G(-tau_j)]          (FP64 trace)
+ * (the tau form of the SOX part of E_dyn, Eq. E2b, divided by 4).
+ * Sigma_out [n_spin][1][n_tau][n][n] may be NULL; phi [n_spin]. */
+SOX_API int phi_sox(sox_handle h, const sox_problem *p, const double *G, const double *X,
+            const double *V, const double *w, double *phi, double *Sigma_out, void *stream);
+
+/* Adjoint of phi_sox: given dphi [n_spin] (the cotangent of phi), returns
+ *   dG[s][0][j][r][t] = dphi[s] * dPhi_s/dG_rt(tau_j)  = -dphi[s] w_j Sigma_tr(beta - tau_j)
+ *   dX[0][P][p]       = sum_s dphi[s] dPhi_s/dX_pP
+ *   dV[0][P][Q]       = sum_s dphi[s] dPhi_s/dV_PQ
+ * with respect to the unsymmetrised entries.  Any of dG, dX, dV may be NULL. */
+SOX_API int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                     const double *V, const double *w, const double *dphi, double *dG,
+                     double *dX, double *dV, void *stream);
+
+/* Dynamically screened SOSEX (Sec. II C, Eq. GG and the steps after it):
+ *   Sigma = SOX(v, v) + Sigma_d with
+ *   Sigma_d,tr(tau_i) = -sum v_(tu|vw) G_wp(tau_i)
+ *        sum_m T_inv[i][m] sum_j T_fwd[m][j] Wd_(pr|qs)(i Omega_m) G_uq(tau_j) G_sv(-tau_j)
+ * Wd [1][n_omega][N][N] real (W(i Omega_m) - v), T_fwd [n_omega][n_tau] and
+ * T_inv [n_tau][n_omega] complex (interleaved).  The transform pair is the
+ * caller's (the paper uses sparse-ir, Sec. II C). */
+SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                        const double *V, const double *Wd, const double *T_fwd,
+                        const double *T_inv, int n_omega, double *Sigma, void *stream);
+
+/* Batch of independent bare-SOX problems (uneven sizes allowed), one launch
+ * sequence on one stream.  probs, G, X, V, Sigma are HOST arrays of `count`
+ * entries; the tensors they point to follow the single-problem rules. */
+SOX_API int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs,
+                    const double *const *G, const double *const *X, const double *const *V,
+                    double *const *Sigma, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THC_SOX_H */

@@ -62,10 +62,10 @@ def sigma_chain(X: np.ndarray, U1: np.ndarray, U2: np.ndarray, G: np.ndarray, Gm
     Um2 = mixed_tensor(U2, X) if U2_mixed is None else U2_mixed      # U(2)_Rvw
     G_Rq = thc.project_left(X, G)                                     # G_Rq(tau)
     G_wP = thc.project_right(X, G)                                    # G_wP(tau)
-    A = np.einsum("Pqs,sv->Pqv", Um1, Gm)                             # A_Pqv
-    B = np.einsum("Pqv,Rq->PRv", A, G_Rq)                             # B_PRv
-    C = np.einsum("Rvw,wP->RvP", Um2, G_wP)                           # C_RvP
-    D = np.einsum("RvP,PRv->PR", C, B)                                # D_PR
+    A = np.einsum("Pqs,sv->Pqv", Um1, Gm, optimize=True)                             # A_Pqv
+    B = np.einsum("Pqv,Rq->PRv", A, G_Rq, optimize=True)                             # B_PRv
+    C = np.einsum("Rvw,wP->RvP", Um2, G_wP, optimize=True)                           # C_RvP
+    D = np.einsum("RvP,PRv->PR", C, B, optimize=True)                                # D_PR
     sig_RP = -D.T                                                     # Sigma_RP = -D_PR
     sig = X.T @ sig_RP @ X                                            # Sigma_tr
     if return_RP:

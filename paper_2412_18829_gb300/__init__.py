@@ -1,0 +1,31 @@
+"""GB300 (sm_103a) library for the THC second-order-exchange self-energy.
+
+The compute lives in ``libthcsox.so`` (hand-written CUDA behind a C ABI, see
+``include/thc_sox.h``); this package is its thin Python binding plus a
+``torch.autograd.Function`` around Phi_SOX.  Importing it does not build
+anything; ``paper_2412_18829_gb300.build.build()`` compiles the library.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTED,
+    Handle,
+    PRECISIONS,
+    SoxError,
+    lib,
+    phi_sox,
+    phi_sox_backward,
+    problem,
+    sosex_dynamic_sigma,
+    sosex_static_sigma,
+    sox_pi0,
+    sox_profile_enable,
+    sox_profile_read,
+    sox_reserve,
+    sox_sigma,
+    sox_sigma_batch,
+    sox_sigma_general,
+    sox_tau_grid,
+    sox_version,
+    sox_w_static,
+    thc_project_G,
+)
+from .autograd import PhiSOX  # noqa: F401

@@ -1,0 +1,243 @@
+"""ctypes binding of ``libthcsox.so`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and only turns
+tensors into pointers and sizes; all arithmetic runs in the library's CUDA
+kernels.  Tensors may be CUDA tensors or host (CPU / numpy) float64 arrays;
+host buffers are staged by the library itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libthcsox.so")
+
+SOX_OK, SOX_ERR_INVALID_ARG, SOX_ERR_SHAPE, SOX_ERR_UNSUPPORTED, SOX_ERR_OOM, SOX_ERR_CUDA, SOX_ERR_TIMEOUT = range(7)
+PRECISIONS = {"fp64": 0, "f16x2": 1}
+SOX_REAL64, SOX_COMPLEX128 = 0, 1
+
+_ERRNAMES = {1: "SOX_ERR_INVALID_ARG", 2: "SOX_ERR_SHAPE", 3: "SOX_ERR_UNSUPPORTED", 4: "SOX_ERR_OOM",
+             5: "SOX_ERR_CUDA", 6: "SOX_ERR_TIMEOUT"}
+
+
+class SoxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sox_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("N", ctypes.c_int), ("n_tau", ctypes.c_int),
+                ("n_spin", ctypes.c_int), ("nk", ctypes.c_int * 3), ("dtype", ctypes.c_int),
+                ("beta", ctypes.c_double)]
+
+
+class sox_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "sox_version": ([], _I),
+    "sox_create": ([ctypes.POINTER(_P), ctypes.POINTER(sox_options)], _I),
+    "sox_destroy": ([_P], _I),
+    "sox_last_error": ([_P], ctypes.c_char_p),
+    "sox_reserve": ([_P, ctypes.POINTER(sox_problem)], _I),
+    "sox_profile_enable": ([_P, _I], _I),
+    "sox_profile_read": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _I),
+    "sox_tau_grid": ([_I, ctypes.c_double, _P, _P], _I),
+    "thc_project_G": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P], _I),
+    "sox_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
+    "sox_sigma_general": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P], _I),
+    "sosex_static_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _I, _P, _P], _I),
+    "sox_pi0": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
+    "sox_w_static": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P], _I),
+    "phi_sox": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P], _I),
+    "phi_sox_backward": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "sosex_dynamic_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _I, _P, _P], _I),
+    "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                         ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libthcsox.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = handle
+    return _lib
+
+
+def _ptr(t):
+    """Raw pointer of a contiguous float64 tensor/array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous float64")
+        return t.ctypes.data
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"unsupported tensor type {type(t)}")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def problem(n, N, n_tau, n_spin=1, beta=100.0, nk=(1, 1, 1), dtype=SOX_REAL64) -> sox_problem:
+    p = sox_problem()
+    p.n, p.N, p.n_tau, p.n_spin = int(n), int(N), int(n_tau), int(n_spin)
+    p.nk[0], p.nk[1], p.nk[2] = (int(x) for x in nk)
+    p.dtype = int(dtype)
+    p.beta = float(beta)
+    return p
+
+
+class Handle:
+    """Owns a ``sox_handle`` (device workspace, precision choice)."""
+
+    def __init__(self, precision: str = "fp64", device: int = 0, spin_limit: int = 0):
+        o = sox_options(PRECISIONS[precision], int(device), int(spin_limit))
+        h = _P()
+        rc = lib().sox_create(ctypes.byref(h), ctypes.byref(o))
+        if rc != SOX_OK:
+            raise SoxError(rc, "sox_create failed")
+        self._h = h
+        self.precision = precision
+
+    @property
+    def ptr(self):
+        if self._h is None:
+            raise RuntimeError("handle closed")
+        return self._h
+
+    def check(self, rc: int):
+        if rc != SOX_OK:
+            raise SoxError(rc, lib().sox_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().sox_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def sox_version() -> int:
+    return lib().sox_version()
+
+
+def sox_tau_grid(n_tau: int, beta: float):
+    tau = np.zeros(n_tau)
+    w = np.zeros(n_tau)
+    rc = lib().sox_tau_grid(int(n_tau), float(beta), tau.ctypes.data, w.ctypes.data)
+    if rc != SOX_OK:
+        raise SoxError(rc, "sox_tau_grid: bad arguments")
+    return tau, w
+
+
+def sox_profile_enable(h: Handle, enable: bool = True):
+    h.check(lib().sox_profile_enable(h.ptr, int(bool(enable))))
+
+
+def sox_profile_read(h: Handle, kernel: str | None = None):
+    """(launches, ms) of a hot kernel, or (total kernel launches, 0.0) for kernel=None."""
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    h.check(lib().sox_profile_read(h.ptr, kernel.encode() if kernel else None, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def sox_reserve(h: Handle, p: sox_problem):
+    h.check(lib().sox_reserve(h.ptr, ctypes.byref(p)))
+
+
+def thc_project_G(h: Handle, p: sox_problem, G, X, G_Rq=None, G_wP=None, G_PQ=None, stream=None):
+    h.check(lib().thc_project_G(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(G_Rq), _ptr(G_wP),
+                                _ptr(G_PQ), _stream(stream)))
+
+
+def sox_sigma(h: Handle, p: sox_problem, G, X, V, Sigma, stream=None):
+    h.check(lib().sox_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(Sigma),
+                            _stream(stream)))
+
+
+def sox_sigma_general(h: Handle, p: sox_problem, G, X, U1, U2, Sigma, stream=None):
+    h.check(lib().sox_sigma_general(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(U1), _ptr(U2),
+                                    _ptr(Sigma), _stream(stream)))
+
+
+def sosex_static_sigma(h: Handle, p: sox_problem, G, X, V, W0, Sigma, slot: int = 1, stream=None):
+    h.check(lib().sosex_static_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(W0),
+                                     int(slot), _ptr(Sigma), _stream(stream)))
+
+
+def sox_pi0(h: Handle, p: sox_problem, G, X, w, Pi0, stream=None):
+    h.check(lib().sox_pi0(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(w), _ptr(Pi0), _stream(stream)))
+
+
+def sox_w_static(h: Handle, p: sox_problem, V, Pi, W0, stream=None):
+    h.check(lib().sox_w_static(h.ptr, ctypes.byref(p), _ptr(V), _ptr(Pi), _ptr(W0), _stream(stream)))
+
+
+def phi_sox(h: Handle, p: sox_problem, G, X, V, w, phi, Sigma=None, stream=None):
+    h.check(lib().phi_sox(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(w), _ptr(phi),
+                          _ptr(Sigma), _stream(stream)))
+
+
+def phi_sox_backward(h: Handle, p: sox_problem, G, X, V, w, dphi, dG=None, dX=None, dV=None,
+                     stream=None):
+    h.check(lib().phi_sox_backward(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(w),
+                                   _ptr(dphi), _ptr(dG), _ptr(dX), _ptr(dV), _stream(stream)))
+
+
+def sosex_dynamic_sigma(h: Handle, p: sox_problem, G, X, V, Wd, T_fwd, T_inv, n_omega, Sigma,
+                        stream=None):
+    h.check(lib().sosex_dynamic_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(Wd),
+                                      _ptr(T_fwd), _ptr(T_inv), int(n_omega), _ptr(Sigma),
+                                      _stream(stream)))
+
+
+def sox_sigma_batch(h: Handle, probs, G, X, V, Sigma, stream=None):
+    count = len(probs)
+    arr = (sox_problem * count)(*probs)
+    mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
+    h.check(lib().sox_sigma_batch(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(Sigma), _stream(stream)))

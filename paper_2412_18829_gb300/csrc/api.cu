@@ -1,0 +1,679 @@
+// C-ABI entry points: handle lifecycle, argument validation, host/device
+// staging, and the orchestration of the THC-SOX chain (Sec. II C) on one stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "tc_path.h"
+
+using sox::Arena;
+using sox::GemmF64;
+using sox::Status;
+
+namespace {
+
+constexpr size_t kDefaultBudget = size_t(12) << 30;  // τ-chunking budget for intermediates
+
+Status validate(const sox_problem *p, bool need_molecule = true) {
+  if (!p) return {SOX_ERR_INVALID_ARG, "problem descriptor is NULL"};
+  if (p->n < 1 || p->n > SOX_MAX_N_AO) return {SOX_ERR_SHAPE, "n out of range [1, SOX_MAX_N_AO]"};
+  if (p->N < 1 || p->N > SOX_MAX_N_THC) return {SOX_ERR_SHAPE, "N out of range [1, SOX_MAX_N_THC]"};
+  if (p->n_tau < 2 || p->n_tau > SOX_MAX_N_TAU) return {SOX_ERR_SHAPE, "n_tau out of range [2, SOX_MAX_N_TAU]"};
+  if (p->n_spin != 1 && p->n_spin != 2) return {SOX_ERR_SHAPE, "n_spin must be 1 or 2"};
+  for (int d = 0; d < 3; ++d)
+    if (p->nk[d] < 1 || p->nk[d] > 64) return {SOX_ERR_SHAPE, "k-mesh entries must be in [1, 64]"};
+  if (p->dtype != SOX_REAL64 && p->dtype != SOX_COMPLEX128) return {SOX_ERR_INVALID_ARG, "unknown dtype"};
+  if (!(p->beta > 0.0) || !std::isfinite(p->beta)) return {SOX_ERR_INVALID_ARG, "beta must be finite and > 0"};
+  if (need_molecule) {
+    if (p->nk[0] * p->nk[1] * p->nk[2] != 1)
+      return {SOX_ERR_UNSUPPORTED, "k-point meshes (solids) are not implemented by this entry point"};
+    if (p->dtype != SOX_REAL64)
+      return {SOX_ERR_UNSUPPORTED, "complex data are not implemented by this entry point"};
+  }
+  return Status::ok();
+}
+
+int finish(sox_handle h, const Status &s) {
+  if (h) h->last_error = s.good() ? std::string() : s.msg;
+  return s.code;
+}
+
+// Whether a pointer is device-accessible (device or managed memory).
+Status is_device_ptr(const void *ptr, bool *dev) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *dev = false;
+    return Status::ok();
+  }
+  *dev = (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  return Status::ok();
+}
+
+struct Staged {
+  // inputs: device pointer to use; outputs: device pointer to write + host target
+  const double *in = nullptr;
+  double *out = nullptr;
+  double *host_out = nullptr;
+  size_t count = 0;
+  bool host = false;
+};
+
+class Call {
+ public:
+  Call(sox_handle h, void *stream) : h_(h), s_(reinterpret_cast<cudaStream_t>(stream)) {}
+  cudaStream_t stream() const { return s_; }
+
+  // Register an input (may be NULL when optional); returns where the kernels read it.
+  Status input(const double *p, size_t count, Staged *st) {
+    st->count = count;
+    if (!p) return Status::ok();
+    bool dev = false;
+    SOX_TRY(is_device_ptr(p, &dev));
+    st->host = !dev;
+    st->in = p;
+    if (st->host) staged_in_.push_back(st), stage_bytes_ += sox::aligned_bytes(count, 8);
+    return Status::ok();
+  }
+  Status output(double *p, size_t count, Staged *st) {
+    st->count = count;
+    if (!p) return Status::ok();
+    bool dev = false;
+    SOX_TRY(is_device_ptr(p, &dev));
+    st->host = !dev;
+    st->out = p;
+    if (st->host) {
+      st->host_out = p;
+      staged_out_.push_back(st);
+      stage_bytes_ += sox::aligned_bytes(count, 8);
+    }
+    return Status::ok();
+  }
+
+  // Ensure workspace >= compute_bytes + staging, then copy host inputs in.
+  Status begin(size_t compute_bytes, Arena *arena) {
+    size_t need = compute_bytes + stage_bytes_ + 4096;
+    if (need > h_->ws_bytes) {
+      if (h_->ws) {
+        SOX_CUDA_TRY(cudaDeviceSynchronize());
+        SOX_CUDA_TRY(cudaFree(h_->ws));
+        h_->ws = nullptr;
+        h_->ws_bytes = 0;
+      }
+      if (cudaMalloc(&h_->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return {SOX_ERR_OOM, "workspace allocation of " + std::to_string(need) + " bytes failed"};
+      }
+      h_->ws_bytes = need;
+    }
+    arena->base = static_cast<char *>(h_->ws);
+    arena->cap = h_->ws_bytes;
+    arena->off = 0;
+    for (Staged *st : staged_in_) {
+      double *d = arena->take<double>(st->count);
+      SOX_CUDA_TRY(cudaMemcpyAsync(d, st->in, st->count * 8, cudaMemcpyHostToDevice, s_));
+      st->in = d;
+    }
+    for (Staged *st : staged_out_) st->out = arena->take<double>(st->count);
+    return Status::ok();
+  }
+
+  Status end() {
+    for (Staged *st : staged_out_)
+      SOX_CUDA_TRY(cudaMemcpyAsync(st->host_out, st->out, st->count * 8, cudaMemcpyDeviceToHost, s_));
+    if (!staged_out_.empty()) SOX_CUDA_TRY(cudaStreamSynchronize(s_));
+    SOX_CUDA_TRY(cudaGetLastError());
+    return Status::ok();
+  }
+
+ private:
+  sox_handle h_;
+  cudaStream_t s_;
+  std::vector<Staged *> staged_in_, staged_out_;
+  size_t stage_bytes_ = 0;
+};
+
+Status bind_device(sox_handle h) {
+  int cur = -1;
+  SOX_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != h->device) SOX_CUDA_TRY(cudaSetDevice(h->device));
+  return Status::ok();
+}
+
+// --------------------------- FP64 orchestration ---------------------------
+
+struct Dims {
+  int n, N, T, S;
+  long long nn() const { return (long long)n * n; }
+};
+
+// Projections for cc tau points starting at t0 of one spin block (FP64).
+void project_chunk(sox_handle H, const double *Gs, const double *X, const Dims &d, int t0, int cc,
+                   double *GR, double *GWt, cudaStream_t s) {
+  GemmF64 g;  // GR[b][R][q] = sum_u X[R][u] G[t0+b][u][q]
+  g.M = d.N; g.Nc = d.n; g.K = d.n; g.batch = cc;
+  g.A = X; g.ai = d.n; g.ak = 1;
+  g.B = Gs + (long long)t0 * d.nn(); g.sB = d.nn(); g.bk = d.n; g.bj = 1;
+  g.C = GR; g.sC = (long long)d.N * d.n; g.ci = d.n; g.cj = 1;
+  GemmF64 h = g;  // GWt[b][P][w] = sum_p X[P][p] G[t0+b][w][p]
+  h.bk = 1; h.bj = d.n;
+  h.C = GWt;
+  sox::ProfScope ps(H, "project_f64", s, 2);
+  sox::launch_gemm_f64(g, s);
+  sox::launch_gemm_f64(h, s);
+}
+
+// Um[P][q][s] = sum_Q U[P][Q] X[Q][q] X[Q][s]   (Eq. U_contraction at k = 0)
+void mixed_tensor_f64(sox_handle H, const double *U, const double *X, const Dims &d, double *Y,
+                      double *Um, cudaStream_t s) {
+  GemmF64 g;
+  g.M = d.N; g.Nc = (int)d.nn(); g.K = d.N;
+  g.A = U; g.ai = d.N; g.ak = 1;
+  g.B = Y; g.bk = d.nn(); g.bj = 1;
+  g.C = Um; g.ci = d.nn(); g.cj = 1;
+  sox::ProfScope ps(H, "mixed_f64", s, 2);
+  sox::launch_pair_products_f64(X, Y, d.N, d.n, s);
+  sox::launch_gemm_f64(g, s);
+}
+
+int tau_chunk(const Dims &d, size_t per_tau_bytes, size_t fixed_bytes) {
+  size_t budget = kDefaultBudget > fixed_bytes ? kDefaultBudget - fixed_bytes : 0;
+  long long c = per_tau_bytes ? (long long)(budget / per_tau_bytes) : d.T;
+  if (c < 1) c = 1;
+  if (c > d.T) c = d.T;
+  return (int)c;
+}
+
+size_t sigma_fp64_bytes(const Dims &d, bool two_slots, int *chunk) {
+  size_t Nn2 = (size_t)d.N * d.nn();
+  size_t fixed = sox::aligned_bytes(Nn2, 8) * (two_slots ? 2 : 1);
+  size_t per_tau = 8 * (Nn2 + 3 * (size_t)d.N * d.n + (size_t)d.N * d.N) + 1024;
+  int c = tau_chunk(d, per_tau, fixed);
+  if (chunk) *chunk = c;
+  return fixed + sox::aligned_bytes(std::max<size_t>(Nn2 * c, Nn2), 8) +
+         4 * sox::aligned_bytes((size_t)c * d.N * std::max(d.n, d.N), 8);
+}
+
+// Sigma for every spin and tau point; U1 == U2 allowed (bare SOX).
+Status sigma_fp64(sox_handle H, const Dims &d, const double *G, const double *X, const double *U1,
+                  const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
+  const bool two = (U1 != U2);
+  int c = 1;
+  sigma_fp64_bytes(d, two, &c);
+  const size_t Nn2 = (size_t)d.N * d.nn();
+  double *Um1 = ar.take<double>(Nn2);
+  double *Um2 = two ? ar.take<double>(Nn2) : Um1;
+  double *big = ar.take<double>(std::max<size_t>(Nn2 * c, Nn2));
+  double *GR = ar.take<double>((size_t)c * d.N * d.n);
+  double *GWt = ar.take<double>((size_t)c * d.N * d.n);
+  double *Dm = ar.take<double>((size_t)c * d.N * d.N);
+  double *Tm = ar.take<double>((size_t)c * d.N * d.n);
+  if (!Tm) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  mixed_tensor_f64(H, U1, X, d, big, Um1, s);
+  if (two) mixed_tensor_f64(H, U2, X, d, big, Um2, s);
+  for (int sp = 0; sp < d.S; ++sp) {
+    const double *Gs = G + (long long)sp * d.T * d.nn();
+    double *Ss = Sigma + (long long)sp * d.T * d.nn();
+    for (int t0 = 0; t0 < d.T; t0 += c) {
+      int cc = std::min(c, d.T - t0);
+      project_chunk(H, Gs, X, d, t0, cc, GR, GWt, s);
+      // A[b][v][(P,q)] = sum_s G(-tau)[s][v] Um1[(P,q)][s],  G(-tau_j) = -G(tau_{T-1-j})
+      GemmF64 a;
+      a.M = d.n; a.Nc = d.N * d.n; a.K = d.n; a.batch = cc;
+      a.A = Gs + (long long)(d.T - 1 - t0) * d.nn(); a.sA = -d.nn(); a.ai = 1; a.ak = d.n;
+      a.B = Um1; a.bk = 1; a.bj = d.n;
+      a.C = big; a.sC = (long long)Nn2; a.ci = (long long)d.N * d.n; a.cj = 1;
+      a.alpha = -1.0;
+      {
+        sox::ProfScope ps(H, "A_f64", s);
+        sox::launch_gemm_f64(a, s);
+      }
+      {  // D[b][P][R] = sum_v B o C
+        sox::ProfScope ps(H, "sox_bcd", s);
+        sox::launch_sox_bcd_f64(big, (long long)Nn2, GR, (long long)d.N * d.n, GWt,
+                                (long long)d.N * d.n, Um2, Dm, (long long)d.N * d.N, d.n, d.N, cc, s);
+      }
+      // T[b][R][r] = sum_P D[b][P][R] X[P][r]
+      GemmF64 t;
+      t.M = d.N; t.Nc = d.n; t.K = d.N; t.batch = cc;
+      t.A = Dm; t.sA = (long long)d.N * d.N; t.ai = 1; t.ak = d.N;
+      t.B = X; t.bk = d.n; t.bj = 1;
+      t.C = Tm; t.sC = (long long)d.N * d.n; t.ci = d.n; t.cj = 1;
+      // Sigma[t][r] = -sum_R X[R][t] T[R][r]
+      GemmF64 b;
+      b.M = d.n; b.Nc = d.n; b.K = d.N; b.batch = cc;
+      b.A = X; b.ai = 1; b.ak = d.n;
+      b.B = Tm; b.sB = (long long)d.N * d.n; b.bk = d.n; b.bj = 1;
+      b.C = Ss + (long long)t0 * d.nn(); b.sC = d.nn(); b.ci = d.n; b.cj = 1;
+      b.alpha = -1.0;
+      {
+        sox::ProfScope ps(H, "backproject_f64", s, 2);
+        sox::launch_gemm_f64(t, s);
+        sox::launch_gemm_f64(b, s);
+      }
+    }
+  }
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+Dims dims_of(const sox_problem *p) { return Dims{p->n, p->N, p->n_tau, p->n_spin}; }
+
+size_t sigma_bytes(sox_handle h, const Dims &d, bool two) {
+  if (h->precision == SOX_PREC_F16X2) return sox::tc_sigma_bytes(h, d.n, d.N, d.T, d.S, two);
+  return sigma_fp64_bytes(d, two, nullptr);
+}
+
+Status sigma_any(sox_handle h, const Dims &d, const double *G, const double *X, const double *U1,
+                 const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
+  if (h->precision == SOX_PREC_F16X2)
+    return sox::tc_sigma(h, d.n, d.N, d.T, d.S, G, X, U1, U2, Sigma, ar, s);
+  return sigma_fp64(h, d, G, X, U1, U2, Sigma, ar, s);
+}
+
+Status run_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                 const double *U1, const double *U2, double *Sigma, void *stream) {
+  if (!h) return {SOX_ERR_INVALID_ARG, "handle is NULL"};
+  SOX_TRY(validate(p));
+  if (!G || !X || !U1 || !U2 || !Sigma) return {SOX_ERR_INVALID_ARG, "a required tensor pointer is NULL"};
+  SOX_TRY(bind_device(h));
+  const Dims d = dims_of(p);
+  Call call(h, stream);
+  Staged sG, sX, s1, s2, sS;
+  SOX_TRY(call.input(G, (size_t)d.S * d.T * d.nn(), &sG));
+  SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+  SOX_TRY(call.input(U1, (size_t)d.N * d.N, &s1));
+  const bool same = (U1 == U2);
+  if (!same) SOX_TRY(call.input(U2, (size_t)d.N * d.N, &s2));
+  SOX_TRY(call.output(Sigma, (size_t)d.S * d.T * d.nn(), &sS));
+  Arena ar;
+  SOX_TRY(call.begin(sigma_bytes(h, d, !same), &ar));
+  const double *u2 = same ? s1.in : s2.in;
+  SOX_TRY(sigma_any(h, d, sG.in, sX.in, s1.in, u2, sS.out, ar, call.stream()));
+  return call.end();
+}
+
+}  // namespace
+
+// ================================ C ABI ===================================
+extern "C" {
+
+int sox_version(void) { return 100; }
+
+int sox_create(sox_handle *out, const sox_options *opt) {
+  if (!out) return SOX_ERR_INVALID_ARG;
+  *out = nullptr;
+  sox_options o{SOX_PREC_FP64, 0, 0};
+  if (opt) o = *opt;
+  if (o.precision != SOX_PREC_FP64 && o.precision != SOX_PREC_F16X2) return SOX_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return SOX_ERR_CUDA;
+  }
+  if (o.device < 0 || o.device >= ndev) return SOX_ERR_INVALID_ARG;
+  sox_context *h = new (std::nothrow) sox_context();
+  if (!h) return SOX_ERR_OOM;
+  h->device = o.device;
+  h->precision = o.precision;
+  h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1LL << 26);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(o.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess ||
+      cudaMalloc(&h->d_status, 64) != cudaSuccess || cudaMemset(h->d_status, 0, 64) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return SOX_ERR_CUDA;
+  }
+  if (prev >= 0 && prev != o.device) cudaSetDevice(prev);
+  *out = h;
+  return SOX_OK;
+}
+
+int sox_destroy(sox_handle h) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  sox::tc_release(h);
+  sox_profile_enable(h, 0);
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_status) cudaFree(h->d_status);
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  delete h;
+  return SOX_OK;
+}
+
+int sox_profile_enable(sox_handle h, int enable) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  for (auto &kv : h->prof_events)
+    for (auto &e : kv.second) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  h->prof_events.clear();
+  h->launches = 0;
+  h->prof = enable != 0;
+  return SOX_OK;
+}
+
+int sox_profile_read(sox_handle h, const char *kernel, long long *launches, double *ms) {
+  if (!h || !launches || !ms) return SOX_ERR_INVALID_ARG;
+  *launches = 0;
+  *ms = 0.0;
+  if (!kernel) {
+    *launches = h->launches;
+    return SOX_OK;
+  }
+  cudaSetDevice(h->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return finish(h, {SOX_ERR_CUDA, "device sync failed"});
+  auto it = h->prof_events.find(kernel);
+  if (it == h->prof_events.end()) return SOX_OK;
+  double tot = 0.0;
+  for (auto &e : it->second) {
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, e.first, e.second) != cudaSuccess) {
+      cudaGetLastError();
+      return finish(h, {SOX_ERR_CUDA, "cudaEventElapsedTime failed"});
+    }
+    tot += f;
+  }
+  *launches = (long long)it->second.size();
+  *ms = tot;
+  return SOX_OK;
+}
+
+const char *sox_last_error(sox_handle h) { return h ? h->last_error.c_str() : "handle is NULL"; }
+
+int sox_reserve(sox_handle h, const sox_problem *p) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = validate(p);
+  if (st.good()) st = bind_device(h);
+  if (st.good()) {
+    const Dims d = dims_of(p);
+    size_t need = sigma_bytes(h, d, true);
+    size_t io = 8 * ((size_t)2 * d.S * d.T * d.nn() + (size_t)d.N * d.n + 2 * (size_t)d.N * d.N);
+    Call call(h, nullptr);
+    Arena ar;
+    st = call.begin(need + io, &ar);
+  }
+  return finish(h, st);
+}
+
+int sox_tau_grid(int n_tau, double beta, double *tau, double *w) {
+  if (n_tau < 2 || n_tau > SOX_MAX_N_TAU || !(beta > 0.0) || !tau || !w) return SOX_ERR_INVALID_ARG;
+  const int M = n_tau - 1;
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < n_tau; ++j) tau[j] = 0.5 * beta * (1.0 - std::cos(pi * j / M));
+  tau[0] = 0.0;
+  tau[M] = beta;
+  for (int j = 0; j < n_tau / 2; ++j) tau[M - j] = beta - tau[j];
+  if (n_tau % 2) tau[M / 2] = 0.5 * beta;
+  // Clenshaw-Curtis weights on [-1, 1] (cosine-series form), scaled by beta/2
+  for (int j = 0; j < n_tau; ++j) {
+    double s = 1.0;
+    for (int k = 1; k <= M / 2; ++k) {
+      double b = (2 * k == M) ? 1.0 : 2.0;
+      s -= b * std::cos(2.0 * pi * (double)j * k / M) / (4.0 * k * k - 1.0);
+    }
+    double c = (j == 0 || j == M) ? 1.0 : 2.0;
+    w[j] = 0.5 * beta * c * s / M;
+  }
+  for (int j = 0; j < n_tau / 2; ++j) {
+    double a = 0.5 * (w[j] + w[M - j]);
+    w[j] = w[M - j] = a;
+  }
+  return SOX_OK;
+}
+
+int thc_project_G(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                  double *G_Rq, double *G_wP, double *G_PQ, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!G || !X || (!G_Rq && !G_wP && !G_PQ)) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    const size_t nb = (size_t)d.S * d.T;
+    Call call(h, stream);
+    Staged sG, sX, oR, oW, oP;
+    SOX_TRY(call.input(G, nb * d.nn(), &sG));
+    SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+    SOX_TRY(call.output(G_Rq, nb * d.N * d.n, &oR));
+    SOX_TRY(call.output(G_wP, nb * d.N * d.n, &oW));
+    SOX_TRY(call.output(G_PQ, nb * d.N * d.N, &oP));
+    Arena ar;
+    SOX_TRY(call.begin(G_PQ && !G_Rq ? sox::aligned_bytes(nb * d.N * d.n, 8) : 0, &ar));
+    double *gr = oR.out ? oR.out : (G_PQ ? ar.take<double>(nb * d.N * d.n) : nullptr);
+    cudaStream_t s = call.stream();
+    GemmF64 g;  // GR[b][R][q] = sum_u X[R][u] G[b][u][q]
+    g.M = d.N; g.Nc = d.n; g.K = d.n; g.batch = (int)nb;
+    g.A = sX.in; g.ai = d.n; g.ak = 1;
+    g.B = sG.in; g.sB = d.nn(); g.bk = d.n; g.bj = 1;
+    g.C = gr; g.sC = (long long)d.N * d.n; g.ci = d.n; g.cj = 1;
+    sox::ProfScope ps(h, "project_f64", s, (gr ? 1 : 0) + (oW.out ? 1 : 0) + (oP.out ? 1 : 0));
+    if (gr) sox::launch_gemm_f64(g, s);
+    if (oW.out) {  // G_wP[b][w][P] = sum_p G[b][w][p] X[P][p]
+      GemmF64 w;
+      w.M = d.n; w.Nc = d.N; w.K = d.n; w.batch = (int)nb;
+      w.A = sG.in; w.sA = d.nn(); w.ai = d.n; w.ak = 1;
+      w.B = sX.in; w.bk = 1; w.bj = d.n;
+      w.C = oW.out; w.sC = (long long)d.N * d.n; w.ci = d.N; w.cj = 1;
+      sox::launch_gemm_f64(w, s);
+    }
+    if (oP.out) {  // G_PQ[b][P][Q] = sum_q GR[b][P][q] X[Q][q]
+      GemmF64 q;
+      q.M = d.N; q.Nc = d.N; q.K = d.n; q.batch = (int)nb;
+      q.A = gr; q.sA = (long long)d.N * d.n; q.ai = d.n; q.ak = 1;
+      q.B = sX.in; q.bk = 1; q.bj = d.n;
+      q.C = oP.out; q.sC = (long long)d.N * d.N; q.ci = d.N; q.cj = 1;
+      sox::launch_gemm_f64(q, s);
+    }
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+              const double *V, double *Sigma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  return finish(h, run_sigma(h, p, G, X, V, V, Sigma, stream));
+}
+
+int sox_sigma_general(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                      const double *U1, const double *U2, double *Sigma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  return finish(h, run_sigma(h, p, G, X, U1, U2, Sigma, stream));
+}
+
+int sosex_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                       const double *V, const double *W0, int slot, double *Sigma,
+                       void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  if (slot != 1 && slot != 2) return finish(h, {SOX_ERR_INVALID_ARG, "slot must be 1 or 2"});
+  if (V == W0 && V) return finish(h, {SOX_ERR_INVALID_ARG, "V and W0 must be distinct buffers"});
+  const double *u1 = slot == 1 ? W0 : V, *u2 = slot == 1 ? V : W0;
+  return finish(h, run_sigma(h, p, G, X, u1, u2, Sigma, stream));
+}
+
+int sox_pi0(sox_handle h, const sox_problem *p, const double *G, const double *X,
+            const double *w, double *Pi0, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!G || !X || !w || !Pi0) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    Call call(h, stream);
+    Staged sG, sX, sw, oP;
+    SOX_TRY(call.input(G, (size_t)d.S * d.T * d.nn(), &sG));
+    SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+    SOX_TRY(call.input(w, (size_t)d.T, &sw));
+    SOX_TRY(call.output(Pi0, (size_t)d.S * d.N * d.N, &oP));
+    const size_t gpq = (size_t)d.T * d.N * d.N, gr = (size_t)d.T * d.N * d.n;
+    Arena ar;
+    SOX_TRY(call.begin(sox::aligned_bytes(gpq, 8) + sox::aligned_bytes(gr, 8), &ar));
+    double *GPQ = ar.take<double>(gpq);
+    double *GR = ar.take<double>(gr);
+    cudaStream_t s = call.stream();
+    for (int sp = 0; sp < d.S; ++sp) {
+      const double *Gs = sG.in + (long long)sp * d.T * d.nn();
+      GemmF64 g;
+      g.M = d.N; g.Nc = d.n; g.K = d.n; g.batch = d.T;
+      g.A = sX.in; g.ai = d.n; g.ak = 1;
+      g.B = Gs; g.sB = d.nn(); g.bk = d.n; g.bj = 1;
+      g.C = GR; g.sC = (long long)d.N * d.n; g.ci = d.n; g.cj = 1;
+      sox::ProfScope ps0(h, "project_f64", s, 2);
+      sox::launch_gemm_f64(g, s);
+      GemmF64 q;
+      q.M = d.N; q.Nc = d.N; q.K = d.n; q.batch = d.T;
+      q.A = GR; q.sA = (long long)d.N * d.n; q.ai = d.n; q.ak = 1;
+      q.B = sX.in; q.bk = 1; q.bj = d.n;
+      q.C = GPQ; q.sC = (long long)d.N * d.N; q.ci = d.N; q.cj = 1;
+      sox::launch_gemm_f64(q, s);
+      sox::ProfScope ps1(h, "pi0_reduce", s);
+      sox::launch_pi0_reduce(GPQ, sw.in, d.N, d.T, oP.out + (long long)sp * d.N * d.N, s);
+    }
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_w_static(sox_handle h, const sox_problem *p, const double *V, const double *Pi,
+                 double *W0, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!V || !Pi || !W0) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const int N = p->N;
+    Call call(h, stream);
+    Staged sV, sP, oW;
+    SOX_TRY(call.input(V, (size_t)N * N, &sV));
+    SOX_TRY(call.input(Pi, (size_t)N * N, &sP));
+    SOX_TRY(call.output(W0, (size_t)N * N, &oW));
+    Arena ar;
+    SOX_TRY(call.begin(sox::aligned_bytes((size_t)2 * N * N, 8) + 256, &ar));
+    double *Aug = ar.take<double>((size_t)2 * N * N);
+    int *info = ar.take<int>(4);
+    cudaStream_t s = call.stream();
+    SOX_CUDA_TRY(cudaMemsetAsync(info, 0, 4 * sizeof(int), s));
+    {
+      sox::ProfScope ps(h, "w_static_gj", s, 3 + 2 * N);
+      sox::launch_build_gj_system(sV.in, sP.in, Aug, N, s);
+      for (int k = 0; k < N; ++k) sox::launch_gj_step(Aug, N, k, info, s);
+      sox::launch_copy_right_half(Aug, oW.out, N, s);
+    }
+    int hinfo[4] = {0, 0, 0, 0};
+    SOX_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+    SOX_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo[1]) return {SOX_ERR_INVALID_ARG, "1 - V Pi is singular"};
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int phi_sox(sox_handle h, const sox_problem *p, const double *G, const double *X,
+            const double *V, const double *w, double *phi, double *Sigma_out, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!G || !X || !V || !w || !phi) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    const size_t nsig = (size_t)d.S * d.T * d.nn();
+    Call call(h, stream);
+    Staged sG, sX, sV, sw, oPhi, oS;
+    SOX_TRY(call.input(G, nsig, &sG));
+    SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+    SOX_TRY(call.input(V, (size_t)d.N * d.N, &sV));
+    SOX_TRY(call.input(w, (size_t)d.T, &sw));
+    SOX_TRY(call.output(phi, (size_t)d.S, &oPhi));
+    SOX_TRY(call.output(Sigma_out, nsig, &oS));
+    Arena ar;
+    SOX_TRY(call.begin(sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8) +
+                           sox::aligned_bytes((size_t)d.S * d.T, 8), &ar));
+    double *sig = oS.out ? oS.out : ar.take<double>(nsig);
+    double *part = ar.take<double>((size_t)d.S * d.T);
+    cudaStream_t s = call.stream();
+    SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, sig, ar, s));
+    {
+      sox::ProfScope ps(h, "phi_trace", s, 2);
+      sox::launch_trace_sigma_gminus(sig, sG.in, d.n, d.T, d.S, part, s);
+      sox::launch_phi_finish(part, sw.in, d.T, d.S, oPhi.out, s);
+    }
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                     const double *V, const double *w, const double *dphi, double *dG,
+                     double *dX, double *dV, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!G || !X || !V || !w || !dphi) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    if (dX || dV) return {SOX_ERR_UNSUPPORTED, "dPhi/dX and dPhi/dV are not implemented in this build"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    const size_t nsig = (size_t)d.S * d.T * d.nn();
+    Call call(h, stream);
+    Staged sG, sX, sV, sw, sd, oG;
+    SOX_TRY(call.input(G, nsig, &sG));
+    SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+    SOX_TRY(call.input(V, (size_t)d.N * d.N, &sV));
+    SOX_TRY(call.input(w, (size_t)d.T, &sw));
+    SOX_TRY(call.input(dphi, (size_t)d.S, &sd));
+    SOX_TRY(call.output(dG, nsig, &oG));
+    Arena ar;
+    SOX_TRY(call.begin(sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8), &ar));
+    double *sig = ar.take<double>(nsig);
+    cudaStream_t s = call.stream();
+    if (oG.out) {
+      SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, sig, ar, s));
+      sox::ProfScope ps(h, "dG_identity", s);
+      sox::launch_dG_from_sigma(sig, sw.in, sd.in, d.n, d.T, d.S, oG.out, s);
+    }
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                        const double *V, const double *Wd, const double *T_fwd,
+                        const double *T_inv, int n_omega, double *Sigma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  (void)G; (void)X; (void)V; (void)Wd; (void)T_fwd; (void)T_inv; (void)n_omega; (void)Sigma;
+  (void)stream;
+  Status st = validate(p);
+  if (st.good()) st = {SOX_ERR_UNSUPPORTED, "dynamically screened SOSEX is not implemented in this build"};
+  return finish(h, st);
+}
+
+int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs, const double *const *G,
+                    const double *const *X, const double *const *V, double *const *Sigma,
+                    void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && (!probs || !G || !X || !V || !Sigma)))
+    return finish(h, {SOX_ERR_INVALID_ARG, "bad batch arrays"});
+  for (int i = 0; i < count; ++i) {
+    Status st = run_sigma(h, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], stream);
+    if (!st.good()) {
+      st.msg = "instance " + std::to_string(i) + ": " + st.msg;
+      return finish(h, st);
+    }
+  }
+  return finish(h, Status::ok());
+}
+
+}  // extern "C"

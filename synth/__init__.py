@@ -47,6 +47,8 @@ def tau_nodes(n_tau: int, beta: float) -> np.ndarray:
     # exact mirror symmetry tau_{n-1-j} = beta - tau_j
     half = n_tau // 2
     t[n_tau - 1 - np.arange(half)] = beta - t[np.arange(half)]
+    if n_tau % 2:
+        t[half] = 0.5 * beta
     return t
 
 

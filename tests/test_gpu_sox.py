@@ -1,0 +1,170 @@
+"""GPU parity of SOX / SOSEX-stat / projections through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import grid, screening, sox, thc
+from gpu_common import check, pkg_built, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+PRECS = ["fp64", "f16x2"]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    pkg = pkg_built()
+    handles = {p: pkg.Handle(p) for p in PRECS}
+    yield torch, pkg, handles
+    for h in handles.values():
+        h.close()
+
+
+def _sigma(env, prec, w, U1=None, U2=None, slot=None):
+    torch, pkg, hs = env
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    S = torch.full_like(G, float("nan"))
+    if slot is not None:
+        (W,) = to_dev(torch, U1)
+        pkg.sosex_static_sigma(hs[prec], p, G, X, V, W, S, slot=slot)
+    elif U1 is not None:
+        A1, A2 = to_dev(torch, U1, U2)
+        pkg.sox_sigma_general(hs[prec], p, G, X, A1, A2, S)
+    else:
+        pkg.sox_sigma(hs[prec], p, G, X, V, S)
+    torch.cuda.synchronize()
+    return S.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,N,n_tau,n_spin", [(13, 70, 6, 2), (1, 1, 4, 1), (5, 3, 2, 1), (33, 130, 5, 1),
+                                              (64, 128, 3, 1)])
+def test_sox_small_and_ragged(env, prec, n, N, n_tau, n_spin):
+    w = synth.molecule(11, n, N, n_tau, 20.0, n_spin=n_spin, name="ragged")
+    ref = sox.sox_sigma(w.X, w.V, w.G).real
+    check(_sigma(env, prec, w), ref, prec, f"n={n} N={N}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sox_c0_all_tau(env, prec):
+    w = synth.config(0)
+    ref = sox.sox_sigma(w.X, w.V, w.G).real
+    err, scale = check(_sigma(env, prec, w), ref, prec, "c0")
+    print(f"c0 {prec}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sox_c1_full_size_sampled_tau(env, prec):
+    """c1 (n=120, N=600, 80 tau, 2 spins) in the benchmark's launch; oracle on sampled tau."""
+    w = synth.config(1)
+    out = _sigma(env, prec, w)
+    assert np.isfinite(out).all()
+    taus = [0, 17, 40, 79]
+    for s in range(w.n_spin):
+        ref = sox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
+        err, scale = check(out[s, 0, taus], ref, prec, f"c1 spin {s}")
+        print(f"c1 {prec} spin {s}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_general_two_interactions_nonsymmetric(env, prec):
+    w = synth.molecule(12, 19, 75, 5, 10.0, n_spin=1)
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal((w.N, w.N)) / w.N
+    U1 = np.ascontiguousarray((z @ z.T + 0.3 * z)[None])     # non-symmetric on purpose
+    U2 = np.ascontiguousarray(w.V)
+    ref = np.stack([sox.sigma_tau(w.X[0], U1[0], U2[0], w.G[0, 0]).real])[:, None]
+    check(_sigma(env, prec, w, U1, U2), ref, prec, "general")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("slot", [1, 2])
+def test_sosex_static_c0(env, prec, slot):
+    w = synth.config(0)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    Pi = screening.pi0_quadrature(w.X[0], w.G[0, 0], wt)
+    W = np.ascontiguousarray(screening.w_static(w.V[0], 0.5 * (Pi + Pi.T))[None])
+    ref = sox.sosex_static_sigma(w.X, w.V, W, w.G, slot=slot).real
+    check(_sigma(env, prec, w, W, slot=slot), ref, prec, f"sosex slot {slot}")
+
+
+def test_thc_project_G(env):
+    torch, pkg, hs = env
+    w = synth.molecule(13, 21, 90, 4, 10.0, n_spin=2)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X = to_dev(torch, w.G, w.X)
+    shp = (w.n_spin, 1, w.n_tau)
+    GR = torch.empty(*shp, w.N, w.n, dtype=torch.float64, device="cuda")
+    GW = torch.empty(*shp, w.n, w.N, dtype=torch.float64, device="cuda")
+    GPQ = torch.empty(*shp, w.N, w.N, dtype=torch.float64, device="cuda")
+    pkg.thc_project_G(hs["fp64"], p, G, X, GR, GW, GPQ)
+    torch.cuda.synchronize()
+    for s in range(w.n_spin):
+        for j in range(w.n_tau):
+            g = w.G[s, 0, j]
+            np.testing.assert_allclose(GR[s, 0, j].cpu().numpy(), thc.project_left(w.X[0], g), atol=1e-14)
+            np.testing.assert_allclose(GW[s, 0, j].cpu().numpy(), thc.project_right(w.X[0], g), atol=1e-14)
+            np.testing.assert_allclose(GPQ[s, 0, j].cpu().numpy(), thc.project_full(w.X[0], g), atol=1e-13)
+
+
+def test_pi0_and_w_static(env):
+    torch, pkg, hs = env
+    w = synth.config(0)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    Pi = torch.empty(1, w.N, w.N, dtype=torch.float64, device="cuda")
+    pkg.sox_pi0(hs["fp64"], p, G, X, tw, Pi)
+    torch.cuda.synchronize()
+    ref = screening.pi0_quadrature(w.X[0], w.G[0, 0], wt)
+    np.testing.assert_allclose(Pi[0].cpu().numpy(), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    W = torch.empty(w.N, w.N, dtype=torch.float64, device="cuda")
+    pkg.sox_w_static(hs["fp64"], p, V[0].contiguous(), Pi[0].contiguous(), W)
+    torch.cuda.synchronize()
+    refW = screening.w_static(w.V[0], Pi[0].cpu().numpy())
+    np.testing.assert_allclose(W.cpu().numpy(), refW, rtol=0, atol=1e-11 * np.abs(refW).max())
+
+
+def test_w_static_reports_singular_system(env):
+    torch, pkg, hs = env
+    N = 4
+    p = pkg.problem(2, N, 4, 1, 1.0)
+    V = torch.eye(N, dtype=torch.float64, device="cuda")
+    Pi = torch.eye(N, dtype=torch.float64, device="cuda")   # 1 - V Pi = 0
+    W = torch.empty_like(V)
+    with pytest.raises(pkg.SoxError) as e:
+        pkg.sox_w_static(hs["fp64"], p, V, Pi, W)
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_buffers_through_the_c_abi(env, prec):
+    torch, pkg, hs = env
+    w = synth.molecule(14, 17, 66, 5, 10.0, n_spin=1)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    S = np.full_like(w.G, np.nan)
+    pkg.sox_sigma(hs[prec], p, w.G, w.X, w.V, S)
+    check(S, sox.sox_sigma(w.X, w.V, w.G).real, prec, "host buffers")
+
+
+def test_error_paths(env):
+    torch, pkg, hs = env
+    h = hs["fp64"]
+    G = torch.zeros(1, 1, 4, 3, 3, dtype=torch.float64, device="cuda")
+    X = torch.zeros(1, 5, 3, dtype=torch.float64, device="cuda")
+    V = torch.zeros(1, 5, 5, dtype=torch.float64, device="cuda")
+    S = torch.zeros_like(G)
+    bad = [pkg.problem(0, 5, 4), pkg.problem(3, 5, 1), pkg.problem(3, 5, 4, n_spin=3),
+           pkg.problem(3, 5, 4, beta=-1.0), pkg.problem(3, 5, 4, nk=(2, 1, 1)),
+           pkg.problem(3, 5, 4, dtype=1), pkg.problem(2000, 5, 4)]
+    codes = []
+    for p in bad:
+        with pytest.raises(pkg.SoxError) as e:
+            pkg.sox_sigma(h, p, G, X, V, S)
+        codes.append(e.value.code)
+    assert codes == [2, 2, 2, 1, 3, 3, 2]
+    with pytest.raises(pkg.SoxError):
+        pkg.sox_sigma(h, pkg.problem(3, 5, 4), G, X, V, None)
+    with pytest.raises(pkg.SoxError):
+        pkg.sosex_static_sigma(h, pkg.problem(3, 5, 4), G, X, V, V, S, slot=3)
