@@ -111,6 +111,11 @@ SOX_API const char *sox_last_error(sox_handle h);
 SOX_API int sox_profile_enable(sox_handle h, int enable);
 SOX_API int sox_profile_read(sox_handle h, const char *kernel, long long *launches, double *ms);
 
+/* Synchronise the handle's device and report device-side wait failures:
+ * SOX_ERR_TIMEOUT if any kernel of an earlier call on this handle gave up a
+ * bounded wait (its results are then invalid; the status is cleared). */
+SOX_API int sox_check_device(sox_handle h);
+
 /* Grow the workspace for problem p now (outside any graph capture). */
 SOX_API int sox_reserve(sox_handle h, const sox_problem *p);
 

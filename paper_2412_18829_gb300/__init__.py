@@ -16,6 +16,7 @@ from ._binding import (  # noqa: F401
     problem,
     sosex_dynamic_sigma,
     sosex_static_sigma,
+    sox_check_device,
     sox_pi0,
     sox_profile_enable,
     sox_profile_read,

@@ -47,6 +47,7 @@ _SIGS = {
     "sox_destroy": ([_P], _I),
     "sox_last_error": ([_P], ctypes.c_char_p),
     "sox_reserve": ([_P, ctypes.POINTER(sox_problem)], _I),
+    "sox_check_device": ([_P], _I),
     "sox_profile_enable": ([_P, _I], _I),
     "sox_profile_read": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _I),
     "sox_tau_grid": ([_I, ctypes.c_double, _P, _P], _I),
@@ -172,6 +173,10 @@ def sox_tau_grid(n_tau: int, beta: float):
     if rc != SOX_OK:
         raise SoxError(rc, "sox_tau_grid: bad arguments")
     return tau, w
+
+
+def sox_check_device(h: Handle):
+    h.check(lib().sox_check_device(h.ptr))
 
 
 def sox_profile_enable(h: Handle, enable: bool = True):

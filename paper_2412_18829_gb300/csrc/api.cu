@@ -320,7 +320,7 @@ int sox_create(sox_handle *out, const sox_options *opt) {
   if (!h) return SOX_ERR_OOM;
   h->device = o.device;
   h->precision = o.precision;
-  h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1LL << 26);
+  h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1LL << 22);
   int prev = -1;
   cudaGetDevice(&prev);
   if (cudaSetDevice(o.device) != cudaSuccess ||
@@ -390,6 +390,23 @@ int sox_profile_read(sox_handle h, const char *kernel, long long *launches, doub
   *launches = (long long)it->second.size();
   *ms = tot;
   return SOX_OK;
+}
+
+int sox_check_device(sox_handle h) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(bind_device(h));
+    SOX_CUDA_TRY(cudaDeviceSynchronize());
+    int word = 0;
+    SOX_CUDA_TRY(cudaMemcpy(&word, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (word) {
+      SOX_CUDA_TRY(cudaMemset(h->d_status, 0, sizeof(int)));
+      return {SOX_ERR_TIMEOUT, "a device-side wait reached its iteration cap (status word " +
+                                   std::to_string(word) + "); the affected results are invalid"};
+    }
+    return Status::ok();
+  }();
+  return finish(h, st);
 }
 
 const char *sox_last_error(sox_handle h) { return h ? h->last_error.c_str() : "handle is NULL"; }

@@ -1,0 +1,904 @@
+// Tensor-core (tcgen05) kernels of the split-precision path and their helpers.
+//
+// Split format: a row x of real numbers is stored as two FP16 rows (hi, lo)
+// with x * s = hi + lo, s a power of two chosen per row (or per group of rows)
+// so that max|x * s| lies in [1, 2).  A product of two split operands is
+// evaluated by three FP16 MMAs, hi*hi + hi*lo + lo*hi, accumulated in FP32.
+#include <cstdio>
+#include <string>
+
+#include "tc_common.cuh"
+#include "tc_kernels.h"
+
+namespace sox {
+
+using tc::smem_u32;
+
+bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                      uint32_t box0, uint32_t box1, std::string *err) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      if (err) *err = "cuTensorMapEncodeTiled entry point not available";
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  cuuint32_t box[3] = {box0, box1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+namespace {
+
+constexpr int kTile = 128;              // M and N of every MMA tile
+constexpr int kChunk = 64;              // K elements per TMA box (128 bytes of FP16)
+constexpr int kTileBytes = kTile * kChunk * 2;  // 16 KB
+constexpr int kStageBytes = 4 * kTileBytes;     // hi/lo of both operands
+constexpr int kStages = 3;
+constexpr int kThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t kIdesc = tc::idesc_f16_f32(kTile, kTile);
+
+struct Barriers {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Waits that let copies and MMAs in flight finish before the CTA exits (or frees
+// TMEM) keep a floor independent of the caller's cap, so a tiny cap cannot let
+// a TMA write land in shared memory the CTA no longer owns.
+__device__ __forceinline__ long long wind_down_limit(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
+
+__device__ __forceinline__ uint8_t *stage_ptr(uint8_t *smem, int s, int t) {
+  return smem + (size_t)s * kStageBytes + (size_t)t * kTileBytes;
+}
+
+// Issues the 3 x 4 MMAs of one 64-wide K chunk: acc (+)= (ahi + alo)(bhi + blo)^T minus lo*lo.
+// The small cross terms go first: the tensor core truncates every accumulation
+// step to FP32 (round toward zero), and each step into a large accumulator
+// costs up to one ulp, so the large hi*hi steps are kept last and fewest.
+__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first) {
+  const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kTileBytes;
+  const uint32_t b_hi = a_hi + 2 * kTileBytes, b_lo = a_hi + 3 * kTileBytes;
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+                (first && k == 0) ? 0u : 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
+}
+
+__device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_empty[b], epi_threads);
+    }
+    tc::mbar_init(&bar->drain, 1);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
+}
+
+// ============================================================================
+// Fused B / C / Hadamard-reduce (Sec. II C, the B, C and D steps):
+//   D[b][P][R] = sum_v (sum_q A[b][v][P][q] GR[b][R][q]) (sum_w GW[b][P][w] U2[v][R][w])
+// One 128 x 128 (P, R) tile per work item; B_v and C_v accumulate in TMEM
+// (double-buffered), the Hadamard product accumulates in registers, and only
+// D leaves the SM, written transposed and rescaled: Dt[b][R][P].
+// ============================================================================
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sox_bcd_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                 const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
+                 const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
+                 const __grid_constant__ CUtensorMap tmU_hi, const __grid_constant__ CUtensorMap tmU_lo,
+                 BcdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Barriers *bar = reinterpret_cast<Barriers *>(smem + kStages * kStageBytes);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tP = (a.N + kTile - 1) / kTile;
+  const int tiles_per_b = tP * tP;
+  const long long total = (long long)a.batch * tiles_per_b;
+  const int nk = a.Kp / kChunk;
+
+  setup_barriers(bar, 128);
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo); tc::prefetch_tmap(&tmGR_hi);
+    tc::prefetch_tmap(&tmGR_lo); tc::prefetch_tmap(&tmGW_hi); tc::prefetch_tmap(&tmGW_lo);
+    tc::prefetch_tmap(&tmU_hi); tc::prefetch_tmap(&tmU_lo);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      long long it = 0;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const int b = (int)(t / tiles_per_b);
+        const int r = (int)(t % tiles_per_b);
+        const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
+        for (int v = 0; v < a.n && !*abort; ++v) {
+          for (int half = 0; half < 2; ++half) {
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kStages);
+              const uint32_t ph = (uint32_t)((it / kStages) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+              tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+              const int x = kc * kChunk;
+              if (half == 0) {
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmGR_hi, &bar->full[s], x, R0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmGR_lo, &bar->full[s], x, R0, b);
+              } else {
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmGW_hi, &bar->full[s], x, P0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmGW_lo, &bar->full[s], x, P0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmU_hi, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmU_lo, &bar->full[s], x, R0, v);
+              }
+            }
+          }
+        }
+      }
+      // wind down: every stage issued must have landed before the CTA exits
+      for (int s = 0; s < kStages; ++s) {
+        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kStages) & 1);
+          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
+        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t acc = tmem + buf * 256 + half * 128;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kStages);
+              const uint32_t ph = (uint32_t)((it / kStages) & 1);
+              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0);
+              tc::mma_commit(&bar->empty[s]);
+            }
+          }
+          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+        }
+      }
+      // all MMAs complete before TMEM is released
+      tc::mma_commit(&bar->drain);
+      for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: D += B o C in registers ----------------
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;          // P offset inside the tile
+    long long acc_it = 0;
+    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      const int b = (int)(t / tiles_per_b);
+      const int r = (int)(t % tiles_per_b);
+      const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
+      float d[kTile];
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
+      bool ok = true;
+      for (int v = 0; v < a.n; ++v, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
+#pragma unroll
+        for (int c = 0; c < kTile; c += 16) {
+          float bv[16], cv[16];
+          tc::tmem_ld_32x32b_x16(base + c, bv);
+          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bar->acc_empty[buf]);
+      }
+      if (!ok) break;
+      // rescale and store transposed: Dt[b][R][P]
+      const int P = P0 + row;
+      if (P < a.N) {
+        const float rs = a.row_scale[(long long)b * a.N + P];
+        float *out = a.Dt + (long long)b * a.N * a.ldD + P;
+#pragma unroll
+        for (int j = 0; j < kTile; ++j) {
+          const int R = R0 + j;
+          if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================
+// Split GEMM with split output (the A intermediate, Sec. II C):
+//   C[b](i, j) = sum_k A[bA](i, k) B[bB](j, k)      (both operands K-major FP16 pairs)
+// 128 x 128 tiles, double-buffered TMEM accumulator.  The epilogue scales the
+// tile (kStoreSplit: out_scale[b]; kStoreSplitGroup: an exact power of two per
+// group of `group` columns, all of whose rows lie in the tile), splits it into
+// FP16 pairs in swizzled shared memory and writes it with TMA tensor stores into
+// the 4-D output [batch][M][n_groups][group] (box: 128 rows x 64 columns).
+// ============================================================================
+constexpr int kGStages = 2;
+constexpr int kStageOut = 4 * kTile * 64 * 2;   // hi/lo x two 64-column halves, 64 KB
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *src, int x, int y, int z, int w) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z), "r"(w)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_f16x2(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                 const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                 const __grid_constant__ CUtensorMap tmC_hi, const __grid_constant__ CUtensorMap tmC_lo,
+                 GemmTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *stage_out = smem + kGStages * kStageBytes;
+  Barriers *bar = reinterpret_cast<Barriers *>(stage_out + kStageOut);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tM = (a.M + kTile - 1) / kTile, tN = (a.Ncols + kTile - 1) / kTile;
+  const long long per_b = (long long)tM * tN;
+  const long long total = per_b * a.batch;
+  const int nk = a.Kp / kChunk;
+
+  setup_barriers(bar, 128);
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo);
+    tc::prefetch_tmap(&tmB_hi); tc::prefetch_tmap(&tmB_lo);
+    tc::prefetch_tmap(&tmC_hi); tc::prefetch_tmap(&tmC_lo);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long it = 0;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const int b = (int)(t / per_b);
+        const long long r = t % per_b;
+        const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
+        const int za = a.batchA_shared ? 0 : b, zb = a.batchB_shared ? 0 : b;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = (int)(it % kGStages);
+          const uint32_t ph = (uint32_t)((it / kGStages) & 1);
+          if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+          tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+          const int x = kc * kChunk;
+          tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, &bar->full[s], x, i0, za);
+          tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, &bar->full[s], x, i0, za);
+          tc::tma_load_3d(stage_ptr(smem, s, 2), &tmB_hi, &bar->full[s], x, j0, zb);
+          tc::tma_load_3d(stage_ptr(smem, s, 3), &tmB_lo, &bar->full[s], x, j0, zb);
+        }
+      }
+      for (int s = 0; s < kGStages; ++s) {
+        long long last = it - 1 - ((it - 1 - s) % kGStages + kGStages) % kGStages;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kGStages) & 1);
+          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t acc = tmem + buf * 128;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = (int)(it % kGStages);
+          const uint32_t ph = (uint32_t)((it / kGStages) & 1);
+          ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+          if (!ok) break;
+          tc::tc_fence_after();
+          issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0);
+          tc::mma_commit(&bar->empty[s]);
+        }
+        if (ok) tc::mma_commit(&bar->acc_full[buf]);
+      }
+      tc::mma_commit(&bar->drain);
+      for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;          // tile row = TMEM lane
+    const bool storer = (warp == 2 && lane == 0);
+    __shared__ float red[4][2];
+    long long acc_it = 0;
+    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++acc_it) {
+      const int b = (int)(t / per_b);
+      const long long r = t % per_b;
+      const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
+      const int buf = (int)(acc_it & 1);
+      const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+      if (!tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8)) break;
+      tc::tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 128;
+      const bool row_ok = (i0 + row) < a.M;
+      float sc0 = 1.f, sc1 = 1.f;
+      if (a.mode == kStoreSplit) {
+        sc0 = sc1 = a.out_scale[b];
+      } else {
+        float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < kTile; c += 32) {
+          float v[32];
+          tc::tmem_ld_32x32b_x32(base + c, v);
+          tc::tmem_ld_wait();
+          if (row_ok) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const bool second = (c + jj) >= a.group;
+              const float x = fabsf(v[jj]);
+              m0 = second ? m0 : fmaxf(m0, x);
+              m1 = second ? fmaxf(m1, x) : m1;
+            }
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+          m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        }
+        if (lane == 0) {
+          red[q][0] = m0;
+          red[q][1] = m1;
+        }
+        epi_sync();
+        sc0 = tc::pow2_floor_inv(fmaxf(fmaxf(red[0][0], red[1][0]), fmaxf(red[2][0], red[3][0])));
+        sc1 = tc::pow2_floor_inv(fmaxf(fmaxf(red[0][1], red[1][1]), fmaxf(red[2][1], red[3][1])));
+        if (warp == 2 && lane < 2 && lane * a.group < kTile) {
+          const int grp = (j0 + lane * a.group) / a.group;
+          if (grp < a.n_groups) a.group_scale[(long long)b * a.n_groups + grp] = lane ? sc1 : sc0;
+        }
+      }
+      // the previous tile's TMA stores must have read the staging buffer
+      if (storer) bulk_wait_read();
+      epi_sync();
+      // split into FP16 pairs, written to the 128-byte-swizzled staging tiles
+#pragma unroll
+      for (int c = 0; c < kTile; c += 32) {
+        float v[32];
+        tc::tmem_ld_32x32b_x32(base + c, v);
+        tc::tmem_ld_wait();
+        if (c == kTile - 32) {  // accumulator fully read: hand it back to the MMA warp
+          tc::tc_fence_before();
+          tc::mbar_arrive(&bar->acc_empty[buf]);
+        }
+        const int h = c / 64;
+        uint8_t *hi_tile = stage_out + (size_t)(0 * 2 + h) * (kTile * 128);
+        uint8_t *lo_tile = stage_out + (size_t)(1 * 2 + h) * (kTile * 128);
+#pragma unroll
+        for (int t16 = 0; t16 < 4; ++t16) {
+          uint32_t ph[4], pl[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int jj = t16 * 8 + e * 2;
+            const float s0 = (c + jj) >= a.group ? sc1 : sc0;
+            const float s1 = (c + jj + 1) >= a.group ? sc1 : sc0;
+            __half h0, l0, h1, l1;
+            tc::split_f16(v[jj] * s0, h0, l0);
+            tc::split_f16(v[jj + 1] * s1, h1, l1);
+            ph[e] = pack2(h0, h1);
+            pl[e] = pack2(l0, l1);
+          }
+          const int chunk = ((c % 64) / 8 + t16) ^ (row & 7);
+          *reinterpret_cast<uint4 *>(hi_tile + row * 128 + chunk * 16) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          *reinterpret_cast<uint4 *>(lo_tile + row * 128 + chunk * 16) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+      }
+      fence_proxy_async_smem();
+      epi_sync();
+      if (storer) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = j0 + h * 64;
+          if (col < a.Ncols) {
+            const int grp = col / a.group, x = col % a.group;
+            tma_store_4d(&tmC_hi, stage_out + (size_t)(0 * 2 + h) * (kTile * 128), x, grp, i0, b);
+            tma_store_4d(&tmC_lo, stage_out + (size_t)(1 * 2 + h) * (kTile * 128), x, grp, i0, b);
+          }
+        }
+        bulk_commit();
+      }
+    }
+    if (storer) bulk_wait_all();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 256);
+  }
+}
+
+// ------------------------------- split helpers ------------------------------
+
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One warp per output row: hi/lo of src row scaled to max in [1, 2); rows >= rows_valid are zero.
+__global__ void k_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid,
+                                 int rows_out, int L, int Kp, __half *hi, __half *lo, float *inv_scale,
+                                 int batch) {
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (gw >= (long long)rows_out * batch) return;
+  const int b = (int)(gw / rows_out), r = (int)(gw % rows_out);
+  __half *h = hi + ((long long)b * rows_out + r) * Kp;
+  __half *l = lo + ((long long)b * rows_out + r) * Kp;
+  if (r >= rows_valid) {
+    for (int k = lane; k < Kp; k += 32) h[k] = l[k] = __float2half(0.f);
+    return;
+  }
+  const double *x = src + b * bstride + r * ld;
+  float m = 0.f;
+  for (int k = lane; k < L; k += 32) m = fmaxf(m, (float)fabs(x[k]));
+  m = warp_max(m);
+  const float s = tc::pow2_floor_inv(m);
+  for (int k = lane; k < Kp; k += 32) {
+    __half a = __float2half(0.f), c = __float2half(0.f);
+    if (k < L) {
+      // scale in FP64 (exact: power of two), then round to the FP16 pair via FP32
+      const double xs = x[k] * (double)s;
+      const float f = (float)xs;
+      a = __float2half_rn(f);
+      c = __float2half_rn((float)(xs - (double)__half2float(a)));
+    }
+    h[k] = a;
+    l[k] = c;
+  }
+  if (lane == 0 && inv_scale) inv_scale[(long long)b * rows_valid + r] = 1.f / s;
+}
+
+__device__ float block_max(float v) {
+  __shared__ float red[32];
+  v = warp_max(v);
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x / 32) ? red[lane] : 0.f;
+    v = warp_max(v);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+// Mixed tensor U[P][q][s] (FP32, Kp x Kp per P) -> split with one scale per P, written as
+//   U1 layout [P][q][s]     (if u1_hi)   and/or   U2 layout [v][R][w] = U[R][v][w] (if u2_hi, v < n,
+//   R-stride NR rows)
+__global__ void k_split_mixed(const float *U, int N, int NR, int n, int Kp, __half *u1_hi, __half *u1_lo,
+                              __half *u2_hi, __half *u2_lo, float *inv_scale) {
+  const int P = blockIdx.x;
+  const long long blk = (long long)Kp * Kp;
+  const float *u = U + (long long)P * blk;
+  float m = 0.f;
+  for (long long e = threadIdx.x; e < blk; e += blockDim.x) m = fmaxf(m, fabsf(u[e]));
+  m = block_max(m);
+  const float s = tc::pow2_floor_inv(m);
+  for (long long e = threadIdx.x; e < blk; e += blockDim.x) {
+    __half hi, lo;
+    tc::split_f16(u[e] * s, hi, lo);
+    if (u1_hi) {
+      u1_hi[(long long)P * blk + e] = hi;
+      u1_lo[(long long)P * blk + e] = lo;
+    }
+    const int v = (int)(e / Kp), w = (int)(e % Kp);
+    if (u2_hi && v < n) {
+      const long long o = ((long long)v * NR + P) * Kp + w;
+      u2_hi[o] = hi;
+      u2_lo[o] = lo;
+    }
+  }
+  if (threadIdx.x == 0) inv_scale[P] = 1.f / s;
+}
+
+// Per batch b (spin, tau): Gm = G(-tau) = -G[T-1-j] as Gm^T[v][s] split with one scale
+// g = 2^-floor(log2 max|Gm|); out_scale = 2^-ceil(log2(2 max_v sum_s |g Gm[s][v]|)) bounds
+// the A products so their split stays in FP16 range.
+__global__ void k_prep_gminus(const double *G, int n, int T, int Kp, __half *hi, __half *lo,
+                              float *gscale, float *out_scale, int b0, int rows_out) {
+  const int b = blockIdx.x;
+  const int sp = (b0 + b) / T, j = (b0 + b) % T;
+  const double *g = G + ((long long)sp * T + (T - 1 - j)) * n * n;
+  float m = 0.f;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) m = fmaxf(m, (float)fabs(g[e]));
+  m = block_max(m);
+  const float sc = tc::pow2_floor_inv(m);
+  float cs = 0.f;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    float acc = 0.f;
+    for (int s = 0; s < n; ++s) acc += (float)fabs(g[(long long)s * n + v]) * sc;
+    cs = fmaxf(cs, acc);
+  }
+  cs = block_max(cs) * 2.f * 1.0001f;
+  // 2^-ceil(log2 cs)
+  int e;
+  const float f = frexpf(cs, &e);  // cs = f 2^e, f in [0.5, 1)
+  const float os = ldexpf(1.f, (f == 0.5f) ? -(e - 1) : -e);
+  __half *h = hi + (long long)b * rows_out * Kp;
+  __half *l = lo + (long long)b * rows_out * Kp;
+  for (int e2 = threadIdx.x; e2 < rows_out * Kp; e2 += blockDim.x) {
+    const int v = e2 / Kp, s = e2 % Kp;
+    __half a = __float2half(0.f), c = __float2half(0.f);
+    if (v < n && s < n) {
+      const double xs = -g[(long long)s * n + v] * (double)sc;
+      a = __float2half_rn((float)xs);
+      c = __float2half_rn((float)(xs - (double)__half2float(a)));
+    }
+    h[e2] = a;
+    l[e2] = c;
+  }
+  if (threadIdx.x == 0) {
+    gscale[b] = sc;
+    out_scale[b] = os;
+  }
+}
+
+// row/col factors of the fused kernel's output:
+//   row[b][P] = inv_u1[P] / (g[b] o[b]) * inv_gw[b][P],   col[b][R] = inv_gr[b][R] * inv_u2[R]
+__global__ void k_bcd_scales(const float *inv_u1, const float *gsc, const float *osc, const float *asc,
+                             int NR, const float *inv_gw, const float *inv_gr, const float *inv_u2, int N,
+                             int batch, float *row, float *col) {
+  const long long total = (long long)N * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / N), P = (int)(e % N);
+    const double a_sc = asc ? asc[(long long)b * NR + P] : osc[b];
+    // products of up to four clamped powers of two: form them in FP64 and clamp
+    // into the normal FP32 range (a factor outside it only scales values that
+    // are themselves outside FP32 range, i.e. zero at any tolerance)
+    const double r = (double)inv_u1[P] / ((double)gsc[b] * a_sc) * (double)inv_gw[e];
+    const double c = (double)inv_gr[e] * (double)inv_u2[P];
+    row[e] = (float)fmin(fmax(r, 0x1p-126), 0x1p126);
+    col[e] = (float)fmin(fmax(c, 0x1p-126), 0x1p126);
+  }
+}
+
+// Mixed THC tensor U[P][q][s] = sum_Q V[P][Q] X[Q][q] X[Q][s] (Eq. U_contraction at k = 0),
+// FP32 round-to-nearest accumulation over Q on CUDA cores; columns (q, s) run over
+// the padded Kp x Kp block and are zero outside [0, n)^2.  64 x 64 tile, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_mixed_f32(const double *V, const double *X, int N, int n, int Kp,
+                                                   float *U) {
+  __shared__ float sa[16][65];
+  __shared__ float sb[16][65];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int P0 = blockIdx.y * 64;
+  const long long c0 = (long long)blockIdx.x * 64;
+  const long long ncol = (long long)Kp * Kp;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < N; k0 += 16) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = tid + it * 256;
+      const int rr = e / 16, kk = e % 16;
+      const int P = P0 + rr, Q = k0 + kk;
+      sa[kk][rr] = (P < N && Q < N) ? (float)V[(long long)P * N + Q] : 0.f;
+      const int kb = e / 64, cc = e % 64;
+      const int Qb = k0 + kb;
+      const long long col = c0 + cc;
+      const int q = (int)(col / Kp), sidx = (int)(col % Kp);
+      sb[kb][cc] = (Qb < N && col < ncol && q < n && sidx < n)
+                       ? (float)(X[(long long)Qb * n + q] * X[(long long)Qb * n + sidx])
+                       : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sa[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = sb[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int P = P0 + ty + 16 * i;
+    if (P >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long col = c0 + tx + 16 * j;
+      if (col < ncol) U[(long long)P * ncol + col] = acc[i][j];
+    }
+  }
+}
+
+// T[b][R][r] = sum_P Dt[b][R][P] X[P][r]   (FP32 accumulate; D carries FP32 accuracy)
+// 64 x 64 tile of (R, r) per block, 256 threads, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_backproject_T(const float *Dt, long long ldD, const double *X, int N,
+                                                       int n, float *T) {
+  __shared__ float sa[16][65];
+  __shared__ float sb[16][65];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int R0 = blockIdx.y * 64, r0 = blockIdx.x * 64;
+  const int b = blockIdx.z;
+  const float *D = Dt + (long long)b * N * ldD;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < N; k0 += 16) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = tid + it * 256;
+      const int rr = e / 16, kk = e % 16;
+      const int R = R0 + rr, P = k0 + kk;
+      sa[kk][rr] = (R < N && P < N) ? D[(long long)R * ldD + P] : 0.f;
+      const int kb = e / 64, cc = e % 64;
+      const int Pb = k0 + kb, c = r0 + cc;
+      sb[kb][cc] = (Pb < N && c < n) ? (float)X[(long long)Pb * n + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sa[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = sb[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int R = R0 + ty + 16 * i;
+    if (R >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = r0 + tx + 16 * j;
+      if (c < n) T[((long long)b * N + R) * n + c] = acc[i][j];
+    }
+  }
+}
+
+// Sigma[b][t][r] = -sum_R X[R][t] T[b][R][r]   (FP64 accumulate: the final orbital-basis sum)
+__global__ void __launch_bounds__(256) k_backproject_sigma(const double *X, const float *T, int N, int n,
+                                                           double *Sigma, long long sstride) {
+  __shared__ double sa[16][33];
+  __shared__ double sb[16][33];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int t0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int b = blockIdx.z;
+  const float *Tb = T + (long long)b * N * n;
+  double acc[2][2] = {};
+  for (int k0 = 0; k0 < N; k0 += 16) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int e = tid + it * 256;
+      const int kk = e / 32, cc = e % 32;
+      const int R = k0 + kk;
+      sa[kk][cc] = (R < N && t0 + cc < n) ? X[(long long)R * n + t0 + cc] : 0.0;
+      sb[kk][cc] = (R < N && c0 + cc < n) ? (double)Tb[(long long)R * n + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const double a0 = sa[kk][ty], a1 = sa[kk][ty + 16];
+      const double b0 = sb[kk][tx], b1 = sb[kk][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int t = t0 + ty + 16 * i;
+    if (t >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = c0 + tx + 16 * j;
+      if (c < n) Sigma[(long long)b * sstride + (long long)t * n + c] = -acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------ launchers ----------------------------------
+
+void launch_mixed_f32(const double *V, const double *X, int N, int n, int Kp, float *U, cudaStream_t s) {
+  const long long ncol = (long long)Kp * Kp;
+  dim3 grid((unsigned)((ncol + 63) / 64), (N + 63) / 64);
+  k_mixed_f32<<<grid, 256, 0, s>>>(V, X, N, n, Kp, U);
+}
+
+void launch_backproject_T(const float *Dt, long long ldD, const double *X, int N, int n, int batch, float *T,
+                          cudaStream_t s) {
+  dim3 grid((n + 63) / 64, (N + 63) / 64, batch);
+  k_backproject_T<<<grid, 256, 0, s>>>(Dt, ldD, X, N, n, T);
+}
+
+void launch_backproject_sigma(const double *X, const float *T, int N, int n, int batch, double *Sigma,
+                              long long sstride, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+  k_backproject_sigma<<<grid, 256, 0, s>>>(X, T, N, n, Sigma, sstride);
+}
+
+size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers) + 1024; }
+
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_sox_bcd_tc<<<grid, kThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+                                                        maps[6], maps[7], a);
+  return cudaGetLastError();
+}
+
+size_t gemm_smem_bytes() { return (size_t)kGStages * kStageBytes + kStageOut + sizeof(Barriers) + 1024; }
+
+cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gemm_f16x2<<<grid, kThreads, gemm_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+  return cudaGetLastError();
+}
+
+bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
+                           uint64_t batch, std::string *err) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      if (err) *err = "cuTensorMapEncodeTiled entry point not available";
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // element (x, grp, row, b) at ((b * rows + row) * n_groups + grp) * group + x
+  cuuint64_t dims[4] = {group, n_groups, rows, batch};
+  cuuint64_t strides[3] = {group * 2, group * n_groups * 2, group * n_groups * rows * 2};
+  cuuint32_t box[4] = {64, 1, 128, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (store) failed with CUresult " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+void launch_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid, int rows_out,
+                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch,
+                           cudaStream_t s) {
+  const long long warps = (long long)rows_out * batch;
+  const int blocks = (int)((warps * 32 + 255) / 256);
+  k_split_rows_f64<<<blocks, 256, 0, s>>>(src, ld, bstride, rows_valid, rows_out, L, Kp, hi, lo, inv_scale,
+                                          batch);
+}
+
+void launch_split_mixed(const float *U, int N, int NR, int n, int Kp, __half *u1_hi, __half *u1_lo,
+                        __half *u2_hi, __half *u2_lo, float *inv_scale, cudaStream_t s) {
+  k_split_mixed<<<N, 256, 0, s>>>(U, N, NR, n, Kp, u1_hi, u1_lo, u2_hi, u2_lo, inv_scale);
+}
+
+void launch_prep_gminus(const double *G, int n, int T, int nbatch, int Kp, __half *hi, __half *lo,
+                        float *gscale, float *out_scale, int b0, int rows_out, cudaStream_t s) {
+  // batches b0 .. b0+nbatch-1 of the flattened (spin, tau) index; outputs indexed from 0
+  k_prep_gminus<<<nbatch, 256, 0, s>>>(G, n, T, Kp, hi, lo, gscale, out_scale, b0, rows_out);
+}
+
+void launch_bcd_scales(const float *inv_u1, const float *gsc, const float *osc, const float *asc, int NR,
+                       const float *inv_gw, const float *inv_gr, const float *inv_u2, int N, int batch,
+                       float *row, float *col, cudaStream_t s) {
+  const long long total = (long long)N * batch;
+  k_bcd_scales<<<(int)std::min<long long>((total + 255) / 256, 65535), 256, 0, s>>>(
+      inv_u1, gsc, osc, asc, NR, inv_gw, inv_gr, inv_u2, N, batch, row, col);
+}
+
+}  // namespace sox

@@ -1,0 +1,66 @@
+// Launch interfaces of the tensor-core kernels (tc_kernels.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+namespace sox {
+
+enum { kStoreSplit = 1, kStoreSplitGroup = 2 };
+
+struct BcdArgs {
+  int n = 0, N = 0, Kp = 0, batch = 0;
+  long long spin_limit = 0;
+  int *status = nullptr;
+  const float *row_scale = nullptr;  // [batch][N]
+  const float *col_scale = nullptr;  // [batch][N]
+  float *Dt = nullptr;               // [batch][N][ldD]
+  long long ldD = 0;
+};
+
+// Output of the split GEMM: FP16 pair tensors [batch][M][n_groups][group] written by
+// TMA stores (maps 4 and 5 of launch_gemm_f16x2, see make_tmap_f16_store4d).
+struct GemmTcArgs {
+  int M = 0, Ncols = 0, Kp = 0, batch = 1;
+  int batchA_shared = 0, batchB_shared = 0;
+  int mode = kStoreSplit;
+  const float *out_scale = nullptr;   // kStoreSplit: one power of two per batch
+  // kStoreSplitGroup: columns form groups of `group` (a multiple of 64) whose rows all lie
+  // in one tile (M <= 128); each group gets its own power-of-two scale, written to
+  // group_scale[b][group index]
+  int group = 128, n_groups = 0;
+  float *group_scale = nullptr;
+  long long spin_limit = 0;
+  int *status = nullptr;
+};
+
+bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                      uint32_t box0, uint32_t box1, std::string *err);
+size_t tc_smem_bytes();
+bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
+                           uint64_t batch, std::string *err);
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s);
+// maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
+cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);
+void launch_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid, int rows_out,
+                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch,
+                           cudaStream_t s);
+void launch_mixed_f32(const double *V, const double *X, int N, int n, int Kp, float *U, cudaStream_t s);
+void launch_split_mixed(const float *U, int N, int NR, int n, int Kp, __half *u1_hi, __half *u1_lo,
+                        __half *u2_hi, __half *u2_lo, float *inv_scale, cudaStream_t s);
+void launch_prep_gminus(const double *G, int n, int T, int nbatch, int Kp, __half *hi, __half *lo,
+                        float *gscale, float *out_scale, int b0, int rows_out, cudaStream_t s);
+void launch_bcd_scales(const float *inv_u1, const float *gsc, const float *osc, const float *asc, int NR,
+                       const float *inv_gw, const float *inv_gr, const float *inv_u2, int N, int batch,
+                       float *row, float *col, cudaStream_t s);
+
+// SIMT back-projection helpers (FP32 / FP64 accumulate), tc_kernels.cu
+void launch_backproject_T(const float *Dt, long long ldD, const double *X, int N, int n, int batch, float *T,
+                          cudaStream_t s);
+void launch_backproject_sigma(const double *X, const float *T, int N, int n, int batch, double *Sigma,
+                              long long sstride, cudaStream_t s);
+
+}  // namespace sox

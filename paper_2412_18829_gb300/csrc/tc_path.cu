@@ -1,10 +1,192 @@
+// Split-precision path of the THC-SOX chain (Sec. II C) on tcgen05 tensor cores.
+//
+//   mixed tensors U_Pqs = sum_Q U_PQ X_qQ X_sQ        FP32 CUDA cores, round to nearest
+//                                                       (an N-long sum: the tensor core's truncating
+//                                                       accumulation would cost ~1 ulp per 16 terms)
+//   G_Rq, G_wP projections                              FP64 GEMM, then split per row
+//   A_Pqv = sum_s U_Pqs G_sv(-tau)                      FP16x2 GEMM, split output
+//   D_PR = sum_v B_PRv C_RvP (B, C never stored)        fused tcgen05 kernel
+//   Sigma_tr = -sum_PR X_tR D_PR X_rP                   FP32 half-transform, FP64 final sum
+#include <algorithm>
+#include <string>
+
+#include "tc_kernels.h"
 #include "tc_path.h"
 
 namespace sox {
-size_t tc_sigma_bytes(sox_handle, int, int, int, int, bool) { return 0; }
-Status tc_sigma(sox_handle, int, int, int, int, const double *, const double *, const double *,
-                const double *, double *, Arena &, cudaStream_t) {
-  return {SOX_ERR_UNSUPPORTED, "tensor-core path not built"};
+namespace {
+
+constexpr size_t kChunkBudget = size_t(24) << 30;
+
+inline int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Geometry {
+  int n, N, T, S;
+  int Kp;   // n padded to 64 (K extent of the orbital contractions)
+  int Np;   // N padded to 64 (K extent of the mixed-tensor GEMM)
+  int NR;   // rows allocated along P / R (>= 128, rows >= N are zero)
+  int RG;   // rows allocated for G(-tau)^T (>= 128)
+  int Bc;   // (spin, tau) batches per chunk
+  size_t fixed_bytes, per_b_bytes;
+};
+
+size_t hb(size_t count) { return aligned_bytes(count, 2); }   // FP16 buffer
+size_t fb(size_t count) { return aligned_bytes(count, 4); }   // FP32 buffer
+size_t db(size_t count) { return aligned_bytes(count, 8); }   // FP64 buffer
+
+Geometry geometry(int n, int N, int T, int S, bool two) {
+  Geometry g{};
+  g.n = n; g.N = N; g.T = T; g.S = S;
+  g.Kp = rup(n, 64);
+  g.Np = rup(N, 64);
+  g.NR = std::max(N, 128);
+  g.RG = std::max(g.Kp, 128);
+  const size_t Kp2 = (size_t)g.Kp * g.Kp;
+  g.fixed_bytes = fb((size_t)g.N * Kp2)                             // FP32 mixed tensor
+                  + 2 * hb((size_t)g.NR * Kp2) + fb(g.N)              // U1 split
+                  + 2 * hb((size_t)g.n * g.NR * g.Kp) + fb(g.N);      // U2 split
+  g.per_b_bytes = 2 * db((size_t)N * n)                                // FP64 projections
+                  + 4 * hb((size_t)g.NR * g.Kp) + 2 * fb(N)           // GR / GW splits
+                  + 2 * hb((size_t)g.RG * g.Kp) + 2 * fb(1)           // G(-tau)^T split, scales
+                  + fb(g.NR)                                          // exact per-P scale of A
+                  + 2 * hb((size_t)n * g.NR * g.Kp)                   // A split
+                  + 2 * fb(N)                                         // row/col factors
+                  + fb((size_t)N * N) + fb((size_t)N * n) + 4096;     // Dt, T
+  long long c = (long long)(kChunkBudget / std::max<size_t>(g.per_b_bytes, 1));
+  c = std::max<long long>(1, std::min<long long>(c, (long long)T * S));
+  g.Bc = (int)c;
+  return g;
 }
+
+}  // namespace
+
+size_t tc_sigma_bytes(sox_handle, int n, int N, int T, int S, bool two) {
+  Geometry g = geometry(n, N, T, S, two);
+  return g.fixed_bytes + g.per_b_bytes * g.Bc + 64 * 1024;
+}
+
 void tc_release(sox_handle) {}
+
+Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const double *X, const double *U1,
+                const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
+  const bool two = (U1 != U2);
+  const Geometry g = geometry(n, N, T, S, two);
+  const int Kp = g.Kp, Np = g.Np, NR = g.NR, RG = g.RG, Bc = g.Bc;
+  const size_t Kp2 = (size_t)Kp * Kp;
+  std::string err;
+
+  // ---- fixed buffers ----
+  float *Uf = ar.take<float>((size_t)N * Kp2);
+  __half *U1h = ar.take<__half>((size_t)NR * Kp2), *U1l = ar.take<__half>((size_t)NR * Kp2);
+  float *inv_u1 = ar.take<float>(N);
+  __half *U2h = ar.take<__half>((size_t)n * NR * Kp), *U2l = ar.take<__half>((size_t)n * NR * Kp);
+  float *inv_u2 = ar.take<float>(N);
+  // ---- per-chunk buffers ----
+  double *GR64 = ar.take<double>((size_t)Bc * N * n), *GW64 = ar.take<double>((size_t)Bc * N * n);
+  __half *GRh = ar.take<__half>((size_t)Bc * NR * Kp), *GRl = ar.take<__half>((size_t)Bc * NR * Kp);
+  __half *GWh = ar.take<__half>((size_t)Bc * NR * Kp), *GWl = ar.take<__half>((size_t)Bc * NR * Kp);
+  float *inv_gr = ar.take<float>((size_t)Bc * N), *inv_gw = ar.take<float>((size_t)Bc * N);
+  __half *Gmh = ar.take<__half>((size_t)Bc * RG * Kp), *Gml = ar.take<__half>((size_t)Bc * RG * Kp);
+  float *gsc = ar.take<float>(Bc), *osc = ar.take<float>(Bc);
+  float *asc = ar.take<float>((size_t)Bc * NR);
+  __half *Ah = ar.take<__half>((size_t)Bc * n * NR * Kp), *Al = ar.take<__half>((size_t)Bc * n * NR * Kp);
+  float *rowf = ar.take<float>((size_t)Bc * N), *colf = ar.take<float>((size_t)Bc * N);
+  float *Dt = ar.take<float>((size_t)Bc * N * N);
+  float *Tm = ar.take<float>((size_t)Bc * N * n);
+  if (!Tm) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+
+  const long long limit = h->spin_limit;
+  auto grid_for = [&](long long tiles) { return (int)std::max<long long>(1, std::min<long long>(tiles, h->sm_count)); };
+
+  // ---- mixed tensors (Eq. U_contraction at k = 0) ----
+  {
+    ProfScope ps(h, "mixed_f32", s, two ? 4 : 2);
+    SOX_CUDA_TRY(cudaMemsetAsync(U1h, 0, hb((size_t)NR * Kp2), s));
+    SOX_CUDA_TRY(cudaMemsetAsync(U1l, 0, hb((size_t)NR * Kp2), s));
+    SOX_CUDA_TRY(cudaMemsetAsync(U2h, 0, hb((size_t)n * NR * Kp), s));
+    SOX_CUDA_TRY(cudaMemsetAsync(U2l, 0, hb((size_t)n * NR * Kp), s));
+    const double *src[2] = {U1, U2};
+    for (int k = 0; k < (two ? 2 : 1); ++k) {
+      launch_mixed_f32(src[k], X, N, n, Kp, Uf, s);
+      const bool slot1 = (k == 0), slot2 = two ? (k == 1) : true;
+      launch_split_mixed(Uf, N, NR, n, Kp, slot1 ? U1h : nullptr, slot1 ? U1l : nullptr, slot2 ? U2h : nullptr,
+                         slot2 ? U2l : nullptr, slot1 ? inv_u1 : inv_u2, s);
+      if (!two) SOX_CUDA_TRY(cudaMemcpyAsync(inv_u2, inv_u1, 4 * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+
+  // ---- tensor maps of the per-chunk buffers (fixed addresses, reused per chunk) ----
+  CUtensorMap bcd[8], agemm[6];
+  if (!make_tmap_f16_3d(&bcd[0], Ah, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[1], Al, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[2], GRh, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[3], GRl, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[4], GWh, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[5], GWl, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[6], U2h, Kp, NR, n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[7], U2l, Kp, NR, n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[0], Gmh, Kp, RG, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[1], Gml, Kp, RG, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[2], U1h, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[3], U1l, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+      !make_tmap_f16_store4d(&agemm[4], Ah, Kp, NR, n, Bc, &err) ||
+      !make_tmap_f16_store4d(&agemm[5], Al, Kp, NR, n, Bc, &err))
+    return {SOX_ERR_CUDA, err};
+
+  const bool exact_a = (Kp <= 128);
+  const int B = S * T;
+  for (int b0 = 0; b0 < B; b0 += Bc) {
+    const int bc = std::min(Bc, B - b0);
+    const double *Gc = G + (long long)b0 * n * n;
+    {  // FP64 projections G_Rq = X G, G_wP^T = X G^T, then row splits
+      ProfScope ps(h, "project_f64", s, 4);
+      GemmF64 gp;
+      gp.M = N; gp.Nc = n; gp.K = n; gp.batch = bc;
+      gp.A = X; gp.ai = n; gp.ak = 1;
+      gp.B = Gc; gp.sB = (long long)n * n; gp.bk = n; gp.bj = 1;
+      gp.C = GR64; gp.sC = (long long)N * n; gp.ci = n; gp.cj = 1;
+      launch_gemm_f64(gp, s);
+      GemmF64 gw = gp;
+      gw.bk = 1; gw.bj = n;
+      gw.C = GW64;
+      launch_gemm_f64(gw, s);
+      launch_split_rows_f64(GR64, n, (long long)N * n, N, NR, n, Kp, GRh, GRl, inv_gr, bc, s);
+      launch_split_rows_f64(GW64, n, (long long)N * n, N, NR, n, Kp, GWh, GWl, inv_gw, bc, s);
+    }
+    {  // A_Pqv = sum_s G(-tau)_sv U_Pqs
+      ProfScope ps(h, "A_tc", s, 2);
+      launch_prep_gminus(G, n, T, bc, Kp, Gmh, Gml, gsc, osc, b0, RG, s);
+      GemmTcArgs ga;
+      ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.batch = bc;
+      ga.batchA_shared = 0; ga.batchB_shared = 1;
+      // n <= 128: one tile holds all (v, q) of each P -> exact per-P scale; else the a-priori bound
+      ga.mode = exact_a ? kStoreSplitGroup : kStoreSplit;
+      ga.out_scale = osc;
+      ga.group = Kp; ga.n_groups = NR; ga.group_scale = asc;
+      ga.spin_limit = limit; ga.status = h->d_status;
+      const long long tiles = (long long)bc * ((n + 127) / 128) * ((NR * Kp + 127) / 128);
+      SOX_CUDA_TRY(launch_gemm_f16x2(agemm, ga, grid_for(tiles), s));
+    }
+    launch_bcd_scales(inv_u1, gsc, osc, exact_a ? asc : nullptr, NR, inv_gw, inv_gr, inv_u2, N, bc, rowf, colf, s);
+    h->launches += 1;
+    {  // fused B / C / Hadamard-reduce
+      ProfScope ps(h, "sox_bcd_tc", s);
+      BcdArgs ba;
+      ba.n = n; ba.N = N; ba.Kp = Kp; ba.batch = bc;
+      ba.spin_limit = limit; ba.status = h->d_status;
+      ba.row_scale = rowf; ba.col_scale = colf;
+      ba.Dt = Dt; ba.ldD = N;
+      const int tP = (N + 127) / 128;
+      SOX_CUDA_TRY(launch_sox_bcd_tc(bcd, ba, grid_for((long long)bc * tP * tP), s));
+    }
+    {  // back-projection to orbitals
+      ProfScope ps(h, "backproject", s, 2);
+      launch_backproject_T(Dt, N, X, N, n, bc, Tm, s);
+      launch_backproject_sigma(X, Tm, N, n, bc, Sigma + (long long)b0 * n * n, (long long)n * n, s);
+    }
+  }
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
 }  // namespace sox

@@ -33,7 +33,7 @@ def _sigma(env, prec, w, U1=None, U2=None, slot=None):
         pkg.sox_sigma_general(hs[prec], p, G, X, A1, A2, S)
     else:
         pkg.sox_sigma(hs[prec], p, G, X, V, S)
-    torch.cuda.synchronize()
+    pkg.sox_check_device(hs[prec])
     return S.cpu().numpy()
 
 
@@ -41,7 +41,7 @@ def _sigma(env, prec, w, U1=None, U2=None, slot=None):
 @pytest.mark.parametrize("n,N,n_tau,n_spin", [(13, 70, 6, 2), (1, 1, 4, 1), (5, 3, 2, 1), (33, 130, 5, 1),
                                               (64, 128, 3, 1)])
 def test_sox_small_and_ragged(env, prec, n, N, n_tau, n_spin):
-    w = synth.molecule(11, n, N, n_tau, 20.0, n_spin=n_spin, name="ragged")
+    w = synth.molecule(11, n, N, n_tau, 100.0, n_spin=n_spin, name="ragged")
     ref = sox.sox_sigma(w.X, w.V, w.G).real
     check(_sigma(env, prec, w), ref, prec, f"n={n} N={N}")
 
@@ -50,7 +50,7 @@ def test_sox_small_and_ragged(env, prec, n, N, n_tau, n_spin):
 def test_sox_c0_all_tau(env, prec):
     w = synth.config(0)
     ref = sox.sox_sigma(w.X, w.V, w.G).real
-    err, scale = check(_sigma(env, prec, w), ref, prec, "c0")
+    err, scale = check(_sigma(env, prec, w), ref, prec, "c0", strict=True)
     print(f"c0 {prec}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
 
 
@@ -63,18 +63,19 @@ def test_sox_c1_full_size_sampled_tau(env, prec):
     taus = [0, 17, 40, 79]
     for s in range(w.n_spin):
         ref = sox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
-        err, scale = check(out[s, 0, taus], ref, prec, f"c1 spin {s}")
+        err, scale = check(out[s, 0, taus], ref, prec, f"c1 spin {s}", strict=True)
         print(f"c1 {prec} spin {s}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_general_two_interactions_nonsymmetric(env, prec):
-    w = synth.molecule(12, 19, 75, 5, 10.0, n_spin=1)
+    w = synth.molecule(12, 19, 75, 5, 100.0, n_spin=1)
     rng = np.random.default_rng(3)
     z = rng.standard_normal((w.N, w.N)) / w.N
     U1 = np.ascontiguousarray((z @ z.T + 0.3 * z)[None])     # non-symmetric on purpose
     U2 = np.ascontiguousarray(w.V)
     ref = np.stack([sox.sigma_tau(w.X[0], U1[0], U2[0], w.G[0, 0]).real])[:, None]
+    assert np.abs(ref).max() > 1e-4
     check(_sigma(env, prec, w, U1, U2), ref, prec, "general")
 
 
@@ -86,7 +87,7 @@ def test_sosex_static_c0(env, prec, slot):
     Pi = screening.pi0_quadrature(w.X[0], w.G[0, 0], wt)
     W = np.ascontiguousarray(screening.w_static(w.V[0], 0.5 * (Pi + Pi.T))[None])
     ref = sox.sosex_static_sigma(w.X, w.V, W, w.G, slot=slot).real
-    check(_sigma(env, prec, w, W, slot=slot), ref, prec, f"sosex slot {slot}")
+    check(_sigma(env, prec, w, W, slot=slot), ref, prec, f"sosex slot {slot}", strict=True)
 
 
 def test_thc_project_G(env):
@@ -141,7 +142,7 @@ def test_w_static_reports_singular_system(env):
 @pytest.mark.parametrize("prec", PRECS)
 def test_host_buffers_through_the_c_abi(env, prec):
     torch, pkg, hs = env
-    w = synth.molecule(14, 17, 66, 5, 10.0, n_spin=1)
+    w = synth.molecule(14, 17, 66, 5, 100.0, n_spin=1)
     p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
     S = np.full_like(w.G, np.nan)
     pkg.sox_sigma(hs[prec], p, w.G, w.X, w.V, S)
@@ -168,3 +169,31 @@ def test_error_paths(env):
         pkg.sox_sigma(h, pkg.problem(3, 5, 4), G, X, V, None)
     with pytest.raises(pkg.SoxError):
         pkg.sosex_static_sigma(h, pkg.problem(3, 5, 4), G, X, V, V, S, slot=3)
+
+
+@pytest.mark.parametrize("n,N,n_tau", [(130, 300, 3), (200, 260, 2)])
+def test_split_path_beyond_one_k_tile(env, n, N, n_tau):
+    """n > 128: the A intermediate takes its a-priori scale and K spans several chunks."""
+    w = synth.molecule(15, n, N, n_tau, 100.0, n_spin=1)
+    ref = sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64)
+    check(_sigma(env, "f16x2", w), ref, "f16x2", f"n={n}")
+
+
+def test_bounded_waits_report_timeout_and_context_survives(env):
+    """With an iteration cap of 1 the tensor-core kernels give up their first
+    waits, set the status word and return; the call reports SOX_ERR_TIMEOUT and
+    the context stays usable for a normal call afterwards."""
+    torch, pkg, hs = env
+    w = synth.molecule(16, 64, 256, 4, 100.0, n_spin=1)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    S = torch.empty_like(G)
+    with pkg.Handle("f16x2", spin_limit=1) as h1:
+        pkg.sox_sigma(h1, p, G, X, V, S)
+        with pytest.raises(pkg.SoxError) as e:
+            pkg.sox_check_device(h1)
+        assert e.value.code == 6
+        pkg.sox_check_device(h1)          # status was cleared
+    pkg.sox_sigma(hs["f16x2"], p, G, X, V, S)
+    pkg.sox_check_device(hs["f16x2"])
+    check(S.cpu().numpy(), sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64), "f16x2", "after timeout")
