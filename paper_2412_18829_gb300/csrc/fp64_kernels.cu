@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g) {
   const int tx = tid % 16, ty = tid / 16;
   const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   const long long b = blockIdx.z;
+  if (g.skip && g.skip[b]) return;
   const double *A = g.A + b * g.sA;
   const double *B = g.B + b * g.sB;
   double *C = g.C + b * g.sC;
@@ -332,6 +333,29 @@ __global__ void k_neg_reflect(const double *src, double *dst, long long mat, int
   }
 }
 
+__global__ void k_symmetry_flags(const double *G, int n, int *flag) {
+  const int b = blockIdx.x;
+  const double *g = G + (long long)b * n * n;
+  double m = 0.0, d = 0.0;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    m = fmax(m, fabs(g[e]));
+    d = fmax(d, fabs(g[e] - g[(long long)j * n + i]));
+  }
+  __shared__ double sm[256], sd[256];
+  sm[threadIdx.x] = m;
+  sd[threadIdx.x] = d;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) flag[b] = (sd[0] <= 1e-14 * sm[0]) ? 1 : 0;
+}
+
 inline int grid_for(long long total, int threads = 256) {
   long long b = (total + threads - 1) / threads;
   if (b > 65535LL * 16) b = 65535LL * 16;
@@ -401,6 +425,10 @@ void launch_build_gj_system(const double *V, const double *Pi, double *Aug, int 
 
 void launch_copy_right_half(const double *Aug, double *W, int N, cudaStream_t s) {
   k_copy_right<<<grid_for((long long)N * N), 256, 0, s>>>(Aug, W, N);
+}
+
+void launch_symmetry_flags(const double *G, int n, int batch, int *flag, cudaStream_t s) {
+  k_symmetry_flags<<<batch, 256, 0, s>>>(G, n, flag);
 }
 
 void launch_neg_reflect(const double *src, double *dst, long long mat, int n_tau, int count,

@@ -97,6 +97,7 @@ struct GemmF64 {
   const double *B = nullptr; long long sB = 0, bk = 0, bj = 0;
   double *C = nullptr; long long sC = 0, ci = 0, cj = 0;
   double alpha = 1.0, beta = 0.0;
+  const int *skip = nullptr;  // optional per-batch flags: batch b is not computed when skip[b] != 0
 };
 void launch_gemm_f64(const GemmF64 &g, cudaStream_t s);
 
@@ -129,6 +130,8 @@ void launch_pi0_reduce(const double *GPQ, const double *w, int N, int n_tau, dou
 void launch_gj_step(double *Aug, int N, int k, int *piv_info, cudaStream_t s);
 void launch_build_gj_system(const double *V, const double *Pi, double *Aug, int N, cudaStream_t s);
 void launch_copy_right_half(const double *Aug, double *W, int N, cudaStream_t s);
+// flag[b] = 1 when G[b] (n x n) equals its transpose to 1e-14 of max|G[b]|, else 0
+void launch_symmetry_flags(const double *G, int n, int batch, int *flag, cudaStream_t s);
 void launch_neg_reflect(const double *src, double *dst, long long mat, int n_tau, int count,
                         cudaStream_t s);
 

@@ -273,6 +273,237 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ============================================================================
+// Resident-operand variant of the fused kernel for Kp <= 128.  The per-tile
+// operands G_Rq[R-tile] and G_wP^T[P-tile] (hi/lo, all of K) stay in shared
+// memory for the whole tile (128 KB); only A_v and U2_v stream, one hi/lo chunk
+// (32 KB) per stage.  That halves the bytes each MMA needs from L2, which is
+// what limits the all-streamed kernel.
+// ============================================================================
+constexpr int kRStages = 3;
+constexpr int kRStageBytes = 2 * kTileBytes;        // hi + lo of one 64-wide chunk
+constexpr int kResBytes = 8 * kTileBytes;           // {GR, GW} x {hi, lo} x 2 chunks
+
+struct ResBarriers {
+  uint64_t full[kRStages];
+  uint64_t empty[kRStages];
+  uint64_t res_full, res_empty;
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// resident tile address: op 0 = GR, 1 = GW; part 0 = hi, 1 = lo; chunk kc
+__device__ __forceinline__ uint8_t *res_ptr(uint8_t *res, int op, int part, int kc) {
+  return res + (size_t)((op * 2 + part) * 2 + kc) * kTileBytes;
+}
+
+__device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                             uint32_t b_lo, bool first) {
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+                (first && k == 0) ? 0u : 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sox_bcd_tc_res(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                     const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
+                     const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
+                     const __grid_constant__ CUtensorMap tmU_hi, const __grid_constant__ CUtensorMap tmU_lo,
+                     BcdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *res = smem;
+  uint8_t *stages = smem + kResBytes;
+  ResBarriers *bar = reinterpret_cast<ResBarriers *>(stages + kRStages * kRStageBytes);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tP = (a.N + kTile - 1) / kTile;
+  const int tiles_per_b = tP * tP;
+  const long long total = (long long)a.batch * tiles_per_b;
+  const int nk = a.Kp / kChunk;   // 1 or 2
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    tc::mbar_init(&bar->res_full, 1);
+    tc::mbar_init(&bar->res_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_empty[b], 128);
+    }
+    tc::mbar_init(&bar->drain, 1);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo); tc::prefetch_tmap(&tmGR_hi);
+    tc::prefetch_tmap(&tmGR_lo); tc::prefetch_tmap(&tmGW_hi); tc::prefetch_tmap(&tmGW_lo);
+    tc::prefetch_tmap(&tmU_hi); tc::prefetch_tmap(&tmU_lo);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long it = 0, tt = 0;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++tt) {
+        const int b = (int)(t / tiles_per_b);
+        const int r = (int)(t % tiles_per_b);
+        const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
+        // resident operands of this tile, once the previous tile's MMAs are done with them
+        if (!tc::mbar_wait(&bar->res_empty, (uint32_t)((tt & 1) ^ 1), a.spin_limit, abort, a.status, 16)) break;
+        tc::mbar_arrive_expect_tx(&bar->res_full, (uint32_t)(4 * nk * kTileBytes));
+        for (int kc = 0; kc < nk; ++kc) {
+          const int x = kc * kChunk;
+          tc::tma_load_3d(res_ptr(res, 0, 0, kc), &tmGR_hi, &bar->res_full, x, R0, b);
+          tc::tma_load_3d(res_ptr(res, 0, 1, kc), &tmGR_lo, &bar->res_full, x, R0, b);
+          tc::tma_load_3d(res_ptr(res, 1, 0, kc), &tmGW_hi, &bar->res_full, x, P0, b);
+          tc::tma_load_3d(res_ptr(res, 1, 1, kc), &tmGW_lo, &bar->res_full, x, P0, b);
+        }
+        for (int v = 0; v < a.n && !*abort; ++v) {
+          for (int half = 0; half < 2; ++half) {
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kRStages);
+              const uint32_t ph = (uint32_t)((it / kRStages) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+              tc::mbar_arrive_expect_tx(&bar->full[s], kRStageBytes);
+              uint8_t *st = stages + (size_t)s * kRStageBytes;
+              const int x = kc * kChunk;
+              if (half == 0) {
+                tc::tma_load_3d(st, &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(st + kTileBytes, &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
+              } else {
+                tc::tma_load_3d(st, &tmU_hi, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(st + kTileBytes, &tmU_lo, &bar->full[s], x, R0, v);
+              }
+            }
+          }
+        }
+      }
+      // wind down: every copy issued must have landed before the CTA exits
+      for (int s = 0; s < kRStages; ++s) {
+        long long last = it - 1 - ((it - 1 - s) % kRStages + kRStages) % kRStages;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kRStages) & 1);
+          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+      if (tt > 0) {
+        const uint32_t ph = (uint32_t)((tt - 1) & 1);
+        for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->res_full, ph); ++i) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long it = 0, acc_it = 0, tt = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++tt) {
+        ok = tc::mbar_wait(&bar->res_full, (uint32_t)(tt & 1), a.spin_limit, abort, a.status, 32);
+        if (!ok) break;
+        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t acc = tmem + buf * 256 + half * 128;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kRStages);
+              const uint32_t ph = (uint32_t)((it / kRStages) & 1);
+              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              const uint32_t sh = smem_u32(stages + (size_t)s * kRStageBytes), sl = sh + kTileBytes;
+              if (half == 0) {   // B_v[P, R] = A_v[P, :] . GR[R, :]
+                issue_chunk4(acc, sh, sl, smem_u32(res_ptr(res, 0, 0, kc)), smem_u32(res_ptr(res, 0, 1, kc)), kc == 0);
+              } else {           // C_v[P, R] = GW[P, :] . U2_v[R, :]
+                issue_chunk4(acc, smem_u32(res_ptr(res, 1, 0, kc)), smem_u32(res_ptr(res, 1, 1, kc)), sh, sl, kc == 0);
+              }
+              tc::mma_commit(&bar->empty[s]);
+            }
+          }
+          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+        }
+        if (ok) tc::mma_commit(&bar->res_empty);   // resident tiles free once these MMAs retire
+      }
+      tc::mma_commit(&bar->drain);
+      for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    long long acc_it = 0;
+    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      const int b = (int)(t / tiles_per_b);
+      const int r = (int)(t % tiles_per_b);
+      const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
+      float d[kTile];
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
+      bool ok = true;
+      for (int v = 0; v < a.n; ++v, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
+#pragma unroll
+        for (int c = 0; c < kTile; c += 16) {
+          float bv[16], cv[16];
+          tc::tmem_ld_32x32b_x16(base + c, bv);
+          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bar->acc_empty[buf]);
+      }
+      if (!ok) break;
+      const int P = P0 + row;
+      if (P < a.N) {
+        const float rs = a.row_scale[(long long)b * a.N + P];
+        float *out = a.Dt + (long long)b * a.N * a.ldD + P;
+#pragma unroll
+        for (int j = 0; j < kTile; ++j) {
+          const int R = R0 + j;
+          if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================
 // Split GEMM with split output (the A intermediate, Sec. II C):
 //   C[b](i, j) = sum_k A[bA](i, k) B[bB](j, k)      (both operands K-major FP16 pairs)
 // 128 x 128 tiles, double-buffered TMEM accumulator.  The epilogue scales the
@@ -509,7 +740,7 @@ __device__ __forceinline__ float warp_max(float v) {
 // One warp per output row: hi/lo of src row scaled to max in [1, 2); rows >= rows_valid are zero.
 __global__ void k_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid,
                                  int rows_out, int L, int Kp, __half *hi, __half *lo, float *inv_scale,
-                                 int batch) {
+                                 int batch, const double *alt_src, const int *use_alt) {
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (gw >= (long long)rows_out * batch) return;
@@ -520,7 +751,7 @@ __global__ void k_split_rows_f64(const double *src, long long ld, long long bstr
     for (int k = lane; k < Kp; k += 32) h[k] = l[k] = __float2half(0.f);
     return;
   }
-  const double *x = src + b * bstride + r * ld;
+  const double *x = ((use_alt && use_alt[b]) ? alt_src : src) + b * bstride + r * ld;
   float m = 0.f;
   for (int k = lane; k < L; k += 32) m = fmaxf(m, (float)fabs(x[k]));
   m = warp_max(m);
@@ -817,7 +1048,21 @@ void launch_backproject_sigma(const double *X, const float *T, int N, int n, int
 
 size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers) + 1024; }
 
+size_t res_smem_bytes() { return (size_t)kResBytes + kRStages * kRStageBytes + sizeof(ResBarriers) + 1024; }
+
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s) {
+  if (a.Kp <= 128) {
+    static bool rattr = false;
+    if (!rattr) {
+      cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)res_smem_bytes());
+      if (e != cudaSuccess) return e;
+      rattr = true;
+    }
+    k_sox_bcd_tc_res<<<grid, kThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+                                                               maps[5], maps[6], maps[7], a);
+    return cudaGetLastError();
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -874,12 +1119,12 @@ bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, u
 }
 
 void launch_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid, int rows_out,
-                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch,
-                           cudaStream_t s) {
+                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch, cudaStream_t s,
+                           const double *alt_src, const int *use_alt) {
   const long long warps = (long long)rows_out * batch;
   const int blocks = (int)((warps * 32 + 255) / 256);
   k_split_rows_f64<<<blocks, 256, 0, s>>>(src, ld, bstride, rows_valid, rows_out, L, Kp, hi, lo, inv_scale,
-                                          batch);
+                                          batch, alt_src, use_alt);
 }
 
 void launch_split_mixed(const float *U, int N, int NR, int n, int Kp, __half *u1_hi, __half *u1_lo,

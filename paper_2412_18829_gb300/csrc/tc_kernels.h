@@ -45,9 +45,10 @@ bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, u
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s);
 // maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);
+// rows of batch b come from alt_src instead of src when use_alt[b] != 0 (both optional)
 void launch_split_rows_f64(const double *src, long long ld, long long bstride, int rows_valid, int rows_out,
-                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch,
-                           cudaStream_t s);
+                           int L, int Kp, __half *hi, __half *lo, float *inv_scale, int batch, cudaStream_t s,
+                           const double *alt_src = nullptr, const int *use_alt = nullptr);
 void launch_mixed_f32(const double *V, const double *X, int N, int n, int Kp, float *U, cudaStream_t s);
 void launch_split_mixed(const float *U, int N, int NR, int n, int Kp, __half *u1_hi, __half *u1_lo,
                         __half *u2_hi, __half *u2_lo, float *inv_scale, cudaStream_t s);

@@ -51,7 +51,8 @@ Geometry geometry(int n, int N, int T, int S, bool two) {
                   + fb(g.NR)                                          // exact per-P scale of A
                   + 2 * hb((size_t)n * g.NR * g.Kp)                   // A split
                   + 2 * fb(N)                                         // row/col factors
-                  + fb((size_t)N * N) + fb((size_t)N * n) + 4096;     // Dt, T
+                  + fb((size_t)N * N) + fb((size_t)N * n) + 4096      // Dt, T
+                  + fb(1);                                            // symmetry flag
   long long c = (long long)(kChunkBudget / std::max<size_t>(g.per_b_bytes, 1));
   c = std::max<long long>(1, std::min<long long>(c, (long long)T * S));
   g.Bc = (int)c;
@@ -93,7 +94,8 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
   float *rowf = ar.take<float>((size_t)Bc * N), *colf = ar.take<float>((size_t)Bc * N);
   float *Dt = ar.take<float>((size_t)Bc * N * N);
   float *Tm = ar.take<float>((size_t)Bc * N * n);
-  if (!Tm) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  int *symf = ar.take<int>((size_t)Bc);
+  if (!symf) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
 
   const long long limit = h->spin_limit;
   auto grid_for = [&](long long tiles) { return (int)std::max<long long>(1, std::min<long long>(tiles, h->sm_count)); };
@@ -138,8 +140,11 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
   for (int b0 = 0; b0 < B; b0 += Bc) {
     const int bc = std::min(Bc, B - b0);
     const double *Gc = G + (long long)b0 * n * n;
-    {  // FP64 projections G_Rq = X G, G_wP^T = X G^T, then row splits
-      ProfScope ps(h, "project_f64", s, 4);
+    {  // FP64 projections G_Rq = X G, G_wP^T = X G^T, then row splits.  For a symmetric
+       // G(tau) (real molecular orbitals) G_wP^T = G_Rq: a device flag per (spin, tau)
+       // lets the second GEMM skip its blocks and the split read G_Rq instead.
+      ProfScope ps(h, "project_f64", s, 5);
+      launch_symmetry_flags(Gc, n, bc, symf, s);
       GemmF64 gp;
       gp.M = N; gp.Nc = n; gp.K = n; gp.batch = bc;
       gp.A = X; gp.ai = n; gp.ak = 1;
@@ -149,9 +154,10 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       GemmF64 gw = gp;
       gw.bk = 1; gw.bj = n;
       gw.C = GW64;
+      gw.skip = symf;
       launch_gemm_f64(gw, s);
       launch_split_rows_f64(GR64, n, (long long)N * n, N, NR, n, Kp, GRh, GRl, inv_gr, bc, s);
-      launch_split_rows_f64(GW64, n, (long long)N * n, N, NR, n, Kp, GWh, GWl, inv_gw, bc, s);
+      launch_split_rows_f64(GW64, n, (long long)N * n, N, NR, n, Kp, GWh, GWl, inv_gw, bc, s, GR64, symf);
     }
     {  // A_Pqv = sum_s G(-tau)_sv U_Pqs
       ProfScope ps(h, "A_tc", s, 2);

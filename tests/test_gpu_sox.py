@@ -197,3 +197,16 @@ def test_bounded_waits_report_timeout_and_context_survives(env):
     pkg.sox_sigma(hs["f16x2"], p, G, X, V, S)
     pkg.sox_check_device(hs["f16x2"])
     check(S.cpu().numpy(), sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64), "f16x2", "after timeout")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nonsymmetric_G_takes_the_general_projection(env, prec):
+    """G(tau) is symmetric for real molecular orbitals, and the split path then
+    reuses G_Rq for G_wP^T; a non-symmetric G must still give the definition."""
+    w = synth.molecule(17, 26, 130, 5, 100.0, n_spin=2)
+    rng = np.random.default_rng(5)
+    G = w.G.copy()
+    G[1] += 0.05 * np.abs(G[1]).max() * rng.standard_normal(G[1].shape)   # spin 1 only
+    w.G = np.ascontiguousarray(G)
+    ref = sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64)
+    check(_sigma(env, prec, w), ref, prec, "non-symmetric G")
