@@ -204,6 +204,39 @@ SOX_API int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs,
                     const double *const *G, const double *const *X, const double *const *V,
                     double *const *Sigma, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant (the paper has no counterpart; this is a service to
+ * callers of the library).
+ *
+ * Some callers cannot allocate device memory at all: a process whose device
+ * memory is handed to another runtime's fixed pool at start-up, or a component
+ * that may only work inside buffers it was given.  They cannot create a
+ * sox_handle, because a handle allocates its workspace and status word with
+ * cudaMalloc.  sox_sigma_fp64_noalloc computes the same bare SOX self-energy as
+ * sox_sigma on an FP64 handle (same kernels, same layouts) without a handle and
+ * without calling cudaMalloc, cudaFree or any allocating library routine.
+ *
+ * - Scratch: a fixed device array of SOX_NOALLOC_SCRATCH_BYTES (64 MiB) in the
+ *   library, held by every GPU that loads the library until the process exits.
+ *   A problem needs 8 * (N n^2 + c (N n^2 + 3 N n + N^2)) bytes (plus 256-byte
+ *   padding per slice) for c = 1 tau point at least; larger problems are
+ *   rejected with SOX_ERR_SHAPE.  n = 80 with N = 480 fits, n = 90 with N = 540
+ *   does not.
+ * - The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ * - Every call shares the one array, and it keeps the last call's contents
+ *   (nothing in it needs to start at zero: every element is written before it
+ *   is read).  Calls that overlap on the GPU race on the array: run them on
+ *   one stream or serialise them.
+ * - G, X, V, Sigma must be device pointers on the current device (host
+ *   pointers return SOX_ERR_INVALID_ARG: staging them would need memory).
+ * - Returns SOX_OK, SOX_ERR_INVALID_ARG, SOX_ERR_SHAPE, SOX_ERR_UNSUPPORTED
+ *   (solids / complex data) or SOX_ERR_CUDA; asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+#define SOX_NOALLOC_SCRATCH_BYTES (64ull << 20)
+SOX_API int sox_sigma_fp64_noalloc(const sox_problem *p, const double *G, const double *X, const double *V,
+                                   double *Sigma, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

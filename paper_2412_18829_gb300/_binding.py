@@ -62,6 +62,7 @@ _SIGS = {
     "sosex_dynamic_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _I, _P, _P], _I),
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
+    "sox_sigma_fp64_noalloc": ([ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -246,3 +247,11 @@ def sox_sigma_batch(h: Handle, probs, G, X, V, Sigma, stream=None):
     arr = (sox_problem * count)(*probs)
     mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
     h.check(lib().sox_sigma_batch(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(Sigma), _stream(stream)))
+
+
+def sox_sigma_fp64_noalloc(p: sox_problem, G, X, V, Sigma, stream=None):
+    """Bare SOX on the FP64 path with the library's fixed scratch array (no handle,
+    no device allocation).  Device tensors only; raises SoxError on failure."""
+    rc = lib().sox_sigma_fp64_noalloc(ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(Sigma), _stream(stream))
+    if rc != SOX_OK:
+        raise SoxError(rc, "sox_sigma_fp64_noalloc failed (see include/thc_sox.h for the status meanings)")
