@@ -10,7 +10,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/thc_sox.h"
+#include "thc_sox.h"
 
 struct sox_context {
   int device = 0;

@@ -108,6 +108,64 @@ __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
   }
 }
 
+// Fused kernels: warp 0 TMA, warp 1 MMA, warps 2..5 epilogue (one per TMEM
+// lane quarter, 128 columns each).  Measured: the epilogue is not the limit (a
+// variant that skips its TMEM loads runs at the same speed), so it stays at
+// four warps with 255 registers available.
+constexpr int kBcdThreads = 192;
+constexpr int kEpiThreads = 128;
+
+// Epilogue of the fused kernels: D[P, R] += B_v[P, R] * C_v[P, R] over v, in
+// registers; B_v at TMEM columns [buf*256, +128), C_v at [buf*256 + 128, +128).
+// At the end of a tile D is rescaled and written transposed, Dt[b][R][P].
+template <class Bar>
+__device__ __forceinline__ void bcd_epilogue(Bar *bar, uint32_t tmem, const BcdArgs &a, int tP,
+                                             long long total, volatile int *abort, int warp, int lane) {
+  const int tiles_per_b = tP * tP;
+  const int q = warp & 3;                 // TMEM lane quarter of this warp
+  const int row = q * 32 + lane;          // P offset inside the tile
+  long long acc_it = 0;
+  for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+    const int b = (int)(t / tiles_per_b);
+    const int r = (int)(t % tiles_per_b);
+    const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
+    float d[kTile];
+#pragma unroll
+    for (int j = 0; j < kTile; ++j) d[j] = 0.f;
+    bool ok = true;
+    for (int v = 0; v < a.n; ++v, ++acc_it) {
+      const int buf = (int)(acc_it & 1);
+      const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+      ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
+#pragma unroll
+      for (int c = 0; c < kTile; c += 16) {
+        float bv[16], cv[16];
+        tc::tmem_ld_32x32b_x16(base + c, bv);
+        tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&bar->acc_empty[buf]);
+    }
+    if (!ok) break;
+    const int P = P0 + row;
+    if (P < a.N) {
+      const float rs = a.row_scale[(long long)b * a.N + P];
+      float *out = a.Dt + (long long)b * a.N * a.ldD + P;
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) {
+        const int R = R0 + j;
+        if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
+      }
+    }
+  }
+}
+
 // ============================================================================
 // Fused B / C / Hadamard-reduce (Sec. II C, the B, C and D steps):
 //   D[b][P][R] = sum_v (sum_q A[b][v][P][q] GR[b][R][q]) (sum_w GW[b][P][w] U2[v][R][w])
@@ -115,7 +173,7 @@ __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
 // (double-buffered), the Hadamard product accumulates in registers, and only
 // D leaves the SM, written transposed and rescaled: Dt[b][R][P].
 // ============================================================================
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kBcdThreads, 1)
     k_sox_bcd_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                  const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                  const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -130,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long total = (long long)a.batch * tiles_per_b;
   const int nk = a.Kp / kChunk;
 
-  setup_barriers(bar, 128);
+  setup_barriers(bar, kEpiThreads);
   if (warp == 1) {
     tc::tmem_alloc(&bar->tmem_base, 512);
     tc::tmem_relinquish();
@@ -220,50 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: D += B o C in registers ----------------
-    const int q = warp & 3;                 // TMEM lane quarter of this warp
-    const int row = q * 32 + lane;          // P offset inside the tile
-    long long acc_it = 0;
-    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
-      const int b = (int)(t / tiles_per_b);
-      const int r = (int)(t % tiles_per_b);
-      const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
-      float d[kTile];
-#pragma unroll
-      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
-      bool ok = true;
-      for (int v = 0; v < a.n; ++v, ++acc_it) {
-        const int buf = (int)(acc_it & 1);
-        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
-        ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
-        if (!ok) break;
-        tc::tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
-#pragma unroll
-        for (int c = 0; c < kTile; c += 16) {
-          float bv[16], cv[16];
-          tc::tmem_ld_32x32b_x16(base + c, bv);
-          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
-        }
-        tc::tc_fence_before();
-        tc::mbar_arrive(&bar->acc_empty[buf]);
-      }
-      if (!ok) break;
-      // rescale and store transposed: Dt[b][R][P]
-      const int P = P0 + row;
-      if (P < a.N) {
-        const float rs = a.row_scale[(long long)b * a.N + P];
-        float *out = a.Dt + (long long)b * a.N * a.ldD + P;
-#pragma unroll
-        for (int j = 0; j < kTile; ++j) {
-          const int R = R0 + j;
-          if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
-        }
-      }
-    }
+    bcd_epilogue(bar, tmem, a, tP, total, abort, warp, lane);
   }
   __syncthreads();
   if (warp == 1) {
@@ -315,7 +330,7 @@ __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kBcdThreads, 1)
     k_sox_bcd_tc_res(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                      const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                      const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_init(&bar->res_empty, 1);
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&bar->acc_full[b], 1);
-      tc::mbar_init(&bar->acc_empty[b], 128);
+      tc::mbar_init(&bar->acc_empty[b], kEpiThreads);
     }
     tc::mbar_init(&bar->drain, 1);
     bar->abort = 0;
@@ -453,48 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
-    long long acc_it = 0;
-    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
-      const int b = (int)(t / tiles_per_b);
-      const int r = (int)(t % tiles_per_b);
-      const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
-      float d[kTile];
-#pragma unroll
-      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
-      bool ok = true;
-      for (int v = 0; v < a.n; ++v, ++acc_it) {
-        const int buf = (int)(acc_it & 1);
-        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
-        ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
-        if (!ok) break;
-        tc::tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
-#pragma unroll
-        for (int c = 0; c < kTile; c += 16) {
-          float bv[16], cv[16];
-          tc::tmem_ld_32x32b_x16(base + c, bv);
-          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
-        }
-        tc::tc_fence_before();
-        tc::mbar_arrive(&bar->acc_empty[buf]);
-      }
-      if (!ok) break;
-      const int P = P0 + row;
-      if (P < a.N) {
-        const float rs = a.row_scale[(long long)b * a.N + P];
-        float *out = a.Dt + (long long)b * a.N * a.ldD + P;
-#pragma unroll
-        for (int j = 0; j < kTile; ++j) {
-          const int R = R0 + j;
-          if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
-        }
-      }
-    }
+    bcd_epilogue(bar, tmem, a, tP, total, abort, warp, lane);
   }
   __syncthreads();
   if (warp == 1) {
@@ -527,13 +501,17 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// The split GEMM runs 8 epilogue warps (two per TMEM lane quarter, one per
+// 64-column half): the epilogue, not the MMA, sets its pace.
+constexpr int kGemmThreads = 320;
+constexpr int kGemmEpi = 256;
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_f16x2(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                  const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                  const __grid_constant__ CUtensorMap tmC_hi, const __grid_constant__ CUtensorMap tmC_lo,
@@ -548,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long total = per_b * a.batch;
   const int nk = a.Kp / kChunk;
 
-  setup_barriers(bar, 128);
+  setup_barriers(bar, kGemmEpi);
   if (warp == 1) {
     tc::tmem_alloc(&bar->tmem_base, 256);
     tc::tmem_relinquish();
@@ -622,8 +600,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     const int q = warp & 3;
     const int row = q * 32 + lane;          // tile row = TMEM lane
+    const int h = (warp - 2) >> 2;          // 64-column half of the tile
     const bool storer = (warp == 2 && lane == 0);
-    __shared__ float red[4][2];
+    __shared__ float red[8];
     long long acc_it = 0;
     for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++acc_it) {
       const int b = (int)(t / per_b);
@@ -633,75 +612,68 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
       if (!tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8)) break;
       tc::tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 128;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 128 + h * 64;
       const bool row_ok = (i0 + row) < a.M;
-      float sc0 = 1.f, sc1 = 1.f;
+      // this half's columns belong to group g (groups are 64 or 128 columns wide)
+      const int g = (h * 64) >= a.group ? 1 : 0;
+      float sc = 1.f;
       if (a.mode == kStoreSplit) {
-        sc0 = sc1 = a.out_scale[b];
+        sc = a.out_scale[b];
       } else {
-        float m0 = 0.f, m1 = 0.f;
+        float m = 0.f;
 #pragma unroll
-        for (int c = 0; c < kTile; c += 32) {
+        for (int c = 0; c < 64; c += 32) {
           float v[32];
           tc::tmem_ld_32x32b_x32(base + c, v);
           tc::tmem_ld_wait();
           if (row_ok) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const bool second = (c + jj) >= a.group;
-              const float x = fabsf(v[jj]);
-              m0 = second ? m0 : fmaxf(m0, x);
-              m1 = second ? fmaxf(m1, x) : m1;
-            }
+            for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, fabsf(v[jj]));
           }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-          m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        }
-        if (lane == 0) {
-          red[q][0] = m0;
-          red[q][1] = m1;
-        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red[warp - 2] = m;
         epi_sync();
-        sc0 = tc::pow2_floor_inv(fmaxf(fmaxf(red[0][0], red[1][0]), fmaxf(red[2][0], red[3][0])));
-        sc1 = tc::pow2_floor_inv(fmaxf(fmaxf(red[0][1], red[1][1]), fmaxf(red[2][1], red[3][1])));
-        if (warp == 2 && lane < 2 && lane * a.group < kTile) {
-          const int grp = (j0 + lane * a.group) / a.group;
-          if (grp < a.n_groups) a.group_scale[(long long)b * a.n_groups + grp] = lane ? sc1 : sc0;
+        float mg = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < 8; ++w2) {
+          const int g2 = ((w2 >> 2) * 64) >= a.group ? 1 : 0;
+          if (g2 == g) mg = fmaxf(mg, red[w2]);
+        }
+        sc = tc::pow2_floor_inv(mg);
+        if (q == 0 && lane == 0 && (g == h)) {   // one writer per group: warp of quarter 0, half g
+          const int grp = (j0 + h * 64) / a.group;
+          if (grp < a.n_groups) a.group_scale[(long long)b * a.n_groups + grp] = sc;
         }
       }
       // the previous tile's TMA stores must have read the staging buffer
       if (storer) bulk_wait_read();
       epi_sync();
-      // split into FP16 pairs, written to the 128-byte-swizzled staging tiles
+      // split into FP16 pairs, written to the 128-byte-swizzled staging tile of this half
+      uint8_t *hi_tile = stage_out + (size_t)(0 * 2 + h) * (kTile * 128);
+      uint8_t *lo_tile = stage_out + (size_t)(1 * 2 + h) * (kTile * 128);
 #pragma unroll
-      for (int c = 0; c < kTile; c += 32) {
+      for (int c = 0; c < 64; c += 32) {
         float v[32];
         tc::tmem_ld_32x32b_x32(base + c, v);
         tc::tmem_ld_wait();
-        if (c == kTile - 32) {  // accumulator fully read: hand it back to the MMA warp
+        if (c == 32) {  // this half of the accumulator is read: hand it back
           tc::tc_fence_before();
           tc::mbar_arrive(&bar->acc_empty[buf]);
         }
-        const int h = c / 64;
-        uint8_t *hi_tile = stage_out + (size_t)(0 * 2 + h) * (kTile * 128);
-        uint8_t *lo_tile = stage_out + (size_t)(1 * 2 + h) * (kTile * 128);
 #pragma unroll
         for (int t16 = 0; t16 < 4; ++t16) {
           uint32_t ph[4], pl[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int jj = t16 * 8 + e * 2;
-            const float s0 = (c + jj) >= a.group ? sc1 : sc0;
-            const float s1 = (c + jj + 1) >= a.group ? sc1 : sc0;
             __half h0, l0, h1, l1;
-            tc::split_f16(v[jj] * s0, h0, l0);
-            tc::split_f16(v[jj + 1] * s1, h1, l1);
+            tc::split_f16(v[jj] * sc, h0, l0);
+            tc::split_f16(v[jj + 1] * sc, h1, l1);
             ph[e] = pack2(h0, h1);
             pl[e] = pack2(l0, l1);
           }
-          const int chunk = ((c % 64) / 8 + t16) ^ (row & 7);
+          const int chunk = (c / 8 + t16) ^ (row & 7);
           *reinterpret_cast<uint4 *>(hi_tile + row * 128 + chunk * 16) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
           *reinterpret_cast<uint4 *>(lo_tile + row * 128 + chunk * 16) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
         }
@@ -710,12 +682,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       epi_sync();
       if (storer) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int col = j0 + h * 64;
+        for (int hh = 0; hh < 2; ++hh) {
+          const int col = j0 + hh * 64;
           if (col < a.Ncols) {
             const int grp = col / a.group, x = col % a.group;
-            tma_store_4d(&tmC_hi, stage_out + (size_t)(0 * 2 + h) * (kTile * 128), x, grp, i0, b);
-            tma_store_4d(&tmC_lo, stage_out + (size_t)(1 * 2 + h) * (kTile * 128), x, grp, i0, b);
+            tma_store_4d(&tmC_hi, stage_out + (size_t)(0 * 2 + hh) * (kTile * 128), x, grp, i0, b);
+            tma_store_4d(&tmC_lo, stage_out + (size_t)(1 * 2 + hh) * (kTile * 128), x, grp, i0, b);
           }
         }
         bulk_commit();
@@ -983,12 +955,15 @@ __global__ void __launch_bounds__(256) k_backproject_T(const float *Dt, long lon
 
 // Sigma[b][t][r] = -sum_R X[R][t] T[b][R][r]   (FP64 accumulate: the final orbital-basis sum)
 __global__ void __launch_bounds__(256) k_backproject_sigma(const double *X, const float *T, int N, int n,
-                                                           double *Sigma, long long sstride) {
+                                                           double *Sigma, long long sstride, const int *sym) {
   __shared__ double sa[16][33];
   __shared__ double sb[16][33];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int t0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int b = blockIdx.z;
+  // symmetric Sigma (bare SOX, symmetric G): lower-triangle blocks are mirrored by the upper ones
+  const bool mirror = sym && sym[b];
+  if (mirror && blockIdx.y > blockIdx.x) return;
   const float *Tb = T + (long long)b * N * n;
   double acc[2][2] = {};
   for (int k0 = 0; k0 < N; k0 += 16) {
@@ -1019,7 +994,10 @@ __global__ void __launch_bounds__(256) k_backproject_sigma(const double *X, cons
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int c = c0 + tx + 16 * j;
-      if (c < n) Sigma[(long long)b * sstride + (long long)t * n + c] = -acc[i][j];
+      if (c < n) {
+        Sigma[(long long)b * sstride + (long long)t * n + c] = -acc[i][j];
+        if (mirror && blockIdx.y < blockIdx.x) Sigma[(long long)b * sstride + (long long)c * n + t] = -acc[i][j];
+      }
     }
   }
 }
@@ -1041,9 +1019,9 @@ void launch_backproject_T(const float *Dt, long long ldD, const double *X, int N
 }
 
 void launch_backproject_sigma(const double *X, const float *T, int N, int n, int batch, double *Sigma,
-                              long long sstride, cudaStream_t s) {
+                              long long sstride, cudaStream_t s, const int *sym) {
   dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
-  k_backproject_sigma<<<grid, 256, 0, s>>>(X, T, N, n, Sigma, sstride);
+  k_backproject_sigma<<<grid, 256, 0, s>>>(X, T, N, n, Sigma, sstride, sym);
 }
 
 size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers) + 1024; }
@@ -1059,7 +1037,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int gri
       if (e != cudaSuccess) return e;
       rattr = true;
     }
-    k_sox_bcd_tc_res<<<grid, kThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+    k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                maps[5], maps[6], maps[7], a);
     return cudaGetLastError();
   }
@@ -1070,7 +1048,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int gri
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_sox_bcd_tc<<<grid, kThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+  k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                                         maps[6], maps[7], a);
   return cudaGetLastError();
 }
@@ -1085,7 +1063,7 @@ cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int 
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gemm_f16x2<<<grid, kThreads, gemm_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
+  k_gemm_f16x2<<<grid, kGemmThreads, gemm_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,9 @@ void launch_bcd_scales(const float *inv_u1, const float *gsc, const float *osc, 
 // SIMT back-projection helpers (FP32 / FP64 accumulate), tc_kernels.cu
 void launch_backproject_T(const float *Dt, long long ldD, const double *X, int N, int n, int batch, float *T,
                           cudaStream_t s);
+// sym (optional, per batch): when set, Sigma[b] is symmetric and only the upper
+// block triangle is computed, then mirrored
 void launch_backproject_sigma(const double *X, const float *T, int N, int n, int batch, double *Sigma,
-                              long long sstride, cudaStream_t s);
+                              long long sstride, cudaStream_t s, const int *sym = nullptr);
 
 }  // namespace sox

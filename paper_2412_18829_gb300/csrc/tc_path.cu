@@ -188,7 +188,9 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
     {  // back-projection to orbitals
       ProfScope ps(h, "backproject", s, 2);
       launch_backproject_T(Dt, N, X, N, n, bc, Tm, s);
-      launch_backproject_sigma(X, Tm, N, n, bc, Sigma + (long long)b0 * n * n, (long long)n * n, s);
+      // bare SOX with a symmetric G(tau) has a symmetric Sigma(tau)
+      launch_backproject_sigma(X, Tm, N, n, bc, Sigma + (long long)b0 * n * n, (long long)n * n, s,
+                               two ? nullptr : symf);
     }
   }
   SOX_CUDA_TRY(cudaGetLastError());
