@@ -181,7 +181,10 @@ SOX_API int phi_sox(sox_handle h, const sox_problem *p, const double *G, const d
  *   dG[s][0][j][r][t] = dphi[s] * dPhi_s/dG_rt(tau_j)  = -dphi[s] w_j Sigma_tr(beta - tau_j)
  *   dX[0][P][p]       = sum_s dphi[s] dPhi_s/dX_pP
  *   dV[0][P][Q]       = sum_s dphi[s] dPhi_s/dV_PQ
- * with respect to the unsymmetrised entries.  Any of dG, dX, dV may be NULL. */
+ * with respect to the unsymmetrised entries.  Any of dG, dX, dV may be NULL.
+ * dG follows from Sigma by the identity above (computed in the handle's
+ * precision); dX and dV come from a reverse pass through the THC chain in FP64
+ * that recomputes B_v and C_v per tau chunk instead of storing them. */
 SOX_API int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const double *X,
                      const double *V, const double *w, const double *dphi, double *dG,
                      double *dX, double *dV, void *stream);

@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.h"
 #include "internal.h"
 #include "tc_path.h"
 
@@ -640,26 +641,37 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
   Status st = [&]() -> Status {
     SOX_TRY(validate(p));
     if (!G || !X || !V || !w || !dphi) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
-    if (dX || dV) return {SOX_ERR_UNSUPPORTED, "dPhi/dX and dPhi/dV are not implemented in this build"};
     SOX_TRY(bind_device(h));
     const Dims d = dims_of(p);
     const size_t nsig = (size_t)d.S * d.T * d.nn();
     Call call(h, stream);
-    Staged sG, sX, sV, sw, sd, oG;
+    Staged sG, sX, sV, sw, sd, oG, oX, oV;
     SOX_TRY(call.input(G, nsig, &sG));
     SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
     SOX_TRY(call.input(V, (size_t)d.N * d.N, &sV));
     SOX_TRY(call.input(w, (size_t)d.T, &sw));
     SOX_TRY(call.input(dphi, (size_t)d.S, &sd));
     SOX_TRY(call.output(dG, nsig, &oG));
+    SOX_TRY(call.output(dX, (size_t)d.N * d.n, &oX));
+    SOX_TRY(call.output(dV, (size_t)d.N * d.N, &oV));
+    size_t need = 0;
+    if (dG) need = sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8);
+    if (dX || dV) need = std::max(need, sox::adjoint_bytes(d.n, d.N, d.T, d.S, nullptr));
     Arena ar;
-    SOX_TRY(call.begin(sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8), &ar));
-    double *sig = ar.take<double>(nsig);
+    SOX_TRY(call.begin(need, &ar));
     cudaStream_t s = call.stream();
     if (oG.out) {
-      SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, sig, ar, s));
+      // dPhi/dG_rt(tau_j) = -w_j Sigma_tr(beta - tau_j) (bare SOX on a mirror-symmetric grid)
+      Arena a2 = ar;
+      double *sig = a2.take<double>(nsig);
+      SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, sig, a2, s));
       sox::ProfScope ps(h, "dG_identity", s);
       sox::launch_dG_from_sigma(sig, sw.in, sd.in, d.n, d.T, d.S, oG.out, s);
+    }
+    if (oX.out || oV.out) {
+      Arena a3 = ar;
+      SOX_TRY(sox::phi_adjoint_xv_f64(h, d.n, d.N, d.T, d.S, sG.in, sX.in, sV.in, sw.in, sd.in, oX.out, oV.out,
+                                      a3, s));
     }
     return call.end();
   }();

@@ -356,6 +356,12 @@ __global__ void k_symmetry_flags(const double *G, int n, int *flag) {
   if (threadIdx.x == 0) flag[b] = (sd[0] <= 1e-14 * sm[0]) ? 1 : 0;
 }
 
+__global__ void k_add(const double *a, const double *b, double *dst, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = a[e] + b[e];
+}
+
 inline int grid_for(long long total, int threads = 256) {
   long long b = (total + threads - 1) / threads;
   if (b > 65535LL * 16) b = 65535LL * 16;
@@ -425,6 +431,10 @@ void launch_build_gj_system(const double *V, const double *Pi, double *Aug, int 
 
 void launch_copy_right_half(const double *Aug, double *W, int N, cudaStream_t s) {
   k_copy_right<<<grid_for((long long)N * N), 256, 0, s>>>(Aug, W, N);
+}
+
+void launch_add_f64(const double *a, const double *b, double *dst, long long count, cudaStream_t s) {
+  k_add<<<grid_for(count), 256, 0, s>>>(a, b, dst, count);
 }
 
 void launch_symmetry_flags(const double *G, int n, int batch, int *flag, cudaStream_t s) {

@@ -130,6 +130,8 @@ void launch_pi0_reduce(const double *GPQ, const double *w, int N, int n_tau, dou
 void launch_gj_step(double *Aug, int N, int k, int *piv_info, cudaStream_t s);
 void launch_build_gj_system(const double *V, const double *Pi, double *Aug, int N, cudaStream_t s);
 void launch_copy_right_half(const double *Aug, double *W, int N, cudaStream_t s);
+// dst[i] = a[i] + b[i]
+void launch_add_f64(const double *a, const double *b, double *dst, long long count, cudaStream_t s);
 // flag[b] = 1 when G[b] (n x n) equals its transpose to 1e-14 of max|G[b]|, else 0
 void launch_symmetry_flags(const double *G, int n, int batch, int *flag, cudaStream_t s);
 void launch_neg_reflect(const double *src, double *dst, long long mat, int n_tau, int count,

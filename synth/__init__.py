@@ -174,8 +174,18 @@ def batch_c4(max_instances: int | None = None) -> list[Workload]:
     sizes = batch_c4_sizes()
     if max_instances is not None:
         sizes = sizes[:max_instances]
-    return [molecule(4, int(n), 6 * int(n), 120, 100.0, 1, instance=i,
-                     name=f"c4-inst{i}-n{int(n)}") for i, n in enumerate(sizes)]
+    return [c4_instance(i) for i in range(len(sizes))]
+
+
+def c4_instance(i: int) -> Workload:
+    """Instance i of the uneven batch (n from the batch-size stream, N = 6n, 120 tau)."""
+    n = int(batch_c4_sizes()[i])
+    return molecule(4, n, 6 * n, 120, 100.0, 1, instance=i, name=f"c4-inst{i}-n{n}")
+
+
+def c4_smallest(k: int = 3) -> list[int]:
+    """Indices of the k smallest instances of the uneven batch."""
+    return [int(i) for i in np.argsort(batch_c4_sizes(), kind="stable")[:k]]
 
 
 def kmesh(nk: tuple) -> np.ndarray:

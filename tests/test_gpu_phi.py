@@ -50,3 +50,79 @@ def test_phi_host_sigma_output(env):
     sig_ref = sox.sox_sigma(w.X, w.V, w.G).real
     np.testing.assert_allclose(out_sig, sig_ref, atol=1e-12 * np.abs(sig_ref).max())
     np.testing.assert_allclose(out_phi[0], phi.phi_trace(sig_ref[0, 0], w.G[0, 0], wt).real, rtol=1e-12)
+
+
+def _grads(env, w, wt, dphi):
+    torch, pkg, h = env
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    d = torch.tensor(dphi, dtype=torch.float64, device="cuda")
+    dX = torch.empty_like(X)
+    dV = torch.empty_like(V)
+    pkg.phi_sox_backward(h, p, G, X, V, tw, d, None, dX, dV)
+    torch.cuda.synchronize()
+    return dX.cpu().numpy()[0], dV.cpu().numpy()[0]
+
+
+@pytest.mark.parametrize("n,N,n_tau,n_spin", [(9, 30, 6, 1), (7, 41, 5, 2), (16, 70, 4, 1)])
+def test_adjoint_X_V_matches_oracle_autograd(env, n, N, n_tau, n_spin):
+    w = synth.molecule(23, n, N, n_tau, 3.0, n_spin=n_spin)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    dphi = [1.0, -0.5][:n_spin]
+    gX, gV = _grads(env, w, wt, dphi)
+    rX = np.zeros_like(gX)
+    rV = np.zeros_like(gV)
+    for s in range(n_spin):
+        _, _, x, v = phi.phi_and_grads(w.X[0], w.V[0], w.G[s, 0], wt)
+        rX += dphi[s] * x
+        rV += dphi[s] * v
+    assert np.abs(gX - rX).max() <= 1e-11 * np.abs(rX).max()
+    assert np.abs(gV - rV).max() <= 1e-11 * np.abs(rV).max()
+
+
+def test_phisox_autograd_returns_X_and_V_gradients(env):
+    torch, pkg, h = env
+    w = synth.molecule(24, 8, 25, 5, 3.0, n_spin=1)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    X.requires_grad_(True)
+    V.requires_grad_(True)
+    pkg.PhiSOX.apply(G, X, V, tw, h, p).sum().backward()
+    _, _, rX, rV = phi.phi_and_grads(w.X[0], w.V[0], w.G[0, 0], wt)
+    assert np.abs(X.grad.cpu().numpy()[0] - rX).max() <= 1e-11 * np.abs(rX).max()
+    assert np.abs(V.grad.cpu().numpy()[0] - rV).max() <= 1e-11 * np.abs(rV).max()
+
+
+@pytest.mark.parametrize("inst", synth.c4_smallest(3))
+def test_adjoint_central_differences_on_smallest_batch_instances(env, inst):
+    """Batch workload's three smallest instances (N = 6n, 120 tau): dPhi/dX and
+    dPhi/dV against central differences (h = 1e-6) of the FP64 Phi at sampled entries."""
+    torch, pkg, h = env
+    w = synth.c4_instance(inst)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def phi_of(Xa, Va):
+        pkg.phi_sox(h, p, G, Xa, Va, tw, out)
+        return float(out.item())
+
+    gX, gV = _grads(env, w, wt, [1.0])
+    rng = np.random.default_rng(inst)
+    hstep = 1e-6
+    for tensor, grad, name in ((X, gX, "X"), (V, gV, "V")):
+        scale = np.abs(grad).max()
+        for _ in range(8):
+            i = tuple(int(rng.integers(0, s)) for s in grad.shape)
+            if name == "V" and rng.random() < 0.5:   # favour the large leading block of V
+                i = (int(rng.integers(0, 8)), int(rng.integers(0, 8)))
+            base = tensor[(0,) + i].item()
+            tensor[(0,) + i] = base + hstep
+            fp = phi_of(X, V)
+            tensor[(0,) + i] = base - hstep
+            fm = phi_of(X, V)
+            tensor[(0,) + i] = base
+            fd = (fp - fm) / (2 * hstep)
+            assert abs(fd - grad[i]) <= 1e-6 * scale + 1e-7 * abs(grad[i]), (name, i, fd, grad[i], scale)

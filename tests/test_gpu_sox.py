@@ -210,3 +210,33 @@ def test_nonsymmetric_G_takes_the_general_projection(env, prec):
     w.G = np.ascontiguousarray(G)
     ref = sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64)
     check(_sigma(env, prec, w), ref, prec, "non-symmetric G")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_capture_in_cuda_graph_and_replay(env, prec):
+    """After one un-captured call sizes the workspace, a whole build is one
+    graph: no allocation, no host synchronisation inside the call."""
+    torch, pkg, hs = env
+    w = synth.molecule(18, 40, 200, 6, 100.0, n_spin=2)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    eager = torch.empty_like(G)
+    pkg.sox_sigma(hs[prec], p, G, X, V, eager)          # sizes the workspace
+    torch.cuda.synchronize()
+    out = torch.full_like(G, float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            pkg.sox_sigma(hs[prec], p, G, X, V, out)
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all()                        # capture ran nothing
+    for k in range(2):
+        G.mul_(1.0 + 0.01 * k)                           # new inputs in the captured buffers
+        graph.replay()
+        ref = torch.empty_like(G)
+        pkg.sox_sigma(hs[prec], p, G, X, V, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    pkg.sox_check_device(hs[prec])
