@@ -24,9 +24,13 @@
  *     X         [n_k][N][n]         X[k][P][p] = X^k_{pP}
  *     V, W0     [n_q][N][N]         U^q_{PQ}   (n_q = n_k)
  *   Real data (SOX_REAL64) are doubles; complex data (SOX_COMPLEX128) are
- *   interleaved (re, im) doubles.  Only SOX_REAL64 with n_k = 1 (molecules)
- *   is implemented by the entry points below; other forms return
- *   SOX_ERR_UNSUPPORTED.
+ *   interleaved (re, im) doubles.  Molecules are SOX_REAL64 with n_k = 1.
+ *   Solids (any k-mesh) are SOX_COMPLEX128: sox_sigma, sox_sigma_general and
+ *   sosex_static_sigma accept them and run the momentum-resolved chain in FP64
+ *   complex whatever the handle's precision; the other entry points return
+ *   SOX_ERR_UNSUPPORTED for complex data.
+ * - k labels run row-major over the mesh (k = 2 pi m / nk, m in [0, nk)^3);
+ *   V[q] is the THC metric of momentum transfer q = k_i - k_j (Sec. II C).
  * - The tau grid must be mirror-symmetric, tau_{n_tau-1-j} = beta - tau_j
  *   (Chebyshev-Lobatto, see sox_tau_grid): G(-tau_j) is taken as
  *   -G(tau_{n_tau-1-j}) (fermionic antiperiodicity of Eq. G_def).
@@ -135,7 +139,11 @@ SOX_API int thc_project_G(sox_handle h, const sox_problem *p, const double *G, c
                   double *G_Rq, double *G_wP, double *G_PQ, void *stream);
 
 /* Bare SOX self-energy, Eq. (sox) with U(1) = U(2) = v in THC form and the
- * static time collapse (Sec. II C):
+ * static time collapse (Sec. II C).  For a solid, with momentum transfers
+ * q1, q2 of the two interactions,
+ *   Sigma^k_tr = -1/N_k^2 sum_{q1,q2} U1^{q1}_(pr|qs) U2^{q2}_(tu|vw)
+ *                G^{k+q1}_wp(tau) G^{k-q2}_uq(tau) G^{k+q1-q2}_sv(-tau).
+ * Molecules:
  *   Sigma_tr(tau) = -sum U1_(pr|qs) U2_(tu|vw) G_wp(tau) G_uq(tau) G_sv(-tau).
  * Computed by the THC chain U_Pqs -> A -> (B o C summed over v) -> D ->
  * Sigma_RP = -D_PR -> Sigma_tr = sum_PR X_tR Sigma_RP X_rP.

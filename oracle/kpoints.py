@@ -1,0 +1,167 @@
+"""SOX self-energy of a periodic solid: the momentum-resolved forms (oracle).
+
+Test infrastructure; see the package docstring.
+
+Orbitals carry a momentum k (Sec. II A: G is block diagonal in k).  The THC
+integrals of Sec. II C are
+
+    (ij|sr) = sum_PQ (X^{k_i}_{iP})^* X^{k_j}_{jP} U^q_{PQ} (X^{k_s}_{sQ})^* X^{k_r}_{rQ},  q = k_i - k_j,
+
+non-zero only when k_i - k_j = k_r - k_s.  Inserting them into Eq. (sox) with
+the static time collapse leaves two free transfers q1 (of U1) and q2 (of U2):
+for the external momentum k (k_t = k_r = k)
+
+    Sigma^k_tr(tau) = -1/N_k^2 sum_{q1,q2} sum_{pqsuvw} U1^{q1}_(pr|qs) U2^{q2}_(tu|vw)
+                       G^{k+q1}_wp(tau) G^{k-q2}_uq(tau) G^{k+q1-q2}_sv(-tau)
+
+(the printed chain carries 1/N_k twice and garbled momentum labels; reading
+both normalisations as one 1/N_k^2 and all labels as k - q with q = k_i - k_j
+makes n_k = 1 the molecular formula and matches the brute force below).
+
+Arrays: X[k][P][p] = X^k_{pP}, V[q][P][Q] = U^q_{PQ}, G[k][n][n] at one tau;
+k labels are row-major integer triples of the mesh (``synth.kmesh``).
+Three routes: brute force over block-diagonal "big" matrices, the pure-THC
+form, and the paper's chain with mixed tensors U^{q,k}.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import grid
+
+
+def _kadd(ks: np.ndarray, nk: tuple, a: int, b: int, sign: int = 1) -> int:
+    m = np.mod(ks[a] + sign * ks[b], nk)
+    return int((m[0] * nk[1] + m[1]) * nk[2] + m[2])
+
+
+def k_tables(nk: tuple):
+    """add[a][b] = index of k_a + k_b, sub[a][b] = index of k_a - k_b."""
+    g = np.stack(np.meshgrid(*[np.arange(d) for d in nk], indexing="ij"), axis=-1).reshape(-1, 3)
+    n = g.shape[0]
+    add = np.array([[_kadd(g, nk, a, b, 1) for b in range(n)] for a in range(n)])
+    sub = np.array([[_kadd(g, nk, a, b, -1) for b in range(n)] for a in range(n)])
+    return add, sub
+
+
+def eri_big(X: np.ndarray, U: np.ndarray, nk: tuple) -> np.ndarray:
+    """4-index tensor over (k, orbital) with momentum conservation and the 1/N_k of a
+    per-cell integral: v[(a,i),(b,j),(c,s),(d,r)] = (ij|sr) / N_k, q = k_a - k_b."""
+    add, sub = k_tables(nk)
+    n_k, N, n = X.shape
+    v = np.zeros((n_k, n, n_k, n, n_k, n, n_k, n), dtype=complex)
+    for a in range(n_k):
+        for b in range(n_k):
+            q = sub[a, b]
+            left = np.einsum("Pi,Pj->ijP", X[a].conj(), X[b])
+            for c in range(n_k):
+                d = add[c, q]          # k_d - k_c = q  (k_r - k_s = k_i - k_j)
+                right = np.einsum("Qs,Qr->srQ", X[c].conj(), X[d])
+                v[a, :, b, :, c, :, d, :] = np.einsum("ijP,PQ,srQ->ijsr", left, U[q], right) / n_k
+    nt = n_k * n
+    return v.reshape(nt, nt, nt, nt)
+
+
+def sigma_bruteforce(X, U1, U2, Gk, Gmk, nk):
+    """Eq. (sox) over the big matrices; returns (Sigma^k blocks, the full big Sigma)."""
+    from .sox import sigma_bruteforce as mol
+
+    n_k, _, n = X.shape
+    nt = n_k * n
+    Gb = np.zeros((nt, nt), complex)
+    Gmb = np.zeros((nt, nt), complex)
+    for k in range(n_k):
+        Gb[k * n:(k + 1) * n, k * n:(k + 1) * n] = Gk[k]
+        Gmb[k * n:(k + 1) * n, k * n:(k + 1) * n] = Gmk[k]
+    big = mol(eri_big(X, U1, nk), eri_big(X, U2, nk), Gb, Gmb)
+    blocks = np.stack([big[k * n:(k + 1) * n, k * n:(k + 1) * n] for k in range(n_k)])
+    return blocks, big
+
+
+def _proj(Xa, G, Xb):
+    """G^{AB} = sum_ab X_a[A][a] G[a][b] conj(X_b[B][b])."""
+    return Xa @ G @ Xb.conj().T
+
+
+def sigma_thc_direct(X, U1, U2, Gk, Gmk, nk):
+    """Sigma^k_RP = -1/N_k^2 sum_{q1,q2} sum_QS U1^{q1}_PQ U2^{q2}_RS
+                     G^{SP}(k+q1) G^{RQ}(k-q2) G^{QS}(k+q1-q2, -tau);  Sigma^k = X_k^H Sigma_RP X_k."""
+    add, sub = k_tables(nk)
+    n_k = X.shape[0]
+    gp = [_proj(X[k], Gk[k], X[k]) for k in range(n_k)]
+    gm = [_proj(X[k], Gmk[k], X[k]) for k in range(n_k)]
+    out = []
+    for k in range(n_k):
+        S_RP = 0.0
+        for q1 in range(n_k):
+            kp = add[k, q1]
+            for q2 in range(n_k):
+                ku = sub[k, q2]
+                ks = sub[kp, q2]
+                M = np.einsum("RS,QS,SP->RQP", U2[q2], gm[ks], gp[kp], optimize=True)
+                S_RP = S_RP - np.einsum("PQ,RQ,RQP->RP", U1[q1], gp[ku], M, optimize=True)
+        S_RP = S_RP / n_k ** 2
+        out.append(X[k].conj().T @ S_RP @ X[k])
+    return np.stack(out)
+
+
+def mixed_tensors(U, X, nk):
+    """U^{q,k'}[P][a][b] = sum_Q U^q_PQ conj(X^{k'-q}_{aQ}) X^{k'}_{bQ}  for every (q, k')."""
+    add, sub = k_tables(nk)
+    n_k = X.shape[0]
+    out = np.empty((n_k, n_k) + (X.shape[1], X.shape[2], X.shape[2]), complex)
+    for q in range(n_k):
+        for kk in range(n_k):
+            out[q, kk] = np.einsum("PQ,Qa,Qb->Pab", U[q], X[sub[kk, q]].conj(), X[kk], optimize=True)
+    return out
+
+
+def sigma_chain(X, U1, U2, Gk, Gmk, nk, M1=None, M2=None):
+    """The paper's THC-SOX algorithm for solids (Sec. II C): mixed tensors, projections,
+    A, B per (q1, k_s), C per (q2, k_w), then the n_k^3 D step and back-projection."""
+    add, sub = k_tables(nk)
+    n_k, N, n = X.shape
+    M1 = mixed_tensors(U1, X, nk) if M1 is None else M1
+    M2 = mixed_tensors(U2, X, nk) if M2 is None else M2
+    GR = np.stack([X[k] @ Gk[k] for k in range(n_k)])                    # G_Rq (k_u)
+    GW = np.stack([Gk[k] @ X[k].conj().T for k in range(n_k)])           # G_wP (k_p)
+    # B^{q1,k_s}_{PRv} and C^{q2,k_w}_{RvP}
+    B = np.empty((n_k, n_k, N, N, n), complex)
+    C = np.empty((n_k, n_k, N, n, N), complex)
+    for q in range(n_k):
+        for kk in range(n_k):
+            A = np.einsum("Pqs,sv->Pqv", M1[q, kk], Gmk[kk], optimize=True)  # k_s = kk
+            B[q, kk] = np.einsum("Pqv,Rq->PRv", A, GR[sub[kk, q]], optimize=True)  # k_q = k_s - q1
+            C[q, kk] = np.einsum("Rvw,wP->RvP", M2[q, kk], GW[kk], optimize=True)  # k_w = kk
+    out = []
+    for k in range(n_k):
+        D = 0.0
+        for q1 in range(n_k):
+            kw = add[k, q1]                        # k_w = k_p = k + q1
+            for q2 in range(n_k):
+                ks = sub[kw, q2]                   # k_s = k + q1 - q2
+                D = D + np.einsum("RvP,PRv->PR", C[q2, kw], B[q1, ks], optimize=True)
+        S_RP = -D.T / n_k ** 2
+        out.append(X[k].conj().T @ S_RP @ X[k])
+    return np.stack(out)
+
+
+def sox_sigma(X, V, G, nk, route="chain", taus=None, U2=None):
+    """Bare SOX (or SOX(V, U2)) for a solid, library layout G [n_spin][n_k][n_tau][n][n]."""
+    U2 = V if U2 is None else U2
+    n_spin, n_k, n_tau = G.shape[:3]
+    idx = range(n_tau) if taus is None else taus
+    res = np.empty((n_spin, n_k, len(list(idx)), G.shape[-1], G.shape[-1]), complex)
+    M1 = mixed_tensors(V, X, nk) if route == "chain" else None
+    M2 = (M1 if U2 is V else mixed_tensors(U2, X, nk)) if route == "chain" else None
+    for s in range(n_spin):
+        Gm = grid.g_minus_tau(np.asarray(G[s], complex))
+        for o, j in enumerate(idx):
+            Gk, Gmk = G[s][:, j], Gm[:, j]
+            if route == "chain":
+                res[s, :, o] = sigma_chain(X, V, U2, Gk, Gmk, nk, M1, M2)
+            elif route == "direct":
+                res[s, :, o] = sigma_thc_direct(X, V, U2, Gk, Gmk, nk)
+            else:
+                res[s, :, o] = sigma_bruteforce(X, V, U2, Gk, Gmk, nk)[0]
+    return res

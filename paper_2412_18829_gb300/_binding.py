@@ -86,19 +86,22 @@ def lib() -> ctypes.CDLL:
 
 
 def _ptr(t):
-    """Raw pointer of a contiguous float64 tensor/array (None -> NULL)."""
+    """Raw pointer of a contiguous float64 or complex128 tensor/array (None -> NULL).
+
+    complex128 data are passed as interleaved (re, im) doubles, the library's
+    SOX_COMPLEX128 layout."""
     if t is None:
         return None
     if isinstance(t, np.ndarray):
-        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
-            raise ValueError("numpy arrays must be C-contiguous float64")
+        if t.dtype not in (np.float64, np.complex128) or not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be C-contiguous float64 or complex128")
         return t.ctypes.data
     import torch
 
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"unsupported tensor type {type(t)}")
-    if t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError("tensors must be contiguous float64")
+    if t.dtype not in (torch.float64, torch.complex128) or not t.is_contiguous():
+        raise ValueError("tensors must be contiguous float64 or complex128")
     return t.data_ptr()
 
 

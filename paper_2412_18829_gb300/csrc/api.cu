@@ -8,6 +8,7 @@
 
 #include "adjoint.h"
 #include "internal.h"
+#include "kpoint.h"
 #include "tc_path.h"
 
 using sox::Arena;
@@ -276,11 +277,37 @@ Status sigma_any(sox_handle h, const Dims &d, const double *G, const double *X, 
   return sigma_fp64(h, d, G, X, U1, U2, Sigma, ar, s);
 }
 
+// Solids (complex data, any k-mesh): the momentum-resolved chain in FP64 complex.
+Status run_sigma_complex(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                         const double *U1, const double *U2, double *Sigma, void *stream) {
+  SOX_TRY(validate(p, false));
+  if (p->dtype != SOX_COMPLEX128)
+    return {SOX_ERR_UNSUPPORTED, "k-point meshes need complex data (SOX_COMPLEX128)"};
+  SOX_TRY(bind_device(h));
+  const int nk = p->nk[0] * p->nk[1] * p->nk[2];
+  const size_t nn = (size_t)p->n * p->n;
+  Call call(h, stream);
+  Staged sG, sX, s1, s2, sS;
+  SOX_TRY(call.input(G, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &sG));
+  SOX_TRY(call.input(X, 2 * (size_t)nk * p->N * p->n, &sX));
+  SOX_TRY(call.input(U1, 2 * (size_t)nk * p->N * p->N, &s1));
+  const bool same = (U1 == U2);
+  if (!same) SOX_TRY(call.input(U2, 2 * (size_t)nk * p->N * p->N, &s2));
+  SOX_TRY(call.output(Sigma, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &sS));
+  Arena ar;
+  const sox::KpointPlan pl = sox::kpoint_plan(p->n, p->N, p->n_tau, p->n_spin, p->nk);
+  SOX_TRY(call.begin(pl.bytes + (same ? 0 : 16 * (size_t)nk * nk * p->N * nn), &ar));
+  SOX_TRY(sox::kpoint_sigma_f64(h, p, sG.in, sX.in, s1.in, same ? s1.in : s2.in, sS.out, ar, call.stream()));
+  return call.end();
+}
+
 Status run_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                  const double *U1, const double *U2, double *Sigma, void *stream) {
   if (!h) return {SOX_ERR_INVALID_ARG, "handle is NULL"};
-  SOX_TRY(validate(p));
   if (!G || !X || !U1 || !U2 || !Sigma) return {SOX_ERR_INVALID_ARG, "a required tensor pointer is NULL"};
+  if (p && (p->dtype == SOX_COMPLEX128 || p->nk[0] * p->nk[1] * p->nk[2] != 1))
+    return run_sigma_complex(h, p, G, X, U1, U2, Sigma, stream);
+  SOX_TRY(validate(p));
   SOX_TRY(bind_device(h));
   const Dims d = dims_of(p);
   Call call(h, stream);

@@ -1,0 +1,331 @@
+// Static SOX for periodic solids (Sec. II C, the algorithm with momenta), FP64
+// complex on CUDA cores.
+//
+// For the external momentum k and transfers q1, q2 (labels k - q with q = k_i - k_j):
+//   M^{q,k'}[P][a][b] = sum_Q U^q_PQ conj(X^{k'-q}_{aQ}) X^{k'}_{bQ}        (mixed tensors)
+//   GR^k = X^k G^k,  GWt^k[P][w] = sum_p conj(X^k[P][p]) G^k[w][p]
+//   A^{q1,ks}[v][P][q] = sum_s G^{ks}(-tau)[s][v] M^{q1,ks}[P][q][s]
+//   B^{q1,ks}_v[P][R]  = sum_q A^{q1,ks}[v][P][q] GR^{ks-q1}[R][q]             (regime 1)
+//   C^{q2,kw}_v[P][R]  = sum_w GWt^{kw}[P][w] M^{q2,kw}[R][v][w]               (regime 1)
+//   D^k[P][R] = sum_{q1,q2} sum_v C^{q2,k+q1}_v[P][R] B^{q1,k+q1-q2}_v[P][R]    (regime 2)
+//   Sigma^k[t][r] = -1/N_k^2 sum_R conj(X^k[R][t]) sum_P D^k[P][R] X^k[P][r]
+// B and C for every (q, k') pair are produced for a chunk of v at a time.
+#include <algorithm>
+#include <vector>
+
+#include "kpoint.h"
+
+namespace sox {
+namespace {
+
+using z = double2;
+__device__ __forceinline__ z zmul(z a, z b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ z zfma(z a, z b, z c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ z zconj(z a) { return make_double2(a.x, -a.y); }
+
+constexpr int TM = 64, TK = 8, NT = 256;
+
+// Grouped complex GEMM: C[b](i,j) = alpha sum_k opA(i,k) opB(k,j) + beta C[b](i,j),
+// opX = conj(X) when conjX; batch b at base + (off ? off[b] : b * stride) elements.
+struct ZGemm {
+  int M, Nc, K, batch;
+  const z *A; long long sA, ai, ak; const long long *offA; int conjA;
+  const z *B; long long sB, bk, bj; const long long *offB; int conjB;
+  z *C; long long sC, ci, cj; const long long *offC;
+  double alpha, beta;
+};
+
+__global__ void __launch_bounds__(NT) k_zgemm(ZGemm g) {
+  __shared__ z sa[TK][TM + 1];
+  __shared__ z sb[TK][TM + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TM;
+  const long long b = blockIdx.z;
+  const z *A = g.A + (g.offA ? g.offA[b] : b * g.sA);
+  const z *B = g.B + (g.offB ? g.offB[b] : b * g.sB);
+  z *C = g.C + (g.offC ? g.offC[b] : b * g.sC);
+  z acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < g.K; k0 += TK) {
+#pragma unroll
+    for (int it = 0; it < (TM * TK) / NT; ++it) {
+      const int e = tid + it * NT;
+      int r, k;
+      if (g.ak == 1) { r = e / TK; k = e % TK; } else { r = e % TM; k = e / TM; }
+      const int gr = i0 + r, gk = k0 + k;
+      z v = make_double2(0.0, 0.0);
+      if (gr < g.M && gk < g.K) v = A[gr * g.ai + gk * g.ak];
+      sa[k][r] = g.conjA ? zconj(v) : v;
+      int c, kb;
+      if (g.bj == 1) { c = e % TM; kb = e / TM; } else { c = e / TK; kb = e % TK; }
+      const int gc = j0 + c, gkb = k0 + kb;
+      z w = make_double2(0.0, 0.0);
+      if (gc < g.Nc && gkb < g.K) w = B[gkb * g.bk + gc * g.bj];
+      sb[kb][c] = g.conjB ? zconj(w) : w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      z av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sa[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = sb[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zfma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + ty + 16 * i;
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tx + 16 * j;
+      if (gj >= g.Nc) continue;
+      z *c = C + gi * g.ci + gj * g.cj;
+      z v = make_double2(g.alpha * acc[i][j].x, g.alpha * acc[i][j].y);
+      if (g.beta != 0.0) v = make_double2(v.x + g.beta * c->x, v.y + g.beta * c->y);
+      *c = v;
+    }
+  }
+}
+
+void zgemm(const ZGemm &g, cudaStream_t s) {
+  if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return;
+  dim3 grid((g.Nc + TM - 1) / TM, (g.M + TM - 1) / TM, g.batch);
+  k_zgemm<<<grid, NT, 0, s>>>(g);
+}
+
+ZGemm zg() {
+  ZGemm g{};
+  g.batch = 1;
+  g.alpha = 1.0;
+  return g;
+}
+
+// Y[pair][Q][a][b] = conj(X[k'-q][Q][a]) X[k'][Q][b] for every (q, k') pair
+__global__ void k_kpair_products(const z *X, const int *sub, int nk, int N, int n, z *Y) {
+  const long long per = (long long)N * n * n;
+  const long long total = per * nk * nk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int pair = (int)(e / per);
+    const long long r = e % per;
+    const int Q = (int)(r / ((long long)n * n));
+    const int a = (int)((r / n) % n), bb = (int)(r % n);
+    const int q = pair / nk, kk = pair % nk;
+    const int ka = sub[kk * nk + q];
+    Y[e] = zmul(zconj(X[((long long)ka * N + Q) * n + a]), X[((long long)kk * N + Q) * n + bb]);
+  }
+}
+
+// D[k][P][R] += sum_{q1,q2} sum_{v<nv} C[(q2, k+q1)][v][P][R] * B[(q1, k+q1-q2)][v][P][R]
+__global__ void k_kpoint_D(const z *B, const z *C, const int *add, const int *sub, int nk, int N, int nv,
+                           z *D) {
+  const int R = blockIdx.x * 32 + threadIdx.x;
+  const int P = blockIdx.y * 8 + threadIdx.y;
+  const int k = blockIdx.z;
+  if (P >= N || R >= N) return;
+  const long long NN = (long long)N * N, pe = (long long)P * N + R;
+  z acc = D[(long long)k * NN + pe];
+  for (int q1 = 0; q1 < nk; ++q1) {
+    const int kw = add[k * nk + q1];
+    for (int q2 = 0; q2 < nk; ++q2) {
+      const int ks = sub[kw * nk + q2];
+      const z *c = C + ((long long)(q2 * nk + kw) * nv) * NN + pe;
+      const z *b = B + ((long long)(q1 * nk + ks) * nv) * NN + pe;
+      for (int v = 0; v < nv; ++v) acc = zfma(c[v * NN], b[v * NN], acc);
+    }
+  }
+  D[(long long)k * NN + pe] = acc;
+}
+
+int grid1(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 65535 * 8)); }
+
+}  // namespace
+
+KpointPlan kpoint_plan(int n, int N, int T, int S, const int nkv[3]) {
+  KpointPlan p{};
+  p.nk = nkv[0] * nkv[1] * nkv[2];
+  const size_t nk2 = (size_t)p.nk * p.nk;
+  const size_t Nn2 = (size_t)N * n * n, NN = (size_t)N * N, Nn = (size_t)N * n;
+  p.fixed_bytes = 16 * (2 * nk2 * Nn2 /*Y, M*/ + (size_t)p.nk * (2 * Nn + NN + Nn) /*GR, GWt, D, T*/) +
+                  8 * 2 * nk2 /*tables*/ + 64 * 1024;
+  const size_t per_v = 16 * nk2 * (2 * NN /*B, C*/ + Nn /*A*/);
+  const size_t budget = size_t(24) << 30;
+  long long nv = budget > p.fixed_bytes ? (long long)((budget - p.fixed_bytes) / per_v) : 1;
+  p.nv = (int)std::max<long long>(1, std::min<long long>(nv, n));
+  p.bytes = p.fixed_bytes + per_v * p.nv + 16 * (size_t)3 * nk2 * p.nv * sizeof(long long) + 64 * 1024;
+  (void)T;
+  (void)S;
+  return p;
+}
+
+Status kpoint_sigma_f64(sox_handle h, const sox_problem *pr, const double *Gd, const double *Xd, const double *U1d,
+                        const double *U2d, double *Sd, Arena &ar, cudaStream_t s) {
+  const int n = pr->n, N = pr->N, T = pr->n_tau, S = pr->n_spin;
+  const KpointPlan pl = kpoint_plan(n, N, T, S, pr->nk);
+  const int nk = pl.nk, nv = pl.nv;
+  const long long nn = (long long)n * n, Nn2 = (long long)N * nn, NN = (long long)N * N, Nn = (long long)N * n;
+  const long long nk2 = (long long)nk * nk;
+  const z *G = reinterpret_cast<const z *>(Gd);
+  const z *X = reinterpret_cast<const z *>(Xd);
+  const z *U1 = reinterpret_cast<const z *>(U1d);
+  const z *U2 = reinterpret_cast<const z *>(U2d);
+  z *Sig = reinterpret_cast<z *>(Sd);
+  const bool two = (U1d != U2d);
+
+  // momentum tables (host -> device, through the workspace)
+  std::vector<int> add(nk * nk), sub(nk * nk);
+  {
+    std::vector<int> m(3 * nk);
+    for (int a = 0; a < nk; ++a) {
+      m[3 * a + 0] = a / (pr->nk[1] * pr->nk[2]);
+      m[3 * a + 1] = (a / pr->nk[2]) % pr->nk[1];
+      m[3 * a + 2] = a % pr->nk[2];
+    }
+    auto idx = [&](int x, int y, int zz) {
+      x = ((x % pr->nk[0]) + pr->nk[0]) % pr->nk[0];
+      y = ((y % pr->nk[1]) + pr->nk[1]) % pr->nk[1];
+      zz = ((zz % pr->nk[2]) + pr->nk[2]) % pr->nk[2];
+      return (x * pr->nk[1] + y) * pr->nk[2] + zz;
+    };
+    for (int a = 0; a < nk; ++a)
+      for (int b = 0; b < nk; ++b) {
+        add[a * nk + b] = idx(m[3 * a] + m[3 * b], m[3 * a + 1] + m[3 * b + 1], m[3 * a + 2] + m[3 * b + 2]);
+        sub[a * nk + b] = idx(m[3 * a] - m[3 * b], m[3 * a + 1] - m[3 * b + 1], m[3 * a + 2] - m[3 * b + 2]);
+      }
+  }
+  int *d_add = ar.take<int>(nk2), *d_sub = ar.take<int>(nk2);
+  z *Y = ar.take<z>(nk2 * Nn2), *M1 = ar.take<z>(nk2 * Nn2);
+  z *M2 = two ? ar.take<z>(nk2 * Nn2) : M1;
+  z *GR = ar.take<z>((size_t)nk * Nn), *GWt = ar.take<z>((size_t)nk * Nn);
+  z *D = ar.take<z>((size_t)nk * NN), *Tm = ar.take<z>((size_t)nk * Nn);
+  z *A = ar.take<z>((size_t)nk2 * nv * Nn);
+  z *Bc = ar.take<z>((size_t)nk2 * nv * NN), *Cc = ar.take<z>((size_t)nk2 * nv * NN);
+  long long *offA = ar.take<long long>(nk2 * nv), *offB = ar.take<long long>(nk2 * nv);
+  long long *offC = ar.take<long long>(nk2 * nv), *offD = ar.take<long long>(nk2 * nv);
+  if (!offD) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  SOX_CUDA_TRY(cudaMemcpyAsync(d_add, add.data(), 4 * nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(d_sub, sub.data(), 4 * nk2, cudaMemcpyHostToDevice, s));
+  ProfScope ps(h, "kpoint_f64", s, 0);
+  long long launches = 0;
+
+  // mixed tensors for every (q, k'): M[q][k'] = U^q Y[q][k']   (Y as [Q][(a,b)])
+  auto mixed = [&](const z *U, z *Mout) {
+    for (int q = 0; q < nk; ++q) {
+      ZGemm g = zg();
+      g.M = N; g.Nc = (int)nn; g.K = N; g.batch = nk;
+      g.A = U + (long long)q * NN; g.ai = N; g.ak = 1;
+      g.B = Y + (long long)q * nk * Nn2; g.sB = Nn2; g.bk = nn; g.bj = 1;
+      g.C = Mout + (long long)q * nk * Nn2; g.sC = Nn2; g.ci = nn; g.cj = 1;
+      zgemm(g, s);
+      ++launches;
+    }
+  };
+  k_kpair_products<<<grid1(nk2 * Nn2), 256, 0, s>>>(X, d_sub, nk, N, n, Y);
+  ++launches;
+  mixed(U1, M1);
+  if (two) mixed(U2, M2);
+
+  // offset tables for the grouped GEMMs of one v-chunk (host-built, uploaded once per chunk shape)
+  std::vector<long long> hA(nk2 * nv), hB(nk2 * nv), hC(nk2 * nv), hD(nk2 * nv);
+  const double inv_nk2 = 1.0 / ((double)nk * nk);
+  for (int sp = 0; sp < S; ++sp) {
+    for (int j = 0; j < T; ++j) {
+      const z *Gj = G + ((long long)sp * nk * T) * nn;   // G[sp][k][t] at + (k*T + t)*nn
+      // projections for every k at tau_j
+      {
+        ZGemm g = zg();  // GR[k] = X[k] G[k](tau_j)
+        g.M = N; g.Nc = n; g.K = n; g.batch = nk;
+        g.A = X; g.sA = Nn; g.ai = n; g.ak = 1;
+        g.B = Gj + (long long)j * nn; g.sB = (long long)T * nn; g.bk = n; g.bj = 1;
+        g.C = GR; g.sC = Nn; g.ci = n; g.cj = 1;
+        zgemm(g, s);
+        ZGemm w = g;     // GWt[k][P][w] = sum_p conj(X[k][P][p]) G[k][w][p]
+        w.conjA = 1; w.bk = 1; w.bj = n; w.C = GWt;
+        zgemm(w, s);
+        launches += 2;
+      }
+      SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)nk * NN, s));
+      for (int v0 = 0; v0 < n; v0 += nv) {
+        const int cv = std::min(nv, n - v0);
+        // A[pair][vl][P][q] = -sum_s G^{k'}(tau_{T-1-j})[s][v0+vl] M1[pair][P][q][s]
+        for (int q = 0; q < nk; ++q) {
+          ZGemm g = zg();
+          g.M = cv; g.Nc = N * n; g.K = n; g.batch = nk;
+          g.A = Gj + (long long)(T - 1 - j) * nn + v0; g.sA = (long long)T * nn; g.ai = 1; g.ak = n;
+          g.B = M1 + (long long)q * nk * Nn2; g.sB = Nn2; g.bk = 1; g.bj = n;
+          g.C = A + (long long)q * nk * cv * Nn; g.sC = (long long)cv * Nn; g.ci = Nn; g.cj = 1;
+          g.alpha = -1.0;
+          zgemm(g, s);
+          ++launches;
+        }
+        // B[pair][vl][P][R] = sum_q A[pair][vl][P][q] GR[k'-q1][R][q]     (grouped over pair, vl)
+        // C[pair][vl][P][R] = sum_w GWt[k'][P][w] M2[pair][R][v][w]      (grouped over pair, vl)
+        for (int q = 0; q < nk; ++q)
+          for (int kk = 0; kk < nk; ++kk)
+            for (int vl = 0; vl < cv; ++vl) {
+              const long long b = ((long long)q * nk + kk) * cv + vl;
+              hA[b] = (((long long)q * nk + kk) * cv + vl) * Nn;       // A slice
+              hB[b] = (long long)sub[kk * nk + q] * Nn;                 // GR[k'-q]
+              hC[b] = (long long)kk * Nn;                               // GWt[k']
+              hD[b] = ((long long)q * nk + kk) * Nn2 + (long long)(v0 + vl) * n;  // M2[pair][.][v][.]
+            }
+        const long long nb = nk2 * cv;
+        SOX_CUDA_TRY(cudaMemcpyAsync(offA, hA.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(offB, hB.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(offC, hC.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(offD, hD.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        ZGemm gb = zg();
+        gb.M = N; gb.Nc = N; gb.K = n; gb.batch = (int)nb;
+        gb.A = A; gb.offA = offA; gb.ai = n; gb.ak = 1;
+        gb.B = GR; gb.offB = offB; gb.bk = 1; gb.bj = n;
+        gb.C = Bc; gb.sC = NN; gb.ci = N; gb.cj = 1;
+        zgemm(gb, s);
+        ZGemm gc = zg();
+        gc.M = N; gc.Nc = N; gc.K = n; gc.batch = (int)nb;
+        gc.A = GWt; gc.offA = offC; gc.ai = n; gc.ak = 1;
+        gc.B = M2; gc.offB = offD; gc.bk = 1; gc.bj = nn;
+        gc.C = Cc; gc.sC = NN; gc.ci = N; gc.cj = 1;
+        zgemm(gc, s);
+        {
+          dim3 grid((N + 31) / 32, (N + 7) / 8, nk);
+          k_kpoint_D<<<grid, dim3(32, 8), 0, s>>>(Bc, Cc, d_add, d_sub, nk, N, cv, D);
+        }
+        launches += 3;
+        // (the host tables may be rewritten now: a copy from pageable memory returns only
+        // once the host buffer has been staged, and stream order protects the device tables)
+      }
+      // Sigma^k = -1/N_k^2 X^H D^T X :  T[k][R][r] = sum_P D[k][P][R] X[k][P][r]
+      ZGemm t = zg();
+      t.M = N; t.Nc = n; t.K = N; t.batch = nk;
+      t.A = D; t.sA = NN; t.ai = 1; t.ak = N;
+      t.B = X; t.sB = Nn; t.bk = n; t.bj = 1;
+      t.C = Tm; t.sC = Nn; t.ci = n; t.cj = 1;
+      zgemm(t, s);
+      ZGemm o = zg();  // Sigma[sp][k][j][t][r] = -1/N_k^2 sum_R conj(X[k][R][t]) T[k][R][r]
+      o.M = n; o.Nc = n; o.K = N; o.batch = nk;
+      o.A = X; o.sA = Nn; o.ai = 1; o.ak = n; o.conjA = 1;
+      o.B = Tm; o.sB = Nn; o.bk = n; o.bj = 1;
+      o.C = Sig + ((long long)sp * nk * T + j) * nn; o.sC = (long long)T * nn; o.ci = n; o.cj = 1;
+      o.alpha = -inv_nk2;
+      zgemm(o, s);
+      launches += 2;
+    }
+  }
+  h->launches += launches;
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+}  // namespace sox
