@@ -20,4 +20,4 @@ real molecular data) written from the paper's definitions:
 * ``dynamic``    dynamically screened SOSEX (Eq. GG onward, Sec. II C).
 * ``kpoints``    the momentum-resolved forms for periodic solids.
 """
-from . import grid, thc, sox, screening, phi  # noqa: F401
+from . import grid, thc, sox, screening, phi, kpoints, dynamic  # noqa: F401

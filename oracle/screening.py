@@ -52,3 +52,22 @@ def w_static(V: np.ndarray, Pi: np.ndarray) -> np.ndarray:
     Vh = (Q * s) @ Q.conj().T
     K = np.eye(V.shape[0]) - Vh @ Pi @ Vh
     return Vh @ np.linalg.solve(K, Vh)
+
+
+def pi_omega(X: np.ndarray, G_tau: np.ndarray, T_fwd: np.ndarray) -> np.ndarray:
+    """Pi_PQ(i Omega_m) = sum_j T_fwd[m][j] G^PQ(tau_j) G^QP(-tau_j): the transform of the
+    bosonic polarisability Pi(tau) = G^PQ(tau) G^QP(-tau) (THC form of the RPA bubble)."""
+    Gm_tau = grid.g_minus_tau(G_tau)
+    pit = np.stack([thc.project_full(X, G_tau[j]) * thc.project_full(X, Gm_tau[j]).T
+                    for j in range(G_tau.shape[0])])
+    return np.einsum("mj,jPQ->mPQ", T_fwd, pit)
+
+
+def w_dynamic(V: np.ndarray, Pi_om: np.ndarray) -> np.ndarray:
+    """W_d(i Omega_m) = W(i Omega_m) - V with W = V^1/2 (1 - V^1/2 Pi V^1/2)^-1 V^1/2 per m;
+    real for a real molecule (Pi(i Omega) is real and even in Omega)."""
+    out = []
+    for m in range(Pi_om.shape[0]):
+        P = Pi_om[m].real
+        out.append(w_static(V, 0.5 * (P + P.T)) - V)
+    return np.stack(out)

@@ -177,6 +177,30 @@ def batch_c4(max_instances: int | None = None) -> list[Workload]:
     return [c4_instance(i) for i in range(len(sizes))]
 
 
+def bosonic_transforms(tau: np.ndarray, beta: float, M: int, n_gl: int = 512):
+    """Caller-side tau <-> i Omega transform pair for bosonic functions on the grid.
+
+    Omega_m = 2 pi m / beta, m = -M..M.  T_fwd[m][j] = int_0^beta e^{i Omega_m s} L_j(s) ds with
+    L_j the cardinal polynomial of the Chebyshev-Lobatto nodes (barycentric form), integrated
+    by n_gl-point Gauss-Legendre; T_inv[i][m] = e^{-i Omega_m tau_i} / beta.  These are inputs
+    (the paper takes its grids and transforms from sparse-ir), not self-energy arithmetic.
+    """
+    n = tau.size
+    om = 2.0 * np.pi * np.arange(-M, M + 1) / beta
+    x, wg = np.polynomial.legendre.leggauss(n_gl)
+    s = 0.5 * beta * (x + 1.0)
+    wg = 0.5 * beta * wg
+    bw = np.array([(-1.0) ** j for j in range(n)])
+    bw[0] *= 0.5
+    bw[-1] *= 0.5
+    d = s[:, None] - tau[None, :]
+    ratio = bw[None, :] / d
+    L = ratio / ratio.sum(axis=1, keepdims=True)          # [gl][j]
+    T_fwd = (np.exp(1j * om[:, None] * s[None, :]) * wg[None, :]) @ L
+    T_inv = np.exp(-1j * tau[:, None] * om[None, :]) / beta
+    return om, np.ascontiguousarray(T_fwd), np.ascontiguousarray(T_inv)
+
+
 def c4_instance(i: int) -> Workload:
     """Instance i of the uneven batch (n from the batch-size stream, N = 6n, 120 tau)."""
     n = int(batch_c4_sizes()[i])
