@@ -197,13 +197,17 @@ SOX_API int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G
                      const double *V, const double *w, const double *dphi, double *dG,
                      double *dX, double *dV, void *stream);
 
-/* Dynamically screened SOSEX (Sec. II C, Eq. GG and the steps after it):
+/* Dynamically screened SOSEX for molecules (Sec. II C, Eq. GG and the steps
+ * after it):
  *   Sigma = SOX(v, v) + Sigma_d with
  *   Sigma_d,tr(tau_i) = -sum v_(tu|vw) G_wp(tau_i)
  *        sum_m T_inv[i][m] sum_j T_fwd[m][j] Wd_(pr|qs)(i Omega_m) G_uq(tau_j) G_sv(-tau_j)
- * Wd [1][n_omega][N][N] real (W(i Omega_m) - v), T_fwd [n_omega][n_tau] and
- * T_inv [n_tau][n_omega] complex (interleaved).  The transform pair is the
- * caller's (the paper uses sparse-ir, Sec. II C). */
+ * Wd [n_omega][N][N] real: W(i Omega_m) - v, real and even in Omega for a real
+ * molecule; T_fwd [n_omega][n_tau] and T_inv [n_tau][n_omega] complex
+ * (interleaved).  The transform pair is the caller's (the paper uses sparse-ir,
+ * Sec. II C).  SOX(v, v) runs in the handle's precision, Sigma_d in FP64 with v in
+ * the outer loop (GG, transform, W_d product, inverse transform, then the fused
+ * B/C/D kernel with X in place of G_Rq).  Solids return SOX_ERR_UNSUPPORTED. */
 SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream);

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "adjoint.h"
+#include "dynamic.h"
 #include "internal.h"
 #include "kpoint.h"
 #include "tc_path.h"
@@ -709,10 +710,34 @@ int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, con
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream) {
   if (!h) return SOX_ERR_INVALID_ARG;
-  (void)G; (void)X; (void)V; (void)Wd; (void)T_fwd; (void)T_inv; (void)n_omega; (void)Sigma;
-  (void)stream;
-  Status st = validate(p);
-  if (st.good()) st = {SOX_ERR_UNSUPPORTED, "dynamically screened SOSEX is not implemented in this build"};
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!G || !X || !V || !Wd || !T_fwd || !T_inv || !Sigma) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    if (n_omega < 1 || n_omega > SOX_MAX_N_TAU) return {SOX_ERR_SHAPE, "n_omega out of range [1, SOX_MAX_N_TAU]"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    const size_t nsig = (size_t)d.S * d.T * d.nn();
+    Call call(h, stream);
+    Staged sG, sX, sV, sW, sF, sI, oS;
+    SOX_TRY(call.input(G, nsig, &sG));
+    SOX_TRY(call.input(X, (size_t)d.N * d.n, &sX));
+    SOX_TRY(call.input(V, (size_t)d.N * d.N, &sV));
+    SOX_TRY(call.input(Wd, (size_t)n_omega * d.N * d.N, &sW));
+    SOX_TRY(call.input(T_fwd, 2 * (size_t)n_omega * d.T, &sF));
+    SOX_TRY(call.input(T_inv, 2 * (size_t)n_omega * d.T, &sI));
+    SOX_TRY(call.output(Sigma, nsig, &oS));
+    Arena ar;
+    SOX_TRY(call.begin(std::max(sigma_bytes(h, d, false), sox::dynamic_bytes(d.n, d.N, d.T, n_omega)), &ar));
+    cudaStream_t s = call.stream();
+    {  // SOX(v, v): the static part, in the handle's precision
+      Arena a1 = ar;
+      SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, oS.out, a1, s));
+    }
+    Arena a2 = ar;
+    SOX_TRY(sox::dynamic_sigma_add_f64(h, d.n, d.N, d.T, d.S, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in,
+                                       oS.out, a2, s));
+    return call.end();
+  }();
   return finish(h, st);
 }
 
