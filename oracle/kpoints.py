@@ -165,3 +165,108 @@ def sox_sigma(X, V, G, nk, route="chain", taus=None, U2=None):
             else:
                 res[s, :, o] = sigma_bruteforce(X, V, U2, Gk, Gmk, nk)[0]
     return res
+
+
+# ---------------------------------------------------------------------------
+# Dynamically screened SOSEX for solids: W_d^{q1}(i Omega) in slot U(1), bare v
+# in U(2), the convolution over the time of the W vertex taken through the
+# caller's transform pair (Sec. II C, Eq. GG onward, with momenta).
+# ---------------------------------------------------------------------------
+
+def sigma_d_bruteforce(X, V, Wd, T_fwd, T_inv, G_tau, nk):
+    """Definition over big matrices: momentum-conserving 4-index tensors for v and for every
+    W_d(i Omega_m), block-diagonal G; returns Sigma_d^k [n_tau][n_k][n][n]."""
+    n_k, N, n = X.shape
+    nt = n_k * n
+    T = G_tau.shape[1]
+    Gm_tau = grid.g_minus_tau(np.asarray(G_tau, complex))   # [n_k][n_tau][n][n]: reflect tau
+    def big(Gk):
+        b = np.zeros((nt, nt), complex)
+        for k in range(n_k):
+            b[k * n:(k + 1) * n, k * n:(k + 1) * n] = Gk[k]
+        return b
+    Gb = np.stack([big(G_tau[:, j]) for j in range(T)])
+    Gmb = np.stack([big(Gm_tau[:, j]) for j in range(T)])
+    v2 = eri_big(X, V, nk)
+    wd = np.stack([eri_big(X, Wd[:, m], nk) for m in range(Wd.shape[1])])
+    F = np.einsum("mj,juq,jsv->muqsv", T_fwd, Gb, Gmb, optimize=True)
+    conv = np.einsum("im,mprqs,muqsv->ipruv", T_inv, wd, F, optimize=True)
+    sig = -np.einsum("tuvw,iwp,ipruv->itr", v2, Gb, conv, optimize=True)
+    return np.stack([[sig[i, k * n:(k + 1) * n, k * n:(k + 1) * n] for k in range(n_k)] for i in range(T)])
+
+
+def sigma_d_chain(X, V, Wd, T_fwd, T_inv, G_tau, nk):
+    """The paper's dynamic algorithm with momenta, v outermost.  For every (q1, k_s):
+    GG_Quv(tau_j) = G^{k_u}_uQ(tau_j) G^{k_s}_Qv(-tau_j) with k_u = k_s - q1, transform,
+    A_Puv(i Omega) = sum_Q W_d^{q1}_PQ(i Omega) GG_Quv(i Omega), inverse transform,
+    B_PRv(tau) = sum_u X^{k_u}_uR A_Puv(tau); C and the n_k^3 D step as in the static chain.
+    Wd: [n_q][n_omega][N][N]; G_tau: [n_k][n_tau][n][n]; returns [n_tau][n_k][n][n]."""
+    add, sub = k_tables(nk)
+    n_k, N, n = X.shape
+    T = G_tau.shape[1]
+    Gm_tau = grid.g_minus_tau(np.asarray(G_tau, complex))   # [n_k][n_tau][n][n]: reflect tau
+    M2 = mixed_tensors(V, X, nk)
+    GuQ = np.einsum("kjuq,kQq->kjuQ", G_tau, X.conj())                  # G^{k}_uQ(tau_j)
+    GQv = np.einsum("kQs,kjsv->kjQv", X, Gm_tau)                         # G^{k}_Qv(-tau_j)
+    GwP = np.einsum("kjwp,kPp->kjwP", G_tau, X.conj())                   # G^{k}_wP(tau_i)
+    D = np.zeros((T, n_k, N, N), complex)
+    for v in range(n):
+        B = np.empty((n_k, n_k, T, N, N), complex)
+        C = np.empty((n_k, n_k, T, N, N), complex)
+        for q in range(n_k):
+            for ks in range(n_k):
+                ku = sub[ks, q]
+                GG = np.einsum("juQ,jQ->jQu", GuQ[ku], GQv[ks][:, :, v])
+                GGw = np.einsum("mj,jQu->mQu", T_fwd, GG)
+                Aw = np.einsum("mPQ,mQu->mPu", Wd[q], GGw)
+                At = np.einsum("im,mPu->iPu", T_inv, Aw)
+                B[q, ks] = np.einsum("iPu,Ru->iPR", At, X[ku])                  # B^{q1,ks}_PRv(tau_i)
+                C[q, ks] = np.einsum("Rw,iwP->iPR", M2[q, ks][:, v, :], GwP[ks])  # C^{q2,kw}_RvP(tau_i)
+        for k in range(n_k):
+            for q1 in range(n_k):
+                kw = add[k, q1]
+                for q2 in range(n_k):
+                    D[:, k] += C[q2, kw] * B[q1, sub[kw, q2]]
+    out = np.empty((T, n_k, n, n), complex)
+    for k in range(n_k):
+        for i in range(T):
+            out[i, k] = X[k].conj().T @ (-D[i, k].T / n_k ** 2) @ X[k]
+    return out
+
+
+def sosex_dynamic_sigma(X, V, Wd, T_fwd, T_inv, G, nk, route="chain"):
+    """SOX(v, v) + Sigma_d for a solid, library layout G [n_spin][n_k][n_tau][n][n];
+    Wd [n_q][n_omega][N][N]."""
+    f = sigma_d_chain if route == "chain" else sigma_d_bruteforce
+    stat = sox_sigma(X, V, G, nk)
+    dyn = np.stack([f(X, V, Wd, T_fwd, T_inv, G[s], nk).transpose(1, 0, 2, 3) for s in range(G.shape[0])])
+    return stat + dyn
+
+
+def pi_omega(X, G_tau, T_fwd, nk):
+    """Pi^q_PQ(i Omega_m) = 1/N_k sum_k sum_j T_fwd[m][j] G^{PQ}_{k+q, k}(tau_j) G^{QP}_{k, k+q}(-tau_j):
+    the THC RPA bubble of transfer q, G^{PQ}_{a,b} = sum X^{a}[P][p] G^{a}[p][p'] conj(X^{a}[Q][p'])
+    mixed with the momenta of the two propagators.  Used to build test inputs for the
+    dynamic solid path."""
+    add, sub = k_tables(nk)
+    n_k = X.shape[0]
+    Gm = grid.g_minus_tau(np.asarray(G_tau, complex))   # [n_k][n_tau][n][n]: reflect tau
+    out = np.zeros((n_k, T_fwd.shape[0], X.shape[1], X.shape[1]), complex)
+    for q in range(n_k):
+        acc = 0.0
+        for k in range(n_k):
+            kq = add[k, q]
+            a = np.einsum("Pp,jpr,Qr->jPQ", X[kq], G_tau[kq], X[kq].conj(), optimize=True)
+            b = np.einsum("Qs,jst,Pt->jQP", X[k], Gm[k], X[k].conj(), optimize=True)
+            acc = acc + a * np.transpose(b, (0, 2, 1))
+        out[q] = np.einsum("mj,jPQ->mPQ", T_fwd, acc) / n_k
+    return out
+
+
+def w_dynamic(V, Pi_om):
+    """W_d^q(i Omega_m) = W^q(i Omega_m) - V^q, W^q = V^q^1/2 (1 - V^q^1/2 Pi^q V^q^1/2)^-1 V^q^1/2
+    per transfer q and frequency m (V^q Hermitian PSD).  Builds test inputs only."""
+    from .screening import w_static
+
+    return np.stack([np.stack([w_static(V[q], Pi_om[q, m]) - V[q] for m in range(Pi_om.shape[1])])
+                     for q in range(V.shape[0])])
