@@ -79,6 +79,12 @@ typedef struct {
   int precision;        /* SOX_PREC_*                                           */
   int device;           /* CUDA device ordinal the handle is bound to            */
   long long spin_limit; /* iteration cap for device-side waits; 0 = default      */
+  long long workspace_limit; /* bytes of chunked intermediates each entry point
+                          * sizes its tau / v chunks for; 0 = the library's
+                          * defaults (12-32 GiB per path).  A chunk of one tau
+                          * point (or one v) is used even when it exceeds the
+                          * limit; fixed-size tensors (mixed tensors, the D
+                          * array of the dynamic paths) are not counted.      */
 } sox_options;
 
 typedef struct {
@@ -207,7 +213,17 @@ SOX_API int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G
  * (interleaved).  The transform pair is the caller's (the paper uses sparse-ir,
  * Sec. II C).  SOX(v, v) runs in the handle's precision, Sigma_d in FP64 with v in
  * the outer loop (GG, transform, W_d product, inverse transform, then the fused
- * B/C/D kernel with X in place of G_Rq).  Solids return SOX_ERR_UNSUPPORTED. */
+ * B/C/D kernel with X in place of G_Rq).
+ * Solids (dtype SOX_COMPLEX128, any k-mesh; Sec. II C with momenta): Wd is
+ * complex [n_q][n_omega][N][N], W_d^q(i Omega_m) for every transfer q in the
+ * k-mesh order of V; W_d sits in the first interaction slot and carries the
+ * transfer q1 of that slot,
+ *   Sigma_d^k(tau_i) = -1/N_k^2 sum_{q1,q2} X_k^H D_d^k(tau_i)^T X_k,
+ * where D_d is the static chain's D with B built from
+ *   A^{q1,ks}_Puv(tau_i) = sum_m T_inv[i][m] sum_Q W_d^{q1}_PQ(i Omega_m)
+ *        sum_j T_fwd[m][j] G^{ks-q1}_uQ(tau_j) G^{ks}_Qv(-tau_j).
+ * Everything runs in FP64 complex on CUDA cores for solids.  G, X, V and Sigma
+ * use the solid layouts of sox_sigma. */
 SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream);

@@ -148,12 +148,12 @@ int grid1(long long total) { return (int)std::max<long long>(1, std::min<long lo
 
 }  // namespace
 
-size_t adjoint_bytes(int n, int N, int T, int S, int *chunk) {
+size_t adjoint_bytes(sox_handle h, int n, int N, int T, int S, int *chunk) {
   const size_t nn = (size_t)n * n, Nn2 = (size_t)N * nn, NN = (size_t)N * N, Nn = (size_t)N * n;
   const size_t fixed = 8 * (2 * Nn2 /*Um, Y*/ + 2 * Nn2 /*U1bar, U2bar*/ + Nn2 /*Z*/ + Nn + NN) + 4096 * 16;
   const size_t per_j = 8 * (2 * Nn2 /*A, Abar*/ + 4 * Nn /*GR, GWt, GRbar, GWtbar*/ + 3 * NN /*D, E, Dbar/Ebar*/ +
                             2 * (size_t)n * NN /*Bbar, Cbar*/ + 3 * Nn /*Xbar parts, M1, M2*/ + Nn) + 4096;
-  const size_t budget = size_t(16) << 30;
+  const size_t budget = chunk_budget(h, size_t(16) << 30);
   long long c = budget > fixed ? (long long)((budget - fixed) / per_j) : 1;
   c = std::max<long long>(1, std::min<long long>(c, T));
   if (chunk) *chunk = (int)c;
@@ -165,7 +165,7 @@ Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double
                           const double *V, const double *w, const double *dphi, double *dX, double *dV,
                           Arena &ar, cudaStream_t s) {
   int c = 1;
-  adjoint_bytes(n, N, T, S, &c);
+  adjoint_bytes(h, n, N, T, S, &c);
   const long long nn = (long long)n * n, Nn2 = (long long)N * nn, NN = (long long)N * N, Nn = (long long)N * n;
   double *Um = ar.take<double>(Nn2), *Y = ar.take<double>(Nn2);
   double *U1bar = ar.take<double>(Nn2), *U2bar = ar.take<double>(Nn2), *Z = ar.take<double>(Nn2);

@@ -4,7 +4,7 @@
 
 namespace sox {
 // Workspace bytes of phi_adjoint_xv_f64; *chunk receives the tau points per pass.
-size_t adjoint_bytes(int n, int N, int T, int S, int *chunk);
+size_t adjoint_bytes(sox_handle h, int n, int N, int T, int S, int *chunk);
 // dX[P][p] = sum_s dphi[s] dPhi_s/dX[P][p],  dV[P][Q] = sum_s dphi[s] dPhi_s/dV[P][Q]  (bare SOX,
 // FP64).  G, X, V, w, dphi device pointers; dX / dV may be NULL.
 Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double *G, const double *X,

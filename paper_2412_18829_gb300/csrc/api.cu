@@ -183,19 +183,20 @@ void mixed_tensor_f64(sox_handle H, const double *U, const double *X, const Dims
   sox::launch_gemm_f64(g, s);
 }
 
-int tau_chunk(const Dims &d, size_t per_tau_bytes, size_t fixed_bytes) {
-  size_t budget = kDefaultBudget > fixed_bytes ? kDefaultBudget - fixed_bytes : 0;
+int tau_chunk(sox_handle h, const Dims &d, size_t per_tau_bytes, size_t fixed_bytes) {
+  const size_t total = sox::chunk_budget(h, kDefaultBudget);
+  size_t budget = total > fixed_bytes ? total - fixed_bytes : 0;
   long long c = per_tau_bytes ? (long long)(budget / per_tau_bytes) : d.T;
   if (c < 1) c = 1;
   if (c > d.T) c = d.T;
   return (int)c;
 }
 
-size_t sigma_fp64_bytes(const Dims &d, bool two_slots, int *chunk) {
+size_t sigma_fp64_bytes(sox_handle h, const Dims &d, bool two_slots, int *chunk) {
   size_t Nn2 = (size_t)d.N * d.nn();
   size_t fixed = sox::aligned_bytes(Nn2, 8) * (two_slots ? 2 : 1);
   size_t per_tau = 8 * (Nn2 + 3 * (size_t)d.N * d.n + (size_t)d.N * d.N) + 1024;
-  int c = tau_chunk(d, per_tau, fixed);
+  int c = tau_chunk(h, d, per_tau, fixed);
   if (chunk) *chunk = c;
   return fixed + sox::aligned_bytes(std::max<size_t>(Nn2 * c, Nn2), 8) +
          4 * sox::aligned_bytes((size_t)c * d.N * std::max(d.n, d.N), 8);
@@ -206,7 +207,7 @@ Status sigma_fp64(sox_handle H, const Dims &d, const double *G, const double *X,
                   const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
   const bool two = (U1 != U2);
   int c = 1;
-  sigma_fp64_bytes(d, two, &c);
+  sigma_fp64_bytes(H, d, two, &c);
   const size_t Nn2 = (size_t)d.N * d.nn();
   double *Um1 = ar.take<double>(Nn2);
   double *Um2 = two ? ar.take<double>(Nn2) : Um1;
@@ -268,7 +269,7 @@ Dims dims_of(const sox_problem *p) { return Dims{p->n, p->N, p->n_tau, p->n_spin
 
 size_t sigma_bytes(sox_handle h, const Dims &d, bool two) {
   if (h->precision == SOX_PREC_F16X2) return sox::tc_sigma_bytes(h, d.n, d.N, d.T, d.S, two);
-  return sigma_fp64_bytes(d, two, nullptr);
+  return sigma_fp64_bytes(h, d, two, nullptr);
 }
 
 Status sigma_any(sox_handle h, const Dims &d, const double *G, const double *X, const double *U1,
@@ -296,7 +297,7 @@ Status run_sigma_complex(sox_handle h, const sox_problem *p, const double *G, co
   if (!same) SOX_TRY(call.input(U2, 2 * (size_t)nk * p->N * p->N, &s2));
   SOX_TRY(call.output(Sigma, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &sS));
   Arena ar;
-  const sox::KpointPlan pl = sox::kpoint_plan(p->n, p->N, p->n_tau, p->n_spin, p->nk);
+  const sox::KpointPlan pl = sox::kpoint_plan(h, p->n, p->N, p->n_tau, p->n_spin, p->nk);
   SOX_TRY(call.begin(pl.bytes + (same ? 0 : 16 * (size_t)nk * nk * p->N * nn), &ar));
   SOX_TRY(sox::kpoint_sigma_f64(h, p, sG.in, sX.in, s1.in, same ? s1.in : s2.in, sS.out, ar, call.stream()));
   return call.end();
@@ -336,7 +337,7 @@ int sox_version(void) { return 100; }
 int sox_create(sox_handle *out, const sox_options *opt) {
   if (!out) return SOX_ERR_INVALID_ARG;
   *out = nullptr;
-  sox_options o{SOX_PREC_FP64, 0, 0};
+  sox_options o{SOX_PREC_FP64, 0, 0, 0};
   if (opt) o = *opt;
   if (o.precision != SOX_PREC_FP64 && o.precision != SOX_PREC_F16X2) return SOX_ERR_INVALID_ARG;
   int ndev = 0;
@@ -350,6 +351,11 @@ int sox_create(sox_handle *out, const sox_options *opt) {
   h->device = o.device;
   h->precision = o.precision;
   h->spin_limit = o.spin_limit > 0 ? o.spin_limit : (1LL << 22);
+  if (o.workspace_limit < 0) {
+    delete h;
+    return SOX_ERR_INVALID_ARG;
+  }
+  h->ws_limit = (size_t)o.workspace_limit;
   int prev = -1;
   cudaGetDevice(&prev);
   if (cudaSetDevice(o.device) != cudaSuccess ||
@@ -684,7 +690,7 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
     SOX_TRY(call.output(dV, (size_t)d.N * d.N, &oV));
     size_t need = 0;
     if (dG) need = sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8);
-    if (dX || dV) need = std::max(need, sox::adjoint_bytes(d.n, d.N, d.T, d.S, nullptr));
+    if (dX || dV) need = std::max(need, sox::adjoint_bytes(h, d.n, d.N, d.T, d.S, nullptr));
     Arena ar;
     SOX_TRY(call.begin(need, &ar));
     cudaStream_t s = call.stream();
@@ -711,9 +717,39 @@ int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, con
                         const double *T_inv, int n_omega, double *Sigma, void *stream) {
   if (!h) return SOX_ERR_INVALID_ARG;
   Status st = [&]() -> Status {
-    SOX_TRY(validate(p));
     if (!G || !X || !V || !Wd || !T_fwd || !T_inv || !Sigma) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
     if (n_omega < 1 || n_omega > SOX_MAX_N_TAU) return {SOX_ERR_SHAPE, "n_omega out of range [1, SOX_MAX_N_TAU]"};
+    if (p && (p->dtype == SOX_COMPLEX128 || p->nk[0] * p->nk[1] * p->nk[2] != 1)) {
+      // solids (complex data, any k-mesh): momentum-resolved chain in FP64 complex
+      SOX_TRY(validate(p, false));
+      if (p->dtype != SOX_COMPLEX128)
+        return {SOX_ERR_UNSUPPORTED, "k-point meshes need complex data (SOX_COMPLEX128)"};
+      SOX_TRY(bind_device(h));
+      const int nk = p->nk[0] * p->nk[1] * p->nk[2];
+      const size_t nn = (size_t)p->n * p->n, NN = (size_t)p->N * p->N;
+      Call call(h, stream);
+      Staged sG, sX, sV, sW, sF, sI, oS;
+      SOX_TRY(call.input(G, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &sG));
+      SOX_TRY(call.input(X, 2 * (size_t)nk * p->N * p->n, &sX));
+      SOX_TRY(call.input(V, 2 * (size_t)nk * NN, &sV));
+      SOX_TRY(call.input(Wd, 2 * (size_t)nk * n_omega * NN, &sW));
+      SOX_TRY(call.input(T_fwd, 2 * (size_t)n_omega * p->n_tau, &sF));
+      SOX_TRY(call.input(T_inv, 2 * (size_t)n_omega * p->n_tau, &sI));
+      SOX_TRY(call.output(Sigma, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &oS));
+      const sox::KpointPlan pl = sox::kpoint_plan(h, p->n, p->N, p->n_tau, p->n_spin, p->nk);
+      Arena ar;
+      SOX_TRY(call.begin(std::max(pl.bytes, sox::kpoint_dynamic_bytes(h, p->n, p->N, p->n_tau, n_omega, p->nk, nullptr)),
+                         &ar));
+      {
+        Arena a1 = ar;
+        SOX_TRY(sox::kpoint_sigma_f64(h, p, sG.in, sX.in, sV.in, sV.in, oS.out, a1, call.stream()));
+      }
+      Arena a2 = ar;
+      SOX_TRY(sox::kpoint_dynamic_add_f64(h, p, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in, oS.out, a2,
+                                          call.stream()));
+      return call.end();
+    }
+    SOX_TRY(validate(p));
     SOX_TRY(bind_device(h));
     const Dims d = dims_of(p);
     const size_t nsig = (size_t)d.S * d.T * d.nn();

@@ -16,6 +16,7 @@ struct sox_context {
   int device = 0;
   int precision = SOX_PREC_FP64;
   long long spin_limit = 0;
+  size_t ws_limit = 0;       // chunk budget override (sox_options.workspace_limit), 0 = defaults
   void *ws = nullptr;        // device workspace
   size_t ws_bytes = 0;
   int *d_status = nullptr;   // device status word for bounded waits
@@ -75,6 +76,9 @@ struct Status {
   } while (0)
 
 // Bump allocator over the handle workspace (256-byte aligned slices).
+// Chunk budget of a planner: the handle's override, else the planner's default.
+inline size_t chunk_budget(const sox_context *h, size_t dflt) { return (h && h->ws_limit) ? h->ws_limit : dflt; }
+
 struct Arena {
   char *base = nullptr;
   size_t cap = 0, off = 0;

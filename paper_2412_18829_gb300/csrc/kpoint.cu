@@ -151,9 +151,47 @@ __global__ void k_kpoint_D(const z *B, const z *C, const int *add, const int *su
 
 int grid1(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 65535 * 8)); }
 
+// GG[ks][j][Q][u] = GWt[ku][j][Q][u] * (-GR[ks][T-1-j][Q][v]),  ku = ks - q1
+__global__ void k_gg_k(const z *GWt, const z *GR, const int *sub, int nk, int q1, int T, int N, int n, int v, z *GG) {
+  const long long Nn = (long long)N * n, per = Nn * T, total = per * nk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ks = (int)(e / per);
+    const long long r = e % per;
+    const int j = (int)(r / Nn);
+    const long long qu = r % Nn;
+    const int Q = (int)(qu / n);
+    const int ku = sub[ks * nk + q1];
+    const z a = GWt[((long long)ku * T + j) * Nn + qu];
+    const z g = GR[((long long)ks * T + (T - 1 - j)) * Nn + (long long)Q * n + v];
+    GG[e] = zmul(a, make_double2(-g.x, -g.y));
+  }
+}
+
+// D[i][k][P][R] += sum_{q1,q2} C[(q2, k+q1)][il][P][R] * B[(q1, k+q1-q2)][il][P][R],  i = i0 + il
+__global__ void k_kpoint_D_tau(const z *B, const z *C, const int *add, const int *sub, int nk, int N, int ct, int i0,
+                               z *D) {
+  const int R = blockIdx.x * 32 + threadIdx.x;
+  const int P = blockIdx.y * 8 + threadIdx.y;
+  const int k = blockIdx.z % nk, il = blockIdx.z / nk;
+  if (P >= N || R >= N) return;
+  const long long NN = (long long)N * N, pe = (long long)P * N + R;
+  z *d = D + ((long long)(i0 + il) * nk + k) * NN + pe;
+  z acc = *d;
+  for (int q1 = 0; q1 < nk; ++q1) {
+    const int kw = add[k * nk + q1];
+    for (int q2 = 0; q2 < nk; ++q2) {
+      const int ks = sub[kw * nk + q2];
+      acc = zfma(C[((long long)(q2 * nk + kw) * ct + il) * NN + pe], B[((long long)(q1 * nk + ks) * ct + il) * NN + pe],
+                 acc);
+    }
+  }
+  *d = acc;
+}
+
 }  // namespace
 
-KpointPlan kpoint_plan(int n, int N, int T, int S, const int nkv[3]) {
+KpointPlan kpoint_plan(sox_handle h, int n, int N, int T, int S, const int nkv[3]) {
   KpointPlan p{};
   p.nk = nkv[0] * nkv[1] * nkv[2];
   const size_t nk2 = (size_t)p.nk * p.nk;
@@ -161,7 +199,7 @@ KpointPlan kpoint_plan(int n, int N, int T, int S, const int nkv[3]) {
   p.fixed_bytes = 16 * (2 * nk2 * Nn2 /*Y, M*/ + (size_t)p.nk * (2 * Nn + NN + Nn) /*GR, GWt, D, T*/) +
                   8 * 2 * nk2 /*tables*/ + 64 * 1024;
   const size_t per_v = 16 * nk2 * (2 * NN /*B, C*/ + Nn /*A*/);
-  const size_t budget = size_t(24) << 30;
+  const size_t budget = chunk_budget(h, size_t(24) << 30);
   long long nv = budget > p.fixed_bytes ? (long long)((budget - p.fixed_bytes) / per_v) : 1;
   p.nv = (int)std::max<long long>(1, std::min<long long>(nv, n));
   p.bytes = p.fixed_bytes + per_v * p.nv + 16 * (size_t)3 * nk2 * p.nv * sizeof(long long) + 64 * 1024;
@@ -173,7 +211,7 @@ KpointPlan kpoint_plan(int n, int N, int T, int S, const int nkv[3]) {
 Status kpoint_sigma_f64(sox_handle h, const sox_problem *pr, const double *Gd, const double *Xd, const double *U1d,
                         const double *U2d, double *Sd, Arena &ar, cudaStream_t s) {
   const int n = pr->n, N = pr->N, T = pr->n_tau, S = pr->n_spin;
-  const KpointPlan pl = kpoint_plan(n, N, T, S, pr->nk);
+  const KpointPlan pl = kpoint_plan(h, n, N, T, S, pr->nk);
   const int nk = pl.nk, nv = pl.nv;
   const long long nn = (long long)n * n, Nn2 = (long long)N * nn, NN = (long long)N * N, Nn = (long long)N * n;
   const long long nk2 = (long long)nk * nk;
@@ -319,6 +357,194 @@ Status kpoint_sigma_f64(sox_handle h, const sox_problem *pr, const double *Gd, c
       o.B = Tm; o.sB = Nn; o.bk = n; o.bj = 1;
       o.C = Sig + ((long long)sp * nk * T + j) * nn; o.sC = (long long)T * nn; o.ci = n; o.cj = 1;
       o.alpha = -inv_nk2;
+      zgemm(o, s);
+      launches += 2;
+    }
+  }
+  h->launches += launches;
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+// ---------------------------------------------------------------------------
+// Dynamically screened SOSEX for solids: adds Sigma_d to Sigma (which holds SOX(v, v)).
+// W_d^{q1}(i Omega) in slot U(1), bare v in U(2); for every v and (q1, k_s):
+//   GG_Quv(tau_j) = G^{k_u}_uQ(tau_j) G^{k_s}_Qv(-tau_j),  k_u = k_s - q1
+//   A_Puv(tau_i)  = sum_m T_inv[i][m] sum_Q W_d^{q1}_PQ(i Omega_m) sum_j T_fwd[m][j] GG_Quv(tau_j)
+//   B^{q1,ks}_v(tau_i)[P][R] = sum_u A_Puv(tau_i) X^{k_u}[R][u]
+// then C and the n_k^3 D step per tau_i, and Sigma^k_d = -1/N_k^2 X_k^H D^T X_k.
+// ---------------------------------------------------------------------------
+size_t kpoint_dynamic_bytes(sox_handle h, int n, int N, int T, int n_omega, const int nkv[3], int *ct_out) {
+  const size_t nk = (size_t)nkv[0] * nkv[1] * nkv[2], nk2 = nk * nk;
+  const size_t Nn2 = (size_t)N * n * n, NN = (size_t)N * N, Nn = (size_t)N * n;
+  const size_t fixed = 16 * (2 * nk2 * Nn2 /*Y, M*/ + 3 * nk * T * Nn /*GWt, GR, GG*/ + 2 * nk * n_omega * Nn /*GGw, Aw*/ +
+                             nk2 * T * Nn /*A*/ + (size_t)T * nk * NN /*D*/ + 2 * nk * Nn /*T1*/) +
+                       8 * 3 * nk2 * n_omega /*offsets of the W product*/ + 64 * 1024;
+  const size_t per_t = 16 * 2 * nk2 * NN + 8 * 4 * nk2;
+  const size_t budget = chunk_budget(h, size_t(32) << 30);
+  long long ct = budget > fixed ? (long long)((budget - fixed) / per_t) : 1;
+  ct = std::min<long long>(ct, 65535 / (long long)nk2);  // grouped-GEMM batch is a grid dimension
+  ct = std::max<long long>(1, std::min<long long>(ct, T));
+  if (ct_out) *ct_out = (int)ct;
+  return fixed + per_t * ct + 64 * 1024;
+}
+
+Status kpoint_dynamic_add_f64(sox_handle h, const sox_problem *pr, int n_omega, const double *Gd, const double *Xd,
+                              const double *Vd, const double *Wdd, const double *Tfd, const double *Tid, double *Sd,
+                              Arena &ar, cudaStream_t s) {
+  const int n = pr->n, N = pr->N, T = pr->n_tau, S = pr->n_spin, nO = n_omega;
+  int ct = 1;
+  kpoint_dynamic_bytes(h, n, N, T, nO, pr->nk, &ct);
+  const int nk = pr->nk[0] * pr->nk[1] * pr->nk[2];
+  const long long nn = (long long)n * n, Nn2 = (long long)N * nn, NN = (long long)N * N, Nn = (long long)N * n;
+  const long long nk2 = (long long)nk * nk;
+  const z *G = reinterpret_cast<const z *>(Gd);
+  const z *X = reinterpret_cast<const z *>(Xd);
+  const z *V = reinterpret_cast<const z *>(Vd);
+  const z *Wd = reinterpret_cast<const z *>(Wdd);
+  const z *Tf = reinterpret_cast<const z *>(Tfd);
+  const z *Ti = reinterpret_cast<const z *>(Tid);
+  z *Sig = reinterpret_cast<z *>(Sd);
+
+  std::vector<int> add(nk * nk), sub(nk * nk);
+  {
+    auto idx = [&](int x, int y, int zz) {
+      x = ((x % pr->nk[0]) + pr->nk[0]) % pr->nk[0];
+      y = ((y % pr->nk[1]) + pr->nk[1]) % pr->nk[1];
+      zz = ((zz % pr->nk[2]) + pr->nk[2]) % pr->nk[2];
+      return (x * pr->nk[1] + y) * pr->nk[2] + zz;
+    };
+    for (int a = 0; a < nk; ++a)
+      for (int b = 0; b < nk; ++b) {
+        const int ax = a / (pr->nk[1] * pr->nk[2]), ay = (a / pr->nk[2]) % pr->nk[1], az = a % pr->nk[2];
+        const int bx = b / (pr->nk[1] * pr->nk[2]), by = (b / pr->nk[2]) % pr->nk[1], bz = b % pr->nk[2];
+        add[a * nk + b] = idx(ax + bx, ay + by, az + bz);
+        sub[a * nk + b] = idx(ax - bx, ay - by, az - bz);
+      }
+  }
+  int *d_add = ar.take<int>(nk2), *d_sub = ar.take<int>(nk2);
+  z *Y = ar.take<z>(nk2 * Nn2), *M2 = ar.take<z>(nk2 * Nn2);
+  z *GWt = ar.take<z>((size_t)nk * T * Nn), *GR = ar.take<z>((size_t)nk * T * Nn);
+  z *GG = ar.take<z>((size_t)nk * T * Nn);
+  z *GGw = ar.take<z>((size_t)nk * nO * Nn), *Aw = ar.take<z>((size_t)nk * nO * Nn);
+  z *A = ar.take<z>((size_t)nk2 * T * Nn);
+  z *D = ar.take<z>((size_t)T * nk * NN), *T1 = ar.take<z>((size_t)2 * nk * Nn);
+  long long *wA = ar.take<long long>((size_t)nk2 * nO), *wB = ar.take<long long>((size_t)nk * nO);
+  z *Bc = ar.take<z>((size_t)nk2 * ct * NN), *Cc = ar.take<z>((size_t)nk2 * ct * NN);
+  long long *oA = ar.take<long long>(nk2 * ct), *oB = ar.take<long long>(nk2 * ct);
+  long long *oC = ar.take<long long>(nk2 * ct), *oD = ar.take<long long>(nk2 * ct);
+  if (!oD) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  SOX_CUDA_TRY(cudaMemcpyAsync(d_add, add.data(), 4 * nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(d_sub, sub.data(), 4 * nk2, cudaMemcpyHostToDevice, s));
+  {  // offsets of the W_d product: batch b = ks * nO + m; A = W_d[q1][m] (q1 added per launch), B/C = [ks][m]
+    std::vector<long long> ha(nk2 * nO), hb(nk * nO);
+    for (int q = 0; q < nk; ++q)
+      for (int ks = 0; ks < nk; ++ks)
+        for (int m = 0; m < nO; ++m) ha[((long long)q * nk + ks) * nO + m] = ((long long)q * nO + m) * NN;
+    for (int ks = 0; ks < nk; ++ks)
+      for (int m = 0; m < nO; ++m) hb[(long long)ks * nO + m] = ((long long)ks * nO + m) * Nn;
+    SOX_CUDA_TRY(cudaMemcpyAsync(wA, ha.data(), 8 * ha.size(), cudaMemcpyHostToDevice, s));
+    SOX_CUDA_TRY(cudaMemcpyAsync(wB, hb.data(), 8 * hb.size(), cudaMemcpyHostToDevice, s));
+  }
+  ProfScope ps(h, "kpoint_dynamic_f64", s, 0);
+  long long launches = 0;
+  // bare mixed tensors M2[q][k'] for C
+  k_kpair_products<<<grid1(nk2 * Nn2), 256, 0, s>>>(X, d_sub, nk, N, n, Y);
+  for (int q = 0; q < nk; ++q) {
+    ZGemm g = zg();
+    g.M = N; g.Nc = (int)nn; g.K = N; g.batch = nk;
+    g.A = V + (long long)q * NN; g.ai = N; g.ak = 1;
+    g.B = Y + (long long)q * nk * Nn2; g.sB = Nn2; g.bk = nn; g.bj = 1;
+    g.C = M2 + (long long)q * nk * Nn2; g.sC = Nn2; g.ci = nn; g.cj = 1;
+    zgemm(g, s);
+  }
+  launches += 1 + nk;
+  std::vector<long long> hA(nk2 * ct), hB(nk2 * ct), hC(nk2 * ct), hD(nk2 * ct);
+  const double inv_nk2 = 1.0 / ((double)nk * nk);
+  for (int sp = 0; sp < S; ++sp) {
+    const z *Gs = G + (long long)sp * nk * T * nn;
+    for (int k = 0; k < nk; ++k) {  // GWt[k][j][Q][u], GR[k][j][Q][v] for every tau
+      ZGemm g = zg();
+      g.M = N; g.Nc = n; g.K = n; g.batch = T;
+      g.A = X + (long long)k * Nn; g.ai = n; g.ak = 1; g.conjA = 1;
+      g.B = Gs + (long long)k * T * nn; g.sB = nn; g.bk = 1; g.bj = n;
+      g.C = GWt + (long long)k * T * Nn; g.sC = Nn; g.ci = n; g.cj = 1;
+      zgemm(g, s);
+      ZGemm r = g;
+      r.conjA = 0; r.bk = n; r.bj = 1; r.C = GR + (long long)k * T * Nn;
+      zgemm(r, s);
+      launches += 2;
+    }
+    SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)T * nk * NN, s));
+    for (int v = 0; v < n; ++v) {
+      for (int q1 = 0; q1 < nk; ++q1) {
+        k_gg_k<<<grid1((long long)nk * T * Nn), 256, 0, s>>>(GWt, GR, d_sub, nk, q1, T, N, n, v, GG);
+        ZGemm f = zg();  // GGw[ks][m] = sum_j T_fwd[m][j] GG[ks][j]
+        f.M = nO; f.Nc = (int)Nn; f.K = T; f.batch = nk;
+        f.A = Tf; f.ai = T; f.ak = 1;
+        f.B = GG; f.sB = (long long)T * Nn; f.bk = Nn; f.bj = 1;
+        f.C = GGw; f.sC = (long long)nO * Nn; f.ci = Nn; f.cj = 1;
+        zgemm(f, s);
+        ZGemm w = zg();  // Aw[ks][m][P][u] = sum_Q W_d[q1][m][P][Q] GGw[ks][m][Q][u]
+        w.M = N; w.Nc = n; w.K = N; w.batch = nk * nO;
+        w.A = Wd; w.offA = wA + (long long)q1 * nk * nO; w.ai = N; w.ak = 1;
+        w.B = GGw; w.offB = wB; w.bk = n; w.bj = 1;
+        w.C = Aw; w.offC = wB; w.ci = n; w.cj = 1;
+        zgemm(w, s);
+        ZGemm iv = zg();  // A[(q1, ks)][i] = sum_m T_inv[i][m] Aw[ks][m]
+        iv.M = T; iv.Nc = (int)Nn; iv.K = nO; iv.batch = nk;
+        iv.A = Ti; iv.ai = nO; iv.ak = 1;
+        iv.B = Aw; iv.sB = (long long)nO * Nn; iv.bk = Nn; iv.bj = 1;
+        iv.C = A + (long long)q1 * nk * T * Nn; iv.sC = (long long)T * Nn; iv.ci = Nn; iv.cj = 1;
+        zgemm(iv, s);
+        launches += 4;
+      }
+      for (int i0 = 0; i0 < T; i0 += ct) {
+        const int cc = std::min(ct, T - i0);
+        for (int q = 0; q < nk; ++q)
+          for (int kk = 0; kk < nk; ++kk)
+            for (int il = 0; il < cc; ++il) {
+              const long long b = ((long long)q * nk + kk) * cc + il;
+              hA[b] = (((long long)q * nk + kk) * T + i0 + il) * Nn;       // A[(q1, ks)][i]
+              hB[b] = (long long)sub[kk * nk + q] * Nn;                    // X[k_u]
+              hC[b] = ((long long)kk * T + i0 + il) * Nn;                  // GWt[k_w][i]
+              hD[b] = ((long long)q * nk + kk) * Nn2 + (long long)v * n;   // M2[(q2, k_w)][.][v][.]
+            }
+        const long long nb = nk2 * cc;
+        SOX_CUDA_TRY(cudaMemcpyAsync(oA, hA.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(oB, hB.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(oC, hC.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        SOX_CUDA_TRY(cudaMemcpyAsync(oD, hD.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+        ZGemm gb = zg();  // B[b][P][R] = sum_u A[b][P][u] X[k_u][R][u]
+        gb.M = N; gb.Nc = N; gb.K = n; gb.batch = (int)nb;
+        gb.A = A; gb.offA = oA; gb.ai = n; gb.ak = 1;
+        gb.B = X; gb.offB = oB; gb.bk = 1; gb.bj = n;
+        gb.C = Bc; gb.sC = NN; gb.ci = N; gb.cj = 1;
+        zgemm(gb, s);
+        ZGemm gc = zg();  // C[b][P][R] = sum_w GWt[k_w][i][P][w] M2[(q2, k_w)][R][v][w]
+        gc.M = N; gc.Nc = N; gc.K = n; gc.batch = (int)nb;
+        gc.A = GWt; gc.offA = oC; gc.ai = n; gc.ak = 1;
+        gc.B = M2; gc.offB = oD; gc.bk = 1; gc.bj = nn;
+        gc.C = Cc; gc.sC = NN; gc.ci = N; gc.cj = 1;
+        zgemm(gc, s);
+        dim3 grid((N + 31) / 32, (N + 7) / 8, nk * cc);
+        k_kpoint_D_tau<<<grid, dim3(32, 8), 0, s>>>(Bc, Cc, d_add, d_sub, nk, N, cc, i0, D);
+        launches += 3;
+      }
+    }
+    for (int i = 0; i < T; ++i) {  // Sigma^k(tau_i) += -1/N_k^2 X_k^H D[i][k]^T X_k
+      ZGemm t = zg();
+      t.M = N; t.Nc = n; t.K = N; t.batch = nk;
+      t.A = D + (long long)i * nk * NN; t.sA = NN; t.ai = 1; t.ak = N;
+      t.B = X; t.sB = Nn; t.bk = n; t.bj = 1;
+      t.C = T1; t.sC = Nn; t.ci = n; t.cj = 1;
+      zgemm(t, s);
+      ZGemm o = zg();
+      o.M = n; o.Nc = n; o.K = N; o.batch = nk;
+      o.A = X; o.sA = Nn; o.ai = 1; o.ak = n; o.conjA = 1;
+      o.B = T1; o.sB = Nn; o.bk = n; o.bj = 1;
+      o.C = Sig + ((long long)sp * nk * T + i) * nn; o.sC = (long long)T * nn; o.ci = n; o.cj = 1;
+      o.alpha = -inv_nk2; o.beta = 1.0;
       zgemm(o, s);
       launches += 2;
     }

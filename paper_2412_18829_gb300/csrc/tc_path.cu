@@ -34,7 +34,7 @@ size_t hb(size_t count) { return aligned_bytes(count, 2); }   // FP16 buffer
 size_t fb(size_t count) { return aligned_bytes(count, 4); }   // FP32 buffer
 size_t db(size_t count) { return aligned_bytes(count, 8); }   // FP64 buffer
 
-Geometry geometry(int n, int N, int T, int S, bool two) {
+Geometry geometry(sox_handle h, int n, int N, int T, int S, bool two) {
   Geometry g{};
   g.n = n; g.N = N; g.T = T; g.S = S;
   g.Kp = rup(n, 64);
@@ -53,7 +53,7 @@ Geometry geometry(int n, int N, int T, int S, bool two) {
                   + 2 * fb(N)                                         // row/col factors
                   + fb((size_t)N * N) + fb((size_t)N * n) + 4096      // Dt, T
                   + fb(1);                                            // symmetry flag
-  long long c = (long long)(kChunkBudget / std::max<size_t>(g.per_b_bytes, 1));
+  long long c = (long long)(chunk_budget(h, kChunkBudget) / std::max<size_t>(g.per_b_bytes, 1));
   c = std::max<long long>(1, std::min<long long>(c, (long long)T * S));
   g.Bc = (int)c;
   return g;
@@ -61,8 +61,8 @@ Geometry geometry(int n, int N, int T, int S, bool two) {
 
 }  // namespace
 
-size_t tc_sigma_bytes(sox_handle, int n, int N, int T, int S, bool two) {
-  Geometry g = geometry(n, N, T, S, two);
+size_t tc_sigma_bytes(sox_handle h, int n, int N, int T, int S, bool two) {
+  Geometry g = geometry(h, n, N, T, S, two);
   return g.fixed_bytes + g.per_b_bytes * g.Bc + 64 * 1024;
 }
 
@@ -71,7 +71,7 @@ void tc_release(sox_handle) {}
 Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const double *X, const double *U1,
                 const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
   const bool two = (U1 != U2);
-  const Geometry g = geometry(n, N, T, S, two);
+  const Geometry g = geometry(h, n, N, T, S, two);
   const int Kp = g.Kp, Np = g.Np, NR = g.NR, RG = g.RG, Bc = g.Bc;
   const size_t Kp2 = (size_t)Kp * Kp;
   std::string err;

@@ -75,3 +75,61 @@ def test_solid_sosex_static(env, slot):
     ref = kpoints.sox_sigma(w.X, U1, w.G, w.nk, U2=U2)
     got = _run(env, w, W=W, slot=slot)
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _dynamic_inputs(nk, n, N, n_tau, M, seed, physical=True, n_spin=1):
+    w = synth.solid(seed, nk, n, N, n_tau, 10.0)
+    G = w.G
+    if n_spin == 2:   # a second, different spin block: the propagator of another solid of the same mesh
+        G = np.concatenate([G, synth.solid(seed + 1, nk, n, N, n_tau, 10.0).G], axis=0)
+    _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, M)
+    if physical:
+        Wd = kpoints.w_dynamic(w.V, kpoints.pi_omega(w.X, w.G[0], Tf, nk))
+    else:
+        rng = np.random.default_rng(seed)
+        shape = (w.X.shape[0], 2 * M + 1, N, N)
+        Wd = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / N
+    return w, np.ascontiguousarray(G), Tf, Ti, np.ascontiguousarray(Wd)
+
+
+def _run_dynamic(env, w, G, Tf, Ti, Wd, handle=None):
+    torch, pkg, hs = env
+    h = hs["fp64"] if handle is None else handle
+    p = pkg.problem(w.n, w.N, w.n_tau, G.shape[0], w.beta, nk=w.nk, dtype=1)
+    Gd, X, V, W = (_dev(torch, a.astype(complex)) for a in (G, w.X, w.V, Wd))
+    S = torch.full_like(Gd, complex("nan"))
+    pkg.sosex_dynamic_sigma(h, p, Gd, X, V, W, _dev(torch, Tf), _dev(torch, Ti), Tf.shape[0], S)
+    pkg.sox_check_device(h)
+    torch.cuda.synchronize()
+    return S.cpu().numpy()
+
+
+@pytest.mark.parametrize("nk,n,N,n_tau,M,physical,n_spin", [
+    ((1, 1, 2), 3, 5, 4, 2, False, 1),
+    ((1, 2, 2), 4, 9, 5, 3, True, 1),
+    ((1, 1, 3), 5, 12, 4, 2, False, 2),
+    ((2, 1, 1), 9, 70, 6, 3, True, 1),
+])
+def test_solid_sosex_dynamic_matches_oracle(env, nk, n, N, n_tau, M, physical, n_spin):
+    w, G, Tf, Ti, Wd = _dynamic_inputs(nk, n, N, n_tau, M, 30 + n, physical, n_spin)
+    ref = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, G, nk)
+    got = _run_dynamic(env, w, G, Tf, Ti, Wd)
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_solid_sosex_dynamic_zero_screening_is_bare_sox(env):
+    w, G, Tf, Ti, Wd = _dynamic_inputs((1, 2, 1), 4, 10, 4, 2, 44)
+    got = _run_dynamic(env, w, G, Tf, Ti, np.zeros_like(Wd))
+    ref = kpoints.sox_sigma(w.X, w.V, G, w.nk)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_single_k_complex_dynamic_equals_real_molecule(env):
+    from oracle import dynamic, screening
+    wm = synth.molecule(42, 8, 36, 6, 20.0)
+    _, Tf, Ti = synth.bosonic_transforms(wm.tau, wm.beta, 3)
+    Wd = screening.w_dynamic(wm.V[0], screening.pi_omega(wm.X[0], wm.G[0, 0], Tf))
+    got = _run_dynamic(env, wm, wm.G, Tf, Ti, Wd[None])
+    ref = dynamic.sosex_dynamic_sigma(wm.X, wm.V, Wd, Tf, Ti, wm.G)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
