@@ -203,6 +203,16 @@ SOX_API int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G
                      const double *V, const double *w, const double *dphi, double *dG,
                      double *dX, double *dV, void *stream);
 
+/* The G part of the adjoint from a Sigma the caller already holds (for example
+ * the Sigma_out of phi_sox), without recomputing it:
+ *   dG[s][0][j][r][t] = -dphi[s] w_j Sigma[s][0][n_tau-1-j][t][r]
+ * (the conserving identity dPhi/dG_rt(tau_j) = -w_j Sigma_tr(beta - tau_j) on a
+ * mirror-symmetric grid, Sec. II C with Eq. E2b).  Sigma and dG
+ * [n_spin][1][n_tau][n][n], w [n_tau], dphi [n_spin]; FP64, molecules only.
+ * dG must not alias Sigma. */
+SOX_API int phi_sox_grad_G(sox_handle h, const sox_problem *p, const double *Sigma, const double *w,
+                   const double *dphi, double *dG, void *stream);
+
 /* Dynamically screened SOSEX for molecules (Sec. II C, Eq. GG and the steps
  * after it):
  *   Sigma = SOX(v, v) + Sigma_d with

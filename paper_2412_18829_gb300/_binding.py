@@ -60,6 +60,7 @@ _SIGS = {
     "sox_w_static": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P], _I),
     "phi_sox": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P], _I),
     "phi_sox_backward": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "phi_sox_grad_G": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
     "sosex_dynamic_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _I, _P, _P], _I),
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
@@ -237,6 +238,11 @@ def phi_sox_backward(h: Handle, p: sox_problem, G, X, V, w, dphi, dG=None, dX=No
                      stream=None):
     h.check(lib().phi_sox_backward(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(w),
                                    _ptr(dphi), _ptr(dG), _ptr(dX), _ptr(dV), _stream(stream)))
+
+
+def phi_sox_grad_G(h: Handle, p: sox_problem, Sigma, w, dphi, dG, stream=None):
+    h.check(lib().phi_sox_grad_G(h.ptr, ctypes.byref(p), _ptr(Sigma), _ptr(w), _ptr(dphi), _ptr(dG),
+                                 _stream(stream)))
 
 
 def sosex_dynamic_sigma(h: Handle, p: sox_problem, G, X, V, Wd, T_fwd, T_inv, n_omega, Sigma,

@@ -712,6 +712,31 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
   return finish(h, st);
 }
 
+int phi_sox_grad_G(sox_handle h, const sox_problem *p, const double *Sigma, const double *w, const double *dphi,
+                   double *dG, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(validate(p));
+    if (!Sigma || !w || !dphi || !dG) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    if (Sigma == dG) return {SOX_ERR_INVALID_ARG, "dG must not alias Sigma"};
+    SOX_TRY(bind_device(h));
+    const Dims d = dims_of(p);
+    const size_t nsig = (size_t)d.S * d.T * d.nn();
+    Call call(h, stream);
+    Staged sS, sw, sd, oG;
+    SOX_TRY(call.input(Sigma, nsig, &sS));
+    SOX_TRY(call.input(w, (size_t)d.T, &sw));
+    SOX_TRY(call.input(dphi, (size_t)d.S, &sd));
+    SOX_TRY(call.output(dG, nsig, &oG));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "dG_identity", call.stream());
+    sox::launch_dG_from_sigma(sS.in, sw.in, sd.in, d.n, d.T, d.S, oG.out, call.stream());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
 int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream) {

@@ -277,3 +277,27 @@ def tiny(n: int, N: int, n_tau: int = 6, beta: float = 4.0, n_spin: int = 1, see
     """Small random molecule-like case for unit tests (same recipe, free seed)."""
     w = molecule(100 + seed, n, N, n_tau, beta, n_spin, name=f"tiny-n{n}-N{N}-t{n_tau}-s{seed}")
     return w
+
+
+def pole_screening(V: np.ndarray, beta: float, M: int, omega_p: float = 0.5, strength: float = 0.5,
+                   seed: int = 0) -> np.ndarray:
+    """Synthetic dynamic screening W_d^q(i Omega_m), m = -M..M, for timing runs.
+
+    A single-pole stand-in with the structure of W - v (no RPA is evaluated here):
+    W_d^q(i Omega) = -strength * omega_p^2 / (Omega^2 + omega_p^2) * V^q D V^q / ||V^0||,
+    D a seeded positive diagonal.  Hermitian and even in Omega per q, and
+    W_d^{-q} = conj(W_d^q) whenever V^{-q} = conj(V^q).  Shape [n_q][2M+1][N][N].
+    """
+    rng = np.random.default_rng([2412188290, 7, seed])
+    nq, N, _ = V.shape
+    d = rng.uniform(0.5, 1.5, size=N)
+    norm = float(np.linalg.norm(V[0], 2))
+    om = 2.0 * np.pi * np.arange(-M, M + 1) / beta
+    f = -strength * omega_p ** 2 / (om ** 2 + omega_p ** 2) / norm
+    out = np.empty((nq, 2 * M + 1, N, N), dtype=np.result_type(V, np.float64))
+    for q in range(nq):
+        vdv = (V[q] * d[None, :]) @ V[q]
+        vdv = 0.5 * (vdv + vdv.conj().T)
+        for m in range(2 * M + 1):
+            out[q, m] = f[m] * vdv
+    return out

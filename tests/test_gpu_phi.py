@@ -126,3 +126,22 @@ def test_adjoint_central_differences_on_smallest_batch_instances(env, inst):
             tensor[(0,) + i] = base
             fd = (fp - fm) / (2 * hstep)
             assert abs(fd - grad[i]) <= 1e-6 * scale + 1e-7 * abs(grad[i]), (name, i, fd, grad[i], scale)
+
+
+def test_grad_G_from_kept_sigma_equals_backward(env):
+    torch, pkg, h = env
+    w = synth.molecule(25, 12, 50, 7, 20.0, n_spin=2)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    d = torch.tensor([0.7, -1.3], dtype=torch.float64, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    S = torch.empty_like(G)
+    pkg.phi_sox(h, p, G, X, V, tw, out, S)
+    a, b = torch.empty_like(G), torch.empty_like(G)
+    pkg.phi_sox_grad_G(h, p, S, tw, d, a)
+    pkg.phi_sox_backward(h, p, G, X, V, tw, d, b, None, None)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    with pytest.raises(pkg.SoxError):
+        pkg.phi_sox_grad_G(h, p, S, tw, d, S)
