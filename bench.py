@@ -1,10 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark: Sigma_SOX builds/s on one GB300 (or N replicas under torchrun).
+"""Benchmark: Sigma_SOX builds/s on one GB300 (or N GPUs under torchrun).
 
-A step is one full bare-SOX build through the C ABI: both THC mixed tensors,
-projections, the A intermediate, the fused B/C/Hadamard reduction, the
-back-projection to orbitals, for every tau point and spin of the workload
-(default: n=120, N=600, 80 tau, unrestricted; the mid-size molecule stand-in).
+A step is one full build through the C ABI.  Workloads (``--workload``):
+
+* c1 (default) bare SOX, mid-size molecule: n=120, N=600, 80 tau, 2 spins.  Both
+  THC mixed tensors, projections, A, the fused B/C/Hadamard reduction and the
+  back-projection to orbitals for every tau point and spin.
+* c0 bare SOX, small molecule (n=20, N=80, 30 tau).
+* c2 statically screened SOSEX (n=250, N=2000, 100 tau): Pi(0), W(0) and
+  SOX(W(0), v) per step.
+* c3 dynamically screened SOSEX of a solid (3x3x3 k-mesh, n=26, N=300, 60 tau),
+  W_d from a synthetic single-pole form; FP64 complex.
+* c4 the uneven batch of 16 molecules (n in [40, 400], N=6n, 120 tau): Phi, Sigma
+  and dPhi/dG of every instance per step; instances are sharded over ranks.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead (a bounded tau sample per step, scaled to builds/s).
@@ -31,12 +39,11 @@ UNIT = "builds/s"
 def workload(name: str):
     import synth
 
-    if name == "c1":
-        return synth.config(1)
-    if name == "c0":
-        return synth.config(0)
-    if name == "c2":
-        return synth.config(2)
+    if name in ("c0", "c1", "c2", "c3"):
+        return synth.config(int(name[1]))
+    if name == "c4":   # the oracle baselines of the batch time points of its median instance
+        sizes = synth.batch_c4_sizes()
+        return synth.c4_instance(int(np.argsort(sizes, kind="stable")[len(sizes) // 2]))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -111,24 +118,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_tau_points_per_s(w, n_points: int):
-    """Time the CPU oracle (complex128 chain) on n_points (spin, tau) pairs."""
-    from oracle import sox as osox
+def oracle_tau_points_per_s(w, n_points: int, budget_s: float = 20.0):
+    """Time the CPU oracle (complex128 chain) on n_points (spin, tau) pairs of one build.
+
+    Molecules: SOX at one tau point (SOSEX has the same chain and cost with W(0) in
+    the first slot).  Solids: the static momentum-resolved chain at one tau point,
+    all k (the dynamic part is not timed by this sample)."""
+    from oracle import grid as ogrid, kpoints as okp, sox as osox
 
     pts = [(s, j) for j in (0, w.n_tau // 2, w.n_tau - 1, w.n_tau // 4) for s in range(w.n_spin)][:n_points]
     t0 = time.perf_counter()
+    done = []
     for s, j in pts:
-        osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=[j])
+        if done and time.perf_counter() - t0 > budget_s:
+            break
+        done.append((s, j))
+        if w.nk == (1, 1, 1):
+            osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=[j])
+        else:
+            Gm = ogrid.g_minus_tau(np.asarray(w.G[s], complex))
+            okp.sigma_chain(w.X, w.V, w.V, w.G[s][:, j], Gm[:, j], w.nk)
     dt = time.perf_counter() - t0
-    return len(pts) / dt, dt, pts
+    return len(done) / dt, dt, done
 
 
-def cpu_baseline(w, n_points: int) -> dict:
-    rate, dt, pts = oracle_tau_points_per_s(w, n_points)
-    per_build = w.n_tau * w.n_spin
-    return {"value": rate / per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{len(pts)} (spin, tau) points of one build ({per_build} per build), "
-                      f"numpy complex128 chain, {dt:.1f} s; builds/s = points/s / {per_build}"}
+def points_per_build(name: str, w) -> float:
+    """Oracle sample points (one tau point of one spin of ``w``) that make one build."""
+    if name != "c4":
+        return float(w.n_tau * w.n_spin)
+    import synth
+    from paper_2412_18829_gb300 import sharding
+
+    sizes = [int(n) for n in synth.batch_c4_sizes()]
+    return sum(sharding.build_cost(n, 6 * n, 120) for n in sizes) / sharding.build_cost(w.n, w.N, 1)
 
 
 def run_reference(args):
@@ -136,7 +158,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args.workload)
-    per_build = w.n_tau * w.n_spin
+    per_build = points_per_build(args.workload, w)
     for _ in range(args.warmup):
         oracle_tau_points_per_s(w, 1)
     times = []
@@ -150,9 +172,346 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau,
                                             "n_spin": w.n_spin, "step": "one (spin, tau) point of a build"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"1 (spin, tau) point per step of {per_build} per build"},
+                             "sample": f"1 (spin, tau) point of {w.name} per step, {per_build:.4g} such points per build"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Case:
+    """One workload on one rank: device-resident step, host-buffer step, accounting."""
+
+    name = ""
+    dtype = "f64"
+    hot = "sox_bcd"
+    units = 1.0                 # builds per step on this rank
+    cpu_points_per_build = 1.0  # oracle sample points that make one build
+    config: dict = {}
+
+    def step(self):
+        raise NotImplementedError
+
+    def e2e_step(self):
+        """One step with host buffers through the C ABI; returns (h2d_bytes, d2h_bytes)."""
+        raise NotImplementedError
+
+    def hot_flops_per_step(self) -> float:
+        raise NotImplementedError
+
+    def accuracy(self) -> dict:
+        return {}
+
+    def fp64_compare(self, value: float) -> dict:
+        return {}
+
+
+def _tensor_peak(pk, pk_src, achieved):
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_source": f"{pk_src} bf16 sustained (fp16 dense rate = bf16 rate)",
+            "mma_issued_tflops": 3 * achieved if achieved else None,
+            "tensor_pipe_frac": 3 * achieved / peak if achieved else None,
+            "note": "achieved counts algorithmic flops 4N^2n^2 + 2N^2n per (tau, spin); "
+                    "the FP16x2 split issues 3 MMAs per product"}
+
+
+def _alu_peak(achieved, what):
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+            "peak_source": "measured FP64 FMA rate (paper_2412_18829_gb300/probes/fp_rate.cu)", "note": what}
+
+
+FP64_PEAK_TFLOPS = 1.20
+
+
+class MoleculeCase(Case):
+    """Bare SOX (c0, c1) or statically screened SOSEX with Pi(0) and W(0) per step (c2)."""
+
+    def __init__(self, torch, pkg, w, prec, dev, stream, screened: bool):
+        self.torch, self.pkg, self.w, self.prec, self.dev, self.stream = torch, pkg, w, prec, dev, stream
+        self.screened = screened
+        self.name = w.name
+        self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
+        self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
+        self.units = 1.0
+        self.cpu_points_per_build = w.n_tau * w.n_spin
+        self.p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        self.G = torch.from_numpy(w.G).to(dev)
+        self.X = torch.from_numpy(w.X).to(dev)
+        self.V = torch.from_numpy(w.V).to(dev)
+        self.S = torch.empty_like(self.G)
+        _, wts = pkg.sox_tau_grid(w.n_tau, w.beta)
+        self.wts_h = np.ascontiguousarray(wts)
+        self.wts = torch.from_numpy(self.wts_h).to(dev)
+        self.Pi = torch.empty(w.n_spin, w.N, w.N, dtype=torch.float64, device=dev)
+        self.W0 = torch.empty(1, w.N, w.N, dtype=torch.float64, device=dev)
+        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.config = {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
+                       "beta": w.beta, "precision": prec,
+                       "step": ("Pi(0) + W(0) + SOX(W(0), v) through the C ABI" if screened
+                                else "bare SOX(v, v) through the C ABI")}
+
+    def _run(self, h, G, X, V, S, Pi, W0, stream):
+        pkg = self.pkg
+        if not self.screened:
+            pkg.sox_sigma(h, self.p, G, X, V, S, stream)
+            return
+        pkg.sox_pi0(h, self.p, G, X, self.wts if isinstance(G, self.torch.Tensor) else self.wts_h, Pi, stream)
+        pkg.sox_w_static(h, self.p, V, Pi[0:1] if self.w.n_spin == 1 else Pi.sum(0, keepdim=True), W0, stream)
+        pkg.sosex_static_sigma(h, self.p, G, X, V, W0, S, slot=1, stream=stream)
+
+    def step(self):
+        self._run(self.h, self.G, self.X, self.V, self.S, self.Pi, self.W0, self.stream)
+
+    def e2e_step(self):
+        if not hasattr(self, "Gh"):
+            pin = lambda a: self.torch.from_numpy(a).pin_memory().numpy()   # noqa: E731
+            self.Gh, self.Xh, self.Vh = pin(self.w.G), pin(self.w.X), pin(self.w.V)
+            self.Sh = pin(np.empty_like(self.w.G))
+        self._run(self.h, self.Gh, self.Xh, self.Vh, self.Sh, self.Pi, self.W0, self.stream)
+        w = self.w
+        h2d = w.G.nbytes + w.X.nbytes + w.V.nbytes
+        if self.screened:   # Pi(0) reads G, X, w; W(0) reads V; SOSEX reads G, X, V again
+            h2d += w.G.nbytes + w.X.nbytes + self.wts_h.nbytes + w.V.nbytes
+        return h2d, w.G.nbytes
+
+    def hot_flops_per_step(self):
+        w = self.w
+        return (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * w.n_tau * w.n_spin
+
+    def accuracy(self) -> dict:
+        from oracle import grid as ogrid, screening as oscr, sox as osox
+
+        w = self.w
+        out = self.S.cpu().numpy()
+        if not self.screened:
+            taus = [0, w.n_tau - 1]
+            err = smax = 0.0
+            for s in range(w.n_spin):
+                ref = osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
+                err = max(err, float(np.abs(out[s, 0, taus] - ref).max()))
+                smax = max(smax, float(np.abs(ref).max()))
+            return {"max_abs_err_Ha_vs_oracle": err, "max_rel_err_vs_oracle": err / smax,
+                    "oracle_sample": f"tau {taus} x {w.n_spin} spins"}
+        wt = ogrid.clenshaw_curtis(w.n_tau, w.beta)
+        Pi = oscr.pi0_quadrature(w.X[0], w.G[0, 0], wt).real
+        Wr = oscr.w_static(w.V[0], 0.5 * (Pi + Pi.T))
+        j = w.n_tau // 2
+        ref = osox.sigma_tau(w.X[0], Wr, w.V[0], w.G[0, 0], taus=[j], dtype=np.float64)
+        err = float(np.abs(out[0, 0, [j]] - ref).max())
+        werr = float((self.W0[0].cpu() - self.torch.from_numpy(Wr)).abs().max()) / float(np.abs(Wr).max())
+        return {"max_abs_err_Ha_vs_oracle": err, "max_rel_err_vs_oracle": err / float(np.abs(ref).max()),
+                "W0_max_rel_err_vs_oracle": werr,
+                "oracle_sample": f"tau index {j}; oracle W(0) from its own Pi(0)"}
+
+    def fp64_compare(self, value: float) -> dict:
+        if self.prec == "fp64":
+            return {}
+        torch = self.torch
+        with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
+            S64 = torch.empty_like(self.G)
+            self.pkg.sox_reserve(h64, self.p)
+            self._run(h64, self.G, self.X, self.V, S64, self.Pi, self.W0, self.stream)   # warm
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            self._run(h64, self.G, self.X, self.V, S64, self.Pi, self.W0, self.stream)
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b) / 1e3
+            return {"fp64_gpu_builds_per_s": 1.0 / t64, "speedup_vs_fp64_gpu": value * t64,
+                    "max_abs_err_Ha_vs_fp64_gpu_all_points": float((self.S - S64).abs().max().item())}
+
+
+def _zflops(*cmacs):
+    return 8.0 * float(sum(cmacs))
+
+
+class SolidCase(Case):
+    """Dynamically screened SOSEX of a solid (c3), FP64 complex: SOX(v, v) + Sigma_d."""
+
+    def __init__(self, torch, pkg, w, dev, stream):
+        import synth
+
+        self.torch, self.pkg, self.w, self.dev, self.stream = torch, pkg, w, dev, stream
+        self.name = w.name
+        self.dtype = "c128"
+        self.hot = "kpoint_dynamic_f64"
+        self.units = 1.0
+        self.cpu_points_per_build = w.n_tau * w.n_spin
+        M = (w.n_tau - 1) // 2
+        _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, M)
+        Wd = synth.pole_screening(w.V, w.beta, M)
+        self.nO = 2 * M + 1
+        self.p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta, nk=w.nk, dtype=1)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=complex)).to(dev)   # noqa: E731
+        self.G, self.X, self.V, self.Wd, self.Tf, self.Ti = (to(a) for a in (w.G, w.X, w.V, Wd, Tf, Ti))
+        self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
+        self.S = torch.empty_like(self.G)
+        self.h = pkg.Handle("fp64", device=dev.index or 0)
+        self.config = {"workload": w.name, "nk": list(w.nk), "n": w.n, "N": w.N, "n_tau": w.n_tau,
+                       "n_omega": self.nO, "beta": w.beta, "precision": "fp64 complex",
+                       "W_d": "synthetic single-pole form (synth.pole_screening), input",
+                       "step": "SOX(v, v) + dynamically screened Sigma_d through the C ABI"}
+
+    def step(self):
+        self.pkg.sosex_dynamic_sigma(self.h, self.p, self.G, self.X, self.V, self.Wd, self.Tf, self.Ti,
+                                     self.nO, self.S, self.stream)
+
+    def e2e_step(self):
+        if not hasattr(self, "hp"):
+            self.hp = [self.torch.from_numpy(np.ascontiguousarray(a, dtype=complex)).pin_memory().numpy()
+                       for a in self.host]
+            self.Sh = self.torch.from_numpy(np.empty_like(self.hp[0])).pin_memory().numpy()
+        G, X, V, Wd, Tf, Ti = self.hp
+        self.pkg.sosex_dynamic_sigma(self.h, self.p, G, X, V, Wd, Tf, Ti, self.nO, self.Sh, self.stream)
+        return sum(a.nbytes for a in self.hp), self.Sh.nbytes
+
+    def phase_flops(self):
+        w = self.w
+        nk = w.nk[0] * w.nk[1] * w.nk[2]
+        n, N, T, nO = w.n, w.N, w.n_tau, self.nO
+        mixed = nk * nk * N * N * n * n
+        static = mixed + T * (nk * nk * N * n ** 3 + 2 * nk * nk * n * N * N * n + nk ** 3 * n * N * N
+                              + nk * (N * N * n + N * n * n))
+        dyn = mixed + 2 * nk * T * N * n * n + n * nk * (nk * nO * T * N * n + nk * nO * N * N * n
+                                                          + nk * T * nO * N * n) \
+            + n * T * (2 * nk * nk * N * N * n + nk ** 3 * N * N) + T * nk * (N * N * n + N * n * n)
+        return _zflops(static), _zflops(dyn)
+
+    def hot_flops_per_step(self):
+        return self.phase_flops()[1]
+
+
+class BatchCase(Case):
+    """The uneven batch (c4): Phi and Sigma of every instance, then dPhi/dG from the kept
+    Sigma; the 16 instances are dealt out over the ranks (no data-path collective)."""
+
+    def __init__(self, torch, pkg, prec, dev, stream, rank, world):
+        import synth
+        from paper_2412_18829_gb300 import sharding
+
+        self.torch, self.pkg, self.prec, self.dev, self.stream = torch, pkg, prec, dev, stream
+        sizes = [int(n) for n in synth.batch_c4_sizes()]
+        costs = [sharding.build_cost(n, 6 * n, 120) for n in sizes]
+        self.mine = sharding.shard(costs, world)[rank]
+        self.world = world
+        self.name = "sox-c4-batch16-N6n-t120"
+        self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
+        self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
+        self.units = 1.0 / world
+        self.cpu_points_per_build = points_per_build("c4", workload("c4"))
+        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.inst = []
+        for i in self.mine:
+            w = synth.c4_instance(i)
+            _, wts = pkg.sox_tau_grid(w.n_tau, w.beta)
+            d = {"w": w, "p": pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta),
+                 "G": torch.from_numpy(w.G).to(dev), "X": torch.from_numpy(w.X).to(dev),
+                 "V": torch.from_numpy(w.V).to(dev), "wt": torch.from_numpy(np.ascontiguousarray(wts)).to(dev),
+                 "wt_h": np.ascontiguousarray(wts)}
+            d["S"] = torch.empty_like(d["G"])
+            d["dG"] = torch.empty_like(d["G"])
+            d["phi"] = torch.empty(w.n_spin, dtype=torch.float64, device=dev)
+            d["dphi"] = torch.ones(w.n_spin, dtype=torch.float64, device=dev)
+            self.inst.append(d)
+        self.config = {"workload": self.name, "instances": len(sizes), "n": sizes, "N": "6n", "n_tau": 120,
+                       "beta": 100.0, "precision": prec, "instances_on_rank0": self.mine if rank == 0 else None,
+                       "step": "per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept "
+                               "Sigma); one launch sequence per instance"}
+
+    def _one(self, h, d, G, X, V, wt, S, phi, dG):
+        self.pkg.phi_sox(h, d["p"], G, X, V, wt, phi, S, self.stream)
+        self.pkg.phi_sox_grad_G(h, d["p"], S, wt, d["dphi"], dG, self.stream)
+
+    def step(self):
+        for d in self.inst:
+            self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"])
+
+    def e2e_step(self):
+        h2d = d2h = 0
+        for d in self.inst:
+            if "Gh" not in d:
+                pin = lambda a: self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+                w = d["w"]
+                d["Gh"], d["Xh"], d["Vh"] = pin(w.G), pin(w.X), pin(w.V)
+                d["Sh"], d["dGh"], d["phih"] = pin(np.empty_like(w.G)), pin(np.empty_like(w.G)), pin(np.zeros(w.n_spin))
+            self._one(self.h, d, d["Gh"], d["Xh"], d["Vh"], d["wt_h"], d["Sh"], d["phih"], d["dGh"])
+            h2d += d["Gh"].nbytes + d["Xh"].nbytes + d["Vh"].nbytes + 2 * d["wt_h"].nbytes + d["Sh"].nbytes
+            d2h += d["Sh"].nbytes + d["phih"].nbytes + d["dGh"].nbytes
+        return h2d, d2h
+
+    def hot_flops_per_step(self):
+        return sum((4.0 * d["w"].N ** 2 * d["w"].n ** 2 + 2.0 * d["w"].N ** 2 * d["w"].n) * d["w"].n_tau
+                   for d in self.inst)
+
+    def _smallest(self):
+        import synth
+
+        small = synth.c4_smallest(3)
+        return [d for i, d in zip(self.mine, self.inst) if i in small]
+
+    def accuracy(self) -> dict:
+        from oracle import sox as osox
+
+        err = rel = 0.0
+        for d in self._smallest():
+            w = d["w"]
+            taus = [0, w.n_tau // 2]
+            ref = osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[0, 0], taus=taus, dtype=np.float64)
+            e = float(np.abs(d["S"].cpu().numpy()[0, 0, taus] - ref).max())
+            err, rel = max(err, e), max(rel, e / float(np.abs(ref).max()))
+        return {"max_abs_err_Ha_vs_oracle": err, "max_rel_err_vs_oracle": rel,
+                "oracle_sample": "tau 0 and n_tau/2 of the three smallest instances"}
+
+    def fp64_compare(self, value: float) -> dict:
+        """FP64 forward, and the FP64 X/V adjoint, on the three smallest instances."""
+        torch = self.torch
+        sub = self._smallest()
+        if not sub:
+            return {}
+        out = {}
+        ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a, b = ev()
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / 1e3
+
+        t_mixed = timed(lambda: [self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"])
+                                 for d in sub])
+        with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
+            S64 = [torch.empty_like(d["S"]) for d in sub]
+            t64 = timed(lambda: [self._one(h64, d, d["G"], d["X"], d["V"], d["wt"], s, d["phi"], d["dG"])
+                                 for d, s in zip(sub, S64)])
+            dX = [torch.empty_like(d["X"]) for d in sub]
+            dV = [torch.empty_like(d["V"]) for d in sub]
+            t_adj = timed(lambda: [self.pkg.phi_sox_backward(h64, d["p"], d["G"], d["X"], d["V"], d["wt"], d["dphi"],
+                                                             None, x, v, self.stream)
+                                   for d, x, v in zip(sub, dX, dV)])
+            out["max_abs_err_Ha_vs_fp64_gpu_smallest3"] = max(float((d["S"] - s).abs().max()) for d, s in zip(sub, S64))
+        adj_flops = sum(12.0 * d["w"].N ** 2 * d["w"].n ** 2 * d["w"].n_tau for d in sub)
+        out.update({"smallest3_n": [d["w"].n for d in sub],
+                    "smallest3_ms_f16x2": 1e3 * t_mixed, "smallest3_ms_fp64": 1e3 * t64,
+                    "speedup_vs_fp64_gpu_smallest3": t64 / t_mixed,
+                    "adjoint_XV_fp64_ms_smallest3": 1e3 * t_adj,
+                    "adjoint_XV_fp64_tflops": adj_flops / t_adj / 1e12,
+                    "adjoint_note": "dPhi/dX, dPhi/dV by the FP64 reverse pass (12 N^2 n^2 per tau counted)"})
+        return out
+
+
+def make_case(args, torch, pkg, dev, stream, rank, world):
+    if args.workload == "c4":
+        return BatchCase(torch, pkg, args.precision, dev, stream, rank, world)
+    w = workload(args.workload)
+    if args.workload == "c3":
+        return SolidCase(torch, pkg, w, dev, stream)
+    return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"))
 
 
 def run_ours(args):
@@ -171,144 +530,109 @@ def run_ours(args):
 
     __graft_entry__.build()
     import paper_2412_18829_gb300 as pkg
+    from paper_2412_18829_gb300 import sharding
 
-    w = workload(args.workload)
     dev = torch.device("cuda", local)
-    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
-    G = torch.from_numpy(w.G).to(dev)
-    X = torch.from_numpy(w.X).to(dev)
-    V = torch.from_numpy(w.V).to(dev)
-    S = torch.empty_like(G)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    h = pkg.Handle(args.precision, device=local)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        pkg.sox_sigma(h, p, G, X, V, S, stream)
+    case = make_case(args, torch, pkg, dev, stream, rank, world)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     for _ in range(args.warmup):
-        step()
+        case.step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    pkg.sox_profile_enable(h, True)
+    pkg.sox_profile_enable(case.h, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        step()
+        case.step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    launches, _ = pkg.sox_profile_read(h, None)
-    hot = "sox_bcd_tc" if args.precision == "f16x2" else "sox_bcd"
-    hot_n, hot_ms = pkg.sox_profile_read(h, hot)
-    pkg.sox_profile_enable(h, False)
+    launches, _ = pkg.sox_profile_read(case.h, None)
+    hot_n, hot_ms = pkg.sox_profile_read(case.h, case.hot)
+    phases = {}
+    if isinstance(case, SolidCase):
+        phases["kpoint_f64"] = pkg.sox_profile_read(case.h, "kpoint_f64")
+    pkg.sox_profile_enable(case.h, False)
     clocks = sampler.stop()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = float(np.sum(ms)) / 1e3
-    t_max = t_local
     if dist:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    builds = args.steps * world
-    value = builds / t_max
+        dist.barrier()
+    t_local = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    t_max = sharding.max_over_ranks(t_local, dist, dev)
+    total_units = case.units * world          # builds of the whole job per step
+    value = total_units * args.steps / t_max
 
-    # accuracy of this build: against the FP64 GPU path (all points) and the oracle (sampled)
-    out = S.cpu().numpy()
     extra = {}
     if rank == 0 and not args.skip_accuracy:
-        from oracle import sox as osox
+        extra.update(case.accuracy())
+    if rank == 0 and not args.skip_fp64:
+        extra.update(case.fp64_compare(case.units / (t_local / args.steps)))
 
-        taus = [0, w.n_tau - 1]
-        err = 0.0
-        smax = 0.0
-        for s in range(w.n_spin):
-            ref = osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
-            err = max(err, float(np.abs(out[s, 0, taus] - ref).max()))
-            smax = max(smax, float(np.abs(ref).max()))
-        extra["max_abs_err_Ha_vs_oracle"] = err
-        extra["max_rel_err_vs_oracle"] = err / smax
-        extra["oracle_sample"] = f"tau {taus} x {w.n_spin} spins"
-    if rank == 0 and args.precision != "fp64" and not args.skip_fp64:
-        with pkg.Handle("fp64", device=local) as h64:
-            S64 = torch.empty_like(G)
-            pkg.sox_sigma(h64, p, G, X, V, S64, stream)   # warm
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.zero_()
-            a.record(stream)
-            pkg.sox_sigma(h64, p, G, X, V, S64, stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t64 = a.elapsed_time(b) / 1e3
-            extra["fp64_gpu_builds_per_s"] = 1.0 / t64
-            extra["speedup_vs_fp64_gpu"] = value / world * t64
-            extra["max_abs_err_Ha_vs_fp64_gpu_all_points"] = float((S - S64).abs().max().item())
-
-    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
-    Gh = torch.from_numpy(w.G).pin_memory()
-    Xh = torch.from_numpy(w.X).pin_memory()
-    Vh = torch.from_numpy(w.V).pin_memory()
-    Sh = torch.empty_like(Gh).pin_memory()
-    pkg.sox_sigma(h, p, Gh.numpy(), Xh.numpy(), Vh.numpy(), Sh.numpy(), stream)
-    e2e_t = []
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.zero_()
+    e2e = None
+    if not args.skip_e2e:
+        h2d, d2h = case.e2e_step()    # warm the pinned buffers and staging workspace
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pkg.sox_sigma(h, p, Gh.numpy(), Xh.numpy(), Vh.numpy(), Sh.numpy(), stream)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_val = world / float(np.mean(e2e_t))
-    h2d = (w.G.nbytes + w.X.nbytes + w.V.nbytes)
-    d2h = w.G.nbytes
+        e2e_t = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            case.e2e_step()
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+        te = sharding.max_over_ranks(float(np.mean(e2e_t)), dist, dev)
+        e2e = {"value": total_units / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    fl = flops_per_build(w)
     pk, pk_src = peaks()
-    per_launch_units = (w.n_tau * w.n_spin) / max(1, hot_n / args.steps)
-    hot_flops_launch = fl["bcd"] / (w.n_tau * w.n_spin) * per_launch_units
-    hot_avg_s = (hot_ms / max(1, hot_n)) / 1e3
-    achieved = hot_flops_launch / hot_avg_s / 1e12 if hot_n else None
-    if args.precision == "f16x2":
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": hot, "peak_source": f"{pk_src} bf16 sustained (fp16 dense rate = bf16 rate)",
-                "mma_issued_tflops": 3 * achieved if achieved else None,
-                "tensor_pipe_frac": 3 * achieved / peak if achieved else None,
-                "note": "achieved counts algorithmic flops 4N^2n^2 per (tau,spin); the FP16x2 split issues 3 MMAs per product"}
+    hot_s = hot_ms / 1e3
+    achieved = case.hot_flops_per_step() * args.steps / hot_s / 1e12 if hot_n and hot_s > 0 else None
+    if isinstance(case, SolidCase):
+        f_static, f_dyn = case.phase_flops()
+        roof = _alu_peak(achieved, "dominant phase: the dynamic part (GG, transforms, W_d product, B/C, "
+                                   "n_k^3 D step) in FP64 complex on CUDA cores; algorithmic flops at 8 per complex MAC")
+        roof["kernel"] = case.hot
+        n_s, ms_s = phases["kpoint_f64"]
+        extra["static_phase_tflops"] = f_static * args.steps / (ms_s / 1e3) / 1e12 if ms_s else None
+        extra["phase_ms_per_step"] = {"kpoint_f64": ms_s / args.steps, case.hot: hot_ms / args.steps}
+    elif case.dtype.startswith("f16x2"):
+        roof = _tensor_peak(pk, pk_src, achieved)
+        roof["kernel"] = case.hot
     else:
-        peak = 1.20
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None, "kernel": hot,
-                "peak_source": "measured FP64 FMA rate (paper_2412_18829_gb300/probes/fp_rate.cu)"}
+        roof = _alu_peak(achieved, "fused FP64 B/C/Hadamard kernel")
+        roof["kernel"] = case.hot
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f16x2+f32acc,f64" if args.precision == "f16x2" else "f64",
-        "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
-                   "beta": w.beta, "precision": args.precision,
-                   "l2": "flushed between steps (256 MiB write outside the events)",
-                   "parallelism": f"{world} independent builds (one per GPU)",
-                   "algorithmic_tflops_per_s": fl["total"] * value / 1e12, **extra},
+        "scaling": "strong" if isinstance(case, BatchCase) else "weak", "vs_baseline": None,
+        "dtype": case.dtype, "data": "synthetic",
+        "config": {**case.config, "l2": "flushed between steps (256 MiB write outside the events)",
+                   "parallelism": (f"batch instances sharded over {world} GPUs" if isinstance(case, BatchCase)
+                                   else f"{world} independent builds (one per GPU)"), **extra},
         "roofline": roof,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
     if world == 1 and not args.skip_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_points)
+        w0 = workload(args.workload)
+        rate, dt, pts = oracle_tau_points_per_s(w0, args.cpu_points)
+        line["cpu_baseline"] = {
+            "value": rate / case.cpu_points_per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(pts)} (spin, tau) points of {w0.name} ({case.cpu_points_per_build:.4g} such points "
+                      f"per build), numpy complex128 chain, {dt:.1f} s; builds/s = points/s / points per build"}
     print(json.dumps(line), flush=True)
-    h.close()
+    case.h.close()
     if dist:
         dist.destroy_process_group()
 
@@ -320,11 +644,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16x2", choices=["f16x2", "fp64"])
-    ap.add_argument("--workload", default="c1")
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--cpu-points", type=int, default=16)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -85,6 +85,12 @@ typedef struct {
                           * point (or one v) is used even when it exceeds the
                           * limit; fixed-size tensors (mixed tensors, the D
                           * array of the dynamic paths) are not counted.      */
+  int no_autotune;      /* 0: on the first call for a new shape, the split path
+                         * times its fused-kernel variants on the call's own
+                         * data (one extra launch each, a host synchronisation)
+                         * and keeps the fastest for that shape on the handle;
+                         * skipped while the stream is being captured.
+                         * nonzero: fixed choice, no timing.                   */
 } sox_options;
 
 typedef struct {

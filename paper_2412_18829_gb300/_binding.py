@@ -37,7 +37,7 @@ class sox_problem(ctypes.Structure):
 
 class sox_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("spin_limit", ctypes.c_longlong),
-                ("workspace_limit", ctypes.c_longlong)]
+                ("workspace_limit", ctypes.c_longlong), ("no_autotune", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -131,8 +131,10 @@ def problem(n, N, n_tau, n_spin=1, beta=100.0, nk=(1, 1, 1), dtype=SOX_REAL64) -
 class Handle:
     """Owns a ``sox_handle`` (device workspace, precision choice)."""
 
-    def __init__(self, precision: str = "fp64", device: int = 0, spin_limit: int = 0, workspace_limit: int = 0):
-        o = sox_options(PRECISIONS[precision], int(device), int(spin_limit), int(workspace_limit))
+    def __init__(self, precision: str = "fp64", device: int = 0, spin_limit: int = 0, workspace_limit: int = 0,
+                 autotune: bool = True):
+        o = sox_options(PRECISIONS[precision], int(device), int(spin_limit), int(workspace_limit),
+                        0 if autotune else 1)
         h = _P()
         rc = lib().sox_create(ctypes.byref(h), ctypes.byref(o))
         if rc != SOX_OK:

@@ -337,7 +337,7 @@ int sox_version(void) { return 100; }
 int sox_create(sox_handle *out, const sox_options *opt) {
   if (!out) return SOX_ERR_INVALID_ARG;
   *out = nullptr;
-  sox_options o{SOX_PREC_FP64, 0, 0, 0};
+  sox_options o{SOX_PREC_FP64, 0, 0, 0, 0};
   if (opt) o = *opt;
   if (o.precision != SOX_PREC_FP64 && o.precision != SOX_PREC_F16X2) return SOX_ERR_INVALID_ARG;
   int ndev = 0;
@@ -356,6 +356,7 @@ int sox_create(sox_handle *out, const sox_options *opt) {
     return SOX_ERR_INVALID_ARG;
   }
   h->ws_limit = (size_t)o.workspace_limit;
+  h->autotune = (o.no_autotune == 0);
   int prev = -1;
   cudaGetDevice(&prev);
   if (cudaSetDevice(o.device) != cudaSuccess ||

@@ -21,6 +21,8 @@ struct sox_context {
   size_t ws_bytes = 0;
   int *d_status = nullptr;   // device status word for bounded waits
   int sm_count = 0;
+  bool autotune = true;      // time the fused-kernel variants on the first call per shape
+  std::map<std::string, int> tuned;  // shape key -> chosen variant
   std::string last_error;
   // launch accounting (sox_profile_enable / sox_profile_read)
   bool prof = false;

@@ -1028,8 +1028,8 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers)
 
 size_t res_smem_bytes() { return (size_t)kResBytes + kRStages * kRStageBytes + sizeof(ResBarriers) + 1024; }
 
-cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s) {
-  if (a.Kp <= 128) {
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant) {
+  if (variant == kBcdResident && a.Kp <= 128) {
     static bool rattr = false;
     if (!rattr) {
       cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -42,7 +42,10 @@ bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t 
 size_t tc_smem_bytes();
 bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
                            uint64_t batch, std::string *err);
-cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s);
+// Variants of the fused kernel: G_R / G_wP^T resident in shared memory for the whole
+// (spin, tau) batch (Kp <= 128 only), or streamed with A_v and U2_v.
+enum { kBcdResident = 1, kBcdStreamed = 2 };
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant);
 // maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);
 // rows of batch b come from alt_src instead of src when use_alt[b] != 0 (both optional)

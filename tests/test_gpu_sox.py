@@ -240,3 +240,25 @@ def test_capture_in_cuda_graph_and_replay(env, prec):
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
     pkg.sox_check_device(hs[prec])
+
+
+@pytest.mark.parametrize("n,N", [(40, 200), (150, 300)])
+def test_autotuned_and_fixed_fused_kernel_agree(env, n, N):
+    """The autotuner times the fused kernel's variants on the first call for a shape;
+    whichever it keeps, the result meets the parity bar and matches the fixed choice."""
+    torch, pkg, _ = env
+    w = synth.molecule(19, n, N, 4, 100.0)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    out = {}
+    for tune in (True, False):
+        with pkg.Handle("f16x2", autotune=tune) as h:
+            for _ in range(2):                       # first call tunes, second uses the kept choice
+                S = torch.full_like(G, float("nan"))
+                pkg.sox_sigma(h, p, G, X, V, S)
+            pkg.sox_check_device(h)
+            out[tune] = S.cpu().numpy()
+    ref = sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64)
+    for r in out.values():
+        check(r, ref, "f16x2", "autotune")
+    assert np.abs(out[True] - out[False]).max() <= 1e-9
