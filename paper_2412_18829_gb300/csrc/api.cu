@@ -9,6 +9,7 @@
 #include "adjoint.h"
 #include "dynamic.h"
 #include "internal.h"
+#include "ctc.h"
 #include "kpoint.h"
 #include "tc_path.h"
 
@@ -297,6 +298,11 @@ Status run_sigma_complex(sox_handle h, const sox_problem *p, const double *G, co
   if (!same) SOX_TRY(call.input(U2, 2 * (size_t)nk * p->N * p->N, &s2));
   SOX_TRY(call.output(Sigma, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &sS));
   Arena ar;
+  if (h->precision == SOX_PREC_F16X2) {
+    SOX_TRY(call.begin(sox::kpoint_tc_bytes(h, p, !same), &ar));
+    SOX_TRY(sox::kpoint_sigma_tc(h, p, sG.in, sX.in, s1.in, same ? s1.in : s2.in, sS.out, ar, call.stream()));
+    return call.end();
+  }
   const sox::KpointPlan pl = sox::kpoint_plan(h, p->n, p->N, p->n_tau, p->n_spin, p->nk);
   SOX_TRY(call.begin(pl.bytes + (same ? 0 : 16 * (size_t)nk * nk * p->N * nn), &ar));
   SOX_TRY(sox::kpoint_sigma_f64(h, p, sG.in, sX.in, s1.in, same ? s1.in : s2.in, sS.out, ar, call.stream()));
@@ -762,8 +768,20 @@ int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, con
       SOX_TRY(call.input(T_fwd, 2 * (size_t)n_omega * p->n_tau, &sF));
       SOX_TRY(call.input(T_inv, 2 * (size_t)n_omega * p->n_tau, &sI));
       SOX_TRY(call.output(Sigma, 2 * (size_t)p->n_spin * nk * p->n_tau * nn, &oS));
-      const sox::KpointPlan pl = sox::kpoint_plan(h, p->n, p->N, p->n_tau, p->n_spin, p->nk);
       Arena ar;
+      if (h->precision == SOX_PREC_F16X2) {
+        SOX_TRY(call.begin(std::max(sox::kpoint_tc_bytes(h, p, false), sox::kpoint_dynamic_tc_bytes(h, p, n_omega)),
+                           &ar));
+        {
+          Arena a1 = ar;
+          SOX_TRY(sox::kpoint_sigma_tc(h, p, sG.in, sX.in, sV.in, sV.in, oS.out, a1, call.stream()));
+        }
+        Arena a2 = ar;
+        SOX_TRY(sox::kpoint_dynamic_tc(h, p, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in, oS.out, a2,
+                                       call.stream()));
+        return call.end();
+      }
+      const sox::KpointPlan pl = sox::kpoint_plan(h, p->n, p->N, p->n_tau, p->n_spin, p->nk);
       SOX_TRY(call.begin(std::max(pl.bytes, sox::kpoint_dynamic_bytes(h, p->n, p->N, p->n_tau, n_omega, p->nk, nullptr)),
                          &ar));
       {

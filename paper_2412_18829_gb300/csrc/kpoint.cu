@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "ctc.h"
 #include "kpoint.h"
 
 namespace sox {
@@ -150,6 +151,26 @@ __global__ void k_kpoint_D(const z *B, const z *C, const int *add, const int *su
 }
 
 int grid1(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 65535 * 8)); }
+
+// add[a][b] = index of k_a + k_b, sub[a][b] = index of k_a - k_b on the problem's mesh
+void mesh_tables(const sox_problem *pr, std::vector<int> &add, std::vector<int> &sub) {
+  const int n1 = pr->nk[0], n2 = pr->nk[1], n3 = pr->nk[2], nk = n1 * n2 * n3;
+  add.assign((size_t)nk * nk, 0);
+  sub.assign((size_t)nk * nk, 0);
+  auto idx = [&](int x, int y, int zz) {
+    x = ((x % n1) + n1) % n1;
+    y = ((y % n2) + n2) % n2;
+    zz = ((zz % n3) + n3) % n3;
+    return (x * n2 + y) * n3 + zz;
+  };
+  for (int a = 0; a < nk; ++a)
+    for (int b = 0; b < nk; ++b) {
+      const int ax = a / (n2 * n3), ay = (a / n3) % n2, az = a % n3;
+      const int bx = b / (n2 * n3), by = (b / n3) % n2, bz = b % n3;
+      add[(size_t)a * nk + b] = idx(ax + bx, ay + by, az + bz);
+      sub[(size_t)a * nk + b] = idx(ax - bx, ay - by, az - bz);
+    }
+}
 
 // GG[ks][j][Q][u] = GWt[ku][j][Q][u] * (-GR[ks][T-1-j][Q][v]),  ku = ks - q1
 __global__ void k_gg_k(const z *GWt, const z *GR, const int *sub, int nk, int q1, int T, int N, int n, int v, z *GG) {
@@ -546,6 +567,382 @@ Status kpoint_dynamic_add_f64(sox_handle h, const sox_problem *pr, int n_omega, 
       o.C = Sig + ((long long)sp * nk * T + i) * nn; o.sC = (long long)T * nn; o.ci = n; o.cj = 1;
       o.alpha = -inv_nk2; o.beta = 1.0;
       zgemm(o, s);
+      launches += 2;
+    }
+  }
+  h->launches += launches;
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision forms (SOX_PREC_F16X2): every contraction of the chain as a
+// complex FP16-pair GEMM on the tensor cores (ctc.cu), FP32 results; the
+// projections, the D accumulation over v and the back-projection stay FP64.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct KTc {
+  int nk, n, N, T, S;
+  long long nk2, nn, Nn, NN, Nn2;
+  int vpad;   // complex row length of A_all (n rounded up to even)
+  int ldN;    // complex row length of B, C and D (N rounded up to even)
+};
+
+KTc ktc_geom(const sox_problem *p) {
+  KTc g;
+  g.nk = p->nk[0] * p->nk[1] * p->nk[2];
+  g.n = p->n;
+  g.N = p->N;
+  g.T = p->n_tau;
+  g.S = p->n_spin;
+  g.nk2 = (long long)g.nk * g.nk;
+  g.nn = (long long)g.n * g.n;
+  g.Nn = (long long)g.N * g.n;
+  g.NN = (long long)g.N * g.N;
+  g.Nn2 = g.Nn * g.n;
+  g.vpad = g.n + (g.n & 1);
+  g.ldN = g.N + (g.N & 1);
+  return g;
+}
+
+// device tables: add, sub (n_k x n_k), kk[pair] = pair % n_k, ku[pair] = sub[pair % n_k][pair / n_k]
+struct KTables {
+  int *add = nullptr, *sub = nullptr, *kk = nullptr, *ku = nullptr, *qq = nullptr;
+  std::vector<int> h_add, h_sub;
+};
+
+Status ktc_tables(const sox_problem *pr, const KTc &g, Arena &ar, cudaStream_t s, KTables *t) {
+  mesh_tables(pr, t->h_add, t->h_sub);
+  std::vector<int> kk(g.nk2), ku(g.nk2), qq(g.nk2);
+  for (long long pr_ = 0; pr_ < g.nk2; ++pr_) {
+    const int ks = (int)(pr_ % g.nk), q = (int)(pr_ / g.nk);
+    kk[pr_] = ks;
+    qq[pr_] = q;
+    ku[pr_] = t->h_sub[(size_t)ks * g.nk + q];
+  }
+  t->add = ar.take<int>(g.nk2);
+  t->sub = ar.take<int>(g.nk2);
+  t->kk = ar.take<int>(g.nk2);
+  t->ku = ar.take<int>(g.nk2);
+  t->qq = ar.take<int>(g.nk2);
+  if (!t->qq) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  SOX_CUDA_TRY(cudaMemcpyAsync(t->add, t->h_add.data(), 4 * g.nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(t->sub, t->h_sub.data(), 4 * g.nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(t->kk, kk.data(), 4 * g.nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(t->ku, ku.data(), 4 * g.nk2, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemcpyAsync(t->qq, qq.data(), 4 * g.nk2, cudaMemcpyHostToDevice, s));
+  return Status::ok();
+}
+
+size_t tables_bytes(const KTc &g) { return 5 * aligned_bytes(g.nk2, 4); }
+
+long long nnpad_of(const KTc &g) { return g.nn + (g.nn & 1); }
+
+// scratch of mixed_tc (released after the call)
+size_t mixed_tc_scratch(const KTc &g) {
+  return csplit_bytes(g.nk, g.N, g.N) + csplit_bytes((int)g.nk2, (int)(2 * g.nn), g.N);
+}
+size_t mixed_tc_bytes(const KTc &g) { return aligned_bytes((size_t)g.nk2 * g.N * nnpad_of(g), 8); }
+
+// Mixed tensor on the tensor cores, FP32 complex [pair][P][(a,b)] with row length nnpad:
+//   M^{q,k'}[P][(a,b)] = sum_Q U^q[P][Q] conj(X^{k'-q}[Q][a]) X^{k'}[Q][b]
+Status mixed_tc(sox_handle h, const z *X, const z *U, const KTables &tb, const KTc &g, Arena scratch, float *M,
+                cudaStream_t s) {
+  CSplit Us = csplit_take(scratch, g.nk, g.N, g.N);
+  CSplit Ys = csplit_take(scratch, (int)g.nk2, (int)(2 * g.nn), g.N);
+  if (!Ys.hi) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  csplit_a(U, false, g.NN, g.N, 0, 0, 1, g.nk, g.N, g.N, Us, s);
+  csplit_pairs(reinterpret_cast<const double *>(X), tb.sub, g.nk, g.N, g.n, Ys, s);
+  h->launches += 2;
+  const long long ld = nnpad_of(g);
+  return cgemm_tc(h, Us, Ys, (int)g.nk2, tb.qq, nullptr, 1.f, M, 2 * ld, 2 * g.N * ld, s);
+}
+
+void split_m1_tc(const float *M, const KTc &g, const CSplit &M1s, cudaStream_t s) {
+  const long long ld = nnpad_of(g);
+  csplit_a(M, true, g.N * ld, ld, g.n, g.n, 1, (int)g.nk2, (int)g.Nn, g.n, M1s, s);
+}
+
+void split_m2_tc(const float *M, const KTc &g, const std::vector<CSplit> &M2s, cudaStream_t s) {
+  const long long ld = nnpad_of(g);
+  for (int v = 0; v < g.n; ++v)
+    csplit_b(reinterpret_cast<const float2 *>(M) + (long long)v * g.n, true, g.N * ld, ld, 0, 0, 1, (int)g.nk2, g.N,
+             g.n, false, false, M2s[v], s);
+}
+
+// Sigma^k(tau_i) (+)= alpha X_k^H D[k]^T X_k for every k (D FP64 [k][N][ldN])
+void backproject_k(const z *D, const z *X, const KTc &g, z *T1, z *Sig_i, long long sS, double alpha, double beta,
+                   cudaStream_t s) {
+  ZGemm t = zg();
+  t.M = g.N; t.Nc = g.n; t.K = g.N; t.batch = g.nk;
+  t.A = D; t.sA = (long long)g.N * g.ldN; t.ai = 1; t.ak = g.ldN;
+  t.B = X; t.sB = g.Nn; t.bk = g.n; t.bj = 1;
+  t.C = T1; t.sC = g.Nn; t.ci = g.n; t.cj = 1;
+  zgemm(t, s);
+  ZGemm o = zg();
+  o.M = g.n; o.Nc = g.n; o.K = g.N; o.batch = g.nk;
+  o.A = X; o.sA = g.Nn; o.ai = 1; o.ak = g.n; o.conjA = 1;
+  o.B = T1; o.sB = g.Nn; o.bk = g.n; o.bj = 1;
+  o.C = Sig_i; o.sC = sS; o.ci = g.n; o.cj = 1;
+  o.alpha = alpha; o.beta = beta;
+  zgemm(o, s);
+}
+
+}  // namespace
+
+size_t kpoint_tc_bytes(sox_handle, const sox_problem *p, bool two) {
+  const KTc g = ktc_geom(p);
+  size_t b = tables_bytes(g) + mixed_tc_bytes(g) * (two ? 2 : 1) + mixed_tc_scratch(g);
+  b += csplit_bytes((int)g.nk2, (int)g.Nn, g.n) + (size_t)g.n * csplit_bytes((int)g.nk2, 2 * g.N, g.n);
+  b += 2 * aligned_bytes(g.nk * g.Nn, 16);
+  b += csplit_bytes(g.nk, 2 * g.N, g.n) + csplit_bytes(g.nk, g.N, g.n) + csplit_bytes(g.nk, 2 * g.n, g.n);
+  b += aligned_bytes(g.nk2 * g.Nn * g.vpad, 8) + csplit_bytes((int)g.nk2, g.N, g.n);
+  b += 2 * aligned_bytes(g.nk2 * g.N * g.ldN, 8);
+  b += aligned_bytes((size_t)g.nk * g.N * g.ldN, 16) + aligned_bytes(g.nk * g.Nn, 16);
+  return b + (1 << 20);
+}
+
+Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, const double *Xd, const double *U1d,
+                       const double *U2d, double *Sd, Arena &ar, cudaStream_t s) {
+  const KTc g = ktc_geom(pr);
+  const bool two = (U1d != U2d);
+  const z *G = reinterpret_cast<const z *>(Gd);
+  const z *X = reinterpret_cast<const z *>(Xd);
+  const z *U1 = reinterpret_cast<const z *>(U1d);
+  const z *U2 = reinterpret_cast<const z *>(U2d);
+  z *Sig = reinterpret_cast<z *>(Sd);
+  KTables tb;
+  SOX_TRY(ktc_tables(pr, g, ar, s, &tb));
+  const size_t mfl = 2 * (size_t)g.nk2 * g.N * nnpad_of(g);
+  float *M1 = ar.take<float>(mfl);
+  float *M2 = two ? ar.take<float>(mfl) : M1;
+  CSplit M1s = csplit_take(ar, (int)g.nk2, (int)g.Nn, g.n);
+  std::vector<CSplit> M2s(g.n);
+  for (int v = 0; v < g.n; ++v) M2s[v] = csplit_take(ar, (int)g.nk2, 2 * g.N, g.n);
+  z *GR = ar.take<z>(g.nk * g.Nn), *GWt = ar.take<z>(g.nk * g.Nn);
+  CSplit GRs = csplit_take(ar, g.nk, 2 * g.N, g.n), GWts = csplit_take(ar, g.nk, g.N, g.n);
+  CSplit Gms = csplit_take(ar, g.nk, 2 * g.n, g.n);
+  float *Aall = ar.take<float>(2 * g.nk2 * g.Nn * g.vpad);
+  CSplit As = csplit_take(ar, (int)g.nk2, g.N, g.n);
+  float *Ball = ar.take<float>(2 * g.nk2 * g.N * g.ldN), *Call = ar.take<float>(2 * g.nk2 * g.N * g.ldN);
+  z *D = ar.take<z>((size_t)g.nk * g.N * g.ldN), *T1 = ar.take<z>(g.nk * g.Nn);
+  if (!T1 || !As.hi || !M1s.hi || !M2s.back().hi || !Gms.hi)
+    return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  ProfScope ps(h, "kpoint_tc", s, 0);
+  SOX_CUDA_TRY(cudaMemsetAsync(Ball, 0, 8 * g.nk2 * g.N * g.ldN, s));   // pad columns stay zero
+  SOX_CUDA_TRY(cudaMemsetAsync(Call, 0, 8 * g.nk2 * g.N * g.ldN, s));
+  SOX_TRY(mixed_tc(h, X, U1, tb, g, ar, M1, s));
+  if (two) SOX_TRY(mixed_tc(h, X, U2, tb, g, ar, M2, s));
+  split_m1_tc(M1, g, M1s, s);
+  split_m2_tc(M2, g, M2s, s);
+  long long launches = 1 + g.n;
+  const double inv_nk2 = 1.0 / (double)g.nk2;
+  for (int sp = 0; sp < g.S; ++sp) {
+    const z *Gs = G + (long long)sp * g.nk * g.T * g.nn;
+    for (int j = 0; j < g.T; ++j) {
+      {  // FP64 projections at tau_j for every k
+        ZGemm p = zg();
+        p.M = g.N; p.Nc = g.n; p.K = g.n; p.batch = g.nk;
+        p.A = X; p.sA = g.Nn; p.ai = g.n; p.ak = 1;
+        p.B = Gs + (long long)j * g.nn; p.sB = (long long)g.T * g.nn; p.bk = g.n; p.bj = 1;
+        p.C = GR; p.sC = g.Nn; p.ci = g.n; p.cj = 1;
+        zgemm(p, s);
+        ZGemm w = p;
+        w.conjA = 1; w.bk = 1; w.bj = g.n; w.C = GWt;
+        zgemm(w, s);
+      }
+      csplit_b(GR, false, g.Nn, g.n, 0, 0, 1, g.nk, g.N, g.n, false, false, GRs, s);
+      csplit_a(GWt, false, g.Nn, g.n, 0, 0, 1, g.nk, g.N, g.n, GWts, s);
+      // B rows v of G(-tau_j)^T: element (v, s) = G^k(tau_{T-1-j})[s][v]; the sign goes into alpha
+      csplit_b(Gs + (long long)(g.T - 1 - j) * g.nn, false, (long long)g.T * g.nn, 1, 0, 0, g.n, g.nk, g.n, g.n,
+               false, false, Gms, s);
+      // A^{q1,ks}[(P,q)][v] = -sum_s M1[(P,q)][s] G^{ks}(tau_{T-1-j})[s][v]
+      SOX_TRY(cgemm_tc(h, M1s, Gms, (int)g.nk2, nullptr, tb.kk, -1.f, Aall, 2LL * g.vpad, 2LL * g.Nn * g.vpad, s));
+      SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)g.nk * g.N * g.ldN, s));
+      launches += 5;
+      for (int v = 0; v < g.n; ++v) {
+        csplit_a(reinterpret_cast<const float2 *>(Aall) + v, true, g.Nn * g.vpad, (long long)g.n * g.vpad, 0, 0,
+                 g.vpad, (int)g.nk2, g.N, g.n, As, s);
+        // B^{q1,ks}_v[P][R] = sum_q A[v][P][q] GR^{ks-q1}[R][q]
+        SOX_TRY(cgemm_tc(h, As, GRs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
+        // C^{q2,kw}_v[P][R] = sum_w GWt^{kw}[P][w] M2^{q2,kw}[R][v][w]
+        SOX_TRY(cgemm_tc(h, GWts, M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
+        SOX_TRY(kpoint_D_f32(Ball, Call, (long long)g.N * g.ldN, 0, tb.add, tb.sub, g.nk, (long long)g.N * g.ldN, 1,
+                             0, 0, reinterpret_cast<double *>(D), s));
+        launches += 2;
+      }
+      backproject_k(D, X, g, T1, Sig + ((long long)sp * g.nk * g.T + j) * g.nn, (long long)g.T * g.nn, -inv_nk2, 0.0,
+                    s);
+      launches += 4;
+    }
+  }
+  h->launches += launches;
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+namespace {
+
+struct KDynTc {
+  KTc g;
+  int nO, ct, upad;
+  long long ldNn;   // complex row length of GG(i Omega) and of A(tau) rows: N n rounded up to even
+};
+
+KDynTc kdyn_geom(sox_handle h, const sox_problem *p, int nO, size_t *fixed_out, size_t *per_t_out) {
+  KDynTc d;
+  d.g = ktc_geom(p);
+  const KTc &g = d.g;
+  d.nO = nO;
+  d.upad = g.n + (g.n & 1);
+  d.ldNn = g.Nn + (g.Nn & 1);
+  size_t f = tables_bytes(g) + aligned_bytes((size_t)g.nk2 * nO, 4);
+  f += mixed_tc_bytes(g) + mixed_tc_scratch(g);                                 // M2 (FP32) and its scratch
+  f += (size_t)g.n * csplit_bytes((int)g.nk2, 2 * g.N, g.n);                    // M2 split per v
+  f += csplit_bytes(g.nk, 2 * g.N, g.n);                                        // X split
+  f += csplit_bytes(g.nk * nO, g.N, g.N);                                       // W_d split
+  f += csplit_bytes(1, nO, g.T) + csplit_bytes(1, g.T, nO);                     // transforms
+  f += 3 * aligned_bytes((size_t)g.nk * g.T * g.Nn, 16);                        // GR, GWt, GG (FP64)
+  f += csplit_bytes(g.nk, g.T * g.N, g.n);                                      // GWt split, all tau
+  f += csplit_bytes(g.nk, (int)(2 * g.Nn), g.T);                                // GG split
+  f += aligned_bytes((size_t)g.nk * nO * d.ldNn, 8);                            // GG(i Omega)
+  f += csplit_bytes(g.nk * nO, 2 * g.n, g.N);                                   // its split
+  f += aligned_bytes((size_t)g.nk * nO * g.N * d.upad, 8);                      // W_d GG
+  f += csplit_bytes(g.nk, (int)(2 * g.Nn), nO);                                 // its split
+  f += aligned_bytes((size_t)g.nk2 * g.T * d.ldNn, 8);                          // A(tau), all pairs
+  f += aligned_bytes((size_t)g.T * g.nk * g.N * g.ldN, 16);                     // D for every tau
+  f += aligned_bytes(g.nk * g.Nn, 16) + (1 << 20);
+  const size_t per_t = csplit_bytes((int)g.nk2, g.N, g.n) + 2 * aligned_bytes(g.nk2 * g.N * g.ldN, 8);
+  const size_t budget = chunk_budget(h, size_t(24) << 30);
+  long long ct = budget > f ? (long long)((budget - f) / per_t) : 1;
+  d.ct = (int)std::max<long long>(1, std::min<long long>(ct, g.T));
+  if (fixed_out) *fixed_out = f;
+  if (per_t_out) *per_t_out = per_t;
+  return d;
+}
+
+}  // namespace
+
+size_t kpoint_dynamic_tc_bytes(sox_handle h, const sox_problem *p, int n_omega) {
+  size_t f = 0, per_t = 0;
+  const KDynTc d = kdyn_geom(h, p, n_omega, &f, &per_t);
+  return f + per_t * d.ct + (1 << 20);
+}
+
+Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const double *Gd, const double *Xd,
+                         const double *Vd, const double *Wdd, const double *Tfd, const double *Tid, double *Sd,
+                         Arena &ar, cudaStream_t s) {
+  const KDynTc d = kdyn_geom(h, pr, n_omega, nullptr, nullptr);
+  const KTc &g = d.g;
+  const int nO = d.nO, T = g.T, n = g.n, N = g.N, nk = g.nk;
+  const z *G = reinterpret_cast<const z *>(Gd);
+  const z *X = reinterpret_cast<const z *>(Xd);
+  const z *V = reinterpret_cast<const z *>(Vd);
+  z *Sig = reinterpret_cast<z *>(Sd);
+  KTables tb;
+  SOX_TRY(ktc_tables(pr, g, ar, s, &tb));
+  int *widx = ar.take<int>((size_t)g.nk2 * nO);
+  float *M2 = ar.take<float>(2 * (size_t)g.nk2 * N * nnpad_of(g));
+  std::vector<CSplit> M2s(n);
+  for (int v = 0; v < n; ++v) M2s[v] = csplit_take(ar, (int)g.nk2, 2 * N, n);
+  CSplit Xs = csplit_take(ar, nk, 2 * N, n);
+  CSplit Wds = csplit_take(ar, nk * nO, N, N);
+  CSplit Tfs = csplit_take(ar, 1, nO, T), Tis = csplit_take(ar, 1, T, nO);
+  z *GR = ar.take<z>((size_t)nk * T * g.Nn), *GWt = ar.take<z>((size_t)nk * T * g.Nn);
+  z *GG = ar.take<z>((size_t)nk * T * g.Nn);
+  CSplit GWts = csplit_take(ar, nk, T * N, n);
+  CSplit GGs = csplit_take(ar, nk, (int)(2 * g.Nn), T);
+  float *GGw = ar.take<float>(2 * (size_t)nk * nO * d.ldNn);
+  CSplit GGws = csplit_take(ar, nk * nO, 2 * n, N);
+  float *Aw = ar.take<float>(2 * (size_t)nk * nO * N * d.upad);
+  CSplit Aws = csplit_take(ar, nk, (int)(2 * g.Nn), nO);
+  float *Adyn = ar.take<float>(2 * (size_t)g.nk2 * T * d.ldNn);
+  z *Dall = ar.take<z>((size_t)T * nk * N * g.ldN), *T1 = ar.take<z>(g.nk * g.Nn);
+  CSplit As = csplit_take(ar, (int)g.nk2, d.ct * N, n);
+  float *Ball = ar.take<float>(2 * (size_t)g.nk2 * d.ct * N * g.ldN);
+  float *Call = ar.take<float>(2 * (size_t)g.nk2 * d.ct * N * g.ldN);
+  if (!Call || !As.hi || !Aws.hi || !GGws.hi || !GWts.hi || !Tis.hi || !M2s.back().hi)
+    return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  {
+    std::vector<int> hw((size_t)g.nk2 * nO);
+    for (int q = 0; q < nk; ++q)
+      for (int ks = 0; ks < nk; ++ks)
+        for (int m = 0; m < nO; ++m) hw[((size_t)q * nk + ks) * nO + m] = q * nO + m;
+    SOX_CUDA_TRY(cudaMemcpyAsync(widx, hw.data(), 4 * hw.size(), cudaMemcpyHostToDevice, s));
+  }
+  ProfScope ps(h, "kpoint_dynamic_tc", s, 0);
+  long long launches = 0;
+  SOX_CUDA_TRY(cudaMemsetAsync(Ball, 0, 8 * (size_t)g.nk2 * d.ct * N * g.ldN, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(Call, 0, 8 * (size_t)g.nk2 * d.ct * N * g.ldN, s));
+  SOX_TRY(mixed_tc(h, X, V, tb, g, ar, M2, s));
+  split_m2_tc(M2, g, M2s, s);
+  csplit_b(X, false, g.Nn, n, 0, 0, 1, nk, N, n, false, false, Xs, s);
+  csplit_a(Wdd, false, g.NN, N, 0, 0, 1, nk * nO, N, N, Wds, s);
+  csplit_a(Tfd, false, 0, T, 0, 0, 1, 1, nO, T, Tfs, s);
+  csplit_a(Tid, false, 0, nO, 0, 0, 1, 1, T, nO, Tis, s);
+  launches += n + 4;
+  const double inv_nk2 = 1.0 / (double)g.nk2;
+  for (int sp = 0; sp < g.S; ++sp) {
+    const z *Gs = G + (long long)sp * nk * T * g.nn;
+    for (int k = 0; k < nk; ++k) {  // GWt[k][j][Q][u], GR[k][j][Q][v] for every tau, FP64
+      ZGemm p = zg();
+      p.M = N; p.Nc = n; p.K = n; p.batch = T;
+      p.A = X + (long long)k * g.Nn; p.ai = n; p.ak = 1; p.conjA = 1;
+      p.B = Gs + (long long)k * T * g.nn; p.sB = g.nn; p.bk = 1; p.bj = n;
+      p.C = GWt + (long long)k * T * g.Nn; p.sC = g.Nn; p.ci = n; p.cj = 1;
+      zgemm(p, s);
+      ZGemm r = p;
+      r.conjA = 0; r.bk = n; r.bj = 1; r.C = GR + (long long)k * T * g.Nn;
+      zgemm(r, s);
+      launches += 2;
+    }
+    // rows (tau_i, P) of GWt^k, K = w
+    csplit_a(GWt, false, (long long)T * g.Nn, n, 0, 0, 1, nk, T * N, n, GWts, s);
+    SOX_CUDA_TRY(cudaMemsetAsync(Dall, 0, 16 * (size_t)T * nk * N * g.ldN, s));
+    ++launches;
+    for (int v = 0; v < n; ++v) {
+      for (int q1 = 0; q1 < nk; ++q1) {
+        k_gg_k<<<grid1((long long)nk * T * g.Nn), 256, 0, s>>>(GWt, GR, tb.sub, nk, q1, T, N, n, v, GG);
+        // B rows (Q,u) of GG^{ks}, K = tau_j
+        csplit_b(GG, false, (long long)T * g.Nn, 1, 0, 0, g.Nn, nk, (int)g.Nn, T, false, false, GGs, s);
+        // GG(i Omega_m)[ks][(Q,u)] = sum_j T_fwd[m][j] GG[ks][j][(Q,u)]
+        SOX_TRY(cgemm_tc(h, Tfs, GGs, nk, nullptr, nullptr, 1.f, GGw, 2 * d.ldNn, 2LL * nO * d.ldNn, s));
+        // B rows u of GG(i Omega_m)^{ks}, K = Q
+        csplit_b(reinterpret_cast<const float2 *>(GGw), true, d.ldNn, 1, 0, 0, n, nk * nO, n, N, false, false, GGws,
+                 s);
+        // (W_d GG)[(ks,m)][P][u] = sum_Q W_d^{q1}(i Omega_m)[P][Q] GG(i Omega_m)[ks][Q][u]
+        SOX_TRY(cgemm_tc(h, Wds, GGws, nk * nO, widx + (size_t)q1 * nk * nO, nullptr, 1.f, Aw, 2LL * d.upad,
+                         2LL * N * d.upad, s));
+        // B rows (P,u) of W_d GG, K = Omega_m
+        csplit_b(reinterpret_cast<const float2 *>(Aw), true, (long long)nO * N * d.upad, d.upad, 1, n,
+                 (long long)N * d.upad, nk, (int)g.Nn, nO, false, false, Aws, s);
+        // A^{q1,ks}(tau_i)[(P,u)] = sum_m T_inv[i][m] (W_d GG)[ks][m][(P,u)]
+        SOX_TRY(cgemm_tc(h, Tis, Aws, nk, nullptr, nullptr, 1.f, Adyn + 2 * (size_t)q1 * nk * T * d.ldNn,
+                         2 * d.ldNn, 2LL * T * d.ldNn, s));
+        launches += 4;
+      }
+      for (int i0 = 0; i0 < T; i0 += d.ct) {
+        const int cc = std::min(d.ct, T - i0);
+        CSplit Ac = As;
+        Ac.rows = cc * N;
+        // rows (il, P) of A^{pair}(tau_{i0+il}), K = u
+        csplit_a(reinterpret_cast<const float2 *>(Adyn) + (size_t)i0 * d.ldNn, true, (long long)T * d.ldNn, d.ldNn, n,
+                 N, 1, (int)g.nk2, cc * N, n, Ac, s);
+        // B^{q1,ks}(tau_i)[P][R] = sum_u A[P][u] X^{ks-q1}[R][u]
+        SOX_TRY(cgemm_tc(h, Ac, Xs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * cc * N * g.ldN, s));
+        // C^{q2,kw}(tau_i)[P][R] = sum_w GWt^{kw}(tau_i)[P][w] M2^{q2,kw}[R][v][w]
+        SOX_TRY(cgemm_tc(h, GWts.view((long long)i0 * N, cc * N), M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call,
+                         2LL * g.ldN, 2LL * cc * N * g.ldN, s));
+        SOX_TRY(kpoint_D_f32(Ball, Call, (long long)cc * N * g.ldN, (long long)N * g.ldN, tb.add, tb.sub, nk,
+                             (long long)N * g.ldN, cc, i0, (long long)nk * N * g.ldN,
+                             reinterpret_cast<double *>(Dall), s));
+        launches += 2;
+      }
+    }
+    for (int i = 0; i < T; ++i) {
+      backproject_k(Dall + (size_t)i * nk * N * g.ldN, X, g, T1, Sig + ((long long)sp * nk * T + i) * g.nn,
+                    (long long)T * g.nn, -inv_nk2, 1.0, s);
       launches += 2;
     }
   }

@@ -16,6 +16,11 @@ using tc::smem_u32;
 
 bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                       uint32_t box0, uint32_t box1, std::string *err) {
+  return make_tmap_f16_3d_bs(map, base, d0, d1, d2, d0 * d1, box0, box1, err);
+}
+
+bool make_tmap_f16_3d_bs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                         uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -29,7 +34,7 @@ bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t 
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   cuuint64_t dims[3] = {d0, d1, d2};
-  cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  cuuint64_t strides[2] = {d0 * 2, batch_stride * 2};
   cuuint32_t box[3] = {box0, box1, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims, strides, box,
@@ -549,7 +554,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int b = (int)(t / per_b);
         const long long r = t % per_b;
         const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
-        const int za = a.batchA_shared ? 0 : b, zb = a.batchB_shared ? 0 : b;
+        const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
+        const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = (int)(it % kGStages);
           const uint32_t ph = (uint32_t)((it / kGStages) & 1);
@@ -614,6 +620,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       tc::tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 128 + h * 64;
       const bool row_ok = (i0 + row) < a.M;
+      if (a.mode == kStoreF32) {
+        // scaled FP32 tile through shared memory (16-byte chunks XOR-swizzled by row), then
+        // written row by row with coalesced 16-byte stores
+        const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
+        const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
+        const float rsc = a.alpha * ((a.row_scale && row_ok) ? a.row_scale[za * a.rs_b + i0 + row] : 1.f);
+        float *tile = reinterpret_cast<float *>(stage_out);
+        epi_sync();   // the previous tile's copy-out has finished reading the staging buffer
+#pragma unroll
+        for (int c = 0; c < 64; c += 32) {
+          float v[32];
+          tc::tmem_ld_32x32b_x32(base + c, v);
+          tc::tmem_ld_wait();
+          if (c == 32) {
+            tc::tc_fence_before();
+            tc::mbar_arrive(&bar->acc_empty[buf]);
+          }
+          const int col0 = j0 + h * 64 + c;
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const float cs = (a.col_scale && col0 + jj < a.Ncols) ? a.col_scale[zb * a.cs_b + col0 + jj] : 1.f;
+            v[jj] *= rsc * cs;
+          }
+#pragma unroll
+          for (int t4 = 0; t4 < 8; ++t4) {
+            const int chunk = (h * 64 + c) / 4 + t4;
+            const int pc = chunk ^ (row & 31);
+            *reinterpret_cast<float4 *>(tile + row * 128 + pc * 4) =
+                make_float4(v[4 * t4], v[4 * t4 + 1], v[4 * t4 + 2], v[4 * t4 + 3]);
+          }
+        }
+        epi_sync();
+        for (int rr = warp - 2; rr < kTile; rr += 8) {
+          const int gi = i0 + rr;
+          if (gi >= a.M) break;
+          const int pc = lane ^ (rr & 31);
+          const float4 val = *reinterpret_cast<const float4 *>(tile + rr * 128 + pc * 4);
+          const int gj = j0 + 4 * lane;
+          float *dst = a.Cf + (long long)b * a.sCb + (long long)gi * a.ldc + gj;
+          if (gj + 3 < a.Ncols) {
+            *reinterpret_cast<float4 *>(dst) = val;
+          } else {
+            if (gj < a.Ncols) dst[0] = val.x;
+            if (gj + 1 < a.Ncols) dst[1] = val.y;
+            if (gj + 2 < a.Ncols) dst[2] = val.z;
+          }
+        }
+        continue;
+      }
       // this half's columns belong to group g (groups are 64 or 128 columns wide)
       const int g = (h * 64) >= a.group ? 1 : 0;
       float sc = 1.f;

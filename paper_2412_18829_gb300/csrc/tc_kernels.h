@@ -9,7 +9,7 @@
 
 namespace sox {
 
-enum { kStoreSplit = 1, kStoreSplitGroup = 2 };
+enum { kStoreSplit = 1, kStoreSplitGroup = 2, kStoreF32 = 3 };
 
 struct BcdArgs {
   int n = 0, N = 0, Kp = 0, batch = 0;
@@ -33,12 +33,25 @@ struct GemmTcArgs {
   // group_scale[b][group index]
   int group = 128, n_groups = 0;
   float *group_scale = nullptr;
+  // kStoreF32: Cf[b * sCb + i * ldc + j] = alpha * acc(i, j) * row_scale[zA * rs_b + i] * col_scale[zB * cs_b + j]
+  // (either scale may be NULL); rows >= M and columns >= Ncols are not written.  Cf 16-byte
+  // aligned, ldc and sCb multiples of 4.
+  float *Cf = nullptr;
+  long long ldc = 0, sCb = 0;
+  float alpha = 1.f;
+  const float *row_scale = nullptr, *col_scale = nullptr;
+  long long rs_b = 0, cs_b = 0;
+  // batch coordinate of the A / B operand for output batch b (overrides batch*_shared)
+  const int *idxA = nullptr, *idxB = nullptr;
   long long spin_limit = 0;
   int *status = nullptr;
 };
 
 bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                       uint32_t box0, uint32_t box1, std::string *err);
+// the same with `batch_stride` elements between consecutive d2 slices (a multiple of 8)
+bool make_tmap_f16_3d_bs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                         uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err);
 size_t tc_smem_bytes();
 bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
                            uint64_t batch, std::string *err);

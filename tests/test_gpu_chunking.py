@@ -63,7 +63,8 @@ def test_solid_static_one_v_per_chunk(env):
     assert np.abs(S.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_solid_dynamic_one_tau_per_chunk(env):
+@pytest.mark.parametrize("prec", ["fp64", "f16x2"])
+def test_solid_dynamic_one_tau_per_chunk(env, prec):
     torch, pkg, hs = env
     w = synth.solid(74, (1, 2, 1), 4, 9, 5, 10.0)
     _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, 2)
@@ -71,10 +72,10 @@ def test_solid_dynamic_one_tau_per_chunk(env):
     p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta, nk=w.nk, dtype=1)
     G, X, V, W, F, I = to_dev(torch, w.G, w.X, w.V, Wd, Tf, Ti)
     S = torch.full_like(G, complex("nan"))
-    pkg.sosex_dynamic_sigma(hs[("fp64", 1)], p, G, X, V, W, F, I, Tf.shape[0], S)
-    pkg.sox_check_device(hs[("fp64", 1)])
+    pkg.sosex_dynamic_sigma(hs[(prec, 1)], p, G, X, V, W, F, I, Tf.shape[0], S)
+    pkg.sox_check_device(hs[(prec, 1)])
     ref = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, w.G, w.nk)
-    assert np.abs(S.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    check(S.cpu().numpy(), ref, prec, "solid dynamic, one tau per chunk")
 
 
 def test_negative_workspace_limit_is_rejected(env):
