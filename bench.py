@@ -222,6 +222,7 @@ def _alu_peak(achieved, what):
 
 
 FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 78.4
 
 
 class MoleculeCase(Case):
@@ -328,15 +329,17 @@ def _zflops(*cmacs):
 
 
 class SolidCase(Case):
-    """Dynamically screened SOSEX of a solid (c3), FP64 complex: SOX(v, v) + Sigma_d."""
+    """Dynamically screened SOSEX of a solid (c3): SOX(v, v) + Sigma_d, split precision on the
+    tensor cores (complex FP16 pairs, FP32 accumulation, FP64 ends) or FP64 complex."""
 
-    def __init__(self, torch, pkg, w, dev, stream):
+    def __init__(self, torch, pkg, w, prec, dev, stream):
         import synth
 
         self.torch, self.pkg, self.w, self.dev, self.stream = torch, pkg, w, dev, stream
+        self.prec = prec
         self.name = w.name
-        self.dtype = "c128"
-        self.hot = "kpoint_dynamic_f64"
+        self.dtype = "cf16x2+f32acc,c128" if prec == "f16x2" else "c128"
+        self.hot = "kpoint_D" if prec == "f16x2" else "kpoint_dynamic_f64"
         self.units = 1.0
         self.cpu_points_per_build = w.n_tau * w.n_spin
         M = (w.n_tau - 1) // 2
@@ -348,9 +351,9 @@ class SolidCase(Case):
         self.G, self.X, self.V, self.Wd, self.Tf, self.Ti = (to(a) for a in (w.G, w.X, w.V, Wd, Tf, Ti))
         self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
         self.S = torch.empty_like(self.G)
-        self.h = pkg.Handle("fp64", device=dev.index or 0)
+        self.h = pkg.Handle(prec, device=dev.index or 0)
         self.config = {"workload": w.name, "nk": list(w.nk), "n": w.n, "N": w.N, "n_tau": w.n_tau,
-                       "n_omega": self.nO, "beta": w.beta, "precision": "fp64 complex",
+                       "n_omega": self.nO, "beta": w.beta, "precision": prec,
                        "W_d": "synthetic single-pole form (synth.pole_screening), input",
                        "step": "SOX(v, v) + dynamically screened Sigma_d through the C ABI"}
 
@@ -380,7 +383,28 @@ class SolidCase(Case):
         return _zflops(static), _zflops(dyn)
 
     def hot_flops_per_step(self):
+        if self.prec == "f16x2":   # the n_k^3 D step, static and dynamic parts: 8 flops per complex MAC
+            w = self.w
+            nk = w.nk[0] * w.nk[1] * w.nk[2]
+            return 2 * _zflops(nk ** 3 * w.N * w.N * w.n * w.n_tau * w.n_spin)
         return self.phase_flops()[1]
+
+    def fp64_compare(self, value: float) -> dict:
+        if self.prec == "fp64":
+            return {}
+        torch = self.torch
+        with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
+            S64 = torch.empty_like(self.S)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            self.pkg.sosex_dynamic_sigma(h64, self.p, self.G, self.X, self.V, self.Wd, self.Tf, self.Ti, self.nO, S64,
+                                         self.stream)
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b) / 1e3
+            return {"fp64_gpu_builds_per_s": 1.0 / t64, "speedup_vs_fp64_gpu": value * t64,
+                    "max_abs_err_Ha_vs_fp64_gpu_all_points": float((self.S - S64).abs().max().item()),
+                    "max_abs_sigma_Ha": float(S64.abs().max().item())}
 
 
 class BatchCase(Case):
@@ -510,7 +534,7 @@ def make_case(args, torch, pkg, dev, stream, rank, world):
         return BatchCase(torch, pkg, args.precision, dev, stream, rank, world)
     w = workload(args.workload)
     if args.workload == "c3":
-        return SolidCase(torch, pkg, w, dev, stream)
+        return SolidCase(torch, pkg, w, args.precision, dev, stream)
     return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"))
 
 
@@ -557,7 +581,8 @@ def run_ours(args):
     hot_n, hot_ms = pkg.sox_profile_read(case.h, case.hot)
     phases = {}
     if isinstance(case, SolidCase):
-        phases["kpoint_f64"] = pkg.sox_profile_read(case.h, "kpoint_f64")
+        for ph in (("kpoint_tc", "kpoint_dynamic_tc") if case.prec == "f16x2" else ("kpoint_f64", "kpoint_dynamic_f64")):
+            phases[ph] = pkg.sox_profile_read(case.h, ph)
     pkg.sox_profile_enable(case.h, False)
     clocks = sampler.stop()
     if dist:
@@ -597,7 +622,17 @@ def run_ours(args):
     pk, pk_src = peaks()
     hot_s = hot_ms / 1e3
     achieved = case.hot_flops_per_step() * args.steps / hot_s / 1e12 if hot_n and hot_s > 0 else None
-    if isinstance(case, SolidCase):
+    if isinstance(case, SolidCase) and case.prec == "f16x2":
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None, "kernel": "k_kpoint_D_reg",
+                "peak_source": "measured FP32 FMA rate (paper_2412_18829_gb300/probes/fp_rate.cu)",
+                "note": "the n_k^3 D step (FP32 complex products, FP64 accumulation over v), static and dynamic "
+                        "parts; 8 flops per complex MAC"}
+        f_static, f_dyn = case.phase_flops()
+        extra["phase_ms_per_step"] = {k: v[1] / args.steps for k, v in phases.items()}
+        extra["phase_ms_per_step"]["kpoint_D"] = hot_ms / args.steps
+        extra["algorithmic_tflops_per_s"] = (f_static + f_dyn) * value / 1e12
+    elif isinstance(case, SolidCase):
         f_static, f_dyn = case.phase_flops()
         roof = _alu_peak(achieved, "dominant phase: the dynamic part (GG, transforms, W_d product, B/C, "
                                    "n_k^3 D step) in FP64 complex on CUDA cores; algorithmic flops at 8 per complex MAC")

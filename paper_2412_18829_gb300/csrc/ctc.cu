@@ -37,6 +37,48 @@ __device__ __forceinline__ void split_pair(double x, float s, __half &h, __half 
   l = __float2half_rn((float)(xs - (double)__half2float(h)));
 }
 
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Eight FP16 pairs (4 complex values, interleaved) of an A row -> one 16-byte store each
+// for hi and lo.  v[j] are the complex values k0..k0+3 (zero beyond K).
+__device__ __forceinline__ void store8_a(const double2 *v, float s, __half *h, __half *l) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __half a0, d0, a1, d1;
+    split_pair(v[j].x, s, a0, d0);
+    split_pair(v[j].y, s, a1, d1);
+    ph[j] = pack_h2(a0, a1);
+    pl[j] = pack_h2(d0, d1);
+  }
+  *reinterpret_cast<uint4 *>(h) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  *reinterpret_cast<uint4 *>(l) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+}
+
+// The same for the re-row and im-row of a B row: re (b_r, -sa sb b_i), im (sb b_i, sa b_r).
+__device__ __forceinline__ void store8_b(const double2 *v, float s, float sa, float sbc, __half *h0, __half *l0,
+                                         __half *h1, __half *l1) {
+  uint32_t p0[4], q0[4], p1[4], q1[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __half a, b, c, d;
+    split_pair(v[j].x, s, a, b);
+    split_pair(-(double)(sa * sbc) * v[j].y, s, c, d);
+    p0[j] = pack_h2(a, c);
+    q0[j] = pack_h2(b, d);
+    split_pair((double)sbc * v[j].y, s, a, b);
+    split_pair((double)sa * v[j].x, s, c, d);
+    p1[j] = pack_h2(a, c);
+    q1[j] = pack_h2(b, d);
+  }
+  *reinterpret_cast<uint4 *>(h0) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+  *reinterpret_cast<uint4 *>(l0) = make_uint4(q0[0], q0[1], q0[2], q0[3]);
+  *reinterpret_cast<uint4 *>(h1) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+  *reinterpret_cast<uint4 *>(l1) = make_uint4(q1[0], q1[1], q1[2], q1[3]);
+}
+
 // Row r of batch b starts at src + b*sb + (r / R2)*sr1 + (r % R2)*sr2; its k-th complex
 // element is k*sk further (all in complex elements).
 struct RowMap {
@@ -47,75 +89,85 @@ struct RowMap {
   }
 };
 
-// A operand: one warp per complex row -> one real row of 2K interleaved values.
+// Lanes per row (a power of two dividing 32): a row of Kp2 halves is Kp2/8 16-byte
+// chunks; short rows share a warp.
+__host__ __device__ __forceinline__ int lanes_per_row(int Kp2) { return Kp2 >= 256 ? 32 : (Kp2 >= 128 ? 16 : 8); }
+
+__device__ __forceinline__ float group_max(float v, int lpr) {
+  for (int o = lpr / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// A operand: LPR lanes per complex row -> one real row of 2K interleaved values.
 template <class T>
 __global__ void k_csplit_a(const T *src, RowMap m, int batch, int rows, int K, int Kp2, __half *hi, __half *lo,
                            float *unscale) {
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
-  if (gw >= (long long)rows * batch) return;
-  const int b = (int)(gw / rows), r = (int)(gw % rows);
+  const int lpr = lanes_per_row(Kp2);
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gr = gt / lpr;                 // row of this lane group
+  const int gl = (int)(gt % lpr);
+  const bool live = gr < (long long)rows * batch;
+  const int b = live ? (int)(gr / rows) : 0, r = live ? (int)(gr % rows) : 0;
   const T *x = src + m.row(b, r);
   float mx = 0.f;
-  for (int k = lane; k < K; k += 32) {
-    const double2 v = ld_c(x + k * m.sk);
-    mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
-  }
-  mx = cwarp_max(mx);
-  const float s = tc::pow2_floor_inv(mx);
-  __half *h = hi + gw * Kp2, *l = lo + gw * Kp2;
-  for (int c = lane; c < Kp2; c += 32) {
-    __half a = __float2half(0.f), d = __float2half(0.f);
-    const int k = c >> 1;
-    if (k < K) {
+  if (live)
+    for (int k = gl; k < K; k += lpr) {
       const double2 v = ld_c(x + k * m.sk);
-      split_pair((c & 1) ? v.y : v.x, s, a, d);
+      mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
     }
-    h[c] = a;
-    l[c] = d;
+  mx = group_max(mx, lpr);
+  if (!live) return;
+  const float s = tc::pow2_floor_inv(mx);
+  __half *h = hi + gr * Kp2, *l = lo + gr * Kp2;
+  for (int c8 = gl; c8 < Kp2 / 8; c8 += lpr) {
+    double2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = c8 * 4 + j;
+      v[j] = k < K ? ld_c(x + k * m.sk) : make_double2(0.0, 0.0);
+    }
+    store8_a(v, s, h + c8 * 8, l + c8 * 8);
   }
-  if (lane == 0) unscale[gw] = 1.f / s;
+  if (gl == 0) unscale[gr] = 1.f / s;
 }
 
-// B operand: one warp per complex row j -> real rows 2j (re-row) and 2j+1 (im-row).
+// B operand: LPR lanes per complex row j -> real rows 2j (re-row) and 2j+1 (im-row).
 template <class T>
 __global__ void k_csplit_b(const T *src, RowMap m, int batch, int cols, int K, int Kp2, float sa, float sbc,
                            __half *hi, __half *lo, float *unscale) {
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x % 32;
-  if (gw >= (long long)cols * batch) return;
-  const int b = (int)(gw / cols), j = (int)(gw % cols);
+  const int lpr = lanes_per_row(Kp2);
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gr = gt / lpr;
+  const int gl = (int)(gt % lpr);
+  const bool live = gr < (long long)cols * batch;
+  const int b = live ? (int)(gr / cols) : 0, j = live ? (int)(gr % cols) : 0;
   const T *x = src + m.row(b, j);
   float mx = 0.f;
-  for (int k = lane; k < K; k += 32) {
-    const double2 v = ld_c(x + k * m.sk);
-    mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
-  }
-  mx = cwarp_max(mx);
+  if (live)
+    for (int k = gl; k < K; k += lpr) {
+      const double2 v = ld_c(x + k * m.sk);
+      mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
+    }
+  mx = group_max(mx, lpr);
+  if (!live) return;
   const float s = tc::pow2_floor_inv(mx);
-  const long long r0 = ((long long)b * cols + j) * 2;
+  const long long r0 = gr * 2;
   __half *h0 = hi + r0 * Kp2, *l0 = lo + r0 * Kp2;
   __half *h1 = h0 + Kp2, *l1 = l0 + Kp2;
-  for (int c = lane; c < Kp2; c += 32) {
-    __half a0 = __float2half(0.f), d0 = __float2half(0.f), a1 = __float2half(0.f), d1 = __float2half(0.f);
-    const int k = c >> 1;
-    if (k < K) {
-      const double2 v = ld_c(x + k * m.sk);
-      const double re = (c & 1) ? -(double)(sa * sbc) * v.y : v.x;
-      const double im = (c & 1) ? (double)sa * v.x : (double)sbc * v.y;
-      split_pair(re, s, a0, d0);
-      split_pair(im, s, a1, d1);
+  for (int c8 = gl; c8 < Kp2 / 8; c8 += lpr) {
+    double2 v[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int k = c8 * 4 + jj;
+      v[jj] = k < K ? ld_c(x + k * m.sk) : make_double2(0.0, 0.0);
     }
-    h0[c] = a0;
-    l0[c] = d0;
-    h1[c] = a1;
-    l1[c] = d1;
+    store8_b(v, s, sa, sbc, h0 + c8 * 8, l0 + c8 * 8, h1 + c8 * 8, l1 + c8 * 8);
   }
-  if (lane == 0) unscale[r0] = unscale[r0 + 1] = 1.f / s;
+  if (gl == 0) unscale[r0] = unscale[r0 + 1] = 1.f / s;
 }
 
-// The n_k^3 D step on FP32 complex B and C, one tile of E consecutive (P, R) elements
-// per block with all n_k^2 pairs of both in shared memory:
+// The n_k^3 D step for any mesh (the fallback of the register forms below), one tile of E
+// consecutive (P, R) elements per block with all n_k^2 pairs of both in shared memory:
 //   D[i][k][e] += sum_{q1,q2} C[i][(q2, k+q1)][e] * B[i][(q1, k+q1-q2)][e]
 // (FP32 sum over the n_k^2 products of one v, added to the FP64 D).
 // B, C: float2, element e of pair p and chunk index il at p * sP + il * sI + e; D: double2
@@ -189,20 +241,201 @@ __global__ void k_csplit_pairs(const double2 *X, const int *sub, int nk, int N, 
   const long long r0 = gw * 2;
   __half *h0 = hi + r0 * Kp2, *l0 = lo + r0 * Kp2;
   __half *h1 = h0 + Kp2, *l1 = l0 + Kp2;
-  for (int c = lane; c < Kp2; c += 32) {
-    __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0;
-    const int Q = c >> 1;
-    if (Q < N) {
-      const double2 v = y(Q);
-      split_pair((c & 1) ? -v.y : v.x, s, a0, d0);
-      split_pair((c & 1) ? v.x : v.y, s, a1, d1);
+  for (int c8 = lane; c8 < Kp2 / 8; c8 += 32) {
+    double2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int Q = c8 * 4 + j;
+      v[j] = Q < N ? y(Q) : make_double2(0.0, 0.0);
     }
-    h0[c] = a0;
-    l0[c] = d0;
-    h1[c] = a1;
-    l1[c] = d1;
+    store8_b(v, s, 1.f, 1.f, h0 + c8 * 8, l0 + c8 * 8, h1 + c8 * 8, l1 + c8 * 8);
   }
   if (lane == 0) unscale[r0] = unscale[r0 + 1] = 1.f / s;
+}
+
+// The D step with one thread per (P, R) element and all NK accumulators in registers:
+// for every (k_s, k_w), c = C[(k_w - k_s, k_w)][e] is loaded once and multiplied with
+// B[(k_w - k, k_s)][e] for every k.  Tables in shared memory; B and C read straight from
+// global memory (coalesced along e), each B value reused from L1 NK times.
+template <int NK>
+__global__ void __launch_bounds__(128) k_kpoint_D_reg(const float2 *B, const float2 *C, long long sP, long long sI,
+                                                     const int *add, const int *sub, long long NN, int i0,
+                                                     long long sDi, double2 *D) {
+  __shared__ int s_sub[NK * NK];
+  for (int t = threadIdx.x; t < NK * NK; t += blockDim.x) s_sub[t] = sub[t];
+  __syncthreads();
+  const int il = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NN) return;
+  const float2 *Bi = B + (long long)il * sI + e, *Ci = C + (long long)il * sI + e;
+  float ar[NK], ai[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) ar[k] = ai[k] = 0.f;
+  // k_s outermost: the NK values B[(., k_s)][e] stay in L1 while k_w and k sweep them
+  for (int ks = 0; ks < NK; ++ks) {
+    for (int kw = 0; kw < NK; ++kw) {
+      const int q2 = s_sub[kw * NK + ks];
+      const float2 c = __ldg(Ci + (long long)(q2 * NK + kw) * sP);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        const int q1 = s_sub[kw * NK + k];
+        const float2 b = __ldg(Bi + (long long)(q1 * NK + ks) * sP);
+        ar[k] = fmaf(c.x, b.x, fmaf(-c.y, b.y, ar[k]));
+        ai[k] = fmaf(c.x, b.y, fmaf(c.y, b.x, ai[k]));
+      }
+    }
+  }
+  (void)add;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    double2 *d = D + (long long)(i0 + il) * sDi + (long long)k * NN + e;
+    double2 v = *d;
+    v.x += ar[k];
+    v.y += ai[k];
+    *d = v;
+  }
+}
+
+// The D step for a mesh known at compile time: with k_w and k unrolled every momentum
+// index is a constant, so the n_k values B[(., k_s)][e] sit in registers and each
+// complex product costs four FMAs and no memory access.
+template <int N1, int N2, int N3>
+struct MeshT {
+  static constexpr int NK = N1 * N2 * N3;
+  __host__ __device__ static constexpr int minus(int a, int b) {
+    return (((a / (N2 * N3)) - (b / (N2 * N3)) + N1) % N1) * N2 * N3 +
+           ((((a / N3) % N2) - ((b / N3) % N2) + N2) % N2) * N3 + (((a % N3) - (b % N3) + N3) % N3);
+  }
+};
+
+template <int N1, int N2, int N3>
+__global__ void __launch_bounds__(128) k_kpoint_D_mesh(const float2 *B, const float2 *C, long long sP, long long sI,
+                                                      long long NN, int i0, long long sDi, double2 *D) {
+  using M = MeshT<N1, N2, N3>;
+  constexpr int NK = M::NK;
+  const int il = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NN) return;
+  const float2 *Bi = B + (long long)il * sI + e, *Ci = C + (long long)il * sI + e;
+  float ar[NK], ai[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) ar[k] = ai[k] = 0.f;
+  for (int ks = 0; ks < NK; ++ks) {
+    float br[NK], bi[NK];
+#pragma unroll
+    for (int q1 = 0; q1 < NK; ++q1) {
+      const float2 b = __ldg(Bi + (long long)(q1 * NK + ks) * sP);
+      br[q1] = b.x;
+      bi[q1] = b.y;
+    }
+#pragma unroll
+    for (int kw = 0; kw < NK; ++kw) {
+      const float2 c = __ldg(Ci + (long long)(M::minus(kw, ks) * NK + kw) * sP);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        const int q1 = M::minus(kw, k);
+        ar[k] = fmaf(c.x, br[q1], fmaf(-c.y, bi[q1], ar[k]));
+        ai[k] = fmaf(c.x, bi[q1], fmaf(c.y, br[q1], ai[k]));
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    double2 *d = D + (long long)(i0 + il) * sDi + (long long)k * NN + e;
+    double2 v = *d;
+    v.x += ar[k];
+    v.y += ai[k];
+    *d = v;
+  }
+}
+
+// Split of rows that are contiguous in memory with K strided (a transposed read):
+// a block stages a tile of RB rows x K in shared memory with coalesced loads, then one
+// warp per row finds its scale and writes the FP16 pairs.  kind 0: A rows, 1: B rows.
+constexpr int kRB = 32;
+template <class T>
+__global__ void __launch_bounds__(256) k_csplit_t(const T *src, RowMap m, int batch, int rows, int K, int Kp2, int kind,
+                                                 float sa, float sbc, __half *hi, __half *lo, float *unscale) {
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  T *tile = reinterpret_cast<T *>(tile_raw);   // [K][kRB + 1]
+  const int nrb = (rows + kRB - 1) / kRB;
+  const int b = blockIdx.x / nrb, r0 = (blockIdx.x % nrb) * kRB;
+  if (b >= batch) return;
+  for (int idx = threadIdx.x; idx < K * kRB; idx += blockDim.x) {
+    const int k = idx / kRB, rr = idx % kRB;
+    T v{};
+    if (r0 + rr < rows) v = src[m.row(b, r0 + rr) + k * m.sk];
+    tile[k * (kRB + 1) + rr] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int rr = warp; rr < kRB; rr += 8) {
+    const int r = r0 + rr;
+    if (r >= rows) break;
+    float mx = 0.f;
+    for (int k = lane; k < K; k += 32) {
+      const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+      mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
+    }
+    mx = cwarp_max(mx);
+    const float s = tc::pow2_floor_inv(mx);
+    // lane pairs share a complex element (conflict-free tile reads); half2 stores
+    if (kind == 0) {
+      const long long row = (long long)b * rows + r;
+      __half2 *h = reinterpret_cast<__half2 *>(hi + row * Kp2), *l = reinterpret_cast<__half2 *>(lo + row * Kp2);
+      for (int k = lane; k < Kp2 / 2; k += 32) {
+        __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0;
+        if (k < K) {
+          const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+          split_pair(v.x, s, a0, d0);
+          split_pair(v.y, s, a1, d1);
+        }
+        h[k] = __halves2half2(a0, a1);
+        l[k] = __halves2half2(d0, d1);
+      }
+      if (lane == 0) unscale[row] = 1.f / s;
+    } else {
+      const long long row = ((long long)b * rows + r) * 2;
+      __half2 *h0 = reinterpret_cast<__half2 *>(hi + row * Kp2), *l0 = reinterpret_cast<__half2 *>(lo + row * Kp2);
+      __half2 *h1 = h0 + Kp2 / 2, *l1 = l0 + Kp2 / 2;
+      for (int k = lane; k < Kp2 / 2; k += 32) {
+        __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0, a2 = a0, d2 = a0, a3 = a0, d3 = a0;
+        if (k < K) {
+          const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+          split_pair(v.x, s, a0, d0);
+          split_pair(-(double)(sa * sbc) * v.y, s, a1, d1);
+          split_pair((double)sbc * v.y, s, a2, d2);
+          split_pair((double)sa * v.x, s, a3, d3);
+        }
+        h0[k] = __halves2half2(a0, a1);
+        l0[k] = __halves2half2(d0, d1);
+        h1[k] = __halves2half2(a2, a3);
+        l1[k] = __halves2half2(d2, d3);
+      }
+      if (lane == 0) unscale[row] = unscale[row + 1] = 1.f / s;
+    }
+  }
+}
+
+// rows contiguous along the row index and K strided: stage through shared memory
+template <class T>
+bool launch_split_t(const T *src, const RowMap &m, int batch, int rows, int K, int Kp2, int kind, float sa, float sbc,
+                    __half *hi, __half *lo, float *unscale, cudaStream_t s) {
+  const bool contiguous = (m.R2 == 1 ? m.sr1 == 1 : m.sr2 == 1);
+  if (!contiguous || m.sk == 1) return false;
+  const size_t smem = (size_t)K * (kRB + 1) * sizeof(T);
+  if (smem > 200 * 1024) return false;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_csplit_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  const long long blocks = (long long)batch * ((rows + kRB - 1) / kRB);
+  k_csplit_t<T><<<(unsigned)blocks, 256, smem, s>>>(src, m, batch, rows, K, Kp2, kind, sa, sbc, hi, lo, unscale);
+  return true;
 }
 
 int blocks_for(long long warps) { return (int)std::max<long long>(1, (warps * 32 + 255) / 256); }
@@ -237,7 +470,13 @@ void csplit_a(const void *src, bool f32, long long sb, long long sr1, long long 
     m.sr2 = 0;
     m.R2 = 1;
   }
-  const int blocks = blocks_for((long long)rows * batch);
+  if (f32 ? launch_split_t(static_cast<const float2 *>(src), m, batch, rows, K, out.Kp2, 0, 1.f, 1.f, out.hi, out.lo,
+                           out.unscale, s)
+          : launch_split_t(static_cast<const double2 *>(src), m, batch, rows, K, out.Kp2, 0, 1.f, 1.f, out.hi, out.lo,
+                           out.unscale, s))
+    return;
+  const int lpr = lanes_per_row(out.Kp2);
+  const int blocks = (int)std::max<long long>(1, ((long long)rows * batch * lpr + 255) / 256);
   if (f32)
     k_csplit_a<float2><<<blocks, 256, 0, s>>>(static_cast<const float2 *>(src), m, batch, rows, K, out.Kp2, out.hi,
                                               out.lo, out.unscale);
@@ -254,8 +493,14 @@ void csplit_b(const void *src, bool f32, long long sb, long long sr1, long long 
     m.sr2 = 0;
     m.R2 = 1;
   }
-  const int blocks = blocks_for((long long)cols * batch);
   const float sa = conjA ? -1.f : 1.f, sbc = conjB ? -1.f : 1.f;
+  if (f32 ? launch_split_t(static_cast<const float2 *>(src), m, batch, cols, K, out.Kp2, 1, sa, sbc, out.hi, out.lo,
+                           out.unscale, s)
+          : launch_split_t(static_cast<const double2 *>(src), m, batch, cols, K, out.Kp2, 1, sa, sbc, out.hi, out.lo,
+                           out.unscale, s))
+    return;
+  const int lpr = lanes_per_row(out.Kp2);
+  const int blocks = (int)std::max<long long>(1, ((long long)cols * batch * lpr + 255) / 256);
   if (f32)
     k_csplit_b<float2><<<blocks, 256, 0, s>>>(static_cast<const float2 *>(src), m, batch, cols, K, out.Kp2, sa, sbc,
                                               out.hi, out.lo, out.unscale);
@@ -314,7 +559,52 @@ Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const
 }
 
 Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, const int *add, const int *sub,
-                    int nk, long long NN, int ct, int i0, long long sDi, double *D, cudaStream_t s) {
+                    const int mesh[3], long long NN, int ct, int i0, long long sDi, double *D, cudaStream_t s) {
+  const int nk = mesh[0] * mesh[1] * mesh[2];
+  {
+    dim3 grid((unsigned)((NN + 127) / 128), (unsigned)ct);
+    const float2 *Bf = reinterpret_cast<const float2 *>(B), *Cf = reinterpret_cast<const float2 *>(C);
+    double2 *Dd = reinterpret_cast<double2 *>(D);
+    const int key = mesh[0] * 100 + mesh[1] * 10 + mesh[2];
+    bool done = true;
+    switch (key) {
+#define SOX_DMESH(A, B_, C_)                                                             \
+  case A * 100 + B_ * 10 + C_:                                                          \
+    k_kpoint_D_mesh<A, B_, C_><<<grid, 128, 0, s>>>(Bf, Cf, sP, sI, NN, i0, sDi, Dd);  \
+    break;
+      SOX_DMESH(1, 1, 1) SOX_DMESH(1, 1, 2) SOX_DMESH(1, 2, 1) SOX_DMESH(2, 1, 1) SOX_DMESH(1, 1, 3)
+      SOX_DMESH(1, 3, 1) SOX_DMESH(3, 1, 1) SOX_DMESH(1, 2, 2) SOX_DMESH(2, 2, 1) SOX_DMESH(2, 1, 2)
+      SOX_DMESH(2, 2, 2) SOX_DMESH(3, 3, 1) SOX_DMESH(3, 3, 3)
+#undef SOX_DMESH
+      default:
+        done = false;
+    }
+    if (done && mesh[0] < 10 && mesh[1] < 10 && mesh[2] < 10) {
+      SOX_CUDA_TRY(cudaGetLastError());
+      return Status::ok();
+    }
+  }
+  {
+    dim3 grid((unsigned)((NN + 127) / 128), (unsigned)ct);
+    const float2 *Bf = reinterpret_cast<const float2 *>(B), *Cf = reinterpret_cast<const float2 *>(C);
+    double2 *Dd = reinterpret_cast<double2 *>(D);
+    bool done = true;
+    switch (nk) {
+#define SOX_DREG(K)                                                                      \
+  case K:                                                                               \
+    k_kpoint_D_reg<K><<<grid, 128, 0, s>>>(Bf, Cf, sP, sI, add, sub, NN, i0, sDi, Dd); \
+    break;
+      SOX_DREG(1) SOX_DREG(2) SOX_DREG(3) SOX_DREG(4) SOX_DREG(5) SOX_DREG(6) SOX_DREG(8) SOX_DREG(9)
+      SOX_DREG(12) SOX_DREG(16) SOX_DREG(18) SOX_DREG(27) SOX_DREG(32) SOX_DREG(36) SOX_DREG(48) SOX_DREG(64)
+#undef SOX_DREG
+      default:
+        done = false;
+    }
+    if (done) {
+      SOX_CUDA_TRY(cudaGetLastError());
+      return Status::ok();
+    }
+  }
   const long long np = (long long)nk * nk;
   const size_t per_e = (size_t)np * 2 * sizeof(float2);
   const size_t cap = 96 * 1024;

@@ -54,7 +54,7 @@ Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const
 // e < NN; B and C FP32 complex with element (pair p, il, e) at p*sP + il*sI + e (complex
 // units), D FP64 complex [.][k][NN] with stride sDi per i.
 Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, const int *add, const int *sub,
-                    int nk, long long NN, int ct, int i0, long long sDi, double *D, cudaStream_t s);
+                    const int mesh[3], long long NN, int ct, int i0, long long sDi, double *D, cudaStream_t s);
 
 // Split-precision forms of the momentum-resolved chain (handle precision SOX_PREC_F16X2).
 size_t kpoint_tc_bytes(sox_handle h, const sox_problem *p, bool two);

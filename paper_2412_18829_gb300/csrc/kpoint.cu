@@ -585,7 +585,6 @@ namespace {
 struct KTc {
   int nk, n, N, T, S;
   long long nk2, nn, Nn, NN, Nn2;
-  int vpad;   // complex row length of A_all (n rounded up to even)
   int ldN;    // complex row length of B, C and D (N rounded up to even)
 };
 
@@ -601,7 +600,6 @@ KTc ktc_geom(const sox_problem *p) {
   g.Nn = (long long)g.N * g.n;
   g.NN = (long long)g.N * g.N;
   g.Nn2 = g.Nn * g.n;
-  g.vpad = g.n + (g.n & 1);
   g.ldN = g.N + (g.N & 1);
   return g;
 }
@@ -659,9 +657,10 @@ Status mixed_tc(sox_handle h, const z *X, const z *U, const KTables &tb, const K
   return cgemm_tc(h, Us, Ys, (int)g.nk2, tb.qq, nullptr, 1.f, M, 2 * ld, 2 * g.N * ld, s);
 }
 
+// B rows (P,q) of the first mixed tensor, K = s
 void split_m1_tc(const float *M, const KTc &g, const CSplit &M1s, cudaStream_t s) {
   const long long ld = nnpad_of(g);
-  csplit_a(M, true, g.N * ld, ld, g.n, g.n, 1, (int)g.nk2, (int)g.Nn, g.n, M1s, s);
+  csplit_b(M, true, g.N * ld, ld, g.n, g.n, 1, (int)g.nk2, (int)g.Nn, g.n, false, false, M1s, s);
 }
 
 void split_m2_tc(const float *M, const KTc &g, const std::vector<CSplit> &M2s, cudaStream_t s) {
@@ -694,10 +693,11 @@ void backproject_k(const z *D, const z *X, const KTc &g, z *T1, z *Sig_i, long l
 size_t kpoint_tc_bytes(sox_handle, const sox_problem *p, bool two) {
   const KTc g = ktc_geom(p);
   size_t b = tables_bytes(g) + mixed_tc_bytes(g) * (two ? 2 : 1) + mixed_tc_scratch(g);
-  b += csplit_bytes((int)g.nk2, (int)g.Nn, g.n) + (size_t)g.n * csplit_bytes((int)g.nk2, 2 * g.N, g.n);
+  const long long ldNn = g.Nn + (g.Nn & 1);
+  b += csplit_bytes((int)g.nk2, (int)(2 * g.Nn), g.n) + (size_t)g.n * csplit_bytes((int)g.nk2, 2 * g.N, g.n);
   b += 2 * aligned_bytes(g.nk * g.Nn, 16);
-  b += csplit_bytes(g.nk, 2 * g.N, g.n) + csplit_bytes(g.nk, g.N, g.n) + csplit_bytes(g.nk, 2 * g.n, g.n);
-  b += aligned_bytes(g.nk2 * g.Nn * g.vpad, 8) + csplit_bytes((int)g.nk2, g.N, g.n);
+  b += csplit_bytes(g.nk, 2 * g.N, g.n) + csplit_bytes(g.nk, g.N, g.n) + csplit_bytes(g.nk, g.n, g.n);
+  b += aligned_bytes(g.nk2 * g.n * ldNn, 8) + csplit_bytes((int)g.nk2, g.N, g.n);
   b += 2 * aligned_bytes(g.nk2 * g.N * g.ldN, 8);
   b += aligned_bytes((size_t)g.nk * g.N * g.ldN, 16) + aligned_bytes(g.nk * g.Nn, 16);
   return b + (1 << 20);
@@ -717,13 +717,14 @@ Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, co
   const size_t mfl = 2 * (size_t)g.nk2 * g.N * nnpad_of(g);
   float *M1 = ar.take<float>(mfl);
   float *M2 = two ? ar.take<float>(mfl) : M1;
-  CSplit M1s = csplit_take(ar, (int)g.nk2, (int)g.Nn, g.n);
+  const long long ldNn = g.Nn + (g.Nn & 1);
+  CSplit M1s = csplit_take(ar, (int)g.nk2, (int)(2 * g.Nn), g.n);
   std::vector<CSplit> M2s(g.n);
   for (int v = 0; v < g.n; ++v) M2s[v] = csplit_take(ar, (int)g.nk2, 2 * g.N, g.n);
   z *GR = ar.take<z>(g.nk * g.Nn), *GWt = ar.take<z>(g.nk * g.Nn);
   CSplit GRs = csplit_take(ar, g.nk, 2 * g.N, g.n), GWts = csplit_take(ar, g.nk, g.N, g.n);
-  CSplit Gms = csplit_take(ar, g.nk, 2 * g.n, g.n);
-  float *Aall = ar.take<float>(2 * g.nk2 * g.Nn * g.vpad);
+  CSplit Gms = csplit_take(ar, g.nk, g.n, g.n);
+  float *Aall = ar.take<float>(2 * g.nk2 * g.n * ldNn);
   CSplit As = csplit_take(ar, (int)g.nk2, g.N, g.n);
   float *Ball = ar.take<float>(2 * g.nk2 * g.N * g.ldN), *Call = ar.take<float>(2 * g.nk2 * g.N * g.ldN);
   z *D = ar.take<z>((size_t)g.nk * g.N * g.ldN), *T1 = ar.take<z>(g.nk * g.Nn);
@@ -754,22 +755,25 @@ Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, co
       }
       csplit_b(GR, false, g.Nn, g.n, 0, 0, 1, g.nk, g.N, g.n, false, false, GRs, s);
       csplit_a(GWt, false, g.Nn, g.n, 0, 0, 1, g.nk, g.N, g.n, GWts, s);
-      // B rows v of G(-tau_j)^T: element (v, s) = G^k(tau_{T-1-j})[s][v]; the sign goes into alpha
-      csplit_b(Gs + (long long)(g.T - 1 - j) * g.nn, false, (long long)g.T * g.nn, 1, 0, 0, g.n, g.nk, g.n, g.n,
-               false, false, Gms, s);
-      // A^{q1,ks}[(P,q)][v] = -sum_s M1[(P,q)][s] G^{ks}(tau_{T-1-j})[s][v]
-      SOX_TRY(cgemm_tc(h, M1s, Gms, (int)g.nk2, nullptr, tb.kk, -1.f, Aall, 2LL * g.vpad, 2LL * g.Nn * g.vpad, s));
+      // A rows v of G(-tau_j)^T: element (v, s) = G^k(tau_{T-1-j})[s][v]; the sign goes into alpha
+      csplit_a(Gs + (long long)(g.T - 1 - j) * g.nn, false, (long long)g.T * g.nn, 1, 0, 0, g.n, g.nk, g.n, g.n, Gms,
+               s);
+      // A^{q1,ks}[v][(P,q)] = -sum_s G^{ks}(tau_{T-1-j})[s][v] M1[(P,q)][s]   ((P,q) contiguous per v)
+      SOX_TRY(cgemm_tc(h, Gms, M1s, (int)g.nk2, tb.kk, nullptr, -1.f, Aall, 2 * ldNn, 2LL * g.n * ldNn, s));
       SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)g.nk * g.N * g.ldN, s));
       launches += 5;
       for (int v = 0; v < g.n; ++v) {
-        csplit_a(reinterpret_cast<const float2 *>(Aall) + v, true, g.Nn * g.vpad, (long long)g.n * g.vpad, 0, 0,
-                 g.vpad, (int)g.nk2, g.N, g.n, As, s);
+        csplit_a(reinterpret_cast<const float2 *>(Aall) + (long long)v * ldNn, true, g.n * ldNn, g.n, 0, 0, 1,
+                 (int)g.nk2, g.N, g.n, As, s);
         // B^{q1,ks}_v[P][R] = sum_q A[v][P][q] GR^{ks-q1}[R][q]
         SOX_TRY(cgemm_tc(h, As, GRs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
         // C^{q2,kw}_v[P][R] = sum_w GWt^{kw}[P][w] M2^{q2,kw}[R][v][w]
         SOX_TRY(cgemm_tc(h, GWts, M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
-        SOX_TRY(kpoint_D_f32(Ball, Call, (long long)g.N * g.ldN, 0, tb.add, tb.sub, g.nk, (long long)g.N * g.ldN, 1,
-                             0, 0, reinterpret_cast<double *>(D), s));
+        {
+          ProfScope pd(h, "kpoint_D", s, 0);
+          SOX_TRY(kpoint_D_f32(Ball, Call, (long long)g.N * g.ldN, 0, tb.add, tb.sub, pr->nk, (long long)g.N * g.ldN,
+                               1, 0, 0, reinterpret_cast<double *>(D), s));
+        }
         launches += 2;
       }
       backproject_k(D, X, g, T1, Sig + ((long long)sp * g.nk * g.T + j) * g.nn, (long long)g.T * g.nn, -inv_nk2, 0.0,
@@ -934,9 +938,12 @@ Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const
         // C^{q2,kw}(tau_i)[P][R] = sum_w GWt^{kw}(tau_i)[P][w] M2^{q2,kw}[R][v][w]
         SOX_TRY(cgemm_tc(h, GWts.view((long long)i0 * N, cc * N), M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call,
                          2LL * g.ldN, 2LL * cc * N * g.ldN, s));
-        SOX_TRY(kpoint_D_f32(Ball, Call, (long long)cc * N * g.ldN, (long long)N * g.ldN, tb.add, tb.sub, nk,
-                             (long long)N * g.ldN, cc, i0, (long long)nk * N * g.ldN,
-                             reinterpret_cast<double *>(Dall), s));
+        {
+          ProfScope pd(h, "kpoint_D", s, 0);
+          SOX_TRY(kpoint_D_f32(Ball, Call, (long long)cc * N * g.ldN, (long long)N * g.ldN, tb.add, tb.sub, pr->nk,
+                               (long long)N * g.ldN, cc, i0, (long long)nk * N * g.ldN,
+                               reinterpret_cast<double *>(Dall), s));
+        }
         launches += 2;
       }
     }
