@@ -116,9 +116,10 @@ def mixed_tensors(U, X, nk):
     return out
 
 
-def sigma_chain(X, U1, U2, Gk, Gmk, nk, M1=None, M2=None):
+def sigma_chain(X, U1, U2, Gk, Gmk, nk, M1=None, M2=None, k_list=None):
     """The paper's THC-SOX algorithm for solids (Sec. II C): mixed tensors, projections,
-    A, B per (q1, k_s), C per (q2, k_w), then the n_k^3 D step and back-projection."""
+    A, B per (q1, k_s), C per (q2, k_w), then the n_k^3 D step and back-projection.
+    k_list restricts the output to those external momenta (all by default)."""
     add, sub = k_tables(nk)
     n_k, N, n = X.shape
     M1 = mixed_tensors(U1, X, nk) if M1 is None else M1
@@ -134,7 +135,7 @@ def sigma_chain(X, U1, U2, Gk, Gmk, nk, M1=None, M2=None):
             B[q, kk] = np.einsum("Pqv,Rq->PRv", A, GR[sub[kk, q]], optimize=True)  # k_q = k_s - q1
             C[q, kk] = np.einsum("Rvw,wP->RvP", M2[q, kk], GW[kk], optimize=True)  # k_w = kk
     out = []
-    for k in range(n_k):
+    for k in (range(n_k) if k_list is None else k_list):
         D = 0.0
         for q1 in range(n_k):
             kw = add[k, q1]                        # k_w = k_p = k + q1
@@ -146,12 +147,14 @@ def sigma_chain(X, U1, U2, Gk, Gmk, nk, M1=None, M2=None):
     return np.stack(out)
 
 
-def sox_sigma(X, V, G, nk, route="chain", taus=None, U2=None):
-    """Bare SOX (or SOX(V, U2)) for a solid, library layout G [n_spin][n_k][n_tau][n][n]."""
+def sox_sigma(X, V, G, nk, route="chain", taus=None, U2=None, k_list=None):
+    """Bare SOX (or SOX(V, U2)) for a solid, library layout G [n_spin][n_k][n_tau][n][n];
+    k_list (chain route) restricts the output to those k."""
     U2 = V if U2 is None else U2
     n_spin, n_k, n_tau = G.shape[:3]
     idx = range(n_tau) if taus is None else taus
-    res = np.empty((n_spin, n_k, len(list(idx)), G.shape[-1], G.shape[-1]), complex)
+    n_out = n_k if k_list is None else len(k_list)
+    res = np.empty((n_spin, n_out, len(list(idx)), G.shape[-1], G.shape[-1]), complex)
     M1 = mixed_tensors(V, X, nk) if route == "chain" else None
     M2 = (M1 if U2 is V else mixed_tensors(U2, X, nk)) if route == "chain" else None
     for s in range(n_spin):
@@ -159,7 +162,7 @@ def sox_sigma(X, V, G, nk, route="chain", taus=None, U2=None):
         for o, j in enumerate(idx):
             Gk, Gmk = G[s][:, j], Gm[:, j]
             if route == "chain":
-                res[s, :, o] = sigma_chain(X, V, U2, Gk, Gmk, nk, M1, M2)
+                res[s, :, o] = sigma_chain(X, V, U2, Gk, Gmk, nk, M1, M2, k_list)
             elif route == "direct":
                 res[s, :, o] = sigma_thc_direct(X, V, U2, Gk, Gmk, nk)
             else:

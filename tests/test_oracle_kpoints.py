@@ -101,3 +101,10 @@ def test_physical_screened_interaction_frequency_symmetry():
     a = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, w.G, nk)
     b = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, w.G, nk, route="brute")
     assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def test_chain_restricted_to_listed_k_points():
+    w = synth.solid(13, (1, 1, 3), 3, 5, 3, 4.0)
+    full = kpoints.sox_sigma(w.X, w.V, w.G, w.nk, taus=[1])
+    part = kpoints.sox_sigma(w.X, w.V, w.G, w.nk, taus=[1], k_list=[2, 0])
+    assert np.array_equal(part[:, 0], full[:, 2]) and np.array_equal(part[:, 1], full[:, 0])
