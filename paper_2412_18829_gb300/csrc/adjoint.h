@@ -10,4 +10,10 @@ size_t adjoint_bytes(sox_handle h, int n, int N, int T, int S, int *chunk);
 Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double *G, const double *X,
                           const double *V, const double *w, const double *dphi, double *dX, double *dV,
                           Arena &ar, cudaStream_t s);
+// The same in split precision (adjoint_tc.cu): every N x N x n contraction of the reverse
+// pass on the tensor cores in FP16 pairs with FP32 accumulation; FP64 projections.
+size_t adjoint_tc_bytes(sox_handle h, int n, int N, int T, int S);
+Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double *G, const double *X,
+                         const double *V, const double *w, const double *dphi, double *dX, double *dV,
+                         Arena &ar, cudaStream_t s);
 }  // namespace sox

@@ -697,7 +697,10 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
     SOX_TRY(call.output(dV, (size_t)d.N * d.N, &oV));
     size_t need = 0;
     if (dG) need = sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8);
-    if (dX || dV) need = std::max(need, sox::adjoint_bytes(h, d.n, d.N, d.T, d.S, nullptr));
+    const bool tc_adj = (h->precision == SOX_PREC_F16X2);
+    if (dX || dV)
+      need = std::max(need, tc_adj ? sox::adjoint_tc_bytes(h, d.n, d.N, d.T, d.S)
+                                   : sox::adjoint_bytes(h, d.n, d.N, d.T, d.S, nullptr));
     Arena ar;
     SOX_TRY(call.begin(need, &ar));
     cudaStream_t s = call.stream();
@@ -711,7 +714,11 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
     }
     if (oX.out || oV.out) {
       Arena a3 = ar;
-      SOX_TRY(sox::phi_adjoint_xv_f64(h, d.n, d.N, d.T, d.S, sG.in, sX.in, sV.in, sw.in, sd.in, oX.out, oV.out,
+      if (tc_adj)
+        SOX_TRY(sox::phi_adjoint_xv_tc(h, d.n, d.N, d.T, d.S, sG.in, sX.in, sV.in, sw.in, sd.in, oX.out, oV.out, a3,
+                                       s));
+      else
+        SOX_TRY(sox::phi_adjoint_xv_f64(h, d.n, d.N, d.T, d.S, sG.in, sX.in, sV.in, sw.in, sd.in, oX.out, oV.out,
                                       a3, s));
     }
     return call.end();

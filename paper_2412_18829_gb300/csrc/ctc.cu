@@ -438,6 +438,115 @@ bool launch_split_t(const T *src, const RowMap &m, int batch, int rows, int K, i
   return true;
 }
 
+// ----------------------------- real operands -----------------------------
+__device__ __forceinline__ double ld_r(const double *p) { return *p; }
+__device__ __forceinline__ double ld_r(const float *p) { return (double)*p; }
+
+__device__ __forceinline__ void store8_r(const double *v, float s, __half *h, __half *l) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __half a0, d0, a1, d1;
+    split_pair(v[2 * j], s, a0, d0);
+    split_pair(v[2 * j + 1], s, a1, d1);
+    ph[j] = pack_h2(a0, a1);
+    pl[j] = pack_h2(d0, d1);
+  }
+  *reinterpret_cast<uint4 *>(h) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  *reinterpret_cast<uint4 *>(l) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+}
+
+// Real rows with K contiguous or strided: LPR lanes per row, 16-byte stores.
+template <class T>
+__global__ void k_rsplit(const T *src, const float *mul, RowMap m, int batch, int rows, int K, int Kp, __half *hi,
+                         __half *lo, float *unscale) {
+  const int lpr = lanes_per_row(Kp);
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gr = gt / lpr;
+  const int gl = (int)(gt % lpr);
+  const bool live = gr < (long long)rows * batch;
+  const int b = live ? (int)(gr / rows) : 0, r = live ? (int)(gr % rows) : 0;
+  const T *x = src + m.row(b, r);
+  const float *mu = mul ? mul + m.row(0, r) : nullptr;
+  auto val = [&](int k) { return mu ? ld_r(x + k * m.sk) * (double)mu[k * m.sk] : ld_r(x + k * m.sk); };
+  float mx = 0.f;
+  if (live)
+    for (int k = gl; k < K; k += lpr) mx = fmaxf(mx, (float)fabs(val(k)));
+  mx = group_max(mx, lpr);
+  if (!live) return;
+  const float s = tc::pow2_floor_inv(mx);
+  __half *h = hi + gr * Kp, *l = lo + gr * Kp;
+  for (int c8 = gl; c8 < Kp / 8; c8 += lpr) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = c8 * 8 + j;
+      v[j] = k < K ? val(k) : 0.0;
+    }
+    store8_r(v, s, h + c8 * 8, l + c8 * 8);
+  }
+  if (gl == 0) unscale[gr] = 1.f / s;
+}
+
+// Real rows contiguous along the row index with K strided: 32 rows per block, K in
+// chunks of 64 through a shared-memory tile, twice (row maxima, then the FP16 pairs).
+template <class T>
+__global__ void __launch_bounds__(256) k_rsplit_t(const T *src, const float *mul, RowMap m, int batch, int rows, int K,
+                                                 int Kp, __half *hi, __half *lo, float *unscale) {
+  __shared__ T tile[64][kRB + 1];
+  __shared__ float rmax[kRB];
+  const int nrb = (rows + kRB - 1) / kRB;
+  const int b = blockIdx.x / nrb, r0 = (blockIdx.x % nrb) * kRB;
+  if (b >= batch) return;
+  const int t = threadIdx.x;
+  if (t < kRB) rmax[t] = 0.f;
+  const int rr = t / 8, part = t % 8;   // phase 2: 8 threads per row, 8 values each
+  float my = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 64) {
+    __syncthreads();
+    for (int idx = t; idx < 64 * kRB; idx += blockDim.x) {
+      const int k = idx / kRB, c = idx % kRB;
+      T v{};
+      if (r0 + c < rows && k0 + k < K) {
+        const long long off = m.row(0, r0 + c) + (long long)(k0 + k) * m.sk;
+        v = src[(long long)b * m.sb + off];
+        if (mul) v = (T)((double)v * (double)mul[off]);
+      }
+      tile[k][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) my = fmaxf(my, (float)fabs((double)tile[part * 8 + j][rr]));
+  }
+  // row maxima: the 8 threads of a row are consecutive lanes
+  for (int o = 4; o > 0; o >>= 1) my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+  const float sc = tc::pow2_floor_inv(my);
+  const int r = r0 + rr;
+  const long long row = (long long)b * rows + r;
+  for (int k0 = 0; k0 < Kp; k0 += 64) {
+    __syncthreads();
+    for (int idx = t; idx < 64 * kRB; idx += blockDim.x) {
+      const int k = idx / kRB, c = idx % kRB;
+      T v{};
+      if (r0 + c < rows && k0 + k < K) {
+        const long long off = m.row(0, r0 + c) + (long long)(k0 + k) * m.sk;
+        v = src[(long long)b * m.sb + off];
+        if (mul) v = (T)((double)v * (double)mul[off]);
+      }
+      tile[k][c] = v;
+    }
+    __syncthreads();
+    if (r < rows) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (double)tile[part * 8 + j][rr];
+      store8_r(v, sc, hi + row * Kp + k0 + part * 8, lo + row * Kp + k0 + part * 8);
+    }
+  }
+  if (r < rows && part == 0) unscale[row] = 1.f / sc;
+  (void)rmax;
+}
+
 int blocks_for(long long warps) { return (int)std::max<long long>(1, (warps * 32 + 255) / 256); }
 
 }  // namespace
@@ -516,7 +625,7 @@ void csplit_pairs(const double *X, const int *sub, int nk, int N, int n, const C
 }
 
 Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const int *idxA, const int *idxB,
-                float alpha, float *C, long long ldc, long long sCb, cudaStream_t s) {
+                float alpha, float *C, long long ldc, long long sCb, cudaStream_t s, bool accumulate) {
   if (batch <= 0 || A.rows <= 0 || B.rows <= 0) return Status::ok();
   if (A.Kp2 != B.Kp2) return {SOX_ERR_INVALID_ARG, "cgemm_tc: operands split with different K"};
   if ((ldc & 3) || (sCb & 3) || (reinterpret_cast<uintptr_t>(C) & 15))
@@ -545,6 +654,7 @@ Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const
   ga.ldc = ldc;
   ga.sCb = sCb;
   ga.alpha = alpha;
+  ga.accumulate = accumulate ? 1 : 0;
   ga.row_scale = A.unscale;
   ga.rs_b = bsA;
   ga.col_scale = B.unscale;
@@ -620,6 +730,54 @@ Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, 
                                               sP, sI, add, sub, nk, NN, E, i0, sDi, reinterpret_cast<double2 *>(D));
   SOX_CUDA_TRY(cudaGetLastError());
   return Status::ok();
+}
+
+int rsplit_kp(int K) { return ((K + 63) / 64) * 64; }
+
+size_t rsplit_bytes(int batch, int rows, int K) {
+  const size_t e = (size_t)batch * rows * rsplit_kp(K);
+  return 2 * aligned_bytes(e, 2) + aligned_bytes((size_t)batch * rows, 4);
+}
+
+CSplit rsplit_take(Arena &ar, int batch, int rows, int K) {
+  CSplit c;
+  c.batch = batch;
+  c.rows = rows;
+  c.Kp2 = rsplit_kp(K);
+  const size_t e = (size_t)batch * rows * c.Kp2;
+  c.hi = ar.take<__half>(e);
+  c.lo = ar.take<__half>(e);
+  c.unscale = ar.take<float>((size_t)batch * rows);
+  if (!c.unscale) c.hi = nullptr;
+  return c;
+}
+
+void rsplit(const void *src, bool f32, long long sb, long long sr1, long long sr2, int R2, long long sk, int batch,
+            int rows, int K, const CSplit &out, cudaStream_t s, const float *mul) {
+  RowMap m{sb, sr1, sr2, sk, R2 > 0 ? R2 : 1};
+  if (R2 <= 0) {
+    m.sr2 = 0;
+    m.R2 = 1;
+  }
+  const bool contiguous_rows = (m.R2 == 1 ? m.sr1 == 1 : m.sr2 == 1);
+  if (contiguous_rows && sk != 1) {
+    const long long blocks = (long long)batch * ((rows + kRB - 1) / kRB);
+    if (f32)
+      k_rsplit_t<float><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float *>(src), mul, m, batch, rows, K,
+                                                         out.Kp2, out.hi, out.lo, out.unscale);
+    else
+      k_rsplit_t<double><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double *>(src), mul, m, batch, rows, K,
+                                                          out.Kp2, out.hi, out.lo, out.unscale);
+    return;
+  }
+  const int lpr = lanes_per_row(out.Kp2);
+  const int blocks = (int)std::max<long long>(1, ((long long)rows * batch * lpr + 255) / 256);
+  if (f32)
+    k_rsplit<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), mul, m, batch, rows, K, out.Kp2, out.hi,
+                                           out.lo, out.unscale);
+  else
+    k_rsplit<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), mul, m, batch, rows, K, out.Kp2, out.hi,
+                                            out.lo, out.unscale);
 }
 
 }  // namespace sox

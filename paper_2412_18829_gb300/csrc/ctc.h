@@ -48,7 +48,18 @@ void csplit_pairs(const double *X, const int *sub, int nk, int N, int n, const C
 // stride ldc and batch stride sCb in floats (multiples of 4, C 16-byte aligned);
 // zA = idxA ? idxA[b] : (A.batch == 1 ? 0 : b), zB likewise.
 Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const int *idxA, const int *idxB,
-                float alpha, float *C, long long ldc, long long sCb, cudaStream_t s);
+                float alpha, float *C, long long ldc, long long sCb, cudaStream_t s, bool accumulate = false);
+
+// Real operands: `rows` real rows of K values (Kp2 = 64*ceil(K/64)), element (b, r, k) at
+// src + b*sb + (r/R2)*sr1 + (r%R2)*sr2 + k*sk (real elements), FP64 or FP32.  cgemm_tc
+// multiplies real splits as well (C[b][i][j] = alpha sum_k A[i][k] B[j][k], FP32).
+int rsplit_kp(int K);
+size_t rsplit_bytes(int batch, int rows, int K);
+CSplit rsplit_take(Arena &ar, int batch, int rows, int K);
+// mul (optional, FP32): each element is multiplied by mul at the same offset without
+// the batch term (a Hadamard factor shared by all batches)
+void rsplit(const void *src, bool f32, long long sb, long long sr1, long long sr2, int R2, long long sk, int batch,
+            int rows, int K, const CSplit &out, cudaStream_t s, const float *mul = nullptr);
 
 // D[i0 + il][k][e] += sum_{q1,q2} C[(q2, k+q1), il][e] B[(q1, k+q1-q2), il][e]  for il < ct and
 // e < NN; B and C FP32 complex with element (pair p, il, e) at p*sP + il*sI + e (complex

@@ -660,11 +660,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const int gj = j0 + 4 * lane;
           float *dst = a.Cf + (long long)b * a.sCb + (long long)gi * a.ldc + gj;
           if (gj + 3 < a.Ncols) {
-            *reinterpret_cast<float4 *>(dst) = val;
+            if (a.accumulate) {
+              const float4 o = *reinterpret_cast<const float4 *>(dst);
+              *reinterpret_cast<float4 *>(dst) = make_float4(o.x + val.x, o.y + val.y, o.z + val.z, o.w + val.w);
+            } else {
+              *reinterpret_cast<float4 *>(dst) = val;
+            }
           } else {
-            if (gj < a.Ncols) dst[0] = val.x;
-            if (gj + 1 < a.Ncols) dst[1] = val.y;
-            if (gj + 2 < a.Ncols) dst[2] = val.z;
+            const float vv[3] = {val.x, val.y, val.z};
+            for (int t = 0; t < 3; ++t)
+              if (gj + t < a.Ncols) dst[t] = a.accumulate ? dst[t] + vv[t] : vv[t];
           }
         }
         continue;

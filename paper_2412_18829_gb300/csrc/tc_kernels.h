@@ -39,6 +39,7 @@ struct GemmTcArgs {
   float *Cf = nullptr;
   long long ldc = 0, sCb = 0;
   float alpha = 1.f;
+  int accumulate = 0;   // kStoreF32: add to Cf instead of overwriting
   const float *row_scale = nullptr, *col_scale = nullptr;
   long long rs_b = 0, cs_b = 0;
   // batch coordinate of the A / B operand for output batch b (overrides batch*_shared)

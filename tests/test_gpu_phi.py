@@ -145,3 +145,47 @@ def test_grad_G_from_kept_sigma_equals_backward(env):
     assert torch.equal(a, b)
     with pytest.raises(pkg.SoxError):
         pkg.phi_sox_grad_G(h, p, S, tw, d, S)
+
+
+def _grads_with(torch, pkg, h, w, wt, dphi):
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, tw = to_dev(torch, w.G, w.X, w.V, wt)
+    d = torch.tensor(dphi, dtype=torch.float64, device="cuda")
+    dX = torch.full_like(X, float("nan"))
+    dV = torch.full_like(V, float("nan"))
+    pkg.phi_sox_backward(h, p, G, X, V, tw, d, None, dX, dV)
+    pkg.sox_check_device(h)
+    torch.cuda.synchronize()
+    return dX.cpu().numpy()[0], dV.cpu().numpy()[0]
+
+
+@pytest.mark.parametrize("n,N,n_tau,n_spin", [(9, 30, 6, 1), (7, 41, 5, 2), (16, 70, 4, 1), (33, 130, 3, 1)])
+def test_split_adjoint_matches_oracle_autograd(env, n, N, n_tau, n_spin):
+    """The tensor-core adjoint (FP16 pairs, FP32 accumulation) against the oracle's
+    autograd gradients, to the split path's FP32-class bound (relative 2e-5)."""
+    torch, pkg, _ = env
+    w = synth.molecule(26, n, N, n_tau, 3.0, n_spin=n_spin)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    dphi = [1.0, -0.5][:n_spin]
+    with pkg.Handle("f16x2") as h:
+        gX, gV = _grads_with(torch, pkg, h, w, wt, dphi)
+    rX = np.zeros_like(gX)
+    rV = np.zeros_like(gV)
+    for s in range(n_spin):
+        _, _, x, v = phi.phi_and_grads(w.X[0], w.V[0], w.G[s, 0], wt)
+        rX += dphi[s] * x
+        rV += dphi[s] * v
+    assert np.isfinite(gX).all() and np.isfinite(gV).all()
+    assert np.abs(gX - rX).max() <= 2e-5 * np.abs(rX).max()
+    assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max()
+
+
+def test_split_adjoint_matches_fp64_adjoint_on_smallest_batch_instance(env):
+    torch, pkg, h64 = env
+    w = synth.c4_instance(synth.c4_smallest(1)[0])
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    rX, rV = _grads_with(torch, pkg, h64, w, wt, [1.0])
+    with pkg.Handle("f16x2") as h:
+        gX, gV = _grads_with(torch, pkg, h, w, wt, [1.0])
+    assert np.abs(gX - rX).max() <= 2e-5 * np.abs(rX).max()
+    assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max()
