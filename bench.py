@@ -411,11 +411,12 @@ class BatchCase(Case):
     """The uneven batch (c4): Phi and Sigma of every instance, then dPhi/dG from the kept
     Sigma; the 16 instances are dealt out over the ranks (no data-path collective)."""
 
-    def __init__(self, torch, pkg, prec, dev, stream, rank, world):
+    def __init__(self, torch, pkg, prec, dev, stream, rank, world, backward=True):
         import synth
         from paper_2412_18829_gb300 import sharding
 
         self.torch, self.pkg, self.prec, self.dev, self.stream = torch, pkg, prec, dev, stream
+        self.backward = backward
         sizes = [int(n) for n in synth.batch_c4_sizes()]
         costs = [sharding.build_cost(n, 6 * n, 120) for n in sizes]
         self.mine = sharding.shard(costs, world)[rank]
@@ -436,21 +437,27 @@ class BatchCase(Case):
                  "wt_h": np.ascontiguousarray(wts)}
             d["S"] = torch.empty_like(d["G"])
             d["dG"] = torch.empty_like(d["G"])
+            d["dX"] = torch.empty_like(d["X"])
+            d["dV"] = torch.empty_like(d["V"])
             d["phi"] = torch.empty(w.n_spin, dtype=torch.float64, device=dev)
             d["dphi"] = torch.ones(w.n_spin, dtype=torch.float64, device=dev)
             self.inst.append(d)
         self.config = {"workload": self.name, "instances": len(sizes), "n": sizes, "N": "6n", "n_tau": 120,
                        "beta": 100.0, "precision": prec, "instances_on_rank0": self.mine if rank == 0 else None,
-                       "step": "per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept "
-                               "Sigma); one launch sequence per instance"}
+                       "step": ("per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept "
+                                "Sigma) + phi_sox_backward (dPhi/dX, dPhi/dV)") if backward else
+                               "per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept Sigma)"}
 
-    def _one(self, h, d, G, X, V, wt, S, phi, dG):
+    def _one(self, h, d, G, X, V, wt, S, phi, dG, dX=None, dV=None):
         self.pkg.phi_sox(h, d["p"], G, X, V, wt, phi, S, self.stream)
         self.pkg.phi_sox_grad_G(h, d["p"], S, wt, d["dphi"], dG, self.stream)
+        if dX is not None:   # dPhi/dX and dPhi/dV by the adjoint of the THC chain
+            self.pkg.phi_sox_backward(h, d["p"], G, X, V, wt, d["dphi"], None, dX, dV, self.stream)
 
     def step(self):
         for d in self.inst:
-            self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"])
+            self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"],
+                      d["dX"] if self.backward else None, d["dV"] if self.backward else None)
 
     def e2e_step(self):
         h2d = d2h = 0
@@ -460,9 +467,17 @@ class BatchCase(Case):
                 w = d["w"]
                 d["Gh"], d["Xh"], d["Vh"] = pin(w.G), pin(w.X), pin(w.V)
                 d["Sh"], d["dGh"], d["phih"] = pin(np.empty_like(w.G)), pin(np.empty_like(w.G)), pin(np.zeros(w.n_spin))
-            self._one(self.h, d, d["Gh"], d["Xh"], d["Vh"], d["wt_h"], d["Sh"], d["phih"], d["dGh"])
+            if "dXh" not in d:
+                d["dXh"] = self.torch.from_numpy(np.empty_like(d["w"].X)).pin_memory().numpy()
+                d["dVh"] = self.torch.from_numpy(np.empty_like(d["w"].V)).pin_memory().numpy()
+            bw = self.backward
+            self._one(self.h, d, d["Gh"], d["Xh"], d["Vh"], d["wt_h"], d["Sh"], d["phih"], d["dGh"],
+                      d["dXh"] if bw else None, d["dVh"] if bw else None)
             h2d += d["Gh"].nbytes + d["Xh"].nbytes + d["Vh"].nbytes + 2 * d["wt_h"].nbytes + d["Sh"].nbytes
             d2h += d["Sh"].nbytes + d["phih"].nbytes + d["dGh"].nbytes
+            if bw:
+                h2d += d["Gh"].nbytes + d["Xh"].nbytes + d["Vh"].nbytes + d["wt_h"].nbytes
+                d2h += d["dXh"].nbytes + d["dVh"].nbytes
         return h2d, d2h
 
     def hot_flops_per_step(self):
@@ -519,6 +534,16 @@ class BatchCase(Case):
                                                              None, x, v, self.stream)
                                    for d, x, v in zip(sub, dX, dV)])
             out["max_abs_err_Ha_vs_fp64_gpu_smallest3"] = max(float((d["S"] - s).abs().max()) for d, s in zip(sub, S64))
+            if self.prec == "f16x2":
+                tX = [torch.empty_like(d["X"]) for d in sub]
+                tV = [torch.empty_like(d["V"]) for d in sub]
+                t_adj_tc = timed(lambda: [self.pkg.phi_sox_backward(self.h, d["p"], d["G"], d["X"], d["V"], d["wt"],
+                                                                    d["dphi"], None, x, v, self.stream)
+                                          for d, x, v in zip(sub, tX, tV)])
+                rel = lambda a, b: float((a - b).abs().max() / b.abs().max())   # noqa: E731
+                out["adjoint_XV_split_ms_smallest3"] = 1e3 * t_adj_tc
+                out["adjoint_split_vs_fp64_max_rel_dX"] = max(rel(a, b) for a, b in zip(tX, dX))
+                out["adjoint_split_vs_fp64_max_rel_dV"] = max(rel(a, b) for a, b in zip(tV, dV))
         adj_flops = sum(12.0 * d["w"].N ** 2 * d["w"].n ** 2 * d["w"].n_tau for d in sub)
         out.update({"smallest3_n": [d["w"].n for d in sub],
                     "smallest3_ms_f16x2": 1e3 * t_mixed, "smallest3_ms_fp64": 1e3 * t64,
@@ -531,7 +556,7 @@ class BatchCase(Case):
 
 def make_case(args, torch, pkg, dev, stream, rank, world):
     if args.workload == "c4":
-        return BatchCase(torch, pkg, args.precision, dev, stream, rank, world)
+        return BatchCase(torch, pkg, args.precision, dev, stream, rank, world, backward=not args.forward_only)
     w = workload(args.workload)
     if args.workload == "c3":
         return SolidCase(torch, pkg, w, args.precision, dev, stream)
@@ -583,6 +608,8 @@ def run_ours(args):
     if isinstance(case, SolidCase):
         for ph in (("kpoint_tc", "kpoint_dynamic_tc") if case.prec == "f16x2" else ("kpoint_f64", "kpoint_dynamic_f64")):
             phases[ph] = pkg.sox_profile_read(case.h, ph)
+    if isinstance(case, BatchCase) and case.backward:
+        phases["adjoint"] = pkg.sox_profile_read(case.h, "phi_adjoint_tc" if case.prec == "f16x2" else "phi_adjoint_f64")
     pkg.sox_profile_enable(case.h, False)
     clocks = sampler.stop()
     if dist:
@@ -643,6 +670,11 @@ def run_ours(args):
     elif case.dtype.startswith("f16x2"):
         roof = _tensor_peak(pk, pk_src, achieved)
         roof["kernel"] = case.hot
+        if "adjoint" in phases and phases["adjoint"][1]:
+            adj_fl = sum(12.0 * d["w"].N ** 2 * d["w"].n ** 2 * d["w"].n_tau for d in case.inst)
+            extra["adjoint_ms_per_step"] = phases["adjoint"][1] / args.steps
+            extra["adjoint_algorithmic_tflops"] = adj_fl * args.steps / (phases["adjoint"][1] / 1e3) / 1e12
+            extra["forward_fused_kernel_ms_per_step"] = hot_ms / args.steps
     else:
         roof = _alu_peak(achieved, "fused FP64 B/C/Hadamard kernel")
         roof["kernel"] = case.hot
@@ -685,6 +717,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--forward-only", action="store_true", help="batch workload: no dPhi/dX, dPhi/dV")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -20,17 +20,18 @@ namespace {
 long long rup4(long long x) { return (x + 3) & ~3LL; }
 int grid1(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 65535 * 8)); }
 
-// Dbar = c E (FP32, row length ld); Ebar = c sum_v B_v o C_v (FP64, N x N)
-__global__ void k_dbar(const float *B, const float *C, const double *E, const double *w, const double *dphi, int j,
-                       int n, int N, long long ld, float *Dbar, double *Ebar) {
-  const double c = -0.25 * w[j] * dphi[0];
+// Dbar = c E and Ebar = c sum_v B_v o C_v (FP32, row length ld; the FP32 class of the split
+// path), c = -w_j dphi / 4
+__global__ void k_dbar(const float *B, const float *C, const float *E, const double *w, const double *dphi, int j,
+                       int n, int N, long long ld, float *Dbar, float *Ebar) {
+  const float c = (float)(-0.25 * w[j] * dphi[0]);
   const long long NN = (long long)N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NN; e += (long long)gridDim.x * blockDim.x) {
     const long long P = e / N, R = e % N, o = P * ld + R;
-    double d = 0.0;
-    for (int v = 0; v < n; ++v) d += (double)B[(long long)v * N * ld + o] * (double)C[(long long)v * N * ld + o];
-    Dbar[o] = (float)(c * E[e]);
-    Ebar[e] = c * d;
+    float d = 0.f;
+    for (int v = 0; v < n; ++v) d = fmaf(B[(long long)v * N * ld + o], C[(long long)v * N * ld + o], d);
+    Dbar[o] = c * E[o];
+    Ebar[o] = c * d;
   }
 }
 
@@ -99,16 +100,16 @@ size_t setup_bytes(const AdjGeom &g) {
   return aligned_bytes((size_t)N * g.nn, 8) + rsplit_bytes(1, N, N) + rsplit_bytes(1, (int)g.nn, N) +
          aligned_bytes((size_t)N * g.nnp, 4) + rsplit_bytes(1, N * n, n) + rsplit_bytes(n, N, n) +
          rsplit_bytes(n, n, N) + aligned_bytes((size_t)N * n * g.np4, 4) + aligned_bytes((size_t)n * N * g.np4, 4) +
-         aligned_bytes((size_t)N * n, 8);
+         aligned_bytes((size_t)N * n, 8) + rsplit_bytes(1, N, n) + rsplit_bytes(1, n, N);
 }
 
 size_t tau_bytes(const AdjGeom &g) {
   const int n = g.n, N = g.N;
-  size_t b = 3 * aligned_bytes((size_t)N * n, 8) + aligned_bytes((size_t)N * N, 8);   // GR, GWt, M1, E
+  size_t b = 3 * aligned_bytes((size_t)N * n, 8) + aligned_bytes((size_t)N * g.ldN, 4);   // GR, GWt, M1, E
   b += 2 * rsplit_bytes(1, N, n) + 2 * rsplit_bytes(1, n, N) + 2 * rsplit_bytes(1, n, n);
   b += aligned_bytes((size_t)n * g.Nnp4, 4) + rsplit_bytes(n, N, n) + rsplit_bytes(n, n, N);
-  b += 2 * aligned_bytes((size_t)n * N * g.ldN, 4) + aligned_bytes((size_t)N * g.ldN, 4) +
-       aligned_bytes((size_t)N * N, 8);
+  b += 2 * aligned_bytes((size_t)n * N * g.ldN, 4) + 2 * aligned_bytes((size_t)N * g.ldN, 4);   // B, C, Dbar, Ebar
+  b += rsplit_bytes(1, N, n) + 2 * rsplit_bytes(1, N, N) + 2 * aligned_bytes((size_t)N * g.np4, 4);   // E, Ebar X
   b += 4 * rsplit_bytes(n, N, N) + 3 * aligned_bytes((size_t)n * N * g.np4, 4) + rsplit_bytes(1, N * n, n);
   b += 4 * aligned_bytes((size_t)N * n, 8);   // GRbar, GWtbar, m1, m2
   return b;
@@ -138,6 +139,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   CSplit U1s = rsplit_take(ar, 1, N * n, n), U2v = rsplit_take(ar, n, N, n), U2vT = rsplit_take(ar, n, n, N);
   float *U1bar = ar.take<float>((size_t)N * n * g.np4), *U2bar = ar.take<float>((size_t)n * N * g.np4);
   double *Xbar = ar.take<double>((size_t)Nn);
+  CSplit Xr = rsplit_take(ar, 1, N, n), XT = rsplit_take(ar, 1, n, N);   // X rows R (K = t); rows t (K = R)
   if (!Xbar || !U2vT.hi) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   ProfScope ps(h, "phi_adjoint_tc", s, 0);
   long long launches = 0;
@@ -151,12 +153,16 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   rsplit(Um, true, 0, g.nnp, n, n, 1, 1, N * n, n, U1s, s);                // rows (P,q), K = s
   rsplit(Um, true, n, g.nnp, 0, 0, 1, n, N, n, U2v, s);                    // [v] rows R, K = w
   rsplit(Um, true, n, 1, 0, 0, g.nnp, n, n, N, U2vT, s);                   // [v] rows w, K = R
-  launches += 6;
+  rsplit(X, false, 0, n, 0, 0, 1, 1, N, n, Xr, s);
+  rsplit(X, false, 0, 1, 0, 0, n, 1, n, N, XT, s);
+  launches += 8;
 
   // ---- per (spin, tau) buffers
   Arena at = ar;
   double *GR = at.take<double>(Nn), *GWt = at.take<double>(Nn), *M1 = at.take<double>(Nn);
-  double *E = at.take<double>(NN);
+  float *E = at.take<float>((size_t)N * g.ldN);
+  CSplit M1s = rsplit_take(at, 1, N, n), Ebs = rsplit_take(at, 1, N, N), EbTs = rsplit_take(at, 1, N, N);
+  float *m1f = at.take<float>((size_t)N * g.np4), *m2f = at.take<float>((size_t)N * g.np4);
   CSplit GRs = rsplit_take(at, 1, N, n), GWts = rsplit_take(at, 1, N, n);
   CSplit GRts = rsplit_take(at, 1, n, N), GWtts = rsplit_take(at, 1, n, N);
   CSplit Gma = rsplit_take(at, 1, n, n), Gmb = rsplit_take(at, 1, n, n);
@@ -164,7 +170,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   CSplit As = rsplit_take(at, n, N, n), Ats = rsplit_take(at, n, n, N);
   float *Ball = at.take<float>((size_t)n * N * g.ldN), *Call = at.take<float>((size_t)n * N * g.ldN);
   float *Dbar = at.take<float>((size_t)N * g.ldN);
-  double *Ebar = at.take<double>(NN);
+  float *Ebar = at.take<float>((size_t)N * g.ldN);
   CSplit Bbs = rsplit_take(at, n, N, N), Cbs = rsplit_take(at, n, N, N);
   CSplit BbTs = rsplit_take(at, n, N, N), CbTs = rsplit_take(at, n, N, N);
   float *Abar = at.take<float>((size_t)n * N * g.np4), *GRbv = at.take<float>((size_t)n * N * g.np4);
@@ -176,6 +182,8 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   SOX_CUDA_TRY(cudaMemsetAsync(Ball, 0, 4 * (size_t)n * N * g.ldN, s));
   SOX_CUDA_TRY(cudaMemsetAsync(Call, 0, 4 * (size_t)n * N * g.ldN, s));
   SOX_CUDA_TRY(cudaMemsetAsync(Dbar, 0, 4 * (size_t)N * g.ldN, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(E, 0, 4 * (size_t)N * g.ldN, s));      // pad columns stay zero
+  SOX_CUDA_TRY(cudaMemsetAsync(Ebar, 0, 4 * (size_t)N * g.ldN, s));
 
   for (int sp = 0; sp < S; ++sp) {
     for (int j = 0; j < T; ++j) {
@@ -194,13 +202,9 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         GemmF64 c = a;
         c.B = Gm; c.C = M1; c.alpha = -1.0;
         launch_gemm_f64(c, s);
-        GemmF64 e;
-        e.M = N; e.Nc = N; e.K = n;
-        e.A = M1; e.ai = n; e.ak = 1;
-        e.B = X; e.bk = 1; e.bj = n;
-        e.C = E; e.ci = N; e.cj = 1;
-        launch_gemm_f64(e, s);
       }
+      rsplit(M1, false, 0, n, 0, 0, 1, 1, N, n, M1s, s);
+      SOX_TRY(cgemm_tc(h, M1s, Xr, 1, nullptr, nullptr, 1.f, E, g.ldN, 0, s));   // E = X G(-tau_j) X^T
       rsplit(GR, false, 0, n, 0, 0, 1, 1, N, n, GRs, s);
       rsplit(GR, false, 0, 1, 0, 0, n, 1, n, N, GRts, s);
       rsplit(GWt, false, 0, n, 0, 0, 1, 1, N, n, GWts, s);
@@ -239,15 +243,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         GemmF64 x2 = x1;
         x2.A = GWtbar; x2.bk = n; x2.bj = 1;
         launch_gemm_f64(x2, s);
-        GemmF64 a1;
-        a1.M = N; a1.Nc = n; a1.K = N;
-        a1.A = Ebar; a1.ai = N; a1.ak = 1;
-        a1.B = X; a1.bk = n; a1.bj = 1;
-        a1.C = m1; a1.ci = n; a1.cj = 1;
-        launch_gemm_f64(a1, s);
-        GemmF64 a2 = a1;
-        a2.ai = 1; a2.ak = N; a2.C = m2;
-        launch_gemm_f64(a2, s);
+        // m1 = Ebar X, m2 = Ebar^T X on the tensor cores
+        rsplit(Ebar, true, 0, g.ldN, 0, 0, 1, 1, N, N, Ebs, s);
+        rsplit(Ebar, true, 0, 1, 0, 0, g.ldN, 1, N, N, EbTs, s);
+        SOX_TRY(cgemm_tc(h, Ebs, XT, 1, nullptr, nullptr, 1.f, m1f, g.np4, 0, s));
+        SOX_TRY(cgemm_tc(h, EbTs, XT, 1, nullptr, nullptr, 1.f, m2f, g.np4, 0, s));
+        k_to_f64<<<grid1(Nn), 256, 0, s>>>(m1f, g.np4, N, n, m1);
+        k_to_f64<<<grid1(Nn), 256, 0, s>>>(m2f, g.np4, N, n, m2);
         GemmF64 x3;
         x3.M = N; x3.Nc = n; x3.K = n;
         x3.A = m1; x3.ai = n; x3.ak = 1;

@@ -24,17 +24,21 @@ __device__ __forceinline__ float cwarp_max(float v) {
   return v;
 }
 
+// loads keep the source precision: FP32 sources are split in FP32 arithmetic (exact: the
+// scale is a power of two and hi's remainder is representable), FP64 sources in FP64
 __device__ __forceinline__ double2 ld_c(const double2 *p) { return *p; }
-__device__ __forceinline__ double2 ld_c(const float2 *p) {
-  const float2 v = *p;
-  return make_double2(v.x, v.y);
-}
+__device__ __forceinline__ float2 ld_c(const float2 *p) { return *p; }
 
-// FP16 pair of x * s (s a power of two, exact in FP64): hi rounds to nearest.
+// FP16 pair of x * s (s a power of two): hi rounds to nearest, lo holds the remainder.
 __device__ __forceinline__ void split_pair(double x, float s, __half &h, __half &l) {
   const double xs = x * (double)s;
   h = __float2half_rn((float)xs);
   l = __float2half_rn((float)(xs - (double)__half2float(h)));
+}
+__device__ __forceinline__ void split_pair(float x, float s, __half &h, __half &l) {
+  const float xs = x * s;
+  h = __float2half_rn(xs);
+  l = __float2half_rn(xs - __half2float(h));
 }
 
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
@@ -43,7 +47,8 @@ __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
 
 // Eight FP16 pairs (4 complex values, interleaved) of an A row -> one 16-byte store each
 // for hi and lo.  v[j] are the complex values k0..k0+3 (zero beyond K).
-__device__ __forceinline__ void store8_a(const double2 *v, float s, __half *h, __half *l) {
+template <class V2>
+__device__ __forceinline__ void store8_a(const V2 *v, float s, __half *h, __half *l) {
   uint32_t ph[4], pl[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -58,18 +63,20 @@ __device__ __forceinline__ void store8_a(const double2 *v, float s, __half *h, _
 }
 
 // The same for the re-row and im-row of a B row: re (b_r, -sa sb b_i), im (sb b_i, sa b_r).
-__device__ __forceinline__ void store8_b(const double2 *v, float s, float sa, float sbc, __half *h0, __half *l0,
+template <class V2>
+__device__ __forceinline__ void store8_b(const V2 *v, float s, float sa, float sbc, __half *h0, __half *l0,
                                          __half *h1, __half *l1) {
+  using R = decltype(v[0].x);
   uint32_t p0[4], q0[4], p1[4], q1[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     __half a, b, c, d;
     split_pair(v[j].x, s, a, b);
-    split_pair(-(double)(sa * sbc) * v[j].y, s, c, d);
+    split_pair(static_cast<R>(-(sa * sbc)) * v[j].y, s, c, d);
     p0[j] = pack_h2(a, c);
     q0[j] = pack_h2(b, d);
-    split_pair((double)sbc * v[j].y, s, a, b);
-    split_pair((double)sa * v[j].x, s, c, d);
+    split_pair(static_cast<R>(sbc) * v[j].y, s, a, b);
+    split_pair(static_cast<R>(sa) * v[j].x, s, c, d);
     p1[j] = pack_h2(a, c);
     q1[j] = pack_h2(b, d);
   }
@@ -112,7 +119,7 @@ __global__ void k_csplit_a(const T *src, RowMap m, int batch, int rows, int K, i
   float mx = 0.f;
   if (live)
     for (int k = gl; k < K; k += lpr) {
-      const double2 v = ld_c(x + k * m.sk);
+      const T v = ld_c(x + k * m.sk);
       mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
     }
   mx = group_max(mx, lpr);
@@ -120,11 +127,11 @@ __global__ void k_csplit_a(const T *src, RowMap m, int batch, int rows, int K, i
   const float s = tc::pow2_floor_inv(mx);
   __half *h = hi + gr * Kp2, *l = lo + gr * Kp2;
   for (int c8 = gl; c8 < Kp2 / 8; c8 += lpr) {
-    double2 v[4];
+    T v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = c8 * 4 + j;
-      v[j] = k < K ? ld_c(x + k * m.sk) : make_double2(0.0, 0.0);
+      v[j] = k < K ? ld_c(x + k * m.sk) : T{};
     }
     store8_a(v, s, h + c8 * 8, l + c8 * 8);
   }
@@ -145,7 +152,7 @@ __global__ void k_csplit_b(const T *src, RowMap m, int batch, int cols, int K, i
   float mx = 0.f;
   if (live)
     for (int k = gl; k < K; k += lpr) {
-      const double2 v = ld_c(x + k * m.sk);
+      const T v = ld_c(x + k * m.sk);
       mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
     }
   mx = group_max(mx, lpr);
@@ -155,11 +162,11 @@ __global__ void k_csplit_b(const T *src, RowMap m, int batch, int cols, int K, i
   __half *h0 = hi + r0 * Kp2, *l0 = lo + r0 * Kp2;
   __half *h1 = h0 + Kp2, *l1 = l0 + Kp2;
   for (int c8 = gl; c8 < Kp2 / 8; c8 += lpr) {
-    double2 v[4];
+    T v[4];
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int k = c8 * 4 + jj;
-      v[jj] = k < K ? ld_c(x + k * m.sk) : make_double2(0.0, 0.0);
+      v[jj] = k < K ? ld_c(x + k * m.sk) : T{};
     }
     store8_b(v, s, sa, sbc, h0 + c8 * 8, l0 + c8 * 8, h1 + c8 * 8, l1 + c8 * 8);
   }
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(256) k_csplit_t(const T *src, RowMap m, int ba
     if (r >= rows) break;
     float mx = 0.f;
     for (int k = lane; k < K; k += 32) {
-      const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+      const T v = tile[k * (kRB + 1) + rr];
       mx = fmaxf(mx, fmaxf((float)fabs(v.x), (float)fabs(v.y)));
     }
     mx = cwarp_max(mx);
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(256) k_csplit_t(const T *src, RowMap m, int ba
       for (int k = lane; k < Kp2 / 2; k += 32) {
         __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0;
         if (k < K) {
-          const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+          const T v = tile[k * (kRB + 1) + rr];
           split_pair(v.x, s, a0, d0);
           split_pair(v.y, s, a1, d1);
         }
@@ -401,11 +408,12 @@ __global__ void __launch_bounds__(256) k_csplit_t(const T *src, RowMap m, int ba
       for (int k = lane; k < Kp2 / 2; k += 32) {
         __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0, a2 = a0, d2 = a0, a3 = a0, d3 = a0;
         if (k < K) {
-          const double2 v = ld_c(&tile[k * (kRB + 1) + rr]);
+          const T v = tile[k * (kRB + 1) + rr];
+          using R = decltype(v.x);
           split_pair(v.x, s, a0, d0);
-          split_pair(-(double)(sa * sbc) * v.y, s, a1, d1);
-          split_pair((double)sbc * v.y, s, a2, d2);
-          split_pair((double)sa * v.x, s, a3, d3);
+          split_pair(static_cast<R>(-(sa * sbc)) * v.y, s, a1, d1);
+          split_pair(static_cast<R>(sbc) * v.y, s, a2, d2);
+          split_pair(static_cast<R>(sa) * v.x, s, a3, d3);
         }
         h0[k] = __halves2half2(a0, a1);
         l0[k] = __halves2half2(d0, d1);
@@ -440,9 +448,10 @@ bool launch_split_t(const T *src, const RowMap &m, int batch, int rows, int K, i
 
 // ----------------------------- real operands -----------------------------
 __device__ __forceinline__ double ld_r(const double *p) { return *p; }
-__device__ __forceinline__ double ld_r(const float *p) { return (double)*p; }
+__device__ __forceinline__ float ld_r(const float *p) { return *p; }
 
-__device__ __forceinline__ void store8_r(const double *v, float s, __half *h, __half *l) {
+template <class R>
+__device__ __forceinline__ void store8_r(const R *v, float s, __half *h, __half *l) {
   uint32_t ph[4], pl[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -468,7 +477,7 @@ __global__ void k_rsplit(const T *src, const float *mul, RowMap m, int batch, in
   const int b = live ? (int)(gr / rows) : 0, r = live ? (int)(gr % rows) : 0;
   const T *x = src + m.row(b, r);
   const float *mu = mul ? mul + m.row(0, r) : nullptr;
-  auto val = [&](int k) { return mu ? ld_r(x + k * m.sk) * (double)mu[k * m.sk] : ld_r(x + k * m.sk); };
+  auto val = [&](int k) -> T { return mu ? ld_r(x + k * m.sk) * static_cast<T>(mu[k * m.sk]) : ld_r(x + k * m.sk); };
   float mx = 0.f;
   if (live)
     for (int k = gl; k < K; k += lpr) mx = fmaxf(mx, (float)fabs(val(k)));
@@ -477,11 +486,11 @@ __global__ void k_rsplit(const T *src, const float *mul, RowMap m, int batch, in
   const float s = tc::pow2_floor_inv(mx);
   __half *h = hi + gr * Kp, *l = lo + gr * Kp;
   for (int c8 = gl; c8 < Kp / 8; c8 += lpr) {
-    double v[8];
+    T v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = c8 * 8 + j;
-      v[j] = k < K ? val(k) : 0.0;
+      v[j] = k < K ? val(k) : T(0);
     }
     store8_r(v, s, h + c8 * 8, l + c8 * 8);
   }
@@ -510,13 +519,13 @@ __global__ void __launch_bounds__(256) k_rsplit_t(const T *src, const float *mul
       if (r0 + c < rows && k0 + k < K) {
         const long long off = m.row(0, r0 + c) + (long long)(k0 + k) * m.sk;
         v = src[(long long)b * m.sb + off];
-        if (mul) v = (T)((double)v * (double)mul[off]);
+        if (mul) v = v * static_cast<T>(mul[off]);
       }
       tile[k][c] = v;
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) my = fmaxf(my, (float)fabs((double)tile[part * 8 + j][rr]));
+    for (int j = 0; j < 8; ++j) my = fmaxf(my, fabsf((float)tile[part * 8 + j][rr]));
   }
   // row maxima: the 8 threads of a row are consecutive lanes
   for (int o = 4; o > 0; o >>= 1) my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
@@ -531,20 +540,70 @@ __global__ void __launch_bounds__(256) k_rsplit_t(const T *src, const float *mul
       if (r0 + c < rows && k0 + k < K) {
         const long long off = m.row(0, r0 + c) + (long long)(k0 + k) * m.sk;
         v = src[(long long)b * m.sb + off];
-        if (mul) v = (T)((double)v * (double)mul[off]);
+        if (mul) v = v * static_cast<T>(mul[off]);
       }
       tile[k][c] = v;
     }
     __syncthreads();
     if (r < rows) {
-      double v[8];
+      T v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = (double)tile[part * 8 + j][rr];
+      for (int j = 0; j < 8; ++j) v[j] = tile[part * 8 + j][rr];
       store8_r(v, sc, hi + row * Kp + k0 + part * 8, lo + row * Kp + k0 + part * 8);
     }
   }
   if (r < rows && part == 0) unscale[row] = 1.f / sc;
   (void)rmax;
+}
+
+// FP32 rows with K contiguous and 16-byte aligned: one warp per row reads the row once
+// into registers (16-byte loads, CH float4 per lane), finds its scale and writes the pairs.
+// Requires the row storage to extend to a multiple of 4 floats (masked beyond K).
+template <int CH>
+__global__ void __launch_bounds__(256) k_rsplit_f32v(const float *src, const float *mul, RowMap m, int batch, int rows,
+                                                    int K, int Kp, __half *hi, __half *lo, float *unscale) {
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (gw >= (long long)rows * batch) return;
+  const int b = (int)(gw / rows), r = (int)(gw % rows);
+  const long long roff = m.row(0, r);
+  const float4 *x = reinterpret_cast<const float4 *>(src + (long long)b * m.sb + roff);
+  const float4 *mu = mul ? reinterpret_cast<const float4 *>(mul + roff) : nullptr;
+  float4 v[CH];
+  float mx = 0.f;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k4 = c * 32 + lane;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k4 * 4 < K) {
+      t = __ldg(x + k4);
+      if (mu) {
+        const float4 u = __ldg(mu + k4);
+        t.x *= u.x; t.y *= u.y; t.z *= u.z; t.w *= u.w;
+      }
+      if (k4 * 4 + 1 >= K) t.y = 0.f;
+      if (k4 * 4 + 2 >= K) t.z = 0.f;
+      if (k4 * 4 + 3 >= K) t.w = 0.f;
+    }
+    v[c] = t;
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(t.x), fabsf(t.y)), fmaxf(fabsf(t.z), fabsf(t.w))));
+  }
+  mx = cwarp_max(mx);
+  const float s = tc::pow2_floor_inv(mx);
+  __half *h = hi + gw * Kp, *l = lo + gw * Kp;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k4 = c * 32 + lane;
+    if (k4 * 4 >= Kp) break;
+    __half a[4], d[4];
+    split_pair(v[c].x, s, a[0], d[0]);
+    split_pair(v[c].y, s, a[1], d[1]);
+    split_pair(v[c].z, s, a[2], d[2]);
+    split_pair(v[c].w, s, a[3], d[3]);
+    *reinterpret_cast<uint2 *>(h + k4 * 4) = make_uint2(pack_h2(a[0], a[1]), pack_h2(a[2], a[3]));
+    *reinterpret_cast<uint2 *>(l + k4 * 4) = make_uint2(pack_h2(d[0], d[1]), pack_h2(d[2], d[3]));
+  }
+  if (lane == 0) unscale[gw] = 1.f / s;
 }
 
 int blocks_for(long long warps) { return (int)std::max<long long>(1, (warps * 32 + 255) / 256); }
@@ -768,6 +827,26 @@ void rsplit(const void *src, bool f32, long long sb, long long sr1, long long sr
     else
       k_rsplit_t<double><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double *>(src), mul, m, batch, rows, K,
                                                           out.Kp2, out.hi, out.lo, out.unscale);
+    return;
+  }
+  // FP32 rows, K contiguous, 16-byte aligned rows whose storage reaches a multiple of 4 floats
+  const bool vec = f32 && sk == 1 && m.R2 == 1 && (m.sr1 % 4 == 0) && (m.sb % 4 == 0) && m.sr1 >= ((K + 3) & ~3) &&
+                   (reinterpret_cast<uintptr_t>(src) % 16 == 0) && (!mul || reinterpret_cast<uintptr_t>(mul) % 16 == 0) &&
+                   out.Kp2 <= 2048;
+  if (vec) {
+    const int blocks = (int)std::max<long long>(1, ((long long)rows * batch * 32 + 255) / 256);
+    const float *fs = static_cast<const float *>(src);
+    const int ch = (out.Kp2 + 127) / 128;
+    if (ch <= 1)
+      k_rsplit_f32v<1><<<blocks, 256, 0, s>>>(fs, mul, m, batch, rows, K, out.Kp2, out.hi, out.lo, out.unscale);
+    else if (ch <= 2)
+      k_rsplit_f32v<2><<<blocks, 256, 0, s>>>(fs, mul, m, batch, rows, K, out.Kp2, out.hi, out.lo, out.unscale);
+    else if (ch <= 4)
+      k_rsplit_f32v<4><<<blocks, 256, 0, s>>>(fs, mul, m, batch, rows, K, out.Kp2, out.hi, out.lo, out.unscale);
+    else if (ch <= 8)
+      k_rsplit_f32v<8><<<blocks, 256, 0, s>>>(fs, mul, m, batch, rows, K, out.Kp2, out.hi, out.lo, out.unscale);
+    else
+      k_rsplit_f32v<16><<<blocks, 256, 0, s>>>(fs, mul, m, batch, rows, K, out.Kp2, out.hi, out.lo, out.unscale);
     return;
   }
   const int lpr = lanes_per_row(out.Kp2);

@@ -5,6 +5,9 @@
     python -m paper_2412_18829_gb300.probes.profile_case solid [f16x2|fp64] [n_tau]
         one sosex_dynamic_sigma on the 3x3x3 solid's shapes (n=26, N=300), 4 tau by default,
         with the synthetic single-pole W_d
+    python -m paper_2412_18829_gb300.probes.profile_case adjoint [f16x2|fp64] [n_tau]
+        phi_sox_backward (dX, dV) twice on the largest batch instance's shapes (n=298,
+        N=1788), 8 tau by default
 """
 from __future__ import annotations
 
@@ -43,6 +46,19 @@ def main(argv):
         p = pkg.problem(w.n, w.N, T, 1, w.beta, nk=w.nk, dtype=1)
         with pkg.Handle(prec) as h:
             pkg.sosex_dynamic_sigma(h, p, G, X, V, W, F, I, 2 * M + 1, S)
+            pkg.sox_check_device(h)
+    elif kind == "adjoint":
+        T = int(argv[3]) if len(argv) > 3 else 8
+        n = int(synth.batch_c4_sizes().max())
+        w = synth.molecule(4, n, 6 * n, T, 100.0, 1)
+        _, wts = pkg.sox_tau_grid(w.n_tau, w.beta)
+        p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        G, X, V, tw = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w.G, w.X, w.V, wts)]
+        d = torch.ones(1, dtype=torch.float64, device="cuda")
+        dX, S = torch.empty_like(X), torch.empty_like(V)
+        with pkg.Handle(prec) as h:
+            for _ in range(2):
+                pkg.phi_sox_backward(h, p, G, X, V, tw, d, None, dX, S)
             pkg.sox_check_device(h)
     else:
         raise SystemExit(f"unknown case {kind}")
