@@ -158,13 +158,13 @@ def test_error_paths(env):
     S = torch.zeros_like(G)
     bad = [pkg.problem(0, 5, 4), pkg.problem(3, 5, 1), pkg.problem(3, 5, 4, n_spin=3),
            pkg.problem(3, 5, 4, beta=-1.0), pkg.problem(3, 5, 4, nk=(2, 1, 1)),
-           pkg.problem(3, 5, 4, dtype=1), pkg.problem(2000, 5, 4)]
+           pkg.problem(3, 5, 4, dtype=7), pkg.problem(2000, 5, 4)]
     codes = []
-    for p in bad:
+    for p in bad:   # every descriptor is rejected before any buffer is touched
         with pytest.raises(pkg.SoxError) as e:
             pkg.sox_sigma(h, p, G, X, V, S)
         codes.append(e.value.code)
-    assert codes == [2, 2, 2, 1, 3, 3, 2]
+    assert codes == [2, 2, 2, 1, 3, 1, 2]
     with pytest.raises(pkg.SoxError):
         pkg.sox_sigma(h, pkg.problem(3, 5, 4), G, X, V, None)
     with pytest.raises(pkg.SoxError):
