@@ -25,10 +25,13 @@
  *     V, W0     [n_q][N][N]         U^q_{PQ}   (n_q = n_k)
  *   Real data (SOX_REAL64) are doubles; complex data (SOX_COMPLEX128) are
  *   interleaved (re, im) doubles.  Molecules are SOX_REAL64 with n_k = 1.
- *   Solids (any k-mesh) are SOX_COMPLEX128: sox_sigma, sox_sigma_general and
- *   sosex_static_sigma accept them and run the momentum-resolved chain in FP64
- *   complex whatever the handle's precision; the other entry points return
- *   SOX_ERR_UNSUPPORTED for complex data.
+ *   Solids (any k-mesh) are SOX_COMPLEX128: sox_sigma, sox_sigma_general,
+ *   sosex_static_sigma and sosex_dynamic_sigma accept them and run the
+ *   momentum-resolved chain, in FP64 complex on CUDA cores (SOX_PREC_FP64) or
+ *   with every contraction as complex FP16-pair GEMMs on the tensor cores
+ *   (SOX_PREC_F16X2; projections, D accumulation over v and the final orbital
+ *   sum in FP64).  The other entry points return SOX_ERR_UNSUPPORTED for
+ *   complex data.
  * - k labels run row-major over the mesh (k = 2 pi m / nk, m in [0, nk)^3);
  *   V[q] is the THC metric of momentum transfer q = k_i - k_j (Sec. II C).
  * - The tau grid must be mirror-symmetric, tau_{n_tau-1-j} = beta - tau_j
@@ -238,8 +241,8 @@ SOX_API int phi_sox_grad_G(sox_handle h, const sox_problem *p, const double *Sig
  * where D_d is the static chain's D with B built from
  *   A^{q1,ks}_Puv(tau_i) = sum_m T_inv[i][m] sum_Q W_d^{q1}_PQ(i Omega_m)
  *        sum_j T_fwd[m][j] G^{ks-q1}_uQ(tau_j) G^{ks}_Qv(-tau_j).
- * Everything runs in FP64 complex on CUDA cores for solids.  G, X, V and Sigma
- * use the solid layouts of sox_sigma. */
+ * Solids run in the handle's precision (see the layout notes above).  G, X, V
+ * and Sigma use the solid layouts of sox_sigma. */
 SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream);
