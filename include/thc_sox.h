@@ -254,6 +254,33 @@ SOX_API int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs,
                     const double *const *G, const double *const *X, const double *const *V,
                     double *const *Sigma, void *stream);
 
+/* Batch plan (graph form of sox_sigma_batch).  The whole launch sequence of
+ * `count` independent bare-SOX problems (uneven sizes allowed; molecules,
+ * SOX_REAL64) is run once eagerly and then recorded once into a CUDA graph;
+ * sox_plan_launch replays it with a single graph launch, reading the current
+ * contents of the same G, X, V and writing the same Sigma.  No paper passage:
+ * this is the batching of Sec. II C's per-instance chains, as an execution plan.
+ *   - h: supplies precision, device and limits; the plan owns its own handle and
+ *     workspace (sized for the largest instance at creation, never regrown), so
+ *     other calls on h cannot invalidate it.  Creation synchronises its device.
+ *   - probs, G, X, V, Sigma: HOST arrays of `count` entries; every tensor must be
+ *     device memory on h's GPU and stay allocated, at the same address, for the
+ *     plan's lifetime.  Host tensors and solids: SOX_ERR_INVALID_ARG /
+ *     SOX_ERR_UNSUPPORTED.
+ *   - sox_plan_launch is asynchronous on `stream`; launches on one stream run in
+ *     order; launches of one plan on different streams at once race (they share
+ *     the plan's workspace).  sox_plan_check_device synchronises the device and
+ *     reports a device-side wait that timed out, like sox_check_device.
+ *   - sox_plan_destroy synchronises the device and frees the plan. */
+typedef struct sox_plan_s *sox_plan;
+SOX_API int sox_sigma_batch_plan(sox_handle h, int count, const sox_problem *probs, const double *const *G,
+                                 const double *const *X, const double *const *V, double *const *Sigma,
+                                 sox_plan *out);
+SOX_API int sox_plan_launch(sox_plan plan, void *stream);
+SOX_API int sox_plan_check_device(sox_plan plan);
+SOX_API const char *sox_plan_last_error(sox_plan plan);
+SOX_API int sox_plan_destroy(sox_plan plan);
+
 /* ------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; this is a service to
  * callers of the library).

@@ -24,6 +24,7 @@ from ._binding import (  # noqa: F401
     sox_reserve,
     sox_sigma,
     sox_sigma_batch,
+    SigmaBatchPlan,
     sox_sigma_fp64_noalloc,
     sox_sigma_general,
     sox_tau_grid,

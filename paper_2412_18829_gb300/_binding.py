@@ -65,6 +65,12 @@ _SIGS = {
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
     "sox_sigma_fp64_noalloc": ([ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
+    "sox_sigma_batch_plan": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
+    "sox_plan_launch": ([_P, _P], _I),
+    "sox_plan_check_device": ([_P], _I),
+    "sox_plan_last_error": ([_P], ctypes.c_char_p),
+    "sox_plan_destroy": ([_P], _I),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -259,6 +265,49 @@ def sox_sigma_batch(h: Handle, probs, G, X, V, Sigma, stream=None):
     arr = (sox_problem * count)(*probs)
     mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
     h.check(lib().sox_sigma_batch(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(Sigma), _stream(stream)))
+
+
+class SigmaBatchPlan:
+    """``sox_sigma_batch_plan``: the sox_sigma sequence of a batch of molecules recorded
+    once into a CUDA graph.  The tensors (device memory) must outlive the plan; each
+    ``launch`` recomputes every Sigma from the current G, X, V."""
+
+    def __init__(self, h: Handle, probs, G, X, V, Sigma):
+        count = len(probs)
+        arr = (sox_problem * count)(*probs)
+        mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
+        self._keep = (list(G), list(X), list(V), list(Sigma))
+        p = _P()
+        h.check(lib().sox_sigma_batch_plan(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(Sigma), ctypes.byref(p)))
+        self._p = p
+
+    def _check(self, rc, what):
+        if rc != SOX_OK:
+            msg = lib().sox_plan_last_error(self._p)
+            raise SoxError(rc, f"{what}: " + (msg.decode() if msg else ""))
+
+    def launch(self, stream=None):
+        self._check(lib().sox_plan_launch(self._p, _stream(stream)), "sox_plan_launch")
+
+    def check_device(self):
+        self._check(lib().sox_plan_check_device(self._p), "sox_plan_check_device")
+
+    def close(self):
+        if self._p:
+            lib().sox_plan_destroy(self._p)
+            self._p = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sox_sigma_fp64_noalloc(p: sox_problem, G, X, V, Sigma, stream=None):

@@ -844,4 +844,121 @@ int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs, const dou
   return finish(h, Status::ok());
 }
 
+// ---------------------------------------------------------------------------
+// Batch plans: the sox_sigma sequence of an uneven batch recorded once into a
+// CUDA graph (own handle and workspace), replayed with one launch.
+// ---------------------------------------------------------------------------
+struct sox_plan_s {
+  sox_handle ih = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int count = 0;
+};
+
+static void plan_free(sox_plan p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->ih) sox_destroy(p->ih);
+  delete p;
+}
+
+static Status plan_device_tensor(sox_handle h, const void *ptr, const char *what) {
+  if (!ptr) return {SOX_ERR_INVALID_ARG, std::string(what) + " is NULL"};
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return {SOX_ERR_INVALID_ARG, std::string(what) + ": not a device pointer"};
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != h->device)
+    return {SOX_ERR_INVALID_ARG, std::string(what) + ": batch plans take device memory of the handle's GPU"};
+  return Status::ok();
+}
+
+int sox_sigma_batch_plan(sox_handle h, int count, const sox_problem *probs, const double *const *G,
+                         const double *const *X, const double *const *V, double *const *Sigma, sox_plan *out) {
+  if (!h || !out) return SOX_ERR_INVALID_ARG;
+  *out = nullptr;
+  sox_plan plan = nullptr;
+  cudaStream_t cs = nullptr;
+  Status st = [&]() -> Status {
+    if (count < 1 || !probs || !G || !X || !V || !Sigma) return {SOX_ERR_INVALID_ARG, "bad batch arrays"};
+    SOX_TRY(bind_device(h));
+    for (int i = 0; i < count; ++i) {
+      Status v = validate(&probs[i]);   // molecules (real data, one k point)
+      if (!v.good()) {
+        v.msg = "instance " + std::to_string(i) + ": " + v.msg;
+        return v;
+      }
+      SOX_TRY(plan_device_tensor(h, G[i], "G"));
+      SOX_TRY(plan_device_tensor(h, X[i], "X"));
+      SOX_TRY(plan_device_tensor(h, V[i], "V"));
+      SOX_TRY(plan_device_tensor(h, Sigma[i], "Sigma"));
+    }
+    plan = new (std::nothrow) sox_plan_s();
+    if (!plan) return {SOX_ERR_OOM, "plan allocation failed"};
+    plan->count = count;
+    sox_options o{h->precision, h->device, h->spin_limit, (long long)h->ws_limit, h->autotune ? 0 : 1};
+    const int rc = sox_create(&plan->ih, &o);
+    if (rc != SOX_OK) return {rc, "could not create the plan's handle"};
+    SOX_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // eager pass: sizes the plan's workspace for the largest instance and settles the
+    // autotuned kernel choices, so that the recorded pass allocates and times nothing
+    for (int i = 0; i < count; ++i) SOX_TRY(run_sigma(plan->ih, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], cs));
+    SOX_CUDA_TRY(cudaStreamSynchronize(cs));
+    SOX_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    Status rec = Status::ok();
+    for (int i = 0; i < count && rec.good(); ++i)
+      rec = run_sigma(plan->ih, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (!rec.good()) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rec;
+    }
+    if (ec != cudaSuccess) return {SOX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec)};
+    plan->graph = g;
+    SOX_CUDA_TRY(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
+    return Status::ok();
+  }();
+  if (cs) cudaStreamDestroy(cs);
+  if (!st.good()) {
+    plan_free(plan);
+    return finish(h, st);
+  }
+  *out = plan;
+  return finish(h, st);
+}
+
+int sox_plan_launch(sox_plan plan, void *stream) {
+  if (!plan || !plan->exec) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(bind_device(plan->ih));
+    SOX_CUDA_TRY(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+    return Status::ok();
+  }();
+  return finish(plan->ih, st);
+}
+
+int sox_plan_check_device(sox_plan plan) {
+  if (!plan) return SOX_ERR_INVALID_ARG;
+  return sox_check_device(plan->ih);
+}
+
+const char *sox_plan_last_error(sox_plan plan) { return plan ? sox_last_error(plan->ih) : "plan is NULL"; }
+
+int sox_plan_destroy(sox_plan plan) {
+  if (!plan) return SOX_ERR_INVALID_ARG;
+  if (plan->ih) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(plan->ih->device);
+    cudaDeviceSynchronize();
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  plan_free(plan);
+  return SOX_OK;
+}
+
 }  // extern "C"
