@@ -222,6 +222,11 @@ def _alu_peak(achieved, what):
 
 
 FP64_PEAK_TFLOPS = 1.20
+# DRAM bytes (read + write) of one fused-kernel launch over 16 (spin, tau) batches at n=120,
+# N=600, from ncu (profiles/bcd_fused_kernel_n120_N600.md); the U2 operand (36.9 MB) is read
+# once per launch, the rest scales with the batches of a launch
+BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726431744 + 20530944, "shared": 36.9e6,
+               "source": "ncu dram__bytes_read+write of k_sox_bcd_tc on 16 batches, scaled to the launch's batches"}
 FP32_PEAK_TFLOPS = 78.4
 
 
@@ -670,6 +675,12 @@ def run_ours(args):
     elif case.dtype.startswith("f16x2"):
         roof = _tensor_peak(pk, pk_src, achieved)
         roof["kernel"] = case.hot
+        w = getattr(case, "w", None)
+        if isinstance(case, MoleculeCase) and (w.n, w.N) == BCD_TRAFFIC["shape"] and hot_n:
+            b_launch = w.n_tau * w.n_spin / (hot_n / args.steps)
+            per_b = (BCD_TRAFFIC["bytes"] - BCD_TRAFFIC["shared"]) / BCD_TRAFFIC["batches"]
+            roof["traffic"] = per_b * b_launch + BCD_TRAFFIC["shared"]
+            roof["traffic_source"] = BCD_TRAFFIC["source"]
         if "adjoint" in phases and phases["adjoint"][1]:
             adj_fl = sum(12.0 * d["w"].N ** 2 * d["w"].n ** 2 * d["w"].n_tau for d in case.inst)
             extra["adjoint_ms_per_step"] = phases["adjoint"][1] / args.steps
