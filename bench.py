@@ -223,8 +223,8 @@ def _alu_peak(achieved, what):
 
 FP64_PEAK_TFLOPS = 1.20
 # DRAM bytes (read + write) of one fused-kernel launch over 16 (spin, tau) batches at n=120,
-# N=600, from ncu (profiles/bcd_fused_kernel_n120_N600.md); the U2 operand (36.9 MB) is read
-# once per launch, the rest scales with the batches of a launch
+# N=600, from an ncu capture of k_sox_bcd_tc; the U2 operand (36.9 MB) is read once per
+# launch, the rest scales with the batches of a launch
 BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726431744 + 20530944, "shared": 36.9e6,
                "source": "ncu dram__bytes_read+write of k_sox_bcd_tc on 16 batches, scaled to the launch's batches"}
 FP32_PEAK_TFLOPS = 78.4
