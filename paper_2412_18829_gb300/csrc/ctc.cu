@@ -683,47 +683,55 @@ void csplit_pairs(const double *X, const int *sub, int nk, int N, int n, const C
                                                    out.lo, out.unscale);
 }
 
+// The tensor core truncates its FP32 accumulator at every MMA step, a bias that grows with
+// the number of steps; K beyond kKChunk is therefore split into windows whose partial
+// products are added to C by the epilogue in round-to-nearest FP32.
+constexpr int kKChunk = 1024;
+
 Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const int *idxA, const int *idxB,
                 float alpha, float *C, long long ldc, long long sCb, cudaStream_t s, bool accumulate) {
   if (batch <= 0 || A.rows <= 0 || B.rows <= 0) return Status::ok();
   if (A.Kp2 != B.Kp2) return {SOX_ERR_INVALID_ARG, "cgemm_tc: operands split with different K"};
   if ((ldc & 3) || (sCb & 3) || (reinterpret_cast<uintptr_t>(C) & 15))
     return {SOX_ERR_INVALID_ARG, "cgemm_tc: output not 16-byte aligned"};
-  CUtensorMap maps[6];
-  std::string err;
   const long long bsA = A.bstride ? A.bstride : A.rows, bsB = B.bstride ? B.bstride : B.rows;
-  if (!make_tmap_f16_3d_bs(&maps[0], A.hi, A.Kp2, A.rows, A.batch, bsA * A.Kp2, 64, 128, &err) ||
-      !make_tmap_f16_3d_bs(&maps[1], A.lo, A.Kp2, A.rows, A.batch, bsA * A.Kp2, 64, 128, &err) ||
-      !make_tmap_f16_3d_bs(&maps[2], B.hi, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err) ||
-      !make_tmap_f16_3d_bs(&maps[3], B.lo, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err))
-    return {SOX_ERR_CUDA, "cgemm_tc: " + err};
-  maps[4] = maps[0];   // no TMA stores in FP32 mode; valid maps for the prefetch
-  maps[5] = maps[1];
-  GemmTcArgs ga;
-  ga.M = A.rows;
-  ga.Ncols = B.rows;
-  ga.Kp = A.Kp2;
-  ga.batch = batch;
-  ga.batchA_shared = (A.batch == 1);
-  ga.batchB_shared = (B.batch == 1);
-  ga.idxA = idxA;
-  ga.idxB = idxB;
-  ga.mode = kStoreF32;
-  ga.Cf = C;
-  ga.ldc = ldc;
-  ga.sCb = sCb;
-  ga.alpha = alpha;
-  ga.accumulate = accumulate ? 1 : 0;
-  ga.row_scale = A.unscale;
-  ga.rs_b = bsA;
-  ga.col_scale = B.unscale;
-  ga.cs_b = bsB;
-  ga.spin_limit = h->spin_limit;
-  ga.status = h->d_status;
-  const long long tiles = (long long)batch * ((A.rows + 127) / 128) * ((B.rows + 127) / 128);
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, h->sm_count));
-  ++h->launches;
-  SOX_CUDA_TRY(launch_gemm_f16x2(maps, ga, grid, s));
+  for (int k0 = 0; k0 < A.Kp2; k0 += kKChunk) {
+    const int kw = std::min(kKChunk, A.Kp2 - k0);
+    CUtensorMap maps[6];
+    std::string err;
+    if (!make_tmap_f16_3d_rs(&maps[0], A.hi + k0, kw, A.Kp2, A.rows, A.batch, bsA * A.Kp2, 64, 128, &err) ||
+        !make_tmap_f16_3d_rs(&maps[1], A.lo + k0, kw, A.Kp2, A.rows, A.batch, bsA * A.Kp2, 64, 128, &err) ||
+        !make_tmap_f16_3d_rs(&maps[2], B.hi + k0, kw, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err) ||
+        !make_tmap_f16_3d_rs(&maps[3], B.lo + k0, kw, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err))
+      return {SOX_ERR_CUDA, "cgemm_tc: " + err};
+    maps[4] = maps[0];   // no TMA stores in FP32 mode; valid maps for the prefetch
+    maps[5] = maps[1];
+    GemmTcArgs ga;
+    ga.M = A.rows;
+    ga.Ncols = B.rows;
+    ga.Kp = kw;
+    ga.batch = batch;
+    ga.batchA_shared = (A.batch == 1);
+    ga.batchB_shared = (B.batch == 1);
+    ga.idxA = idxA;
+    ga.idxB = idxB;
+    ga.mode = kStoreF32;
+    ga.Cf = C;
+    ga.ldc = ldc;
+    ga.sCb = sCb;
+    ga.alpha = alpha;
+    ga.accumulate = (accumulate || k0 > 0) ? 1 : 0;
+    ga.row_scale = A.unscale;
+    ga.rs_b = bsA;
+    ga.col_scale = B.unscale;
+    ga.cs_b = bsB;
+    ga.spin_limit = h->spin_limit;
+    ga.status = h->d_status;
+    const long long tiles = (long long)batch * ((A.rows + 127) / 128) * ((B.rows + 127) / 128);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, h->sm_count));
+    ++h->launches;
+    SOX_CUDA_TRY(launch_gemm_f16x2(maps, ga, grid, s));
+  }
   return Status::ok();
 }
 

@@ -21,6 +21,11 @@ bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t 
 
 bool make_tmap_f16_3d_bs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                          uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err) {
+  return make_tmap_f16_3d_rs(map, base, d0, d0, d1, d2, batch_stride, box0, box1, err);
+}
+
+bool make_tmap_f16_3d_rs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t row_stride, uint64_t d1,
+                         uint64_t d2, uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -34,7 +39,7 @@ bool make_tmap_f16_3d_bs(CUtensorMap *map, const void *base, uint64_t d0, uint64
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   cuuint64_t dims[3] = {d0, d1, d2};
-  cuuint64_t strides[2] = {d0 * 2, batch_stride * 2};
+  cuuint64_t strides[2] = {row_stride * 2, batch_stride * 2};
   cuuint32_t box[3] = {box0, box1, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims, strides, box,

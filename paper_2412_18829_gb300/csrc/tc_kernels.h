@@ -53,6 +53,9 @@ bool make_tmap_f16_3d(CUtensorMap *map, const void *base, uint64_t d0, uint64_t 
 // the same with `batch_stride` elements between consecutive d2 slices (a multiple of 8)
 bool make_tmap_f16_3d_bs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                          uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err);
+// and with `row_stride` elements between rows (>= d0, a multiple of 8): a window of d0 columns
+bool make_tmap_f16_3d_rs(CUtensorMap *map, const void *base, uint64_t d0, uint64_t row_stride, uint64_t d1,
+                         uint64_t d2, uint64_t batch_stride, uint32_t box0, uint32_t box1, std::string *err);
 size_t tc_smem_bytes();
 bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
                            uint64_t batch, std::string *err);

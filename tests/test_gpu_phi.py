@@ -180,6 +180,19 @@ def test_split_adjoint_matches_oracle_autograd(env, n, N, n_tau, n_spin):
     assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max()
 
 
+@pytest.mark.parametrize("n,N,n_tau", [(150, 300, 2), (131, 263, 3)])
+def test_split_adjoint_beyond_one_k_tile(env, n, N, n_tau):
+    """n > 128 and odd sizes: split rows of several 64-wide chunks, padded row lengths."""
+    torch, pkg, h64 = env
+    w = synth.molecule(27, n, N, n_tau, 3.0)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    rX, rV = _grads_with(torch, pkg, h64, w, wt, [1.0])
+    with pkg.Handle("f16x2") as h:
+        gX, gV = _grads_with(torch, pkg, h, w, wt, [1.0])
+    assert np.abs(gX - rX).max() <= 2e-5 * np.abs(rX).max()
+    assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max()
+
+
 def test_split_adjoint_matches_fp64_adjoint_on_smallest_batch_instance(env):
     torch, pkg, h64 = env
     w = synth.c4_instance(synth.c4_smallest(1)[0])
