@@ -125,3 +125,23 @@ def sosex_static_sigma(X: np.ndarray, V: np.ndarray, W: np.ndarray, G: np.ndarra
     U1, U2 = (W0, V0) if slot == 1 else (V0, W0)
     return np.stack([sigma_tau(X0, U1, U2, G[s, 0], route, taus, dtype)
                      for s in range(G.shape[0])])[:, None]
+
+
+def g3w2_static_sigma(X: np.ndarray, W: np.ndarray, G: np.ndarray, route: str = "chain", taus=None,
+                      dtype=np.complex128) -> np.ndarray:
+    """G3W2 with static screening: both interactions screened, SOX(W(0), W(0)) (Sec. III C)."""
+    return sox_sigma(X, W if W.ndim == 3 else W[None], G, route, taus, dtype)
+
+
+def sosex2_static_sigma(X: np.ndarray, V: np.ndarray, W: np.ndarray, G: np.ndarray, route: str = "chain",
+                        taus=None, dtype=np.complex128) -> np.ndarray:
+    """2SOSEX with static screening, the paper's decomposition of Sec. III C with
+    W_d = W(0) - v:  SOX(v, v) + SOX(v, W_d) + SOX(W_d, v)."""
+    X0, V0 = X[0], V[0]
+    W0 = W[0] if W.ndim == 3 else W
+    Wd = W0 - V0
+    out = []
+    for s in range(G.shape[0]):
+        terms = [sigma_tau(X0, U1, U2, G[s, 0], route, taus, dtype) for U1, U2 in ((V0, V0), (V0, Wd), (Wd, V0))]
+        out.append(terms[0] + terms[1] + terms[2])
+    return np.stack(out)[:, None]

@@ -169,3 +169,35 @@ def test_sosex_static_slots():
     for j in range(w.n_tau):
         np.testing.assert_allclose(s1[0, 0, j], sox.sigma_bruteforce(v1, v2, w.G[0, 0, j], Gm[j]), atol=1e-16)
         np.testing.assert_allclose(s2[0, 0, j], sox.sigma_bruteforce(v2, v1, w.G[0, 0, j], Gm[j]), atol=1e-16)
+
+
+def test_screened_compositions_follow_the_dielectric_scalings():
+    """With W = v / eps exactly, the paper's effective-dielectric argument (Sec. III C) is
+    exact: SOSEX = SOX(v,v)/eps, G3W2 = SOX(v,v)/eps^2, 2SOSEX = (2 - eps)/eps SOX(v,v)."""
+    w = synth.tiny(4, 9, n_tau=4)
+    eps = 1.7
+    W = w.V / eps
+    base = sox.sox_sigma(w.X, w.V, w.G)
+    scale = np.abs(base).max()
+    assert np.abs(sox.sosex_static_sigma(w.X, w.V, W, w.G, slot=2) - base / eps).max() < 1e-14 * scale
+    assert np.abs(sox.g3w2_static_sigma(w.X, W, w.G) - base / eps ** 2).max() < 1e-14 * scale
+    assert np.abs(sox.sosex2_static_sigma(w.X, w.V, W, w.G) - (2 - eps) / eps * base).max() < 1e-14 * scale
+
+
+def test_g3w2_decomposition_identity():
+    """G3W2 = 2SOSEX + SOX(W_d, W_d) and 2SOSEX = SOSEX + SOX(W_d, v) with a generic symmetric
+    W (Sec. III C), each term from the brute-force 4-index route."""
+    w = synth.tiny(3, 7, n_tau=3)
+    rng = np.random.default_rng(4)
+    z = rng.standard_normal((7, 7)) / 7
+    W = w.V[0] + z @ z.T - 0.3 * w.V[0]
+    Wd = W - w.V[0]
+    X, V, G = w.X[0], w.V[0], w.G[0, 0]
+    br = lambda U1, U2: sox.sigma_tau(X, U1, U2, G, route="brute")   # noqa: E731
+    g3w2 = sox.g3w2_static_sigma(w.X, W[None], w.G)[0, 0]
+    two = sox.sosex2_static_sigma(w.X, w.V, W[None], w.G)[0, 0]
+    sosex = sox.sosex_static_sigma(w.X, w.V, W[None], w.G, slot=2)[0, 0]
+    scale = np.abs(g3w2).max()
+    assert np.abs(g3w2 - (two + br(Wd, Wd))).max() < 1e-13 * scale
+    assert np.abs(two - (sosex + br(Wd, V))).max() < 1e-13 * scale
+    assert np.abs(g3w2 - br(W, W)).max() < 1e-13 * scale
