@@ -175,6 +175,20 @@ SOX_API int sosex_static_sigma(sox_handle h, const sox_problem *p, const double 
                        const double *V, const double *W0, int slot, double *Sigma,
                        void *stream);
 
+/* Compositions of statically screened SOX (Sec. III C, the G3W2 decomposition
+ * with W_d = W(0) - v):
+ *   g3w2_static_sigma:   Sigma^G3W2stat = SOX(W0, W0), both interactions screened;
+ *   sosex2_static_sigma: Sigma^2SOSEXstat = SOX(v, v) + SOX(v, W_d) + SOX(W_d, v),
+ *                        computed as SOX(v, W0) + SOX(W0 - v, v).
+ * Layouts and precision as sox_sigma (molecules and solids; V, W0 [n_q][N][N]).
+ * sosex2_static_sigma takes device tensors only (SOX_ERR_INVALID_ARG otherwise),
+ * keeps its partial result and W_d in a second buffer of the handle that grows
+ * on demand (the growth synchronises the device), and costs two SOX builds. */
+SOX_API int g3w2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                              const double *W0, double *Sigma, void *stream);
+SOX_API int sosex2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                                const double *V, const double *W0, double *Sigma, void *stream);
+
 /* General static SOX(U1, U2) (Eq. sox with two static interactions). */
 SOX_API int sox_sigma_general(sox_handle h, const sox_problem *p, const double *G, const double *X,
                       const double *U1, const double *U2, double *Sigma, void *stream);

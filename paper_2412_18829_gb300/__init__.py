@@ -24,6 +24,8 @@ from ._binding import (  # noqa: F401
     sox_reserve,
     sox_sigma,
     sox_sigma_batch,
+    g3w2_static_sigma,
+    sosex2_static_sigma,
     SigmaBatchPlan,
     sox_sigma_fp64_noalloc,
     sox_sigma_general,

@@ -65,6 +65,8 @@ _SIGS = {
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
     "sox_sigma_fp64_noalloc": ([ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
+    "g3w2_static_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
+    "sosex2_static_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P], _I),
     "sox_sigma_batch_plan": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sox_plan_launch": ([_P, _P], _I),
@@ -227,6 +229,16 @@ def sox_sigma_general(h: Handle, p: sox_problem, G, X, U1, U2, Sigma, stream=Non
 def sosex_static_sigma(h: Handle, p: sox_problem, G, X, V, W0, Sigma, slot: int = 1, stream=None):
     h.check(lib().sosex_static_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(W0),
                                      int(slot), _ptr(Sigma), _stream(stream)))
+
+
+def g3w2_static_sigma(h: Handle, p: sox_problem, G, X, W0, Sigma, stream=None):
+    h.check(lib().g3w2_static_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(W0), _ptr(Sigma),
+                                    _stream(stream)))
+
+
+def sosex2_static_sigma(h: Handle, p: sox_problem, G, X, V, W0, Sigma, stream=None):
+    h.check(lib().sosex2_static_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(W0), _ptr(Sigma),
+                                      _stream(stream)))
 
 
 def sox_pi0(h: Handle, p: sox_problem, G, X, w, Pi0, stream=None):

@@ -333,6 +333,42 @@ Status run_sigma(sox_handle h, const sox_problem *p, const double *G, const doub
   return call.end();
 }
 
+// dst = a - b
+__global__ void k_sub_f64(const double *a, const double *b, double *dst, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = a[e] - b[e];
+}
+
+// Grows the handle's second buffer (synchronises the device when it reallocates).
+Status ensure_aux(sox_handle h, size_t bytes) {
+  if (bytes <= h->aux_bytes) return Status::ok();
+  if (h->aux) {
+    SOX_CUDA_TRY(cudaDeviceSynchronize());
+    SOX_CUDA_TRY(cudaFree(h->aux));
+    h->aux = nullptr;
+    h->aux_bytes = 0;
+  }
+  if (cudaMalloc(&h->aux, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return {SOX_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes for partial results failed"};
+  }
+  h->aux_bytes = bytes;
+  return Status::ok();
+}
+
+Status device_tensor(sox_handle h, const void *ptr, const char *what) {
+  if (!ptr) return {SOX_ERR_INVALID_ARG, std::string(what) + " is NULL"};
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return {SOX_ERR_INVALID_ARG, std::string(what) + ": not a device pointer"};
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != h->device)
+    return {SOX_ERR_INVALID_ARG, std::string(what) + ": composed entry points take device memory of the handle's GPU"};
+  return Status::ok();
+}
+
 }  // namespace
 
 // ================================ C ABI ===================================
@@ -387,6 +423,7 @@ int sox_destroy(sox_handle h) {
   sox::tc_release(h);
   sox_profile_enable(h, 0);
   if (h->ws) cudaFree(h->ws);
+  if (h->aux) cudaFree(h->aux);
   if (h->d_status) cudaFree(h->d_status);
   if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
   delete h;
@@ -562,6 +599,47 @@ int sosex_static_sigma(sox_handle h, const sox_problem *p, const double *G, cons
   if (V == W0 && V) return finish(h, {SOX_ERR_INVALID_ARG, "V and W0 must be distinct buffers"});
   const double *u1 = slot == 1 ? W0 : V, *u2 = slot == 1 ? V : W0;
   return finish(h, run_sigma(h, p, G, X, u1, u2, Sigma, stream));
+}
+
+int g3w2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X, const double *W0,
+                      double *Sigma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  return finish(h, run_sigma(h, p, G, X, W0, W0, Sigma, stream));
+}
+
+int sosex2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X, const double *V,
+                        const double *W0, double *Sigma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    if (!p) return {SOX_ERR_INVALID_ARG, "problem descriptor is NULL"};
+    SOX_TRY(validate(p, false));
+    if (V == W0) return {SOX_ERR_INVALID_ARG, "V and W0 must be distinct buffers"};
+    SOX_TRY(bind_device(h));
+    SOX_TRY(device_tensor(h, G, "G"));
+    SOX_TRY(device_tensor(h, X, "X"));
+    SOX_TRY(device_tensor(h, V, "V"));
+    SOX_TRY(device_tensor(h, W0, "W0"));
+    SOX_TRY(device_tensor(h, Sigma, "Sigma"));
+    const long long mult = p->dtype == SOX_COMPLEX128 ? 2 : 1;
+    const long long nk = (long long)p->nk[0] * p->nk[1] * p->nk[2];
+    const long long nsig = mult * p->n_spin * nk * p->n_tau * (long long)p->n * p->n;
+    const long long nV = mult * nk * (long long)p->N * p->N;
+    SOX_TRY(ensure_aux(h, sox::aligned_bytes(nsig, 8) + sox::aligned_bytes(nV, 8)));
+    double *part = static_cast<double *>(h->aux);
+    double *Wd = part + (sox::aligned_bytes(nsig, 8) / 8);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((nV + 255) / 256, 65535 * 8));
+    k_sub_f64<<<grid, 256, 0, s>>>(W0, V, Wd, nV);     // W_d = W0 - v
+    ++h->launches;
+    SOX_CUDA_TRY(cudaGetLastError());
+    SOX_TRY(run_sigma(h, p, G, X, V, W0, Sigma, stream));   // SOX(v, W0) = SOX(v,v) + SOX(v, W_d)
+    SOX_TRY(run_sigma(h, p, G, X, Wd, V, part, stream));    // SOX(W_d, v)
+    sox::launch_add_f64(Sigma, part, Sigma, nsig, s);
+    ++h->launches;
+    SOX_CUDA_TRY(cudaGetLastError());
+    return Status::ok();
+  }();
+  return finish(h, st);
 }
 
 int sox_pi0(sox_handle h, const sox_problem *p, const double *G, const double *X,

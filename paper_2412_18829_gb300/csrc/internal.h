@@ -19,6 +19,8 @@ struct sox_context {
   size_t ws_limit = 0;       // chunk budget override (sox_options.workspace_limit), 0 = defaults
   void *ws = nullptr;        // device workspace
   size_t ws_bytes = 0;
+  void *aux = nullptr;       // second device buffer: partial results of composed entry points
+  size_t aux_bytes = 0;
   int *d_status = nullptr;   // device status word for bounded waits
   int sm_count = 0;
   bool autotune = true;      // time the fused-kernel variants on the first call per shape

@@ -149,3 +149,22 @@ def test_single_k_complex_dynamic_equals_real_molecule(env):
     got = _run_dynamic(env, wm, wm.G, Tf, Ti, Wd[None])
     ref = dynamic.sosex_dynamic_sigma(wm.X, wm.V, Wd, Tf, Ti, wm.G)
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x2"])
+def test_solid_2sosex_static(env, prec):
+    """2SOSEXstat for a solid: SOX(v, W0) + SOX(W0 - v, v) against the oracle's terms."""
+    torch, pkg, hs = env
+    w = synth.solid(15, (1, 1, 2), 4, 12, 3, 10.0)
+    rng = np.random.default_rng(6)
+    W = np.empty_like(w.V)
+    for q in range(W.shape[0]):     # on a 1x1x2 mesh every q equals -q: real symmetric W^q
+        z = rng.standard_normal((w.N, w.N)) / w.N
+        W[q] = 0.6 * w.V[q].real + 0.05 * z @ z.T
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta, nk=w.nk, dtype=1)
+    G, X, V, Wt = (_dev(torch, a.astype(complex)) for a in (w.G, w.X, w.V, W))
+    S = torch.full_like(G, complex("nan"))
+    pkg.sosex2_static_sigma(hs[prec], p, G, X, V, Wt, S)
+    pkg.sox_check_device(hs[prec])
+    ref = kpoints.sox_sigma(w.X, w.V, w.G, w.nk, U2=W) + kpoints.sox_sigma(w.X, W - w.V, w.G, w.nk, U2=w.V)
+    check(S.cpu().numpy(), ref, prec, "solid 2SOSEXstat")

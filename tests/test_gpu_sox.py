@@ -262,3 +262,24 @@ def test_autotuned_and_fixed_fused_kernel_agree(env, n, N):
     for r in out.values():
         check(r, ref, "f16x2", "autotune")
     assert np.abs(out[True] - out[False]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_g3w2_and_2sosex_static(env, prec):
+    """The screened compositions of Sec. III C on the GPU against the oracle's decomposition."""
+    torch, pkg, hs = env
+    w = synth.molecule(28, 18, 90, 6, 100.0, n_spin=2)
+    rng = np.random.default_rng(5)
+    z = rng.standard_normal((w.N, w.N)) / w.N
+    W = (0.6 * w.V[0] + 0.05 * z @ z.T)[None]
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V, Wd = to_dev(torch, w.G, w.X, w.V, W)
+    S = torch.full_like(G, float("nan"))
+    pkg.g3w2_static_sigma(hs[prec], p, G, X, Wd, S)
+    check(S.cpu().numpy(), sox.g3w2_static_sigma(w.X, W, w.G, dtype=np.float64), prec, "G3W2stat")
+    S.fill_(float("nan"))
+    pkg.sosex2_static_sigma(hs[prec], p, G, X, V, Wd, S)
+    pkg.sox_check_device(hs[prec])
+    check(S.cpu().numpy(), sox.sosex2_static_sigma(w.X, w.V, W, w.G, dtype=np.float64), prec, "2SOSEXstat")
+    with pytest.raises(pkg.SoxError):
+        pkg.sosex2_static_sigma(hs[prec], p, w.G, X, V, Wd, S)     # host G: device tensors only
