@@ -233,9 +233,10 @@ FP32_PEAK_TFLOPS = 78.4
 class MoleculeCase(Case):
     """Bare SOX (c0, c1) or statically screened SOSEX with Pi(0) and W(0) per step (c2)."""
 
-    def __init__(self, torch, pkg, w, prec, dev, stream, screened: bool):
+    def __init__(self, torch, pkg, w, prec, dev, stream, screened: bool, variant: str = "sosex"):
         self.torch, self.pkg, self.w, self.prec, self.dev, self.stream = torch, pkg, w, prec, dev, stream
         self.screened = screened
+        self.variant = variant
         self.name = w.name
         self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
         self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
@@ -254,8 +255,10 @@ class MoleculeCase(Case):
         self.h = pkg.Handle(prec, device=dev.index or 0)
         self.config = {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
                        "beta": w.beta, "precision": prec,
-                       "step": ("Pi(0) + W(0) + SOX(W(0), v) through the C ABI" if screened
-                                else "bare SOX(v, v) through the C ABI")}
+                       "step": ({"sosex": "Pi(0) + W(0) + SOX(W(0), v)",
+                                 "2sosex": "Pi(0) + W(0) + 2SOSEX = SOX(v, W(0)) + SOX(W(0) - v, v)",
+                                 "g3w2": "Pi(0) + W(0) + SOX(W(0), W(0))"}[variant] + " through the C ABI"
+                                if screened else "bare SOX(v, v) through the C ABI")}
 
     def _run(self, h, G, X, V, S, Pi, W0, stream):
         pkg = self.pkg
@@ -264,7 +267,12 @@ class MoleculeCase(Case):
             return
         pkg.sox_pi0(h, self.p, G, X, self.wts if isinstance(G, self.torch.Tensor) else self.wts_h, Pi, stream)
         pkg.sox_w_static(h, self.p, V, Pi[0:1] if self.w.n_spin == 1 else Pi.sum(0, keepdim=True), W0, stream)
-        pkg.sosex_static_sigma(h, self.p, G, X, V, W0, S, slot=1, stream=stream)
+        if self.variant == "2sosex":
+            pkg.sosex2_static_sigma(h, self.p, G, X, V, W0, S, stream=stream)
+        elif self.variant == "g3w2":
+            pkg.g3w2_static_sigma(h, self.p, G, X, W0, S, stream=stream)
+        else:
+            pkg.sosex_static_sigma(h, self.p, G, X, V, W0, S, slot=1, stream=stream)
 
     def step(self):
         self._run(self.h, self.G, self.X, self.V, self.S, self.Pi, self.W0, self.stream)
@@ -283,7 +291,8 @@ class MoleculeCase(Case):
 
     def hot_flops_per_step(self):
         w = self.w
-        return (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * w.n_tau * w.n_spin
+        builds = 2 if (self.screened and self.variant == "2sosex") else 1   # 2SOSEX: two SOX builds
+        return builds * (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * w.n_tau * w.n_spin
 
     def accuracy(self) -> dict:
         from oracle import grid as ogrid, screening as oscr, sox as osox
@@ -302,8 +311,14 @@ class MoleculeCase(Case):
         wt = ogrid.clenshaw_curtis(w.n_tau, w.beta)
         Pi = oscr.pi0_quadrature(w.X[0], w.G[0, 0], wt).real
         Wr = oscr.w_static(w.V[0], 0.5 * (Pi + Pi.T))
-        j = w.n_tau // 2
-        ref = osox.sigma_tau(w.X[0], Wr, w.V[0], w.G[0, 0], taus=[j], dtype=np.float64)
+        j = 0   # the largest |Sigma|
+        st = lambda U1, U2: osox.sigma_tau(w.X[0], U1, U2, w.G[0, 0], taus=[j], dtype=np.float64)  # noqa: E731
+        if self.variant == "2sosex":
+            ref = st(w.V[0], Wr) + st(Wr - w.V[0], w.V[0])
+        elif self.variant == "g3w2":
+            ref = st(Wr, Wr)
+        else:
+            ref = st(Wr, w.V[0])
         err = float(np.abs(out[0, 0, [j]] - ref).max())
         werr = float((self.W0[0].cpu() - self.torch.from_numpy(Wr)).abs().max()) / float(np.abs(Wr).max())
         return {"max_abs_err_Ha_vs_oracle": err, "max_rel_err_vs_oracle": err / float(np.abs(ref).max()),
@@ -565,7 +580,8 @@ def make_case(args, torch, pkg, dev, stream, rank, world):
     w = workload(args.workload)
     if args.workload == "c3":
         return SolidCase(torch, pkg, w, args.precision, dev, stream)
-    return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"))
+    return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"),
+                        variant=args.variant)
 
 
 def run_ours(args):
@@ -729,6 +745,8 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--forward-only", action="store_true", help="batch workload: no dPhi/dX, dPhi/dV")
+    ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
+                    help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -181,9 +181,10 @@ SOX_API int sosex_static_sigma(sox_handle h, const sox_problem *p, const double 
  *   sosex2_static_sigma: Sigma^2SOSEXstat = SOX(v, v) + SOX(v, W_d) + SOX(W_d, v),
  *                        computed as SOX(v, W0) + SOX(W0 - v, v).
  * Layouts and precision as sox_sigma (molecules and solids; V, W0 [n_q][N][N]).
- * sosex2_static_sigma takes device tensors only (SOX_ERR_INVALID_ARG otherwise),
- * keeps its partial result and W_d in a second buffer of the handle that grows
- * on demand (the growth synchronises the device), and costs two SOX builds. */
+ * sosex2_static_sigma keeps its partial result, W_d and any host tensors it
+ * stages in a second buffer of the handle that grows on demand (the growth
+ * synchronises the device); with a host Sigma it synchronises the stream at
+ * the end.  It costs two SOX builds. */
 SOX_API int g3w2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                               const double *W0, double *Sigma, void *stream);
 SOX_API int sosex2_static_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,

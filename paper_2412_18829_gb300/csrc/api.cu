@@ -357,18 +357,6 @@ Status ensure_aux(sox_handle h, size_t bytes) {
   return Status::ok();
 }
 
-Status device_tensor(sox_handle h, const void *ptr, const char *what) {
-  if (!ptr) return {SOX_ERR_INVALID_ARG, std::string(what) + " is NULL"};
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return {SOX_ERR_INVALID_ARG, std::string(what) + ": not a device pointer"};
-  }
-  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != h->device)
-    return {SOX_ERR_INVALID_ARG, std::string(what) + ": composed entry points take device memory of the handle's GPU"};
-  return Status::ok();
-}
-
 }  // namespace
 
 // ================================ C ABI ===================================
@@ -613,30 +601,60 @@ int sosex2_static_sigma(sox_handle h, const sox_problem *p, const double *G, con
   Status st = [&]() -> Status {
     if (!p) return {SOX_ERR_INVALID_ARG, "problem descriptor is NULL"};
     SOX_TRY(validate(p, false));
+    if (!G || !X || !V || !W0 || !Sigma) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
     if (V == W0) return {SOX_ERR_INVALID_ARG, "V and W0 must be distinct buffers"};
     SOX_TRY(bind_device(h));
-    SOX_TRY(device_tensor(h, G, "G"));
-    SOX_TRY(device_tensor(h, X, "X"));
-    SOX_TRY(device_tensor(h, V, "V"));
-    SOX_TRY(device_tensor(h, W0, "W0"));
-    SOX_TRY(device_tensor(h, Sigma, "Sigma"));
     const long long mult = p->dtype == SOX_COMPLEX128 ? 2 : 1;
     const long long nk = (long long)p->nk[0] * p->nk[1] * p->nk[2];
     const long long nsig = mult * p->n_spin * nk * p->n_tau * (long long)p->n * p->n;
+    const long long nX = mult * nk * (long long)p->N * p->n;
     const long long nV = mult * nk * (long long)p->N * p->N;
-    SOX_TRY(ensure_aux(h, sox::aligned_bytes(nsig, 8) + sox::aligned_bytes(nV, 8)));
-    double *part = static_cast<double *>(h->aux);
-    double *Wd = part + (sox::aligned_bytes(nsig, 8) / 8);
+    // host tensors are staged through the second buffer: [part][W_d][G][X][V][W0][Sigma]
+    const void *ptrs[5] = {G, X, V, W0, Sigma};
+    const long long cnt[5] = {nsig, nX, nV, nV, nsig};
+    bool host[5];
+    for (int i = 0; i < 5; ++i) {
+      cudaPointerAttributes a{};
+      if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
+        cudaGetLastError();
+        a.type = cudaMemoryTypeUnregistered;
+      }
+      host[i] = (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered);
+      if (!host[i] && a.device != h->device)
+        return {SOX_ERR_INVALID_ARG, "device tensors must live on the handle's GPU"};
+    }
+    size_t need = sox::aligned_bytes(nsig, 8) + sox::aligned_bytes(nV, 8);
+    for (int i = 0; i < 5; ++i)
+      if (host[i]) need += sox::aligned_bytes(cnt[i], 8);
+    SOX_TRY(ensure_aux(h, need));
+    char *base = static_cast<char *>(h->aux);
+    double *part = reinterpret_cast<double *>(base);
+    double *Wd = reinterpret_cast<double *>(base + sox::aligned_bytes(nsig, 8));
+    size_t off = sox::aligned_bytes(nsig, 8) + sox::aligned_bytes(nV, 8);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *dev[5];
+    for (int i = 0; i < 5; ++i) {
+      if (!host[i]) {
+        dev[i] = const_cast<double *>(static_cast<const double *>(ptrs[i]));
+        continue;
+      }
+      dev[i] = reinterpret_cast<double *>(base + off);
+      off += sox::aligned_bytes(cnt[i], 8);
+      if (i < 4) SOX_CUDA_TRY(cudaMemcpyAsync(dev[i], ptrs[i], 8 * (size_t)cnt[i], cudaMemcpyHostToDevice, s));
+    }
     const int grid = (int)std::max<long long>(1, std::min<long long>((nV + 255) / 256, 65535 * 8));
-    k_sub_f64<<<grid, 256, 0, s>>>(W0, V, Wd, nV);     // W_d = W0 - v
+    k_sub_f64<<<grid, 256, 0, s>>>(dev[3], dev[2], Wd, nV);     // W_d = W0 - v
     ++h->launches;
     SOX_CUDA_TRY(cudaGetLastError());
-    SOX_TRY(run_sigma(h, p, G, X, V, W0, Sigma, stream));   // SOX(v, W0) = SOX(v,v) + SOX(v, W_d)
-    SOX_TRY(run_sigma(h, p, G, X, Wd, V, part, stream));    // SOX(W_d, v)
-    sox::launch_add_f64(Sigma, part, Sigma, nsig, s);
+    SOX_TRY(run_sigma(h, p, dev[0], dev[1], dev[2], dev[3], dev[4], stream));   // SOX(v, W0)
+    SOX_TRY(run_sigma(h, p, dev[0], dev[1], Wd, dev[2], part, stream));         // SOX(W_d, v)
+    sox::launch_add_f64(dev[4], part, dev[4], nsig, s);
     ++h->launches;
     SOX_CUDA_TRY(cudaGetLastError());
+    if (host[4]) {
+      SOX_CUDA_TRY(cudaMemcpyAsync(Sigma, dev[4], 8 * (size_t)nsig, cudaMemcpyDeviceToHost, s));
+      SOX_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     return Status::ok();
   }();
   return finish(h, st);

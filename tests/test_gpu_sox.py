@@ -281,5 +281,6 @@ def test_g3w2_and_2sosex_static(env, prec):
     pkg.sosex2_static_sigma(hs[prec], p, G, X, V, Wd, S)
     pkg.sox_check_device(hs[prec])
     check(S.cpu().numpy(), sox.sosex2_static_sigma(w.X, w.V, W, w.G, dtype=np.float64), prec, "2SOSEXstat")
-    with pytest.raises(pkg.SoxError):
-        pkg.sosex2_static_sigma(hs[prec], p, w.G, X, V, Wd, S)     # host G: device tensors only
+    Sh = np.full_like(w.G, np.nan)
+    pkg.sosex2_static_sigma(hs[prec], p, w.G, X, V, W, Sh)      # host G and Sigma are staged
+    assert np.array_equal(Sh, S.cpu().numpy())
