@@ -233,10 +233,12 @@ FP32_PEAK_TFLOPS = 78.4
 class MoleculeCase(Case):
     """Bare SOX (c0, c1) or statically screened SOSEX with Pi(0) and W(0) per step (c2)."""
 
-    def __init__(self, torch, pkg, w, prec, dev, stream, screened: bool, variant: str = "sosex"):
+    def __init__(self, torch, pkg, w, prec, dev, stream, screened: bool, variant: str = "sosex",
+                 tau_shard=None):
         self.torch, self.pkg, self.w, self.prec, self.dev, self.stream = torch, pkg, w, prec, dev, stream
         self.screened = screened
         self.variant = variant
+        self.tau_shard = tau_shard   # (rank, world, dist): this rank's mirror pairs of one build
         self.name = w.name
         self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
         self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
@@ -253,6 +255,19 @@ class MoleculeCase(Case):
         self.Pi = torch.empty(w.n_spin, w.N, w.N, dtype=torch.float64, device=dev)
         self.W0 = torch.empty(1, w.N, w.N, dtype=torch.float64, device=dev)
         self.h = pkg.Handle(prec, device=dev.index or 0)
+        if tau_shard is not None:
+            from paper_2412_18829_gb300 import sharding
+
+            rank, world, _ = tau_shard
+            self.orders = sharding.tau_shards(w.n_tau, world)
+            order = self.orders[rank]
+            self.kmax = max(len(o) for o in self.orders)
+            self.p = pkg.problem(w.n, w.N, len(order), w.n_spin, w.beta)
+            self.G = self.G[:, :, order].contiguous()
+            self.S = torch.empty_like(self.G)
+            self.padded = torch.zeros(w.n_spin, 1, self.kmax, w.n, w.n, dtype=torch.float64, device=dev)
+            self.gathered = torch.empty(world, w.n_spin, 1, self.kmax, w.n, w.n, dtype=torch.float64, device=dev)
+            self.units = 1.0 / world
         self.config = {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
                        "beta": w.beta, "precision": prec,
                        "step": ({"sosex": "Pi(0) + W(0) + SOX(W(0), v)",
@@ -276,14 +291,34 @@ class MoleculeCase(Case):
 
     def step(self):
         self._run(self.h, self.G, self.X, self.V, self.S, self.Pi, self.W0, self.stream)
+        if self.tau_shard is not None:   # the one exchange: every rank receives every rank's slices
+            _, world, dist = self.tau_shard
+            k = self.S.shape[2]
+            self.padded[:, :, :k].copy_(self.S)
+            if dist is None:
+                self.gathered[0].copy_(self.padded)
+            else:
+                dist.all_gather_into_tensor(self.gathered, self.padded)
 
     def e2e_step(self):
-        if not hasattr(self, "Gh"):
-            pin = lambda a: self.torch.from_numpy(a).pin_memory().numpy()   # noqa: E731
-            self.Gh, self.Xh, self.Vh = pin(self.w.G), pin(self.w.X), pin(self.w.V)
-            self.Sh = pin(np.empty_like(self.w.G))
-        self._run(self.h, self.Gh, self.Xh, self.Vh, self.Sh, self.Pi, self.W0, self.stream)
         w = self.w
+        if not hasattr(self, "Gh"):
+            pin = lambda a: self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()   # noqa: E731
+            Gsrc = w.G if self.tau_shard is None else w.G[:, :, self.orders[self.tau_shard[0]]]
+            self.Gh, self.Xh, self.Vh = pin(Gsrc), pin(w.X), pin(w.V)
+            self.Sh = pin(np.empty_like(Gsrc))
+        self._run(self.h, self.Gh, self.Xh, self.Vh, self.Sh, self.Pi, self.W0, self.stream)
+        if self.tau_shard is not None:   # the slices of every rank, back on this rank's host
+            _, world, dist = self.tau_shard
+            k = self.Sh.shape[2]
+            self.padded[:, :, :k].copy_(self.torch.from_numpy(self.Sh), non_blocking=True)
+            if dist is None:
+                self.gathered[0].copy_(self.padded)
+            else:
+                dist.all_gather_into_tensor(self.gathered, self.padded)
+            gathered_h = self.gathered.cpu()
+            return (self.Gh.nbytes + w.X.nbytes + w.V.nbytes + self.Sh.nbytes,
+                    self.Sh.nbytes + gathered_h.numel() * 8)
         h2d = w.G.nbytes + w.X.nbytes + w.V.nbytes
         if self.screened:   # Pi(0) reads G, X, w; W(0) reads V; SOSEX reads G, X, V again
             h2d += w.G.nbytes + w.X.nbytes + self.wts_h.nbytes + w.V.nbytes
@@ -292,13 +327,20 @@ class MoleculeCase(Case):
     def hot_flops_per_step(self):
         w = self.w
         builds = 2 if (self.screened and self.variant == "2sosex") else 1   # 2SOSEX: two SOX builds
-        return builds * (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * w.n_tau * w.n_spin
+        return builds * (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * self.p.n_tau * w.n_spin
 
     def accuracy(self) -> dict:
         from oracle import grid as ogrid, screening as oscr, sox as osox
 
         w = self.w
-        out = self.S.cpu().numpy()
+        if self.tau_shard is not None:   # Sigma of the whole build from the gathered slices
+            from paper_2412_18829_gb300 import sharding
+
+            g = self.gathered.cpu()
+            out = sharding.assemble([g[r][:, :, :len(o)] for r, o in enumerate(self.orders)], self.orders,
+                                    w.n_tau).numpy()
+        else:
+            out = self.S.cpu().numpy()
         if not self.screened:
             taus = [0, w.n_tau - 1]
             err = smax = 0.0
@@ -326,7 +368,7 @@ class MoleculeCase(Case):
                 "oracle_sample": f"tau index {j}; oracle W(0) from its own Pi(0)"}
 
     def fp64_compare(self, value: float) -> dict:
-        if self.prec == "fp64":
+        if self.prec == "fp64" or self.tau_shard is not None:
             return {}
         torch = self.torch
         with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
@@ -574,14 +616,15 @@ class BatchCase(Case):
         return out
 
 
-def make_case(args, torch, pkg, dev, stream, rank, world):
+def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
     if args.workload == "c4":
         return BatchCase(torch, pkg, args.precision, dev, stream, rank, world, backward=not args.forward_only)
     w = workload(args.workload)
     if args.workload == "c3":
         return SolidCase(torch, pkg, w, args.precision, dev, stream)
+    shard = (rank, world, dist_mod) if (args.shard == "tau" and args.workload in ("c0", "c1")) else None
     return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"),
-                        variant=args.variant)
+                        variant=args.variant, tau_shard=shard)
 
 
 def run_ours(args):
@@ -604,7 +647,7 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    case = make_case(args, torch, pkg, dev, stream, rank, world)
+    case = make_case(args, torch, pkg, dev, stream, rank, world, dist)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -693,7 +736,7 @@ def run_ours(args):
         roof["kernel"] = case.hot
         w = getattr(case, "w", None)
         if isinstance(case, MoleculeCase) and (w.n, w.N) == BCD_TRAFFIC["shape"] and hot_n:
-            b_launch = w.n_tau * w.n_spin / (hot_n / args.steps)
+            b_launch = case.p.n_tau * w.n_spin / (hot_n / args.steps)
             per_b = (BCD_TRAFFIC["bytes"] - BCD_TRAFFIC["shared"]) / BCD_TRAFFIC["batches"]
             roof["traffic"] = per_b * b_launch + BCD_TRAFFIC["shared"]
             roof["traffic_source"] = BCD_TRAFFIC["source"]
@@ -708,11 +751,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "strong" if isinstance(case, BatchCase) else "weak", "vs_baseline": None,
+        "scaling": "strong" if (isinstance(case, BatchCase) or getattr(case, "tau_shard", None)) else "weak",
+        "vs_baseline": None,
         "dtype": case.dtype, "data": "synthetic",
         "config": {**case.config, "l2": "flushed between steps (256 MiB write outside the events)",
                    "parallelism": (f"batch instances sharded over {world} GPUs" if isinstance(case, BatchCase)
-                                   else f"{world} independent builds (one per GPU)"), **extra},
+                                   else (f"one build split over {world} GPUs by tau mirror pairs, all-gather of "
+                                         f"Sigma in the step" if getattr(case, "tau_shard", None)
+                                         else f"{world} independent builds (one per GPU)")), **extra},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -745,6 +791,9 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--forward-only", action="store_true", help="batch workload: no dPhi/dX, dPhi/dV")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "tau"],
+                    help="bare-SOX workloads on N GPUs: N independent builds, or one build split by tau "
+                         "mirror pairs with an all-gather of Sigma")
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     args = ap.parse_args()

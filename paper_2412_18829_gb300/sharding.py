@@ -41,3 +41,58 @@ def max_over_ranks(t_local: float, dist=None, device=None) -> float:
     t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# One build split over ranks by tau.  The static chain is local in tau except for the
+# reflection G(-tau_j) = -G(tau_{n_tau-1-j}) (Sec. II C on a mirror-symmetric grid), so a
+# rank owns whole mirror pairs {j, n_tau-1-j}: packed as [a_1 .. a_k, (mid), mirrors of
+# a_k .. a_1], its G slices are themselves mirror-symmetric and sox_sigma on them returns
+# exactly the Sigma(tau) of those points.  Gathering the slices is the one exchange.
+# ---------------------------------------------------------------------------
+def tau_shards(n_tau: int, world: int) -> list[list[int]]:
+    """Tau indices per rank in compact (mirror-symmetric) order; every index exactly once.
+
+    The n_tau // 2 mirror pairs are dealt round-robin (equal cost per pair); an odd grid's
+    middle point goes to the rank with the fewest pairs."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    if n_tau < 2:
+        raise ValueError("n_tau must be >= 2")
+    pairs = [[] for _ in range(world)]
+    for j in range(n_tau // 2):
+        pairs[j % world].append(j)
+    mid_rank = min(range(world), key=lambda r: (len(pairs[r]), r)) if n_tau % 2 else None
+    out = []
+    for r in range(world):
+        first = sorted(pairs[r])
+        mids = [n_tau // 2] if r == mid_rank else []
+        out.append(first + mids + [n_tau - 1 - j for j in reversed(first)])
+    return out
+
+
+def compact_is_mirror(order: list[int], n_tau: int) -> bool:
+    """True when position p and len-1-p hold reflected tau indices for every p."""
+    m = len(order)
+    return all(order[p] + order[m - 1 - p] == n_tau - 1 for p in range(m))
+
+
+def assemble(parts, orders, n_tau: int, axis: int = 2):
+    """Sigma over the full grid from the ranks' compact slices (numpy or torch, along `axis`)."""
+    first = parts[0]
+    shape = list(first.shape)
+    shape[axis] = n_tau
+    if hasattr(first, "new_empty"):
+        out = first.new_empty(shape)
+    else:
+        import numpy as np
+
+        out = np.empty(shape, dtype=first.dtype)
+    for part, order in zip(parts, orders):
+        for p, j in enumerate(order):
+            idx = [slice(None)] * len(shape)
+            src = [slice(None)] * len(shape)
+            idx[axis] = j
+            src[axis] = p
+            out[tuple(idx)] = part[tuple(src)]
+    return out

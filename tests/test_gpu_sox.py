@@ -284,3 +284,28 @@ def test_g3w2_and_2sosex_static(env, prec):
     Sh = np.full_like(w.G, np.nan)
     pkg.sosex2_static_sigma(hs[prec], p, w.G, X, V, W, Sh)      # host G and Sigma are staged
     assert np.array_equal(Sh, S.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tau_shards_through_the_library_reassemble_the_build(env, prec):
+    """One build split by mirror-pair tau shards (three ranks, run one after the other on
+    this GPU): each shard's sox_sigma on its compact G, reassembled, equals the whole build."""
+    from paper_2412_18829_gb300 import sharding
+
+    torch, pkg, hs = env
+    w = synth.molecule(29, 21, 100, 9, 100.0, n_spin=2)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    full = torch.empty_like(G)
+    pkg.sox_sigma(hs[prec], pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta), G, X, V, full)
+    orders = sharding.tau_shards(w.n_tau, 3)
+    parts = []
+    for order in orders:
+        Gc = G[:, :, order].contiguous()
+        Sc = torch.full_like(Gc, float("nan"))
+        pkg.sox_sigma(hs[prec], pkg.problem(w.n, w.N, len(order), w.n_spin, w.beta), Gc, X, V, Sc)
+        parts.append(Sc)
+    got = sharding.assemble(parts, orders, w.n_tau)
+    pkg.sox_check_device(hs[prec])
+    err = float((got - full).abs().max())
+    assert err <= (1e-14 if prec == "fp64" else 1e-9) * float(full.abs().max())
+    check(got.cpu().numpy(), sox.sox_sigma(w.X, w.V, w.G, dtype=np.float64), prec, "tau shards")

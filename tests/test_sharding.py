@@ -3,6 +3,7 @@ time, with two gloo ranks (no GPU)."""
 import os
 import socket
 
+import numpy as np
 import pytest
 
 from paper_2412_18829_gb300 import sharding
@@ -68,3 +69,64 @@ def test_two_gloo_ranks_agree_on_the_partition_and_the_slowest_time():
         assert got[rank] == sharding.shard([sharding.build_cost(int(n), 6 * int(n), 120)
                                             for n in synth.batch_c4_sizes()], 2)[rank]
         assert t == 1.5
+
+
+@pytest.mark.parametrize("n_tau", [2, 3, 8, 30, 31, 80])
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_tau_shards_partition_the_grid_in_mirror_pairs(n_tau, world):
+    parts = sharding.tau_shards(n_tau, world)
+    assert sorted(j for p in parts for j in p) == list(range(n_tau))
+    for p in parts:
+        assert sharding.compact_is_mirror(p, n_tau)
+    sizes = [len(p) for p in parts]
+    assert max(sizes) - min(sizes) <= 3
+
+
+def test_compact_grid_reproduces_the_full_build():
+    """Sigma on each rank's compact G equals the full build's slices (oracle, CPU)."""
+    from oracle import sox
+
+    w = synth.tiny(4, 9, n_tau=7)
+    full = sox.sox_sigma(w.X, w.V, w.G)
+    parts, orders = [], sharding.tau_shards(w.n_tau, 3)
+    for order in orders:
+        parts.append(sox.sox_sigma(w.X, w.V, w.G[:, :, order]))
+    got = sharding.assemble(parts, orders, w.n_tau)
+    assert np.abs(got - full).max() <= 1e-15 * np.abs(full).max()
+
+
+def _tau_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    from oracle import sox
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.tiny(3, 7, n_tau=6)
+        orders = sharding.tau_shards(w.n_tau, world)
+        mine = torch.from_numpy(sox.sox_sigma(w.X, w.V, w.G[:, :, orders[rank]]).real.copy())
+        got = [None] * world
+        dist.all_gather_object(got, mine)
+        full = sharding.assemble(got, orders, w.n_tau)
+        ref = sox.sox_sigma(w.X, w.V, w.G).real
+        q.put((rank, float(np.abs(full.numpy() - ref).max()), float(np.abs(ref).max())))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_one_build_by_tau():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_tau_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, err, scale in res:
+        assert err <= 1e-15 * scale
