@@ -5,6 +5,8 @@
     python -m paper_2412_18829_gb300.probes.profile_case solid [f16x2|fp64] [n_tau]
         one sosex_dynamic_sigma on the 3x3x3 solid's shapes (n=26, N=300), 4 tau by default,
         with the synthetic single-pole W_d
+    python -m paper_2412_18829_gb300.probes.profile_case screened [f16x2|fp64] [n_tau]
+        sox_sigma twice on the screened molecule's shapes (n=250, N=2000), 4 tau by default
     python -m paper_2412_18829_gb300.probes.profile_case adjoint [f16x2|fp64] [n_tau]
         phi_sox_backward (dX, dV) twice on the largest batch instance's shapes (n=298,
         N=1788), 8 tau by default
@@ -27,6 +29,16 @@ def main(argv):
     if kind == "molecule":
         T = int(argv[3]) if len(argv) > 3 else 8
         w = synth.molecule(1, 120, 600, T, 100.0, n_spin=2)
+        p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        G, X, V = [torch.from_numpy(a).cuda() for a in (w.G, w.X, w.V)]
+        S = torch.empty_like(G)
+        with pkg.Handle(prec) as h:
+            for _ in range(2):
+                pkg.sox_sigma(h, p, G, X, V, S)
+            pkg.sox_check_device(h)
+    elif kind == "screened":
+        T = int(argv[3]) if len(argv) > 3 else 4
+        w = synth.molecule(2, 250, 2000, T, 100.0, 1)
         p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
         G, X, V = [torch.from_numpy(a).cuda() for a in (w.G, w.X, w.V)]
         S = torch.empty_like(G)
