@@ -621,6 +621,11 @@ def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
         return BatchCase(torch, pkg, args.precision, dev, stream, rank, world, backward=not args.forward_only)
     w = workload(args.workload)
     if args.workload == "c3":
+        if args.mesh != "3,3,3":   # the same solid recipe on another mesh
+            import synth
+
+            nk = tuple(int(x) for x in args.mesh.split(","))
+            w = synth.solid(3, nk, w.n, w.N, w.n_tau, w.beta, name=f"sosexdyn-k{''.join(map(str, nk))}-n{w.n}-N{w.N}-t{w.n_tau}")
         return SolidCase(torch, pkg, w, args.precision, dev, stream)
     shard = (rank, world, dist_mod) if (args.shard == "tau" and args.workload in ("c0", "c1")) else None
     return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"),
@@ -794,6 +799,7 @@ def main():
     ap.add_argument("--shard", default="replicas", choices=["replicas", "tau"],
                     help="bare-SOX workloads on N GPUs: N independent builds, or one build split by tau "
                          "mirror pairs with an all-gather of Sigma")
+    ap.add_argument("--mesh", default="3,3,3", help="solid workload: k-mesh (default 3,3,3)")
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     args = ap.parse_args()

@@ -433,13 +433,10 @@ bool launch_split_t(const T *src, const RowMap &m, int batch, int rows, int K, i
   if (!contiguous || m.sk == 1) return false;
   const size_t smem = (size_t)K * (kRB + 1) * sizeof(T);
   if (smem > 200 * 1024) return false;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_csplit_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    attr = true;
+  static std::atomic<unsigned long long> attr{0};
+  if (set_smem_once(k_csplit_t<T>, 200 * 1024, attr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
   const long long blocks = (long long)batch * ((rows + kRB - 1) / kRB);
   k_csplit_t<T><<<(unsigned)blocks, 256, smem, s>>>(src, m, batch, rows, K, Kp2, kind, sa, sbc, hi, lo, unscale);
@@ -787,11 +784,8 @@ Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, 
   const size_t cap = 96 * 1024;
   if (per_e > cap) return {SOX_ERR_SHAPE, "k-mesh too large for the split-precision D step"};
   const int E = (int)std::min<size_t>(8, cap / per_e);
-  static bool attr = false;
-  if (!attr) {
-    SOX_CUDA_TRY(cudaFuncSetAttribute(k_kpoint_D_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  SOX_CUDA_TRY(set_smem_once(k_kpoint_D_blk, (int)cap, attr));
   dim3 grid((unsigned)((NN + E - 1) / E), (unsigned)ct);
   k_kpoint_D_blk<<<grid, 256, per_e * E, s>>>(reinterpret_cast<const float2 *>(B), reinterpret_cast<const float2 *>(C),
                                               sP, sI, add, sub, nk, NN, E, i0, sDi, reinterpret_cast<double2 *>(D));

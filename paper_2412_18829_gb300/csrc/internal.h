@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "smem_attr.h"
 #include "thc_sox.h"
 
 struct sox_context {

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "tc_common.cuh"
+#include "smem_attr.h"
 #include "tc_kernels.h"
 
 namespace sox {
@@ -1095,24 +1096,16 @@ size_t res_smem_bytes() { return (size_t)kResBytes + kRStages * kRStageBytes + s
 
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant) {
   if (variant == kBcdResident && a.Kp <= 128) {
-    static bool rattr = false;
-    if (!rattr) {
-      cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)res_smem_bytes());
-      if (e != cudaSuccess) return e;
-      rattr = true;
-    }
+    static std::atomic<unsigned long long> rattr{0};
+    const cudaError_t e = set_smem_once(k_sox_bcd_tc_res, (int)res_smem_bytes(), rattr);
+    if (e != cudaSuccess) return e;
     k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                maps[5], maps[6], maps[7], a);
     return cudaGetLastError();
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sox_bcd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  const cudaError_t e = set_smem_once(k_sox_bcd_tc, (int)tc_smem_bytes(), attr);
+  if (e != cudaSuccess) return e;
   k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                                         maps[6], maps[7], a);
   return cudaGetLastError();
@@ -1121,13 +1114,9 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int gri
 size_t gemm_smem_bytes() { return (size_t)kGStages * kStageBytes + kStageOut + sizeof(Barriers) + 1024; }
 
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gemm_smem_bytes());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  const cudaError_t e = set_smem_once(k_gemm_f16x2, (int)gemm_smem_bytes(), attr);
+  if (e != cudaSuccess) return e;
   k_gemm_f16x2<<<grid, kGemmThreads, gemm_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
   return cudaGetLastError();
 }

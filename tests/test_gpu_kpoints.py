@@ -67,7 +67,7 @@ def test_solid_sigma_is_hermitian_in_both_precisions(env):
 @pytest.mark.parametrize("nk,n,N,n_tau", [((1, 1, 2), 3, 5, 3), ((1, 2, 2), 4, 7, 3), ((1, 1, 3), 5, 12, 4),
                                           ((2, 2, 2), 6, 20, 3), ((2, 1, 1), 9, 70, 2), ((3, 1, 1), 26, 300, 3),
                                           ((1, 1, 4), 3, 8, 2), ((1, 1, 7), 2, 5, 2), ((1, 1, 2), 40, 161, 2),
-                                          ((2, 1, 1), 70, 210, 2), ((3, 3, 3), 3, 7, 2)])
+                                          ((2, 1, 1), 70, 210, 2), ((3, 3, 3), 3, 7, 2), ((4, 4, 4), 2, 3, 2)])
 def test_solid_split_precision_matches_oracle(env, nk, n, N, n_tau):
     """Meshes with a compile-time D step, the register form (n_k = 4) and the generic one (n_k = 7)."""
     w = synth.solid(9, nk, n, N, n_tau, 10.0)
