@@ -30,16 +30,19 @@ __device__ __forceinline__ double2 ld_c(const double2 *p) { return *p; }
 __device__ __forceinline__ float2 ld_c(const float2 *p) { return *p; }
 
 // FP16 pair of x * s (s a power of two): hi rounds to nearest, lo holds the remainder.
-__device__ __forceinline__ void split_pair(double x, float s, __half &h, __half &l) {
-  const double xs = x * (double)s;
-  h = __float2half_rn((float)xs);
-  l = __float2half_rn((float)(xs - (double)__half2float(h)));
-}
 __device__ __forceinline__ void split_pair(float x, float s, __half &h, __half &l) {
   const float xs = x * s;
   h = __float2half_rn(xs);
   l = __float2half_rn(xs - __half2float(h));
 }
+__device__ __forceinline__ void split_pair(double x, float s, __half &h, __half &l) {
+  const double xs = x * (double)s;
+  h = __float2half_rn((float)xs);
+  l = __float2half_rn((float)(xs - (double)__half2float(h)));
+}
+// rounding to nearest is symmetric, so the pair of -x is the negated pair of x: a B row's
+// four signed copies of (b_r, b_i) take two splits
+__device__ __forceinline__ __half neg_if(bool n, __half v) { return n ? __hneg(v) : v; }
 
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
@@ -66,19 +69,17 @@ __device__ __forceinline__ void store8_a(const V2 *v, float s, __half *h, __half
 template <class V2>
 __device__ __forceinline__ void store8_b(const V2 *v, float s, float sa, float sbc, __half *h0, __half *l0,
                                          __half *h1, __half *l1) {
-  using R = decltype(v[0].x);
   uint32_t p0[4], q0[4], p1[4], q1[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    __half a, b, c, d;
-    split_pair(v[j].x, s, a, b);
-    split_pair(static_cast<R>(-(sa * sbc)) * v[j].y, s, c, d);
-    p0[j] = pack_h2(a, c);
-    q0[j] = pack_h2(b, d);
-    split_pair(static_cast<R>(sbc) * v[j].y, s, a, b);
-    split_pair(static_cast<R>(sa) * v[j].x, s, c, d);
-    p1[j] = pack_h2(a, c);
-    q1[j] = pack_h2(b, d);
+    __half xh, xl, yh, yl;
+    split_pair(v[j].x, s, xh, xl);
+    split_pair(v[j].y, s, yh, yl);
+    const bool n_re = sa * sbc > 0.f, n_im = sbc < 0.f, n_x = sa < 0.f;
+    p0[j] = pack_h2(xh, neg_if(n_re, yh));   // (b_r, -sa sb b_i)
+    q0[j] = pack_h2(xl, neg_if(n_re, yl));
+    p1[j] = pack_h2(neg_if(n_im, yh), neg_if(n_x, xh));   // (sb b_i, sa b_r)
+    q1[j] = pack_h2(neg_if(n_im, yl), neg_if(n_x, xl));
   }
   *reinterpret_cast<uint4 *>(h0) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
   *reinterpret_cast<uint4 *>(l0) = make_uint4(q0[0], q0[1], q0[2], q0[3]);
@@ -356,6 +357,218 @@ __global__ void __launch_bounds__(128) k_kpoint_D_mesh(const float2 *B, const fl
   }
 }
 
+// The D step through the convolution theorem on the k mesh.  For one (P, R) element and
+// one k_s, with c(x) = C[(x - k_s, x)] and b(y) = B[(y, k_s)],
+//   D[k] += sum_x c(x) b(x - k),
+// a cyclic cross-correlation over Z_N1 x Z_N2 x Z_N3.  With F-(m) = sum_x f(x) w^{-m.x},
+// F+(m) = sum_x f(x) w^{+m.x}:  Dhat(m) = sum_{k_s} c^-(m) b^+(m), and
+// D[k] = (1/n_k) sum_m w^{+m.k} Dhat(m): n_k^2 products per element instead of n_k^3, and
+// for mesh sides up to 4 the small DFTs need additions only (sides of 3: one real scale).
+// Thread (e, m1) owns one slab m1 of Dhat: the side-N1 transform is folded into the loads,
+// the N2 x N3 transform runs in registers; the inverse side-N1 transform at the end goes
+// through shared memory.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// v * i^sgn
+__device__ __forceinline__ float2 mul_i(float2 v, int sgn) {
+  return sgn > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+constexpr float kHalfSqrt3 = 0.86602540378443864676f;   // sin(2 pi / 3)
+
+// v * exp(sgn 2 pi i j / n) for n in {1, 2, 3, 4}; with n, j, sgn constants after
+// unrolling every branch folds away
+__device__ __forceinline__ float2 twiddle(float2 v, int n, int j, int sgn) {
+  j %= n;
+  if (j == 0) return v;
+  if (2 * j == n) return make_float2(-v.x, -v.y);
+  if (4 * j == n) return mul_i(v, sgn);
+  if (4 * j == 3 * n) return mul_i(v, -sgn);
+  const float s = (j == 1 ? sgn : -sgn) * kHalfSqrt3;   // n == 3: cos = -1/2
+  return make_float2(-0.5f * v.x - s * v.y, -0.5f * v.y + s * v.x);
+}
+
+// in-place length-N DFT with exponent sign sgn of x[o], x[o + st], ...
+template <int N>
+__device__ __forceinline__ void dft1(float2 *x, int o, int st, int sgn) {
+  if (N == 2) {
+    const float2 a = x[o], b = x[o + st];
+    x[o] = cadd(a, b);
+    x[o + st] = csub(a, b);
+  } else if (N == 3) {
+    const float2 a = x[o], b = x[o + st], c = x[o + 2 * st];
+    const float2 t = cadd(b, c), d = csub(b, c);
+    const float2 m = make_float2(a.x - 0.5f * t.x, a.y - 0.5f * t.y);
+    const float2 s = make_float2(sgn * kHalfSqrt3 * d.x, sgn * kHalfSqrt3 * d.y);
+    x[o] = cadd(a, t);
+    x[o + st] = cadd(m, mul_i(s, 1));
+    x[o + 2 * st] = csub(m, mul_i(s, 1));
+  } else if (N == 4) {
+    const float2 a = x[o], b = x[o + st], c = x[o + 2 * st], d = x[o + 3 * st];
+    const float2 s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), w = mul_i(csub(b, d), sgn);
+    x[o] = cadd(s0, s1);
+    x[o + st] = cadd(d0, w);
+    x[o + 2 * st] = csub(s0, s1);
+    x[o + 3 * st] = csub(d0, w);
+  }
+}
+
+// 2-D DFT over the (N2, N3) slab x[a * N3 + b]
+template <int N2, int N3>
+__device__ __forceinline__ void dft2(float2 (&x)[N2 * N3], int sgn) {
+#pragma unroll
+  for (int a = 0; a < N2; ++a) dft1<N3>(x, a * N3, 1, sgn);
+#pragma unroll
+  for (int b = 0; b < N3; ++b) dft1<N2>(x, b, N3, sgn);
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only); bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// slab m1 of b^+ and c^- at one k_s, from the staged planes (b: q = (x1, r) rows 0..NK-1,
+// c: k_w rows NK..2NK-1, each EB elements apart), accumulated into acc
+template <int N1, int N2, int N3, int EB, int M1>
+__device__ __forceinline__ void dfft_step(const float2 *st, float2 (&acc)[N2 * N3]) {
+  constexpr int P = N2 * N3, NK = N1 * P;
+  float2 bt[P], ct[P];
+#pragma unroll
+  for (int x1 = 0; x1 < N1; ++x1)
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+      const float2 v = st[(x1 * P + r) * EB], w = st[(NK + x1 * P + r) * EB];
+      bt[r] = x1 == 0 ? v : cadd(bt[r], twiddle(v, N1, M1 * x1, 1));
+      ct[r] = x1 == 0 ? w : cadd(ct[r], twiddle(w, N1, M1 * x1, -1));
+    }
+  dft2<N2, N3>(bt, 1);
+  dft2<N2, N3>(ct, -1);
+#pragma unroll
+  for (int r = 0; r < P; ++r) {
+    acc[r].x = fmaf(ct[r].x, bt[r].x, fmaf(-ct[r].y, bt[r].y, acc[r].x));
+    acc[r].y = fmaf(ct[r].x, bt[r].y, fmaf(ct[r].y, bt[r].x, acc[r].y));
+  }
+}
+
+// slab k1 of D: the inverse side-N1 transform of the exchanged (m1, k') values
+template <int N1, int N2, int N3, int EB, int K1>
+__device__ __forceinline__ void dfft_out(const float2 *s_x, int el, float inv_nk, double2 *Dk, long long NN) {
+  constexpr int P = N2 * N3;
+#pragma unroll
+  for (int r = 0; r < P; ++r) {
+    float2 s = s_x[r * EB + el];
+#pragma unroll
+    for (int m1 = 1; m1 < N1; ++m1) s = cadd(s, twiddle(s_x[(m1 * P + r) * EB + el], N1, m1 * K1, 1));
+    double2 *d = Dk + (long long)(K1 * P + r) * NN;
+    double2 v = *d;
+    v.x += (double)(s.x * inv_nk);
+    v.y += (double)(s.y * inv_nk);
+    *d = v;
+  }
+}
+
+template <int N1, int N2, int N3, int EB, int M1 = 0>
+__device__ __forceinline__ void dfft_step_at(int m1, const float2 *st, float2 (&acc)[N2 * N3]) {
+  if constexpr (M1 < N1) {
+    if (m1 == M1)
+      dfft_step<N1, N2, N3, EB, M1>(st, acc);
+    else
+      dfft_step_at<N1, N2, N3, EB, M1 + 1>(m1, st, acc);
+  }
+}
+
+template <int N1, int N2, int N3, int EB, int K1 = 0>
+__device__ __forceinline__ void dfft_out_at(int k1, const float2 *s_x, int el, float inv_nk, double2 *Dk, long long NN) {
+  if constexpr (K1 < N1) {
+    if (k1 == K1)
+      dfft_out<N1, N2, N3, EB, K1>(s_x, el, inv_nk, Dk, NN);
+    else
+      dfft_out_at<N1, N2, N3, EB, K1 + 1>(k1, s_x, el, inv_nk, Dk, NN);
+  }
+}
+
+template <int N1, int N2, int N3, int R, int S>
+struct DfftShape {
+  static constexpr int P = N2 * N3, NK = N1 * P, EB = 32 * R, NT = 32 * N1 * R;
+  static constexpr size_t stage_elems = (size_t)2 * NK * EB;   // float2: NK b planes, NK c planes
+  static constexpr size_t smem = S * stage_elems * sizeof(float2) + ((NK * NK + 15) / 16) * 16;
+};
+
+// Block: EB = 32 R elements x N1 slabs (warp w: slab w % N1, element group w / N1).  The
+// 2 NK planes of one k_s (b: B[(q, k_s)], c: C[(k_w - k_s, k_w)]) are staged for the block
+// by 16-byte asynchronous copies, S - 1 steps of k_s ahead of the arithmetic.
+// Requires B, C 16-byte aligned and sP, sI, NN even (checked by the launcher).
+template <int N1, int N2, int N3, int R, int S>
+__global__ void __launch_bounds__(32 * N1 * R) k_kpoint_D_fft(const float2 *B, const float2 *C, long long sP,
+                                                             long long sI, const int *sub, long long NN, int i0,
+                                                             long long sDi, double2 *D) {
+  using Sh = DfftShape<N1, N2, N3, R, S>;
+  constexpr int P = Sh::P, NK = Sh::NK, EB = Sh::EB, NT = Sh::NT, CH = EB / 2;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float2 *buf = reinterpret_cast<float2 *>(dsm);
+  unsigned char *s_sub = dsm + S * Sh::stage_elems * sizeof(float2);   // [k_w][k_s] -> k_w - k_s
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  for (int t = tid; t < NK * NK; t += NT) s_sub[t] = (unsigned char)sub[t];
+  __syncthreads();
+  const int il = blockIdx.y;
+  const long long e0 = (long long)blockIdx.x * EB, rem = NN - e0;
+  const float2 *Bb = B + (long long)il * sI + e0, *Cb = C + (long long)il * sI + e0;
+  auto issue = [&](int ks) {
+    float2 *dst = buf + (size_t)(ks % S) * Sh::stage_elems;
+#pragma unroll 4
+    for (int c = tid; c < 2 * NK * CH; c += NT) {
+      const int j = c / CH, u = c % CH;
+      const float2 *src = j < NK ? Bb + (long long)(j * NK + ks) * sP
+                                 : Cb + (long long)(s_sub[(j - NK) * NK + ks] * NK + (j - NK)) * sP;
+      const long long off = 2LL * u;
+      const int bytes = off + 1 < rem ? 16 : (off < rem ? 8 : 0);
+      cp_async16(dst + j * EB + 2 * u, bytes ? src + off : src, bytes);
+    }
+  };
+#pragma unroll 1
+  for (int st = 0; st < S - 1; ++st) {
+    if (st < NK) issue(st);
+    cp_async_commit();
+  }
+  const int m1 = threadIdx.y % N1, el = (threadIdx.y / N1) * 32 + threadIdx.x;
+  float2 acc[P];
+#pragma unroll
+  for (int r = 0; r < P; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int ks = 0; ks < NK; ++ks) {
+    cp_async_wait<S - 2>();   // this thread's copies of step ks have landed
+    __syncthreads();          // everyone's have, and step ks - 1's slot is free
+    if (ks + S - 1 < NK) issue(ks + S - 1);
+    cp_async_commit();
+    dfft_step_at<N1, N2, N3, EB>(m1, buf + (size_t)(ks % S) * Sh::stage_elems + el, acc);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  dft2<N2, N3>(acc, 1);
+#pragma unroll
+  for (int r = 0; r < P; ++r) buf[(m1 * P + r) * EB + el] = acc[r];
+  __syncthreads();
+  if (el < rem)
+    dfft_out_at<N1, N2, N3, EB>(m1, buf, el, 1.f / (float)NK, D + (long long)(i0 + il) * sDi + e0 + el, NN);
+}
+
+template <int N1, int N2, int N3, int R, int S>
+cudaError_t launch_dfft(const float2 *B, const float2 *C, long long sP, long long sI, const int *sub, long long NN,
+                        int ct, int i0, long long sDi, double2 *D, cudaStream_t s) {
+  using Sh = DfftShape<N1, N2, N3, R, S>;
+  static std::atomic<unsigned long long> attr{0};
+  const cudaError_t e = set_smem_once(k_kpoint_D_fft<N1, N2, N3, R, S>, (int)Sh::smem, attr);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((NN + Sh::EB - 1) / Sh::EB), (unsigned)ct), block(32, N1 * R);
+  k_kpoint_D_fft<N1, N2, N3, R, S><<<grid, block, Sh::smem, s>>>(B, C, sP, sI, sub, NN, i0, sDi, D);
+  return cudaGetLastError();
+}
+
 // Split of rows that are contiguous in memory with K strided (a transposed read):
 // a block stages a tile of RB rows x K in shared memory with coalesced loads, then one
 // warp per row finds its scale and writes the FP16 pairs.  kind 0: A rows, 1: B rows.
@@ -409,11 +622,16 @@ __global__ void __launch_bounds__(256) k_csplit_t(const T *src, RowMap m, int ba
         __half a0 = __float2half(0.f), d0 = a0, a1 = a0, d1 = a0, a2 = a0, d2 = a0, a3 = a0, d3 = a0;
         if (k < K) {
           const T v = tile[k * (kRB + 1) + rr];
-          using R = decltype(v.x);
+          __half yh, yl;
           split_pair(v.x, s, a0, d0);
-          split_pair(static_cast<R>(-(sa * sbc)) * v.y, s, a1, d1);
-          split_pair(static_cast<R>(sbc) * v.y, s, a2, d2);
-          split_pair(static_cast<R>(sa) * v.x, s, a3, d3);
+          split_pair(v.y, s, yh, yl);
+          const bool n_re = sa * sbc > 0.f, n_im = sbc < 0.f, n_x = sa < 0.f;
+          a1 = neg_if(n_re, yh);
+          d1 = neg_if(n_re, yl);
+          a2 = neg_if(n_im, yh);
+          d2 = neg_if(n_im, yl);
+          a3 = neg_if(n_x, a0);
+          d3 = neg_if(n_x, d0);
         }
         h0[k] = __halves2half2(a0, a1);
         l0[k] = __halves2half2(d0, d1);
@@ -735,6 +953,30 @@ Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const
 Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, const int *add, const int *sub,
                     const int mesh[3], long long NN, int ct, int i0, long long sDi, double *D, cudaStream_t s) {
   const int nk = mesh[0] * mesh[1] * mesh[2];
+  // mesh sides up to 4: the Fourier form (n_k^2 products per element), 16-byte staged copies
+  const bool aligned16 = ((reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) == 0 &&
+                         (sP % 2) == 0 && (sI % 2) == 0 && (NN % 2) == 0;
+  if (aligned16) {
+    const float2 *Bf = reinterpret_cast<const float2 *>(B), *Cf = reinterpret_cast<const float2 *>(C);
+    double2 *Dd = reinterpret_cast<double2 *>(D);
+    const int key = mesh[0] * 100 + mesh[1] * 10 + mesh[2];
+    bool done = true;
+    switch (key) {
+#define SOX_DFFT(A, B_, C_, R, S)                                                              \
+  case A * 100 + B_ * 10 + C_:                                                                \
+    SOX_CUDA_TRY((launch_dfft<A, B_, C_, R, S>(Bf, Cf, sP, sI, sub, NN, ct, i0, sDi, Dd, s))); \
+    break;
+      SOX_DFFT(1, 1, 1, 4, 3) SOX_DFFT(1, 1, 2, 4, 3) SOX_DFFT(1, 2, 1, 4, 3) SOX_DFFT(2, 1, 1, 2, 3)
+      SOX_DFFT(1, 1, 3, 4, 3) SOX_DFFT(1, 3, 1, 4, 3) SOX_DFFT(3, 1, 1, 1, 3) SOX_DFFT(1, 2, 2, 4, 3)
+      SOX_DFFT(2, 2, 1, 2, 3) SOX_DFFT(2, 1, 2, 2, 3) SOX_DFFT(2, 2, 2, 2, 3) SOX_DFFT(3, 3, 1, 1, 3)
+      SOX_DFFT(3, 3, 3, 1, 3) SOX_DFFT(1, 1, 4, 4, 3) SOX_DFFT(4, 1, 1, 1, 3) SOX_DFFT(2, 2, 4, 2, 2)
+      SOX_DFFT(4, 4, 4, 1, 2)
+#undef SOX_DFFT
+      default:
+        done = false;
+    }
+    if (done) return Status::ok();
+  }
   {
     dim3 grid((unsigned)((NN + 127) / 128), (unsigned)ct);
     const float2 *Bf = reinterpret_cast<const float2 *>(B), *Cf = reinterpret_cast<const float2 *>(C);

@@ -2,9 +2,9 @@
 
     python -m paper_2412_18829_gb300.probes.profile_case molecule [f16x2|fp64] [n_tau]
         sox_sigma twice on the mid-size molecule's shapes (n=120, N=600, 2 spins), 8 tau by default
-    python -m paper_2412_18829_gb300.probes.profile_case solid [f16x2|fp64] [n_tau]
+    python -m paper_2412_18829_gb300.probes.profile_case solid [f16x2|fp64] [n_tau] [mesh] [n,N]
         one sosex_dynamic_sigma on the 3x3x3 solid's shapes (n=26, N=300), 4 tau by default,
-        with the synthetic single-pole W_d
+        with the synthetic single-pole W_d; another mesh ("4,4,4") and sizes ("10,100") optional
     python -m paper_2412_18829_gb300.probes.profile_case screened [f16x2|fp64] [n_tau]
         sox_sigma twice on the screened molecule's shapes (n=250, N=2000), 4 tau by default
     python -m paper_2412_18829_gb300.probes.profile_case adjoint [f16x2|fp64] [n_tau]
@@ -48,7 +48,9 @@ def main(argv):
             pkg.sox_check_device(h)
     elif kind == "solid":
         T = int(argv[3]) if len(argv) > 3 else 4
-        w = synth.solid(3, (3, 3, 3), 26, 300, T, 300.0)
+        mesh = tuple(int(x) for x in argv[4].split(",")) if len(argv) > 4 else (3, 3, 3)
+        n, N = (int(x) for x in argv[5].split(",")) if len(argv) > 5 else (26, 300)
+        w = synth.solid(3, mesh, n, N, T, 300.0)
         M = (T - 1) // 2
         _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, M)
         Wd = synth.pole_screening(w.V, w.beta, M)

@@ -67,9 +67,11 @@ def test_solid_sigma_is_hermitian_in_both_precisions(env):
 @pytest.mark.parametrize("nk,n,N,n_tau", [((1, 1, 2), 3, 5, 3), ((1, 2, 2), 4, 7, 3), ((1, 1, 3), 5, 12, 4),
                                           ((2, 2, 2), 6, 20, 3), ((2, 1, 1), 9, 70, 2), ((3, 1, 1), 26, 300, 3),
                                           ((1, 1, 4), 3, 8, 2), ((1, 1, 7), 2, 5, 2), ((1, 1, 2), 40, 161, 2),
-                                          ((2, 1, 1), 70, 210, 2), ((3, 3, 3), 3, 7, 2), ((4, 4, 4), 2, 3, 2)])
+                                          ((2, 1, 1), 70, 210, 2), ((3, 3, 3), 3, 7, 2), ((4, 4, 4), 2, 3, 2),
+                                          ((2, 2, 4), 2, 5, 2), ((1, 1, 5), 3, 8, 2)])
 def test_solid_split_precision_matches_oracle(env, nk, n, N, n_tau):
-    """Meshes with a compile-time D step, the register form (n_k = 4) and the generic one (n_k = 7)."""
+    """Meshes with sides up to 4 take the Fourier D step (sides of 1, 2, 3 and 4, mixed); n_k = 5
+    the register form and n_k = 7 the generic one."""
     w = synth.solid(9, nk, n, N, n_tau, 10.0)
     ref = kpoints.sox_sigma(w.X, w.V, w.G, nk)
     got = _run(env, w, "f16x2")
@@ -119,6 +121,9 @@ def _run_dynamic(env, w, G, Tf, Ti, Wd, handle=None, prec="fp64"):
     return S.cpu().numpy()
 
 
+_DYN_REF = {}
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f16x2"])
 @pytest.mark.parametrize("nk,n,N,n_tau,M,physical,n_spin", [
     ((1, 1, 2), 3, 5, 4, 2, False, 1),
@@ -126,10 +131,15 @@ def _run_dynamic(env, w, G, Tf, Ti, Wd, handle=None, prec="fp64"):
     ((1, 1, 3), 5, 12, 4, 2, False, 2),
     ((2, 1, 1), 9, 70, 6, 3, True, 1),
     ((3, 3, 3), 2, 5, 3, 1, False, 1),
+    ((2, 2, 4), 2, 5, 3, 1, False, 1),
+    ((4, 4, 4), 2, 3, 3, 1, False, 1),
 ])
 def test_solid_sosex_dynamic_matches_oracle(env, nk, n, N, n_tau, M, physical, n_spin, prec):
     w, G, Tf, Ti, Wd = _dynamic_inputs(nk, n, N, n_tau, M, 30 + n, physical, n_spin)
-    ref = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, G, nk)
+    key = (nk, n, N, n_tau, M, physical, n_spin)
+    if key not in _DYN_REF:   # both precisions compare against one oracle run
+        _DYN_REF[key] = kpoints.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, G, nk)
+    ref = _DYN_REF[key]
     got = _run_dynamic(env, w, G, Tf, Ti, Wd, prec=prec)
     assert np.isfinite(got).all()
     check(got, ref, prec, f"solid dynamic {nk} n={n} N={N}", strict=(prec == "f16x2" and N >= 4 * n))
