@@ -919,8 +919,9 @@ Status cgemm_tc(sox_handle h, const CSplit &A, const CSplit &B, int batch, const
         !make_tmap_f16_3d_rs(&maps[2], B.hi + k0, kw, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err) ||
         !make_tmap_f16_3d_rs(&maps[3], B.lo + k0, kw, B.Kp2, B.rows, B.batch, bsB * B.Kp2, 64, 128, &err))
       return {SOX_ERR_CUDA, "cgemm_tc: " + err};
-    maps[4] = maps[0];   // no TMA stores in FP32 mode; valid maps for the prefetch
-    maps[5] = maps[1];
+    if (!make_tmap_f32_store3d(&maps[4], C, B.rows, A.rows, batch, ldc, sCb, &err))
+      return {SOX_ERR_CUDA, "cgemm_tc: " + err};
+    maps[5] = maps[4];
     GemmTcArgs ga;
     ga.M = A.rows;
     ga.Ncols = B.rows;

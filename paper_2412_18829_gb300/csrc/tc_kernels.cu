@@ -517,6 +517,47 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 constexpr int kGemmThreads = 320;
 constexpr int kGemmEpi = 256;
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// the epilogue warps agree on ok (all of them, or none, go on: no warp is left waiting at a
+// named barrier that the others have stopped reaching)
+__device__ __forceinline__ bool epi_all(bool ok) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)ok)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+// element-wise FP32 add of the shared tile into global memory (round to nearest)
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+  asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+// kStoreF32 scale of tile t for epilogue thread e: e < 128 the column scale of tile column e,
+// else alpha times the row scale of tile row e - 128
+__device__ __forceinline__ float f32_tile_scale(const GemmTcArgs &a, long long t, int e, int tN, long long per_b) {
+  const int b = (int)(t / per_b);
+  const long long r = t % per_b;
+  if (e < kTile) {
+    const int col = (int)(r % tN) * kTile + e;
+    if (!a.col_scale || col >= a.Ncols) return 1.f;
+    const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
+    return a.col_scale[zb * a.cs_b + col];
+  }
+  const int row = (int)(r / tN) * kTile + (e - kTile);
+  if (!a.row_scale || row >= a.M) return a.alpha;
+  const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
+  return a.alpha * a.row_scale[za * a.rs_b + row];
+}
 
 __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
@@ -615,25 +656,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int h = (warp - 2) >> 2;          // 64-column half of the tile
     const bool storer = (warp == 2 && lane == 0);
     __shared__ float red[8];
+    __shared__ __align__(16) float s_sc[2 * kTile];   // kStoreF32: column scales, then alpha x row scales
+    const int ep = (warp - 2) * 32 + lane;
+    // the scales of the next tile are loaded one tile ahead (their latency hides behind this one)
+    float pre = (a.mode == kStoreF32 && blockIdx.x < total) ? f32_tile_scale(a, blockIdx.x, ep, tN, per_b) : 0.f;
     long long acc_it = 0;
-    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++acc_it) {
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++acc_it) {
       const int b = (int)(t / per_b);
       const long long r = t % per_b;
       const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
       const int buf = (int)(acc_it & 1);
       const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
-      if (!tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8)) break;
+      const bool got = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+      if (!epi_all(got && !*abort)) break;
       tc::tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 128 + h * 64;
       const bool row_ok = (i0 + row) < a.M;
       if (a.mode == kStoreF32) {
-        // scaled FP32 tile through shared memory (16-byte chunks XOR-swizzled by row), then
-        // written row by row with coalesced 16-byte stores
-        const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
-        const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
-        const float rsc = a.alpha * ((a.row_scale && row_ok) ? a.row_scale[za * a.rs_b + i0 + row] : 1.f);
+        // scaled FP32 tile in four 128-byte-swizzled boxes of 128 rows x 32 columns, written
+        // (or added, in accumulate mode) by TMA tensor stores; rows >= M and columns >= Ncols
+        // fall outside the tensor map and are not written
+        if (storer) bulk_wait_read();   // the previous tile's stores have read the staging boxes
+        epi_sync();
+        s_sc[ep] = pre;
+        epi_sync();
+        if (t + gridDim.x < total) pre = f32_tile_scale(a, t + gridDim.x, ep, tN, per_b);
+        const float rsc = s_sc[kTile + row];
         float *tile = reinterpret_cast<float *>(stage_out);
-        epi_sync();   // the previous tile's copy-out has finished reading the staging buffer
 #pragma unroll
         for (int c = 0; c < 64; c += 32) {
           float v[32];
@@ -643,40 +692,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc::tc_fence_before();
             tc::mbar_arrive(&bar->acc_empty[buf]);
           }
-          const int col0 = j0 + h * 64 + c;
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const float cs = (a.col_scale && col0 + jj < a.Ncols) ? a.col_scale[zb * a.cs_b + col0 + jj] : 1.f;
-            v[jj] *= rsc * cs;
-          }
+          const int col = h * 64 + c;    // tile column of v[0]; box col / 32 holds v[0..31]
+          float *box = tile + (col / 32) * (kTile * 32) + row * 32;
 #pragma unroll
           for (int t4 = 0; t4 < 8; ++t4) {
-            const int chunk = (h * 64 + c) / 4 + t4;
-            const int pc = chunk ^ (row & 31);
-            *reinterpret_cast<float4 *>(tile + row * 128 + pc * 4) =
-                make_float4(v[4 * t4], v[4 * t4 + 1], v[4 * t4 + 2], v[4 * t4 + 3]);
+            const float4 cs = *reinterpret_cast<const float4 *>(&s_sc[col + 4 * t4]);
+            *reinterpret_cast<float4 *>(box + ((t4 ^ (row & 7)) * 4)) =
+                make_float4(v[4 * t4] * (rsc * cs.x), v[4 * t4 + 1] * (rsc * cs.y), v[4 * t4 + 2] * (rsc * cs.z),
+                            v[4 * t4 + 3] * (rsc * cs.w));
           }
         }
+        fence_proxy_async_smem();
         epi_sync();
-        for (int rr = warp - 2; rr < kTile; rr += 8) {
-          const int gi = i0 + rr;
-          if (gi >= a.M) break;
-          const int pc = lane ^ (rr & 31);
-          const float4 val = *reinterpret_cast<const float4 *>(tile + rr * 128 + pc * 4);
-          const int gj = j0 + 4 * lane;
-          float *dst = a.Cf + (long long)b * a.sCb + (long long)gi * a.ldc + gj;
-          if (gj + 3 < a.Ncols) {
-            if (a.accumulate) {
-              const float4 o = *reinterpret_cast<const float4 *>(dst);
-              *reinterpret_cast<float4 *>(dst) = make_float4(o.x + val.x, o.y + val.y, o.z + val.z, o.w + val.w);
-            } else {
-              *reinterpret_cast<float4 *>(dst) = val;
+        if (storer) {
+#pragma unroll
+          for (int bx = 0; bx < 4; ++bx) {
+            const int x = j0 + 32 * bx;
+            if (x < a.Ncols) {
+              if (a.accumulate)
+                tma_reduce_add_3d(&tmC_hi, stage_out + (size_t)bx * (kTile * 128), x, i0, b);
+              else
+                tma_store_3d(&tmC_hi, stage_out + (size_t)bx * (kTile * 128), x, i0, b);
             }
-          } else {
-            const float vv[3] = {val.x, val.y, val.z};
-            for (int t = 0; t < 3; ++t)
-              if (gj + t < a.Ncols) dst[t] = a.accumulate ? dst[t] + vv[t] : vv[t];
           }
+          bulk_commit();
         }
         continue;
       }
@@ -1145,6 +1184,35 @@ bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, u
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     if (err) *err = "cuTensorMapEncodeTiled (store) failed with CUresult " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+bool make_tmap_f32_store3d(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint64_t batch,
+                           uint64_t ld, uint64_t batch_stride, std::string *err) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      if (err) *err = "cuTensorMapEncodeTiled entry point not available";
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // element (x, row, b) at b * batch_stride + row * ld + x; box 32 columns (128 B) x 128 rows
+  cuuint64_t dims[3] = {cols, rows, batch};
+  cuuint64_t strides[2] = {ld * 4, batch_stride * 4};
+  cuuint32_t box[3] = {32, 128, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (err) *err = "cuTensorMapEncodeTiled (FP32 store) failed with CUresult " + std::to_string((int)r);
     return false;
   }
   return true;

@@ -35,7 +35,8 @@ struct GemmTcArgs {
   float *group_scale = nullptr;
   // kStoreF32: Cf[b * sCb + i * ldc + j] = alpha * acc(i, j) * row_scale[zA * rs_b + i] * col_scale[zB * cs_b + j]
   // (either scale may be NULL); rows >= M and columns >= Ncols are not written.  Cf 16-byte
-  // aligned, ldc and sCb multiples of 4.
+  // aligned, ldc and sCb multiples of 4; the stores go through the FP32 tensor map passed as
+  // the first output map (make_tmap_f32_store3d over Ncols x M x batch).
   float *Cf = nullptr;
   long long ldc = 0, sCb = 0;
   float alpha = 1.f;
@@ -59,6 +60,10 @@ bool make_tmap_f16_3d_rs(CUtensorMap *map, const void *base, uint64_t d0, uint64
 size_t tc_smem_bytes();
 bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, uint64_t n_groups, uint64_t rows,
                            uint64_t batch, std::string *err);
+// FP32 output [batch][rows][ld] (cols <= ld valid columns) for the kStoreF32 epilogue's TMA
+// stores: base 16-byte aligned, ld and batch_stride multiples of 4 elements
+bool make_tmap_f32_store3d(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint64_t batch,
+                           uint64_t ld, uint64_t batch_stride, std::string *err);
 // Variants of the fused kernel: G_R / G_wP^T resident in shared memory for the whole
 // (spin, tau) batch (Kp <= 128 only), or streamed with A_v and U2_v.
 enum { kBcdResident = 1, kBcdStreamed = 2 };
