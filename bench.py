@@ -228,6 +228,11 @@ FP64_PEAK_TFLOPS = 1.20
 BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726431744 + 20530944, "shared": 36.9e6,
                "source": "ncu dram__bytes_read+write of k_sox_bcd_tc on 16 batches, scaled to the launch's batches"}
 FP32_PEAK_TFLOPS = 78.4
+# DRAM bytes (read + write) of the B and C GEMM launches of one static (tau, v) pair of the
+# 3x3x3 solid (n=26, N=300), from an ncu capture; compared with the pair's algorithmic bytes
+SOLID_BC_TRAFFIC = {"shape": ((3, 3, 3), 26, 300), "bytes": 64460032 + 467337216 + 117393152 + 464741376,
+                    "source": "ncu dram__bytes_read+write of the B and C k_gemm_f16x2 launches of one static "
+                              "(tau, v) pair (profile_case solid f16x2 4)"}
 
 
 class MoleculeCase(Case):
@@ -401,7 +406,7 @@ class SolidCase(Case):
         self.prec = prec
         self.name = w.name
         self.dtype = "cf16x2+f32acc,c128" if prec == "f16x2" else "c128"
-        self.hot = "kpoint_D" if prec == "f16x2" else "kpoint_dynamic_f64"
+        self.hot = "kpoint_bc" if prec == "f16x2" else "kpoint_dynamic_f64"
         self.units = 1.0
         self.cpu_points_per_build = w.n_tau * w.n_spin
         M = (w.n_tau - 1) // 2
@@ -445,11 +450,25 @@ class SolidCase(Case):
         return _zflops(static), _zflops(dyn)
 
     def hot_flops_per_step(self):
-        if self.prec == "f16x2":   # the n_k^3 D step, static and dynamic parts: 8 flops per complex MAC
-            w = self.w
-            nk = w.nk[0] * w.nk[1] * w.nk[2]
-            return 2 * _zflops(nk ** 3 * w.N * w.N * w.n * w.n_tau * w.n_spin)
         return self.phase_flops()[1]
+
+    def bc_bytes_per_step(self):
+        """Algorithmic HBM bytes of the B and C GEMMs, static and dynamic parts: per (tau, v)
+        the two n_k^2 x N x N complex FP32 outputs and their FP16-pair operands (K = n)."""
+        w = self.w
+        nk = w.nk[0] * w.nk[1] * w.nk[2]
+        N, n = w.N, w.n
+        kp2 = -(-2 * n // 64) * 64                 # halves per split row
+        out = 2 * nk * nk * N * N * 8
+        ops = (nk * nk * N + nk * 2 * N + nk * N + nk * nk * 2 * N) * kp2 * 4
+        return 2 * w.n_tau * n * w.n_spin * (out + ops)
+
+    def d_bytes_per_step(self):
+        """Algorithmic HBM bytes of the D step: B and C read once, D (FP64 complex) read and written."""
+        w = self.w
+        nk = w.nk[0] * w.nk[1] * w.nk[2]
+        ldn = w.N + (w.N & 1)
+        return 2 * w.n_tau * w.n * w.n_spin * (2 * nk * nk * w.N * w.N * 8 + 2 * nk * w.N * ldn * 16)
 
     def fp64_compare(self, value: float) -> dict:
         if self.prec == "fp64":
@@ -675,7 +694,8 @@ def run_ours(args):
     hot_n, hot_ms = pkg.sox_profile_read(case.h, case.hot)
     phases = {}
     if isinstance(case, SolidCase):
-        for ph in (("kpoint_tc", "kpoint_dynamic_tc") if case.prec == "f16x2" else ("kpoint_f64", "kpoint_dynamic_f64")):
+        for ph in (("kpoint_tc", "kpoint_dynamic_tc", "kpoint_D") if case.prec == "f16x2"
+                   else ("kpoint_f64", "kpoint_dynamic_f64")):
             phases[ph] = pkg.sox_profile_read(case.h, ph)
     if isinstance(case, BatchCase) and case.backward:
         phases["adjoint"] = pkg.sox_profile_read(case.h, "phi_adjoint_tc" if case.prec == "f16x2" else "phi_adjoint_f64")
@@ -719,14 +739,26 @@ def run_ours(args):
     hot_s = hot_ms / 1e3
     achieved = case.hot_flops_per_step() * args.steps / hot_s / 1e12 if hot_n and hot_s > 0 else None
     if isinstance(case, SolidCase) and case.prec == "f16x2":
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None, "kernel": "k_kpoint_D_reg",
-                "peak_source": "measured FP32 FMA rate (paper_2412_18829_gb300/probes/fp_rate.cu)",
-                "note": "the n_k^3 D step (FP32 complex products, FP64 accumulation over v), static and dynamic "
-                        "parts; 8 flops per complex MAC"}
+        gbs = case.bc_bytes_per_step() * args.steps / hot_s / 1e9 if hot_n and hot_s > 0 else None
+        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"] if gbs else None, "traffic": None,
+                "kernel": "k_gemm_f16x2 (the B and C GEMMs of the solid chain)", "peak_source": pk_src,
+                "note": "algorithmic bytes: per (tau, v) the n_k^2 N x N complex FP32 B and C tiles written "
+                        "and their FP16-pair operands read, static and dynamic parts"}
         f_static, f_dyn = case.phase_flops()
         extra["phase_ms_per_step"] = {k: v[1] / args.steps for k, v in phases.items()}
-        extra["phase_ms_per_step"]["kpoint_D"] = hot_ms / args.steps
+        extra["phase_ms_per_step"]["kpoint_bc"] = hot_ms / args.steps
+        w = case.w
+        if (tuple(w.nk), w.n, w.N) == SOLID_BC_TRAFFIC["shape"]:
+            pair = case.bc_bytes_per_step() / (2 * w.n_tau * w.n * w.n_spin)
+            roof["traffic"] = SOLID_BC_TRAFFIC["bytes"]
+            roof["traffic_unit"] = "bytes per static (tau, v) pair of B and C launches"
+            roof["algorithmic_bytes_per_pair"] = pair
+            roof["traffic_source"] = SOLID_BC_TRAFFIC["source"]
+        d_n, d_ms = phases.get("kpoint_D", (0, 0.0))
+        extra["phase_ms_per_step"]["kpoint_D"] = d_ms / args.steps
+        if d_ms:
+            extra["d_step_gbs"] = case.d_bytes_per_step() * args.steps / (d_ms / 1e3) / 1e9
         extra["algorithmic_tflops_per_s"] = (f_static + f_dyn) * value / 1e12
     elif isinstance(case, SolidCase):
         f_static, f_dyn = case.phase_flops()

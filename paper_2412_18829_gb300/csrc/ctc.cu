@@ -304,59 +304,6 @@ __global__ void __launch_bounds__(128) k_kpoint_D_reg(const float2 *B, const flo
   }
 }
 
-// The D step for a mesh known at compile time: with k_w and k unrolled every momentum
-// index is a constant, so the n_k values B[(., k_s)][e] sit in registers and each
-// complex product costs four FMAs and no memory access.
-template <int N1, int N2, int N3>
-struct MeshT {
-  static constexpr int NK = N1 * N2 * N3;
-  __host__ __device__ static constexpr int minus(int a, int b) {
-    return (((a / (N2 * N3)) - (b / (N2 * N3)) + N1) % N1) * N2 * N3 +
-           ((((a / N3) % N2) - ((b / N3) % N2) + N2) % N2) * N3 + (((a % N3) - (b % N3) + N3) % N3);
-  }
-};
-
-template <int N1, int N2, int N3>
-__global__ void __launch_bounds__(128) k_kpoint_D_mesh(const float2 *B, const float2 *C, long long sP, long long sI,
-                                                      long long NN, int i0, long long sDi, double2 *D) {
-  using M = MeshT<N1, N2, N3>;
-  constexpr int NK = M::NK;
-  const int il = blockIdx.y;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= NN) return;
-  const float2 *Bi = B + (long long)il * sI + e, *Ci = C + (long long)il * sI + e;
-  float ar[NK], ai[NK];
-#pragma unroll
-  for (int k = 0; k < NK; ++k) ar[k] = ai[k] = 0.f;
-  for (int ks = 0; ks < NK; ++ks) {
-    float br[NK], bi[NK];
-#pragma unroll
-    for (int q1 = 0; q1 < NK; ++q1) {
-      const float2 b = __ldg(Bi + (long long)(q1 * NK + ks) * sP);
-      br[q1] = b.x;
-      bi[q1] = b.y;
-    }
-#pragma unroll
-    for (int kw = 0; kw < NK; ++kw) {
-      const float2 c = __ldg(Ci + (long long)(M::minus(kw, ks) * NK + kw) * sP);
-#pragma unroll
-      for (int k = 0; k < NK; ++k) {
-        const int q1 = M::minus(kw, k);
-        ar[k] = fmaf(c.x, br[q1], fmaf(-c.y, bi[q1], ar[k]));
-        ai[k] = fmaf(c.x, bi[q1], fmaf(c.y, br[q1], ai[k]));
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NK; ++k) {
-    double2 *d = D + (long long)(i0 + il) * sDi + (long long)k * NN + e;
-    double2 v = *d;
-    v.x += ar[k];
-    v.y += ai[k];
-    *d = v;
-  }
-}
-
 // The D step through the convolution theorem on the k mesh.  For one (P, R) element and
 // one k_s, with c(x) = C[(x - k_s, x)] and b(y) = B[(y, k_s)],
 //   D[k] += sum_x c(x) b(x - k),
@@ -977,29 +924,6 @@ Status kpoint_D_f32(const float *B, const float *C, long long sP, long long sI, 
         done = false;
     }
     if (done) return Status::ok();
-  }
-  {
-    dim3 grid((unsigned)((NN + 127) / 128), (unsigned)ct);
-    const float2 *Bf = reinterpret_cast<const float2 *>(B), *Cf = reinterpret_cast<const float2 *>(C);
-    double2 *Dd = reinterpret_cast<double2 *>(D);
-    const int key = mesh[0] * 100 + mesh[1] * 10 + mesh[2];
-    bool done = true;
-    switch (key) {
-#define SOX_DMESH(A, B_, C_)                                                             \
-  case A * 100 + B_ * 10 + C_:                                                          \
-    k_kpoint_D_mesh<A, B_, C_><<<grid, 128, 0, s>>>(Bf, Cf, sP, sI, NN, i0, sDi, Dd);  \
-    break;
-      SOX_DMESH(1, 1, 1) SOX_DMESH(1, 1, 2) SOX_DMESH(1, 2, 1) SOX_DMESH(2, 1, 1) SOX_DMESH(1, 1, 3)
-      SOX_DMESH(1, 3, 1) SOX_DMESH(3, 1, 1) SOX_DMESH(1, 2, 2) SOX_DMESH(2, 2, 1) SOX_DMESH(2, 1, 2)
-      SOX_DMESH(2, 2, 2) SOX_DMESH(3, 3, 1) SOX_DMESH(3, 3, 3)
-#undef SOX_DMESH
-      default:
-        done = false;
-    }
-    if (done && mesh[0] < 10 && mesh[1] < 10 && mesh[2] < 10) {
-      SOX_CUDA_TRY(cudaGetLastError());
-      return Status::ok();
-    }
   }
   {
     dim3 grid((unsigned)((NN + 127) / 128), (unsigned)ct);

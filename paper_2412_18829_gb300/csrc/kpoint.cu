@@ -765,10 +765,14 @@ Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, co
       for (int v = 0; v < g.n; ++v) {
         csplit_a(reinterpret_cast<const float2 *>(Aall) + (long long)v * ldNn, true, g.n * ldNn, g.n, 0, 0, 1,
                  (int)g.nk2, g.N, g.n, As, s);
-        // B^{q1,ks}_v[P][R] = sum_q A[v][P][q] GR^{ks-q1}[R][q]
-        SOX_TRY(cgemm_tc(h, As, GRs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
-        // C^{q2,kw}_v[P][R] = sum_w GWt^{kw}[P][w] M2^{q2,kw}[R][v][w]
-        SOX_TRY(cgemm_tc(h, GWts, M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
+        {
+          ProfScope pb(h, "kpoint_bc", s, 0);
+          // B^{q1,ks}_v[P][R] = sum_q A[v][P][q] GR^{ks-q1}[R][q]
+          SOX_TRY(cgemm_tc(h, As, GRs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
+          // C^{q2,kw}_v[P][R] = sum_w GWt^{kw}[P][w] M2^{q2,kw}[R][v][w]
+          SOX_TRY(
+              cgemm_tc(h, GWts, M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call, 2LL * g.ldN, 2LL * g.N * g.ldN, s));
+        }
         {
           ProfScope pd(h, "kpoint_D", s, 0);
           SOX_TRY(kpoint_D_f32(Ball, Call, (long long)g.N * g.ldN, 0, tb.add, tb.sub, pr->nk, (long long)g.N * g.ldN,
@@ -933,11 +937,14 @@ Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const
         // rows (il, P) of A^{pair}(tau_{i0+il}), K = u
         csplit_a(reinterpret_cast<const float2 *>(Adyn) + (size_t)i0 * d.ldNn, true, (long long)T * d.ldNn, d.ldNn, n,
                  N, 1, (int)g.nk2, cc * N, n, Ac, s);
-        // B^{q1,ks}(tau_i)[P][R] = sum_u A[P][u] X^{ks-q1}[R][u]
-        SOX_TRY(cgemm_tc(h, Ac, Xs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * cc * N * g.ldN, s));
-        // C^{q2,kw}(tau_i)[P][R] = sum_w GWt^{kw}(tau_i)[P][w] M2^{q2,kw}[R][v][w]
-        SOX_TRY(cgemm_tc(h, GWts.view((long long)i0 * N, cc * N), M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call,
-                         2LL * g.ldN, 2LL * cc * N * g.ldN, s));
+        {
+          ProfScope pb(h, "kpoint_bc", s, 0);
+          // B^{q1,ks}(tau_i)[P][R] = sum_u A[P][u] X^{ks-q1}[R][u]
+          SOX_TRY(cgemm_tc(h, Ac, Xs, (int)g.nk2, nullptr, tb.ku, 1.f, Ball, 2LL * g.ldN, 2LL * cc * N * g.ldN, s));
+          // C^{q2,kw}(tau_i)[P][R] = sum_w GWt^{kw}(tau_i)[P][w] M2^{q2,kw}[R][v][w]
+          SOX_TRY(cgemm_tc(h, GWts.view((long long)i0 * N, cc * N), M2s[v], (int)g.nk2, tb.kk, nullptr, 1.f, Call,
+                           2LL * g.ldN, 2LL * cc * N * g.ldN, s));
+        }
         {
           ProfScope pd(h, "kpoint_D", s, 0);
           SOX_TRY(kpoint_D_f32(Ball, Call, (long long)cc * N * g.ldN, (long long)N * g.ldN, tb.add, tb.sub, pr->nk,
