@@ -399,10 +399,11 @@ class SolidCase(Case):
     """Dynamically screened SOSEX of a solid (c3): SOX(v, v) + Sigma_d, split precision on the
     tensor cores (complex FP16 pairs, FP32 accumulation, FP64 ends) or FP64 complex."""
 
-    def __init__(self, torch, pkg, w, prec, dev, stream):
+    def __init__(self, torch, pkg, w, prec, dev, stream, rpa_w=False):
         import synth
 
         self.torch, self.pkg, self.w, self.dev, self.stream = torch, pkg, w, dev, stream
+        self.rpa_w = rpa_w
         self.prec = prec
         self.name = w.name
         self.dtype = "cf16x2+f32acc,c128" if prec == "f16x2" else "c128"
@@ -421,10 +422,13 @@ class SolidCase(Case):
         self.h = pkg.Handle(prec, device=dev.index or 0)
         self.config = {"workload": w.name, "nk": list(w.nk), "n": w.n, "N": w.N, "n_tau": w.n_tau,
                        "n_omega": self.nO, "beta": w.beta, "precision": prec,
-                       "W_d": "synthetic single-pole form (synth.pole_screening), input",
+                       "W_d": ("RPA W(i Omega) - v from G on the GPU (sox_w_dynamic) inside every step" if rpa_w
+                               else "synthetic single-pole form (synth.pole_screening), input"),
                        "step": "SOX(v, v) + dynamically screened Sigma_d through the C ABI"}
 
     def step(self):
+        if self.rpa_w:   # W_d(i Omega) = RPA W - v from this step's G, on the GPU
+            self.pkg.sox_w_dynamic(self.h, self.p, self.G, self.X, self.V, self.Tf, self.nO, self.Wd, self.stream)
         self.pkg.sosex_dynamic_sigma(self.h, self.p, self.G, self.X, self.V, self.Wd, self.Tf, self.Ti,
                                      self.nO, self.S, self.stream)
 
@@ -645,7 +649,7 @@ def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
 
             nk = tuple(int(x) for x in args.mesh.split(","))
             w = synth.solid(3, nk, w.n, w.N, w.n_tau, w.beta, name=f"sosexdyn-k{''.join(map(str, nk))}-n{w.n}-N{w.N}-t{w.n_tau}")
-        return SolidCase(torch, pkg, w, args.precision, dev, stream)
+        return SolidCase(torch, pkg, w, args.precision, dev, stream, rpa_w=args.rpa_w)
     shard = (rank, world, dist_mod) if (args.shard == "tau" and args.workload in ("c0", "c1")) else None
     return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"),
                         variant=args.variant, tau_shard=shard)
@@ -695,7 +699,7 @@ def run_ours(args):
     phases = {}
     if isinstance(case, SolidCase):
         for ph in (("kpoint_tc", "kpoint_dynamic_tc", "kpoint_D") if case.prec == "f16x2"
-                   else ("kpoint_f64", "kpoint_dynamic_f64")):
+                   else ("kpoint_f64", "kpoint_dynamic_f64")) + (("w_dynamic",) if case.rpa_w else ()):
             phases[ph] = pkg.sox_profile_read(case.h, ph)
     if isinstance(case, BatchCase) and case.backward:
         phases["adjoint"] = pkg.sox_profile_read(case.h, "phi_adjoint_tc" if case.prec == "f16x2" else "phi_adjoint_f64")
@@ -832,6 +836,8 @@ def main():
                     help="bare-SOX workloads on N GPUs: N independent builds, or one build split by tau "
                          "mirror pairs with an all-gather of Sigma")
     ap.add_argument("--mesh", default="3,3,3", help="solid workload: k-mesh (default 3,3,3)")
+    ap.add_argument("--rpa-w", action="store_true",
+                    help="solid workload: build W_d(i Omega) from G on the GPU inside every step")
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     args = ap.parse_args()

@@ -262,6 +262,25 @@ SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream);
 
+/* RPA screened interaction on the transform's bosonic frequencies: the W_d input of
+ * sosex_dynamic_sigma built on the GPU from G (Sec. III C, W = v^1/2 (1 - v^1/2 Pi
+ * v^1/2)^-1 v^1/2, with the THC form of the bubble, Sec. II C):
+ *   Pi(tau_j)_PQ    = sum_s G_s^PQ(tau_j) G_s^QP(-tau_j),   G^PQ = sum_pp' X_Pp G_pp' X_Qp'
+ *   Pi(i Omega_m)   = sum_j T_fwd[m][j] Pi(tau_j)
+ *   Wd(i Omega_m)   = (1 - V Pi(i Omega_m))^-1 V - V
+ * (the same W as the symmetric form for positive semidefinite V), with
+ * G(-tau_j) = -G(tau_{n_tau-1-j}) on the mirror-symmetric grid and the spin blocks of
+ * G summed.  Molecules (SOX_REAL64): the real part of Pi(i Omega_m), symmetrised; Wd
+ * [n_omega][N][N] real.  Solids (SOX_COMPLEX128, mesh sides <= 8): per transfer q,
+ *   Pi^q(tau_j)_PQ = 1/N_k sum_k G^PQ_{k+q}(tau_j) G^QP_k(-tau_j),  G^PQ_k = X^k G^k X^k^H,
+ * and Wd [n_q][n_omega][N][N] complex, the layout sosex_dynamic_sigma reads.
+ * T_fwd [n_omega][n_tau] complex (interleaved).  FP64 throughout; the solve is
+ * Gauss-Jordan with partial pivoting batched over (q, m).  Synchronises `stream`.
+ * Returns SOX_ERR_INVALID_ARG if some 1 - V Pi is singular, SOX_ERR_SHAPE for a mesh
+ * side above 8 or more than 65535 (q, m) systems. */
+SOX_API int sox_w_dynamic(sox_handle h, const sox_problem *p, const double *G, const double *X,
+                          const double *V, const double *T_fwd, int n_omega, double *Wd, void *stream);
+
 /* Batch of independent bare-SOX problems (uneven sizes allowed), one launch
  * sequence on one stream.  probs, G, X, V, Sigma are HOST arrays of `count`
  * entries; the tensors they point to follow the single-problem rules. */

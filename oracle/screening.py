@@ -45,6 +45,30 @@ def pi0_pole_sum(X: np.ndarray, eps: np.ndarray, U: np.ndarray, mu: float, beta:
     return -np.einsum("Pa,Qa,ab,Pb,Qb->PQ", y, y, c, y, y, optimize=True)
 
 
+def pi_omega_pole_sum(X: np.ndarray, eps: np.ndarray, U: np.ndarray, mu: float, beta: float,
+                      omegas: np.ndarray) -> np.ndarray:
+    """Exact int_0^beta e^{i Omega tau} G^PQ(tau) G^QP(-tau) d tau at bosonic Omega_m for
+    G = -U diag(e^{-xi tau}/(1+e^{-beta xi})) U^T.
+
+    With y = X U and f_a = 1/(1 + e^{beta xi_a}), G^PQ(tau) = -sum_a y_Pa y_Qa (1-f_a) e^{-xi_a tau}
+    and G^QP(-tau) = sum_b y_Qb y_Pb f_b e^{xi_b tau}; since e^{i Omega beta} = 1 and
+    (1-f_a) f_b (e^{beta (xi_b - xi_a)} - 1) = f_a - f_b the integral is
+        Pi_PQ(i Omega) = -sum_ab y_Pa y_Qa y_Pb y_Qb (f_a - f_b) / (i Omega - xi_a + xi_b),
+    the a = b terms vanishing for Omega != 0 and giving pi0_pole_sum's limit at Omega = 0.
+    """
+    xi = eps - mu
+    f = 0.5 * (1.0 - np.tanh(0.5 * beta * xi))
+    y = X @ U
+    out = []
+    for om in np.atleast_1d(omegas):
+        if om == 0.0:
+            out.append(pi0_pole_sum(X, eps, U, mu, beta).astype(complex))
+            continue
+        c = (f[:, None] - f[None, :]) / (1j * om - xi[:, None] + xi[None, :])
+        out.append(-np.einsum("Pa,Qa,ab,Pb,Qb->PQ", y, y, c, y, y, optimize=True))
+    return np.stack(out)
+
+
 def w_static(V: np.ndarray, Pi: np.ndarray) -> np.ndarray:
     """W = V^1/2 (1 - V^1/2 Pi V^1/2)^-1 V^1/2 with V^1/2 from the eigendecomposition of V."""
     lam, Q = np.linalg.eigh(V)

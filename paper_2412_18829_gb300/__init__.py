@@ -16,6 +16,7 @@ from ._binding import (  # noqa: F401
     phi_sox_grad_G,
     problem,
     sosex_dynamic_sigma,
+    sox_w_dynamic,
     sosex_static_sigma,
     sox_check_device,
     sox_pi0,

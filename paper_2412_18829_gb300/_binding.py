@@ -62,6 +62,7 @@ _SIGS = {
     "phi_sox_backward": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "phi_sox_grad_G": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
     "sosex_dynamic_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _I, _P, _P], _I),
+    "sox_w_dynamic": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _I, _P, _P], _I),
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
     "sox_sigma_fp64_noalloc": ([ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
@@ -270,6 +271,11 @@ def sosex_dynamic_sigma(h: Handle, p: sox_problem, G, X, V, Wd, T_fwd, T_inv, n_
     h.check(lib().sosex_dynamic_sigma(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(Wd),
                                       _ptr(T_fwd), _ptr(T_inv), int(n_omega), _ptr(Sigma),
                                       _stream(stream)))
+
+
+def sox_w_dynamic(h: Handle, p: sox_problem, G, X, V, T_fwd, n_omega, Wd, stream=None):
+    h.check(lib().sox_w_dynamic(h.ptr, ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(T_fwd), int(n_omega),
+                                _ptr(Wd), _stream(stream)))
 
 
 def sox_sigma_batch(h: Handle, probs, G, X, V, Sigma, stream=None):

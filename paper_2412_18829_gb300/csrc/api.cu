@@ -847,6 +847,41 @@ int phi_sox_grad_G(sox_handle h, const sox_problem *p, const double *Sigma, cons
   return finish(h, st);
 }
 
+int sox_w_dynamic(sox_handle h, const sox_problem *p, const double *G, const double *X, const double *V,
+                  const double *T_fwd, int n_omega, double *Wd, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    if (!G || !X || !V || !T_fwd || !Wd) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    if (n_omega < 1 || n_omega > SOX_MAX_N_TAU) return {SOX_ERR_SHAPE, "n_omega out of range [1, SOX_MAX_N_TAU]"};
+    const bool solid = p && (p->dtype == SOX_COMPLEX128 || p->nk[0] * p->nk[1] * p->nk[2] != 1);
+    if (solid) {
+      SOX_TRY(validate(p, false));
+      if (p->dtype != SOX_COMPLEX128)
+        return {SOX_ERR_UNSUPPORTED, "k-point meshes need complex data (SOX_COMPLEX128)"};
+    } else {
+      SOX_TRY(validate(p));
+    }
+    const int nk = p->nk[0] * p->nk[1] * p->nk[2];
+    if (p->nk[0] > 8 || p->nk[1] > 8 || p->nk[2] > 8) return {SOX_ERR_SHAPE, "mesh sides above 8"};
+    if ((long long)nk * n_omega > 65535) return {SOX_ERR_SHAPE, "more than 65535 (q, Omega) systems"};
+    SOX_TRY(bind_device(h));
+    const size_t c = solid ? 2 : 1;
+    const size_t nn = (size_t)p->n * p->n, NN = (size_t)p->N * p->N;
+    Call call(h, stream);
+    Staged sG, sX, sV, sF, oW;
+    SOX_TRY(call.input(G, c * p->n_spin * nk * p->n_tau * nn, &sG));
+    SOX_TRY(call.input(X, c * nk * p->N * p->n, &sX));
+    SOX_TRY(call.input(V, c * nk * NN, &sV));
+    SOX_TRY(call.input(T_fwd, 2 * (size_t)n_omega * p->n_tau, &sF));
+    SOX_TRY(call.output(Wd, c * nk * n_omega * NN, &oW));
+    Arena ar;
+    SOX_TRY(call.begin(sox::w_dynamic_bytes(p, n_omega), &ar));
+    SOX_TRY(sox::w_dynamic(h, p, n_omega, sG.in, sX.in, sV.in, sF.in, oW.out, ar, call.stream()));
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
 int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, const double *X,
                         const double *V, const double *Wd, const double *T_fwd,
                         const double *T_inv, int n_omega, double *Sigma, void *stream) {

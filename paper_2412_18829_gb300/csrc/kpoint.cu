@@ -965,4 +965,336 @@ Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const
   return Status::ok();
 }
 
+
+// ===========================================================================
+// RPA screened interaction on the transform's bosonic frequencies (the input of the
+// dynamic path), for every transfer q of the mesh (a molecule is the mesh 1x1x1):
+//   Pi^q(tau_j)_PQ = 1/N_k sum_k G^PQ_{k+q}(tau_j) G^QP_k(-tau_j),  G^PQ_k = X^k G^k X^k^H
+//   Pi^q(i Omega_o) = sum_j T_fwd[o][j] Pi^q(tau_j)
+//   W_d^q(i Omega_o) = (1 - V^q Pi^q(i Omega_o))^-1 V^q - V^q
+// The k sum is a cyclic cross-correlation over the mesh: with A-hat(m) = sum_k w^{-m.k}
+// A_k (one in-place DFT of the projections over k), its transform is the pointwise product
+// A-hat_{tau_j}(m)[P][Q] A-hat_{tau_{T-1-j}}(-m)[Q][P] (G(-tau_j) = -G(tau_{T-1-j})), so
+// the bubble of every q costs one pass over the projections and an inverse DFT over m.
+// FP64 throughout; the solve is Gauss-Jordan with partial pivoting, batched over (q, o).
+namespace {
+
+constexpr int kMaxSide = 8;
+
+__global__ void k_r2c(const double *src, z *dst, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = make_double2(src[e], 0.0);
+}
+
+// in-place DFT along mesh dimension dim of buf[k][inner] (k row-major over n1 x n2 x n3):
+// out[m] = scale sum_t exp(sgn 2 pi i m t / Nd) in[t]
+__global__ void k_mesh_dft(z *buf, long long inner, int n1, int n2, int n3, int dim, int sgn, double scale) {
+  const int Nd = dim == 0 ? n1 : (dim == 1 ? n2 : n3);
+  const long long sd = dim == 0 ? (long long)n2 * n3 : (dim == 1 ? n3 : 1);
+  const long long lines = (long long)(n1 * n2 * n3 / Nd) * inner;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < lines;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long e = g % inner;
+    const int r = (int)(g / inner);
+    int kb;
+    if (dim == 0)
+      kb = r;                                   // (c1, c2) with c0 = 0: r = c1 n3 + c2
+    else if (dim == 1)
+      kb = (r / n3) * n2 * n3 + (r % n3);       // (c0, c2)
+    else
+      kb = r * n3;                              // (c0, c1)
+    z v[kMaxSide];
+#pragma unroll
+    for (int t = 0; t < kMaxSide; ++t)
+      if (t < Nd) v[t] = buf[(kb + t * sd) * inner + e];
+#pragma unroll
+    for (int m = 0; m < kMaxSide; ++m) {
+      if (m >= Nd) break;
+      z acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int t = 0; t < kMaxSide; ++t) {
+        if (t >= Nd) break;
+        double sn, cs;
+        sincospi(2.0 * (double)((m * t) % Nd) / (double)Nd, &sn, &cs);
+        acc = zfma(make_double2(cs, sgn * sn), v[t], acc);
+      }
+      buf[(kb + m * sd) * inner + e] = make_double2(scale * acc.x, scale * acc.y);
+    }
+  }
+}
+
+// H[m][o][P][Q] += alpha sum_j T_fwd[o][j] Ah[m][j][P][Q] Ah[negm[m]][T-1-j][Q][P] for the
+// kBubF frequencies o of chunk blockIdx.z % n_chunks; 32 x 32 tiles, the transposed
+// partner through shared memory
+constexpr int kBubF = 4;
+__global__ void __launch_bounds__(256) k_bubble_reduce(const z *Ah, const z *Tf, const int *negm, int N, int T, int nO,
+                                                       int n_chunks, double alpha, z *H) {
+  __shared__ z ta[32][33];
+  __shared__ z tb[32][33];
+  const int m = blockIdx.z / n_chunks, o0 = (blockIdx.z % n_chunks) * kBubF;
+  const int P0 = blockIdx.y * 32, Q0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const long long NN = (long long)N * N;
+  const z *Am = Ah + (long long)m * T * NN, *Bm = Ah + (long long)negm[m] * T * NN;
+  z acc[4][kBubF];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int f = 0; f < kBubF; ++f) acc[i][f] = make_double2(0.0, 0.0);
+  for (int j = 0; j < T; ++j) {
+    const z *Aj = Am + (long long)j * NN, *Bj = Bm + (long long)(T - 1 - j) * NN;
+    for (int r = ty; r < 32; r += 8) {
+      const int P = P0 + r, Q = Q0 + tx;
+      ta[r][tx] = (P < N && Q < N) ? Aj[(long long)P * N + Q] : make_double2(0.0, 0.0);
+      const int Qb = Q0 + r, Pb = P0 + tx;
+      tb[r][tx] = (Qb < N && Pb < N) ? Bj[(long long)Qb * N + Pb] : make_double2(0.0, 0.0);   // tb[Q][P]
+    }
+    __syncthreads();
+    z w[kBubF];
+#pragma unroll
+    for (int f = 0; f < kBubF; ++f) w[f] = (o0 + f < nO) ? Tf[(long long)(o0 + f) * T + j] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ty + 8 * i;
+      const z pr = zmul(ta[r][tx], tb[tx][r]);
+#pragma unroll
+      for (int f = 0; f < kBubF; ++f) acc[i][f] = zfma(w[f], pr, acc[i][f]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int P = P0 + ty + 8 * i, Q = Q0 + tx;
+    if (P >= N || Q >= N) continue;
+#pragma unroll
+    for (int f = 0; f < kBubF; ++f) {
+      if (o0 + f >= nO) break;
+      z *h = H + ((long long)m * nO + o0 + f) * NN + (long long)P * N + Q;
+      const z v = *h;
+      *h = make_double2(v.x + alpha * acc[i][f].x, v.y + alpha * acc[i][f].y);
+    }
+  }
+}
+
+// molecules: Pi(i Omega) <- (Re Pi + Re Pi^T) / 2 in place, per frequency
+__global__ void k_sym_real(z *Pi, int N, int nO) {
+  const long long NN = (long long)N * N, total = NN * nO;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long o = g / NN, e = g % NN;
+    const int P = (int)(e / N), Q = (int)(e % N);
+    if (P > Q) continue;
+    z *a = Pi + o * NN + (long long)P * N + Q, *b = Pi + o * NN + (long long)Q * N + P;
+    const double s = 0.5 * (a->x + b->x);
+    *a = make_double2(s, 0.0);
+    *b = make_double2(s, 0.0);
+  }
+}
+
+// Aug[b] = [I | V^{b / nO}] for every system b, [N][2N]
+__global__ void k_gj_init_c(const z *V, int N, int nO, int batch, z *Aug) {
+  const long long NN = (long long)N * N, total = NN * batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long b = g / NN, e = g % NN;
+    const int i = (int)(e / N), j = (int)(e % N);
+    z *row = Aug + b * 2 * NN + (long long)i * 2 * N;
+    row[j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    row[N + j] = V[(b / nO) * NN + e];
+  }
+}
+
+// Gauss-Jordan step k of every system (one block each): the row of largest |a_ik|, i >= k,
+// is swapped into row k and row k is divided by its pivot; info[1] is set for a zero column
+__global__ void __launch_bounds__(256) k_gj_pivot_c(z *Aug, int N, int k, int *info) {
+  __shared__ double best[256];
+  __shared__ int bidx[256];
+  const long long W = 2LL * N;
+  z *A = Aug + (long long)blockIdx.x * N * W;
+  double bv = -1.0;
+  int bi = k;
+  for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
+    const z a = A[(long long)i * W + k];
+    const double m2 = a.x * a.x + a.y * a.y;
+    if (m2 > bv) {
+      bv = m2;
+      bi = i;
+    }
+  }
+  best[threadIdx.x] = bv;
+  bidx[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double ov = best[threadIdx.x + o];
+      const int oi = bidx[threadIdx.x + o];
+      if (ov > best[threadIdx.x] || (ov == best[threadIdx.x] && oi < bidx[threadIdx.x])) {
+        best[threadIdx.x] = ov;
+        bidx[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (!(best[0] > 0.0)) {
+    if (threadIdx.x == 0) atomicExch(&info[1], 1);
+    return;
+  }
+  const int p = bidx[0];
+  const z pv = A[(long long)p * W + k];
+  const double d = pv.x * pv.x + pv.y * pv.y;
+  const z inv = make_double2(pv.x / d, -pv.y / d);
+  for (long long j = k + threadIdx.x; j < W; j += blockDim.x) {
+    const z a = A[(long long)k * W + j];
+    const z b = A[(long long)p * W + j];
+    if (p != k) A[(long long)p * W + j] = a;
+    A[(long long)k * W + j] = zmul(b, inv);
+  }
+}
+
+// step k, part 2: column k eliminated from every other row (columns > k of both halves)
+__global__ void k_gj_elim_c(z *Aug, int N, int k, const int *info) {
+  if (info[1]) return;
+  const long long W = 2LL * N;
+  z *A = Aug + (long long)blockIdx.z * N * W;
+  const int ncols = (int)(W - (k + 1));
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  const long long col = k + 1 + j;
+  const z rk = A[(long long)k * W + col];
+  for (int i = blockIdx.y; i < N; i += gridDim.y) {
+    if (i == k) continue;
+    const z f = A[(long long)i * W + k];
+    z *c = A + (long long)i * W + col;
+    *c = zfma(make_double2(-f.x, -f.y), rk, *c);
+  }
+}
+
+// W_d[b] = right half of Aug[b] - V^{b / nO}; molecules keep the real part
+__global__ void k_gj_out(const z *Aug, const z *V, int N, int nO, int batch, int real_out, double *Wd) {
+  const long long NN = (long long)N * N, total = NN * batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long b = g / NN, e = g % NN;
+    const int i = (int)(e / N), j = (int)(e % N);
+    const z w = Aug[b * 2 * NN + (long long)i * 2 * N + N + j], v = V[(b / nO) * NN + e];
+    if (real_out)
+      Wd[g] = w.x - v.x;
+    else
+      reinterpret_cast<z *>(Wd)[g] = make_double2(w.x - v.x, w.y - v.y);
+  }
+}
+
+unsigned grid_of(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 1 << 20)); }
+
+void mesh_dft(z *buf, long long inner, const int nk3[3], int sgn, cudaStream_t s) {
+  for (int d = 0; d < 3; ++d) {
+    if (nk3[d] == 1) continue;
+    const long long lines = (long long)(nk3[0] * nk3[1] * nk3[2] / nk3[d]) * inner;
+    k_mesh_dft<<<grid_of(lines), 256, 0, s>>>(buf, inner, nk3[0], nk3[1], nk3[2], d, sgn, 1.0);
+  }
+}
+
+}  // namespace
+
+size_t w_dynamic_bytes(const sox_problem *p, int n_omega) {
+  const size_t nk = (size_t)p->nk[0] * p->nk[1] * p->nk[2];
+  const size_t N = p->N, n = p->n, T = p->n_tau, NN = N * N;
+  size_t b = 0;
+  if (p->dtype != SOX_COMPLEX128)   // complex copies of G, X, V
+    b += aligned_bytes((size_t)p->n_spin * T * n * n, 16) + aligned_bytes(N * n, 16) + aligned_bytes(NN, 16);
+  b += aligned_bytes(T * N * n, 16);                 // X^k G^k(tau)
+  b += aligned_bytes(nk * T * NN, 16);               // projections, then their DFT over k
+  b += aligned_bytes(nk * n_omega * NN, 16);         // the bubble per (m, o), then per (q, o)
+  b += aligned_bytes(nk * n_omega * 2 * NN, 16);     // [1 - V Pi | V] per (q, o)
+  b += aligned_bytes(nk, 4) + aligned_bytes(4, 4);
+  return b + (1 << 20);
+}
+
+Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *Gd, const double *Xd,
+                 const double *Vd, const double *Tfd, double *Wd, Arena &ar, cudaStream_t s) {
+  const int nk3[3] = {p->nk[0], p->nk[1], p->nk[2]};
+  const int nk = nk3[0] * nk3[1] * nk3[2];
+  if (nk3[0] > kMaxSide || nk3[1] > kMaxSide || nk3[2] > kMaxSide)
+    return {SOX_ERR_SHAPE, "sox_w_dynamic: mesh sides above 8 are not supported"};
+  const int N = p->N, n = p->n, T = p->n_tau, S = p->n_spin, nO = n_omega;
+  const long long NN = (long long)N * N, nn = (long long)n * n;
+  const bool real = p->dtype != SOX_COMPLEX128;
+  const z *G = reinterpret_cast<const z *>(Gd), *X = reinterpret_cast<const z *>(Xd);
+  const z *V = reinterpret_cast<const z *>(Vd);
+  if (real) {
+    z *Gc = ar.take<z>((size_t)S * T * nn), *Xc = ar.take<z>((size_t)N * n), *Vc = ar.take<z>((size_t)NN);
+    if (!Vc) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+    k_r2c<<<grid_of((long long)S * T * nn), 256, 0, s>>>(Gd, Gc, (long long)S * T * nn);
+    k_r2c<<<grid_of((long long)N * n), 256, 0, s>>>(Xd, Xc, (long long)N * n);
+    k_r2c<<<grid_of(NN), 256, 0, s>>>(Vd, Vc, NN);
+    G = Gc;
+    X = Xc;
+    V = Vc;
+  }
+  const z *Tf = reinterpret_cast<const z *>(Tfd);
+  z *GR = ar.take<z>((size_t)T * N * n), *Ah = ar.take<z>((size_t)nk * T * NN);
+  z *H = ar.take<z>((size_t)nk * nO * NN), *Aug = ar.take<z>((size_t)nk * nO * 2 * NN);
+  int *negm = ar.take<int>(nk), *info = ar.take<int>(4);
+  if (!info) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  std::vector<int> h_neg(nk);
+  for (int m = 0; m < nk; ++m) {
+    const int a = m / (nk3[1] * nk3[2]), b = (m / nk3[2]) % nk3[1], c = m % nk3[2];
+    h_neg[m] = (((nk3[0] - a) % nk3[0]) * nk3[1] + (nk3[1] - b) % nk3[1]) * nk3[2] + (nk3[2] - c) % nk3[2];
+  }
+  SOX_CUDA_TRY(cudaMemcpyAsync(negm, h_neg.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(info, 0, 4 * sizeof(int), s));
+  SOX_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(z) * (size_t)nk * nO * NN, s));
+  ProfScope ps(h, "w_dynamic", s, 0);
+  long long launches = 0;
+  const int n_chunks = (nO + kBubF - 1) / kBubF;
+  for (int sp = 0; sp < S; ++sp) {
+    for (int k = 0; k < nk; ++k) {
+      ZGemm a = zg();   // GR[j] = X^k G^k(tau_j)
+      a.M = N; a.Nc = n; a.K = n; a.batch = T;
+      a.A = X + (long long)k * N * n; a.sA = 0; a.ai = n; a.ak = 1;
+      a.B = G + ((long long)sp * nk + k) * T * nn; a.sB = nn; a.bk = n; a.bj = 1;
+      a.C = GR; a.sC = (long long)N * n; a.ci = n; a.cj = 1;
+      zgemm(a, s);
+      ZGemm b = zg();   // A_k(tau_j) = GR[j] X^k^H
+      b.M = N; b.Nc = N; b.K = n; b.batch = T;
+      b.A = GR; b.sA = (long long)N * n; b.ai = n; b.ak = 1;
+      b.B = X + (long long)k * N * n; b.sB = 0; b.bk = 1; b.bj = n; b.conjB = 1;
+      b.C = Ah + (long long)k * T * NN; b.sC = NN; b.ci = N; b.cj = 1;
+      zgemm(b, s);
+      launches += 2;
+    }
+    mesh_dft(Ah, (long long)T * NN, nk3, -1, s);   // A-hat(m) = sum_k w^{-m.k} A_k
+    dim3 grid((N + 31) / 32, (N + 31) / 32, (unsigned)(nk * n_chunks));
+    k_bubble_reduce<<<grid, 256, 0, s>>>(Ah, Tf, negm, N, T, nO, n_chunks, -1.0 / ((double)nk * nk), H);
+    launches += 4;
+  }
+  mesh_dft(H, (long long)nO * NN, nk3, 1, s);       // Pi^q = sum_m w^{+m.q} H(m)
+  if (real) k_sym_real<<<grid_of((long long)nO * NN), 256, 0, s>>>(H, N, nO);
+  const int batch = nk * nO;
+  k_gj_init_c<<<grid_of((long long)batch * NN), 256, 0, s>>>(V, N, nO, batch, Aug);
+  for (int q = 0; q < nk; ++q) {   // left half: I - V^q Pi^q(i Omega_o)
+    ZGemm g = zg();
+    g.M = N; g.Nc = N; g.K = N; g.batch = nO;
+    g.A = V + (long long)q * NN; g.sA = 0; g.ai = N; g.ak = 1;
+    g.B = H + (long long)q * nO * NN; g.sB = NN; g.bk = N; g.bj = 1;
+    g.C = Aug + (long long)q * nO * 2 * NN; g.sC = 2 * NN; g.ci = 2LL * N; g.cj = 1;
+    g.alpha = -1.0; g.beta = 1.0;
+    zgemm(g, s);
+  }
+  for (int k = 0; k < N; ++k) {
+    k_gj_pivot_c<<<batch, 256, 0, s>>>(Aug, N, k, info);
+    const int ncols = 2 * N - (k + 1);
+    k_gj_elim_c<<<dim3((ncols + 255) / 256, std::min(N, 64), batch), 256, 0, s>>>(Aug, N, k, info);
+  }
+  k_gj_out<<<grid_of((long long)batch * NN), 256, 0, s>>>(Aug, V, N, nO, batch, real ? 1 : 0, Wd);
+  h->launches += launches + 2LL * N + 4 + nk;
+  SOX_CUDA_TRY(cudaGetLastError());
+  int hinfo[4] = {0, 0, 0, 0};
+  SOX_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+  SOX_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hinfo[1]) return {SOX_ERR_INVALID_ARG, "1 - V Pi(i Omega) is singular"};
+  return Status::ok();
+}
+
 }  // namespace sox

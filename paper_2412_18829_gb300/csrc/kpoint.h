@@ -21,4 +21,11 @@ size_t kpoint_dynamic_bytes(sox_handle h, int n, int N, int T, int n_omega, cons
 Status kpoint_dynamic_add_f64(sox_handle h, const sox_problem *p, int n_omega, const double *G, const double *X,
                               const double *V, const double *Wd, const double *T_fwd, const double *T_inv,
                               double *Sigma, Arena &ar, cudaStream_t s);
+// RPA screened interaction W_d^q(i Omega_o) = (1 - V^q Pi^q)^-1 V^q - V^q on the transform's
+// frequencies for every transfer q (molecules: the mesh 1x1x1, real data, real W_d
+// [n_omega][N][N]; solids: complex W_d [n_q][n_omega][N][N]); device inputs in the
+// library layouts, T_fwd [n_omega][n_tau] complex.  Synchronises s (reads the singular flag).
+size_t w_dynamic_bytes(const sox_problem *p, int n_omega);
+Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *G, const double *X, const double *V,
+                 const double *T_fwd, double *Wd, Arena &ar, cudaStream_t s);
 }  // namespace sox

@@ -49,3 +49,18 @@ def test_w_static_push_through_identity_and_screening():
     assert lam.min() > -1e-10 * np.abs(V).max()
     # no polarisation -> no screening
     np.testing.assert_allclose(screening.w_static(V, np.zeros_like(V)), V, atol=1e-12 * np.abs(V).max())
+
+
+def test_pi_omega_converges_to_pole_sum_at_every_frequency():
+    """The bubble through the caller's transform equals the exact transform of the pole
+    form at Omega_m = 2 pi m / beta, m = -3..3 (real, even in Omega)."""
+    beta, M = 2.0, 3
+    X, G, e, u, mu, tau = _small_system(beta=beta)
+    om, Tf, _ = synth.bosonic_transforms(tau, beta, M)
+    quad = screening.pi_omega(X, G, Tf)
+    exact = screening.pi_omega_pole_sum(X, e, u, mu, beta, om)
+    assert np.abs(quad - exact).max() < 1e-11 * np.abs(exact).max()
+    assert np.abs(exact.imag).max() < 1e-13 * np.abs(exact).max()
+    assert np.abs(exact - exact[::-1]).max() < 1e-13 * np.abs(exact).max()
+    # a dropped transform sign or a misplaced reflection would break the nonzero rows
+    assert np.abs(exact[0] - exact[M]).max() > 1e-3 * np.abs(exact).max()
