@@ -126,7 +126,8 @@ def oracle_tau_points_per_s(w, n_points: int, budget_s: float = 20.0):
     all k (the dynamic part is not timed by this sample)."""
     from oracle import grid as ogrid, kpoints as okp, sox as osox
 
-    pts = [(s, j) for j in (0, w.n_tau // 2, w.n_tau - 1, w.n_tau // 4) for s in range(w.n_spin)][:n_points]
+    taus = sorted({int(round(x)) for x in np.linspace(0, w.n_tau - 1, max(1, -(-n_points // w.n_spin)))})
+    pts = [(s, j) for j in taus for s in range(w.n_spin)][:n_points]
     t0 = time.perf_counter()
     done = []
     for s, j in pts:
