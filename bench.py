@@ -84,10 +84,14 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        t0 = time.perf_counter()   # the timed region starts once nvidia-smi is sampling
+        while time.perf_counter() - t0 < 5.0 and self.p.poll() is None and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.p is None:
@@ -822,7 +826,9 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default per workload: c0 100, c1 40, c2 10, c3 5, c4 3; "
+                         "the reference arm 10, 10, 3, 1, 3)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16x2", choices=["f16x2", "fp64"])
@@ -842,6 +848,10 @@ def main():
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     args = ap.parse_args()
+    if args.steps is None:   # about a second of timed GPU work for c1; bounded oracle runs for the reference
+        ours = {"c0": 100, "c1": 40, "c2": 10, "c3": 5, "c4": 3}
+        ref = {"c0": 10, "c1": 10, "c2": 3, "c3": 1, "c4": 3}
+        args.steps = (ref if args.impl == "reference" else ours)[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:
