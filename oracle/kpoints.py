@@ -266,6 +266,33 @@ def pi_omega(X, G_tau, T_fwd, nk):
     return out
 
 
+def pi_omega_pole_sum(X, eps, U, mu, beta, omegas, nk):
+    """Exact bubble of transfer q at bosonic Omega for G^k(tau) = -U_k diag(e^{-xi tau}/(1+e^{-beta xi})) U_k^H:
+    with y^k = X^k U_k and f^k_a = 1/(1 + e^{beta xi^k_a}),
+        Pi^q_PQ(i Omega) = -1/N_k sum_k sum_ab y^{k+q}_Pa conj(y^{k+q}_Qa) y^k_Qb conj(y^k_Pb) c_ab,
+        c_ab = (f^{k+q}_a - f^k_b) / (i Omega - xi^{k+q}_a + xi^k_b),
+    (the k-resolved form of the molecular pole sum), with c_ab = beta f (1 - f) where Omega = 0
+    and the two energies coincide."""
+    add, _ = k_tables(nk)
+    n_k = X.shape[0]
+    xi = np.asarray(eps) - mu
+    f = 0.5 * (1.0 - np.tanh(0.5 * beta * xi))
+    y = np.einsum("kPp,kpa->kPa", X, U)
+    out = np.zeros((n_k, len(omegas), X.shape[1], X.shape[1]), complex)
+    for q in range(n_k):
+        for k in range(n_k):
+            kq = add[k, q]
+            d = xi[kq][:, None] - xi[k][None, :]
+            df = f[kq][:, None] - f[k][None, :]
+            for m, om in enumerate(omegas):
+                den = 1j * om - d
+                same = np.abs(den) < 1e-12
+                c = np.where(same, beta * f[kq][:, None] * (1.0 - f[kq][:, None]), df / np.where(same, 1.0, den))
+                out[q, m] -= np.einsum("Pa,Qa,ab,Qb,Pb->PQ", y[kq], y[kq].conj(), c, y[k], y[k].conj(),
+                                       optimize=True) / n_k
+    return out
+
+
 def w_dynamic(V, Pi_om):
     """W_d^q(i Omega_m) = W^q(i Omega_m) - V^q, W^q = V^q^1/2 (1 - V^q^1/2 Pi^q V^q^1/2)^-1 V^q^1/2
     per transfer q and frequency m (V^q Hermitian PSD).  Builds test inputs only."""

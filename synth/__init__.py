@@ -270,7 +270,7 @@ def solid(cfg: int, nk: tuple, n: int, N: int, n_tau: int, beta: float,
         done[iq] = done[jq] = True
     return Workload(name or f"solid-c{cfg}", n, N, n_tau, 1, beta, tuple(nk), tau,
                     np.ascontiguousarray(G), np.ascontiguousarray(X), np.ascontiguousarray(V),
-                    {"mu": mu, "eps": evals, "kvec": kvec, "r_P": rP})
+                    {"mu": mu, "eps": evals, "U": evecs, "kvec": kvec, "r_P": rP})
 
 
 def tiny(n: int, N: int, n_tau: int = 6, beta: float = 4.0, n_spin: int = 1, seed: int = 7) -> Workload:

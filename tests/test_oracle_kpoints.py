@@ -108,3 +108,19 @@ def test_chain_restricted_to_listed_k_points():
     full = kpoints.sox_sigma(w.X, w.V, w.G, w.nk, taus=[1])
     part = kpoints.sox_sigma(w.X, w.V, w.G, w.nk, taus=[1], k_list=[2, 0])
     assert np.array_equal(part[:, 0], full[:, 2]) and np.array_equal(part[:, 1], full[:, 0])
+
+
+def test_solid_bubble_converges_to_pole_sum_for_every_transfer():
+    """The k-resolved bubble through the caller's transform equals the exact transform of
+    the pole form for every transfer q and frequency (a dropped momentum shift, a swapped
+    pair of propagators or a misplaced conjugate changes the q != 0 blocks)."""
+    nk = (1, 2, 2)
+    beta, M = 2.0, 2
+    w = synth.solid(21, nk, 4, 6, 65, beta)
+    om, Tf, _ = synth.bosonic_transforms(w.tau, beta, M)
+    quad = kpoints.pi_omega(w.X, w.G[0], Tf, nk)
+    exact = kpoints.pi_omega_pole_sum(w.X, w.extras["eps"], w.extras["U"], w.extras["mu"], beta, om, nk)
+    scale = np.abs(exact).max()
+    assert np.abs(quad - exact).max() < 1e-11 * scale
+    assert np.abs(exact[1:] - exact[:1]).max() > 1e-3 * scale    # the transfers differ
+    assert np.abs(exact[:, M] - exact[:, M + 1]).max() > 1e-3 * scale   # so do the frequencies
