@@ -275,7 +275,10 @@ SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double
  *   Pi^q(tau_j)_PQ = 1/N_k sum_k G^PQ_{k+q}(tau_j) G^QP_k(-tau_j),  G^PQ_k = X^k G^k X^k^H,
  * and Wd [n_q][n_omega][N][N] complex, the layout sosex_dynamic_sigma reads.
  * T_fwd [n_omega][n_tau] complex (interleaved).  FP64 throughout; the solve is
- * Gauss-Jordan with partial pivoting batched over (q, m).  Synchronises `stream`.
+ * Gauss-Jordan with partial pivoting batched over (q, m).  When the rows of T_fwd pair
+ * up as +-Omega (row n_omega-1-m the conjugate of row m) and G is Hermitian (a real
+ * molecule: the pairs suffice), Wd(-Omega) = Wd(Omega)^H and only m < (n_omega+1)/2 is
+ * solved.  Synchronises `stream`.
  * Returns SOX_ERR_INVALID_ARG if some 1 - V Pi is singular, SOX_ERR_SHAPE for a mesh
  * side above 8 or more than 65535 (q, m) systems. */
 SOX_API int sox_w_dynamic(sox_handle h, const sox_problem *p, const double *G, const double *X,

@@ -11,6 +11,8 @@
 //   Sigma^k[t][r] = -1/N_k^2 sum_R conj(X^k[R][t]) sum_P D^k[P][R] X^k[P][r]
 // B and C for every (q, k') pair are produced for a chunk of v at a time.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ctc.h"
@@ -1092,8 +1094,8 @@ __global__ void k_sym_real(z *Pi, int N, int nO) {
   }
 }
 
-// Aug[b] = [I | V^{b / nO}] for every system b, [N][2N]
-__global__ void k_gj_init_c(const z *V, int N, int nO, int batch, z *Aug) {
+// Aug[b] = [I | V^{b / ns}] for every system b (ns systems per transfer), [N][2N]
+__global__ void k_gj_init_c(const z *V, int N, int ns, int batch, z *Aug) {
   const long long NN = (long long)N * N, total = NN * batch;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
@@ -1101,7 +1103,7 @@ __global__ void k_gj_init_c(const z *V, int N, int nO, int batch, z *Aug) {
     const int i = (int)(e / N), j = (int)(e % N);
     z *row = Aug + b * 2 * NN + (long long)i * 2 * N;
     row[j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-    row[N + j] = V[(b / nO) * NN + e];
+    row[N + j] = V[(b / ns) * NN + e];
   }
 }
 
@@ -1170,18 +1172,62 @@ __global__ void k_gj_elim_c(z *Aug, int N, int k, const int *info) {
   }
 }
 
-// W_d[b] = right half of Aug[b] - V^{b / nO}; molecules keep the real part
-__global__ void k_gj_out(const z *Aug, const z *V, int N, int nO, int batch, int real_out, double *Wd) {
+// W_d[q][o] = right half of Aug[b] - V^q for system b = q ns + o (o < ns); molecules keep
+// the real part
+__global__ void k_gj_out(const z *Aug, const z *V, int N, int nO, int ns, int batch, int real_out, double *Wd) {
   const long long NN = (long long)N * N, total = NN * batch;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const long long b = g / NN, e = g % NN;
     const int i = (int)(e / N), j = (int)(e % N);
-    const z w = Aug[b * 2 * NN + (long long)i * 2 * N + N + j], v = V[(b / nO) * NN + e];
+    const long long q = b / ns, out = (q * nO + b % ns) * NN + e;
+    const z w = Aug[b * 2 * NN + (long long)i * 2 * N + N + j], v = V[q * NN + e];
     if (real_out)
-      Wd[g] = w.x - v.x;
+      Wd[out] = w.x - v.x;
     else
-      reinterpret_cast<z *>(Wd)[g] = make_double2(w.x - v.x, w.y - v.y);
+      reinterpret_cast<z *>(Wd)[out] = make_double2(w.x - v.x, w.y - v.y);
+  }
+}
+
+// W_d^q(-Omega) = W_d^q(Omega)^H: frequencies o >= ns from o' = nO - 1 - o < ns
+__global__ void k_w_mirror(double *Wd, int N, int nO, int ns, int nq, int real_out) {
+  const long long NN = (long long)N * N, per = (long long)(nO - ns) * NN, total = per * nq;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long q = g / per, r = g % per;
+    const int o = ns + (int)(r / NN);
+    const long long e = r % NN;
+    const int i = (int)(e / N), j = (int)(e % N);
+    const long long dst = (q * nO + o) * NN + e, src = (q * nO + (nO - 1 - o)) * NN + (long long)j * N + i;
+    if (real_out) {
+      Wd[dst] = Wd[src];
+    } else {
+      const z v = reinterpret_cast<const z *>(Wd)[src];
+      reinterpret_cast<z *>(Wd)[dst] = make_double2(v.x, -v.y);
+    }
+  }
+}
+
+// out[0] = max |G|, out[1] = max |G_pq - conj(G_qp)| over count matrices n x n (as the bit
+// patterns of non-negative doubles, which order like the values)
+__global__ void k_herm_dev(const z *G, int n, long long count, unsigned long long *out) {
+  const long long nn = (long long)n * n, total = nn * count;
+  double m = 0.0, d = 0.0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long c = g / nn, e = g % nn;
+    const int p = (int)(e / n), q = (int)(e % n);
+    const z a = G[g], b = G[c * nn + (long long)q * n + p];
+    m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
+    d = fmax(d, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(m));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(d));
   }
 }
 
@@ -1207,7 +1253,7 @@ size_t w_dynamic_bytes(const sox_problem *p, int n_omega) {
   b += aligned_bytes(nk * T * NN, 16);               // projections, then their DFT over k
   b += aligned_bytes(nk * n_omega * NN, 16);         // the bubble per (m, o), then per (q, o)
   b += aligned_bytes(nk * n_omega * 2 * NN, 16);     // [1 - V Pi | V] per (q, o)
-  b += aligned_bytes(nk, 4) + aligned_bytes(4, 4);
+  b += aligned_bytes(nk, 4) + aligned_bytes(4, 4) + aligned_bytes(2, 8);
   return b + (1 << 20);
 }
 
@@ -1236,7 +1282,8 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
   z *GR = ar.take<z>((size_t)T * N * n), *Ah = ar.take<z>((size_t)nk * T * NN);
   z *H = ar.take<z>((size_t)nk * nO * NN), *Aug = ar.take<z>((size_t)nk * nO * 2 * NN);
   int *negm = ar.take<int>(nk), *info = ar.take<int>(4);
-  if (!info) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  unsigned long long *hdev = ar.take<unsigned long long>(2);
+  if (!hdev) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   std::vector<int> h_neg(nk);
   for (int m = 0; m < nk; ++m) {
     const int a = m / (nk3[1] * nk3[2]), b = (m / nk3[2]) % nk3[1], c = m % nk3[2];
@@ -1245,6 +1292,34 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
   SOX_CUDA_TRY(cudaMemcpyAsync(negm, h_neg.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s));
   SOX_CUDA_TRY(cudaMemsetAsync(info, 0, 4 * sizeof(int), s));
   SOX_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(z) * (size_t)nk * nO * NN, s));
+  // Frequencies in +-pairs (row nO-1-o of T_fwd the conjugate of row o) and G Hermitian give
+  // Pi^q(-Omega) = Pi^q(Omega)^H and W_d^q(-Omega) = W_d^q(Omega)^H: only o < ns are solved.
+  // A real molecule's bubble (the real part, symmetrised) needs the frequency pairs only.
+  int ns = nO;
+  {
+    std::vector<double> hT(2 * (size_t)nO * T);
+    unsigned long long hh[2] = {0, 0};
+    SOX_CUDA_TRY(cudaMemcpyAsync(hT.data(), Tfd, sizeof(double) * hT.size(), cudaMemcpyDeviceToHost, s));
+    if (!real) {
+      SOX_CUDA_TRY(cudaMemsetAsync(hdev, 0, 2 * sizeof(unsigned long long), s));
+      k_herm_dev<<<grid_of((long long)S * nk * T * nn), 256, 0, s>>>(G, n, (long long)S * nk * T, hdev);
+      SOX_CUDA_TRY(cudaMemcpyAsync(hh, hdev, sizeof(hh), cudaMemcpyDeviceToHost, s));
+    }
+    SOX_CUDA_TRY(cudaStreamSynchronize(s));
+    double tmax = 0.0, tdev = 0.0;
+    for (int o = 0; o < nO; ++o)
+      for (int j = 0; j < T; ++j) {
+        const double *a = &hT[2 * ((size_t)o * T + j)], *b = &hT[2 * ((size_t)(nO - 1 - o) * T + j)];
+        tmax = std::max(tmax, std::max(std::fabs(a[0]), std::fabs(a[1])));
+        tdev = std::max(tdev, std::max(std::fabs(a[0] - b[0]), std::fabs(a[1] + b[1])));
+      }
+    double gmax = 0.0, gdev = 0.0;
+    std::memcpy(&gmax, &hh[0], sizeof(double));
+    std::memcpy(&gdev, &hh[1], sizeof(double));
+    const bool pairs = tdev <= 1e-12 * tmax;
+    const bool herm = real || gdev <= 1e-12 * gmax;
+    if (pairs && herm) ns = (nO + 1) / 2;
+  }
   ProfScope ps(h, "w_dynamic", s, 0);
   long long launches = 0;
   const int n_chunks = (nO + kBubF - 1) / kBubF;
@@ -1271,14 +1346,14 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
   }
   mesh_dft(H, (long long)nO * NN, nk3, 1, s);       // Pi^q = sum_m w^{+m.q} H(m)
   if (real) k_sym_real<<<grid_of((long long)nO * NN), 256, 0, s>>>(H, N, nO);
-  const int batch = nk * nO;
-  k_gj_init_c<<<grid_of((long long)batch * NN), 256, 0, s>>>(V, N, nO, batch, Aug);
-  for (int q = 0; q < nk; ++q) {   // left half: I - V^q Pi^q(i Omega_o)
+  const int batch = nk * ns;
+  k_gj_init_c<<<grid_of((long long)batch * NN), 256, 0, s>>>(V, N, ns, batch, Aug);
+  for (int q = 0; q < nk; ++q) {   // left half: I - V^q Pi^q(i Omega_o), o < ns
     ZGemm g = zg();
-    g.M = N; g.Nc = N; g.K = N; g.batch = nO;
+    g.M = N; g.Nc = N; g.K = N; g.batch = ns;
     g.A = V + (long long)q * NN; g.sA = 0; g.ai = N; g.ak = 1;
     g.B = H + (long long)q * nO * NN; g.sB = NN; g.bk = N; g.bj = 1;
-    g.C = Aug + (long long)q * nO * 2 * NN; g.sC = 2 * NN; g.ci = 2LL * N; g.cj = 1;
+    g.C = Aug + (long long)q * ns * 2 * NN; g.sC = 2 * NN; g.ci = 2LL * N; g.cj = 1;
     g.alpha = -1.0; g.beta = 1.0;
     zgemm(g, s);
   }
@@ -1287,7 +1362,9 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
     const int ncols = 2 * N - (k + 1);
     k_gj_elim_c<<<dim3((ncols + 255) / 256, std::min(N, 64), batch), 256, 0, s>>>(Aug, N, k, info);
   }
-  k_gj_out<<<grid_of((long long)batch * NN), 256, 0, s>>>(Aug, V, N, nO, batch, real ? 1 : 0, Wd);
+  k_gj_out<<<grid_of((long long)batch * NN), 256, 0, s>>>(Aug, V, N, nO, ns, batch, real ? 1 : 0, Wd);
+  if (ns < nO)
+    k_w_mirror<<<grid_of((long long)nk * (nO - ns) * NN), 256, 0, s>>>(Wd, N, nO, ns, nk, real ? 1 : 0);
   h->launches += launches + 2LL * N + 4 + nk;
   SOX_CUDA_TRY(cudaGetLastError());
   int hinfo[4] = {0, 0, 0, 0};

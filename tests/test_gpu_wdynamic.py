@@ -111,3 +111,27 @@ def test_w_dynamic_rejects_wide_meshes(env):
     with pytest.raises(pkg.SoxError) as e:
         pkg.sox_w_dynamic(h, p, G, X, V, F, 3, Wd)
     assert e.value.code == 2
+
+
+def test_w_dynamic_without_the_frequency_symmetry(env):
+    """Unpaired frequencies (a molecule's last transform row dropped) and a non-Hermitian G
+    (a solid) take the full solve of every (q, Omega); both against the oracle."""
+    w = synth.molecule(93, 8, 30, 8, 20.0)
+    _, Tf, _ = synth.bosonic_transforms(w.tau, w.beta, 3)
+    Tf = np.ascontiguousarray(Tf[:-1])
+    ref = screening.w_dynamic(w.V[0], screening.pi_omega(w.X[0], w.G[0, 0], Tf))
+    got = _w_gpu(env, w, Tf, False)
+    assert np.abs(got - ref).max() <= W_REL * np.abs(ref).max()
+
+    nk = (1, 1, 3)
+    ws = synth.solid(94, nk, 3, 8, 4, 10.0)
+    rng = np.random.default_rng(5)
+    ws.G = ws.G + 1e-3 * np.abs(ws.G).max() * (rng.standard_normal(ws.G.shape)
+                                               + 1j * rng.standard_normal(ws.G.shape))
+    _, Tf, _ = synth.bosonic_transforms(ws.tau, ws.beta, 2)
+    ref = kpoints.w_dynamic(ws.V, kpoints.pi_omega(ws.X, ws.G[0], Tf, nk))
+    got = _w_gpu(env, ws, Tf, True)
+    assert np.abs(got - ref).max() <= W_REL * np.abs(ref).max()
+    # without Hermitian G the -Omega block is no conjugate transpose
+    H = np.conj(np.swapaxes(ref, -1, -2))
+    assert np.abs(ref[:, ::-1] - H).max() > 1e-6 * np.abs(ref).max()
