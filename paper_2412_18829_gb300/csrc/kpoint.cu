@@ -989,11 +989,17 @@ __global__ void k_r2c(const double *src, z *dst, long long count) {
     dst[e] = make_double2(src[e], 0.0);
 }
 
-// in-place DFT along mesh dimension dim of buf[k][inner] (k row-major over n1 x n2 x n3):
-// out[m] = scale sum_t exp(sgn 2 pi i m t / Nd) in[t]
-__global__ void k_mesh_dft(z *buf, long long inner, int n1, int n2, int n3, int dim, int sgn, double scale) {
+// twiddles exp(sgn 2 pi i r / Nd), r < Nd (computed on the host)
+struct MeshTw {
+  double2 w[kMaxSide];
+};
+
+// in-place DFT along mesh dimension dim of buf[k][.] (k row-major over n1 x n2 x n3, k-th
+// block at k * kstride, its first `inner` elements transformed):
+// out[m] = sum_t exp(sgn 2 pi i m t / Nd) in[t]
+__global__ void k_mesh_dft(z *buf, long long inner, long long kstride, int n1, int n2, int n3, int dim, MeshTw tw) {
   const int Nd = dim == 0 ? n1 : (dim == 1 ? n2 : n3);
-  const long long sd = dim == 0 ? (long long)n2 * n3 : (dim == 1 ? n3 : 1);
+  const long long sd = (dim == 0 ? (long long)n2 * n3 : (dim == 1 ? n3 : 1)) * kstride;
   const long long lines = (long long)(n1 * n2 * n3 / Nd) * inner;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < lines;
        g += (long long)gridDim.x * blockDim.x) {
@@ -1006,22 +1012,21 @@ __global__ void k_mesh_dft(z *buf, long long inner, int n1, int n2, int n3, int 
       kb = (r / n3) * n2 * n3 + (r % n3);       // (c0, c2)
     else
       kb = r * n3;                              // (c0, c1)
+    z *base = buf + (long long)kb * kstride + e;
     z v[kMaxSide];
 #pragma unroll
     for (int t = 0; t < kMaxSide; ++t)
-      if (t < Nd) v[t] = buf[(kb + t * sd) * inner + e];
+      if (t < Nd) v[t] = base[t * sd];
 #pragma unroll
     for (int m = 0; m < kMaxSide; ++m) {
       if (m >= Nd) break;
-      z acc = make_double2(0.0, 0.0);
+      z acc = v[0];
 #pragma unroll
-      for (int t = 0; t < kMaxSide; ++t) {
+      for (int t = 1; t < kMaxSide; ++t) {
         if (t >= Nd) break;
-        double sn, cs;
-        sincospi(2.0 * (double)((m * t) % Nd) / (double)Nd, &sn, &cs);
-        acc = zfma(make_double2(cs, sgn * sn), v[t], acc);
+        acc = zfma(tw.w[(m * t) % Nd], v[t], acc);
       }
-      buf[(kb + m * sd) * inner + e] = make_double2(scale * acc.x, scale * acc.y);
+      base[m * sd] = acc;
     }
   }
 }
@@ -1031,7 +1036,7 @@ __global__ void k_mesh_dft(z *buf, long long inner, int n1, int n2, int n3, int 
 // partner through shared memory
 constexpr int kBubF = 4;
 __global__ void __launch_bounds__(256) k_bubble_reduce(const z *Ah, const z *Tf, const int *negm, int N, int T, int nO,
-                                                       int n_chunks, double alpha, z *H) {
+                                                       int n_solve, int n_chunks, double alpha, z *H) {
   __shared__ z ta[32][33];
   __shared__ z tb[32][33];
   const int m = blockIdx.z / n_chunks, o0 = (blockIdx.z % n_chunks) * kBubF;
@@ -1055,7 +1060,7 @@ __global__ void __launch_bounds__(256) k_bubble_reduce(const z *Ah, const z *Tf,
     __syncthreads();
     z w[kBubF];
 #pragma unroll
-    for (int f = 0; f < kBubF; ++f) w[f] = (o0 + f < nO) ? Tf[(long long)(o0 + f) * T + j] : make_double2(0.0, 0.0);
+    for (int f = 0; f < kBubF; ++f) w[f] = (o0 + f < n_solve) ? Tf[(long long)(o0 + f) * T + j] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = ty + 8 * i;
@@ -1071,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_bubble_reduce(const z *Ah, const z *Tf,
     if (P >= N || Q >= N) continue;
 #pragma unroll
     for (int f = 0; f < kBubF; ++f) {
-      if (o0 + f >= nO) break;
+      if (o0 + f >= n_solve) break;
       z *h = H + ((long long)m * nO + o0 + f) * NN + (long long)P * N + Q;
       const z v = *h;
       *h = make_double2(v.x + alpha * acc[i][f].x, v.y + alpha * acc[i][f].y);
@@ -1233,11 +1238,16 @@ __global__ void k_herm_dev(const z *G, int n, long long count, unsigned long lon
 
 unsigned grid_of(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 1 << 20)); }
 
-void mesh_dft(z *buf, long long inner, const int nk3[3], int sgn, cudaStream_t s) {
+void mesh_dft(z *buf, long long inner, long long kstride, const int nk3[3], int sgn, cudaStream_t s) {
   for (int d = 0; d < 3; ++d) {
     if (nk3[d] == 1) continue;
+    MeshTw tw{};
+    for (int r = 0; r < nk3[d]; ++r) {
+      const double a = 2.0 * 3.14159265358979323846 * r / nk3[d];
+      tw.w[r] = make_double2(std::cos(a), sgn * std::sin(a));
+    }
     const long long lines = (long long)(nk3[0] * nk3[1] * nk3[2] / nk3[d]) * inner;
-    k_mesh_dft<<<grid_of(lines), 256, 0, s>>>(buf, inner, nk3[0], nk3[1], nk3[2], d, sgn, 1.0);
+    k_mesh_dft<<<grid_of(lines), 256, 0, s>>>(buf, inner, kstride, nk3[0], nk3[1], nk3[2], d, tw);
   }
 }
 
@@ -1322,7 +1332,7 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
   }
   ProfScope ps(h, "w_dynamic", s, 0);
   long long launches = 0;
-  const int n_chunks = (nO + kBubF - 1) / kBubF;
+  const int n_chunks = (ns + kBubF - 1) / kBubF;   // the bubble of the frequencies solved
   for (int sp = 0; sp < S; ++sp) {
     for (int k = 0; k < nk; ++k) {
       ZGemm a = zg();   // GR[j] = X^k G^k(tau_j)
@@ -1339,13 +1349,13 @@ Status w_dynamic(sox_handle h, const sox_problem *p, int n_omega, const double *
       zgemm(b, s);
       launches += 2;
     }
-    mesh_dft(Ah, (long long)T * NN, nk3, -1, s);   // A-hat(m) = sum_k w^{-m.k} A_k
+    mesh_dft(Ah, (long long)T * NN, (long long)T * NN, nk3, -1, s);   // A-hat(m) = sum_k w^{-m.k} A_k
     dim3 grid((N + 31) / 32, (N + 31) / 32, (unsigned)(nk * n_chunks));
-    k_bubble_reduce<<<grid, 256, 0, s>>>(Ah, Tf, negm, N, T, nO, n_chunks, -1.0 / ((double)nk * nk), H);
+    k_bubble_reduce<<<grid, 256, 0, s>>>(Ah, Tf, negm, N, T, nO, ns, n_chunks, -1.0 / ((double)nk * nk), H);
     launches += 4;
   }
-  mesh_dft(H, (long long)nO * NN, nk3, 1, s);       // Pi^q = sum_m w^{+m.q} H(m)
-  if (real) k_sym_real<<<grid_of((long long)nO * NN), 256, 0, s>>>(H, N, nO);
+  mesh_dft(H, (long long)ns * NN, (long long)nO * NN, nk3, 1, s);   // Pi^q = sum_m w^{+m.q} H(m), o < ns
+  if (real) k_sym_real<<<grid_of((long long)ns * NN), 256, 0, s>>>(H, N, ns);
   const int batch = nk * ns;
   k_gj_init_c<<<grid_of((long long)batch * NN), 256, 0, s>>>(V, N, ns, batch, Aug);
   for (int q = 0; q < nk; ++q) {   // left half: I - V^q Pi^q(i Omega_o), o < ns

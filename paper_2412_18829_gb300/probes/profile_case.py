@@ -7,6 +7,9 @@
         with the synthetic single-pole W_d; another mesh ("4,4,4") and sizes ("10,100") optional
     python -m paper_2412_18829_gb300.probes.profile_case screened [f16x2|fp64] [n_tau]
         sox_sigma twice on the screened molecule's shapes (n=250, N=2000), 4 tau by default
+    python -m paper_2412_18829_gb300.probes.profile_case wdyn [-] [n_tau]
+        sox_w_dynamic (RPA W_d for every transfer and frequency, FP64) on the 3x3x3 solid's
+        shapes (n=26, N=300), 60 tau and 59 frequencies by default
     python -m paper_2412_18829_gb300.probes.profile_case adjoint [f16x2|fp64] [n_tau]
         phi_sox_backward (dX, dV) twice on the largest batch instance's shapes (n=298,
         N=1788), 8 tau by default
@@ -74,6 +77,17 @@ def main(argv):
             for _ in range(2):
                 pkg.phi_sox_backward(h, p, G, X, V, tw, d, None, dX, S)
             pkg.sox_check_device(h)
+    elif kind == "wdyn":
+        T = int(argv[3]) if len(argv) > 3 else 60
+        w = synth.solid(3, (3, 3, 3), 26, 300, T, 300.0)
+        M = (T - 1) // 2
+        _, Tf, _ = synth.bosonic_transforms(w.tau, w.beta, M)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=complex)).cuda()   # noqa: E731
+        G, X, V, F = (to(a) for a in (w.G, w.X, w.V, Tf))
+        S = torch.empty(27, 2 * M + 1, w.N, w.N, dtype=torch.complex128, device="cuda")
+        p = pkg.problem(w.n, w.N, T, 1, w.beta, nk=w.nk, dtype=1)
+        with pkg.Handle("fp64") as h:
+            pkg.sox_w_dynamic(h, p, G, X, V, F, 2 * M + 1, S)
     else:
         raise SystemExit(f"unknown case {kind}")
     torch.cuda.synchronize()
