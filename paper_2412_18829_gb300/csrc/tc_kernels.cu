@@ -60,7 +60,6 @@ constexpr int kChunk = 64;              // K elements per TMA box (128 bytes of 
 constexpr int kTileBytes = kTile * kChunk * 2;  // 16 KB
 constexpr int kStageBytes = 4 * kTileBytes;     // hi/lo of both operands
 constexpr int kStages = 3;
-constexpr int kThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t kIdesc = tc::idesc_f16_f32(kTile, kTile);
 
 struct Barriers {

@@ -121,7 +121,7 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
                 const double *U2, double *Sigma, Arena &ar, cudaStream_t s) {
   const bool two = (U1 != U2);
   const Geometry g = geometry(h, n, N, T, S, two);
-  const int Kp = g.Kp, Np = g.Np, NR = g.NR, RG = g.RG, Bc = g.Bc;
+  const int Kp = g.Kp, NR = g.NR, RG = g.RG, Bc = g.Bc;
   const size_t Kp2 = (size_t)Kp * Kp;
   std::string err;
 
