@@ -19,5 +19,8 @@ real molecular data) written from the paper's definitions:
 * ``phi``        the Luttinger-Ward functional Phi_SOX and its gradients.
 * ``dynamic``    dynamically screened SOSEX (Eq. GG onward, Sec. II C).
 * ``kpoints``    the momentum-resolved forms for periodic solids.
+* ``scloop``     the self-consistent loop around Sigma for molecules (Dyson equation
+                 on fermionic Matsubara frequencies, chemical potential, Galitskii-Migdal
+                 energies, Sec. II A).
 """
-from . import grid, thc, sox, screening, phi, kpoints, dynamic  # noqa: F401
+from . import grid, thc, sox, screening, phi, kpoints, dynamic, scloop  # noqa: F401
