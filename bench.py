@@ -3,19 +3,29 @@
 
 A step is one full build through the C ABI.  Workloads (``--workload``):
 
-* c1 (default) bare SOX, mid-size molecule: n=120, N=600, 80 tau, 2 spins.  Both
+* c4 (default, the largest configuration) the uneven batch of 16 molecules
+  (n in [40, 400], N=6n, 120 tau): per instance Phi and Sigma (phi_sox), dPhi/dG
+  from the kept Sigma (phi_sox_grad_G) and dPhi/dX, dPhi/dV (phi_sox_backward);
+  instances are sharded over ranks.
+* c1 bare SOX, mid-size molecule: n=120, N=600, 80 tau, 2 spins.  Both
   THC mixed tensors, projections, A, the fused B/C/Hadamard reduction and the
   back-projection to orbitals for every tau point and spin.
 * c0 bare SOX, small molecule (n=20, N=80, 30 tau).
 * c2 statically screened SOSEX (n=250, N=2000, 100 tau): Pi(0), W(0) and
   SOX(W(0), v) per step.
 * c3 dynamically screened SOSEX of a solid (3x3x3 k-mesh, n=26, N=300, 60 tau),
-  W_d from a synthetic single-pole form; FP64 complex.
-* c4 the uneven batch of 16 molecules (n in [40, 400], N=6n, 120 tau): Phi, Sigma
-  and dPhi/dG of every instance per step; instances are sharded over ranks.
+  W_d from a synthetic single-pole form (or the GPU RPA with --rpa-w).
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
-the host cores instead (a bounded tau sample per step, scaled to builds/s).
+the host cores instead (a bounded sample per step, scaled to builds/s).
+
+``--profile-case KIND`` runs one small case for an ncu capture instead (one
+process, one GPU, a few GB on the device): KIND is molecule (sox_sigma twice at
+n=120, N=600, 2 spins), screened (sox_sigma twice at n=250, N=2000), batch
+(phi_sox + phi_sox_grad_G twice at the batch's largest instance, n=298, N=1788),
+adjoint (phi_sox_backward twice at that instance), solid (sosex_dynamic_sigma at
+the 3x3x3 solid's shapes; --mesh and --profile-sizes n,N change them) or wdyn
+(sox_w_dynamic at the solid's shapes); --profile-tau sets the tau points.
 """
 from __future__ import annotations
 
@@ -149,35 +159,84 @@ def oracle_tau_points_per_s(w, n_points: int, budget_s: float = 20.0):
 
 def points_per_build(name: str, w) -> float:
     """Oracle sample points (one tau point of one spin of ``w``) that make one build."""
-    if name != "c4":
-        return float(w.n_tau * w.n_spin)
+    return float(w.n_tau * w.n_spin)
+
+
+def batch_oracle_sample(budget_s: float = 20.0):
+    """The oracle on the uneven batch: one tau point (complex128 chain) of instances taken
+    smallest first over distinct sizes, stopping once `budget_s` is spent (at least three
+    sizes).  The time of one tau point of every instance is predicted from a power-law fit
+    t = a * cost^b over the sampled (cost, time) pairs, cost = 4 N^2 n^2 (the fit follows
+    the oracle's own growth, which is slower than the cost model at large n), and one build
+    is the predicted sum over instances times 120 tau points.  Returns
+    (builds/s, seconds spent, description)."""
     import synth
+    from oracle import sox as osox
     from paper_2412_18829_gb300 import sharding
 
     sizes = [int(n) for n in synth.batch_c4_sizes()]
-    return sum(sharding.build_cost(n, 6 * n, 120) for n in sizes) / sharding.build_cost(w.n, w.N, 1)
+    order = sorted(range(len(sizes)), key=lambda i: (sizes[i], i))
+    seen, picks = set(), []
+    for i in order:
+        if sizes[i] not in seen:
+            seen.add(sizes[i])
+            picks.append(i)
+    t0 = time.perf_counter()
+    pts = []
+    for i in picks:
+        if len(pts) >= 3 and time.perf_counter() - t0 > budget_s:
+            break
+        w = synth.c4_instance(i)
+        a = time.perf_counter()
+        osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[0, 0], taus=[0])
+        pts.append((sharding.build_cost(w.n, w.N, 1), time.perf_counter() - a, w.n))
+    spent = time.perf_counter() - t0
+    c = np.log([p[0] for p in pts])
+    t = np.log([p[1] for p in pts])
+    b, loga = np.polyfit(c, t, 1)
+    per_point = sum(float(np.exp(loga + b * np.log(sharding.build_cost(n, 6 * n, 1)))) for n in sizes)
+    value = 1.0 / (per_point * 120)
+    desc = (f"1 tau point of each of {len(pts)} instances (n = {[p[2] for p in pts]}), numpy complex128 chain, "
+            f"{spent:.1f} s; per-point time of all 16 instances from the fit t = a cost^{b:.3f} "
+            f"(cost 4 N^2 n^2) over those points, x 120 tau points per build")
+    return value, spent, desc
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload)
-    per_build = points_per_build(args.workload, w)
-    for _ in range(args.warmup):
-        oracle_tau_points_per_s(w, 1)
-    times = []
-    for _ in range(args.steps):
-        rate, dt, _ = oracle_tau_points_per_s(w, 1)
-        times.append(dt)
-    value = 1.0 / (np.mean(times) * per_build)
+    if args.workload == "c4":
+        for _ in range(args.warmup):
+            batch_oracle_sample(budget_s=0.0)
+        vals, times = [], []
+        for _ in range(args.steps):
+            v, dt, desc = batch_oracle_sample()
+            vals.append(v)
+            times.append(dt)
+        value = float(np.mean(vals))
+        cfg = {"workload": "sox-c4-batch16-N6n-t120", "n": [int(n) for n in __import__("synth").batch_c4_sizes()],
+               "N": "6n", "n_tau": 120, "step": "one tau point of several batch instances"}
+        sample = desc
+    else:
+        w = workload(args.workload)
+        per_build = points_per_build(args.workload, w)
+        for _ in range(args.warmup):
+            oracle_tau_points_per_s(w, 1)
+        times = []
+        for _ in range(args.steps):
+            rate, dt, _ = oracle_tau_points_per_s(w, 1)
+            times.append(dt)
+        value = 1.0 / (np.mean(times) * per_build)
+        cfg = {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
+               "step": "one (spin, tau) point of a build"}
+        sample = f"1 (spin, tau) point of {w.name} per step, {per_build:.4g} such points per build"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "N": w.N, "n_tau": w.n_tau,
-                                            "n_spin": w.n_spin, "step": "one (spin, tau) point of a build"},
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"1 (spin, tau) point of {w.name} per step, {per_build:.4g} such points per build"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -223,16 +282,15 @@ def _tensor_peak(pk, pk_src, achieved):
 def _alu_peak(achieved, what):
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-            "peak_source": "measured FP64 FMA rate (paper_2412_18829_gb300/probes/fp_rate.cu)", "note": what}
+            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s dense)", "note": what}
 
 
-FP64_PEAK_TFLOPS = 1.20
+FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one fused-kernel launch over 16 (spin, tau) batches at n=120,
 # N=600, from an ncu capture of k_sox_bcd_tc; the U2 operand (36.9 MB) is read once per
 # launch, the rest scales with the batches of a launch
 BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726431744 + 20530944, "shared": 36.9e6,
                "source": "ncu dram__bytes_read+write of k_sox_bcd_tc on 16 batches, scaled to the launch's batches"}
-FP32_PEAK_TFLOPS = 78.4
 # DRAM bytes (read + write) of the B and C GEMM launches of one static (tau, v) pair of the
 # 3x3x3 solid (n=26, N=300), from an ncu capture; compared with the pair's algorithmic bytes
 SOLID_BC_TRAFFIC = {"shape": ((3, 3, 3), 26, 300), "bytes": 64460032 + 467337216 + 117393152 + 464741376,
@@ -515,7 +573,6 @@ class BatchCase(Case):
         self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
         self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
         self.units = 1.0 / world
-        self.cpu_points_per_build = points_per_build("c4", workload("c4"))
         self.h = pkg.Handle(prec, device=dev.index or 0)
         self.inst = []
         for i in self.mine:
@@ -580,26 +637,38 @@ class BatchCase(Case):
         small = synth.c4_smallest(3)
         return [d for i, d in zip(self.mine, self.inst) if i in small]
 
+    def _largest(self):
+        return max(self.inst, key=lambda d: d["w"].n) if self.inst else None
+
     def accuracy(self) -> dict:
+        """max|dSigma| against the oracle: two tau points of the three smallest instances and
+        tau index 0 (the largest |Sigma|) of the largest instance on this rank."""
         from oracle import sox as osox
 
         err = rel = 0.0
-        for d in self._smallest():
+        picks = [(d, [0, d["w"].n_tau // 2]) for d in self._smallest()]
+        big = self._largest()
+        if big is not None and all(big is not d for d, _ in picks):
+            picks.append((big, [0]))
+        for d, taus in picks:
             w = d["w"]
-            taus = [0, w.n_tau // 2]
             ref = osox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[0, 0], taus=taus, dtype=np.float64)
             e = float(np.abs(d["S"].cpu().numpy()[0, 0, taus] - ref).max())
             err, rel = max(err, e), max(rel, e / float(np.abs(ref).max()))
         return {"max_abs_err_Ha_vs_oracle": err, "max_rel_err_vs_oracle": rel,
-                "oracle_sample": "tau 0 and n_tau/2 of the three smallest instances"}
+                "oracle_sample": "tau 0 and n_tau/2 of the three smallest instances, tau 0 of the largest "
+                                 f"(n={big['w'].n})" if big is not None else ""}
 
     def fp64_compare(self, value: float) -> dict:
-        """FP64 forward, and the FP64 X/V adjoint, on the three smallest instances."""
+        """The plain FP64 GPU path on one mirror pair of tau points {j, n_tau-1-j} of EVERY
+        instance, scaled by n_tau / 2: static SOX, Phi and the adjoint are local in tau (the
+        pair is itself a mirror-symmetric grid), so the per-point cost is the same at every
+        tau and the scaled time is the full build's.  Forward (phi_sox + phi_sox_grad_G) and
+        the X/V adjoint (phi_sox_backward) are timed separately; the split path is timed on the
+        same pairs and compared value by value."""
         torch = self.torch
-        sub = self._smallest()
-        if not sub:
+        if not self.inst:
             return {}
-        out = {}
         ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
 
         def timed(fn):
@@ -612,35 +681,46 @@ class BatchCase(Case):
             torch.cuda.synchronize()
             return a.elapsed_time(b) / 1e3
 
-        t_mixed = timed(lambda: [self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"])
-                                 for d in sub])
+        sub = []
+        for d in self.inst:
+            w = d["w"]
+            j = w.n_tau // 4
+            order = [j, w.n_tau - 1 - j]
+            e = {"d": d, "p": self.pkg.problem(w.n, w.N, 2, w.n_spin, w.beta), "G": d["G"][:, :, order].contiguous(),
+                 "wt": d["wt"][order].contiguous(), "scale": w.n_tau / 2.0}
+            for k in ("S", "S64", "dG", "dX", "dV", "dX64", "dV64"):
+                src = d["X"] if "X" in k else (d["V"] if "V" in k else e["G"])
+                e[k] = torch.empty_like(src)
+            e["phi"] = torch.empty(w.n_spin, dtype=torch.float64, device=self.dev)
+            sub.append(e)
+
+        def fwd(h, key):
+            for e in sub:
+                self.pkg.phi_sox(h, e["p"], e["G"], e["d"]["X"], e["d"]["V"], e["wt"], e["phi"], e[key], self.stream)
+                self.pkg.phi_sox_grad_G(h, e["p"], e[key], e["wt"], e["d"]["dphi"], e["dG"], self.stream)
+
+        def adj(h, kx, kv):
+            for e in sub:
+                self.pkg.phi_sox_backward(h, e["p"], e["G"], e["d"]["X"], e["d"]["V"], e["wt"], e["d"]["dphi"], None,
+                                          e[kx], e[kv], self.stream)
+
+        scale = sub[0]["scale"] if all(e["scale"] == sub[0]["scale"] for e in sub) else None
+        t_fwd = timed(lambda: fwd(self.h, "S")) * scale
+        t_adj = timed(lambda: adj(self.h, "dX", "dV")) * scale if self.backward else 0.0
         with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
-            S64 = [torch.empty_like(d["S"]) for d in sub]
-            t64 = timed(lambda: [self._one(h64, d, d["G"], d["X"], d["V"], d["wt"], s, d["phi"], d["dG"])
-                                 for d, s in zip(sub, S64)])
-            dX = [torch.empty_like(d["X"]) for d in sub]
-            dV = [torch.empty_like(d["V"]) for d in sub]
-            t_adj = timed(lambda: [self.pkg.phi_sox_backward(h64, d["p"], d["G"], d["X"], d["V"], d["wt"], d["dphi"],
-                                                             None, x, v, self.stream)
-                                   for d, x, v in zip(sub, dX, dV)])
-            out["max_abs_err_Ha_vs_fp64_gpu_smallest3"] = max(float((d["S"] - s).abs().max()) for d, s in zip(sub, S64))
-            if self.prec == "f16x2":
-                tX = [torch.empty_like(d["X"]) for d in sub]
-                tV = [torch.empty_like(d["V"]) for d in sub]
-                t_adj_tc = timed(lambda: [self.pkg.phi_sox_backward(self.h, d["p"], d["G"], d["X"], d["V"], d["wt"],
-                                                                    d["dphi"], None, x, v, self.stream)
-                                          for d, x, v in zip(sub, tX, tV)])
-                rel = lambda a, b: float((a - b).abs().max() / b.abs().max())   # noqa: E731
-                out["adjoint_XV_split_ms_smallest3"] = 1e3 * t_adj_tc
-                out["adjoint_split_vs_fp64_max_rel_dX"] = max(rel(a, b) for a, b in zip(tX, dX))
-                out["adjoint_split_vs_fp64_max_rel_dV"] = max(rel(a, b) for a, b in zip(tV, dV))
-        adj_flops = sum(12.0 * d["w"].N ** 2 * d["w"].n ** 2 * d["w"].n_tau for d in sub)
-        out.update({"smallest3_n": [d["w"].n for d in sub],
-                    "smallest3_ms_f16x2": 1e3 * t_mixed, "smallest3_ms_fp64": 1e3 * t64,
-                    "speedup_vs_fp64_gpu_smallest3": t64 / t_mixed,
-                    "adjoint_XV_fp64_ms_smallest3": 1e3 * t_adj,
-                    "adjoint_XV_fp64_tflops": adj_flops / t_adj / 1e12,
-                    "adjoint_note": "dPhi/dX, dPhi/dV by the FP64 reverse pass (12 N^2 n^2 per tau counted)"})
+            t64_fwd = timed(lambda: fwd(h64, "S64")) * scale
+            t64_adj = timed(lambda: adj(h64, "dX64", "dV64")) * scale if self.backward else 0.0
+        rel = lambda a, b: float((a - b).abs().max() / b.abs().max())   # noqa: E731
+        out = {"fp64_gpu_sample": "one mirror pair {n_tau/4, 3 n_tau/4 - 1} of tau points of every instance, "
+                                  "times scaled by n_tau/2 (static SOX, Phi and the adjoint are local in tau)",
+               "fp64_gpu_builds_per_s": self.units / (t64_fwd + t64_adj),
+               "fp64_gpu_forward_s": t64_fwd, "fp64_gpu_adjoint_s": t64_adj,
+               "split_forward_s_same_sample": t_fwd, "split_adjoint_s_same_sample": t_adj,
+               "speedup_vs_fp64_gpu": (t64_fwd + t64_adj) / (t_fwd + t_adj),
+               "max_abs_err_Ha_vs_fp64_gpu_sampled_pairs": max(float((e["S"] - e["S64"]).abs().max()) for e in sub)}
+        if self.backward:
+            out["adjoint_split_vs_fp64_max_rel_dX"] = max(rel(e["dX"], e["dX64"]) for e in sub)
+            out["adjoint_split_vs_fp64_max_rel_dV"] = max(rel(e["dV"], e["dV64"]) for e in sub)
         return out
 
 
@@ -811,16 +891,98 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and not args.skip_cpu_baseline:
-        w0 = workload(args.workload)
-        rate, dt, pts = oracle_tau_points_per_s(w0, args.cpu_points)
-        line["cpu_baseline"] = {
-            "value": rate / case.cpu_points_per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{len(pts)} (spin, tau) points of {w0.name} ({case.cpu_points_per_build:.4g} such points "
-                      f"per build), numpy complex128 chain, {dt:.1f} s; builds/s = points/s / points per build"}
+        if isinstance(case, BatchCase):
+            v, dt, desc = batch_oracle_sample()
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": desc + " (forward Sigma only: the oracle has no adjoint chain)"}
+        else:
+            w0 = workload(args.workload)
+            rate, dt, pts = oracle_tau_points_per_s(w0, args.cpu_points)
+            line["cpu_baseline"] = {
+                "value": rate / case.cpu_points_per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": f"{len(pts)} (spin, tau) points of {w0.name} ({case.cpu_points_per_build:.4g} such points "
+                          f"per build), numpy complex128 chain, {dt:.1f} s; builds/s = points/s / points per build"}
     print(json.dumps(line), flush=True)
     case.h.close()
     if dist:
         dist.destroy_process_group()
+
+
+def profile_case(args):
+    """One small case on cuda:0 for an ncu capture (a few GB on the device at most)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2412_18829_gb300 as pkg
+    import synth
+
+    kind, prec = args.profile_case, args.precision
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+    if kind in ("molecule", "screened"):
+        T = args.profile_tau or (8 if kind == "molecule" else 4)
+        w = (synth.molecule(1, 120, 600, T, 100.0, n_spin=2) if kind == "molecule"
+             else synth.molecule(2, 250, 2000, T, 100.0, 1))
+        p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        G, X, V = (dev(a) for a in (w.G, w.X, w.V))
+        out = torch.empty_like(G)
+        with pkg.Handle(prec) as h:
+            for _ in range(2):
+                pkg.sox_sigma(h, p, G, X, V, out)
+            pkg.sox_check_device(h)
+    elif kind in ("batch", "adjoint"):
+        T = args.profile_tau or 8
+        n = int(synth.batch_c4_sizes().max())
+        w = synth.molecule(4, n, 6 * n, T, 100.0, 1)
+        _, wts = pkg.sox_tau_grid(w.n_tau, w.beta)
+        p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        G, X, V, tw = (dev(a) for a in (w.G, w.X, w.V, wts))
+        d = torch.ones(1, dtype=torch.float64, device="cuda")
+        phi = torch.empty(1, dtype=torch.float64, device="cuda")
+        S, dG, dX, out = torch.empty_like(G), torch.empty_like(G), torch.empty_like(X), torch.empty_like(V)
+        with pkg.Handle(prec) as h:
+            for _ in range(2):
+                if kind == "batch":
+                    pkg.phi_sox(h, p, G, X, V, tw, phi, S)
+                    pkg.phi_sox_grad_G(h, p, S, tw, d, dG)
+                else:
+                    pkg.phi_sox_backward(h, p, G, X, V, tw, d, None, dX, out)
+            pkg.sox_check_device(h)
+    elif kind in ("solid", "dynmol"):
+        T = args.profile_tau or 4
+        M = (T - 1) // 2
+        if kind == "solid":
+            mesh = tuple(int(x) for x in args.mesh.split(","))
+            n, N = (int(x) for x in args.profile_sizes.split(",")) if args.profile_sizes else (26, 300)
+            w = synth.solid(3, mesh, n, N, T, 300.0)
+            p = pkg.problem(w.n, w.N, T, 1, w.beta, nk=w.nk, dtype=1)
+            cast = lambda a: dev(np.asarray(a, dtype=complex))   # noqa: E731
+        else:
+            n, N = (int(x) for x in args.profile_sizes.split(",")) if args.profile_sizes else (120, 600)
+            w = synth.molecule(1, n, N, T, 100.0, 1)
+            p = pkg.problem(w.n, w.N, T, 1, w.beta)
+            cast = dev
+        _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, M)
+        Wd = synth.pole_screening(w.V, w.beta, M)
+        G, X, V, W = (cast(a) for a in (w.G, w.X, w.V, Wd))
+        F, I = (dev(np.asarray(a, dtype=complex)) for a in (Tf, Ti))
+        out = torch.empty_like(G)
+        with pkg.Handle(prec) as h:
+            pkg.sosex_dynamic_sigma(h, p, G, X, V, W, F, I, 2 * M + 1, out)
+            pkg.sox_check_device(h)
+    else:   # wdyn
+        T = args.profile_tau or 60
+        w = synth.solid(3, (3, 3, 3), 26, 300, T, 300.0)
+        M = (T - 1) // 2
+        _, Tf, _ = synth.bosonic_transforms(w.tau, w.beta, M)
+        G, X, V, F = (dev(np.asarray(a, dtype=complex)) for a in (w.G, w.X, w.V, Tf))
+        out = torch.empty(27, 2 * M + 1, w.N, w.N, dtype=torch.complex128, device="cuda")
+        p = pkg.problem(w.n, w.N, T, 1, w.beta, nk=w.nk, dtype=1)
+        with pkg.Handle("fp64") as h:
+            pkg.sox_w_dynamic(h, p, G, X, V, F, 2 * M + 1, out)
+    torch.cuda.synchronize()
+    print("profile case", kind, "ok", float(out.abs().max()))
 
 
 def main():
@@ -832,7 +994,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16x2", choices=["f16x2", "fp64"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c4", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--cpu-points", type=int, default=16)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
@@ -847,7 +1009,15 @@ def main():
                     help="solid workload: build W_d(i Omega) from G on the GPU inside every step")
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["molecule", "screened", "batch", "adjoint", "solid", "wdyn", "dynmol"],
+                    help="run one small case for an ncu capture instead of the benchmark")
+    ap.add_argument("--profile-tau", type=int, default=None, help="tau points of the profile case")
+    ap.add_argument("--profile-sizes", default=None, help="profile case sizes n,N (solid, dynmol)")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.steps is None:   # about a second of timed GPU work for c1; bounded oracle runs for the reference
         ours = {"c0": 100, "c1": 40, "c2": 10, "c3": 5, "c4": 3}
         ref = {"c0": 10, "c1": 10, "c2": 3, "c3": 1, "c4": 3}

@@ -337,13 +337,19 @@ SOX_API int sox_plan_destroy(sox_plan plan);
  *   rejected with SOX_ERR_SHAPE.  n = 80 with N = 480 fits, n = 90 with N = 540
  *   does not.
  * - The first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current); make that first call before any stream capture.  The
+ *   address is kept per device with the id of the context it belongs to; after a
+ *   cudaDeviceReset the next call on that device looks it up again (set-up again),
+ *   so that call too should come before any capture.
  * - Every call shares the one array, and it keeps the last call's contents
  *   (nothing in it needs to start at zero: every element is written before it
  *   is read).  Calls that overlap on the GPU race on the array: run them on
  *   one stream or serialise them.
- * - G, X, V, Sigma must be device pointers on the current device (host
- *   pointers return SOX_ERR_INVALID_ARG: staging them would need memory).
+ * - G, X, V, Sigma must be device (or managed) pointers of the current device:
+ *   host pointers and device memory of another GPU return SOX_ERR_INVALID_ARG
+ *   (staging them would need memory).
+ * - A launch error left pending by the caller's earlier work on this thread is
+ *   cleared on entry and not reported; SOX_ERR_CUDA reports this call's launches.
  * - Returns SOX_OK, SOX_ERR_INVALID_ARG, SOX_ERR_SHAPE, SOX_ERR_UNSUPPORTED
  *   (solids / complex data) or SOX_ERR_CUDA; asynchronous on `stream`.
  * ------------------------------------------------------------------------ */

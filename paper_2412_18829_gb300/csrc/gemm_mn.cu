@@ -1,0 +1,418 @@
+// Split-precision GEMM on tcgen05 with FP32 output and operands in either shared-memory
+// major order, plus per-tensor FP16-pair splits.
+//
+// Why MN-major: the reverse pass of Phi (Sec. II C chain run backwards) contracts the
+// same tensors over different indices -- Bbar_v[P][R] over R (rows P) and over P (rows
+// R), A_v[P][q] over q and over P.  A K-major-only GEMM needs a transposed copy of each
+// such tensor; with the MMA reading an MN-major tile (instruction-descriptor transpose
+// bit, 64-element MN blocks of 128-byte swizzled rows) one stored layout serves both.
+// That needs one scale per tensor (a per-row scale would vary along K in one of the
+// two uses), hence the per-tensor splits below: every tensor is scaled by a power of
+// two that puts its largest entry in [2^14, 2^15), so entries down to 2^-17 of the
+// largest keep the full 22 bits of the (hi, lo) pair and smaller ones an absolute error
+// of 2^-25 (FP16 subnormal spacing) -- far below the FP32-class bound of the sums.
+#include <algorithm>
+#include <atomic>
+
+#include "gemm_mn.h"
+#include "smem_attr.h"
+#include "tc_common.cuh"
+
+namespace sox {
+
+using tc::smem_u32;
+
+namespace {
+
+constexpr int kT = 128;                       // tile rows / columns
+constexpr int kC = 64;                        // K elements per chunk
+constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of one operand for one chunk
+constexpr int kStageBytes = 4 * kPart;        // A hi, A lo, B hi, B lo
+constexpr int kStages = 2;
+constexpr int kOutBytes = kT * kT * 4;        // FP32 staging of one output tile
+constexpr int kThreads = 320;                 // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpi = 256;
+
+struct Bars {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ long long wind_down(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
+
+// MN-major shared-memory descriptor, 128-byte swizzle: rows of 128 bytes hold 64
+// consecutive MN elements for one k, 8 rows (k .. k+7) form a 1024-byte atom (SBO), and
+// the second 64-element MN block of the 128-wide tile starts `lbo` bytes further.
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ uint64_t op_desc(uint32_t base, int mn, int k16) {
+  // K step of 16: 32 bytes along a K-major row, or 16 rows (2 atoms, 2048 bytes) MN-major
+  return mn ? desc_mn_sw128(base + k16 * 2048, kPart / 2) : tc::desc_kmajor_sw128(base + k16 * 32);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool epi_all(bool ok) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)ok)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+struct Item {
+  int b, i0, j0;
+  long long c0, c1;   // chunk range
+};
+
+// work item t -> (batch, split, tile row, tile column); tile columns run fastest so
+// items in flight together share their A chunks through L2
+__device__ __forceinline__ Item item_of(const GemmMnArgs &a, long long t, int tM, int tN, long long total) {
+  Item it;
+  const long long tiles = (long long)tM * tN;
+  const long long per_b = tiles * a.ksplit;
+  it.b = (int)(t / per_b);
+  long long r = t % per_b;
+  const long long ks = r / tiles;
+  r %= tiles;
+  it.i0 = (int)(r / tN) * kT;
+  it.j0 = (int)(r % tN) * kT;
+  it.c0 = ks * a.cps;
+  it.c1 = it.c0 + a.cps < total ? it.c0 + a.cps : total;
+  return it;
+}
+
+__device__ __forceinline__ void load_operand(uint8_t *dst, const CUtensorMap *hi, const CUtensorMap *lo, uint64_t *bar,
+                                             int mn, int row0, int k0, int z) {
+  if (mn) {
+    tc::tma_load_3d(dst, hi, bar, row0, k0, z);
+    tc::tma_load_3d(dst + kPart / 2, hi, bar, row0 + 64, k0, z);
+    tc::tma_load_3d(dst + kPart, lo, bar, row0, k0, z);
+    tc::tma_load_3d(dst + kPart + kPart / 2, lo, bar, row0 + 64, k0, z);
+  } else {
+    tc::tma_load_3d(dst, hi, bar, k0, row0, z);
+    tc::tma_load_3d(dst + kPart, lo, bar, k0, row0, z);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_mn(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+              const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+              const __grid_constant__ CUtensorMap tmC, GemmMnArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *stage_out = smem + kStages * kStageBytes;
+  Bars *bar = reinterpret_cast<Bars *>(stage_out + kOutBytes);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tM = (a.M + kT - 1) / kT, tN = (a.Ncols + kT - 1) / kT;
+  const long long chunks = (long long)a.kc_inner * a.nk_outer;
+  const long long items = (long long)a.batch * tM * tN * a.ksplit;
+  const uint32_t idesc = tc::idesc_f16_f32(kT, kT) | ((uint32_t)a.a.mn_major << 15) | ((uint32_t)a.b.mn_major << 16);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_empty[b], kEpi);
+    }
+    tc::mbar_init(&bar->drain, 1);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo);
+    tc::prefetch_tmap(&tmB_hi); tc::prefetch_tmap(&tmB_lo);
+    tc::prefetch_tmap(&tmC);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      long long it = 0;
+      for (long long t = blockIdx.x; t < items && !*abort; t += gridDim.x) {
+        const Item w = item_of(a, t, tM, tN, chunks);
+        for (long long c = w.c0; c < w.c1 && !*abort; ++c, ++it) {
+          const int s = (int)(it % kStages);
+          const uint32_t ph = (uint32_t)((it / kStages) & 1);
+          if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+          tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+          const long long kz = c / a.kc_inner;
+          const int k0 = (int)(c % a.kc_inner) * kC;
+          uint8_t *st = smem + (size_t)s * kStageBytes;
+          load_operand(st, &tmA_hi, &tmA_lo, &bar->full[s], a.a.mn_major, w.i0, k0,
+                       (int)(w.b * a.a.zb + kz * a.a.zk));
+          load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, &bar->full[s], a.b.mn_major, w.j0, k0,
+                       (int)(w.b * a.b.zb + kz * a.b.zk));
+        }
+      }
+      for (int s = 0; s < kStages; ++s) {   // every copy issued has landed before the CTA exits
+        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kStages) & 1);
+          for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < items && ok && !*abort; t += gridDim.x) {
+        const Item w = item_of(a, t, tM, tN, chunks);
+        for (long long w0 = w.c0; w0 < w.c1 && ok; w0 += a.window, ++acc_it) {
+          const long long w1 = w0 + a.window < w.c1 ? w0 + a.window : w.c1;
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          const uint32_t acc = tmem + buf * kT;
+          for (long long c = w0; c < w1; ++c, ++it) {
+            const int s = (int)(it % kStages);
+            const uint32_t ph = (uint32_t)((it / kStages) & 1);
+            ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+            if (!ok) break;
+            tc::tc_fence_after();
+            const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
+            const uint32_t ahi = st, alo = st + kPart, bhi = st + 2 * kPart, blo = st + 3 * kPart;
+            const bool first = (c == w0);
+            // the small cross terms first, the large hi*hi steps last (truncating accumulation)
+#pragma unroll
+            for (int k = 0; k < kC / 16; ++k) {
+              tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(blo, a.b.mn_major, k), idesc,
+                          (first && k == 0) ? 0u : 1u);
+              tc::mma_f16(acc, op_desc(alo, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
+            }
+#pragma unroll
+            for (int k = 0; k < kC / 16; ++k)
+              tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
+            tc::mma_commit(&bar->empty[s]);
+          }
+          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+        }
+      }
+      tc::mma_commit(&bar->drain);
+      for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: 8 warps, lane quarter q, 64-column half h ----------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int h = (warp - 2) >> 2;
+    const bool storer = (warp == 2 && lane == 0);
+    const float alpha = a.alpha_host * (a.alpha ? *a.alpha : 1.f);
+    long long acc_it = 0;
+    bool live = true;
+    for (long long t = blockIdx.x; t < items && live; t += gridDim.x) {
+      const Item w = item_of(a, t, tM, tN, chunks);
+      float sum[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) sum[j] = 0.f;
+      for (long long w0 = w.c0; w0 < w.c1; w0 += a.window, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        const bool got = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+        if (!epi_all(got && !*abort)) {
+          live = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * kT + h * 64;
+#pragma unroll
+        for (int c = 0; c < 64; c += 32) {
+          float v[32];
+          tc::tmem_ld_32x32b_x32(base + c, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[c + j] += v[j];
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bar->acc_empty[buf]);
+      }
+      if (!live) break;
+      // scaled tile -> four 128-byte-swizzled boxes of 128 rows x 32 columns -> TMA
+      if (storer) bulk_wait_read();
+      epi_sync();
+      float *tile = reinterpret_cast<float *>(stage_out);
+#pragma unroll
+      for (int c = 0; c < 64; c += 32) {
+        const int col = h * 64 + c;
+        float *box = tile + (col / 32) * (kT * 32) + row * 32;
+#pragma unroll
+        for (int t4 = 0; t4 < 8; ++t4)
+          *reinterpret_cast<float4 *>(box + ((t4 ^ (row & 7)) * 4)) =
+              make_float4(sum[c + 4 * t4] * alpha, sum[c + 4 * t4 + 1] * alpha, sum[c + 4 * t4 + 2] * alpha,
+                          sum[c + 4 * t4 + 3] * alpha);
+      }
+      fence_proxy_async_smem();
+      epi_sync();
+      if (storer) {
+        const bool add = a.accumulate || a.ksplit > 1;
+#pragma unroll
+        for (int bx = 0; bx < 4; ++bx) {
+          const int x = w.j0 + 32 * bx;
+          if (x < a.Ncols) {
+            if (add)
+              tma_reduce_add_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
+            else
+              tma_store_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
+          }
+        }
+        bulk_commit();
+      }
+    }
+    if (storer) bulk_wait_all();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 256);
+  }
+}
+
+// ------------------------------ per-tensor splits ------------------------------
+
+template <class T>
+__global__ void k_absmax(const T *src, long long ld, long long rows, int cols, float *out) {
+  float m = 0.f;
+  const long long total = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / cols, c = e % cols;
+    m = fmaxf(m, (float)fabs((double)src[r * ld + c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative floats order like their bit patterns
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(m));
+}
+
+// 2^(14 - floor(log2 m)) for m > 0 (m in [2^e, 2^(e+1)) -> scaled max in [2^14, 2^15)), 1 for
+// m == 0; clamped to normal FP32 powers of two
+__device__ __forceinline__ float big_scale(float m) {
+  if (!(m > 0.f)) return 1.f;
+  int e;
+  frexpf(m, &e);   // m = f 2^e, f in [0.5, 1): floor(log2 m) = e - 1
+  int k = 15 - e;
+  k = k < -120 ? -120 : (k > 120 ? 120 : k);
+  return ldexpf(1.f, k);
+}
+
+template <class T>
+__global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long ld1, int rows1, int cols, int ldo,
+                               float sign, const float *absmax, const float *scale_in, __half *hi, __half *lo,
+                               float *scale_out) {
+  const float s = scale_in ? *scale_in : big_scale(*absmax);
+  const double sd = (double)sign * (double)s;
+  const long long total = (long long)rows0 * rows1 * ldo;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ldo;
+    const int c = (int)(e % ldo);
+    __half a = __float2half(0.f), b = __float2half(0.f);
+    if (c < cols) {
+      const long long r1 = r / rows0, r0 = r % rows0;
+      const double x = (double)src[r1 * ld1 + r0 * ld0 + c] * sd;   // exact: a power of two
+      a = __float2half_rn((float)x);
+      b = __float2half_rn((float)(x - (double)__half2float(a)));
+    }
+    hi[e] = a;
+    lo[e] = b;
+  }
+  if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
+}
+
+int blocks_for(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152 * 32)); }
+
+}  // namespace
+
+int plan_gemm_mn(GemmMnArgs &a, int sms, int max_ksplit) {
+  const long long tiles = (long long)a.batch * ((a.M + kT - 1) / kT) * ((a.Ncols + kT - 1) / kT);
+  const long long chunks = (long long)a.kc_inner * a.nk_outer;
+  long long ks = 1;
+  if (tiles < sms && max_ksplit > 1) ks = std::min<long long>((sms + tiles - 1) / tiles, max_ksplit);
+  const long long windows = (chunks + a.window - 1) / a.window;
+  ks = std::max<long long>(1, std::min(ks, windows));
+  const long long wps = (windows + ks - 1) / ks;       // windows per split item
+  a.cps = wps * a.window;
+  a.ksplit = (int)((chunks + a.cps - 1) / a.cps);      // every item has at least one chunk
+  const long long items = tiles * a.ksplit;
+  return (int)std::max<long long>(1, std::min<long long>(items, sms));
+}
+
+cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int grid, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr{0};
+  const int bytes = kStages * kStageBytes + kOutBytes + (int)sizeof(Bars) + 1024;
+  const cudaError_t e = set_smem_once(k_gemm_mn, bytes, attr);
+  if (e != cudaSuccess) return e;
+  k_gemm_mn<<<grid, kThreads, bytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a);
+  return cudaGetLastError();
+}
+
+void launch_absmax(const void *src, bool f32, long long ld, long long rows, int cols, float *out, cudaStream_t s) {
+  const int blocks = blocks_for(rows * cols);
+  if (f32)
+    k_absmax<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld, rows, cols, out);
+  else
+    k_absmax<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld, rows, cols, out);
+}
+
+void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, int cols,
+                         int ldo, float sign, const float *absmax, const float *scale_in, __half *hi, __half *lo,
+                         float *scale_out, cudaStream_t s) {
+  const int blocks = blocks_for((long long)rows0 * rows1 * ldo);
+  if (f32)
+    k_split_tensor<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, cols, ldo,
+                                                 sign, absmax, scale_in, hi, lo, scale_out);
+  else
+    k_split_tensor<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld0, rows0, ld1, rows1, cols,
+                                                  ldo, sign, absmax, scale_in, hi, lo, scale_out);
+}
+
+}  // namespace sox

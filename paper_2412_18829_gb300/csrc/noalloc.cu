@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace {
@@ -23,34 +25,75 @@ constexpr size_t kScratchBytes = SOX_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Host code may not use g_scratch's name as a device address: it is a host-side
-// stand-in.  The device address is looked up once per device, with that device
-// current, and cached here.
+// stand-in.  The device address is looked up with the device current and cached
+// per device together with the unique id of the context it was looked up under.
+// A cudaDeviceReset (or any teardown of the primary context) gives the next
+// context a new id, so the address is looked up again instead of reusing a
+// stale one.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context, 0 when none is current yet.
+int current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1 ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2) {
+      cudaGetLastError();
+      return SOX_ERR_CUDA;
+    }
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  *id = 0;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return SOX_ERR_CUDA;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return SOX_ERR_CUDA;
+  return SOX_OK;
+}
 
 int scratch_address(int dev, void **out) {
   if (dev < 0 || dev >= kMaxDevices) return SOX_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc != SOX_OK) return rc;
+  if (!g_addr[dev] || id == 0 || g_ctx_id[dev] != id) {
+    // set-up for this device (first call, or a new context since the last one)
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return SOX_ERR_CUDA;
     }
+    rc = current_context_id(&id);   // the lookup has made the primary context current
+    if (rc != SOX_OK) return rc;
+    if (id == 0) return SOX_ERR_CUDA;
     g_addr[dev] = p;
+    g_ctx_id[dev] = id;
   }
   *out = g_addr[dev];
   return SOX_OK;
 }
 
-bool on_device(const void *p) {
+// true when p is device (or managed) memory that belongs to device `dev`
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+  return a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -63,7 +106,13 @@ extern "C" int sox_sigma_fp64_noalloc(const sox_problem *p, const double *G, con
     return SOX_ERR_SHAPE;
   if (p->nk[0] != 1 || p->nk[1] != 1 || p->nk[2] != 1 || p->dtype != SOX_REAL64) return SOX_ERR_UNSUPPORTED;
   if (!(p->beta > 0.0)) return SOX_ERR_INVALID_ARG;
-  if (!on_device(G) || !on_device(X) || !on_device(V) || !on_device(Sigma)) return SOX_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SOX_ERR_CUDA;
+  }
+  if (!on_device(G, dev) || !on_device(X, dev) || !on_device(V, dev) || !on_device(Sigma, dev))
+    return SOX_ERR_INVALID_ARG;
 
   const int n = p->n, N = p->N, T = p->n_tau, S = p->n_spin;
   const size_t nn = (size_t)n * n, Nn2 = (size_t)N * nn;
@@ -75,8 +124,6 @@ extern "C" int sox_sigma_fp64_noalloc(const sox_problem *p, const double *G, con
   if (fixed + per_tau > kScratchBytes / 8) return SOX_ERR_SHAPE;
   int c = (int)std::min<size_t>((kScratchBytes / 8 - fixed) / per_tau, (size_t)T);
 
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SOX_ERR_CUDA;
   void *base = nullptr;
   int rc = scratch_address(dev, &base);
   if (rc != SOX_OK) return rc;
@@ -88,6 +135,9 @@ extern "C" int sox_sigma_fp64_noalloc(const sox_problem *p, const double *G, con
   double *Tm = GWt + (size_t)c * aligned((size_t)N * n);
   double *Dm = Tm + (size_t)c * aligned((size_t)N * n);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // A launch error left pending by the caller's earlier work on this thread is
+  // cleared here, so the check after the launches below reports only this call's.
+  cudaGetLastError();
 
   // Um[P][q][s] = sum_Q V[P][Q] X[Q][q] X[Q][s]
   sox::launch_pair_products_f64(X, big, N, n, s);

@@ -54,11 +54,16 @@ def tau_shards(n_tau: int, world: int) -> list[list[int]]:
     """Tau indices per rank in compact (mirror-symmetric) order; every index exactly once.
 
     The n_tau // 2 mirror pairs are dealt round-robin (equal cost per pair); an odd grid's
-    middle point goes to the rank with the fewest pairs."""
+    middle point joins the rank with the fewest pairs.  Every shard is itself a valid
+    grid for sox_sigma (at least one pair, so at least 2 points): a split with more
+    ranks than mirror pairs is refused with ValueError."""
     if world < 1:
         raise ValueError("world must be >= 1")
     if n_tau < 2:
         raise ValueError("n_tau must be >= 2")
+    if world > n_tau // 2:
+        raise ValueError(f"{n_tau} tau points have {n_tau // 2} mirror pairs: too few for {world} ranks "
+                         "(every rank needs a pair)")
     pairs = [[] for _ in range(world)]
     for j in range(n_tau // 2):
         pairs[j % world].append(j)

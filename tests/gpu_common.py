@@ -3,12 +3,17 @@ import numpy as np
 import pytest
 
 # Parity bars.  FP64 path: rounding-order differences only.  Split-precision
-# tensor-core path: the absolute bound max|dSigma| <= 1e-8 Ha on the workloads
-# (strict=True); on degenerate shapes whose |Sigma| is far above a molecule's
-# (N < n, tiny beta) the FP32-class relative bound 2e-6 max|Sigma| applies.
+# tensor-core path: the absolute bound max|dSigma| <= 1e-8 Ha of the target, on
+# every shape, with one exception that the check decides by itself (no caller can
+# opt in): degenerate shapes, with fewer THC points than orbitals (N < n) or a
+# self-energy of order 1 Ha (max|Sigma| >= 0.05 Ha: twenty times the largest
+# |Sigma| of the molecular and solid workloads, reached only by toy inputs at
+# beta = 10 or with N < n), are held to the FP32-class relative bound
+# 2e-6 max|Sigma| instead.
 FP64_REL = 1e-12
 MIXED_ABS = 1e-8
 MIXED_REL = 2e-6
+DEGENERATE_SIGMA = 0.05
 
 
 def torch_cuda():
@@ -32,13 +37,16 @@ def to_dev(torch, *arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
 
 
-def check(out, ref, prec, what="", strict=False):
+def check(out, ref, prec, what="", n=None, N=None):
+    """Element-wise parity of `out` with the oracle's `ref`; returns (max|d|, max|ref|).
+    n, N (orbitals, THC points) let the check recognise the N < n degenerate case."""
     err = float(np.abs(out - ref).max())
     scale = float(np.abs(ref).max())
     if prec == "fp64":
         assert err <= FP64_REL * max(scale, 1e-300), f"{what}: fp64 max|d| {err:.3e} vs max|ref| {scale:.3e}"
-    elif strict:
-        assert err <= MIXED_ABS, f"{what}: {prec} max|d| {err:.3e} Ha (max|ref| {scale:.3e})"
-    else:
-        assert err <= max(MIXED_ABS, MIXED_REL * scale), f"{what}: {prec} max|d| {err:.3e} (max|ref| {scale:.3e})"
+        return err, scale
+    degenerate = (n is not None and N is not None and N < n) or scale >= DEGENERATE_SIGMA
+    bar = max(MIXED_ABS, MIXED_REL * scale) if degenerate else MIXED_ABS
+    assert err <= bar, (f"{what}: {prec} max|d| {err:.3e} Ha > {bar:.1e} (max|ref| {scale:.3e}"
+                        f"{', degenerate shape' if degenerate else ''})")
     return err, scale

@@ -96,3 +96,47 @@ def test_batch_largest_instance_full_size(env):
     ident = -0.75 * wts[:, None, None] * np.swapaxes(got[0, 0, ::-1], -1, -2)
     assert np.abs(dG.cpu().numpy()[0, 0] - ident).max() <= 1e-15 * np.abs(ident).max()
     assert np.isfinite(phi.item())
+
+
+def _golden():
+    import importlib.util
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_solid_dynamic_fullsize.py")
+    spec = importlib.util.spec_from_file_location("make_solid_dynamic_fullsize", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name", ["solid_dynamic_k311_n26_N300_t4", "solid_dynamic_k222_n26_N300_t3",
+                                  "solid_dynamic_k333_n12_N130_t3"])
+def test_solid_dynamic_full_tiles_against_stored_oracle(env, name):
+    """Dynamically screened SOSEX of a solid at the full solid's tile counts (N = 300: three
+    128-row P/R tiles; 3x3x3 with N = 130: two), every element against the oracle's stored
+    result (tests/golden/make_solid_dynamic_fullsize.py, which calls only synth/ and
+    oracle/): FP64 to 1e-12 relative, split precision to 1e-8 Ha with the default chunking
+    and with one tau point per chunk (workspace_limit = 1 byte)."""
+    torch, pkg, _ = env
+    gold = _golden()
+    nk, n, N, T = gold.CASES[name]
+    w, Tf, Ti, Wd = gold.inputs(name)
+    stored = np.load(gold.path(name))
+    assert np.allclose(stored["fingerprint"], gold.fingerprint(w, Tf, Ti, Wd), rtol=1e-12, atol=1e-300), \
+        "stored oracle result belongs to other inputs: rerun tests/golden/make_solid_dynamic_fullsize.py"
+    ref = stored["sigma"]
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta, nk=w.nk, dtype=1)
+    cx = lambda a: np.ascontiguousarray(a, dtype=complex)   # noqa: E731
+    G, X, V, W, F, I = to_dev(torch, cx(w.G), cx(w.X), cx(w.V), cx(Wd), cx(Tf), cx(Ti))
+    for prec, limit in (("fp64", 0), ("f16x2", 0), ("f16x2", 1)):
+        with pkg.Handle(prec, workspace_limit=limit) as hh:
+            S = torch.full_like(G, complex("nan"))
+            pkg.sosex_dynamic_sigma(hh, p, G, X, V, W, F, I, Tf.shape[0], S)
+            pkg.sox_check_device(hh)
+            got = S.cpu().numpy()
+        assert np.isfinite(got).all()
+        err = float(np.abs(got - ref).max())
+        scale = float(np.abs(ref).max())
+        bar = 1e-12 * scale if prec == "fp64" else MIXED_ABS
+        print(f"{name} {prec} limit={limit}: max|dSigma| {err:.3e} Ha (max|Sigma| {scale:.3e})")
+        assert err <= bar, f"{name} {prec} limit={limit}: max|dSigma| {err:.3e} > {bar:.1e}"

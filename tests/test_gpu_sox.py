@@ -43,14 +43,14 @@ def _sigma(env, prec, w, U1=None, U2=None, slot=None):
 def test_sox_small_and_ragged(env, prec, n, N, n_tau, n_spin):
     w = synth.molecule(11, n, N, n_tau, 100.0, n_spin=n_spin, name="ragged")
     ref = sox.sox_sigma(w.X, w.V, w.G).real
-    check(_sigma(env, prec, w), ref, prec, f"n={n} N={N}")
+    check(_sigma(env, prec, w), ref, prec, f"n={n} N={N}", n=n, N=N)
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_sox_c0_all_tau(env, prec):
     w = synth.config(0)
     ref = sox.sox_sigma(w.X, w.V, w.G).real
-    err, scale = check(_sigma(env, prec, w), ref, prec, "c0", strict=True)
+    err, scale = check(_sigma(env, prec, w), ref, prec, "c0")
     print(f"c0 {prec}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
 
 
@@ -63,7 +63,7 @@ def test_sox_c1_full_size_sampled_tau(env, prec):
     taus = [0, 17, 40, 79]
     for s in range(w.n_spin):
         ref = sox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
-        err, scale = check(out[s, 0, taus], ref, prec, f"c1 spin {s}", strict=True)
+        err, scale = check(out[s, 0, taus], ref, prec, f"c1 spin {s}")
         print(f"c1 {prec} spin {s}: max|dSigma| {err:.3e} Ha, relative {err / scale:.3e}")
 
 
@@ -87,7 +87,7 @@ def test_sosex_static_c0(env, prec, slot):
     Pi = screening.pi0_quadrature(w.X[0], w.G[0, 0], wt)
     W = np.ascontiguousarray(screening.w_static(w.V[0], 0.5 * (Pi + Pi.T))[None])
     ref = sox.sosex_static_sigma(w.X, w.V, W, w.G, slot=slot).real
-    check(_sigma(env, prec, w, W, slot=slot), ref, prec, f"sosex slot {slot}", strict=True)
+    check(_sigma(env, prec, w, W, slot=slot), ref, prec, f"sosex slot {slot}")
 
 
 def test_thc_project_G(env):

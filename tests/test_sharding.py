@@ -74,10 +74,15 @@ def test_two_gloo_ranks_agree_on_the_partition_and_the_slowest_time():
 @pytest.mark.parametrize("n_tau", [2, 3, 8, 30, 31, 80])
 @pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
 def test_tau_shards_partition_the_grid_in_mirror_pairs(n_tau, world):
+    if world > n_tau // 2:   # some rank would get no mirror pair: refused up front
+        with pytest.raises(ValueError):
+            sharding.tau_shards(n_tau, world)
+        return
     parts = sharding.tau_shards(n_tau, world)
     assert sorted(j for p in parts for j in p) == list(range(n_tau))
     for p in parts:
         assert sharding.compact_is_mirror(p, n_tau)
+        assert len(p) >= 2   # every shard is a grid sox_sigma accepts (n_tau >= 2)
     sizes = [len(p) for p in parts]
     assert max(sizes) - min(sizes) <= 3
 

@@ -49,6 +49,30 @@ def test_noalloc_matches_handle_path_on_two_calls(dims):
         assert np.abs(got - ref).max() <= FP64_REL * scale
 
 
+def test_noalloc_chunks_tau_near_its_scratch_bound_on_a_side_stream():
+    """n = 80, N = 480 leaves room for one tau point per chunk in the 64 MiB array, so
+    the chunk loop runs n_tau times (the G(-tau) stride then starts at T-1-t0 with t0 > 0);
+    the calls are queued on a non-default stream and checked against the handle path."""
+    torch = torch_cuda()
+    pkg = pkg_built()
+    w = synth.molecule(33, 80, 480, 6, 100.0, n_spin=2)
+    p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+    G, X, V = to_dev(torch, w.G, w.X, w.V)
+    ref = _handle_result(torch, pkg, p, G, X, V)
+    scale = np.abs(ref).max()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        outs = [torch.full_like(G, float("nan")) for _ in range(2)]
+        for out in outs:   # two calls in a row on the side stream
+            pkg.sox_sigma_fp64_noalloc(p, G, X, V, out, stream=side)
+    side.synchronize()
+    for out in outs:
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= FP64_REL * scale
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     torch = torch_cuda()
     pkg = pkg_built()
