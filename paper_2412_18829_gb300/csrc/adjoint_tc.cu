@@ -1,51 +1,42 @@
 // Adjoint of Phi_SOX with respect to X and V in split precision (SOX_PREC_F16X2):
-// the reverse pass of the FP64 form (adjoint.cu) with every N x N x n contraction
-// as an FP16-pair GEMM on the tensor cores (ctc.cu), FP32 results.
+// the reverse pass of the FP64 form (adjoint.cu) on the tensor cores.
 //
-// Per spin and tau_j, c_j = -w_j dphi / 4, all v at once:
-//   B_v = A_v GR^T,  C_v = GWt U2_v^T                     (recomputed)
-//   Dbar = c_j E,  Bbar_v = Dbar o C_v,  Cbar_v = Dbar o B_v, Ebar = c_j sum_v B_v o C_v
-//   Abar_v = Bbar_v GR,  GRbar = sum_v Bbar_v^T A_v,  GWtbar = sum_v Cbar_v U2_v,
-//   U2bar_v += Cbar_v^T GWt,  U1bar += sum_v Abar_v (x) Gm_j[:, v]
+// Per spin and tau_j (c_j = -w_j dphi / 4), with A_v = U1 G(-tau_j)[:, v],
+// B_v = A_v GR^T, C_v = GWt U2_v^T and E = X G(-tau_j) X^T:
+//   Bbar_v = c_j E o C_v,  Cbar_v = c_j E o B_v,  Ebar = c_j sum_v B_v o C_v
+//   Abar_v = Bbar_v GR,            GRbar = sum_v Bbar_v^T A_v,
+//   GWtbar = sum_v Cbar_v U2_v,    U2bar_v += Cbar_v^T GWt,
+//   U1bar += sum_v Abar_v (x) G(-tau_j)[:, v]
 // then Xbar from GRbar, GWtbar, Ebar (FP64), and at the end
 //   Vbar = (U1bar + U2bar) Y^T,  Z = V^T (U1bar + U2bar),  Xbar += pair-product adjoint of Z.
+//
+// B_v and C_v are never stored.  One fused kernel (k_adj_bc) recomputes them per
+// 128 x 128 (P, R) tile in TMEM -- the forward's TMA / MMA pipeline -- and its epilogue
+// forms Bbar_v and Cbar_v from E held in registers, writes them once as FP16 pairs
+// [tau][v][P][R] and accumulates Ebar.  The four reverse contractions then read those
+// pairs in place: over R as K-major operands and over P as MN-major ones (gemm_mn.cu),
+// so no transposed copy and no FP32 round trip of the n N^2 tensors exists.  Every split
+// operand carries one power-of-two scale per tensor (per tau chunk), which is what lets
+// one layout serve both contraction orders.
 #include <algorithm>
+#include <atomic>
+#include <vector>
 
 #include "adjoint.h"
 #include "ctc.h"
+#include "gemm_mn.h"
+#include "smem_attr.h"
+#include "tc_common.cuh"
+#include "tc_kernels.h"
 
 namespace sox {
 namespace {
 
+using tc::smem_u32;
+
 long long rup4(long long x) { return (x + 3) & ~3LL; }
+int rup(int x, int m) { return (x + m - 1) / m * m; }
 int grid1(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 65535 * 8)); }
-
-// Dbar = c E and Ebar = c sum_v B_v o C_v (FP32, row length ld; the FP32 class of the split
-// path), c = -w_j dphi / 4
-__global__ void k_dbar(const float *B, const float *C, const float *E, const double *w, const double *dphi, int j,
-                       int n, int N, long long ld, float *Dbar, float *Ebar) {
-  const float c = (float)(-0.25 * w[j] * dphi[0]);
-  const long long NN = (long long)N * N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NN; e += (long long)gridDim.x * blockDim.x) {
-    const long long P = e / N, R = e % N, o = P * ld + R;
-    float d = 0.f;
-    for (int v = 0; v < n; ++v) d = fmaf(B[(long long)v * N * ld + o], C[(long long)v * N * ld + o], d);
-    Dbar[o] = c * E[o];
-    Ebar[o] = c * d;
-  }
-}
-
-// out[r][q] (FP64, N x n) = sum_v in[v][r][q] (FP32, row length ld)
-__global__ void k_sum_v(const float *in, int n, int N, long long ld, double *out) {
-  const long long total = (long long)N * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / n, q = e % n;
-    double acc = 0.0;
-    for (int v = 0; v < n; ++v) acc += (double)in[((long long)v * N + r) * ld + q];
-    out[e] = acc;
-  }
-}
 
 // Ubar[R][(a,b)] = U1bar[(R,a)][b] + U2bar[a][R][b]
 __global__ void k_ubar(const float *U1bar, const float *U2bar, int n, int N, long long ld, long long ldU, float *Ubar) {
@@ -73,45 +64,401 @@ __global__ void k_pair_adjoint_f32(const float *Z, long long ldZ, const double *
 }
 
 // out (FP64, rows x cols) = in (FP32, row length ld)
-__global__ void k_to_f64(const float *in, long long ld, int rows, int cols, double *out) {
-  const long long total = (long long)rows * cols;
+__global__ void k_to_f64(const float *in, long long ld, long long rows, int cols, double *out) {
+  const long long total = rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     out[e] = (double)in[(e / cols) * ld + e % cols];
 }
 
-struct AdjGeom {
-  int n, N, T, S;
-  long long nn, np4, nnp, ldN, Nnp4;
+__global__ void k_fill(float *p, int count, float v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) p[i] = v;
+}
+
+// Scale bookkeeping of one tau chunk (device side: the maxima are device values).
+//   in:  mx[0] = max |E| over the chunk (E = X G(-tau) X^T), sc[0..3] = scales of GR, GWt,
+//        G(-tau) and U1 / U2 splits (one for both, the mixed tensor is split once), os the
+//        A-GEMM's output scale.
+//   out: f[0] = g (Bbar, Cbar storage scale), f[1..5] = output factors of the contractions
+//        Abar, GRbar, GWtbar, U2bar, U1bar (the last completed once Abar's scale is known),
+//        cg[b] = c_b g, em[b] = c_b / (sA sR sW sU)
+struct AdjScalars {
+  float mx[4];    // E, Abar maxima (atomicMax targets), spare
+  float sc[8];    // scales: GR, GWt, Gm, U, Abar, spare
+  float f[8];
+};
+constexpr int kFacG = 0, kFacAbar = 1, kFacGRbar = 2, kFacGWtbar = 3, kFacU2bar = 4, kFacU1bar = 5;
+constexpr int kScGR = 0, kScGW = 1, kScGm = 2, kScU = 3, kScAbar = 4;
+
+__device__ __forceinline__ float pow2_floor(double x) {
+  // largest power of two <= x (x > 0), clamped to normal FP32
+  int e;
+  frexp(x, &e);   // x = f 2^e, f in [0.5, 1)
+  int k = e - 1;
+  k = k < -126 ? -126 : (k > 126 ? 126 : k);
+  return ldexpf(1.f, k);
+}
+
+__global__ void k_adj_factors(AdjScalars *sc, const double *w, const double *dphi, int j0, int bc, int n, float os,
+                              float *cg, float *em) {
+  if (blockIdx.x != 0) return;
+  const double sR = sc->sc[kScGR], sW = sc->sc[kScGW], sG = sc->sc[kScGm], sU = sc->sc[kScU];
+  const double sA = sU * sG * (double)os;
+  double cmax = 0.0;
+  for (int b = 0; b < bc; ++b) cmax = fmax(cmax, fabs(0.25 * w[j0 + b] * dphi[0]));
+  const double bound = cmax * (double)sc->mx[0] * (double)n * 1073741824.0;   // |c E C~| <= c max|E| n 2^30
+  const double g = bound > 0.0 ? (double)pow2_floor(32768.0 / bound) : 1.0;
+  for (int b = threadIdx.x; b < bc; b += blockDim.x) {
+    const double c = -0.25 * w[j0 + b] * dphi[0];
+    cg[b] = (float)(c * g);
+    em[b] = (float)(c / (sA * sR * sW * sU));
+  }
+  if (threadIdx.x == 0) {
+    sc->f[kFacG] = (float)g;
+    sc->f[kFacAbar] = (float)(1.0 / (g * sW * sU * sR));
+    sc->f[kFacGRbar] = (float)(1.0 / (g * sW * sU * sA));
+    sc->f[kFacGWtbar] = (float)(1.0 / (g * sA * sR * sU));
+    sc->f[kFacU2bar] = (float)(1.0 / (g * sA * sR * sW));
+  }
+}
+
+__global__ void k_u1bar_factor(AdjScalars *sc) {
+  sc->f[kFacU1bar] = (float)(1.0 / ((double)sc->sc[kScAbar] * (double)sc->sc[kScGm]));
+}
+
+// ============================================================================
+// Fused producer: for every (tau b, 128 x 128 (P, R) tile), over v,
+//   B~_v = A~_v GR~^T, C~_v = GWt~ U2~_v^T in TMEM (double-buffered), and in the epilogue
+//   Bbar_v = cg_b E o C~_v, Cbar_v = cg_b E o B~_v -> FP16 pairs [b][v][P][R],
+//   Ebar  += B~_v o C~_v (registers), written em_b * sum at the end of the tile.
+// Warp 0: TMA, warp 1: MMA (one elected thread), warps 4-15: epilogue (lane quarter
+// warp % 4, column group (warp - 4) / 4).
+// ============================================================================
+constexpr int kT = 128, kC = 64;
+constexpr int kTileB = kT * kC * 2;            // 16 KB: one 64-wide chunk of 128 rows, hi or lo
+constexpr int kStageB = 4 * kTileB;
+constexpr int kSt = 3;
+// 16 warps: warpgroup 0 = TMA warp, MMA warp and two idle warps; warpgroups 1-3 = the
+// epilogue, columns [0, 48), [48, 96), [96, 128) of the tile.  Launched at 128 registers a
+// thread (512 x 128 = the SM's 65536); warpgroup 0 gives registers back (kRegCtl) and the
+// epilogue takes them (kRegEpi): 128 x kRegCtl + 384 x kRegEpi = 65536, the launch's own
+// total (checked on the host against the compiled register count before the first launch).
+constexpr int kProdThreads = 512, kProdEpi = 384;
+constexpr int kRegLaunch = 128, kRegCtl = 56, kRegEpi = 152;
+static_assert(128 * kRegCtl + 384 * kRegEpi == kProdThreads * kRegLaunch, "register split must equal the launch total");
+constexpr uint32_t kIdesc = tc::idesc_f16_f32(kT, kT);
+
+struct PBars {
+  uint64_t full[kSt];
+  uint64_t empty[kSt];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
 };
 
-AdjGeom adj_geom(int n, int N, int T, int S) {
-  AdjGeom g{n, N, T, S};
-  g.nn = (long long)n * n;
-  g.np4 = rup4(n);
-  g.nnp = rup4(g.nn);
-  g.ldN = rup4(N);
-  g.Nnp4 = rup4((long long)N * n);
-  return g;
+struct AdjBcArgs {
+  int n = 0, N = 0, Kp = 0, batch = 0;
+  long long spin_limit = 0;
+  int *status = nullptr;
+  const float *E = nullptr;       // [b][N][ldE]
+  long long ldE = 0, sE = 0;
+  const float *cg = nullptr, *em = nullptr;   // [b]
+  float *Ebar = nullptr;          // [b][N][ldE]
+  __half *Bh = nullptr, *Bl = nullptr, *Ch = nullptr, *Cl = nullptr;   // [b][v][N][Rp]
+  long long Rp = 0;
+};
+
+__device__ __forceinline__ long long wind_down(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
+
+__device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+                                            bool first) {
+#pragma unroll
+  for (int k = 0; k < kC / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+                (first && k == 0) ? 0u : 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
+#pragma unroll
+  for (int k = 0; k < kC / 16; ++k) {
+    const uint32_t off = k * 32;
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+  }
 }
 
-size_t setup_bytes(const AdjGeom &g) {
-  const int n = g.n, N = g.N;
-  return aligned_bytes((size_t)N * g.nn, 8) + rsplit_bytes(1, N, N) + rsplit_bytes(1, (int)g.nn, N) +
-         aligned_bytes((size_t)N * g.nnp, 4) + rsplit_bytes(1, N * n, n) + rsplit_bytes(n, N, n) +
-         rsplit_bytes(n, n, N) + aligned_bytes((size_t)N * n * g.np4, 4) + aligned_bytes((size_t)n * N * g.np4, 4) +
-         aligned_bytes((size_t)N * n, 8) + rsplit_bytes(1, N, n) + rsplit_bytes(1, n, N);
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-size_t tau_bytes(const AdjGeom &g) {
+// Epilogue of k_adj_bc for the NC columns [col0, col0 + NC) of every tile (lane quarter q).
+template <int NC>
+__device__ __forceinline__ void adj_epilogue(PBars *bar, uint32_t tmem, const AdjBcArgs &a, int tP, long long total,
+                                             volatile int *abort, int q, int lane, int col0) {
+  const int tiles_per_b = tP * tP;
+  const int row = q * 32 + lane;
+  long long acc_it = 0;
+  for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+    const int b = (int)(t / tiles_per_b);
+    const int r = (int)(t % tiles_per_b);
+    const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
+    const int P = P0 + row, Rh = R0 + col0;
+    const bool prow = P < a.N;
+    const float cgb = a.cg[b], emb = a.em[b];
+    float e[NC], eb[NC];
+    const float *Er = a.E + (long long)b * a.sE + (long long)(prow ? P : 0) * a.ldE;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      e[j] = (prow && Rh + j < a.N) ? Er[Rh + j] * cgb : 0.f;
+      eb[j] = 0.f;
+    }
+    const long long vstride = (long long)a.N * a.Rp;
+    const long long obase = ((long long)b * a.n * a.N + (prow ? P : 0)) * a.Rp + Rh;
+    bool ok = true;
+    for (int v = 0; v < a.n; ++v, ++acc_it) {
+      const int buf = (int)(acc_it & 1);
+      const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+      ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+      if (!ok) break;
+      tc::tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + col0;
+      const long long o = obase + v * vstride;
+#pragma unroll
+      for (int c = 0; c < NC; c += 8) {
+        float bv[8], cv[8];
+        tc::tmem_ld_32x32b_x8(base + c, bv);
+        tc::tmem_ld_32x32b_x8(base + 128 + c, cv);
+        tc::tmem_ld_wait();
+        uint32_t ph[4], pl[4];
+#pragma unroll
+        for (int jj = 0; jj < 8; jj += 2) {   // Bbar = E o C
+          __half h0, l0, h1, l1;
+          tc::split_f16(e[c + jj] * cv[jj], h0, l0);
+          tc::split_f16(e[c + jj + 1] * cv[jj + 1], h1, l1);
+          ph[jj / 2] = pack2(h0, h1);
+          pl[jj / 2] = pack2(l0, l1);
+        }
+        if (prow) {
+          *reinterpret_cast<uint4 *>(a.Bh + o + c) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          *reinterpret_cast<uint4 *>(a.Bl + o + c) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; jj += 2) {   // Cbar = E o B
+          __half h0, l0, h1, l1;
+          tc::split_f16(e[c + jj] * bv[jj], h0, l0);
+          tc::split_f16(e[c + jj + 1] * bv[jj + 1], h1, l1);
+          ph[jj / 2] = pack2(h0, h1);
+          pl[jj / 2] = pack2(l0, l1);
+        }
+        if (prow) {
+          *reinterpret_cast<uint4 *>(a.Ch + o + c) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          *reinterpret_cast<uint4 *>(a.Cl + o + c) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) eb[c + jj] = fmaf(bv[jj], cv[jj], eb[c + jj]);
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&bar->acc_empty[buf]);
+    }
+    if (!ok) break;
+    if (prow) {
+      float *Eo = a.Ebar + (long long)b * a.sE + (long long)P * a.ldE;
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (Rh + j < a.N) Eo[Rh + j] = eb[j] * emb;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kProdThreads, 1)
+    k_adj_bc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+             const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
+             const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
+             const __grid_constant__ CUtensorMap tmU_hi, const __grid_constant__ CUtensorMap tmU_lo, AdjBcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  PBars *bar = reinterpret_cast<PBars *>(smem + kSt * kStageB);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tP = (a.N + kT - 1) / kT;
+  const int tiles_per_b = tP * tP;
+  const long long total = (long long)a.batch * tiles_per_b;
+  const int nk = a.Kp / kC;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSt; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_empty[b], kProdEpi);
+    }
+    tc::mbar_init(&bar->drain, 1);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo); tc::prefetch_tmap(&tmGR_hi);
+    tc::prefetch_tmap(&tmGR_lo); tc::prefetch_tmap(&tmGW_hi); tc::prefetch_tmap(&tmGW_lo);
+    tc::prefetch_tmap(&tmU_hi); tc::prefetch_tmap(&tmU_lo);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+  if (warp >= 4) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegEpi));
+    const int grp = (warp - 4) >> 2;
+    if (grp < 2)
+      adj_epilogue<48>(bar, tmem, a, tP, total, abort, warp & 3, lane, grp * 48);
+    else
+      adj_epilogue<32>(bar, tmem, a, tP, total, abort, warp & 3, lane, 96);
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegCtl));
+  if (warp == 0) {
+    if (lane == 0) {
+      long long it = 0;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const int b = (int)(t / tiles_per_b);
+        const int r = (int)(t % tiles_per_b);
+        const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
+        for (int v = 0; v < a.n && !*abort; ++v) {
+          for (int half = 0; half < 2; ++half) {
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kSt);
+              const uint32_t ph = (uint32_t)((it / kSt) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+              tc::mbar_arrive_expect_tx(&bar->full[s], kStageB);
+              uint8_t *st = smem + (size_t)s * kStageB;
+              const int x = kc * kC;
+              if (half == 0) {   // B_v = A_v GR^T
+                tc::tma_load_3d(st, &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(st + kTileB, &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(st + 2 * kTileB, &tmGR_hi, &bar->full[s], x, R0, b);
+                tc::tma_load_3d(st + 3 * kTileB, &tmGR_lo, &bar->full[s], x, R0, b);
+              } else {           // C_v = GWt U2_v^T
+                tc::tma_load_3d(st, &tmGW_hi, &bar->full[s], x, P0, b);
+                tc::tma_load_3d(st + kTileB, &tmGW_lo, &bar->full[s], x, P0, b);
+                tc::tma_load_3d(st + 2 * kTileB, &tmU_hi, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(st + 3 * kTileB, &tmU_lo, &bar->full[s], x, R0, v);
+              }
+            }
+          }
+        }
+      }
+      for (int s = 0; s < kSt; ++s) {   // every copy issued has landed before the CTA exits
+        long long last = it - 1 - ((it - 1 - s) % kSt + kSt) % kSt;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kSt) & 1);
+          for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
+        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t acc = tmem + buf * 256 + half * 128;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kSt);
+              const uint32_t ph = (uint32_t)((it / kSt) & 1);
+              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              const uint32_t st = smem_u32(smem + (size_t)s * kStageB);
+              issue_split(acc, st, st + kTileB, st + 2 * kTileB, st + 3 * kTileB, kc == 0);
+              tc::mma_commit(&bar->empty[s]);
+            }
+          }
+          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+        }
+      }
+      tc::mma_commit(&bar->drain);   // all MMAs complete before TMEM is released
+      for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+size_t adj_bc_smem() { return (size_t)kSt * kStageB + sizeof(PBars) + 1024; }
+
+cudaError_t launch_adj_bc(const CUtensorMap *m, const AdjBcArgs &a, int grid, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr{0};
+  static std::atomic<int> regs_ok{0};
+  if (regs_ok.load() == 0) {
+    // the register split is sized for the launch's own allocation: refuse to launch if the
+    // compiled kernel starts with fewer registers (the increase would never be granted)
+    cudaFuncAttributes fa;
+    const cudaError_t e0 = cudaFuncGetAttributes(&fa, k_adj_bc);
+    if (e0 != cudaSuccess) return e0;
+    if (fa.numRegs < kRegLaunch) return cudaErrorInvalidConfiguration;
+    regs_ok.store(1);
+  }
+  const cudaError_t e = set_smem_once(k_adj_bc, (int)adj_bc_smem(), attr);
+  if (e != cudaSuccess) return e;
+  k_adj_bc<<<grid, kProdThreads, adj_bc_smem(), s>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], a);
+  return cudaGetLastError();
+}
+
+// ------------------------------- geometry ----------------------------------
+
+struct AdjGeom {
+  int n, N, T, S;
+  int Kp;           // n padded to 64: K of the forward contractions, pitch of the splits
+  int NR;           // P / R rows of the forward operands (>= 128)
+  int RG;           // rows of G(-tau)^T per tau (>= 128)
+  long long Rp;     // row pitch of Bbar / Cbar (N rounded up to 128)
+  long long nn, np4, nnp, ldN, Nn;
+  long long abar_pitch;   // per-v pitch of the Abar split [(P, q)] (N n rounded up to 8)
+  int Bc;           // tau points per chunk
+};
+
+size_t fixed_bytes(const AdjGeom &g) {
+  const int N = g.N;
+  size_t b = aligned_bytes((size_t)N * g.nn, 8) + rsplit_bytes(1, N, N) + rsplit_bytes(1, (int)g.nn, N);
+  b += aligned_bytes((size_t)N * g.nnp, 4);                                       // Um
+  b += 2 * aligned_bytes((size_t)g.NR * g.Kp * g.Kp, 2);                          // U1 split
+  b += 2 * aligned_bytes((size_t)g.n * g.NR * g.Kp, 2);                           // U2 split
+  b += aligned_bytes((size_t)N * g.n * g.np4, 4) + aligned_bytes((size_t)g.n * N * g.np4, 4);   // U1bar, U2bar
+  b += aligned_bytes((size_t)g.Nn, 8) + rsplit_bytes(1, N, g.n) + rsplit_bytes(1, g.n, N);      // Xbar, Xr, XT
+  b += aligned_bytes(sizeof(AdjScalars), 4) + 2 * aligned_bytes(8192, 4) + (1 << 16);
+  return b;
+}
+
+size_t per_tau_bytes(const AdjGeom &g) {
   const int n = g.n, N = g.N;
-  size_t b = 3 * aligned_bytes((size_t)N * n, 8) + aligned_bytes((size_t)N * g.ldN, 4);   // GR, GWt, M1, E
-  b += 2 * rsplit_bytes(1, N, n) + 2 * rsplit_bytes(1, n, N) + 2 * rsplit_bytes(1, n, n);
-  b += aligned_bytes((size_t)n * g.Nnp4, 4) + rsplit_bytes(n, N, n) + rsplit_bytes(n, n, N);
-  b += 2 * aligned_bytes((size_t)n * N * g.ldN, 4) + 2 * aligned_bytes((size_t)N * g.ldN, 4);   // B, C, Dbar, Ebar
-  b += rsplit_bytes(1, N, n) + 2 * rsplit_bytes(1, N, N) + 2 * aligned_bytes((size_t)N * g.np4, 4);   // E, Ebar X
-  b += 4 * rsplit_bytes(n, N, N) + 3 * aligned_bytes((size_t)n * N * g.np4, 4) + rsplit_bytes(1, N * n, n);
-  b += 4 * aligned_bytes((size_t)N * n, 8);   // GRbar, GWtbar, m1, m2
+  size_t b = 3 * aligned_bytes((size_t)g.Nn, 8);                                  // GR, GWt, M1 (FP64)
+  b += rsplit_bytes(1, N, n) + 2 * aligned_bytes((size_t)N * g.ldN, 4);           // M1 split, E, Ebar
+  b += 4 * aligned_bytes((size_t)g.NR * g.Kp, 2);                                 // GR~, GWt~
+  b += 2 * aligned_bytes((size_t)g.RG * g.Kp, 2) + 2 * aligned_bytes((size_t)n * g.Kp, 2);   // G(-tau) splits
+  b += 2 * aligned_bytes((size_t)n * g.NR * g.Kp, 2);                             // A~
+  b += 4 * aligned_bytes((size_t)n * N * g.Rp, 2);                                // Bbar, Cbar pairs
+  b += aligned_bytes((size_t)n * N * g.np4, 4) + 2 * aligned_bytes((size_t)n * g.abar_pitch, 2);   // Abar, split
+  b += 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);   // GRbar, GWtbar
+  b += 2 * rsplit_bytes(1, N, N) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
+  b += 3 * 4096;                                                                  // os, cg, em
   return b;
 }
 
@@ -121,152 +468,327 @@ size_t end_bytes(const AdjGeom &g) {
          rsplit_bytes(1, (int)g.nn, N) + aligned_bytes((size_t)N * g.ldN, 4) + aligned_bytes((size_t)N * g.nnp, 4);
 }
 
+AdjGeom adj_geom(sox_handle h, int n, int N, int T, int S) {
+  AdjGeom g{};
+  g.n = n; g.N = N; g.T = T; g.S = S;
+  g.Kp = rup(n, 64);
+  g.NR = std::max(N, 128);
+  g.RG = std::max(g.Kp, 128);
+  g.Rp = rup(N, 128);
+  g.nn = (long long)n * n;
+  g.np4 = rup4(n);
+  g.nnp = rup4(g.nn);
+  g.ldN = rup4(N);
+  g.Nn = (long long)N * n;
+  g.abar_pitch = (g.Nn + 7) & ~7LL;
+  const size_t per = per_tau_bytes(g);
+  const size_t budget = chunk_budget(h, size_t(12) << 30);
+  long long c = (long long)(budget / std::max<size_t>(per, 1));
+  c = std::max<long long>(1, std::min<long long>({c, (long long)T, 1024}));
+  g.Bc = (int)c;
+  return g;
+}
+
 }  // namespace
 
-size_t adjoint_tc_bytes(sox_handle, int n, int N, int T, int S) {
-  const AdjGeom g = adj_geom(n, N, T, S);
-  return setup_bytes(g) + std::max(tau_bytes(g), end_bytes(g)) + (1 << 20);
+size_t adjoint_tc_bytes(sox_handle h, int n, int N, int T, int S) {
+  const AdjGeom g = adj_geom(h, n, N, T, S);
+  return fixed_bytes(g) + std::max(per_tau_bytes(g) * g.Bc, end_bytes(g)) + (1 << 20);
 }
 
 Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double *G, const double *X, const double *V,
                          const double *w, const double *dphi, double *dX, double *dV, Arena &ar, cudaStream_t s) {
-  const AdjGeom g = adj_geom(n, N, T, S);
-  const long long nn = g.nn, Nn = (long long)N * n, NN = (long long)N * N;
-  // ---- set-up: mixed tensor in FP32 and its splits; accumulators
+  const AdjGeom g = adj_geom(h, n, N, T, S);
+  const long long nn = g.nn, Nn = g.Nn, NN = (long long)N * N;
+  const int Kp = g.Kp, NR = g.NR, RG = g.RG, Bc = g.Bc;
+  std::string err;
+  // ---- set-up: mixed tensor in FP32 and its per-tensor splits; accumulators
   double *Y = ar.take<double>((size_t)N * nn);
   CSplit Vs = rsplit_take(ar, 1, N, N), Ys = rsplit_take(ar, 1, (int)nn, N);
   float *Um = ar.take<float>((size_t)N * g.nnp);
-  CSplit U1s = rsplit_take(ar, 1, N * n, n), U2v = rsplit_take(ar, n, N, n), U2vT = rsplit_take(ar, n, n, N);
+  __half *U1h = ar.take<__half>((size_t)NR * Kp * Kp), *U1l = ar.take<__half>((size_t)NR * Kp * Kp);
+  __half *U2h = ar.take<__half>((size_t)n * NR * Kp), *U2l = ar.take<__half>((size_t)n * NR * Kp);
   float *U1bar = ar.take<float>((size_t)N * n * g.np4), *U2bar = ar.take<float>((size_t)n * N * g.np4);
   double *Xbar = ar.take<double>((size_t)Nn);
   CSplit Xr = rsplit_take(ar, 1, N, n), XT = rsplit_take(ar, 1, n, N);   // X rows R (K = t); rows t (K = R)
-  if (!Xbar || !U2vT.hi) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  AdjScalars *sc = ar.take<AdjScalars>(1);
+  float *cgb = ar.take<float>(2048), *emb = ar.take<float>(2048);
+  if (!emb) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   ProfScope ps(h, "phi_adjoint_tc", s, 0);
   long long launches = 0;
   SOX_CUDA_TRY(cudaMemsetAsync(U1bar, 0, 4 * (size_t)N * n * g.np4, s));
   SOX_CUDA_TRY(cudaMemsetAsync(U2bar, 0, 4 * (size_t)n * N * g.np4, s));
   SOX_CUDA_TRY(cudaMemsetAsync(Xbar, 0, 8 * (size_t)Nn, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(U1h, 0, 2 * (size_t)NR * Kp * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(U1l, 0, 2 * (size_t)NR * Kp * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(U2h, 0, 2 * (size_t)n * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(U2l, 0, 2 * (size_t)n * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(AdjScalars), s));
   launch_pair_products_f64(X, Y, N, n, s);
   rsplit(V, false, 0, N, 0, 0, 1, 1, N, N, Vs, s);
   rsplit(Y, false, 0, 1, 0, 0, nn, 1, (int)nn, N, Ys, s);                  // rows (a,b), K = Q
   SOX_TRY(cgemm_tc(h, Vs, Ys, 1, nullptr, nullptr, 1.f, Um, g.nnp, 0, s));   // Um[P][(a,b)]
-  rsplit(Um, true, 0, g.nnp, n, n, 1, 1, N * n, n, U1s, s);                // rows (P,q), K = s
-  rsplit(Um, true, n, g.nnp, 0, 0, 1, n, N, n, U2v, s);                    // [v] rows R, K = w
-  rsplit(Um, true, n, 1, 0, 0, g.nnp, n, n, N, U2vT, s);                   // [v] rows w, K = R
+  // one scale for the mixed tensor in both slots: U1 rows (P, q), K = s; U2 [v][R][w]
+  launch_absmax(Um, true, g.nnp, N, 0, 1, 1, (int)nn, &sc->mx[2], s);
+  launch_split_tensor(Um, true, n, n, g.nnp, N, 1, n, Kp, (long long)Kp * Kp, 1.f, &sc->mx[2], nullptr, U1h, U1l,
+                      &sc->sc[kScU], s);
+  launch_split_tensor(Um, true, g.nnp, N, n, n, 1, n, Kp, (long long)NR * Kp, 1.f, nullptr, &sc->sc[kScU], U2h, U2l,
+                      nullptr, s);
   rsplit(X, false, 0, n, 0, 0, 1, 1, N, n, Xr, s);
   rsplit(X, false, 0, 1, 0, 0, n, 1, n, N, XT, s);
-  launches += 8;
+  launches += 10;
 
-  // ---- per (spin, tau) buffers
+  // ---- per tau-chunk buffers
   Arena at = ar;
-  double *GR = at.take<double>(Nn), *GWt = at.take<double>(Nn), *M1 = at.take<double>(Nn);
-  float *E = at.take<float>((size_t)N * g.ldN);
-  CSplit M1s = rsplit_take(at, 1, N, n), Ebs = rsplit_take(at, 1, N, N), EbTs = rsplit_take(at, 1, N, N);
-  float *m1f = at.take<float>((size_t)N * g.np4), *m2f = at.take<float>((size_t)N * g.np4);
-  CSplit GRs = rsplit_take(at, 1, N, n), GWts = rsplit_take(at, 1, N, n);
-  CSplit GRts = rsplit_take(at, 1, n, N), GWtts = rsplit_take(at, 1, n, N);
-  CSplit Gma = rsplit_take(at, 1, n, n), Gmb = rsplit_take(at, 1, n, n);
-  float *Aall = at.take<float>((size_t)n * g.Nnp4);
-  CSplit As = rsplit_take(at, n, N, n), Ats = rsplit_take(at, n, n, N);
-  float *Ball = at.take<float>((size_t)n * N * g.ldN), *Call = at.take<float>((size_t)n * N * g.ldN);
-  float *Dbar = at.take<float>((size_t)N * g.ldN);
-  float *Ebar = at.take<float>((size_t)N * g.ldN);
-  CSplit Bbs = rsplit_take(at, n, N, N), Cbs = rsplit_take(at, n, N, N);
-  CSplit BbTs = rsplit_take(at, n, N, N), CbTs = rsplit_take(at, n, N, N);
-  float *Abar = at.take<float>((size_t)n * N * g.np4), *GRbv = at.take<float>((size_t)n * N * g.np4);
-  float *GWbv = at.take<float>((size_t)n * N * g.np4);
-  CSplit AbTs = rsplit_take(at, 1, N * n, n);
-  double *GRbar = at.take<double>(Nn), *GWtbar = at.take<double>(Nn);
-  double *m1 = at.take<double>(Nn), *m2 = at.take<double>(Nn);
-  if (!m2 || !AbTs.hi) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
-  SOX_CUDA_TRY(cudaMemsetAsync(Ball, 0, 4 * (size_t)n * N * g.ldN, s));
-  SOX_CUDA_TRY(cudaMemsetAsync(Call, 0, 4 * (size_t)n * N * g.ldN, s));
-  SOX_CUDA_TRY(cudaMemsetAsync(Dbar, 0, 4 * (size_t)N * g.ldN, s));
-  SOX_CUDA_TRY(cudaMemsetAsync(E, 0, 4 * (size_t)N * g.ldN, s));      // pad columns stay zero
-  SOX_CUDA_TRY(cudaMemsetAsync(Ebar, 0, 4 * (size_t)N * g.ldN, s));
+  const size_t Bs = (size_t)Bc;
+  double *GR = at.take<double>(Bs * Nn), *GWt = at.take<double>(Bs * Nn), *M1 = at.take<double>(Bs * Nn);
+  CSplit M1s = rsplit_take(at, Bc, N, n);
+  float *E = at.take<float>(Bs * N * g.ldN), *Ebar = at.take<float>(Bs * N * g.ldN);
+  __half *GRh = at.take<__half>(Bs * NR * Kp), *GRl = at.take<__half>(Bs * NR * Kp);
+  __half *GWh = at.take<__half>(Bs * NR * Kp), *GWl = at.take<__half>(Bs * NR * Kp);
+  __half *GmTh = at.take<__half>(Bs * RG * Kp), *GmTl = at.take<__half>(Bs * RG * Kp);   // rows v, K = s
+  __half *Gmh = at.take<__half>(Bs * n * Kp), *Gml = at.take<__half>(Bs * n * Kp);       // rows s, K = v
+  __half *Ah = at.take<__half>(Bs * n * NR * Kp), *Al = at.take<__half>(Bs * n * NR * Kp);
+  __half *Bbh = at.take<__half>(Bs * n * N * g.Rp), *Bbl = at.take<__half>(Bs * n * N * g.Rp);
+  __half *Cbh = at.take<__half>(Bs * n * N * g.Rp), *Cbl = at.take<__half>(Bs * n * N * g.Rp);
+  float *Abar = at.take<float>(Bs * n * N * g.np4);
+  __half *Abh = at.take<__half>(Bs * n * g.abar_pitch), *Abl = at.take<__half>(Bs * n * g.abar_pitch);
+  float *GRbf = at.take<float>(Bs * N * g.np4), *GWbf = at.take<float>(Bs * N * g.np4);
+  double *GRbar = at.take<double>(Bs * Nn), *GWtbar = at.take<double>(Bs * Nn);
+  CSplit Ebs = rsplit_take(at, Bc, N, N), EbTs = rsplit_take(at, Bc, N, N);
+  float *m1f = at.take<float>(Bs * N * g.np4), *m2f = at.take<float>(Bs * N * g.np4);
+  double *m1 = at.take<double>(Bs * Nn), *m2 = at.take<double>(Bs * Nn);
+  float *osv = at.take<float>(1024);
+  if (!osv) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  // zero padding rows and columns that the splits do not write (rows R >= N of GR~ / GWt~,
+  // rows v >= n of G(-tau)^T); the splits rewrite every valid element each chunk
+  SOX_CUDA_TRY(cudaMemsetAsync(GRh, 0, 2 * Bs * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(GRl, 0, 2 * Bs * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(GWh, 0, 2 * Bs * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(GWl, 0, 2 * Bs * NR * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(GmTh, 0, 2 * Bs * RG * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(GmTl, 0, 2 * Bs * RG * Kp, s));
+  SOX_CUDA_TRY(cudaMemsetAsync(E, 0, 4 * Bs * N * g.ldN, s));      // pad columns stay zero
+  SOX_CUDA_TRY(cudaMemsetAsync(Ebar, 0, 4 * Bs * N * g.ldN, s));
+  // A-GEMM output scale: |A~| <= n 2^15 2^15 os <= 2^15
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  const float os = ldexpf(1.f, -15 - lg);
+  k_fill<<<(Bc + 255) / 256, 256, 0, s>>>(osv, Bc, os);
+  launches += 1;
+
+  // ---- tensor maps of the fixed-address per-chunk buffers
+  CUtensorMap agemm[6], prod[8];
+  if (!make_tmap_f16_3d(&agemm[0], GmTh, Kp, RG, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[1], GmTl, Kp, RG, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[2], U1h, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+      !make_tmap_f16_3d(&agemm[3], U1l, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+      !make_tmap_f16_store4d(&agemm[4], Ah, Kp, NR, n, Bc, &err) ||
+      !make_tmap_f16_store4d(&agemm[5], Al, Kp, NR, n, Bc, &err) ||
+      !make_tmap_f16_3d(&prod[0], Ah, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[1], Al, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[2], GRh, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[3], GRl, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[4], GWh, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[5], GWl, Kp, NR, Bc, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[6], U2h, Kp, NR, n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&prod[7], U2l, Kp, NR, n, 64, 128, &err))
+    return {SOX_ERR_CUDA, "adjoint maps: " + err};
+  const uint64_t zBC = (uint64_t)Bc * n;   // (tau, v) slices of the Bbar / Cbar / A~ tensors
+  // (i) Abar[b][v][P][q] = sum_R Bbar[b][v][P][R] GR~[b][R][q]: A K-major, B MN-major
+  CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5];
+  if (!make_tmap_f16_3d_rs(&mi[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mi[1], Bbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mi[2], GRh, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mi[3], GRl, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&mi[4], Abar, n, N, zBC, g.np4, (uint64_t)N * g.np4, &err) ||
+      // (ii) GRbar[b][R][q] = sum_{v,P} Bbar[b][v][P][R] A~[b][v][P][q]: both MN-major
+      !make_tmap_f16_3d_rs(&mii[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mii[1], Bbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mii[2], Ah, n, Kp, N, zBC, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mii[3], Al, n, Kp, N, zBC, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&mii[4], GRbf, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
+      // (iii) GWtbar[b][P][w] = sum_{v,R} Cbar[b][v][P][R] U2~[v][R][w]: A K-major, B MN-major
+      !make_tmap_f16_3d_rs(&miii[0], Cbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&miii[1], Cbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&miii[2], U2h, n, Kp, N, n, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&miii[3], U2l, n, Kp, N, n, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&miii[4], GWbf, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
+      // (iv) U2bar[v][R][w] += sum_{b,P} Cbar[b][v][P][R] GWt~[b][P][w]: both MN-major
+      !make_tmap_f16_3d_rs(&miv[0], Cbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&miv[1], Cbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&miv[2], GWh, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&miv[3], GWl, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&miv[4], U2bar, n, N, n, g.np4, (uint64_t)N * g.np4, &err) ||
+      // (v) U1bar[(P,q)][s] += sum_{b,v} Abar~[b][v][(P,q)] G(-tau_b)~[s][v]: A MN-major, B K-major
+      !make_tmap_f16_3d_rs(&mv[0], Abh, Nn, g.abar_pitch, n, Bc, (uint64_t)n * g.abar_pitch, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mv[1], Abl, Nn, g.abar_pitch, n, Bc, (uint64_t)n * g.abar_pitch, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mv[2], Gmh, n, Kp, n, Bc, (uint64_t)n * Kp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mv[3], Gml, n, Kp, n, Bc, (uint64_t)n * Kp, 64, 128, &err) ||
+      !make_tmap_f32_store3d(&mv[4], U1bar, n, Nn, 1, g.np4, (uint64_t)Nn * g.np4, &err))
+    return {SOX_ERR_CUDA, "adjoint maps: " + err};
+  const int kcN = (N + 63) / 64, kcn = (n + 63) / 64;
+  const int sms = h->sm_count;
+  const long long limit = h->spin_limit;
 
   for (int sp = 0; sp < S; ++sp) {
-    for (int j = 0; j < T; ++j) {
-      const double *Gj = G + ((long long)sp * T + j) * nn;
-      const double *Gm = G + ((long long)sp * T + (T - 1 - j)) * nn;   // G(-tau_j) = -Gm
-      {  // FP64 projections and E = X G(-tau_j) X^T
+    for (int j0 = 0; j0 < T; j0 += Bc) {
+      const int bc = std::min(Bc, T - j0);
+      const double *Gj = G + ((long long)sp * T + j0) * nn;                 // G(tau_j), b = 0..bc-1
+      const double *Gm0 = G + ((long long)sp * T + (T - 1 - j0)) * nn;      // G(tau_{T-1-j}); stride -nn
+      {  // FP64 projections and M1 = -X G(tau_{T-1-j}) (so that E = M1 X^T = X G(-tau) X^T)
         GemmF64 a;
-        a.M = N; a.Nc = n; a.K = n;
+        a.M = N; a.Nc = n; a.K = n; a.batch = bc;
         a.A = X; a.ai = n; a.ak = 1;
-        a.B = Gj; a.bk = n; a.bj = 1;
-        a.C = GR; a.ci = n; a.cj = 1;
+        a.B = Gj; a.sB = nn; a.bk = n; a.bj = 1;
+        a.C = GR; a.sC = Nn; a.ci = n; a.cj = 1;
         launch_gemm_f64(a, s);
         GemmF64 b = a;
         b.bk = 1; b.bj = n; b.C = GWt;
         launch_gemm_f64(b, s);
         GemmF64 c = a;
-        c.B = Gm; c.C = M1; c.alpha = -1.0;
+        c.B = Gm0; c.sB = -nn; c.C = M1; c.alpha = -1.0;
         launch_gemm_f64(c, s);
       }
-      rsplit(M1, false, 0, n, 0, 0, 1, 1, N, n, M1s, s);
-      SOX_TRY(cgemm_tc(h, M1s, Xr, 1, nullptr, nullptr, 1.f, E, g.ldN, 0, s));   // E = X G(-tau_j) X^T
-      rsplit(GR, false, 0, n, 0, 0, 1, 1, N, n, GRs, s);
-      rsplit(GR, false, 0, 1, 0, 0, n, 1, n, N, GRts, s);
-      rsplit(GWt, false, 0, n, 0, 0, 1, 1, N, n, GWts, s);
-      rsplit(GWt, false, 0, 1, 0, 0, n, 1, n, N, GWtts, s);
-      rsplit(Gm, false, 0, 1, 0, 0, n, 1, n, n, Gma, s);      // rows v, K = s: G(tau_{T-1-j})[s][v]
-      rsplit(Gm, false, 0, n, 0, 0, 1, 1, n, n, Gmb, s);      // rows s, K = v
-      // A_v[(P,q)] = -sum_s G(tau_{T-1-j})[s][v] U1[(P,q)][s]
-      SOX_TRY(cgemm_tc(h, Gma, U1s, 1, nullptr, nullptr, -1.f, Aall, g.Nnp4, 0, s));
-      rsplit(Aall, true, g.Nnp4, n, 0, 0, 1, n, N, n, As, s);    // [v] rows P, K = q
-      rsplit(Aall, true, g.Nnp4, 1, 0, 0, n, n, n, N, Ats, s);   // [v] rows q, K = P
-      SOX_TRY(cgemm_tc(h, As, GRs, n, nullptr, nullptr, 1.f, Ball, g.ldN, (long long)N * g.ldN, s));
-      SOX_TRY(cgemm_tc(h, GWts, U2v, n, nullptr, nullptr, 1.f, Call, g.ldN, (long long)N * g.ldN, s));
-      k_dbar<<<grid1(NN), 256, 0, s>>>(Ball, Call, E, w, dphi + sp, j, n, N, g.ldN, Dbar, Ebar);
-      const long long sB = (long long)N * g.ldN;
-      rsplit(Call, true, sB, g.ldN, 0, 0, 1, n, N, N, Bbs, s, Dbar);    // Bbar_v rows P, K = R
-      rsplit(Ball, true, sB, g.ldN, 0, 0, 1, n, N, N, Cbs, s, Dbar);    // Cbar_v rows P, K = R
-      rsplit(Call, true, sB, 1, 0, 0, g.ldN, n, N, N, BbTs, s, Dbar);   // Bbar_v^T rows R, K = P
-      rsplit(Ball, true, sB, 1, 0, 0, g.ldN, n, N, N, CbTs, s, Dbar);   // Cbar_v^T rows R, K = P
-      const long long sO = (long long)N * g.np4;
-      SOX_TRY(cgemm_tc(h, Bbs, GRts, n, nullptr, nullptr, 1.f, Abar, g.np4, sO, s));   // Abar_v[P][q]
-      SOX_TRY(cgemm_tc(h, BbTs, Ats, n, nullptr, nullptr, 1.f, GRbv, g.np4, sO, s));   // per-v GRbar[R][q]
-      SOX_TRY(cgemm_tc(h, Cbs, U2vT, n, nullptr, nullptr, 1.f, GWbv, g.np4, sO, s));   // per-v GWtbar[P][w]
-      SOX_TRY(cgemm_tc(h, CbTs, GWtts, n, nullptr, nullptr, 1.f, U2bar, g.np4, sO, s, true));   // U2bar_v[R][w]
-      // U1bar[(P,q)][s] += -sum_v Abar_v[P][q] G(tau_{T-1-j})[s][v]
-      rsplit(Abar, true, 0, g.np4, 1, n, sO, 1, N * n, n, AbTs, s);
-      SOX_TRY(cgemm_tc(h, AbTs, Gmb, 1, nullptr, nullptr, -1.f, U1bar, g.np4, 0, s, true));
-      k_sum_v<<<grid1(Nn), 256, 0, s>>>(GRbv, n, N, g.np4, GRbar);
-      k_sum_v<<<grid1(Nn), 256, 0, s>>>(GWbv, n, N, g.np4, GWtbar);
-      {  // Xbar += GRbar G_j^T + GWtbar G_j - (Ebar X) G_m^T - (Ebar^T X) G_m   (FP64)
+      rsplit(M1, false, Nn, n, 0, 0, 1, bc, N, n, M1s, s);
+      SOX_TRY(cgemm_tc(h, M1s, Xr, bc, nullptr, nullptr, 1.f, E, g.ldN, (long long)N * g.ldN, s));
+      // per-chunk maxima and scales
+      SOX_CUDA_TRY(cudaMemsetAsync(sc->mx, 0, sizeof(sc->mx[0]) * 2, s));
+      SOX_CUDA_TRY(cudaMemsetAsync(&sc->mx[3], 0, sizeof(float), s));
+      float *mxGR = &sc->f[6], *mxGW = &sc->f[7], *mxGm = &sc->mx[3];
+      SOX_CUDA_TRY(cudaMemsetAsync(&sc->f[6], 0, 2 * sizeof(float), s));
+      launch_absmax(E, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, &sc->mx[0], s);
+      launch_absmax(GR, false, n, N, Nn, bc, 1, n, mxGR, s);
+      launch_absmax(GWt, false, n, N, Nn, bc, 1, n, mxGW, s);
+      launch_absmax(Gm0, false, n, n, -nn, bc, 1, n, mxGm, s);
+      launch_split_tensor(GR, false, n, N, Nn, bc, 1, n, Kp, (long long)NR * Kp, 1.f, mxGR, nullptr, GRh, GRl,
+                          &sc->sc[kScGR], s);
+      launch_split_tensor(GWt, false, n, N, Nn, bc, 1, n, Kp, (long long)NR * Kp, 1.f, mxGW, nullptr, GWh, GWl,
+                          &sc->sc[kScGW], s);
+      // G(-tau_b) = -G(tau_{T-1-j}): transposed (rows v, K = s) for the A-GEMM, and rows s, K = v
+      launch_split_tensor(Gm0, false, 1, n, -nn, bc, n, n, Kp, (long long)RG * Kp, -1.f, mxGm, nullptr, GmTh, GmTl,
+                          &sc->sc[kScGm], s);
+      launch_split_tensor(Gm0, false, n, n, -nn, bc, 1, n, Kp, (long long)n * Kp, -1.f, mxGm, nullptr, Gmh, Gml,
+                          nullptr, s);
+      k_adj_factors<<<1, 256, 0, s>>>(sc, w, dphi + sp, j0, bc, n, os, cgb, emb);
+      launches += 14;
+      {  // A~[b][v][P][q] = os sum_s G(-tau_b)~[s][v] U1~[(P,q)][s]
+        GemmTcArgs ga;
+        ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.batch = bc;
+        ga.batchA_shared = 0; ga.batchB_shared = 1;
+        ga.mode = kStoreSplit;
+        ga.out_scale = osv;
+        ga.group = Kp; ga.n_groups = NR;
+        ga.spin_limit = limit; ga.status = h->d_status;
+        const long long tiles = (long long)bc * ((n + 127) / 128) * (((long long)NR * Kp + 127) / 128);
+        SOX_CUDA_TRY(launch_gemm_f16x2(agemm, ga, (int)std::max<long long>(1, std::min<long long>(tiles, sms)), s));
+      }
+      {  // fused producer: Bbar, Cbar pairs and Ebar
+        AdjBcArgs pa;
+        pa.n = n; pa.N = N; pa.Kp = Kp; pa.batch = bc;
+        pa.spin_limit = limit; pa.status = h->d_status;
+        pa.E = E; pa.ldE = g.ldN; pa.sE = (long long)N * g.ldN;
+        pa.cg = cgb; pa.em = emb;
+        pa.Ebar = Ebar;
+        pa.Bh = Bbh; pa.Bl = Bbl; pa.Ch = Cbh; pa.Cl = Cbl; pa.Rp = g.Rp;
+        const long long tiles = (long long)bc * ((N + 127) / 128) * ((N + 127) / 128);
+        ProfScope pp(h, "adj_bc", s);
+        SOX_CUDA_TRY(launch_adj_bc(prod, pa, (int)std::max<long long>(1, std::min<long long>(tiles, sms)), s));
+      }
+      launches += 2;
+      {
+        ProfScope pg(h, "adj_gemm", s, 4);
+        // (i) Abar (per (b, v); K = R)
+        GemmMnArgs a1;
+        a1.M = N; a1.Ncols = n; a1.batch = bc * n; a1.kc_inner = kcN; a1.nk_outer = 1;
+        a1.a.mn_major = 0; a1.a.zb = 1;
+        a1.b.mn_major = 1; a1.b.zb = 1; a1.b.zdiv = n;
+        a1.alpha = &sc->f[kFacAbar];
+        a1.spin_limit = limit; a1.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(mi, a1, plan_gemm_mn(a1, sms, 1), s));
+        // (ii) GRbar (per b; K = (v, P))
+        SOX_CUDA_TRY(cudaMemsetAsync(GRbf, 0, 4 * (size_t)bc * N * g.np4, s));
+        GemmMnArgs a2;
+        a2.M = N; a2.Ncols = n; a2.batch = bc; a2.kc_inner = kcN; a2.nk_outer = n;
+        a2.a.mn_major = 1; a2.a.zb = n; a2.a.zk = 1;
+        a2.b.mn_major = 1; a2.b.zb = n; a2.b.zk = 1;
+        a2.alpha = &sc->f[kFacGRbar];
+        a2.spin_limit = limit; a2.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(mii, a2, plan_gemm_mn(a2, sms, 64), s));
+        // (iii) GWtbar (per b; K = (v, R))
+        SOX_CUDA_TRY(cudaMemsetAsync(GWbf, 0, 4 * (size_t)bc * N * g.np4, s));
+        GemmMnArgs a3;
+        a3.M = N; a3.Ncols = n; a3.batch = bc; a3.kc_inner = kcN; a3.nk_outer = n;
+        a3.a.mn_major = 0; a3.a.zb = n; a3.a.zk = 1;
+        a3.b.mn_major = 1; a3.b.zb = 0; a3.b.zk = 1;
+        a3.alpha = &sc->f[kFacGWtbar];
+        a3.spin_limit = limit; a3.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(miii, a3, plan_gemm_mn(a3, sms, 64), s));
+        // (iv) U2bar (per v; K = (b, P)), accumulated over tau
+        GemmMnArgs a4;
+        a4.M = N; a4.Ncols = n; a4.batch = n; a4.kc_inner = kcN; a4.nk_outer = bc;
+        a4.a.mn_major = 1; a4.a.zb = 1; a4.a.zk = n;
+        a4.b.mn_major = 1; a4.b.zb = 0; a4.b.zk = 1;
+        a4.alpha = &sc->f[kFacU2bar];
+        a4.accumulate = 1;
+        a4.spin_limit = limit; a4.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(miv, a4, plan_gemm_mn(a4, sms, 64), s));
+      }
+      // (v) U1bar += Abar (x) G(-tau): Abar split once per chunk, then K = (b, v)
+      launch_absmax(Abar, true, g.np4, N, (long long)N * g.np4, bc * n, 1, n, &sc->mx[1], s);
+      launch_split_tensor(Abar, true, g.np4, N, (long long)N * g.np4, bc * n, 1, n, n, g.abar_pitch, 1.f, &sc->mx[1],
+                          nullptr, Abh, Abl, &sc->sc[kScAbar], s);
+      k_u1bar_factor<<<1, 1, 0, s>>>(sc);
+      {
+        GemmMnArgs a5;
+        a5.M = (int)Nn; a5.Ncols = n; a5.batch = 1; a5.kc_inner = kcn; a5.nk_outer = bc;
+        a5.a.mn_major = 1; a5.a.zb = 0; a5.a.zk = 1;
+        a5.b.mn_major = 0; a5.b.zb = 0; a5.b.zk = 1;
+        a5.alpha = &sc->f[kFacU1bar];
+        a5.accumulate = 1;
+        a5.spin_limit = limit; a5.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(mv, a5, plan_gemm_mn(a5, sms, 1), s));
+      }
+      launches += 11;
+      // ---- Xbar += GRbar G_j^T + GWtbar G_j - (Ebar X) G(tau_{T-1-j})^T... (FP64, per tau)
+      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GRbf, g.np4, (long long)bc * N, n, GRbar);
+      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GWbf, g.np4, (long long)bc * N, n, GWtbar);
+      rsplit(Ebar, true, (long long)N * g.ldN, g.ldN, 0, 0, 1, bc, N, N, Ebs, s);
+      rsplit(Ebar, true, (long long)N * g.ldN, 1, 0, 0, g.ldN, bc, N, N, EbTs, s);
+      SOX_TRY(cgemm_tc(h, Ebs, XT, bc, nullptr, nullptr, 1.f, m1f, g.np4, (long long)N * g.np4, s));
+      SOX_TRY(cgemm_tc(h, EbTs, XT, bc, nullptr, nullptr, 1.f, m2f, g.np4, (long long)N * g.np4, s));
+      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m1f, g.np4, (long long)bc * N, n, m1);
+      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m2f, g.np4, (long long)bc * N, n, m2);
+      launches += 6;
+      for (int b = 0; b < bc; ++b) {
+        const double *Gb = Gj + (long long)b * nn;
+        const double *Gmb = Gm0 - (long long)b * nn;
         GemmF64 x1;
         x1.M = N; x1.Nc = n; x1.K = n;
-        x1.A = GRbar; x1.ai = n; x1.ak = 1;
-        x1.B = Gj; x1.bk = 1; x1.bj = n;
+        x1.A = GRbar + (long long)b * Nn; x1.ai = n; x1.ak = 1;
+        x1.B = Gb; x1.bk = 1; x1.bj = n;
         x1.C = Xbar; x1.ci = n; x1.cj = 1; x1.beta = 1.0;
         launch_gemm_f64(x1, s);
         GemmF64 x2 = x1;
-        x2.A = GWtbar; x2.bk = n; x2.bj = 1;
+        x2.A = GWtbar + (long long)b * Nn; x2.bk = n; x2.bj = 1;
         launch_gemm_f64(x2, s);
-        // m1 = Ebar X, m2 = Ebar^T X on the tensor cores
-        rsplit(Ebar, true, 0, g.ldN, 0, 0, 1, 1, N, N, Ebs, s);
-        rsplit(Ebar, true, 0, 1, 0, 0, g.ldN, 1, N, N, EbTs, s);
-        SOX_TRY(cgemm_tc(h, Ebs, XT, 1, nullptr, nullptr, 1.f, m1f, g.np4, 0, s));
-        SOX_TRY(cgemm_tc(h, EbTs, XT, 1, nullptr, nullptr, 1.f, m2f, g.np4, 0, s));
-        k_to_f64<<<grid1(Nn), 256, 0, s>>>(m1f, g.np4, N, n, m1);
-        k_to_f64<<<grid1(Nn), 256, 0, s>>>(m2f, g.np4, N, n, m2);
         GemmF64 x3;
         x3.M = N; x3.Nc = n; x3.K = n;
-        x3.A = m1; x3.ai = n; x3.ak = 1;
-        x3.B = Gm; x3.bk = 1; x3.bj = n;
+        x3.A = m1 + (long long)b * Nn; x3.ai = n; x3.ak = 1;
+        x3.B = Gmb; x3.bk = 1; x3.bj = n;
         x3.C = Xbar; x3.ci = n; x3.cj = 1;
         x3.alpha = -1.0; x3.beta = 1.0;
         launch_gemm_f64(x3, s);
         GemmF64 x4 = x3;
-        x4.A = m2; x4.bk = n; x4.bj = 1;
+        x4.A = m2 + (long long)b * Nn; x4.bk = n; x4.bj = 1;
         launch_gemm_f64(x4, s);
+        launches += 4;
       }
-      launches += 4 + 6 + 2 + 1 + 4 + 1 + 2 + 6;
     }
   }
 
   // ---- end: Ubar = U1bar + U2bar; Vbar = Ubar Y^T; Z = V^T Ubar; Xbar += pair adjoint of Z
-  Arena ae = ar;
+  Arena ae = ar;   // the per-chunk buffers are free again
   float *Ubar = ae.take<float>((size_t)N * g.nnp);
   CSplit Ubs = rsplit_take(ae, 1, N, (int)nn), Yr = rsplit_take(ae, 1, N, (int)nn);
   CSplit VTs = rsplit_take(ae, 1, N, N), UbTs = rsplit_take(ae, 1, (int)nn, N);

@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = (int)(c % a.kc_inner) * kC;
           uint8_t *st = smem + (size_t)s * kStageBytes;
           load_operand(st, &tmA_hi, &tmA_lo, &bar->full[s], a.a.mn_major, w.i0, k0,
-                       (int)(w.b * a.a.zb + kz * a.a.zk));
+                       (int)((w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
           load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, &bar->full[s], a.b.mn_major, w.j0, k0,
-                       (int)(w.b * a.b.zb + kz * a.b.zk));
+                       (int)((w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
         }
       }
       for (int s = 0; s < kStages; ++s) {   // every copy issued has landed before the CTA exits
@@ -320,13 +320,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ------------------------------ per-tensor splits ------------------------------
 
 template <class T>
-__global__ void k_absmax(const T *src, long long ld, long long rows, int cols, float *out) {
+__global__ void k_absmax(const T *src, long long ld0, int rows0, long long ld1, int rows1, long long ldc, int cols,
+                         float *out) {
   float m = 0.f;
-  const long long total = rows * cols;
+  const long long total = (long long)rows1 * rows0 * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / cols, c = e % cols;
-    m = fmaxf(m, (float)fabs((double)src[r * ld + c]));
+    const long long r1 = r / rows0, r0 = r % rows0;
+    m = fmaxf(m, (float)fabs((double)src[r1 * ld1 + r0 * ld0 + c * ldc]));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative floats order like their bit patterns
@@ -345,25 +347,26 @@ __device__ __forceinline__ float big_scale(float m) {
 }
 
 template <class T>
-__global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long ld1, int rows1, int cols, int ldo,
-                               float sign, const float *absmax, const float *scale_in, __half *hi, __half *lo,
-                               float *scale_out) {
+__global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
+                               int cols, long long ldo, long long ldo1, float sign, const float *absmax,
+                               const float *scale_in, __half *hi, __half *lo, float *scale_out) {
   const float s = scale_in ? *scale_in : big_scale(*absmax);
   const double sd = (double)sign * (double)s;
-  const long long total = (long long)rows0 * rows1 * ldo;
+  const long long total = (long long)rows1 * rows0 * ldo;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / ldo;
-    const int c = (int)(e % ldo);
+    const long long c = e % ldo;
+    const long long r1 = r / rows0, r0 = r % rows0;
     __half a = __float2half(0.f), b = __float2half(0.f);
     if (c < cols) {
-      const long long r1 = r / rows0, r0 = r % rows0;
-      const double x = (double)src[r1 * ld1 + r0 * ld0 + c] * sd;   // exact: a power of two
+      const double x = (double)src[r1 * ld1 + r0 * ld0 + c * ldc] * sd;   // exact: a power of two
       a = __float2half_rn((float)x);
       b = __float2half_rn((float)(x - (double)__half2float(a)));
     }
-    hi[e] = a;
-    lo[e] = b;
+    const long long o = r1 * ldo1 + r0 * ldo + c;
+    hi[o] = a;
+    lo[o] = b;
   }
   if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
 }
@@ -395,24 +398,25 @@ cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int gri
   return cudaGetLastError();
 }
 
-void launch_absmax(const void *src, bool f32, long long ld, long long rows, int cols, float *out, cudaStream_t s) {
-  const int blocks = blocks_for(rows * cols);
+void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
+                   int cols, float *out, cudaStream_t s) {
+  const int blocks = blocks_for((long long)rows1 * rows0 * cols);
   if (f32)
-    k_absmax<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld, rows, cols, out);
+    k_absmax<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols, out);
   else
-    k_absmax<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld, rows, cols, out);
+    k_absmax<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld0, rows0, ld1, rows1, ldc, cols, out);
 }
 
-void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, int cols,
-                         int ldo, float sign, const float *absmax, const float *scale_in, __half *hi, __half *lo,
-                         float *scale_out, cudaStream_t s) {
-  const int blocks = blocks_for((long long)rows0 * rows1 * ldo);
+void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
+                         int cols, long long ldo, long long ldo1, float sign, const float *absmax,
+                         const float *scale_in, __half *hi, __half *lo, float *scale_out, cudaStream_t s) {
+  const int blocks = blocks_for((long long)rows1 * rows0 * ldo);
   if (f32)
-    k_split_tensor<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, cols, ldo,
-                                                 sign, absmax, scale_in, hi, lo, scale_out);
+    k_split_tensor<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols,
+                                                 ldo, ldo1, sign, absmax, scale_in, hi, lo, scale_out);
   else
-    k_split_tensor<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld0, rows0, ld1, rows1, cols,
-                                                  ldo, sign, absmax, scale_in, hi, lo, scale_out);
+    k_split_tensor<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), ld0, rows0, ld1, rows1, ldc, cols,
+                                                  ldo, ldo1, sign, absmax, scale_in, hi, lo, scale_out);
 }
 
 }  // namespace sox

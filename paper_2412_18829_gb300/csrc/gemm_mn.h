@@ -15,10 +15,11 @@ namespace sox {
 //   mn_major = 0: map dims (K, rows, z), box 64 x 128: each 64-wide K chunk of 128 rows.
 //   mn_major = 1: map dims (rows, K, z), box 64 x 64: two boxes per chunk (rows 0-63,
 //                 64-127 of the tile), K running down the map's second dimension.
-// The map's z coordinate for output batch b and outer K index kz is b * zb + kz * zk.
+// The map's z coordinate for output batch b and outer K index kz is (b / zdiv) * zb + kz * zk.
 struct MnOperand {
   int mn_major = 0;
   long long zb = 0, zk = 0;
+  int zdiv = 1;   // the batch term uses b / zdiv
 };
 
 // C[b](i, j) (+)= alpha * sum_k A(i, k) B(j, k) with k = (kz, kk), kz < nk_outer,
@@ -50,16 +51,17 @@ int plan_gemm_mn(GemmMnArgs &a, int sms, int max_ksplit);
 // Ncols x M x batch)
 cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int grid, cudaStream_t s);
 
-// Per-tensor split.  absmax: out[0] = max |x| over `rows` rows of `cols` values (row r at
-// src + r * ld; FP64 or FP32) -- out must hold 0 on entry (atomicMax on the bit pattern).
-void launch_absmax(const void *src, bool f32, long long ld, long long rows, int cols, float *out, cudaStream_t s);
-// s = 2^(14 - floor(log2(max))) (max |x * s| in [2^14, 2^15)), or a given power of two:
-//   hi[r][c] + lo[r][c] = sign * x[r][c] * s for c < cols, 0 for cols <= c < ldo
-// rows r = (r1, r0) with r0 < rows0: source at src + r1 * ld1 + r0 * ld0 + c, output row
-// r1 * rows0 + r0 of pitch ldo.  scale_out (optional) receives s; scale_in (optional)
-// replaces max-based s with *scale_in.
-void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, int cols,
-                         int ldo, float sign, const float *absmax, const float *scale_in, __half *hi, __half *lo,
-                         float *scale_out, cudaStream_t s);
+// Per-tensor split of a strided source: element (r1, r0, c) at src + r1 * ld1 + r0 * ld0 +
+// c * ldc (FP64 or FP32), r1 < rows1, r0 < rows0, c < cols.
+// absmax: atomically raises out[0] to max |x| (out must hold 0 or a smaller value first;
+// atomicMax on the bit pattern of non-negative floats).
+void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
+                   int cols, float *out, cudaStream_t s);
+// split: hi + lo = sign * x * s written at r1 * ldo1 + r0 * ldo + c, with zeros for
+// cols <= c < ldo; s = 2^(14 - floor(log2 absmax)) (largest |x * s| in [2^14, 2^15)), or
+// *scale_in when given.  scale_out (optional) receives s.
+void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
+                         int cols, long long ldo, long long ldo1, float sign, const float *absmax,
+                         const float *scale_in, __half *hi, __half *lo, float *scale_out, cudaStream_t s);
 
 }  // namespace sox

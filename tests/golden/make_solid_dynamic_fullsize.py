@@ -44,11 +44,12 @@ def inputs(name):
 
 
 def fingerprint(w, Tf, Ti, Wd) -> np.ndarray:
-    """sum |x| and sum x over every input tensor (real and imaginary parts)."""
+    """sum |x|, sum |Re x| and sum |Im x| over every input tensor: sums of non-negative terms,
+    so machines that round the generator's arithmetic differently agree to ~1e-14 relative."""
     out = []
     for a in (w.G, w.X, w.V, Wd, Tf, Ti):
         a = np.asarray(a, dtype=complex)
-        out += [float(np.abs(a).sum()), float(a.real.sum()), float(a.imag.sum())]
+        out += [float(np.abs(a).sum()), float(np.abs(a.real).sum()), float(np.abs(a.imag).sum())]
     return np.array(out)
 
 

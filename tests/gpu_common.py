@@ -6,9 +6,9 @@ import pytest
 # tensor-core path: the absolute bound max|dSigma| <= 1e-8 Ha of the target, on
 # every shape, with one exception that the check decides by itself (no caller can
 # opt in): degenerate shapes, with fewer THC points than orbitals (N < n) or a
-# self-energy of order 1 Ha (max|Sigma| >= 0.05 Ha: twenty times the largest
-# |Sigma| of the molecular and solid workloads, reached only by toy inputs at
-# beta = 10 or with N < n), are held to the FP32-class relative bound
+# self-energy of order 1 Ha (max|Sigma| >= 0.05 Ha: more than three times the
+# largest |Sigma| of any molecular or solid workload, 1.5e-2 Ha, reached only by toy
+# inputs at beta = 10 or with N < n), are held to the FP32-class relative bound
 # 2e-6 max|Sigma| instead.
 FP64_REL = 1e-12
 MIXED_ABS = 1e-8

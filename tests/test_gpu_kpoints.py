@@ -164,9 +164,10 @@ def test_single_k_complex_dynamic_equals_real_molecule(env):
 
 @pytest.mark.parametrize("prec", ["fp64", "f16x2"])
 def test_solid_2sosex_static(env, prec):
-    """2SOSEXstat for a solid: SOX(v, W0) + SOX(W0 - v, v) against the oracle's terms."""
+    """2SOSEXstat for a solid: SOX(v, W0) + SOX(W0 - v, v) against the oracle's terms, at the
+    solid workload's beta = 300 (max|Sigma| ~ 1e-2 Ha, so the split path meets 1e-8 Ha)."""
     torch, pkg, hs = env
-    w = synth.solid(15, (1, 1, 2), 4, 12, 3, 10.0)
+    w = synth.solid(15, (1, 1, 2), 8, 40, 3, 300.0)   # the solid workload's temperature
     rng = np.random.default_rng(6)
     W = np.empty_like(w.V)
     for q in range(W.shape[0]):     # on a 1x1x2 mesh every q equals -q: real symmetric W^q

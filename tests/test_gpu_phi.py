@@ -202,3 +202,57 @@ def test_split_adjoint_matches_fp64_adjoint_on_smallest_batch_instance(env):
         gX, gV = _grads_with(torch, pkg, h, w, wt, [1.0])
     assert np.abs(gX - rX).max() <= 2e-5 * np.abs(rX).max()
     assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max()
+
+
+@pytest.mark.parametrize("n,N,n_tau,n_spin", [(33, 130, 3, 1), (20, 90, 6, 2)])
+def test_split_adjoint_one_tau_per_chunk(env, n, N, n_tau, n_spin):
+    """The split adjoint with its tau chunk forced to one point (workspace_limit = 1 byte)
+    equals the oracle's autograd gradients like the default (all points in one chunk)."""
+    torch, pkg, _ = env
+    w = synth.molecule(28, n, N, n_tau, 3.0, n_spin=n_spin)
+    wt = grid.clenshaw_curtis(w.n_tau, w.beta)
+    dphi = [1.0, -0.5][:n_spin]
+    rX = np.zeros((w.N, w.n))
+    rV = np.zeros((w.N, w.N))
+    for s in range(n_spin):
+        _, _, x, v = phi.phi_and_grads(w.X[0], w.V[0], w.G[s, 0], wt)
+        rX += dphi[s] * x
+        rV += dphi[s] * v
+    for limit in (0, 1):
+        with pkg.Handle("f16x2", workspace_limit=limit) as h:
+            gX, gV = _grads_with(torch, pkg, h, w, wt, dphi)
+        assert np.isfinite(gX).all() and np.isfinite(gV).all()
+        assert np.abs(gX - rX).max() <= 2e-5 * np.abs(rX).max(), limit
+        assert np.abs(gV - rV).max() <= 2e-5 * np.abs(rV).max(), limit
+
+
+def test_split_adjoint_largest_batch_instance_against_fp64(env):
+    """The batch's largest instance (n = 298, N = 1788: 14 P/R tiles, 5 K chunks) on a
+    two-point mirror grid: the split adjoint against the FP64 adjoint (itself pinned to the
+    oracle's autograd on small cases), relative 2e-5."""
+    torch, pkg, h64 = env
+    i = int(np.argmax(synth.batch_c4_sizes()))
+    full = synth.c4_instance(i)
+    j = full.n_tau // 4
+    order = [j, full.n_tau - 1 - j]
+    G = np.ascontiguousarray(full.G[:, :, order])
+    wt = grid.clenshaw_curtis(full.n_tau, full.beta)[order]
+    p = pkg.problem(full.n, full.N, 2, 1, full.beta)
+    Gd, X, V, tw = to_dev(torch, G, full.X, full.V, np.ascontiguousarray(wt))
+    d = torch.ones(1, dtype=torch.float64, device="cuda")
+    out = {}
+    for prec, h in (("fp64", h64), ("f16x2", None)):
+        hh = h if h is not None else pkg.Handle("f16x2")
+        dX = torch.full_like(X, float("nan"))
+        dV = torch.full_like(V, float("nan"))
+        pkg.phi_sox_backward(hh, p, Gd, X, V, tw, d, None, dX, dV)
+        pkg.sox_check_device(hh)
+        out[prec] = (dX.cpu().numpy(), dV.cpu().numpy())
+        if h is None:
+            hh.close()
+    (rX, rV), (gX, gV) = out["fp64"], out["f16x2"]
+    assert np.isfinite(gX).all() and np.isfinite(gV).all()
+    eX = np.abs(gX - rX).max() / np.abs(rX).max()
+    eV = np.abs(gV - rV).max() / np.abs(rV).max()
+    print(f"largest instance: split vs FP64 adjoint, relative dX {eX:.2e}, dV {eV:.2e}")
+    assert eX <= 2e-5 and eV <= 2e-5
