@@ -51,6 +51,8 @@ def workload(name: str):
 
     if name in ("c0", "c1", "c2", "c3"):
         return synth.config(int(name[1]))
+    if name == "c1d":   # the dynamic molecule's shapes are c1's
+        return synth.config(1)
     if name == "c4":   # the oracle baselines of the batch time points of its median instance
         sizes = synth.batch_c4_sizes()
         return synth.c4_instance(int(np.argsort(sizes, kind="stable")[len(sizes) // 2]))
@@ -239,6 +241,40 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _apply_v_shard(case, pkg, n):
+    """A build split over the orbital index v: this rank keeps the terms of its v range
+    (sox_set_v_range), and the step ends with one all-reduce of the orbital-basis Sigma."""
+    case.units = 1.0
+    if getattr(case, "v_shard", None) is None:
+        return
+    from paper_2412_18829_gb300 import sharding
+
+    rank, world, _ = case.v_shard
+    v0, v1 = sharding.v_shards(n, world)[rank]
+    pkg.sox_set_v_range(case.h, v0, v1)
+    case.units = 1.0 / world
+
+
+def _reduce_v_shard_host(case, Sh):
+    """The e2e form of the exchange: the rank's partial Sigma from its host buffer to the
+    device, the all-reduce, the sum back to the host; returns the extra (h2d, d2h) bytes."""
+    if getattr(case, "v_shard", None) is None or case.v_shard[1] == 1 or case.v_shard[2] is None:
+        return 0, 0
+    t = case.torch.from_numpy(Sh).to(case.dev)
+    _reduce_v_shard(case, t)
+    Sh[...] = t.cpu().numpy()
+    return Sh.nbytes, Sh.nbytes
+
+
+def _reduce_v_shard(case, S):
+    if getattr(case, "v_shard", None) is None:
+        return
+    _, world, dist = case.v_shard
+    if dist is not None and world > 1:
+        t = case.torch.view_as_real(S) if S.is_complex() else S
+        dist.all_reduce(t)
 
 
 class Case:
@@ -462,10 +498,11 @@ class SolidCase(Case):
     """Dynamically screened SOSEX of a solid (c3): SOX(v, v) + Sigma_d, split precision on the
     tensor cores (complex FP16 pairs, FP32 accumulation, FP64 ends) or FP64 complex."""
 
-    def __init__(self, torch, pkg, w, prec, dev, stream, rpa_w=False):
+    def __init__(self, torch, pkg, w, prec, dev, stream, rpa_w=False, v_shard=None):
         import synth
 
         self.torch, self.pkg, self.w, self.dev, self.stream = torch, pkg, w, dev, stream
+        self.v_shard = v_shard   # (rank, world, dist): this rank's v range of one build
         self.rpa_w = rpa_w
         self.prec = prec
         self.name = w.name
@@ -483,6 +520,7 @@ class SolidCase(Case):
         self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
         self.S = torch.empty_like(self.G)
         self.h = pkg.Handle(prec, device=dev.index or 0)
+        _apply_v_shard(self, pkg, w.n)
         self.config = {"workload": w.name, "nk": list(w.nk), "n": w.n, "N": w.N, "n_tau": w.n_tau,
                        "n_omega": self.nO, "beta": w.beta, "precision": prec,
                        "W_d": ("RPA W(i Omega) - v from G on the GPU (sox_w_dynamic) inside every step" if rpa_w
@@ -494,6 +532,7 @@ class SolidCase(Case):
             self.pkg.sox_w_dynamic(self.h, self.p, self.G, self.X, self.V, self.Tf, self.nO, self.Wd, self.stream)
         self.pkg.sosex_dynamic_sigma(self.h, self.p, self.G, self.X, self.V, self.Wd, self.Tf, self.Ti,
                                      self.nO, self.S, self.stream)
+        _reduce_v_shard(self, self.S)
 
     def e2e_step(self):
         if not hasattr(self, "hp"):
@@ -502,7 +541,8 @@ class SolidCase(Case):
             self.Sh = self.torch.from_numpy(np.empty_like(self.hp[0])).pin_memory().numpy()
         G, X, V, Wd, Tf, Ti = self.hp
         self.pkg.sosex_dynamic_sigma(self.h, self.p, G, X, V, Wd, Tf, Ti, self.nO, self.Sh, self.stream)
-        return sum(a.nbytes for a in self.hp), self.Sh.nbytes
+        xh, xd = _reduce_v_shard_host(self, self.Sh)
+        return sum(a.nbytes for a in self.hp) + xh, self.Sh.nbytes + xd
 
     def phase_flops(self):
         w = self.w
@@ -553,6 +593,91 @@ class SolidCase(Case):
             return {"fp64_gpu_builds_per_s": 1.0 / t64, "speedup_vs_fp64_gpu": value * t64,
                     "max_abs_err_Ha_vs_fp64_gpu_all_points": float((self.S - S64).abs().max().item()),
                     "max_abs_sigma_Ha": float(S64.abs().max().item())}
+
+
+class DynMoleculeCase(Case):
+    """Dynamically screened SOSEX of the mid-size molecule (n=120, N=600, 80 tau, 2 spins):
+    SOX(v, v) + Sigma_d per step, W_d from the synthetic single-pole form."""
+
+    def __init__(self, torch, pkg, w, prec, dev, stream, v_shard=None):
+        import synth
+
+        self.torch, self.pkg, self.w, self.prec, self.dev, self.stream = torch, pkg, w, prec, dev, stream
+        self.v_shard = v_shard   # (rank, world, dist): this rank's v range of one build
+        self.name = w.name + "-dyn"
+        self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
+        self.hot = "sox_bcd_dyn_tc" if prec == "f16x2" else "sosex_dynamic_f64"
+        self.units = 1.0
+        self.cpu_points_per_build = w.n_tau * w.n_spin
+        M = (w.n_tau - 1) // 2
+        _, Tf, Ti = synth.bosonic_transforms(w.tau, w.beta, M)
+        Wd = synth.pole_screening(w.V, w.beta, M)
+        self.nO = 2 * M + 1
+        self.p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)   # noqa: E731
+        self.G, self.X, self.V, self.Wd = (to(a) for a in (w.G, w.X, w.V, Wd))
+        self.Tf, self.Ti = to(Tf), to(Ti)
+        self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
+        self.S = torch.empty_like(self.G)
+        self.h = pkg.Handle(prec, device=dev.index or 0)
+        _apply_v_shard(self, pkg, w.n)
+        self.config = {"workload": self.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
+                       "n_omega": self.nO, "beta": w.beta, "precision": prec,
+                       "W_d": "synthetic single-pole form (synth.pole_screening), input",
+                       "step": "SOX(v, v) + dynamically screened Sigma_d through the C ABI"}
+
+    def _run(self, h, S):
+        self.pkg.sosex_dynamic_sigma(h, self.p, self.G, self.X, self.V, self.Wd, self.Tf, self.Ti, self.nO, S,
+                                     self.stream)
+
+    def step(self):
+        self._run(self.h, self.S)
+        _reduce_v_shard(self, self.S)
+
+    def e2e_step(self):
+        if not hasattr(self, "hp"):
+            self.hp = [self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in self.host]
+            self.Sh = self.torch.from_numpy(np.empty_like(self.hp[0])).pin_memory().numpy()
+        G, X, V, Wd, Tf, Ti = self.hp
+        self.pkg.sosex_dynamic_sigma(self.h, self.p, G, X, V, Wd, Tf, Ti, self.nO, self.Sh, self.stream)
+        xh, xd = _reduce_v_shard_host(self, self.Sh)
+        return sum(a.nbytes for a in self.hp) + xh, self.Sh.nbytes + xd
+
+    def phase_flops(self):
+        """Algorithmic flops: the static SOX(v, v) and the dynamic part (per v: transform
+        2 T N n (x 2 re/im) x n_omega, W_d product 2 n_omega N^2 n x 2, inverse transform
+        2 T N n x 2 n_omega, then the fused B/C/D 4 N^2 n per (tau, v) and the Hadamard)."""
+        w = self.w
+        n, N, T, S, nO = w.n, w.N, w.n_tau, w.n_spin, self.nO
+        static = (4.0 * N * N * n * n + 2.0 * N * N * n + 2.0 * N * n ** 3) * T * S + 2.0 * N * N * n * n
+        dyn = S * n * (4.0 * nO * T * N * n + 4.0 * nO * N * N * n + 4.0 * T * nO * N * n) \
+            + (4.0 * N * N * n * n + 2.0 * N * N * n) * T * S
+        return static, dyn
+
+    def hot_flops_per_step(self):
+        w = self.w
+        return (4.0 * w.N ** 2 * w.n ** 2 + 2.0 * w.N ** 2 * w.n) * w.n_tau * w.n_spin
+
+    def accuracy(self) -> dict:
+        """Against the FP64 GPU path (the oracle's dynamic chain at this size takes hours)."""
+        return {}
+
+    def fp64_compare(self, value: float) -> dict:
+        if self.prec == "fp64":
+            return {}
+        torch = self.torch
+        with self.pkg.Handle("fp64", device=self.dev.index or 0) as h64:
+            S64 = torch.empty_like(self.S)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            self._run(h64, S64)
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b) / 1e3
+            return {"fp64_gpu_builds_per_s": 1.0 / t64, "speedup_vs_fp64_gpu": value * t64,
+                    "max_abs_err_Ha_vs_fp64_gpu_all_points": float((self.S - S64).abs().max().item()),
+                    "max_abs_sigma_Ha": float(S64.abs().max().item()),
+                    "accuracy_note": "against the FP64 GPU path, itself at 1e-12 of the oracle in the parity tests"}
 
 
 class BatchCase(Case):
@@ -727,6 +852,9 @@ class BatchCase(Case):
 def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
     if args.workload == "c4":
         return BatchCase(torch, pkg, args.precision, dev, stream, rank, world, backward=not args.forward_only)
+    vsh = (rank, world, dist_mod) if (args.shard in ("v", "auto") and world > 1) else None
+    if args.workload == "c1d":
+        return DynMoleculeCase(torch, pkg, workload("c1"), args.precision, dev, stream, v_shard=vsh)
     w = workload(args.workload)
     if args.workload == "c3":
         if args.mesh != "3,3,3":   # the same solid recipe on another mesh
@@ -734,8 +862,10 @@ def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
 
             nk = tuple(int(x) for x in args.mesh.split(","))
             w = synth.solid(3, nk, w.n, w.N, w.n_tau, w.beta, name=f"sosexdyn-k{''.join(map(str, nk))}-n{w.n}-N{w.N}-t{w.n_tau}")
-        return SolidCase(torch, pkg, w, args.precision, dev, stream, rpa_w=args.rpa_w)
+        return SolidCase(torch, pkg, w, args.precision, dev, stream, rpa_w=args.rpa_w, v_shard=vsh)
     shard = (rank, world, dist_mod) if (args.shard == "tau" and args.workload in ("c0", "c1")) else None
+    if args.shard == "v" and args.workload in ("c0", "c1", "c2"):
+        raise SystemExit("--shard v is wired for the dynamic workloads (c3, c1d)")
     return MoleculeCase(torch, pkg, w, args.precision, dev, stream, screened=(args.workload == "c2"),
                         variant=args.variant, tau_shard=shard)
 
@@ -786,6 +916,8 @@ def run_ours(args):
         for ph in (("kpoint_tc", "kpoint_dynamic_tc", "kpoint_D") if case.prec == "f16x2"
                    else ("kpoint_f64", "kpoint_dynamic_f64")) + (("w_dynamic",) if case.rpa_w else ()):
             phases[ph] = pkg.sox_profile_read(case.h, ph)
+    if isinstance(case, DynMoleculeCase):
+        phases["sosex_dynamic_tc"] = pkg.sox_profile_read(case.h, "sosex_dynamic_tc")
     if isinstance(case, BatchCase) and case.backward:
         phases["adjoint"] = pkg.sox_profile_read(case.h, "phi_adjoint_tc" if case.prec == "f16x2" else "phi_adjoint_f64")
     pkg.sox_profile_enable(case.h, False)
@@ -857,6 +989,12 @@ def run_ours(args):
         n_s, ms_s = phases["kpoint_f64"]
         extra["static_phase_tflops"] = f_static * args.steps / (ms_s / 1e3) / 1e12 if ms_s else None
         extra["phase_ms_per_step"] = {"kpoint_f64": ms_s / args.steps, case.hot: hot_ms / args.steps}
+    elif isinstance(case, DynMoleculeCase) and case.prec == "f16x2":
+        roof = _tensor_peak(pk, pk_src, achieved)
+        roof["kernel"] = "k_sox_bcd_tc with X in the G_Rq slot (the dynamic part's fused B/C/D)"
+        f_static, f_dyn = case.phase_flops()
+        extra["algorithmic_tflops_per_s"] = (f_static + f_dyn) * value / 1e12
+        extra["phase_ms_per_step"] = {k: v[1] / args.steps for k, v in phases.items()}
     elif case.dtype.startswith("f16x2"):
         roof = _tensor_peak(pk, pk_src, achieved)
         roof["kernel"] = case.hot
@@ -877,14 +1015,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "strong" if (isinstance(case, BatchCase) or getattr(case, "tau_shard", None)) else "weak",
+        "scaling": "strong" if (isinstance(case, BatchCase) or getattr(case, "tau_shard", None)
+                                or getattr(case, "v_shard", None)) else "weak",
         "vs_baseline": None,
         "dtype": case.dtype, "data": "synthetic",
         "config": {**case.config, "l2": "flushed between steps (256 MiB write outside the events)",
                    "parallelism": (f"batch instances sharded over {world} GPUs" if isinstance(case, BatchCase)
                                    else (f"one build split over {world} GPUs by tau mirror pairs, all-gather of "
                                          f"Sigma in the step" if getattr(case, "tau_shard", None)
-                                         else f"{world} independent builds (one per GPU)")), **extra},
+                                         else (f"one build split over {world} GPUs by the orbital index v, one "
+                                               f"all-reduce of Sigma in the step" if getattr(case, "v_shard", None)
+                                               else f"{world} independent builds (one per GPU)"))), **extra},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -901,7 +1042,10 @@ def run_ours(args):
             line["cpu_baseline"] = {
                 "value": rate / case.cpu_points_per_build, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                 "sample": f"{len(pts)} (spin, tau) points of {w0.name} ({case.cpu_points_per_build:.4g} such points "
-                          f"per build), numpy complex128 chain, {dt:.1f} s; builds/s = points/s / points per build"}
+                          f"per build), numpy complex128 chain, {dt:.1f} s; builds/s = points/s / points per build"
+                          + ("; the static SOX(v, v) chain only: the dynamic part is not tau-local and the "
+                             "oracle's dynamic chain at this size runs for hours, so this bounds the oracle's "
+                             "rate from above" if isinstance(case, DynMoleculeCase) else "")}
     print(json.dumps(line), flush=True)
     case.h.close()
     if dist:
@@ -994,16 +1138,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16x2", choices=["f16x2", "fp64"])
-    ap.add_argument("--workload", default="c4", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c4", choices=["c0", "c1", "c2", "c3", "c4", "c1d"])
     ap.add_argument("--cpu-points", type=int, default=16)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--forward-only", action="store_true", help="batch workload: no dPhi/dX, dPhi/dV")
-    ap.add_argument("--shard", default="replicas", choices=["replicas", "tau"],
-                    help="bare-SOX workloads on N GPUs: N independent builds, or one build split by tau "
-                         "mirror pairs with an all-gather of Sigma")
+    ap.add_argument("--shard", default="auto", choices=["auto", "replicas", "tau", "v"],
+                    help="N GPUs: auto = one build split by the orbital index v with one all-reduce of Sigma "
+                         "for the dynamic workloads (c3, c1d), N independent builds for bare SOX and SOSEX "
+                         "(c0-c2), instances dealt out for the batch (c4); tau = one bare-SOX build split by "
+                         "tau mirror pairs with an all-gather; v = the v split; replicas = independent builds")
     ap.add_argument("--mesh", default="3,3,3", help="solid workload: k-mesh (default 3,3,3)")
     ap.add_argument("--rpa-w", action="store_true",
                     help="solid workload: build W_d(i Omega) from G on the GPU inside every step")
@@ -1019,8 +1165,8 @@ def main():
         profile_case(args)
         return
     if args.steps is None:   # about a second of timed GPU work for c1; bounded oracle runs for the reference
-        ours = {"c0": 100, "c1": 40, "c2": 10, "c3": 5, "c4": 3}
-        ref = {"c0": 10, "c1": 10, "c2": 3, "c3": 1, "c4": 3}
+        ours = {"c0": 100, "c1": 40, "c2": 10, "c3": 5, "c4": 3, "c1d": 5}
+        ref = {"c0": 10, "c1": 10, "c2": 3, "c3": 1, "c4": 3, "c1d": 3}
         args.steps = (ref if args.impl == "reference" else ours)[args.workload]
     if args.impl == "reference":
         run_reference(args)

@@ -135,6 +135,22 @@ SOX_API int sox_profile_read(sox_handle h, const char *kernel, long long *launch
  * bounded wait (its results are then invalid; the status is cleared). */
 SOX_API int sox_check_device(sox_handle h);
 
+/* Partial builds for a split over GPUs (no paper passage: the partition of Sec. II C's
+ * sums over the orbital index v, which the paper moves to the outside loop of the dynamic
+ * algorithm for the same purpose).  After sox_set_v_range(h, v0, v1) every self-energy
+ * call on h keeps only the terms of Eq. (sox) whose index v (the column of G(-tau) in
+ * G_sv(-tau)) lies in [v0, v1): sox_sigma, sox_sigma_general, sosex_static_sigma,
+ * g3w2_static_sigma, sosex2_static_sigma and sosex_dynamic_sigma (static and dynamic parts,
+ * molecules and solids, both precisions) return the partial Sigma, phi_sox the partial Phi
+ * and phi_sox_backward the gradients dX, dV of that partial Phi.  Every chain is linear in
+ * that sum, so the partial results of a partition of [0, n), summed (one all-reduce),
+ * equal the whole build.  v1 <= 0 (or v1 >= n) means up to n; (0, 0) restores the whole
+ * build.  With a partial range phi_sox_backward refuses dG (SOX_ERR_UNSUPPORTED: the
+ * identity dPhi/dG = -w Sigma(beta - tau)^T needs the whole Sigma), and the projections,
+ * sox_pi0, sox_w_static and sox_w_dynamic are not affected.  Batch plans keep the range of
+ * their handle at creation.  Returns SOX_ERR_INVALID_ARG for v0 < 0 or 0 < v1 < v0. */
+SOX_API int sox_set_v_range(sox_handle h, int v0, int v1);
+
 /* Grow the workspace for problem p now (outside any graph capture). */
 SOX_API int sox_reserve(sox_handle h, const sox_problem *p);
 

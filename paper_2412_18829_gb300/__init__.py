@@ -19,6 +19,7 @@ from ._binding import (  # noqa: F401
     sox_w_dynamic,
     sosex_static_sigma,
     sox_check_device,
+    sox_set_v_range,
     sox_pi0,
     sox_profile_enable,
     sox_profile_read,

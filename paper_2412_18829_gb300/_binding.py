@@ -49,6 +49,7 @@ _SIGS = {
     "sox_last_error": ([_P], ctypes.c_char_p),
     "sox_reserve": ([_P, ctypes.POINTER(sox_problem)], _I),
     "sox_check_device": ([_P], _I),
+    "sox_set_v_range": ([_P, _I, _I], _I),
     "sox_profile_enable": ([_P, _I], _I),
     "sox_profile_read": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _I),
     "sox_tau_grid": ([_I, ctypes.c_double, _P, _P], _I),
@@ -194,6 +195,11 @@ def sox_tau_grid(n_tau: int, beta: float):
 
 def sox_check_device(h: Handle):
     h.check(lib().sox_check_device(h.ptr))
+
+
+def sox_set_v_range(h: Handle, v0: int = 0, v1: int = 0):
+    """Restrict the handle's later builds to the terms with v in [v0, v1) (0, 0: all)."""
+    h.check(lib().sox_set_v_range(h.ptr, int(v0), int(v1)))
 
 
 def sox_profile_enable(h: Handle, enable: bool = True):

@@ -182,6 +182,8 @@ Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double
 
   ProfScope ps(h, "phi_adjoint_f64", s, 0);
   long long launches = 0;
+  int v_lo = 0, v_hi = n;   // the handle's v range (sox_set_v_range): Phi's v sum runs over [v_lo, v_hi)
+  v_range(h, n, &v_lo, &v_hi);
   SOX_CUDA_TRY(cudaMemsetAsync(U1bar, 0, 8 * Nn2, s));
   SOX_CUDA_TRY(cudaMemsetAsync(U2bar, 0, 8 * Nn2, s));
   SOX_CUDA_TRY(cudaMemsetAsync(Xbar, 0, 8 * Nn, s));
@@ -217,7 +219,7 @@ Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double
       a.C = A; a.sC = Nn2; a.ci = Nn; a.cj = 1;
       a.alpha = -1.0;
       launch_gemm_f64(a, s);
-      launch_sox_bcd_f64(A, Nn2, GR, Nn, GWt, Nn, Um, D, NN, n, N, cc, s);
+      launch_sox_bcd_f64(A, Nn2, GR, Nn, GWt, Nn, Um, D, NN, n, N, cc, s, v_lo, v_hi);
       // E[j] = X Gm_j X^T = -X G_{T-1-j} X^T : M1 = -X G_{T-1-j}, E = M1 X^T
       GemmF64 e1;
       e1.M = N; e1.Nc = n; e1.K = n; e1.batch = cc;
@@ -242,7 +244,7 @@ Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double
       launches += 2;
       SOX_CUDA_TRY(cudaMemsetAsync(GRbar, 0, 8 * Nn * cc, s));
       SOX_CUDA_TRY(cudaMemsetAsync(GWtbar, 0, 8 * Nn * cc, s));
-      for (int v = 0; v < n; ++v) {
+      for (int v = v_lo; v < v_hi; ++v) {
         const double *Bb = Bbar + (long long)v * cc * NN;   // [j][P][R]
         const double *Cb = Cbar + (long long)v * cc * NN;
         GemmF64 ab;  // Abar[j][v][P][q] = sum_R Bbar_v[j][P][R] GR[j][R][q]
@@ -276,10 +278,10 @@ Status phi_adjoint_xv_f64(sox_handle h, int n, int N, int T, int S, const double
       }
       // U1bar[(P,q)][s] += sum_v Abar[j][v][(P,q)] Gm_j[s][v]   (one launch per j: shared output)
       for (int j = 0; j < cc; ++j) {
-        GemmF64 u1;
-        u1.M = N * n; u1.Nc = n; u1.K = n;
-        u1.A = Abar + (long long)j * Nn2; u1.ai = 1; u1.ak = Nn;
-        u1.B = Gs + (long long)(T - 1 - (t0 + j)) * nn; u1.bk = 1; u1.bj = n;
+        GemmF64 u1;   // K = v over the handle's v range
+        u1.M = N * n; u1.Nc = n; u1.K = v_hi - v_lo;
+        u1.A = Abar + (long long)j * Nn2 + (long long)v_lo * Nn; u1.ai = 1; u1.ak = Nn;
+        u1.B = Gs + (long long)(T - 1 - (t0 + j)) * nn + v_lo; u1.bk = 1; u1.bj = n;
         u1.C = U1bar; u1.ci = n; u1.cj = 1;
         u1.alpha = -1.0; u1.beta = 1.0;
         launch_gemm_f64(u1, s);

@@ -161,6 +161,7 @@ struct PBars {
 
 struct AdjBcArgs {
   int n = 0, N = 0, Kp = 0, batch = 0;
+  int v0 = 0, v1 = 0;             // the v sum runs over [v0, v1); outputs hold v - v0
   long long spin_limit = 0;
   int *status = nullptr;
   const float *E = nullptr;       // [b][N][ldE]
@@ -215,16 +216,17 @@ __device__ __forceinline__ void adj_epilogue(PBars *bar, uint32_t tmem, const Ad
       eb[j] = 0.f;
     }
     const long long vstride = (long long)a.N * a.Rp;
-    const long long obase = ((long long)b * a.n * a.N + (prow ? P : 0)) * a.Rp + Rh;
+    const int nv = a.v1 - a.v0;
+    const long long obase = ((long long)b * nv * a.N + (prow ? P : 0)) * a.Rp + Rh;
     bool ok = true;
-    for (int v = 0; v < a.n; ++v, ++acc_it) {
+    for (int v = a.v0; v < a.v1; ++v, ++acc_it) {
       const int buf = (int)(acc_it & 1);
       const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
       ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
       if (!ok) break;
       tc::tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + col0;
-      const long long o = obase + v * vstride;
+      const long long o = obase + (v - a.v0) * vstride;
 #pragma unroll
       for (int c = 0; c < NC; c += 8) {
         float bv[8], cv[8];
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
         const int b = (int)(t / tiles_per_b);
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
-        for (int v = 0; v < a.n && !*abort; ++v) {
+        for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int half = 0; half < 2; ++half) {
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kSt);
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
-        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+        for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
@@ -594,7 +596,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       !make_tmap_f16_3d(&prod[6], U2h, Kp, NR, n, 64, 128, &err) ||
       !make_tmap_f16_3d(&prod[7], U2l, Kp, NR, n, 64, 128, &err))
     return {SOX_ERR_CUDA, "adjoint maps: " + err};
-  const uint64_t zBC = (uint64_t)Bc * n;   // (tau, v) slices of the Bbar / Cbar / A~ tensors
+  // the handle's v range (sox_set_v_range): Phi's v sum, and with it every reverse
+  // contraction over v, runs over [v_lo, v_hi); Bbar / Cbar / Abar hold the nv local slices
+  int v_lo = 0, v_hi = n;
+  v_range(h, n, &v_lo, &v_hi);
+  const int nv = v_hi - v_lo;
+  const int Kpv = rup(std::max(nv, 1), 64);
+  const uint64_t zBC = (uint64_t)Bc * std::max(nv, 1);   // (tau, local v) slices of Bbar / Cbar
   // (i) Abar[b][v][P][q] = sum_R Bbar[b][v][P][R] GR~[b][R][q]: A K-major, B MN-major
   CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5];
   if (!make_tmap_f16_3d_rs(&mi[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
@@ -605,8 +613,8 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       // (ii) GRbar[b][R][q] = sum_{v,P} Bbar[b][v][P][R] A~[b][v][P][q]: both MN-major
       !make_tmap_f16_3d_rs(&mii[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mii[1], Bbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mii[2], Ah, n, Kp, N, zBC, (uint64_t)NR * Kp, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mii[3], Al, n, Kp, N, zBC, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mii[2], Ah, n, Kp, N, (uint64_t)Bc * n, (uint64_t)NR * Kp, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mii[3], Al, n, Kp, N, (uint64_t)Bc * n, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f32_store3d(&mii[4], GRbf, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
       // (iii) GWtbar[b][P][w] = sum_{v,R} Cbar[b][v][P][R] U2~[v][R][w]: A K-major, B MN-major
       !make_tmap_f16_3d_rs(&miii[0], Cbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
@@ -619,19 +627,22 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       !make_tmap_f16_3d_rs(&miv[1], Cbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&miv[2], GWh, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&miv[3], GWl, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
-      !make_tmap_f32_store3d(&miv[4], U2bar, n, N, n, g.np4, (uint64_t)N * g.np4, &err) ||
+      !make_tmap_f32_store3d(&miv[4], U2bar + (size_t)v_lo * N * g.np4, n, N, std::max(nv, 1), g.np4,
+                             (uint64_t)N * g.np4, &err) ||
       // (v) U1bar[(P,q)][s] += sum_{b,v} Abar~[b][v][(P,q)] G(-tau_b)~[s][v]: A MN-major, B K-major
-      !make_tmap_f16_3d_rs(&mv[0], Abh, Nn, g.abar_pitch, n, Bc, (uint64_t)n * g.abar_pitch, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mv[1], Abl, Nn, g.abar_pitch, n, Bc, (uint64_t)n * g.abar_pitch, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mv[2], Gmh, n, Kp, n, Bc, (uint64_t)n * Kp, 64, 128, &err) ||
-      !make_tmap_f16_3d_rs(&mv[3], Gml, n, Kp, n, Bc, (uint64_t)n * Kp, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mv[0], Abh, Nn, g.abar_pitch, std::max(nv, 1), Bc,
+                           (uint64_t)std::max(nv, 1) * g.abar_pitch, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mv[1], Abl, Nn, g.abar_pitch, std::max(nv, 1), Bc,
+                           (uint64_t)std::max(nv, 1) * g.abar_pitch, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mv[2], Gmh, std::max(nv, 1), Kpv, n, Bc, (uint64_t)n * Kpv, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mv[3], Gml, std::max(nv, 1), Kpv, n, Bc, (uint64_t)n * Kpv, 64, 128, &err) ||
       !make_tmap_f32_store3d(&mv[4], U1bar, n, Nn, 1, g.np4, (uint64_t)Nn * g.np4, &err))
     return {SOX_ERR_CUDA, "adjoint maps: " + err};
-  const int kcN = (N + 63) / 64, kcn = (n + 63) / 64;
+  const int kcN = (N + 63) / 64;
   const int sms = h->sm_count;
   const long long limit = h->spin_limit;
 
-  for (int sp = 0; sp < S; ++sp) {
+  for (int sp = 0; sp < S && nv > 0; ++sp) {
     for (int j0 = 0; j0 < T; j0 += Bc) {
       const int bc = std::min(Bc, T - j0);
       const double *Gj = G + ((long long)sp * T + j0) * nn;                 // G(tau_j), b = 0..bc-1
@@ -668,8 +679,8 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       // G(-tau_b) = -G(tau_{T-1-j}): transposed (rows v, K = s) for the A-GEMM, and rows s, K = v
       launch_split_tensor(Gm0, false, 1, n, -nn, bc, n, n, Kp, (long long)RG * Kp, -1.f, mxGm, nullptr, GmTh, GmTl,
                           &sc->sc[kScGm], s);
-      launch_split_tensor(Gm0, false, n, n, -nn, bc, 1, n, Kp, (long long)n * Kp, -1.f, mxGm, nullptr, Gmh, Gml,
-                          nullptr, s);
+      launch_split_tensor(Gm0 + v_lo, false, n, n, -nn, bc, 1, nv, Kpv, (long long)n * Kpv, -1.f, mxGm, nullptr,
+                          Gmh, Gml, nullptr, s);   // columns v in the range only
       k_adj_factors<<<1, 256, 0, s>>>(sc, w, dphi + sp, j0, bc, n, os, cgb, emb);
       launches += 14;
       {  // A~[b][v][P][q] = os sum_s G(-tau_b)~[s][v] U1~[(P,q)][s]
@@ -686,6 +697,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       {  // fused producer: Bbar, Cbar pairs and Ebar
         AdjBcArgs pa;
         pa.n = n; pa.N = N; pa.Kp = Kp; pa.batch = bc;
+        pa.v0 = v_lo; pa.v1 = v_hi;
         pa.spin_limit = limit; pa.status = h->d_status;
         pa.E = E; pa.ldE = g.ldN; pa.sE = (long long)N * g.ldN;
         pa.cg = cgb; pa.em = emb;
@@ -700,34 +712,34 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         ProfScope pg(h, "adj_gemm", s, 4);
         // (i) Abar (per (b, v); K = R)
         GemmMnArgs a1;
-        a1.M = N; a1.Ncols = n; a1.batch = bc * n; a1.kc_inner = kcN; a1.nk_outer = 1;
+        a1.M = N; a1.Ncols = n; a1.batch = bc * nv; a1.kc_inner = kcN; a1.nk_outer = 1;
         a1.a.mn_major = 0; a1.a.zb = 1;
-        a1.b.mn_major = 1; a1.b.zb = 1; a1.b.zdiv = n;
+        a1.b.mn_major = 1; a1.b.zb = 1; a1.b.zdiv = nv;
         a1.alpha = &sc->f[kFacAbar];
         a1.spin_limit = limit; a1.status = h->d_status;
         SOX_CUDA_TRY(launch_gemm_mn(mi, a1, plan_gemm_mn(a1, sms, 1), s));
         // (ii) GRbar (per b; K = (v, P))
         SOX_CUDA_TRY(cudaMemsetAsync(GRbf, 0, 4 * (size_t)bc * N * g.np4, s));
         GemmMnArgs a2;
-        a2.M = N; a2.Ncols = n; a2.batch = bc; a2.kc_inner = kcN; a2.nk_outer = n;
-        a2.a.mn_major = 1; a2.a.zb = n; a2.a.zk = 1;
-        a2.b.mn_major = 1; a2.b.zb = n; a2.b.zk = 1;
+        a2.M = N; a2.Ncols = n; a2.batch = bc; a2.kc_inner = kcN; a2.nk_outer = nv;
+        a2.a.mn_major = 1; a2.a.zb = nv; a2.a.zk = 1;
+        a2.b.mn_major = 1; a2.b.zb = n; a2.b.zk = 1; a2.b.z0 = v_lo;
         a2.alpha = &sc->f[kFacGRbar];
         a2.spin_limit = limit; a2.status = h->d_status;
         SOX_CUDA_TRY(launch_gemm_mn(mii, a2, plan_gemm_mn(a2, sms, 64), s));
         // (iii) GWtbar (per b; K = (v, R))
         SOX_CUDA_TRY(cudaMemsetAsync(GWbf, 0, 4 * (size_t)bc * N * g.np4, s));
         GemmMnArgs a3;
-        a3.M = N; a3.Ncols = n; a3.batch = bc; a3.kc_inner = kcN; a3.nk_outer = n;
-        a3.a.mn_major = 0; a3.a.zb = n; a3.a.zk = 1;
-        a3.b.mn_major = 1; a3.b.zb = 0; a3.b.zk = 1;
+        a3.M = N; a3.Ncols = n; a3.batch = bc; a3.kc_inner = kcN; a3.nk_outer = nv;
+        a3.a.mn_major = 0; a3.a.zb = nv; a3.a.zk = 1;
+        a3.b.mn_major = 1; a3.b.zb = 0; a3.b.zk = 1; a3.b.z0 = v_lo;
         a3.alpha = &sc->f[kFacGWtbar];
         a3.spin_limit = limit; a3.status = h->d_status;
         SOX_CUDA_TRY(launch_gemm_mn(miii, a3, plan_gemm_mn(a3, sms, 64), s));
         // (iv) U2bar (per v; K = (b, P)), accumulated over tau
         GemmMnArgs a4;
-        a4.M = N; a4.Ncols = n; a4.batch = n; a4.kc_inner = kcN; a4.nk_outer = bc;
-        a4.a.mn_major = 1; a4.a.zb = 1; a4.a.zk = n;
+        a4.M = N; a4.Ncols = n; a4.batch = nv; a4.kc_inner = kcN; a4.nk_outer = bc;
+        a4.a.mn_major = 1; a4.a.zb = 1; a4.a.zk = nv;
         a4.b.mn_major = 1; a4.b.zb = 0; a4.b.zk = 1;
         a4.alpha = &sc->f[kFacU2bar];
         a4.accumulate = 1;
@@ -735,13 +747,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         SOX_CUDA_TRY(launch_gemm_mn(miv, a4, plan_gemm_mn(a4, sms, 64), s));
       }
       // (v) U1bar += Abar (x) G(-tau): Abar split once per chunk, then K = (b, v)
-      launch_absmax(Abar, true, g.np4, N, (long long)N * g.np4, bc * n, 1, n, &sc->mx[1], s);
-      launch_split_tensor(Abar, true, g.np4, N, (long long)N * g.np4, bc * n, 1, n, n, g.abar_pitch, 1.f, &sc->mx[1],
+      launch_absmax(Abar, true, g.np4, N, (long long)N * g.np4, bc * nv, 1, n, &sc->mx[1], s);
+      launch_split_tensor(Abar, true, g.np4, N, (long long)N * g.np4, bc * nv, 1, n, n, g.abar_pitch, 1.f, &sc->mx[1],
                           nullptr, Abh, Abl, &sc->sc[kScAbar], s);
       k_u1bar_factor<<<1, 1, 0, s>>>(sc);
       {
         GemmMnArgs a5;
-        a5.M = (int)Nn; a5.Ncols = n; a5.batch = 1; a5.kc_inner = kcn; a5.nk_outer = bc;
+        a5.M = (int)Nn; a5.Ncols = n; a5.batch = 1; a5.kc_inner = (nv + 63) / 64; a5.nk_outer = bc;
         a5.a.mn_major = 1; a5.a.zb = 0; a5.a.zk = 1;
         a5.b.mn_major = 0; a5.b.zb = 0; a5.b.zk = 1;
         a5.alpha = &sc->f[kFacU1bar];

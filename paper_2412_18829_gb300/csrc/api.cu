@@ -240,7 +240,8 @@ Status sigma_fp64(sox_handle H, const Dims &d, const double *G, const double *X,
       {  // D[b][P][R] = sum_v B o C
         sox::ProfScope ps(H, "sox_bcd", s);
         sox::launch_sox_bcd_f64(big, (long long)Nn2, GR, (long long)d.N * d.n, GWt,
-                                (long long)d.N * d.n, Um2, Dm, (long long)d.N * d.N, d.n, d.N, cc, s);
+                                (long long)d.N * d.n, Um2, Dm, (long long)d.N * d.N, d.n, d.N, cc, s,
+                                H ? H->v0 : 0, H ? H->v1 : 0);
       }
       // T[b][R][r] = sum_P D[b][P][R] X[P][r]
       GemmF64 t;
@@ -477,6 +478,14 @@ int sox_check_device(sox_handle h) {
 }
 
 const char *sox_last_error(sox_handle h) { return h ? h->last_error.c_str() : "handle is NULL"; }
+
+int sox_set_v_range(sox_handle h, int v0, int v1) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  if (v0 < 0 || (v1 > 0 && v1 < v0)) return finish(h, {SOX_ERR_INVALID_ARG, "v range must satisfy 0 <= v0 <= v1"});
+  h->v0 = v0;
+  h->v1 = v1;
+  return finish(h, Status::ok());
+}
 
 int sox_reserve(sox_handle h, const sox_problem *p) {
   if (!h) return SOX_ERR_INVALID_ARG;
@@ -791,6 +800,9 @@ int phi_sox_backward(sox_handle h, const sox_problem *p, const double *G, const 
     SOX_TRY(call.output(dG, nsig, &oG));
     SOX_TRY(call.output(dX, (size_t)d.N * d.n, &oX));
     SOX_TRY(call.output(dV, (size_t)d.N * d.N, &oV));
+    if (dG && !sox::v_range_is_full(h, d.n))
+      return {SOX_ERR_UNSUPPORTED, "dG needs the whole Sigma (the identity dPhi/dG = -w Sigma(beta - tau)^T does not "
+                                   "hold for a partial v range); clear the v range or request dX / dV only"};
     size_t need = 0;
     if (dG) need = sigma_bytes(h, d, false) + sox::aligned_bytes(nsig, 8);
     const bool tc_adj = (h->precision == SOX_PREC_F16X2);
@@ -945,15 +957,22 @@ int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, con
     SOX_TRY(call.input(T_inv, 2 * (size_t)n_omega * d.T, &sI));
     SOX_TRY(call.output(Sigma, nsig, &oS));
     Arena ar;
-    SOX_TRY(call.begin(std::max(sigma_bytes(h, d, false), sox::dynamic_bytes(d.n, d.N, d.T, n_omega)), &ar));
+    const bool tc_dyn = (h->precision == SOX_PREC_F16X2);
+    const size_t dyn_bytes = tc_dyn ? sox::dynamic_tc_bytes(h, d.n, d.N, d.T, d.S, n_omega)
+                                    : sox::dynamic_bytes(d.n, d.N, d.T, n_omega);
+    SOX_TRY(call.begin(std::max(sigma_bytes(h, d, false), dyn_bytes), &ar));
     cudaStream_t s = call.stream();
     {  // SOX(v, v): the static part, in the handle's precision
       Arena a1 = ar;
       SOX_TRY(sigma_any(h, d, sG.in, sX.in, sV.in, sV.in, oS.out, a1, s));
     }
     Arena a2 = ar;
-    SOX_TRY(sox::dynamic_sigma_add_f64(h, d.n, d.N, d.T, d.S, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in,
-                                       oS.out, a2, s));
+    if (tc_dyn)
+      SOX_TRY(sox::dynamic_sigma_add_tc(h, d.n, d.N, d.T, d.S, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in,
+                                        oS.out, a2, s));
+    else
+      SOX_TRY(sox::dynamic_sigma_add_f64(h, d.n, d.N, d.T, d.S, n_omega, sG.in, sX.in, sV.in, sW.in, sF.in, sI.in,
+                                         oS.out, a2, s));
     return call.end();
   }();
   return finish(h, st);
@@ -1032,6 +1051,8 @@ int sox_sigma_batch_plan(sox_handle h, int count, const sox_problem *probs, cons
     sox_options o{h->precision, h->device, h->spin_limit, (long long)h->ws_limit, h->autotune ? 0 : 1};
     const int rc = sox_create(&plan->ih, &o);
     if (rc != SOX_OK) return {rc, "could not create the plan's handle"};
+    plan->ih->v0 = h->v0;   // the plan keeps the v range of its handle at creation
+    plan->ih->v1 = h->v1;
     SOX_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     // eager pass: sizes the plan's workspace for the largest instance and settles the
     // autotuned kernel choices, so that the recorded pass allocates and times nothing

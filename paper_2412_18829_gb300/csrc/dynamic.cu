@@ -54,6 +54,8 @@ Status dynamic_sigma_add_f64(sox_handle h, int n, int N, int T, int S, int n_ome
   if (!Tm) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   ProfScope ps(h, "sosex_dynamic_f64", s, 0);
   long long launches = 0;
+  int v_lo = 0, v_hi = n;   // the handle's v range (sox_set_v_range)
+  v_range(h, n, &v_lo, &v_hi);
   // U[P][q][s] = sum_Q V[P][Q] X[Q][q] X[Q][s]
   launch_pair_products_f64(X, Y, N, n, s);
   GemmF64 m;
@@ -75,7 +77,7 @@ Status dynamic_sigma_add_f64(sox_handle h, int n, int N, int T, int S, int n_ome
     gw.bk = 1; gw.bj = n; gw.C = GWt;
     launch_gemm_f64(gw, s);
     launches += 2;
-    for (int v = 0; v < n; ++v) {
+    for (int v = v_lo; v < v_hi; ++v) {
       k_gg<<<grid1((long long)T * Nn), 256, 0, s>>>(GWt, GR, T, N, n, v, GG);
       for (int c = 0; c < 2; ++c) {  // GGw[m][(Q,u)][c] = sum_j {Re, Im} T_fwd[m][j] GG[j][(Q,u)]
         GemmF64 f;
@@ -105,7 +107,7 @@ Status dynamic_sigma_add_f64(sox_handle h, int n, int N, int T, int S, int n_ome
       launches += 6;
     }
     // D[i] = sum_v (A[i][v] X^T) o (GWt_i U_v^T): the fused kernel with X in the G_Rq slot
-    launch_sox_bcd_f64(A, (long long)n * Nn, X, 0, GWt, Nn, Um, D, NN, n, N, T, s);
+    launch_sox_bcd_f64(A, (long long)n * Nn, X, 0, GWt, Nn, Um, D, NN, n, N, T, s, v_lo, v_hi);
     GemmF64 t;  // T[i][R][r] = sum_P D[i][P][R] X[P][r]
     t.M = N; t.Nc = n; t.K = N; t.batch = T;
     t.A = D; t.sA = NN; t.ai = 1; t.ak = N;

@@ -9,4 +9,10 @@ size_t dynamic_bytes(int n, int N, int T, int n_omega);
 Status dynamic_sigma_add_f64(sox_handle h, int n, int N, int T, int S, int n_omega, const double *G, const double *X,
                              const double *V, const double *Wd, const double *Tf, const double *Ti, double *Sigma,
                              Arena &ar, cudaStream_t s);
+// The same in split precision (dynamic_tc.cu): the transforms and the W_d product as
+// FP16-pair GEMMs on the tensor cores, then the fused B/C/D kernel with X in the G_Rq slot.
+size_t dynamic_tc_bytes(sox_handle h, int n, int N, int T, int S, int n_omega);
+Status dynamic_sigma_add_tc(sox_handle h, int n, int N, int T, int S, int n_omega, const double *G, const double *X,
+                            const double *V, const double *Wd, const double *Tf, const double *Ti, double *Sigma,
+                            Arena &ar, cudaStream_t s);
 }  // namespace sox

@@ -92,7 +92,7 @@ __global__ void k_pair_products(const double *X, double *Y, int N, int n) {
 __global__ void __launch_bounds__(NT) k_sox_bcd_f64(const double *A, long long sA, const double *GR,
                                                    long long sGR, const double *GWt, long long sGW,
                                                    const double *U2, double *D, long long sD, int n,
-                                                   int N) {
+                                                   int N, int v0, int v1) {
   __shared__ double s_a[TK][TM + 1];
   __shared__ double s_gr[TK][TN + 1];
   __shared__ double s_gw[TK][TM + 1];
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NT) k_sox_bcd_f64(const double *A, long long s
   const double *GWb = GWt + b * sGW;
   double d[4][4] = {};
   const long long nn = (long long)n * n;
-  for (int v = 0; v < n; ++v) {
+  for (int v = v0; v < v1; ++v) {
     double bacc[4][4] = {}, cacc[4][4] = {};
     const double *Av = Ab + (long long)v * N * n;  // A[v][P][q]
     const double *Uv = U2 + (long long)v * n;      // U2[R][v][w], row stride n^2
@@ -383,9 +383,11 @@ void launch_pair_products_f64(const double *X, double *Y, int N, int n, cudaStre
 
 void launch_sox_bcd_f64(const double *A, long long sA, const double *GR, long long sGR,
                         const double *GWt, long long sGW, const double *U2, double *D,
-                        long long sD, int n, int N, int batch, cudaStream_t s) {
+                        long long sD, int n, int N, int batch, cudaStream_t s, int v0, int v1) {
   dim3 grid((N + TN - 1) / TN, (N + TM - 1) / TM, batch);
-  k_sox_bcd_f64<<<grid, NT, 0, s>>>(A, sA, GR, sGR, GWt, sGW, U2, D, sD, n, N);
+  v1 = (v1 <= 0 || v1 > n) ? n : v1;
+  v0 = v0 < 0 ? 0 : (v0 > v1 ? v1 : v0);
+  k_sox_bcd_f64<<<grid, NT, 0, s>>>(A, sA, GR, sGR, GWt, sGW, U2, D, sD, n, N, v0, v1);
 }
 
 void launch_trace_sigma_gminus(const double *Sigma, const double *G, int n, int n_tau,

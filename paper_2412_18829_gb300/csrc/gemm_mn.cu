@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k0 = (int)(c % a.kc_inner) * kC;
           uint8_t *st = smem + (size_t)s * kStageBytes;
           load_operand(st, &tmA_hi, &tmA_lo, &bar->full[s], a.a.mn_major, w.i0, k0,
-                       (int)((w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
+                       (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
           load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, &bar->full[s], a.b.mn_major, w.j0, k0,
-                       (int)((w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
+                       (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
         }
       }
       for (int s = 0; s < kStages; ++s) {   // every copy issued has landed before the CTA exits

@@ -15,11 +15,13 @@ namespace sox {
 //   mn_major = 0: map dims (K, rows, z), box 64 x 128: each 64-wide K chunk of 128 rows.
 //   mn_major = 1: map dims (rows, K, z), box 64 x 64: two boxes per chunk (rows 0-63,
 //                 64-127 of the tile), K running down the map's second dimension.
-// The map's z coordinate for output batch b and outer K index kz is (b / zdiv) * zb + kz * zk.
+// The map's z coordinate for output batch b and outer K index kz is
+// z0 + (b / zdiv) * zb + kz * zk.
 struct MnOperand {
   int mn_major = 0;
   long long zb = 0, zk = 0;
   int zdiv = 1;   // the batch term uses b / zdiv
+  long long z0 = 0;   // constant offset of the z coordinate
 };
 
 // C[b](i, j) (+)= alpha * sum_k A(i, k) B(j, k) with k = (kz, kk), kz < nk_outer,

@@ -24,6 +24,7 @@ struct sox_context {
   size_t aux_bytes = 0;
   int *d_status = nullptr;   // device status word for bounded waits
   int sm_count = 0;
+  int v0 = 0, v1 = 0;        // sox_set_v_range: sums over the orbital index v run over [v0, v1) (v1 = 0: all)
   bool autotune = true;      // time the fused-kernel variants on the first call per shape
   std::map<std::string, int> tuned;  // shape key -> chosen variant
   std::string last_error;
@@ -80,6 +81,20 @@ struct Status {
     if (!s_.good()) return s_;        \
   } while (0)
 
+// The handle's v range clamped to [0, n]: *lo <= *hi.
+inline void v_range(const sox_context *h, int n, int *lo, int *hi) {
+  int b = (h && h->v1 > 0) ? (h->v1 < n ? h->v1 : n) : n;
+  int a = h ? h->v0 : 0;
+  a = a < 0 ? 0 : (a > b ? b : a);
+  *lo = a;
+  *hi = b;
+}
+inline bool v_range_is_full(const sox_context *h, int n) {
+  int a, b;
+  v_range(h, n, &a, &b);
+  return a == 0 && b == n;
+}
+
 // Bump allocator over the handle workspace (256-byte aligned slices).
 // Chunk budget of a planner: the handle's override, else the planner's default.
 inline size_t chunk_budget(const sox_context *h, size_t dflt) { return (h && h->ws_limit) ? h->ws_limit : dflt; }
@@ -114,10 +129,11 @@ void launch_gemm_f64(const GemmF64 &g, cudaStream_t s);
 void launch_pair_products_f64(const double *X, double *Y, int N, int n, cudaStream_t s);
 
 // D[b][P][R] = sum_v (sum_q A[b][v][P][q] GR[b][R][q]) * (sum_w GWt[b][P][w] U2[R][v][w])
-// b runs over `batch` (tau points of one spin); strides in elements.
+// b runs over `batch` (tau points of one spin); strides in elements.  The v sum runs over
+// [v0, v1) (v1 <= 0: all n).
 void launch_sox_bcd_f64(const double *A, long long sA, const double *GR, long long sGR,
                         const double *GWt, long long sGW, const double *U2, double *D,
-                        long long sD, int n, int N, int batch, cudaStream_t s);
+                        long long sD, int n, int N, int batch, cudaStream_t s, int v0 = 0, int v1 = 0);
 
 // phi_part[b] = sum_tr Sigma[b][t][r] * Gm[b][r][t] with Gm[b] = -G[n_tau-1-tau(b)]
 void launch_trace_sigma_gminus(const double *Sigma, const double *G, int n, int n_tau,

@@ -233,6 +233,8 @@ KpointPlan kpoint_plan(sox_handle h, int n, int N, int T, int S, const int nkv[3
 
 Status kpoint_sigma_f64(sox_handle h, const sox_problem *pr, const double *Gd, const double *Xd, const double *U1d,
                         const double *U2d, double *Sd, Arena &ar, cudaStream_t s) {
+  int v_lo = 0, v_hi = pr->n;   // the handle's v range (sox_set_v_range)
+  v_range(h, pr->n, &v_lo, &v_hi);
   const int n = pr->n, N = pr->N, T = pr->n_tau, S = pr->n_spin;
   const KpointPlan pl = kpoint_plan(h, n, N, T, S, pr->nk);
   const int nk = pl.nk, nv = pl.nv;
@@ -318,8 +320,8 @@ Status kpoint_sigma_f64(sox_handle h, const sox_problem *pr, const double *Gd, c
         launches += 2;
       }
       SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)nk * NN, s));
-      for (int v0 = 0; v0 < n; v0 += nv) {
-        const int cv = std::min(nv, n - v0);
+      for (int v0 = v_lo; v0 < v_hi; v0 += nv) {   // the handle's v range (sox_set_v_range)
+        const int cv = std::min(nv, v_hi - v0);
         // A[pair][vl][P][q] = -sum_s G^{k'}(tau_{T-1-j})[s][v0+vl] M1[pair][P][q][s]
         for (int q = 0; q < nk; ++q) {
           ZGemm g = zg();
@@ -415,6 +417,8 @@ size_t kpoint_dynamic_bytes(sox_handle h, int n, int N, int T, int n_omega, cons
 Status kpoint_dynamic_add_f64(sox_handle h, const sox_problem *pr, int n_omega, const double *Gd, const double *Xd,
                               const double *Vd, const double *Wdd, const double *Tfd, const double *Tid, double *Sd,
                               Arena &ar, cudaStream_t s) {
+  int v_lo = 0, v_hi = pr->n;   // the handle's v range (sox_set_v_range)
+  v_range(h, pr->n, &v_lo, &v_hi);
   const int n = pr->n, N = pr->N, T = pr->n_tau, S = pr->n_spin, nO = n_omega;
   int ct = 1;
   kpoint_dynamic_bytes(h, n, N, T, nO, pr->nk, &ct);
@@ -499,7 +503,7 @@ Status kpoint_dynamic_add_f64(sox_handle h, const sox_problem *pr, int n_omega, 
       launches += 2;
     }
     SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)T * nk * NN, s));
-    for (int v = 0; v < n; ++v) {
+    for (int v = v_lo; v < v_hi; ++v) {   // the handle's v range (sox_set_v_range)
       for (int q1 = 0; q1 < nk; ++q1) {
         k_gg_k<<<grid1((long long)nk * T * Nn), 256, 0, s>>>(GWt, GR, d_sub, nk, q1, T, N, n, v, GG);
         ZGemm f = zg();  // GGw[ks][m] = sum_j T_fwd[m][j] GG[ks][j]
@@ -707,6 +711,8 @@ size_t kpoint_tc_bytes(sox_handle, const sox_problem *p, bool two) {
 
 Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, const double *Xd, const double *U1d,
                        const double *U2d, double *Sd, Arena &ar, cudaStream_t s) {
+  int v_lo = 0, v_hi = pr->n;   // the handle's v range (sox_set_v_range)
+  v_range(h, pr->n, &v_lo, &v_hi);
   const KTc g = ktc_geom(pr);
   const bool two = (U1d != U2d);
   const z *G = reinterpret_cast<const z *>(Gd);
@@ -764,7 +770,7 @@ Status kpoint_sigma_tc(sox_handle h, const sox_problem *pr, const double *Gd, co
       SOX_TRY(cgemm_tc(h, Gms, M1s, (int)g.nk2, tb.kk, nullptr, -1.f, Aall, 2 * ldNn, 2LL * g.n * ldNn, s));
       SOX_CUDA_TRY(cudaMemsetAsync(D, 0, 16 * (size_t)g.nk * g.N * g.ldN, s));
       launches += 5;
-      for (int v = 0; v < g.n; ++v) {
+      for (int v = v_lo; v < v_hi; ++v) {   // the handle's v range (sox_set_v_range)
         csplit_a(reinterpret_cast<const float2 *>(Aall) + (long long)v * ldNn, true, g.n * ldNn, g.n, 0, 0, 1,
                  (int)g.nk2, g.N, g.n, As, s);
         {
@@ -843,6 +849,8 @@ size_t kpoint_dynamic_tc_bytes(sox_handle h, const sox_problem *p, int n_omega) 
 Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const double *Gd, const double *Xd,
                          const double *Vd, const double *Wdd, const double *Tfd, const double *Tid, double *Sd,
                          Arena &ar, cudaStream_t s) {
+  int v_lo = 0, v_hi = pr->n;   // the handle's v range (sox_set_v_range)
+  v_range(h, pr->n, &v_lo, &v_hi);
   const KDynTc d = kdyn_geom(h, pr, n_omega, nullptr, nullptr);
   const KTc &g = d.g;
   const int nO = d.nO, T = g.T, n = g.n, N = g.N, nk = g.nk;
@@ -911,7 +919,7 @@ Status kpoint_dynamic_tc(sox_handle h, const sox_problem *pr, int n_omega, const
     csplit_a(GWt, false, (long long)T * g.Nn, n, 0, 0, 1, nk, T * N, n, GWts, s);
     SOX_CUDA_TRY(cudaMemsetAsync(Dall, 0, 16 * (size_t)T * nk * N * g.ldN, s));
     ++launches;
-    for (int v = 0; v < n; ++v) {
+    for (int v = v_lo; v < v_hi; ++v) {   // the handle's v range (sox_set_v_range)
       for (int q1 = 0; q1 < nk; ++q1) {
         k_gg_k<<<grid1((long long)nk * T * g.Nn), 256, 0, s>>>(GWt, GR, tb.sub, nk, q1, T, N, n, v, GG);
         // B rows (Q,u) of GG^{ks}, K = tau_j

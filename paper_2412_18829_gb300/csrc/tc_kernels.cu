@@ -143,7 +143,7 @@ __device__ __forceinline__ void bcd_epilogue(Bar *bar, uint32_t tmem, const BcdA
 #pragma unroll
     for (int j = 0; j < kTile; ++j) d[j] = 0.f;
     bool ok = true;
-    for (int v = 0; v < a.n; ++v, ++acc_it) {
+    for (int v = a.v0; v < a.v1; ++v, ++acc_it) {
       const int buf = (int)(acc_it & 1);
       const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
       ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         const int b = (int)(t / tiles_per_b);
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
-        for (int v = 0; v < a.n && !*abort; ++v) {
+        for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int half = 0; half < 2; ++half) {
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kStages);
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
-        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+        for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           tc::tma_load_3d(res_ptr(res, 1, 0, kc), &tmGW_hi, &bar->res_full, x, P0, b);
           tc::tma_load_3d(res_ptr(res, 1, 1, kc), &tmGW_lo, &bar->res_full, x, P0, b);
         }
-        for (int v = 0; v < a.n && !*abort; ++v) {
+        for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int half = 0; half < 2; ++half) {
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kRStages);
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++tt) {
         ok = tc::mbar_wait(&bar->res_full, (uint32_t)(tt & 1), a.spin_limit, abort, a.status, 32);
         if (!ok) break;
-        for (int v = 0; v < a.n && ok; ++v, ++acc_it) {
+        for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
@@ -1132,7 +1132,10 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers)
 
 size_t res_smem_bytes() { return (size_t)kResBytes + kRStages * kRStageBytes + sizeof(ResBarriers) + 1024; }
 
-cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant) {
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int grid, cudaStream_t s, int variant) {
+  BcdArgs a = args;
+  a.v1 = (a.v1 <= 0 || a.v1 > a.n) ? a.n : a.v1;
+  a.v0 = a.v0 < 0 ? 0 : (a.v0 > a.v1 ? a.v1 : a.v0);
   if (variant == kBcdResident && a.Kp <= 128) {
     static std::atomic<unsigned long long> rattr{0};
     const cudaError_t e = set_smem_once(k_sox_bcd_tc_res, (int)res_smem_bytes(), rattr);

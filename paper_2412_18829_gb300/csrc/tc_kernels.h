@@ -13,6 +13,7 @@ enum { kStoreSplit = 1, kStoreSplitGroup = 2, kStoreF32 = 3 };
 
 struct BcdArgs {
   int n = 0, N = 0, Kp = 0, batch = 0;
+  int v0 = 0, v1 = 0;                // the v sum runs over [v0, v1) (launch_sox_bcd_tc: v1 <= 0 means n)
   long long spin_limit = 0;
   int *status = nullptr;
   const float *row_scale = nullptr;  // [batch][N]

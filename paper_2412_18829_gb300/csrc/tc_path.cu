@@ -228,6 +228,7 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       ProfScope ps(h, "sox_bcd_tc", s);
       BcdArgs ba;
       ba.n = n; ba.N = N; ba.Kp = Kp; ba.batch = bc;
+      v_range(h, n, &ba.v0, &ba.v1);
       ba.spin_limit = limit; ba.status = h->d_status;
       ba.row_scale = rowf; ba.col_scale = colf;
       ba.Dt = Dt; ba.ldD = N;
@@ -241,8 +242,9 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       ProfScope ps(h, "backproject", s, 2);
       launch_backproject_T(Dt, N, X, N, n, bc, Tm, s);
       // bare SOX with a symmetric G(tau) has a symmetric Sigma(tau)
+      // (a partial v range breaks that symmetry: then every block is computed)
       launch_backproject_sigma(X, Tm, N, n, bc, Sigma + (long long)b0 * n * n, (long long)n * n, s,
-                               two ? nullptr : symf);
+                               (two || !v_range_is_full(h, n)) ? nullptr : symf);
     }
   }
   SOX_CUDA_TRY(cudaGetLastError());

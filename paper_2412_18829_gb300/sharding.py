@@ -101,3 +101,30 @@ def assemble(parts, orders, n_tau: int, axis: int = 2):
             src[axis] = p
             out[tuple(idx)] = part[tuple(src)]
     return out
+
+
+# ---------------------------------------------------------------------------
+# One build split over ranks by the orbital index v.  Eq. (sox) sums over v, the column of
+# G(-tau) in G_sv(-tau) (the index the dynamic algorithm of Sec. II C moves to the outside
+# loop); every step of the static and dynamic chains is linear in that sum, so a rank that
+# keeps only its own v range (sox_set_v_range) returns a partial Sigma, and the sum of the
+# partials over a partition of [0, n) is the whole build: one all-reduce of the orbital-basis
+# Sigma.  Every v costs the same (one B_v / C_v pair per tile and tau), so equal contiguous
+# ranges balance the ranks.  This split also keeps a solid's n_k^3 D step whole: each rank
+# runs the Fourier form of the D step over the full k mesh for its own v.
+# ---------------------------------------------------------------------------
+def v_shards(n: int, world: int) -> list[tuple[int, int]]:
+    """Contiguous [v0, v1) ranges of the orbital index, one per rank, sizes differing by at
+    most one; every v in exactly one range.  Refuses more ranks than orbitals."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    if n < world:
+        raise ValueError(f"{n} orbitals cannot give each of {world} ranks a v")
+    base, extra = divmod(n, world)
+    out, v0 = [], 0
+    for r in range(world):
+        v1 = v0 + base + (1 if r < extra else 0)
+        out.append((v0, v1))
+        v0 = v1
+    return out
+

@@ -27,14 +27,16 @@ def _inputs(n, N, n_tau, beta, M, n_spin, seed):
 
 
 def _run(env, prec, w, Tf, Ti, Wd):
+    """prec: "fp64" / "f16x2" (the module's handles) or a Handle of its own."""
     torch, pkg, hs = env
+    h = hs[prec] if isinstance(prec, str) else prec
     p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
     G, X, V, W = to_dev(torch, w.G, w.X, w.V, Wd)
     F = torch.from_numpy(Tf).cuda()
     I = torch.from_numpy(Ti).cuda()
     S = torch.full_like(G, float("nan"))
-    pkg.sosex_dynamic_sigma(hs[prec], p, G, X, V, W, F, I, Tf.shape[0], S)
-    pkg.sox_check_device(hs[prec])
+    pkg.sosex_dynamic_sigma(h, p, G, X, V, W, F, I, Tf.shape[0], S)
+    pkg.sox_check_device(h)
     return S.cpu().numpy()
 
 
@@ -44,7 +46,7 @@ def test_sosex_dynamic_matches_oracle(env, prec, n, N, n_tau, M, n_spin):
     w, Tf, Ti, Wd = _inputs(n, N, n_tau, 20.0, M, n_spin, seed=50 + n)
     ref = dynamic.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, w.G).real
     got = _run(env, prec, w, Tf, Ti, Wd)
-    check(got, ref, prec, f"dynamic n={n}")
+    check(got, ref, prec, f"dynamic n={n}", n=n, N=N)
 
 
 def test_dynamic_part_alone_with_zero_screening_is_bare_sox(env):
@@ -53,3 +55,17 @@ def test_dynamic_part_alone_with_zero_screening_is_bare_sox(env):
     from oracle import sox
     ref = sox.sox_sigma(w.X, w.V, w.G).real
     check(got, ref, "fp64", "W_d = 0")
+
+
+def test_sosex_dynamic_split_two_tiles_and_tau_chunks(env):
+    """Split precision on the tensor cores (transforms, W_d product, fused B/C/D) at two
+    128-row P/R tiles and beta = 100, with the default tau chunk and with one tau point per
+    chunk (workspace_limit = 1 byte), every element against the oracle at 1e-8 Ha."""
+    torch, pkg, _ = env
+    w, Tf, Ti, Wd = _inputs(40, 200, 10, 100.0, 5, 1, seed=70)
+    ref = dynamic.sosex_dynamic_sigma(w.X, w.V, Wd, Tf, Ti, w.G).real
+    for limit in (0, 1):
+        with pkg.Handle("f16x2", workspace_limit=limit) as h:
+            got = _run(env, h, w, Tf, Ti, Wd)
+        err, scale = check(got, ref, "f16x2", f"dynamic split, workspace_limit={limit}", n=w.n, N=w.N)
+        print(f"dynamic split limit={limit}: max|dSigma| {err:.3e} Ha (max|Sigma| {scale:.3e})")

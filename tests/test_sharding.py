@@ -135,3 +135,86 @@ def test_two_gloo_ranks_share_one_build_by_tau():
         assert p.exitcode == 0
     for _, err, scale in res:
         assert err <= 1e-15 * scale
+
+
+@pytest.mark.parametrize("n,world", [(1, 1), (5, 2), (7, 3), (120, 8), (26, 4)])
+def test_v_shards_partition_the_orbital_index(n, world):
+    parts = sharding.v_shards(n, world)
+    assert len(parts) == world
+    assert parts[0][0] == 0 and parts[-1][1] == n
+    for (a, b), (c, _) in zip(parts, parts[1:]):
+        assert b == c
+    sizes = [b - a for a, b in parts]
+    assert min(sizes) >= 1 and max(sizes) - min(sizes) <= 1
+
+
+def test_v_shards_refuse_more_ranks_than_orbitals():
+    with pytest.raises(ValueError):
+        sharding.v_shards(3, 4)
+    with pytest.raises(ValueError):
+        sharding.v_shards(3, 0)
+
+
+def _mask_columns(Gm, v0, v1):
+    """G(-tau) with the columns v outside [v0, v1) set to zero: Eq. (sox) then keeps only the
+    terms of the rank's v range (v enters through G_sv(-tau) and the mixed tensor U2_Rvw,
+    whose products with the zeroed columns vanish)."""
+    out = np.zeros_like(Gm)
+    out[..., v0:v1] = Gm[..., v0:v1]
+    return out
+
+
+def _v_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    from oracle import grid, kpoints, sox
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = {}
+        # molecule: partial Sigma of the rank's v range at every tau, summed over ranks
+        w = synth.tiny(5, 11, n_tau=4)
+        v0, v1 = sharding.v_shards(w.n, world)[rank]
+        Gm = grid.g_minus_tau(w.G[0, 0].astype(complex))
+        part = np.stack([sox.sigma_chain(w.X[0], w.V[0], w.V[0], w.G[0, 0, j], _mask_columns(Gm[j], v0, v1))
+                         for j in range(w.n_tau)])
+        t = torch.from_numpy(np.ascontiguousarray(part.real))
+        dist.all_reduce(t)
+        full = sox.sox_sigma(w.X, w.V, w.G)[0, 0].real
+        out["molecule"] = (float(np.abs(t.numpy() - full).max()), float(np.abs(full).max()))
+        # solid: the momentum-resolved chain, G(-tau)^k masked for every k
+        s = synth.solid(9, (1, 1, 2), 4, 9, 3, 10.0)
+        v0, v1 = sharding.v_shards(s.n, world)[rank]
+        Gs = np.asarray(s.G[0], complex)
+        Gms = grid.g_minus_tau(Gs)
+        part = np.stack([kpoints.sigma_chain(s.X, s.V, s.V, Gs[:, j], _mask_columns(Gms[:, j], v0, v1), s.nk)
+                         for j in range(s.n_tau)])
+        t = torch.from_numpy(np.ascontiguousarray(part))
+        dist.all_reduce(t)
+        full = kpoints.sox_sigma(s.X, s.V, s.G, s.nk)[0].transpose(1, 0, 2, 3)
+        out["solid"] = (float(np.abs(t.numpy() - full).max()), float(np.abs(full).max()))
+        q.put((rank, out))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_one_build_by_v():
+    """Each rank keeps the terms of its own v range; one all-reduce of the orbital-basis
+    Sigma gives the whole build (molecule and solid, oracle chains on CPU)."""
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_v_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=180) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, out in res:
+        for what, (err, scale) in out.items():
+            assert scale > 0
+            assert err <= 1e-14 * scale, what
