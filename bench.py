@@ -23,7 +23,7 @@ the host cores instead (a bounded sample per step, scaled to builds/s).
 process, one GPU, a few GB on the device): KIND is molecule (sox_sigma twice at
 n=120, N=600, 2 spins), screened (sox_sigma twice at n=250, N=2000), batch
 (phi_sox + phi_sox_grad_G twice at the batch's largest instance, n=298, N=1788),
-adjoint (phi_sox_backward twice at that instance), solid (sosex_dynamic_sigma at
+adjoint (phi_sox_backward twice at that instance; --profile-sizes n,N for others), solid (sosex_dynamic_sigma at
 the 3x3x3 solid's shapes; --mesh and --profile-sizes n,N change them) or wdyn
 (sox_w_dynamic at the solid's shapes); --profile-tau sets the tau points.
 """
@@ -1078,7 +1078,8 @@ def profile_case(args):
     elif kind in ("batch", "adjoint"):
         T = args.profile_tau or 8
         n = int(synth.batch_c4_sizes().max())
-        w = synth.molecule(4, n, 6 * n, T, 100.0, 1)
+        n, N = (int(x) for x in args.profile_sizes.split(",")) if args.profile_sizes else (n, 6 * n)
+        w = synth.molecule(4, n, N, T, 100.0, 1)
         _, wts = pkg.sox_tau_grid(w.n_tau, w.beta)
         p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
         G, X, V, tw = (dev(a) for a in (w.G, w.X, w.V, wts))

@@ -335,6 +335,78 @@ SOX_API const char *sox_plan_last_error(sox_plan plan);
 SOX_API int sox_plan_destroy(sox_plan plan);
 
 /* ------------------------------------------------------------------------
+ * The self-consistent loop around Sigma for molecules (Sec. II A): its device steps.
+ * Real molecular data (SOX_REAL64, n_k = 1); layouts as above plus
+ *   omegas  [n_w]                        fermionic Matsubara frequencies w = (2m+1) pi / beta
+ *   F, Sigma_hf, gamma, tails             [n_spin][n][n] real (tails: [n_spin][3][n][n])
+ *   Sigma_iw, G_iw                        [n_spin][n_w][n][n] complex (interleaved)
+ *   G_tau, Sigma_tau                      [n_spin][n_tau][n][n] real
+ * Host or device pointers like the other calls (sox_mix_green: device only).  FP64.
+ * ------------------------------------------------------------------------ */
+
+/* Dyson equation on the Matsubara frequencies (Eqs. Dyson and G0, S = 1):
+ *   G_iw[s][w] = [(i w + mu) 1 - F[s] - Sigma_iw[s][w]]^-1
+ * with F = H0 + Sigma_HF (the static part) and Sigma_iw the dynamic part (NULL: zero).
+ * Complex Gauss-Jordan with partial pivoting, one CUDA block per (spin, frequency).
+ * Synchronises `stream`; SOX_ERR_INVALID_ARG for a singular system. */
+SOX_API int sox_dyson(sox_handle h, const sox_problem *p, int n_w, const double *omegas, double mu, const double *F,
+                      const double *Sigma_iw, double *G_iw, void *stream);
+
+/* High-frequency coefficients of G = [i w - (F - mu) - Sigma(i w)]^-1:
+ *   tails[s] = {1, F[s] - mu, (F[s] - mu)^2 + Sigma_1[s]},  Sigma_1 = -(Sigma(tau_{n_tau-1}) + Sigma(tau_0))
+ * (the jump of the antiperiodic Sigma(tau); Sigma_tau NULL: zero). */
+SOX_API int sox_green_tails(sox_handle h, const sox_problem *p, double mu, const double *F, const double *Sigma_tau,
+                            double *tails, void *stream);
+
+/* Back to imaginary time with the tails summed exactly:
+ *   G_tau[s][t] = Re[(1/beta) sum_w e^{-i w tau_t} (G(i w) - c1/(i w) - c2/(i w)^2 - c3/(i w)^3)]
+ *                 - c1/2 + (2 tau_t - beta)/4 c2 + tau_t (beta - tau_t)/4 c3
+ * (the closed-form tau images of the three tail powers summed over all fermionic w), at the
+ * caller's n_t points tau [n_t] of [0, beta] (end points read as 0^+ and beta^-). */
+SOX_API int sox_iw_to_tau(sox_handle h, const sox_problem *p, int n_w, const double *omegas, const double *G_iw,
+                          const double *tails, int n_t, const double *tau, double *G_tau, void *stream);
+
+/* To the Matsubara frequencies with the caller's transform (the paper takes its transforms
+ * from sparse-ir; any quadrature of F(i w) = int_0^beta e^{i w tau} F(tau) d tau for the
+ * interpolant on the tau grid): F_iw[s][w] = sum_j T_w[w][j] F_tau[s][j], T_w [n_w][n_tau] complex. */
+SOX_API int sox_tau_to_iw(sox_handle h, const sox_problem *p, int n_w, const double *T_w, const double *F_tau,
+                          double *F_iw, void *stream);
+
+/* Chemical potential for the target electron count (Sec. II A): bisection on [lo, hi] of
+ *   count(mu) = sum_s Tr gamma^s(mu),  gamma = -G(beta^-)^T  from the Dyson G at mu
+ * until hi - lo < tol or max_iter steps; *mu (host) receives the midpoint.  Synchronises. */
+SOX_API int sox_find_mu(sox_handle h, const sox_problem *p, int n_w, const double *omegas, double target,
+                        const double *F, const double *Sigma_iw, const double *Sigma_tau, double lo, double hi,
+                        double tol, int max_iter, double *mu);
+
+/* Correlated density matrix gamma_pq = G_qp(0^-) = -G_qp(beta^-) from G_tau's last point
+ * (the sign reading of Sec. II A's gamma that gives positive occupations). */
+SOX_API int sox_density_matrix(sox_handle h, const sox_problem *p, const double *G_tau, double *gamma, void *stream);
+
+/* Hartree-Fock self-energy in THC form, (pq|rs) = sum_PQ X_Pp X_Pq V_PQ X_Qr X_Qs:
+ *   Sigma_hf[s] = J - K[s],  J_pq = sum_rs (pq|rs) rho_rs (rho = sum_s gamma[s]),
+ *   K[s]_pq = sum_rs (pr|sq) gamma[s]_rs,
+ * and, when F is not NULL, the static part of the Dyson equation F[s] = H0 + Sigma_hf[s]
+ * (H0 [n][n], needed then).  X [N][n], V [N][N]. */
+SOX_API int sox_sigma_hf(sox_handle h, const sox_problem *p, const double *X, const double *V, const double *gamma,
+                         const double *H0, double *Sigma_hf, double *F, void *stream);
+
+/* Galitskii-Migdal energies summed over spin blocks (Eqs. E1b and E2b, the latter in
+ * imaginary time on the mirror-symmetric grid with weights w [n_tau]):
+ *   E[0] = E_inf = sum_s sum_pq (H0 + Sigma_hf[s] / 2)_pq gamma[s]_pq
+ *   E[1] = E_dyn = -sum_s sum_j w_j Tr[Sigma[s](tau_{n_tau-1-j}) G[s](tau_j)]
+ * H0 [n][n]; E [2] (host or device). */
+SOX_API int sox_gm_energies(sox_handle h, const sox_problem *p, const double *H0, const double *Sigma_hf,
+                            const double *gamma, const double *Sigma_tau, const double *G_tau, const double *w,
+                            double *E, void *stream);
+
+/* Linear mixing of the iteration (the paper's CDIIS is not part of this library):
+ *   G = (1 - a) G + a G_new over `count` doubles (device), *change (host) = max |G_new - G|
+ * before the update.  Synchronises `stream`. */
+SOX_API int sox_mix_green(sox_handle h, long long count, double a, double *G, const double *G_new, double *change,
+                          void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free variant (the paper has no counterpart; this is a service to
  * callers of the library).
  *

@@ -20,6 +20,15 @@ from ._binding import (  # noqa: F401
     sosex_static_sigma,
     sox_check_device,
     sox_set_v_range,
+    sox_dyson,
+    sox_green_tails,
+    sox_iw_to_tau,
+    sox_tau_to_iw,
+    sox_find_mu,
+    sox_density_matrix,
+    sox_sigma_hf,
+    sox_gm_energies,
+    sox_mix_green,
     sox_pi0,
     sox_profile_enable,
     sox_profile_read,

@@ -75,6 +75,16 @@ _SIGS = {
     "sox_plan_check_device": ([_P], _I),
     "sox_plan_last_error": ([_P], ctypes.c_char_p),
     "sox_plan_destroy": ([_P], _I),
+    "sox_dyson": ([_P, ctypes.POINTER(sox_problem), _I, _P, ctypes.c_double, _P, _P, _P, _P], _I),
+    "sox_green_tails": ([_P, ctypes.POINTER(sox_problem), ctypes.c_double, _P, _P, _P, _P], _I),
+    "sox_iw_to_tau": ([_P, ctypes.POINTER(sox_problem), _I, _P, _P, _P, _I, _P, _P, _P], _I),
+    "sox_tau_to_iw": ([_P, ctypes.POINTER(sox_problem), _I, _P, _P, _P, _P], _I),
+    "sox_find_mu": ([_P, ctypes.POINTER(sox_problem), _I, _P, ctypes.c_double, _P, _P, _P, ctypes.c_double,
+                     ctypes.c_double, ctypes.c_double, _I, ctypes.POINTER(ctypes.c_double)], _I),
+    "sox_density_matrix": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P], _I),
+    "sox_sigma_hf": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P], _I),
+    "sox_gm_energies": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "sox_mix_green": ([_P, ctypes.c_longlong, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double), _P], _I),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -115,6 +125,11 @@ def _ptr(t):
     if t.dtype not in (torch.float64, torch.complex128) or not t.is_contiguous():
         raise ValueError("tensors must be contiguous float64 or complex128")
     return t.data_ptr()
+
+
+def _len(t) -> int:
+    """Length of a 1-D array or tensor."""
+    return int(t.shape[0])
 
 
 def _stream(stream):
@@ -340,3 +355,57 @@ def sox_sigma_fp64_noalloc(p: sox_problem, G, X, V, Sigma, stream=None):
     rc = lib().sox_sigma_fp64_noalloc(ctypes.byref(p), _ptr(G), _ptr(X), _ptr(V), _ptr(Sigma), _stream(stream))
     if rc != SOX_OK:
         raise SoxError(rc, "sox_sigma_fp64_noalloc failed (see include/thc_sox.h for the status meanings)")
+
+
+# ---------------------------------------------------------------------------
+# The self-consistent loop's device steps (Sec. II A); argument marshalling only.
+# ---------------------------------------------------------------------------
+def sox_dyson(h: Handle, p: sox_problem, omegas, mu: float, F, Sigma_iw, G_iw, stream=None):
+    h.check(lib().sox_dyson(h.ptr, ctypes.byref(p), _len(omegas), _ptr(omegas), float(mu), _ptr(F), _ptr(Sigma_iw),
+                            _ptr(G_iw), _stream(stream)))
+
+
+def sox_green_tails(h: Handle, p: sox_problem, mu: float, F, Sigma_tau, tails, stream=None):
+    h.check(lib().sox_green_tails(h.ptr, ctypes.byref(p), float(mu), _ptr(F), _ptr(Sigma_tau), _ptr(tails),
+                                  _stream(stream)))
+
+
+def sox_iw_to_tau(h: Handle, p: sox_problem, omegas, G_iw, tails, tau, G_tau, stream=None):
+    h.check(lib().sox_iw_to_tau(h.ptr, ctypes.byref(p), _len(omegas), _ptr(omegas), _ptr(G_iw), _ptr(tails),
+                                _len(tau), _ptr(tau), _ptr(G_tau), _stream(stream)))
+
+
+def sox_tau_to_iw(h: Handle, p: sox_problem, T_w, F_tau, F_iw, stream=None):
+    n_w = int(T_w.shape[0])
+    h.check(lib().sox_tau_to_iw(h.ptr, ctypes.byref(p), n_w, _ptr(T_w), _ptr(F_tau), _ptr(F_iw), _stream(stream)))
+
+
+def sox_find_mu(h: Handle, p: sox_problem, omegas, target: float, F, Sigma_iw=None, Sigma_tau=None,
+                lo: float = -50.0, hi: float = 50.0, tol: float = 1e-13, max_iter: int = 200) -> float:
+    mu = ctypes.c_double(0.0)
+    h.check(lib().sox_find_mu(h.ptr, ctypes.byref(p), _len(omegas), _ptr(omegas), float(target), _ptr(F),
+                              _ptr(Sigma_iw), _ptr(Sigma_tau), float(lo), float(hi), float(tol), int(max_iter),
+                              ctypes.byref(mu)))
+    return mu.value
+
+
+def sox_density_matrix(h: Handle, p: sox_problem, G_tau, gamma, stream=None):
+    h.check(lib().sox_density_matrix(h.ptr, ctypes.byref(p), _ptr(G_tau), _ptr(gamma), _stream(stream)))
+
+
+def sox_sigma_hf(h: Handle, p: sox_problem, X, V, gamma, Sigma_hf, H0=None, F=None, stream=None):
+    h.check(lib().sox_sigma_hf(h.ptr, ctypes.byref(p), _ptr(X), _ptr(V), _ptr(gamma), _ptr(H0), _ptr(Sigma_hf),
+                               _ptr(F), _stream(stream)))
+
+
+def sox_gm_energies(h: Handle, p: sox_problem, H0, Sigma_hf, gamma, Sigma_tau, G_tau, w, E, stream=None):
+    h.check(lib().sox_gm_energies(h.ptr, ctypes.byref(p), _ptr(H0), _ptr(Sigma_hf), _ptr(gamma), _ptr(Sigma_tau),
+                                  _ptr(G_tau), _ptr(w), _ptr(E), _stream(stream)))
+
+
+def sox_mix_green(h: Handle, G, G_new, a: float, stream=None) -> float:
+    change = ctypes.c_double(0.0)
+    h.check(lib().sox_mix_green(h.ptr, int(G.numel()), float(a), _ptr(G), _ptr(G_new), ctypes.byref(change),
+                                _stream(stream)))
+    return change.value
+

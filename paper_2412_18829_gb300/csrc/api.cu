@@ -11,6 +11,7 @@
 #include "internal.h"
 #include "ctc.h"
 #include "kpoint.h"
+#include "scloop.h"
 #include "tc_path.h"
 
 using sox::Arena;
@@ -1114,3 +1115,269 @@ int sox_plan_destroy(sox_plan plan) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// The self-consistent loop around Sigma for molecules (Sec. II A)
+// ----------------------------------------------------------------------------
+namespace {
+Status loop_problem(const sox_problem *p) {
+  SOX_TRY(validate(p));
+  if (p->dtype != SOX_REAL64) return {SOX_ERR_UNSUPPORTED, "the loop steps take real molecular data"};
+  return Status::ok();
+}
+}  // namespace
+
+int sox_dyson(sox_handle h, const sox_problem *p, int n_w, const double *omegas, double mu, const double *F,
+              const double *Sigma_iw, double *G_iw, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (n_w < 1 || n_w > (1 << 20)) return {SOX_ERR_SHAPE, "n_w out of range [1, 2^20]"};
+    if (!omegas || !F || !G_iw) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, stream);
+    Staged sw, sF, sS, oG;
+    SOX_TRY(call.input(omegas, (size_t)n_w, &sw));
+    SOX_TRY(call.input(F, S * nn, &sF));
+    SOX_TRY(call.input(Sigma_iw, 2 * S * n_w * nn, &sS));
+    SOX_TRY(call.output(G_iw, 2 * S * n_w * nn, &oG));
+    Arena ar;
+    SOX_TRY(call.begin(sox::dyson_bytes(p->n, n_w, p->n_spin), &ar));
+    SOX_TRY(sox::dyson(h, p->n, n_w, p->n_spin, sw.in, mu, sF.in, sS.in, oG.out, ar, call.stream()));
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_green_tails(sox_handle h, const sox_problem *p, double mu, const double *F, const double *Sigma_tau,
+                    double *tails, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (!F || !tails) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, stream);
+    Staged sF, sS, oT;
+    SOX_TRY(call.input(F, S * nn, &sF));
+    SOX_TRY(call.input(Sigma_tau, S * p->n_tau * nn, &sS));
+    SOX_TRY(call.output(tails, 3 * S * nn, &oT));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "green_tails", call.stream());
+    sox::launch_green_tails(sF.in, mu, sS.in, p->n, p->n_tau, p->n_spin, oT.out, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_iw_to_tau(sox_handle h, const sox_problem *p, int n_w, const double *omegas, const double *G_iw,
+                  const double *tails, int n_t, const double *tau, double *G_tau, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (n_w < 1 || n_t < 1 || n_t > SOX_MAX_N_TAU) return {SOX_ERR_SHAPE, "n_w or n_t out of range"};
+    if (!omegas || !G_iw || !tails || !tau || !G_tau) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, stream);
+    Staged sw, sG, sT, st_, oG;
+    SOX_TRY(call.input(omegas, (size_t)n_w, &sw));
+    SOX_TRY(call.input(G_iw, 2 * S * n_w * nn, &sG));
+    SOX_TRY(call.input(tails, 3 * S * nn, &sT));
+    SOX_TRY(call.input(tau, (size_t)n_t, &st_));
+    SOX_TRY(call.output(G_tau, S * n_t * nn, &oG));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "iw_to_tau", call.stream());
+    sox::launch_iw_to_tau(sG.in, sw.in, n_w, sT.in, st_.in, n_t, p->n, p->n_spin, p->beta, oG.out, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_tau_to_iw(sox_handle h, const sox_problem *p, int n_w, const double *T_w, const double *F_tau, double *F_iw,
+                  void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (n_w < 1 || n_w > (1 << 20)) return {SOX_ERR_SHAPE, "n_w out of range [1, 2^20]"};
+    if (!T_w || !F_tau || !F_iw) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, stream);
+    Staged sT, sF, oF;
+    SOX_TRY(call.input(T_w, 2 * (size_t)n_w * p->n_tau, &sT));
+    SOX_TRY(call.input(F_tau, S * p->n_tau * nn, &sF));
+    SOX_TRY(call.output(F_iw, 2 * S * n_w * nn, &oF));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "tau_to_iw", call.stream());
+    sox::launch_tau_to_iw(sT.in, sF.in, n_w, p->n_tau, p->n, p->n_spin, oF.out, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_find_mu(sox_handle h, const sox_problem *p, int n_w, const double *omegas, double target, const double *F,
+                const double *Sigma_iw, const double *Sigma_tau, double lo, double hi, double tol, int max_iter,
+                double *mu) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (n_w < 1 || n_w > (1 << 20)) return {SOX_ERR_SHAPE, "n_w out of range [1, 2^20]"};
+    if (!omegas || !F || !mu) return {SOX_ERR_INVALID_ARG, "NULL pointer"};
+    if (!(hi > lo) || !(tol > 0.0) || max_iter < 1) return {SOX_ERR_INVALID_ARG, "need lo < hi, tol > 0, max_iter >= 1"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, nullptr);
+    Staged sw, sF, sSi, sSt;
+    SOX_TRY(call.input(omegas, (size_t)n_w, &sw));
+    SOX_TRY(call.input(F, S * nn, &sF));
+    SOX_TRY(call.input(Sigma_iw, 2 * S * n_w * nn, &sSi));
+    SOX_TRY(call.input(Sigma_tau, S * p->n_tau * nn, &sSt));
+    Arena ar;
+    const size_t extra = sox::aligned_bytes(2 * S * n_w * nn, 8) + sox::aligned_bytes(3 * S * nn, 8) + 4096;
+    SOX_TRY(call.begin(sox::dyson_bytes(p->n, n_w, p->n_spin) + extra, &ar));
+    cudaStream_t s = call.stream();
+    double *Giw = ar.take<double>(2 * S * n_w * nn), *tails = ar.take<double>(3 * S * nn);
+    double *count = ar.take<double>(1);
+    if (!count) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+    // bisection on the electron count sum_s Tr gamma^s(mu), which rises with mu (Sec. II A)
+    for (int it = 0; it < max_iter && hi - lo >= tol; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      Arena a2 = ar;
+      SOX_TRY(sox::dyson(h, p->n, n_w, p->n_spin, sw.in, mid, sF.in, sSi.in, Giw, a2, s));
+      sox::launch_green_tails(sF.in, mid, sSt.in, p->n, p->n_tau, p->n_spin, tails, s);
+      SOX_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(double), s));
+      sox::launch_trace_gamma(Giw, sw.in, n_w, tails, p->n, p->n_spin, p->beta, count, s);
+      h->launches += 3;
+      double c = 0.0;
+      SOX_CUDA_TRY(cudaMemcpyAsync(&c, count, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SOX_CUDA_TRY(cudaStreamSynchronize(s));
+      if (c < target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    *mu = 0.5 * (lo + hi);
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_sigma_hf(sox_handle h, const sox_problem *p, const double *X, const double *V, const double *gamma,
+                 const double *H0, double *Sigma_hf, double *F, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (!X || !V || !gamma || !Sigma_hf) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin, N = p->N;
+    Call call(h, stream);
+    if (F && !H0) return {SOX_ERR_INVALID_ARG, "F needs H0"};
+    Staged sX, sV, sg, sH, oS, oF;
+    SOX_TRY(call.input(X, N * p->n, &sX));
+    SOX_TRY(call.input(V, N * N, &sV));
+    SOX_TRY(call.input(gamma, S * nn, &sg));
+    SOX_TRY(call.input(H0, nn, &sH));
+    SOX_TRY(call.output(Sigma_hf, S * nn, &oS));
+    SOX_TRY(call.output(F, S * nn, &oF));
+    Arena ar;
+    SOX_TRY(call.begin(sox::aligned_bytes(N + S * N * p->n, 8) + sox::aligned_bytes(S * N * N, 8), &ar));
+    double *d = ar.take<double>(N + S * N * p->n), *Gam = ar.take<double>(S * N * N);
+    if (!Gam) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+    sox::ProfScope ps(h, "sigma_hf", call.stream(), 2 + 2 * p->n_spin);
+    sox::launch_sigma_hf(sX.in, sV.in, sg.in, p->N, p->n, p->n_spin, d, Gam, oS.out, call.stream());
+    for (int sp = 0; oF.out && sp < p->n_spin; ++sp)   // F[s] = H0 + Sigma_HF[s]
+      sox::launch_add_f64(sH.in, oS.out + sp * nn, oF.out + sp * nn, (long long)nn, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_density_matrix(sox_handle h, const sox_problem *p, const double *G_tau, double *gamma, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (!G_tau || !gamma) return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin;
+    Call call(h, stream);
+    Staged sG, og;
+    SOX_TRY(call.input(G_tau, S * p->n_tau * nn, &sG));
+    SOX_TRY(call.output(gamma, S * nn, &og));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "density_matrix", call.stream());
+    sox::launch_gamma_from_tau(sG.in, p->n, p->n_tau, p->n_spin, og.out, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_gm_energies(sox_handle h, const sox_problem *p, const double *H0, const double *Sigma_hf, const double *gamma,
+                    const double *Sigma_tau, const double *G_tau, const double *w, double *E, void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    SOX_TRY(loop_problem(p));
+    if (!H0 || !Sigma_hf || !gamma || !Sigma_tau || !G_tau || !w || !E)
+      return {SOX_ERR_INVALID_ARG, "NULL tensor pointer"};
+    SOX_TRY(bind_device(h));
+    const size_t nn = (size_t)p->n * p->n, S = p->n_spin, T = p->n_tau;
+    Call call(h, stream);
+    Staged sH, sS, sg, sSt, sG, sw, oE;
+    SOX_TRY(call.input(H0, nn, &sH));
+    SOX_TRY(call.input(Sigma_hf, S * nn, &sS));
+    SOX_TRY(call.input(gamma, S * nn, &sg));
+    SOX_TRY(call.input(Sigma_tau, S * T * nn, &sSt));
+    SOX_TRY(call.input(G_tau, S * T * nn, &sG));
+    SOX_TRY(call.input(w, T, &sw));
+    SOX_TRY(call.output(E, 2, &oE));
+    Arena ar;
+    SOX_TRY(call.begin(0, &ar));
+    sox::ProfScope ps(h, "gm_energies", call.stream());
+    SOX_CUDA_TRY(cudaMemsetAsync(oE.out, 0, 2 * sizeof(double), call.stream()));
+    sox::launch_energies(sH.in, sS.in, sg.in, sSt.in, sG.in, sw.in, p->n, p->n_tau, p->n_spin, oE.out, call.stream());
+    SOX_CUDA_TRY(cudaGetLastError());
+    return call.end();
+  }();
+  return finish(h, st);
+}
+
+int sox_mix_green(sox_handle h, long long count, double a, double *G, const double *G_new, double *change,
+                  void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  Status st = [&]() -> Status {
+    if (count < 0 || !G || !G_new || !change) return {SOX_ERR_INVALID_ARG, "bad arguments"};
+    if (!(a >= 0.0 && a <= 1.0)) return {SOX_ERR_INVALID_ARG, "mixing weight must lie in [0, 1]"};
+    SOX_TRY(bind_device(h));
+    bool dG = false, dN = false;
+    SOX_TRY(is_device_ptr(G, &dG));
+    SOX_TRY(is_device_ptr(G_new, &dN));
+    if (!dG || !dN) return {SOX_ERR_INVALID_ARG, "G and G_new must be device memory"};
+    Call call(h, nullptr);
+    Arena ar;
+    SOX_TRY(call.begin(64, &ar));
+    unsigned long long *chg = ar.take<unsigned long long>(1);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SOX_CUDA_TRY(cudaMemsetAsync(chg, 0, sizeof(unsigned long long), s));
+    sox::ProfScope ps(h, "mix_green", s);
+    sox::launch_mix(G, G_new, count, a, chg, s);
+    unsigned long long bits = 0;
+    SOX_CUDA_TRY(cudaMemcpyAsync(&bits, chg, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    SOX_CUDA_TRY(cudaStreamSynchronize(s));
+    double c;
+    std::memcpy(&c, &bits, sizeof(c));
+    *change = c;
+    return Status::ok();
+  }();
+  return finish(h, st);
+}
+

@@ -201,6 +201,39 @@ def bosonic_transforms(tau: np.ndarray, beta: float, M: int, n_gl: int = 512):
     return om, np.ascontiguousarray(T_fwd), np.ascontiguousarray(T_inv)
 
 
+def fermionic_transform(tau: np.ndarray, beta: float, n_max: int, n_gl: int = 16):
+    """Caller-side tau -> i w transform for fermionic functions on the grid.
+
+    w_m = (2m+1) pi / beta, m = -n_max .. n_max-1.  T_w[m][j] = int_0^beta e^{i w_m s} L_j(s) ds
+    with L_j the cardinal polynomial of the Chebyshev-Lobatto nodes (barycentric form),
+    integrated by composite n_gl-point Gauss-Legendre with at least two panels per period of
+    the highest frequency.  An input of the loop's frequency transform (the paper takes its
+    grids and transforms from sparse-ir), not self-energy arithmetic.  Returns (w, T_w)."""
+    n = tau.size
+    m = np.arange(-n_max, n_max)
+    om = (2 * m + 1) * np.pi / beta
+    n_pan = max(8, int(np.ceil(np.abs(om).max() * beta / np.pi)) + 1)
+    x, wg = np.polynomial.legendre.leggauss(n_gl)
+    edges = np.linspace(0.0, beta, n_pan + 1)
+    half = 0.5 * np.diff(edges)
+    s = (edges[:-1, None] + half[:, None] * (x[None, :] + 1.0)).ravel()
+    ws = (half[:, None] * wg[None, :]).ravel()
+    bw = np.array([(-1.0) ** j for j in range(n)])
+    bw[0] *= 0.5
+    bw[-1] *= 0.5
+    d = s[:, None] - tau[None, :]
+    exact = np.abs(d) < 1e-300
+    d = np.where(exact, 1.0, d)
+    ratio = bw[None, :] / d
+    L = ratio / ratio.sum(axis=1, keepdims=True)
+    rows = exact.any(axis=1)
+    L[rows] = exact[rows].astype(float)
+    T_w = np.empty((om.size, n), complex)
+    for a in range(0, om.size, 64):
+        T_w[a:a + 64] = (np.exp(1j * om[a:a + 64, None] * s[None, :]) * ws[None, :]) @ L
+    return om, np.ascontiguousarray(T_w)
+
+
 def c4_instance(i: int) -> Workload:
     """Instance i of the uneven batch (n from the batch-size stream, N = 6n, 120 tau)."""
     n = int(batch_c4_sizes()[i])
