@@ -13,7 +13,7 @@
 // B_v and C_v are never stored.  One fused kernel (k_adj_bc) recomputes them per
 // 128 x 128 (P, R) tile in TMEM -- the forward's TMA / MMA pipeline -- and its epilogue
 // forms Bbar_v and Cbar_v from E held in registers, writes them once as FP16 pairs
-// [tau][v][P][R] and accumulates Ebar.  The four reverse contractions then read those
+// [tau][v][R][P] (coalesced: a warp's lanes hold consecutive P) and accumulates Ebar.  The four reverse contractions then read those
 // pairs in place: over R as K-major operands and over P as MN-major ones (gemm_mn.cu),
 // so no transposed copy and no FP32 round trip of the n N^2 tensors exists.  Every split
 // operand carries one power-of-two scale per tensor (per tau chunk), which is what lets
@@ -84,12 +84,12 @@ __global__ void k_fill(float *p, int count, float v) {
 //        Abar, GRbar, GWtbar, U2bar, U1bar (the last completed once Abar's scale is known),
 //        cg[b] = c_b g, em[b] = c_b / (sA sR sW sU)
 struct AdjScalars {
-  float mx[4];    // E, Abar maxima (atomicMax targets), spare
-  float sc[8];    // scales: GR, GWt, Gm, U, Abar, spare
-  float f[8];
+  float mx[8];    // atomicMax targets: E, Abar, mixed tensor, X, G(-tau), GR, GWt, Ebar
+  float sc[8];    // scales: GR, GWt, G(-tau), U, Abar, X, Ebar
+  float f[8];     // output factors of the contractions
 };
-constexpr int kFacG = 0, kFacAbar = 1, kFacGRbar = 2, kFacGWtbar = 3, kFacU2bar = 4, kFacU1bar = 5;
-constexpr int kScGR = 0, kScGW = 1, kScGm = 2, kScU = 3, kScAbar = 4;
+constexpr int kFacG = 0, kFacAbar = 1, kFacGRbar = 2, kFacGWtbar = 3, kFacU2bar = 4, kFacU1bar = 5, kFacEX = 6;
+constexpr int kScGR = 0, kScGW = 1, kScGm = 2, kScU = 3, kScAbar = 4, kScX = 5, kScEbar = 6;
 
 __device__ __forceinline__ float pow2_floor(double x) {
   // largest power of two <= x (x > 0), clamped to normal FP32
@@ -127,26 +127,31 @@ __global__ void k_u1bar_factor(AdjScalars *sc) {
   sc->f[kFacU1bar] = (float)(1.0 / ((double)sc->sc[kScAbar] * (double)sc->sc[kScGm]));
 }
 
+__global__ void k_ex_factor(AdjScalars *sc) {
+  sc->f[kFacEX] = (float)(1.0 / ((double)sc->sc[kScEbar] * (double)sc->sc[kScX]));
+}
+
 // ============================================================================
 // Fused producer: for every (tau b, 128 x 128 (P, R) tile), over v,
 //   B~_v = A~_v GR~^T, C~_v = GWt~ U2~_v^T in TMEM (double-buffered), and in the epilogue
-//   Bbar_v = cg_b E o C~_v, Cbar_v = cg_b E o B~_v -> FP16 pairs [b][v][P][R],
+//   Bbar_v = cg_b E o C~_v, Cbar_v = cg_b E o B~_v -> FP16 pairs [b][v][R][P],
 //   Ebar  += B~_v o C~_v (registers), written em_b * sum at the end of the tile.
-// Warp 0: TMA, warp 1: MMA (one elected thread), warps 4-15: epilogue (lane quarter
-// warp % 4, column group (warp - 4) / 4).
+// Warp 0: TMA, warp 1: MMA (one elected thread), warps 4-11: pair writers, warps 12-19:
+// Ebar accumulators (lane quarter warp % 4, column half by warpgroup).
 // ============================================================================
 constexpr int kT = 128, kC = 64;
 constexpr int kTileB = kT * kC * 2;            // 16 KB: one 64-wide chunk of 128 rows, hi or lo
 constexpr int kStageB = 4 * kTileB;
 constexpr int kSt = 3;
-// 16 warps: warpgroup 0 = TMA warp, MMA warp and two idle warps; warpgroups 1-3 = the
-// epilogue, columns [0, 48), [48, 96), [96, 128) of the tile.  Launched at 128 registers a
-// thread (512 x 128 = the SM's 65536); warpgroup 0 gives registers back (kRegCtl) and the
-// epilogue takes them (kRegEpi): 128 x kRegCtl + 384 x kRegEpi = 65536, the launch's own
-// total (checked on the host against the compiled register count before the first launch).
-constexpr int kProdThreads = 512, kProdEpi = 384;
-constexpr int kRegLaunch = 128, kRegCtl = 56, kRegEpi = 152;
-static_assert(128 * kRegCtl + 384 * kRegEpi == kProdThreads * kRegLaunch, "register split must equal the launch total");
+// 20 warps: warpgroup 0 = TMA warp, MMA warp and two idle warps; warpgroups 1-2 write the
+// pairs of columns [0, 64) and [64, 128) of the tile (E held in registers), warpgroups 3-4
+// accumulate Ebar over the same halves.  Launched at 96 registers a thread (640 x 96 of the
+// SM's 65536); warpgroup 0 gives registers back (kRegCtl) and the epilogue takes them
+// (kRegEpi): 128 x kRegCtl + 512 x kRegEpi <= 640 x 96, the launch's own total (checked
+// on the host against the compiled register count before the first launch).
+constexpr int kProdThreads = 640, kProdEpi = 512;
+constexpr int kRegLaunch = 96, kRegCtl = 56, kRegEpi = 104;
+static_assert(128 * kRegCtl + 512 * kRegEpi <= kProdThreads * kRegLaunch, "register split above the launch total");
 constexpr uint32_t kIdesc = tc::idesc_f16_f32(kT, kT);
 
 struct PBars {
@@ -168,8 +173,8 @@ struct AdjBcArgs {
   long long ldE = 0, sE = 0;
   const float *cg = nullptr, *em = nullptr;   // [b]
   float *Ebar = nullptr;          // [b][N][ldE]
-  __half *Bh = nullptr, *Bl = nullptr, *Ch = nullptr, *Cl = nullptr;   // [b][v][N][Rp]
-  long long Rp = 0;
+  __half *Bh = nullptr, *Bl = nullptr, *Ch = nullptr, *Cl = nullptr;   // [b][v][R][P], Rp x Rp
+  long long Rp = 0;   // N rounded up to 128: rows R and row length P of the pairs
 };
 
 __device__ __forceinline__ long long wind_down(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
@@ -194,8 +199,29 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-// Epilogue of k_adj_bc for the NC columns [col0, col0 + NC) of every tile (lane quarter q).
+// Columns c .. c+7 of E o y for this lane's row as FP16 pairs: lanes 2i and 2i+1 (rows P, P+1)
+// swap halves so the even lane stores rows (P, P+1) of column c+2k and the odd lane those of
+// column c+2k+1, each as one 4-byte word at dh / dl + column * Rp (P contiguous).
 template <int NC>
+__device__ __forceinline__ void store_pairs(const float (&e)[NC], int c, const float (&y)[8], __half *dh, __half *dl,
+                                            long long Rp, bool even) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __half h0, l0, h1, l1;
+    tc::split_f16(e[c + 2 * k] * y[2 * k], h0, l0);
+    tc::split_f16(e[c + 2 * k + 1] * y[2 * k + 1], h1, l1);
+    const uint32_t mh = pack2(h0, h1), ml = pack2(l0, l1);
+    const uint32_t oh = __shfl_xor_sync(0xffffffffu, mh, 1), ol = __shfl_xor_sync(0xffffffffu, ml, 1);
+    const long long col = (long long)(c + 2 * k + (even ? 0 : 1)) * Rp;
+    *reinterpret_cast<uint32_t *>(dh + col) = even ? __byte_perm(mh, oh, 0x5410) : __byte_perm(oh, mh, 0x7632);
+    *reinterpret_cast<uint32_t *>(dl + col) = even ? __byte_perm(ml, ol, 0x5410) : __byte_perm(ol, ml, 0x7632);
+  }
+}
+
+// Epilogue of k_adj_bc for the NC columns [col0, col0 + NC) of every tile (lane quarter q):
+// kWrite threads hold E and write the pairs, the others accumulate Ebar.  Both wait for every
+// v's accumulators and hand them back.
+template <int NC, bool kWrite>
 __device__ __forceinline__ void adj_epilogue(PBars *bar, uint32_t tmem, const AdjBcArgs &a, int tP, long long total,
                                              volatile int *abort, int q, int lane, int col0) {
   const int tiles_per_b = tP * tP;
@@ -207,17 +233,23 @@ __device__ __forceinline__ void adj_epilogue(PBars *bar, uint32_t tmem, const Ad
     const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
     const int P = P0 + row, Rh = R0 + col0;
     const bool prow = P < a.N;
-    const float cgb = a.cg[b], emb = a.em[b];
-    float e[NC], eb[NC];
-    const float *Er = a.E + (long long)b * a.sE + (long long)(prow ? P : 0) * a.ldE;
+    float x[NC];   // kWrite: E * c_b g; else: the Ebar accumulator
+    if (kWrite) {
+      const float cgb = a.cg[b];
+      const float *Er = a.E + (long long)b * a.sE + (long long)(prow ? P : 0) * a.ldE;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      e[j] = (prow && Rh + j < a.N) ? Er[Rh + j] * cgb : 0.f;
-      eb[j] = 0.f;
+      for (int j = 0; j < NC; ++j) x[j] = (prow && Rh + j < a.N) ? Er[Rh + j] * cgb : 0.f;
+    } else {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) x[j] = 0.f;
     }
-    const long long vstride = (long long)a.N * a.Rp;
+    // pairs [b][v][R][P] (pitch Rp for both): lanes hold 32 consecutive P, and lane pairs swap
+    // halves so each writes 4 bytes of two consecutive P of one column R
+    const long long vstride = a.Rp * a.Rp;
     const int nv = a.v1 - a.v0;
-    const long long obase = ((long long)b * nv * a.N + (prow ? P : 0)) * a.Rp + Rh;
+    const bool even = (lane & 1) == 0;
+    const int Pe = P0 + q * 32 + (lane & ~1);   // the even row of this lane's pair
+    const long long obase = (long long)b * nv * vstride + (long long)Rh * a.Rp + Pe;
     bool ok = true;
     for (int v = a.v0; v < a.v1; ++v, ++acc_it) {
       const int buf = (int)(acc_it & 1);
@@ -233,43 +265,24 @@ __device__ __forceinline__ void adj_epilogue(PBars *bar, uint32_t tmem, const Ad
         tc::tmem_ld_32x32b_x8(base + c, bv);
         tc::tmem_ld_32x32b_x8(base + 128 + c, cv);
         tc::tmem_ld_wait();
-        uint32_t ph[4], pl[4];
+        if (kWrite) {   // Bbar = E o C, then Cbar = E o B
+          store_pairs<NC>(x, c, cv, a.Bh + o, a.Bl + o, a.Rp, even);
+          store_pairs<NC>(x, c, bv, a.Ch + o, a.Cl + o, a.Rp, even);
+        } else {
 #pragma unroll
-        for (int jj = 0; jj < 8; jj += 2) {   // Bbar = E o C
-          __half h0, l0, h1, l1;
-          tc::split_f16(e[c + jj] * cv[jj], h0, l0);
-          tc::split_f16(e[c + jj + 1] * cv[jj + 1], h1, l1);
-          ph[jj / 2] = pack2(h0, h1);
-          pl[jj / 2] = pack2(l0, l1);
+          for (int jj = 0; jj < 8; ++jj) x[c + jj] = fmaf(bv[jj], cv[jj], x[c + jj]);
         }
-        if (prow) {
-          *reinterpret_cast<uint4 *>(a.Bh + o + c) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-          *reinterpret_cast<uint4 *>(a.Bl + o + c) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; jj += 2) {   // Cbar = E o B
-          __half h0, l0, h1, l1;
-          tc::split_f16(e[c + jj] * bv[jj], h0, l0);
-          tc::split_f16(e[c + jj + 1] * bv[jj + 1], h1, l1);
-          ph[jj / 2] = pack2(h0, h1);
-          pl[jj / 2] = pack2(l0, l1);
-        }
-        if (prow) {
-          *reinterpret_cast<uint4 *>(a.Ch + o + c) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-          *reinterpret_cast<uint4 *>(a.Cl + o + c) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) eb[c + jj] = fmaf(bv[jj], cv[jj], eb[c + jj]);
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&bar->acc_empty[buf]);
     }
     if (!ok) break;
-    if (prow) {
+    if (!kWrite && prow) {
+      const float emb = a.em[b];
       float *Eo = a.Ebar + (long long)b * a.sE + (long long)P * a.ldE;
 #pragma unroll
       for (int j = 0; j < NC; ++j)
-        if (Rh + j < a.N) Eo[Rh + j] = eb[j] * emb;
+        if (Rh + j < a.N) Eo[Rh + j] = x[j] * emb;
     }
   }
 }
@@ -317,11 +330,11 @@ __global__ void __launch_bounds__(kProdThreads, 1)
   volatile int *abort = &bar->abort;
   if (warp >= 4) {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegEpi));
-    const int grp = (warp - 4) >> 2;
+    const int grp = (warp - 4) >> 2;   // 0, 1: pair writers; 2, 3: Ebar
     if (grp < 2)
-      adj_epilogue<48>(bar, tmem, a, tP, total, abort, warp & 3, lane, grp * 48);
+      adj_epilogue<64, true>(bar, tmem, a, tP, total, abort, warp & 3, lane, grp * 64);
     else
-      adj_epilogue<32>(bar, tmem, a, tP, total, abort, warp & 3, lane, 96);
+      adj_epilogue<64, false>(bar, tmem, a, tP, total, abort, warp & 3, lane, (grp - 2) * 64);
   } else {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegCtl));
   if (warp == 0) {
@@ -432,7 +445,7 @@ struct AdjGeom {
   int NR;           // P / R rows of the forward operands (>= 128)
   int RG;           // rows of G(-tau)^T per tau (>= 128)
   long long Rp;     // row pitch of Bbar / Cbar (N rounded up to 128)
-  long long nn, np4, nnp, ldN, Nn;
+  long long nn, np4, np8, nnp, ldN, Nn;
   long long abar_pitch;   // per-v pitch of the Abar split [(P, q)] (N n rounded up to 8)
   int Bc;           // tau points per chunk
 };
@@ -444,7 +457,7 @@ size_t fixed_bytes(const AdjGeom &g) {
   b += 2 * aligned_bytes((size_t)g.NR * g.Kp * g.Kp, 2);                          // U1 split
   b += 2 * aligned_bytes((size_t)g.n * g.NR * g.Kp, 2);                           // U2 split
   b += aligned_bytes((size_t)N * g.n * g.np4, 4) + aligned_bytes((size_t)g.n * N * g.np4, 4);   // U1bar, U2bar
-  b += aligned_bytes((size_t)g.Nn, 8) + rsplit_bytes(1, N, g.n) + rsplit_bytes(1, g.n, N);      // Xbar, Xr, XT
+  b += aligned_bytes((size_t)g.Nn, 8) + rsplit_bytes(1, N, g.n) + 2 * aligned_bytes((size_t)N * g.np8, 2);   // Xbar, X
   b += aligned_bytes(sizeof(AdjScalars), 4) + 2 * aligned_bytes(8192, 4) + (1 << 16);
   return b;
 }
@@ -456,10 +469,10 @@ size_t per_tau_bytes(const AdjGeom &g) {
   b += 4 * aligned_bytes((size_t)g.NR * g.Kp, 2);                                 // GR~, GWt~
   b += 2 * aligned_bytes((size_t)g.RG * g.Kp, 2) + 2 * aligned_bytes((size_t)n * g.Kp, 2);   // G(-tau) splits
   b += 2 * aligned_bytes((size_t)n * g.NR * g.Kp, 2);                             // A~
-  b += 4 * aligned_bytes((size_t)n * N * g.Rp, 2);                                // Bbar, Cbar pairs
+  b += 4 * aligned_bytes((size_t)n * g.Rp * g.Rp, 2);                             // Bbar, Cbar pairs [v][R][P]
   b += aligned_bytes((size_t)n * N * g.np4, 4) + 2 * aligned_bytes((size_t)n * g.abar_pitch, 2);   // Abar, split
   b += 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);   // GRbar, GWtbar
-  b += 2 * rsplit_bytes(1, N, N) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
+  b += 2 * aligned_bytes((size_t)N * g.ldN, 2) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
   b += 3 * 4096;                                                                  // os, cg, em
   return b;
 }
@@ -479,6 +492,7 @@ AdjGeom adj_geom(sox_handle h, int n, int N, int T, int S) {
   g.Rp = rup(N, 128);
   g.nn = (long long)n * n;
   g.np4 = rup4(n);
+  g.np8 = (n + 7) & ~7LL;
   g.nnp = rup4(g.nn);
   g.ldN = rup4(N);
   g.Nn = (long long)N * n;
@@ -512,7 +526,8 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   __half *U2h = ar.take<__half>((size_t)n * NR * Kp), *U2l = ar.take<__half>((size_t)n * NR * Kp);
   float *U1bar = ar.take<float>((size_t)N * n * g.np4), *U2bar = ar.take<float>((size_t)n * N * g.np4);
   double *Xbar = ar.take<double>((size_t)Nn);
-  CSplit Xr = rsplit_take(ar, 1, N, n), XT = rsplit_take(ar, 1, n, N);   // X rows R (K = t); rows t (K = R)
+  CSplit Xr = rsplit_take(ar, 1, N, n);   // X rows R, K = t (E = M1 X^T)
+  __half *Xh = ar.take<__half>((size_t)N * g.np8), *Xl = ar.take<__half>((size_t)N * g.np8);   // X pairs [R][t]
   AdjScalars *sc = ar.take<AdjScalars>(1);
   float *cgb = ar.take<float>(2048), *emb = ar.take<float>(2048);
   if (!emb) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
@@ -537,7 +552,8 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   launch_split_tensor(Um, true, g.nnp, N, n, n, 1, n, Kp, (long long)NR * Kp, 1.f, nullptr, &sc->sc[kScU], U2h, U2l,
                       nullptr, s);
   rsplit(X, false, 0, n, 0, 0, 1, 1, N, n, Xr, s);
-  rsplit(X, false, 0, 1, 0, 0, n, 1, n, N, XT, s);
+  launch_absmax(X, false, n, N, 0, 1, 1, n, &sc->mx[3], s);
+  launch_split_tensor(X, false, n, N, 0, 1, 1, n, g.np8, 0, 1.f, &sc->mx[3], nullptr, Xh, Xl, &sc->sc[kScX], s);
   launches += 10;
 
   // ---- per tau-chunk buffers
@@ -551,13 +567,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   __half *GmTh = at.take<__half>(Bs * RG * Kp), *GmTl = at.take<__half>(Bs * RG * Kp);   // rows v, K = s
   __half *Gmh = at.take<__half>(Bs * n * Kp), *Gml = at.take<__half>(Bs * n * Kp);       // rows s, K = v
   __half *Ah = at.take<__half>(Bs * n * NR * Kp), *Al = at.take<__half>(Bs * n * NR * Kp);
-  __half *Bbh = at.take<__half>(Bs * n * N * g.Rp), *Bbl = at.take<__half>(Bs * n * N * g.Rp);
-  __half *Cbh = at.take<__half>(Bs * n * N * g.Rp), *Cbl = at.take<__half>(Bs * n * N * g.Rp);
+  __half *Bbh = at.take<__half>(Bs * n * g.Rp * g.Rp), *Bbl = at.take<__half>(Bs * n * g.Rp * g.Rp);
+  __half *Cbh = at.take<__half>(Bs * n * g.Rp * g.Rp), *Cbl = at.take<__half>(Bs * n * g.Rp * g.Rp);
   float *Abar = at.take<float>(Bs * n * N * g.np4);
   __half *Abh = at.take<__half>(Bs * n * g.abar_pitch), *Abl = at.take<__half>(Bs * n * g.abar_pitch);
   float *GRbf = at.take<float>(Bs * N * g.np4), *GWbf = at.take<float>(Bs * N * g.np4);
   double *GRbar = at.take<double>(Bs * Nn), *GWtbar = at.take<double>(Bs * Nn);
-  CSplit Ebs = rsplit_take(at, Bc, N, N), EbTs = rsplit_take(at, Bc, N, N);
+  __half *Ebh = at.take<__half>(Bs * N * g.ldN), *Ebl = at.take<__half>(Bs * N * g.ldN);   // Ebar pairs
   float *m1f = at.take<float>(Bs * N * g.np4), *m2f = at.take<float>(Bs * N * g.np4);
   double *m1 = at.take<double>(Bs * Nn), *m2 = at.take<double>(Bs * Nn);
   float *osv = at.take<float>(1024);
@@ -603,28 +619,29 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   const int nv = v_hi - v_lo;
   const int Kpv = rup(std::max(nv, 1), 64);
   const uint64_t zBC = (uint64_t)Bc * std::max(nv, 1);   // (tau, local v) slices of Bbar / Cbar
-  // (i) Abar[b][v][P][q] = sum_R Bbar[b][v][P][R] GR~[b][R][q]: A K-major, B MN-major
-  CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5];
-  if (!make_tmap_f16_3d_rs(&mi[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
-      !make_tmap_f16_3d_rs(&mi[1], Bbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+  // (i) Abar[b][v][P][q] = sum_R Bbar[b][v][R][P] GR~[b][R][q]: A MN-major, B MN-major
+  CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5], mm1[5], mm2[5];
+  const uint64_t sPR = (uint64_t)g.Rp * g.Rp;   // one (tau, v) slice of the pairs: rows R, P contiguous
+  if (!make_tmap_f16_3d_rs(&mi[0], Bbh, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mi[1], Bbl, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mi[2], GRh, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mi[3], GRl, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f32_store3d(&mi[4], Abar, n, N, zBC, g.np4, (uint64_t)N * g.np4, &err) ||
-      // (ii) GRbar[b][R][q] = sum_{v,P} Bbar[b][v][P][R] A~[b][v][P][q]: both MN-major
-      !make_tmap_f16_3d_rs(&mii[0], Bbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mii[1], Bbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      // (ii) GRbar[b][R][q] = sum_{v,P} Bbar[b][v][R][P] A~[b][v][P][q]: A K-major, B MN-major
+      !make_tmap_f16_3d_rs(&mii[0], Bbh, N, g.Rp, N, zBC, sPR, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mii[1], Bbl, N, g.Rp, N, zBC, sPR, 64, 128, &err) ||
       !make_tmap_f16_3d_rs(&mii[2], Ah, n, Kp, N, (uint64_t)Bc * n, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mii[3], Al, n, Kp, N, (uint64_t)Bc * n, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f32_store3d(&mii[4], GRbf, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
-      // (iii) GWtbar[b][P][w] = sum_{v,R} Cbar[b][v][P][R] U2~[v][R][w]: A K-major, B MN-major
-      !make_tmap_f16_3d_rs(&miii[0], Cbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
-      !make_tmap_f16_3d_rs(&miii[1], Cbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 128, &err) ||
+      // (iii) GWtbar[b][P][w] = sum_{v,R} Cbar[b][v][R][P] U2~[v][R][w]: A MN-major, B MN-major
+      !make_tmap_f16_3d_rs(&miii[0], Cbh, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&miii[1], Cbl, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&miii[2], U2h, n, Kp, N, n, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&miii[3], U2l, n, Kp, N, n, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f32_store3d(&miii[4], GWbf, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
-      // (iv) U2bar[v][R][w] += sum_{b,P} Cbar[b][v][P][R] GWt~[b][P][w]: both MN-major
-      !make_tmap_f16_3d_rs(&miv[0], Cbh, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&miv[1], Cbl, N, g.Rp, N, zBC, (uint64_t)N * g.Rp, 64, 64, &err) ||
+      // (iv) U2bar[v][R][w] += sum_{b,P} Cbar[b][v][R][P] GWt~[b][P][w]: A K-major, B MN-major
+      !make_tmap_f16_3d_rs(&miv[0], Cbh, N, g.Rp, N, zBC, sPR, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&miv[1], Cbl, N, g.Rp, N, zBC, sPR, 64, 128, &err) ||
       !make_tmap_f16_3d_rs(&miv[2], GWh, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&miv[3], GWl, n, Kp, N, Bc, (uint64_t)NR * Kp, 64, 64, &err) ||
       !make_tmap_f32_store3d(&miv[4], U2bar + (size_t)v_lo * N * g.np4, n, N, std::max(nv, 1), g.np4,
@@ -636,8 +653,20 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
                            (uint64_t)std::max(nv, 1) * g.abar_pitch, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mv[2], Gmh, std::max(nv, 1), Kpv, n, Bc, (uint64_t)n * Kpv, 64, 128, &err) ||
       !make_tmap_f16_3d_rs(&mv[3], Gml, std::max(nv, 1), Kpv, n, Bc, (uint64_t)n * Kpv, 64, 128, &err) ||
-      !make_tmap_f32_store3d(&mv[4], U1bar, n, Nn, 1, g.np4, (uint64_t)Nn * g.np4, &err))
+      !make_tmap_f32_store3d(&mv[4], U1bar, n, Nn, 1, g.np4, (uint64_t)Nn * g.np4, &err) ||
+      // m1[b][P][t] = sum_R Ebar[b][P][R] X[R][t] (A K-major), m2[b][R][t] = sum_P Ebar[b][P][R] X[P][t]
+      // (A MN-major); X pairs [R][t] MN-major in both
+      !make_tmap_f16_3d_rs(&mm1[0], Ebh, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mm1[1], Ebl, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mm1[2], Xh, n, g.np8, N, 1, (uint64_t)N * g.np8, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mm1[3], Xl, n, g.np8, N, 1, (uint64_t)N * g.np8, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&mm1[4], m1f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
+      !make_tmap_f16_3d_rs(&mm2[0], Ebh, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mm2[1], Ebl, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 64, &err) ||
+      !make_tmap_f32_store3d(&mm2[4], m2f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err))
     return {SOX_ERR_CUDA, "adjoint maps: " + err};
+  mm2[2] = mm1[2];
+  mm2[3] = mm1[3];
   const int kcN = (N + 63) / 64;
   const int sms = h->sm_count;
   const long long limit = h->spin_limit;
@@ -664,10 +693,9 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       rsplit(M1, false, Nn, n, 0, 0, 1, bc, N, n, M1s, s);
       SOX_TRY(cgemm_tc(h, M1s, Xr, bc, nullptr, nullptr, 1.f, E, g.ldN, (long long)N * g.ldN, s));
       // per-chunk maxima and scales
-      SOX_CUDA_TRY(cudaMemsetAsync(sc->mx, 0, sizeof(sc->mx[0]) * 2, s));
-      SOX_CUDA_TRY(cudaMemsetAsync(&sc->mx[3], 0, sizeof(float), s));
-      float *mxGR = &sc->f[6], *mxGW = &sc->f[7], *mxGm = &sc->mx[3];
-      SOX_CUDA_TRY(cudaMemsetAsync(&sc->f[6], 0, 2 * sizeof(float), s));
+      SOX_CUDA_TRY(cudaMemsetAsync(sc->mx, 0, sizeof(sc->mx[0]) * 2, s));       // E, Abar
+      SOX_CUDA_TRY(cudaMemsetAsync(&sc->mx[4], 0, sizeof(sc->mx[0]) * 4, s));   // G(-tau), GR, GWt, Ebar
+      float *mxGR = &sc->mx[5], *mxGW = &sc->mx[6], *mxGm = &sc->mx[4];
       launch_absmax(E, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, &sc->mx[0], s);
       launch_absmax(GR, false, n, N, Nn, bc, 1, n, mxGR, s);
       launch_absmax(GWt, false, n, N, Nn, bc, 1, n, mxGW, s);
@@ -713,7 +741,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         // (i) Abar (per (b, v); K = R)
         GemmMnArgs a1;
         a1.M = N; a1.Ncols = n; a1.batch = bc * nv; a1.kc_inner = kcN; a1.nk_outer = 1;
-        a1.a.mn_major = 0; a1.a.zb = 1;
+        a1.a.mn_major = 1; a1.a.zb = 1;   // pairs [R][P]: rows P run along the MN side
         a1.b.mn_major = 1; a1.b.zb = 1; a1.b.zdiv = nv;
         a1.alpha = &sc->f[kFacAbar];
         a1.spin_limit = limit; a1.status = h->d_status;
@@ -722,7 +750,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         SOX_CUDA_TRY(cudaMemsetAsync(GRbf, 0, 4 * (size_t)bc * N * g.np4, s));
         GemmMnArgs a2;
         a2.M = N; a2.Ncols = n; a2.batch = bc; a2.kc_inner = kcN; a2.nk_outer = nv;
-        a2.a.mn_major = 1; a2.a.zb = nv; a2.a.zk = 1;
+        a2.a.mn_major = 0; a2.a.zb = nv; a2.a.zk = 1;
         a2.b.mn_major = 1; a2.b.zb = n; a2.b.zk = 1; a2.b.z0 = v_lo;
         a2.alpha = &sc->f[kFacGRbar];
         a2.spin_limit = limit; a2.status = h->d_status;
@@ -731,7 +759,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         SOX_CUDA_TRY(cudaMemsetAsync(GWbf, 0, 4 * (size_t)bc * N * g.np4, s));
         GemmMnArgs a3;
         a3.M = N; a3.Ncols = n; a3.batch = bc; a3.kc_inner = kcN; a3.nk_outer = nv;
-        a3.a.mn_major = 0; a3.a.zb = nv; a3.a.zk = 1;
+        a3.a.mn_major = 1; a3.a.zb = nv; a3.a.zk = 1;
         a3.b.mn_major = 1; a3.b.zb = 0; a3.b.zk = 1; a3.b.z0 = v_lo;
         a3.alpha = &sc->f[kFacGWtbar];
         a3.spin_limit = limit; a3.status = h->d_status;
@@ -739,7 +767,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         // (iv) U2bar (per v; K = (b, P)), accumulated over tau
         GemmMnArgs a4;
         a4.M = N; a4.Ncols = n; a4.batch = nv; a4.kc_inner = kcN; a4.nk_outer = bc;
-        a4.a.mn_major = 1; a4.a.zb = 1; a4.a.zk = nv;
+        a4.a.mn_major = 0; a4.a.zb = 1; a4.a.zk = nv;
         a4.b.mn_major = 1; a4.b.zb = 0; a4.b.zk = 1;
         a4.alpha = &sc->f[kFacU2bar];
         a4.accumulate = 1;
@@ -765,10 +793,22 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       // ---- Xbar += GRbar G_j^T + GWtbar G_j - (Ebar X) G(tau_{T-1-j})^T... (FP64, per tau)
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GRbf, g.np4, (long long)bc * N, n, GRbar);
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GWbf, g.np4, (long long)bc * N, n, GWtbar);
-      rsplit(Ebar, true, (long long)N * g.ldN, g.ldN, 0, 0, 1, bc, N, N, Ebs, s);
-      rsplit(Ebar, true, (long long)N * g.ldN, 1, 0, 0, g.ldN, bc, N, N, EbTs, s);
-      SOX_TRY(cgemm_tc(h, Ebs, XT, bc, nullptr, nullptr, 1.f, m1f, g.np4, (long long)N * g.np4, s));
-      SOX_TRY(cgemm_tc(h, EbTs, XT, bc, nullptr, nullptr, 1.f, m2f, g.np4, (long long)N * g.np4, s));
+      launch_absmax(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, &sc->mx[7], s);
+      launch_split_tensor(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, g.ldN, (long long)N * g.ldN, 1.f,
+                          &sc->mx[7], nullptr, Ebh, Ebl, &sc->sc[kScEbar], s);
+      k_ex_factor<<<1, 1, 0, s>>>(sc);
+      {
+        GemmMnArgs e1;
+        e1.M = N; e1.Ncols = n; e1.batch = bc; e1.kc_inner = kcN; e1.nk_outer = 1;
+        e1.a.mn_major = 0; e1.a.zb = 1;
+        e1.b.mn_major = 1;
+        e1.alpha = &sc->f[kFacEX];
+        e1.spin_limit = limit; e1.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(mm1, e1, plan_gemm_mn(e1, sms, 1), s));
+        GemmMnArgs e2 = e1;
+        e2.a.mn_major = 1;
+        SOX_CUDA_TRY(launch_gemm_mn(mm2, e2, plan_gemm_mn(e2, sms, 1), s));
+      }
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m1f, g.np4, (long long)bc * N, n, m1);
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m2f, g.np4, (long long)bc * N, n, m2);
       launches += 6;

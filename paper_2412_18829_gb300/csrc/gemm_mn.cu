@@ -28,8 +28,8 @@ constexpr int kT = 128;                       // tile rows / columns
 constexpr int kC = 64;                        // K elements per chunk
 constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of one operand for one chunk
 constexpr int kStageBytes = 4 * kPart;        // A hi, A lo, B hi, B lo
-constexpr int kStages = 2;
-constexpr int kOutBytes = kT * kT * 4;        // FP32 staging of one output tile
+constexpr int kStages = 3;
+constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column half of an output tile
 constexpr int kThreads = 320;                 // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpi = 256;
 
@@ -277,35 +277,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mbar_arrive(&bar->acc_empty[buf]);
       }
       if (!live) break;
-      // scaled tile -> four 128-byte-swizzled boxes of 128 rows x 32 columns -> TMA
-      if (storer) bulk_wait_read();
-      epi_sync();
+      // scaled tile -> TMA, one 64-column half at a time through the staging buffer (two
+      // 128-byte-swizzled boxes of 128 rows x 32 columns); the half-h warps fill it
       float *tile = reinterpret_cast<float *>(stage_out);
+      const bool add = a.accumulate || a.ksplit > 1;
 #pragma unroll
-      for (int c = 0; c < 64; c += 32) {
-        const int col = h * 64 + c;
-        float *box = tile + (col / 32) * (kT * 32) + row * 32;
+      for (int half = 0; half < 2; ++half) {
+        if (storer) bulk_wait_read();   // the previous stores have read the staging buffer
+        epi_sync();
+        if (h == half) {
 #pragma unroll
-        for (int t4 = 0; t4 < 8; ++t4)
-          *reinterpret_cast<float4 *>(box + ((t4 ^ (row & 7)) * 4)) =
-              make_float4(sum[c + 4 * t4] * alpha, sum[c + 4 * t4 + 1] * alpha, sum[c + 4 * t4 + 2] * alpha,
-                          sum[c + 4 * t4 + 3] * alpha);
-      }
-      fence_proxy_async_smem();
-      epi_sync();
-      if (storer) {
-        const bool add = a.accumulate || a.ksplit > 1;
+          for (int c = 0; c < 64; c += 32) {
+            float *box = tile + (c / 32) * (kT * 32) + row * 32;
 #pragma unroll
-        for (int bx = 0; bx < 4; ++bx) {
-          const int x = w.j0 + 32 * bx;
-          if (x < a.Ncols) {
-            if (add)
-              tma_reduce_add_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
-            else
-              tma_store_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
+            for (int t4 = 0; t4 < 8; ++t4)
+              *reinterpret_cast<float4 *>(box + ((t4 ^ (row & 7)) * 4)) =
+                  make_float4(sum[c + 4 * t4] * alpha, sum[c + 4 * t4 + 1] * alpha, sum[c + 4 * t4 + 2] * alpha,
+                              sum[c + 4 * t4 + 3] * alpha);
           }
         }
-        bulk_commit();
+        fence_proxy_async_smem();
+        epi_sync();
+        if (storer) {
+#pragma unroll
+          for (int bx = 0; bx < 2; ++bx) {
+            const int x = w.j0 + half * 64 + 32 * bx;
+            if (x < a.Ncols) {
+              if (add)
+                tma_reduce_add_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
+              else
+                tma_store_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
+            }
+          }
+          bulk_commit();
+        }
       }
     }
     if (storer) bulk_wait_all();
@@ -319,20 +324,33 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ------------------------------ per-tensor splits ------------------------------
 
+// Work unit u of the per-tensor kernels: one warp, 256 consecutive columns (lane + 32 k,
+// k < 8) of one row r = (r1, r0); the index divisions happen once per unit.
+constexpr int kUnitCols = 256;
+
 template <class T>
 __global__ void k_absmax(const T *src, long long ld0, int rows0, long long ld1, int rows1, long long ldc, int cols,
                          float *out) {
+  const long long cpr = (cols + kUnitCols - 1) / kUnitCols;
+  const long long units = (long long)rows1 * rows0 * cpr;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   float m = 0.f;
-  const long long total = (long long)rows1 * rows0 * cols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / cols, c = e % cols;
+  for (long long u = warp0; u < units; u += nwarps) {
+    const long long r = u / cpr;
+    const int c0 = (int)(u % cpr) * kUnitCols;
     const long long r1 = r / rows0, r0 = r % rows0;
-    m = fmaxf(m, (float)fabs((double)src[r1 * ld1 + r0 * ld0 + c * ldc]));
+    const T *row = src + r1 * ld1 + r0 * ld0;
+#pragma unroll
+    for (int k = 0; k < kUnitCols / 32; ++k) {
+      const int c = c0 + lane + 32 * k;
+      if (c < cols) m = fmaxf(m, (float)fabs((double)row[(long long)c * ldc]));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative floats order like their bit patterns
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(m));
+  if (lane == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(m));
 }
 
 // 2^(14 - floor(log2 m)) for m > 0 (m in [2^e, 2^(e+1)) -> scaled max in [2^14, 2^15)), 1 for
@@ -352,26 +370,38 @@ __global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long
                                const float *scale_in, __half *hi, __half *lo, float *scale_out) {
   const float s = scale_in ? *scale_in : big_scale(*absmax);
   const double sd = (double)sign * (double)s;
-  const long long total = (long long)rows1 * rows0 * ldo;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / ldo;
-    const long long c = e % ldo;
+  const long long cpr = (ldo + kUnitCols - 1) / kUnitCols;
+  const long long units = (long long)rows1 * rows0 * cpr;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = warp0; u < units; u += nwarps) {
+    const long long r = u / cpr;
+    const long long c0 = (u % cpr) * kUnitCols;
     const long long r1 = r / rows0, r0 = r % rows0;
-    __half a = __float2half(0.f), b = __float2half(0.f);
-    if (c < cols) {
-      const double x = (double)src[r1 * ld1 + r0 * ld0 + c * ldc] * sd;   // exact: a power of two
-      a = __float2half_rn((float)x);
-      b = __float2half_rn((float)(x - (double)__half2float(a)));
+    const T *row = src + r1 * ld1 + r0 * ld0;
+    __half *h = hi + r1 * ldo1 + r0 * ldo, *l = lo + r1 * ldo1 + r0 * ldo;
+#pragma unroll
+    for (int k = 0; k < kUnitCols / 32; ++k) {
+      const long long c = c0 + lane + 32 * k;
+      if (c >= ldo) break;
+      __half a = __float2half(0.f), b = __float2half(0.f);
+      if (c < cols) {
+        const double x = (double)row[c * ldc] * sd;   // exact: a power of two
+        a = __float2half_rn((float)x);
+        b = __float2half_rn((float)(x - (double)__half2float(a)));
+      }
+      h[c] = a;
+      l[c] = b;
     }
-    const long long o = r1 * ldo1 + r0 * ldo + c;
-    hi[o] = a;
-    lo[o] = b;
   }
   if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
 }
 
-int blocks_for(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152 * 32)); }
+// blocks of 256 threads (8 warps) for `units` warp-sized work units, at most 32 per SM
+int blocks_for_units(long long units) {
+  return (int)std::max<long long>(1, std::min<long long>((units + 7) / 8, 152 * 32));
+}
 
 }  // namespace
 
@@ -400,7 +430,7 @@ cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int gri
 
 void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
                    int cols, float *out, cudaStream_t s) {
-  const int blocks = blocks_for((long long)rows1 * rows0 * cols);
+  const int blocks = blocks_for_units((long long)rows1 * rows0 * ((cols + kUnitCols - 1) / kUnitCols));
   if (f32)
     k_absmax<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols, out);
   else
@@ -410,7 +440,7 @@ void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long lon
 void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
                          int cols, long long ldo, long long ldo1, float sign, const float *absmax,
                          const float *scale_in, __half *hi, __half *lo, float *scale_out, cudaStream_t s) {
-  const int blocks = blocks_for((long long)rows1 * rows0 * ldo);
+  const int blocks = blocks_for_units((long long)rows1 * rows0 * ((ldo + kUnitCols - 1) / kUnitCols));
   if (f32)
     k_split_tensor<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols,
                                                  ldo, ldo1, sign, absmax, scale_in, hi, lo, scale_out);
