@@ -445,7 +445,7 @@ struct AdjGeom {
   int NR;           // P / R rows of the forward operands (>= 128)
   int RG;           // rows of G(-tau)^T per tau (>= 128)
   long long Rp;     // row pitch of Bbar / Cbar (N rounded up to 128)
-  long long nn, np4, np8, nnp, ldN, Nn;
+  long long nn, np4, np8, nnp, ldN, ldN8, Nn;
   long long abar_pitch;   // per-v pitch of the Abar split [(P, q)] (N n rounded up to 8)
   int Bc;           // tau points per chunk
 };
@@ -472,7 +472,7 @@ size_t per_tau_bytes(const AdjGeom &g) {
   b += 4 * aligned_bytes((size_t)n * g.Rp * g.Rp, 2);                             // Bbar, Cbar pairs [v][R][P]
   b += aligned_bytes((size_t)n * N * g.np4, 4) + 2 * aligned_bytes((size_t)n * g.abar_pitch, 2);   // Abar, split
   b += 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);   // GRbar, GWtbar
-  b += 2 * aligned_bytes((size_t)N * g.ldN, 2) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
+  b += 2 * aligned_bytes((size_t)N * g.ldN8, 2) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
   b += 3 * 4096;                                                                  // os, cg, em
   return b;
 }
@@ -495,6 +495,7 @@ AdjGeom adj_geom(sox_handle h, int n, int N, int T, int S) {
   g.np8 = (n + 7) & ~7LL;
   g.nnp = rup4(g.nn);
   g.ldN = rup4(N);
+  g.ldN8 = (N + 7) & ~7LL;   // FP16 rows: a TMA row stride is a multiple of 16 bytes
   g.Nn = (long long)N * n;
   g.abar_pitch = (g.Nn + 7) & ~7LL;
   const size_t per = per_tau_bytes(g);
@@ -573,7 +574,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   __half *Abh = at.take<__half>(Bs * n * g.abar_pitch), *Abl = at.take<__half>(Bs * n * g.abar_pitch);
   float *GRbf = at.take<float>(Bs * N * g.np4), *GWbf = at.take<float>(Bs * N * g.np4);
   double *GRbar = at.take<double>(Bs * Nn), *GWtbar = at.take<double>(Bs * Nn);
-  __half *Ebh = at.take<__half>(Bs * N * g.ldN), *Ebl = at.take<__half>(Bs * N * g.ldN);   // Ebar pairs
+  __half *Ebh = at.take<__half>(Bs * N * g.ldN8), *Ebl = at.take<__half>(Bs * N * g.ldN8);   // Ebar pairs
   float *m1f = at.take<float>(Bs * N * g.np4), *m2f = at.take<float>(Bs * N * g.np4);
   double *m1 = at.take<double>(Bs * Nn), *m2 = at.take<double>(Bs * Nn);
   float *osv = at.take<float>(1024);
@@ -656,13 +657,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       !make_tmap_f32_store3d(&mv[4], U1bar, n, Nn, 1, g.np4, (uint64_t)Nn * g.np4, &err) ||
       // m1[b][P][t] = sum_R Ebar[b][P][R] X[R][t] (A K-major), m2[b][R][t] = sum_P Ebar[b][P][R] X[P][t]
       // (A MN-major); X pairs [R][t] MN-major in both
-      !make_tmap_f16_3d_rs(&mm1[0], Ebh, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 128, &err) ||
-      !make_tmap_f16_3d_rs(&mm1[1], Ebl, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mm1[0], Ebh, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mm1[1], Ebl, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 128, &err) ||
       !make_tmap_f16_3d_rs(&mm1[2], Xh, n, g.np8, N, 1, (uint64_t)N * g.np8, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mm1[3], Xl, n, g.np8, N, 1, (uint64_t)N * g.np8, 64, 64, &err) ||
       !make_tmap_f32_store3d(&mm1[4], m1f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
-      !make_tmap_f16_3d_rs(&mm2[0], Ebh, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 64, &err) ||
-      !make_tmap_f16_3d_rs(&mm2[1], Ebl, N, g.ldN, N, Bc, (uint64_t)N * g.ldN, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mm2[0], Ebh, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 64, &err) ||
+      !make_tmap_f16_3d_rs(&mm2[1], Ebl, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 64, &err) ||
       !make_tmap_f32_store3d(&mm2[4], m2f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err))
     return {SOX_ERR_CUDA, "adjoint maps: " + err};
   mm2[2] = mm1[2];
@@ -794,7 +795,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GRbf, g.np4, (long long)bc * N, n, GRbar);
       k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GWbf, g.np4, (long long)bc * N, n, GWtbar);
       launch_absmax(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, &sc->mx[7], s);
-      launch_split_tensor(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, g.ldN, (long long)N * g.ldN, 1.f,
+      launch_split_tensor(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, g.ldN8, (long long)N * g.ldN8, 1.f,
                           &sc->mx[7], nullptr, Ebh, Ebl, &sc->sc[kScEbar], s);
       k_ex_factor<<<1, 1, 0, s>>>(sc);
       {
