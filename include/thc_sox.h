@@ -151,6 +151,22 @@ SOX_API int sox_check_device(sox_handle h);
  * their handle at creation.  Returns SOX_ERR_INVALID_ARG for v0 < 0 or 0 < v1 < v0. */
 SOX_API int sox_set_v_range(sox_handle h, int v0, int v1);
 
+/* Fused B/C/Hadamard kernel of the split-precision molecular chain (Sec. II C, the B, C
+ * and D steps; used by sox_sigma, sox_sigma_general, sosex_static_sigma, phi_sox and the
+ * batch calls on an SOX_PREC_F16X2 handle).  SOX_KERNEL_AUTO (the default) times the
+ * variants on the first call per shape and keeps the fastest (outside a stream capture
+ * and unless sox_options.no_autotune; else resident for n <= 128, streamed above);
+ * the others force one variant for every later call on h:
+ *   SOX_KERNEL_RESIDENT  G_Rq / G_wP^T tiles resident in shared memory (n <= 128 only;
+ *                        larger n run the streamed kernel),
+ *   SOX_KERNEL_STREAMED  all four operands streamed through a 3-stage TMA pipeline,
+ *   SOX_KERNEL_PAIR      streamed on CTA pairs (tcgen05 cta_group::2, 256 x 128 tiles,
+ *                        each SM loading half of the R-side operand).
+ * Every variant computes the same Sigma up to FP32 accumulation order.  Returns
+ * SOX_ERR_INVALID_ARG for another value. */
+enum { SOX_KERNEL_AUTO = 0, SOX_KERNEL_RESIDENT = 1, SOX_KERNEL_STREAMED = 2, SOX_KERNEL_PAIR = 3 };
+SOX_API int sox_set_kernel_variant(sox_handle h, int variant);
+
 /* Grow the workspace for problem p now (outside any graph capture). */
 SOX_API int sox_reserve(sox_handle h, const sox_problem *p);
 

@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     sosex_static_sigma,
     sox_check_device,
     sox_set_v_range,
+    sox_set_kernel_variant,
     sox_dyson,
     sox_green_tails,
     sox_iw_to_tau,

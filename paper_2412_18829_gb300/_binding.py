@@ -50,6 +50,7 @@ _SIGS = {
     "sox_reserve": ([_P, ctypes.POINTER(sox_problem)], _I),
     "sox_check_device": ([_P], _I),
     "sox_set_v_range": ([_P, _I, _I], _I),
+    "sox_set_kernel_variant": ([_P, _I], _I),
     "sox_profile_enable": ([_P, _I], _I),
     "sox_profile_read": ([_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)], _I),
     "sox_tau_grid": ([_I, ctypes.c_double, _P, _P], _I),
@@ -215,6 +216,15 @@ def sox_check_device(h: Handle):
 def sox_set_v_range(h: Handle, v0: int = 0, v1: int = 0):
     """Restrict the handle's later builds to the terms with v in [v0, v1) (0, 0: all)."""
     h.check(lib().sox_set_v_range(h.ptr, int(v0), int(v1)))
+
+
+KERNEL_VARIANTS = {"auto": 0, "resident": 1, "streamed": 2, "pair": 3}
+
+
+def sox_set_kernel_variant(h: Handle, variant: str = "auto"):
+    """Force the split path's fused B/C/D kernel variant ("resident", "streamed", "pair")
+    or return to timing them on the first call per shape ("auto")."""
+    h.check(lib().sox_set_kernel_variant(h.ptr, KERNEL_VARIANTS[variant]))
 
 
 def sox_profile_enable(h: Handle, enable: bool = True):

@@ -7,14 +7,17 @@
 //   Abar_v = Bbar_v GR,            GRbar = sum_v Bbar_v^T A_v,
 //   GWtbar = sum_v Cbar_v U2_v,    U2bar_v += Cbar_v^T GWt,
 //   U1bar += sum_v Abar_v (x) G(-tau_j)[:, v]
-// then Xbar from GRbar, GWtbar, Ebar (FP64), and at the end
+// then Xbar += GRbar G(tau_j)^T + GWtbar G(tau_j) - (Ebar X) G(-tau_j)^T - (Ebar^T X) G(-tau_j)
+// (one split GEMM per chunk, accumulated in FP64), and at the end
 //   Vbar = (U1bar + U2bar) Y^T,  Z = V^T (U1bar + U2bar),  Xbar += pair-product adjoint of Z.
+// The projections G_Rq = X G(tau), G_wP^T = X G(tau)^T stay FP64, computed once per spin for
+// every tau (E of tau_j reuses G_Rq of tau_{T-1-j}).
 //
 // B_v and C_v are never stored.  One fused kernel (k_adj_bc) recomputes them per
 // 128 x 128 (P, R) tile in TMEM -- the forward's TMA / MMA pipeline -- and its epilogue
 // forms Bbar_v and Cbar_v from E held in registers, writes them once as FP16 pairs
-// [tau][v][R][P] (coalesced: a warp's lanes hold consecutive P) and accumulates Ebar.  The four reverse contractions then read those
-// pairs in place: over R as K-major operands and over P as MN-major ones (gemm_mn.cu),
+// [tau][v][R][P] (coalesced: a warp's lanes hold consecutive P) and accumulates Ebar.  The
+// four reverse contractions then read those pairs in place: over R as K-major operands and over P as MN-major ones (gemm_mn.cu),
 // so no transposed copy and no FP32 round trip of the n N^2 tensors exists.  Every split
 // operand carries one power-of-two scale per tensor (per tau chunk), which is what lets
 // one layout serve both contraction orders.
@@ -71,6 +74,22 @@ __global__ void k_to_f64(const float *in, long long ld, long long rows, int cols
     out[e] = (double)in[(e / cols) * ld + e % cols];
 }
 
+// out (FP64, rows x cols) += in (FP32, row length ld)
+__global__ void k_add_f64(const float *in, long long ld, long long rows, int cols, double *out) {
+  const long long total = rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] += (double)in[(e / cols) * ld + e % cols];
+}
+
+// dst[b] = src[b] (count values each) where flag[b] is set
+__global__ void k_copy_flagged(const double *src, double *dst, long long count, int batch, const int *flag) {
+  const long long total = count * batch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    if (flag[e / count]) dst[e] = src[e];
+}
+
 __global__ void k_fill(float *p, int count, float v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) p[i] = v;
@@ -84,12 +103,15 @@ __global__ void k_fill(float *p, int count, float v) {
 //        Abar, GRbar, GWtbar, U2bar, U1bar (the last completed once Abar's scale is known),
 //        cg[b] = c_b g, em[b] = c_b / (sA sR sW sU)
 struct AdjScalars {
-  float mx[8];    // atomicMax targets: E, Abar, mixed tensor, X, G(-tau), GR, GWt, Ebar
-  float sc[8];    // scales: GR, GWt, G(-tau), U, Abar, X, Ebar
-  float f[8];     // output factors of the contractions
+  float mx[12];   // atomicMax targets: E, Abar, mixed tensor, X, G(-tau), GR, GWt, Ebar,
+                  // the Xbar GEMM's A (projection adjoints) and B (G(tau), G(-tau)) operands
+  float sc[12];   // scales: GR, GWt, G(-tau), U, Abar, X, Ebar, Xbar A, Xbar B
+  float f[12];    // output factors of the contractions
 };
-constexpr int kFacG = 0, kFacAbar = 1, kFacGRbar = 2, kFacGWtbar = 3, kFacU2bar = 4, kFacU1bar = 5, kFacEX = 6;
-constexpr int kScGR = 0, kScGW = 1, kScGm = 2, kScU = 3, kScAbar = 4, kScX = 5, kScEbar = 6;
+constexpr int kFacG = 0, kFacAbar = 1, kFacGRbar = 2, kFacGWtbar = 3, kFacU2bar = 4, kFacU1bar = 5, kFacEX = 6,
+              kFacXbar = 7;
+constexpr int kScGR = 0, kScGW = 1, kScGm = 2, kScU = 3, kScAbar = 4, kScX = 5, kScEbar = 6, kScXa = 7, kScXb = 8;
+constexpr int kMxXa = 8, kMxXb = 9;
 
 __device__ __forceinline__ float pow2_floor(double x) {
   // largest power of two <= x (x > 0), clamped to normal FP32
@@ -129,6 +151,10 @@ __global__ void k_u1bar_factor(AdjScalars *sc) {
 
 __global__ void k_ex_factor(AdjScalars *sc) {
   sc->f[kFacEX] = (float)(1.0 / ((double)sc->sc[kScEbar] * (double)sc->sc[kScX]));
+}
+
+__global__ void k_xbar_factor(AdjScalars *sc) {
+  sc->f[kFacXbar] = (float)(1.0 / ((double)sc->sc[kScXa] * (double)sc->sc[kScXb]));
 }
 
 // ============================================================================
@@ -179,10 +205,13 @@ struct AdjBcArgs {
 
 __device__ __forceinline__ long long wind_down(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
 
+// 3 x ks MMAs of one 64-wide K chunk (ks 16-wide steps; the last chunk of the n-long
+// contraction stops at its first all-padding step)
 __device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            bool first) {
+                                            bool first, int ks) {
 #pragma unroll
   for (int k = 0; k < kC / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
@@ -190,6 +219,7 @@ __device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_
   }
 #pragma unroll
   for (int k = 0; k < kC / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
@@ -397,7 +427,8 @@ __global__ void __launch_bounds__(kProdThreads, 1)
               if (!ok) break;
               tc::tc_fence_after();
               const uint32_t st = smem_u32(smem + (size_t)s * kStageB);
-              issue_split(acc, st, st + kTileB, st + 2 * kTileB, st + 3 * kTileB, kc == 0);
+              issue_split(acc, st, st + kTileB, st + 2 * kTileB, st + 3 * kTileB, kc == 0,
+                          a.n - kc * kC >= kC ? kC / 16 : (a.n - kc * kC + 15) / 16);
               tc::mma_commit(&bar->empty[s]);
             }
           }
@@ -459,20 +490,22 @@ size_t fixed_bytes(const AdjGeom &g) {
   b += aligned_bytes((size_t)N * g.n * g.np4, 4) + aligned_bytes((size_t)g.n * N * g.np4, 4);   // U1bar, U2bar
   b += aligned_bytes((size_t)g.Nn, 8) + rsplit_bytes(1, N, g.n) + 2 * aligned_bytes((size_t)N * g.np8, 2);   // Xbar, X
   b += aligned_bytes(sizeof(AdjScalars), 4) + 2 * aligned_bytes(8192, 4) + (1 << 16);
+  b += 2 * aligned_bytes((size_t)g.T * g.Nn, 8) + aligned_bytes((size_t)g.T, 4);   // G_Rq, G_wP^T of every tau
+  b += aligned_bytes((size_t)N * g.np4, 4);                                        // Xbar of one chunk (FP32)
   return b;
 }
 
 size_t per_tau_bytes(const AdjGeom &g) {
   const int n = g.n, N = g.N;
-  size_t b = 3 * aligned_bytes((size_t)g.Nn, 8);                                  // GR, GWt, M1 (FP64)
-  b += rsplit_bytes(1, N, n) + 2 * aligned_bytes((size_t)N * g.ldN, 4);           // M1 split, E, Ebar
+  size_t b = rsplit_bytes(1, N, n) + 2 * aligned_bytes((size_t)N * g.ldN, 4);           // M1 split, E, Ebar
   b += 4 * aligned_bytes((size_t)g.NR * g.Kp, 2);                                 // GR~, GWt~
   b += 2 * aligned_bytes((size_t)g.RG * g.Kp, 2) + 2 * aligned_bytes((size_t)n * g.Kp, 2);   // G(-tau) splits
   b += 2 * aligned_bytes((size_t)n * g.NR * g.Kp, 2);                             // A~
   b += 4 * aligned_bytes((size_t)n * g.Rp * g.Rp, 2);                             // Bbar, Cbar pairs [v][R][P]
   b += aligned_bytes((size_t)n * N * g.np4, 4) + 2 * aligned_bytes((size_t)n * g.abar_pitch, 2);   // Abar, split
-  b += 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);   // GRbar, GWtbar
-  b += 2 * aligned_bytes((size_t)N * g.ldN8, 2) + 2 * aligned_bytes((size_t)N * g.np4, 4) + 2 * aligned_bytes((size_t)g.Nn, 8);
+  b += 2 * aligned_bytes((size_t)N * g.np4, 4);                                   // GRbar, GWtbar
+  b += 2 * aligned_bytes((size_t)N * g.ldN8, 2) + 2 * aligned_bytes((size_t)N * g.np4, 4);   // Ebar pairs, m1, m2
+  b += 2 * aligned_bytes((size_t)4 * N * g.np8, 2) + 2 * aligned_bytes((size_t)4 * n * g.np8, 2);   // Xbar operands
   b += 3 * 4096;                                                                  // os, cg, em
   return b;
 }
@@ -531,7 +564,10 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   __half *Xh = ar.take<__half>((size_t)N * g.np8), *Xl = ar.take<__half>((size_t)N * g.np8);   // X pairs [R][t]
   AdjScalars *sc = ar.take<AdjScalars>(1);
   float *cgb = ar.take<float>(2048), *emb = ar.take<float>(2048);
-  if (!emb) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+  double *GRall = ar.take<double>((size_t)T * Nn), *GWall = ar.take<double>((size_t)T * Nn);   // one spin
+  int *symf = ar.take<int>((size_t)T);
+  float *Xbf = ar.take<float>((size_t)N * g.np4);
+  if (!Xbf) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   ProfScope ps(h, "phi_adjoint_tc", s, 0);
   long long launches = 0;
   SOX_CUDA_TRY(cudaMemsetAsync(U1bar, 0, 4 * (size_t)N * n * g.np4, s));
@@ -560,7 +596,6 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   // ---- per tau-chunk buffers
   Arena at = ar;
   const size_t Bs = (size_t)Bc;
-  double *GR = at.take<double>(Bs * Nn), *GWt = at.take<double>(Bs * Nn), *M1 = at.take<double>(Bs * Nn);
   CSplit M1s = rsplit_take(at, Bc, N, n);
   float *E = at.take<float>(Bs * N * g.ldN), *Ebar = at.take<float>(Bs * N * g.ldN);
   __half *GRh = at.take<__half>(Bs * NR * Kp), *GRl = at.take<__half>(Bs * NR * Kp);
@@ -573,10 +608,12 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   float *Abar = at.take<float>(Bs * n * N * g.np4);
   __half *Abh = at.take<__half>(Bs * n * g.abar_pitch), *Abl = at.take<__half>(Bs * n * g.abar_pitch);
   float *GRbf = at.take<float>(Bs * N * g.np4), *GWbf = at.take<float>(Bs * N * g.np4);
-  double *GRbar = at.take<double>(Bs * Nn), *GWtbar = at.take<double>(Bs * Nn);
   __half *Ebh = at.take<__half>(Bs * N * g.ldN8), *Ebl = at.take<__half>(Bs * N * g.ldN8);   // Ebar pairs
   float *m1f = at.take<float>(Bs * N * g.np4), *m2f = at.take<float>(Bs * N * g.np4);
-  double *m1 = at.take<double>(Bs * Nn), *m2 = at.take<double>(Bs * Nn);
+  // Xbar GEMM operands: A [b][t][R][k] = GRbar, GWtbar, m1, m2; B [b][t][p][k] = G(tau_b)[p][k],
+  // G(tau_b)[k][p], -G(-tau_b)[p][k], -G(-tau_b)[k][p]  (K = (b, t, k))
+  __half *Xah = at.take<__half>(Bs * 4 * N * g.np8), *Xal = at.take<__half>(Bs * 4 * N * g.np8);
+  __half *Xbh = at.take<__half>(Bs * 4 * n * g.np8), *Xbl = at.take<__half>(Bs * 4 * n * g.np8);
   float *osv = at.take<float>(1024);
   if (!osv) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
   // zero padding rows and columns that the splits do not write (rows R >= N of GR~ / GWt~,
@@ -621,7 +658,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   const int Kpv = rup(std::max(nv, 1), 64);
   const uint64_t zBC = (uint64_t)Bc * std::max(nv, 1);   // (tau, local v) slices of Bbar / Cbar
   // (i) Abar[b][v][P][q] = sum_R Bbar[b][v][R][P] GR~[b][R][q]: A MN-major, B MN-major
-  CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5], mm1[5], mm2[5];
+  CUtensorMap mi[5], mii[5], miii[5], miv[5], mv[5], mm1[5], mm2[5], mxb[5];
   const uint64_t sPR = (uint64_t)g.Rp * g.Rp;   // one (tau, v) slice of the pairs: rows R, P contiguous
   if (!make_tmap_f16_3d_rs(&mi[0], Bbh, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mi[1], Bbl, N, g.Rp, N, zBC, sPR, 64, 64, &err) ||
@@ -664,7 +701,13 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       !make_tmap_f32_store3d(&mm1[4], m1f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
       !make_tmap_f16_3d_rs(&mm2[0], Ebh, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 64, &err) ||
       !make_tmap_f16_3d_rs(&mm2[1], Ebl, N, g.ldN8, N, Bc, (uint64_t)N * g.ldN8, 64, 64, &err) ||
-      !make_tmap_f32_store3d(&mm2[4], m2f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err))
+      !make_tmap_f32_store3d(&mm2[4], m2f, n, N, Bc, g.np4, (uint64_t)N * g.np4, &err) ||
+      // Xbar[R][p] = sum_{b,t,k} A[b][t][R][k] B[b][t][p][k]: both K-major
+      !make_tmap_f16_3d_rs(&mxb[0], Xah, n, g.np8, N, 4 * (uint64_t)Bc, (uint64_t)N * g.np8, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mxb[1], Xal, n, g.np8, N, 4 * (uint64_t)Bc, (uint64_t)N * g.np8, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mxb[2], Xbh, n, g.np8, n, 4 * (uint64_t)Bc, (uint64_t)n * g.np8, 64, 128, &err) ||
+      !make_tmap_f16_3d_rs(&mxb[3], Xbl, n, g.np8, n, 4 * (uint64_t)Bc, (uint64_t)n * g.np8, 64, 128, &err) ||
+      !make_tmap_f32_store3d(&mxb[4], Xbf, n, N, 1, g.np4, (uint64_t)N * g.np4, &err))
     return {SOX_ERR_CUDA, "adjoint maps: " + err};
   mm2[2] = mm1[2];
   mm2[3] = mm1[3];
@@ -673,26 +716,30 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
   const long long limit = h->spin_limit;
 
   for (int sp = 0; sp < S && nv > 0; ++sp) {
+    {  // FP64 projections of every tau of this spin: G_Rq = X G(tau), G_wP^T = X G(tau)^T
+       // (copied from G_Rq where G(tau) is symmetric); M1 below reuses G_Rq of the mirror point
+      const double *Gs = G + (long long)sp * T * nn;
+      launch_symmetry_flags(Gs, n, T, symf, s);
+      GemmF64 a;
+      a.M = N; a.Nc = n; a.K = n; a.batch = T;
+      a.A = X; a.ai = n; a.ak = 1;
+      a.B = Gs; a.sB = nn; a.bk = n; a.bj = 1;
+      a.C = GRall; a.sC = Nn; a.ci = n; a.cj = 1;
+      launch_gemm_f64(a, s);
+      GemmF64 b = a;
+      b.bk = 1; b.bj = n; b.C = GWall; b.skip = symf;
+      launch_gemm_f64(b, s);
+      k_copy_flagged<<<grid1((long long)T * Nn), 256, 0, s>>>(GRall, GWall, Nn, T, symf);
+      launches += 4;
+    }
     for (int j0 = 0; j0 < T; j0 += Bc) {
       const int bc = std::min(Bc, T - j0);
       const double *Gj = G + ((long long)sp * T + j0) * nn;                 // G(tau_j), b = 0..bc-1
       const double *Gm0 = G + ((long long)sp * T + (T - 1 - j0)) * nn;      // G(tau_{T-1-j}); stride -nn
-      {  // FP64 projections and M1 = -X G(tau_{T-1-j}) (so that E = M1 X^T = X G(-tau) X^T)
-        GemmF64 a;
-        a.M = N; a.Nc = n; a.K = n; a.batch = bc;
-        a.A = X; a.ai = n; a.ak = 1;
-        a.B = Gj; a.sB = nn; a.bk = n; a.bj = 1;
-        a.C = GR; a.sC = Nn; a.ci = n; a.cj = 1;
-        launch_gemm_f64(a, s);
-        GemmF64 b = a;
-        b.bk = 1; b.bj = n; b.C = GWt;
-        launch_gemm_f64(b, s);
-        GemmF64 c = a;
-        c.B = Gm0; c.sB = -nn; c.C = M1; c.alpha = -1.0;
-        launch_gemm_f64(c, s);
-      }
-      rsplit(M1, false, Nn, n, 0, 0, 1, bc, N, n, M1s, s);
-      SOX_TRY(cgemm_tc(h, M1s, Xr, bc, nullptr, nullptr, 1.f, E, g.ldN, (long long)N * g.ldN, s));
+      const double *GR = GRall + (long long)j0 * Nn, *GWt = GWall + (long long)j0 * Nn;
+      // E = X G(-tau) X^T = -(X G(tau_{T-1-j})) X^T: G_Rq of the mirror points (batch stride -Nn)
+      rsplit(GRall + (long long)(T - 1 - j0) * Nn, false, -Nn, n, 0, 0, 1, bc, N, n, M1s, s);
+      SOX_TRY(cgemm_tc(h, M1s, Xr, bc, nullptr, nullptr, -1.f, E, g.ldN, (long long)N * g.ldN, s));
       // per-chunk maxima and scales
       SOX_CUDA_TRY(cudaMemsetAsync(sc->mx, 0, sizeof(sc->mx[0]) * 2, s));       // E, Abar
       SOX_CUDA_TRY(cudaMemsetAsync(&sc->mx[4], 0, sizeof(sc->mx[0]) * 4, s));   // G(-tau), GR, GWt, Ebar
@@ -714,7 +761,7 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
       launches += 14;
       {  // A~[b][v][P][q] = os sum_s G(-tau_b)~[s][v] U1~[(P,q)][s]
         GemmTcArgs ga;
-        ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.batch = bc;
+        ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.K = n; ga.batch = bc;
         ga.batchA_shared = 0; ga.batchB_shared = 1;
         ga.mode = kStoreSplit;
         ga.out_scale = osv;
@@ -791,9 +838,9 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         SOX_CUDA_TRY(launch_gemm_mn(mv, a5, plan_gemm_mn(a5, sms, 1), s));
       }
       launches += 11;
-      // ---- Xbar += GRbar G_j^T + GWtbar G_j - (Ebar X) G(tau_{T-1-j})^T... (FP64, per tau)
-      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GRbf, g.np4, (long long)bc * N, n, GRbar);
-      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(GWbf, g.np4, (long long)bc * N, n, GWtbar);
+      // ---- Xbar += sum_b GRbar_b G(tau_b)^T + GWtbar_b G(tau_b) - m1_b G(-tau_b)^T - m2_b G(-tau_b)
+      // (m1 = Ebar X, m2 = Ebar^T X; G(-tau_b) = -G(tau_{T-1-j}) enters through the signs): one
+      // split GEMM over K = (b, term, k), its FP32 result added to the FP64 accumulator
       launch_absmax(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, &sc->mx[7], s);
       launch_split_tensor(Ebar, true, g.ldN, N, (long long)N * g.ldN, bc, 1, N, g.ldN8, (long long)N * g.ldN8, 1.f,
                           &sc->mx[7], nullptr, Ebh, Ebl, &sc->sc[kScEbar], s);
@@ -810,33 +857,39 @@ Status phi_adjoint_xv_tc(sox_handle h, int n, int N, int T, int S, const double 
         e2.a.mn_major = 1;
         SOX_CUDA_TRY(launch_gemm_mn(mm2, e2, plan_gemm_mn(e2, sms, 1), s));
       }
-      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m1f, g.np4, (long long)bc * N, n, m1);
-      k_to_f64<<<grid1((long long)bc * Nn), 256, 0, s>>>(m2f, g.np4, (long long)bc * N, n, m2);
-      launches += 6;
-      for (int b = 0; b < bc; ++b) {
-        const double *Gb = Gj + (long long)b * nn;
-        const double *Gmb = Gm0 - (long long)b * nn;
-        GemmF64 x1;
-        x1.M = N; x1.Nc = n; x1.K = n;
-        x1.A = GRbar + (long long)b * Nn; x1.ai = n; x1.ak = 1;
-        x1.B = Gb; x1.bk = 1; x1.bj = n;
-        x1.C = Xbar; x1.ci = n; x1.cj = 1; x1.beta = 1.0;
-        launch_gemm_f64(x1, s);
-        GemmF64 x2 = x1;
-        x2.A = GWtbar + (long long)b * Nn; x2.bk = n; x2.bj = 1;
-        launch_gemm_f64(x2, s);
-        GemmF64 x3;
-        x3.M = N; x3.Nc = n; x3.K = n;
-        x3.A = m1 + (long long)b * Nn; x3.ai = n; x3.ak = 1;
-        x3.B = Gmb; x3.bk = 1; x3.bj = n;
-        x3.C = Xbar; x3.ci = n; x3.cj = 1;
-        x3.alpha = -1.0; x3.beta = 1.0;
-        launch_gemm_f64(x3, s);
-        GemmF64 x4 = x3;
-        x4.A = m2 + (long long)b * Nn; x4.bk = n; x4.bj = 1;
-        launch_gemm_f64(x4, s);
-        launches += 4;
+      SOX_CUDA_TRY(cudaMemsetAsync(&sc->mx[kMxXa], 0, 2 * sizeof(float), s));
+      const float *xa[4] = {GRbf, GWbf, m1f, m2f};
+      for (int t = 0; t < 4; ++t)
+        launch_absmax(xa[t], true, g.np4, N, (long long)N * g.np4, bc, 1, n, &sc->mx[kMxXa], s);
+      for (int t = 0; t < 4; ++t)
+        launch_split_tensor(xa[t], true, g.np4, N, (long long)N * g.np4, bc, 1, n, g.np8, 4LL * N * g.np8, 1.f,
+                            &sc->mx[kMxXa], nullptr, Xah + (size_t)t * N * g.np8, Xal + (size_t)t * N * g.np8,
+                            t == 0 ? &sc->sc[kScXa] : nullptr, s);
+      launch_absmax(Gj, false, n, n, nn, bc, 1, n, &sc->mx[kMxXb], s);
+      launch_absmax(Gm0, false, n, n, -nn, bc, 1, n, &sc->mx[kMxXb], s);
+      struct XbTerm {
+        const double *src;
+        long long ld0, ldc, ld1;
+        float sign;
+      };
+      const XbTerm xb[4] = {{Gj, n, 1, nn, 1.f}, {Gj, 1, n, nn, 1.f}, {Gm0, n, 1, -nn, -1.f}, {Gm0, 1, n, -nn, -1.f}};
+      for (int t = 0; t < 4; ++t)
+        launch_split_tensor(xb[t].src, false, xb[t].ld0, n, xb[t].ld1, bc, xb[t].ldc, n, g.np8, 4LL * n * g.np8,
+                            xb[t].sign, &sc->mx[kMxXb], nullptr, Xbh + (size_t)t * n * g.np8,
+                            Xbl + (size_t)t * n * g.np8, t == 0 ? &sc->sc[kScXb] : nullptr, s);
+      k_xbar_factor<<<1, 1, 0, s>>>(sc);
+      SOX_CUDA_TRY(cudaMemsetAsync(Xbf, 0, 4 * (size_t)N * g.np4, s));
+      {
+        GemmMnArgs x;
+        x.M = N; x.Ncols = n; x.batch = 1; x.kc_inner = (n + 63) / 64; x.nk_outer = 4 * bc;
+        x.a.mn_major = 0; x.a.zk = 1;
+        x.b.mn_major = 0; x.b.zk = 1;
+        x.alpha = &sc->f[kFacXbar];
+        x.spin_limit = limit; x.status = h->d_status;
+        SOX_CUDA_TRY(launch_gemm_mn(mxb, x, plan_gemm_mn(x, sms, 64), s));
       }
+      k_add_f64<<<grid1(Nn), 256, 0, s>>>(Xbf, g.np4, N, n, Xbar);
+      launches += 22;
     }
   }
 

@@ -488,6 +488,14 @@ int sox_set_v_range(sox_handle h, int v0, int v1) {
   return finish(h, Status::ok());
 }
 
+int sox_set_kernel_variant(sox_handle h, int variant) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  if (variant < SOX_KERNEL_AUTO || variant > SOX_KERNEL_PAIR)
+    return finish(h, {SOX_ERR_INVALID_ARG, "unknown fused-kernel variant"});
+  h->variant = variant;
+  return finish(h, Status::ok());
+}
+
 int sox_reserve(sox_handle h, const sox_problem *p) {
   if (!h) return SOX_ERR_INVALID_ARG;
   Status st = validate(p);

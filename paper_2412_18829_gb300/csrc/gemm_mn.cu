@@ -328,6 +328,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 // k < 8) of one row r = (r1, r0); the index divisions happen once per unit.
 constexpr int kUnitCols = 256;
 
+// |x| as FP32 (an FP64 value rounds up to at most one FP32 ulp); FP32 sources stay on the
+// FP32 pipe (the FP64 rate is 1/64 of it)
+__device__ __forceinline__ float abs_f(float x) { return fabsf(x); }
+__device__ __forceinline__ float abs_f(double x) { return (float)fabs(x); }
+
+// FP16 pair of x * sd (sd a signed power of two; x * sd exact): hi rounds to nearest and
+// lo = RN(x sd - hi).  For an FP32 x both steps are exact in FP32, so no FP64 arithmetic
+// is needed; an FP64 x keeps its remainder in FP64.
+__device__ __forceinline__ void split_scaled(float x, float sf, double, __half &a, __half &b) {
+  const float xs = x * sf;
+  a = __float2half_rn(xs);
+  b = __float2half_rn(xs - __half2float(a));
+}
+__device__ __forceinline__ void split_scaled(double x, float, double sd, __half &a, __half &b) {
+  const double xs = x * sd;
+  a = __float2half_rn((float)xs);
+  b = __float2half_rn((float)(xs - (double)__half2float(a)));
+}
+
 template <class T>
 __global__ void k_absmax(const T *src, long long ld0, int rows0, long long ld1, int rows1, long long ldc, int cols,
                          float *out) {
@@ -345,7 +364,7 @@ __global__ void k_absmax(const T *src, long long ld0, int rows0, long long ld1, 
 #pragma unroll
     for (int k = 0; k < kUnitCols / 32; ++k) {
       const int c = c0 + lane + 32 * k;
-      if (c < cols) m = fmaxf(m, (float)fabs((double)row[(long long)c * ldc]));
+      if (c < cols) m = fmaxf(m, abs_f(row[(long long)c * ldc]));
     }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -370,6 +389,7 @@ __global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long
                                const float *scale_in, __half *hi, __half *lo, float *scale_out) {
   const float s = scale_in ? *scale_in : big_scale(*absmax);
   const double sd = (double)sign * (double)s;
+  const float sf = sign * s;
   const long long cpr = (ldo + kUnitCols - 1) / kUnitCols;
   const long long units = (long long)rows1 * rows0 * cpr;
   const int lane = threadIdx.x & 31;
@@ -386,11 +406,7 @@ __global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long
       const long long c = c0 + lane + 32 * k;
       if (c >= ldo) break;
       __half a = __float2half(0.f), b = __float2half(0.f);
-      if (c < cols) {
-        const double x = (double)row[c * ldc] * sd;   // exact: a power of two
-        a = __float2half_rn((float)x);
-        b = __float2half_rn((float)(x - (double)__half2float(a)));
-      }
+      if (c < cols) split_scaled(row[c * ldc], sf, sd, a, b);
       h[c] = a;
       l[c] = b;
     }
@@ -408,13 +424,26 @@ int blocks_for_units(long long units) {
 int plan_gemm_mn(GemmMnArgs &a, int sms, int max_ksplit) {
   const long long tiles = (long long)a.batch * ((a.M + kT - 1) / kT) * ((a.Ncols + kT - 1) / kT);
   const long long chunks = (long long)a.kc_inner * a.nk_outer;
-  long long ks = 1;
-  if (tiles < sms && max_ksplit > 1) ks = std::min<long long>((sms + tiles - 1) / tiles, max_ksplit);
   const long long windows = (chunks + a.window - 1) / a.window;
-  ks = std::max<long long>(1, std::min(ks, windows));
-  const long long wps = (windows + ks - 1) / ks;       // windows per split item
+  // Items run in waves of `sms` (one CTA per SM, items strided over the grid); each costs
+  // its windows plus about a quarter window of epilogue.  Pick the split with the least
+  // modelled time: ceil(items / sms) x (windows per item + 1/4).
+  long long best_ks = 1;
+  double best = -1.0;
+  const long long kmax = std::max<long long>(1, std::min<long long>(max_ksplit, windows));
+  for (long long ks = 1; ks <= kmax; ++ks) {
+    const long long wps = (windows + ks - 1) / ks;
+    const long long split = (windows + wps - 1) / wps;
+    const long long items = tiles * split;
+    const double cost = (double)((items + sms - 1) / sms) * ((double)wps + 0.25);
+    if (best < 0.0 || cost < best - 1e-9) {
+      best = cost;
+      best_ks = ks;
+    }
+  }
+  const long long wps = (windows + best_ks - 1) / best_ks;   // windows per split item
   a.cps = wps * a.window;
-  a.ksplit = (int)((chunks + a.cps - 1) / a.cps);      // every item has at least one chunk
+  a.ksplit = (int)((chunks + a.cps - 1) / a.cps);            // every item has at least one chunk
   const long long items = tiles * a.ksplit;
   return (int)std::max<long long>(1, std::min<long long>(items, sms));
 }

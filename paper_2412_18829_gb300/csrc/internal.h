@@ -26,6 +26,7 @@ struct sox_context {
   int sm_count = 0;
   int v0 = 0, v1 = 0;        // sox_set_v_range: sums over the orbital index v run over [v0, v1) (v1 = 0: all)
   bool autotune = true;      // time the fused-kernel variants on the first call per shape
+  int variant = 0;           // SOX_KERNEL_*: 0 = autotune, else the forced fused-kernel variant
   std::map<std::string, int> tuned;  // shape key -> chosen variant
   std::string last_error;
   // launch accounting (sox_profile_enable / sox_profile_read)

@@ -81,15 +81,18 @@ __device__ __forceinline__ uint8_t *stage_ptr(uint8_t *smem, int s, int t) {
   return smem + (size_t)s * kStageBytes + (size_t)t * kTileBytes;
 }
 
-// Issues the 3 x 4 MMAs of one 64-wide K chunk: acc (+)= (ahi + alo)(bhi + blo)^T minus lo*lo.
+// Issues the 3 x ks MMAs of one 64-wide K chunk (ks 16-wide steps, 1..4: the last chunk
+// of a contraction stops at the first all-padding step):
+// acc (+)= (ahi + alo)(bhi + blo)^T minus lo*lo.
 // The small cross terms go first: the tensor core truncates every accumulation
 // step to FP32 (round toward zero), and each step into a large accumulator
 // costs up to one ulp, so the large hi*hi steps are kept last and fewest.
-__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first) {
+__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first, int ks) {
   const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kTileBytes;
   const uint32_t b_hi = a_hi + 2 * kTileBytes, b_lo = a_hi + 3 * kTileBytes;
 #pragma unroll
   for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
@@ -97,9 +100,17 @@ __device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool firs
   }
 #pragma unroll
   for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
+}
+
+// 16-wide K steps of chunk kc when the contraction has K valid elements (the rest of the
+// padded extent is zero): 4, except in the last chunk.
+__device__ __forceinline__ int chunk_steps(int kc, int K) {
+  const int rem = K - kc * kChunk;
+  return rem >= kChunk ? kChunk / 16 : (rem + 15) / 16;
 }
 
 __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
               ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
-              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0);
+              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, a.n));
               tc::mma_commit(&bar->empty[s]);
             }
           }
@@ -325,9 +336,10 @@ __device__ __forceinline__ uint8_t *res_ptr(uint8_t *res, int op, int part, int 
 }
 
 __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                             uint32_t b_lo, bool first) {
+                                             uint32_t b_lo, bool first, int ks) {
 #pragma unroll
   for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
@@ -335,6 +347,7 @@ __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32
   }
 #pragma unroll
   for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
@@ -462,9 +475,11 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
               tc::tc_fence_after();
               const uint32_t sh = smem_u32(stages + (size_t)s * kRStageBytes), sl = sh + kTileBytes;
               if (half == 0) {   // B_v[P, R] = A_v[P, :] . GR[R, :]
-                issue_chunk4(acc, sh, sl, smem_u32(res_ptr(res, 0, 0, kc)), smem_u32(res_ptr(res, 0, 1, kc)), kc == 0);
+                issue_chunk4(acc, sh, sl, smem_u32(res_ptr(res, 0, 0, kc)), smem_u32(res_ptr(res, 0, 1, kc)), kc == 0,
+                             chunk_steps(kc, a.n));
               } else {           // C_v[P, R] = GW[P, :] . U2_v[R, :]
-                issue_chunk4(acc, smem_u32(res_ptr(res, 1, 0, kc)), smem_u32(res_ptr(res, 1, 1, kc)), sh, sl, kc == 0);
+                issue_chunk4(acc, smem_u32(res_ptr(res, 1, 0, kc)), smem_u32(res_ptr(res, 1, 1, kc)), sh, sl, kc == 0,
+                             chunk_steps(kc, a.n));
               }
               tc::mma_commit(&bar->empty[s]);
             }
@@ -484,6 +499,238 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
   if (warp == 1) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================
+// Pair variant of the fused kernel: two CTAs on neighbouring SMs share every MMA
+// (tcgen05 cta_group::2, M = 256 over the pair, N = 128).  A work unit is (batch b,
+// a pair of 128-row P tiles, one 128-column R tile); each CTA owns one P tile (its
+// A_v / G_wP^T rows, its TMEM rows of B_v and C_v, its rows of D) and loads HALF of
+// the shared R-side operand (G_Rq or U2_v rows R0 + 64 rank .. +64).  Per SM every
+// MMA reads 128 + 64 operand rows from shared memory instead of 128 + 128, and the
+// copies into shared memory shrink by the same quarter.  The even CTA issues the
+// MMAs; both CTAs' copies of a stage complete on the even CTA's `full` barrier, the
+// MMA commits arrive on both CTAs' `empty` / `acc_full` barriers, and both CTAs'
+// epilogue warps release an accumulator buffer on the even CTA's `acc_empty`.
+// An odd P-tile count leaves the odd CTA of the last pair on rows >= N (loaded as
+// zeros, never written).
+// ============================================================================
+constexpr int kPStages = 4;
+constexpr int kPATile = kTile * kChunk * 2;               // 128 rows x 64 K, FP16: 16 KB
+constexpr int kPBTile = (kTile / 2) * kChunk * 2;         // 64 rows: 8 KB
+constexpr int kPStageBytes = 2 * kPATile + 2 * kPBTile;   // A hi/lo + B-half hi/lo: 48 KB
+constexpr uint32_t kPairIdesc = tc::idesc_f16_f32(2 * kTile, kTile);
+
+struct PairBarriers {
+  uint64_t full[kPStages];    // even CTA: both CTAs' copies of a stage have landed
+  uint64_t empty[kPStages];   // each CTA: the pair's MMAs are done with its copy of a stage
+  uint64_t acc_full[2];       // each CTA: B_v and C_v of an accumulator buffer are complete
+  uint64_t acc_empty[2];      // even CTA: the 8 epilogue warps of the pair have read a buffer
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ void issue_chunk_pair(uint32_t acc, uint32_t st, bool first, int ks) {
+  const uint32_t a_hi = st, a_lo = st + kPATile, b_hi = st + 2 * kPATile, b_lo = b_hi + kPBTile;
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
+    const uint32_t off = k * 32;
+    tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kPairIdesc,
+                     (first && k == 0) ? 0u : 1u);
+    tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kPairIdesc, 1u);
+  }
+#pragma unroll
+  for (int k = 0; k < kChunk / 16; ++k) {
+    if (k >= ks) break;
+    const uint32_t off = k * 32;
+    tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kPairIdesc, 1u);
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
+    k_sox_bcd_pair(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                   const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
+                   const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
+                   const __grid_constant__ CUtensorMap tmU_hi, const __grid_constant__ CUtensorMap tmU_lo,
+                   BcdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  PairBarriers *bar = reinterpret_cast<PairBarriers *>(smem + kPStages * kPStageBytes);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = tc::cluster_ctarank();   // 0: the CTA that issues the pair's MMAs
+  const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int tP = (a.N + kTile - 1) / kTile;
+  const int tPP = (tP + 1) / 2;
+  const long long units_per_b = (long long)tPP * tP;
+  const long long total = (long long)a.batch * units_per_b;
+  const int nk = a.Kp / kChunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_empty[b], 8);
+    }
+    tc::mbar_init(&bar->drain, 1);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc_pair(&bar->tmem_base, 512);
+    tc::tmem_relinquish_pair();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA_hi); tc::prefetch_tmap(&tmA_lo); tc::prefetch_tmap(&tmGR_hi);
+    tc::prefetch_tmap(&tmGR_lo); tc::prefetch_tmap(&tmGW_hi); tc::prefetch_tmap(&tmGW_lo);
+    tc::prefetch_tmap(&tmU_hi); tc::prefetch_tmap(&tmU_lo);
+  }
+  // both CTAs' barriers initialised (and TMEM allocated) before either CTA touches the other's
+  tc::tc_fence_before();
+  tc::cluster_sync();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+  const uint32_t full0 = tc::mapa_shared(tc::smem_u32(&bar->full[0]), 0);
+  const uint32_t acc_empty0 = tc::mapa_shared(tc::smem_u32(&bar->acc_empty[0]), 0);
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    if (lane == 0) {
+      long long it = 0;
+      for (long long u = pair; u < total && !*abort; u += npairs) {
+        const int b = (int)(u / units_per_b);
+        const int r = (int)(u % units_per_b);
+        const int P0 = (2 * (r / tP) + (int)rank) * kTile;
+        const int R0 = (r % tP) * kTile + (int)rank * (kTile / 2);
+        for (int v = a.v0; v < a.v1 && !*abort; ++v) {
+          for (int half = 0; half < 2; ++half) {
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kPStages);
+              const uint32_t ph = (uint32_t)((it / kPStages) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+              if (rank == 0) tc::mbar_arrive_expect_tx(&bar->full[s], 2 * kPStageBytes);
+              const uint32_t fb = full0 + (uint32_t)s * 8u;
+              uint8_t *st = smem + (size_t)s * kPStageBytes;
+              const int x = kc * kChunk;
+              if (half == 0) {   // B_v = A_v . GR^T
+                tc::tma_load_3d_pair(st, &tmA_hi, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d_pair(st + kPATile, &tmA_lo, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d_pair(st + 2 * kPATile, &tmGR_hi, fb, x, R0, b);
+                tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmGR_lo, fb, x, R0, b);
+              } else {           // C_v = G_wP^T . U2_v^T
+                tc::tma_load_3d_pair(st, &tmGW_hi, fb, x, P0, b);
+                tc::tma_load_3d_pair(st + kPATile, &tmGW_lo, fb, x, P0, b);
+                tc::tma_load_3d_pair(st + 2 * kPATile, &tmU_hi, fb, x, R0, v);
+                tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmU_lo, fb, x, R0, v);
+              }
+            }
+          }
+        }
+      }
+      // wind down (even CTA): every stage issued by either CTA has landed
+      if (rank == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+          long long last = it - 1 - ((it - 1 - s) % kPStages + kPStages) % kPStages;
+          if (last >= 0 && last < it) {
+            const uint32_t ph = (uint32_t)((last / kPStages) & 1);
+            for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (even CTA) ----------------
+    if (lane == 0 && rank == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long u = pair; u < total && ok && !*abort; u += npairs) {
+        for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t acc = tmem + buf * 256 + half * 128;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kPStages);
+              const uint32_t ph = (uint32_t)((it / kPStages) & 1);
+              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              issue_chunk_pair(acc, tc::smem_u32(smem + (size_t)s * kPStageBytes), kc == 0, chunk_steps(kc, a.n));
+              tc::mma_commit_pair_mc(&bar->empty[s], 3);
+            }
+          }
+          if (ok) tc::mma_commit_pair_mc(&bar->acc_full[buf], 3);
+        }
+      }
+      // all MMAs complete before TMEM is released
+      tc::mma_commit_pair(&bar->drain);
+      for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    // ---------------- epilogue (both CTAs): D[P, R] += B_v * C_v in registers ----------------
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;          // P offset inside this CTA's tile
+    long long acc_it = 0;
+    for (long long u = pair; u < total && !*abort; u += npairs) {
+      const int b = (int)(u / units_per_b);
+      const int r = (int)(u % units_per_b);
+      const int P0 = (2 * (r / tP) + (int)rank) * kTile, R0 = (r % tP) * kTile;
+      float d[kTile];
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
+      bool ok = true;
+      for (int v = a.v0; v < a.v1; ++v, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        ok = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
+#pragma unroll
+        for (int c = 0; c < kTile; c += 16) {
+          float bv[16], cv[16];
+          tc::tmem_ld_32x32b_x16(base + c, bv);
+          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_cluster(acc_empty0 + (uint32_t)buf * 8u);
+      }
+      if (!ok) break;
+      const int P = P0 + row;
+      if (P < a.N) {
+        const float rs = a.row_scale[(long long)b * a.N + P];
+        float *out = a.Dt + (long long)b * a.N * a.ldD + P;
+#pragma unroll
+        for (int j = 0; j < kTile; ++j) {
+          const int R = R0 + j;
+          if (R < a.N) out[(long long)R * a.ldD] = d[j] * rs * a.col_scale[(long long)b * a.N + R];
+        }
+      }
+    }
+  }
+  // neither CTA leaves (or frees TMEM) while the other may still read its shared memory
+  // or arrive on its barriers
+  __syncwarp();
+  tc::tc_fence_before();
+  tc::cluster_sync();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc_pair(tmem, 512);
   }
 }
 
@@ -576,6 +823,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const long long per_b = (long long)tM * tN;
   const long long total = per_b * a.batch;
   const int nk = a.Kp / kChunk;
+  const int kv = (a.K > 0 && a.K < a.Kp) ? a.K : a.Kp;   // valid K (the rest is zero padding)
 
   setup_barriers(bar, kGemmEpi);
   if (warp == 1) {
@@ -640,7 +888,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
           if (!ok) break;
           tc::tc_fence_after();
-          issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0);
+          issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, kv));
           tc::mma_commit(&bar->empty[s]);
         }
         if (ok) tc::mma_commit(&bar->acc_full[buf]);
@@ -1132,6 +1380,32 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(Barriers)
 
 size_t res_smem_bytes() { return (size_t)kResBytes + kRStages * kRStageBytes + sizeof(ResBarriers) + 1024; }
 
+size_t pair_smem_bytes() { return (size_t)kPStages * kPStageBytes + sizeof(PairBarriers) + 1024; }
+
+// How many CTA pairs of the pair kernel fit on the device at once (queried once per device).
+cudaError_t pair_capacity(int *pairs) {
+  static std::atomic<int> cache[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int c = cache[dev & 63].load();
+  if (c > 0) {
+    *pairs = c;
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(kBcdThreads, 1, 1);
+  cfg.dynamicSmemBytes = pair_smem_bytes();
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, k_sox_bcd_pair, &cfg);
+  if (e != cudaSuccess) return e;
+  if (n < 1) return cudaErrorInvalidConfiguration;
+  cache[dev & 63].store(n);
+  *pairs = n;
+  return cudaSuccess;
+}
+
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int grid, cudaStream_t s, int variant) {
   BcdArgs a = args;
   a.v1 = (a.v1 <= 0 || a.v1 > a.n) ? a.n : a.v1;
@@ -1142,6 +1416,20 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     if (e != cudaSuccess) return e;
     k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                maps[5], maps[6], maps[7], a);
+    return cudaGetLastError();
+  }
+  if (variant == kBcdPair) {
+    static std::atomic<unsigned long long> pattr{0};
+    cudaError_t e = set_smem_once(k_sox_bcd_pair, (int)pair_smem_bytes(), pattr);
+    if (e != cudaSuccess) return e;
+    int pairs = 0;
+    e = pair_capacity(&pairs);
+    if (e != cudaSuccess) return e;
+    const int tP = (a.N + kTile - 1) / kTile;
+    const long long units = (long long)a.batch * ((tP + 1) / 2) * tP;
+    const int g = 2 * (int)std::max<long long>(1, std::min<long long>(units, pairs));
+    k_sox_bcd_pair<<<g, kBcdThreads, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
+                                                            maps[10], maps[11], a);
     return cudaGetLastError();
   }
   static std::atomic<unsigned long long> attr{0};

@@ -12,6 +12,8 @@ namespace sox {
 enum { kStoreSplit = 1, kStoreSplitGroup = 2, kStoreF32 = 3 };
 
 struct BcdArgs {
+  // K extent Kp (a multiple of 64): n valid columns, then zeros; the MMAs of the last
+  // 64-wide chunk stop after ceil(n / 16) 16-wide steps in total
   int n = 0, N = 0, Kp = 0, batch = 0;
   int v0 = 0, v1 = 0;                // the v sum runs over [v0, v1) (launch_sox_bcd_tc: v1 <= 0 means n)
   long long spin_limit = 0;
@@ -26,6 +28,7 @@ struct BcdArgs {
 // TMA stores (maps 4 and 5 of launch_gemm_f16x2, see make_tmap_f16_store4d).
 struct GemmTcArgs {
   int M = 0, Ncols = 0, Kp = 0, batch = 1;
+  int K = 0;   // valid K (operand columns >= K are zero; MMAs stop there); 0 = Kp
   int batchA_shared = 0, batchB_shared = 0;
   int mode = kStoreSplit;
   const float *out_scale = nullptr;   // kStoreSplit: one power of two per batch
@@ -66,8 +69,11 @@ bool make_tmap_f16_store4d(CUtensorMap *map, const void *base, uint64_t group, u
 bool make_tmap_f32_store3d(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint64_t batch,
                            uint64_t ld, uint64_t batch_stride, std::string *err);
 // Variants of the fused kernel: G_R / G_wP^T resident in shared memory for the whole
-// (spin, tau) batch (Kp <= 128 only), or streamed with A_v and U2_v.
-enum { kBcdResident = 1, kBcdStreamed = 2 };
+// (spin, tau) batch (Kp <= 128 only), streamed with A_v and U2_v, or streamed on CTA
+// pairs (cta_group::2; the grid is then the device's pair capacity, `grid` is ignored).
+// maps: 0/1 A hi/lo, 2/3 G_Rq hi/lo, 4/5 G_wP^T hi/lo, 6/7 U2 hi/lo (boxes 64 x 128); the
+// pair variant reads 8/9 G_Rq hi/lo and 10/11 U2 hi/lo with 64 x 64 boxes instead of 2/3, 6/7.
+enum { kBcdResident = 1, kBcdStreamed = 2, kBcdPair = 3 };
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant);
 // maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);

@@ -60,12 +60,16 @@ Geometry geometry(sox_handle h, int n, int N, int T, int S, bool two) {
 }
 
 
-// Fused-kernel variant for this shape: the handle's cached choice, else (outside
-// a stream capture, with autotuning on) each candidate is launched twice on the
-// call's own data and the faster second launch wins.  The kernel is a pure
-// function of its inputs, so the extra launches only cost time.
+// Fused-kernel variant for this shape: the handle's forced choice, its cached choice, else
+// (outside a stream capture, with autotuning on) each candidate is launched twice on the
+// call's own data and the faster second launch wins.  The kernel is a pure function of
+// its inputs, so the extra launches only cost time.
 Status tune_bcd(sox_handle h, const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int *variant) {
   const int dflt = a.Kp <= 128 ? kBcdResident : kBcdStreamed;
+  if (h->variant != SOX_KERNEL_AUTO) {
+    *variant = (h->variant == kBcdResident && a.Kp > 128) ? kBcdStreamed : h->variant;
+    return Status::ok();
+  }
   const std::string key = "bcd:" + std::to_string(a.n) + ":" + std::to_string(a.N) + ":" + std::to_string(a.batch) +
                           ":" + std::to_string(grid);
   auto it = h->tuned.find(key);
@@ -77,7 +81,7 @@ Status tune_bcd(sox_handle h, const CUtensorMap *maps, const BcdArgs &a, int gri
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SOX_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   if (!h->autotune || cap != cudaStreamCaptureStatusNone) return Status::ok();
-  const int cands[2] = {kBcdResident, kBcdStreamed};
+  const int cands[3] = {kBcdResident, kBcdStreamed, kBcdPair};
   float best = 0.f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SOX_CUDA_TRY(cudaEventCreate(&e0));
@@ -167,7 +171,7 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
   }
 
   // ---- tensor maps of the per-chunk buffers (fixed addresses, reused per chunk) ----
-  CUtensorMap bcd[8], agemm[6];
+  CUtensorMap bcd[12], agemm[6];
   if (!make_tmap_f16_3d(&bcd[0], Ah, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
       !make_tmap_f16_3d(&bcd[1], Al, Kp, NR, (uint64_t)Bc * n, 64, 128, &err) ||
       !make_tmap_f16_3d(&bcd[2], GRh, Kp, NR, Bc, 64, 128, &err) ||
@@ -176,6 +180,10 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       !make_tmap_f16_3d(&bcd[5], GWl, Kp, NR, Bc, 64, 128, &err) ||
       !make_tmap_f16_3d(&bcd[6], U2h, Kp, NR, n, 64, 128, &err) ||
       !make_tmap_f16_3d(&bcd[7], U2l, Kp, NR, n, 64, 128, &err) ||
+      !make_tmap_f16_3d(&bcd[8], GRh, Kp, NR, Bc, 64, 64, &err) ||
+      !make_tmap_f16_3d(&bcd[9], GRl, Kp, NR, Bc, 64, 64, &err) ||
+      !make_tmap_f16_3d(&bcd[10], U2h, Kp, NR, n, 64, 64, &err) ||
+      !make_tmap_f16_3d(&bcd[11], U2l, Kp, NR, n, 64, 64, &err) ||
       !make_tmap_f16_3d(&agemm[0], Gmh, Kp, RG, Bc, 64, 128, &err) ||
       !make_tmap_f16_3d(&agemm[1], Gml, Kp, RG, Bc, 64, 128, &err) ||
       !make_tmap_f16_3d(&agemm[2], U1h, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
@@ -212,7 +220,7 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       ProfScope ps(h, "A_tc", s, 2);
       launch_prep_gminus(G, n, T, bc, Kp, Gmh, Gml, gsc, osc, b0, RG, s);
       GemmTcArgs ga;
-      ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.batch = bc;
+      ga.M = n; ga.Ncols = NR * Kp; ga.Kp = Kp; ga.K = n; ga.batch = bc;
       ga.batchA_shared = 0; ga.batchB_shared = 1;
       // n <= 128: one tile holds all (v, q) of each P -> exact per-P scale; else the a-priori bound
       ga.mode = exact_a ? kStoreSplitGroup : kStoreSplit;
