@@ -358,7 +358,7 @@ class MoleculeCase(Case):
         self.wts = torch.from_numpy(self.wts_h).to(dev)
         self.Pi = torch.empty(w.n_spin, w.N, w.N, dtype=torch.float64, device=dev)
         self.W0 = torch.empty(1, w.N, w.N, dtype=torch.float64, device=dev)
-        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.h = _kernel_handle(pkg, prec, dev.index or 0)
         if tau_shard is not None:
             from paper_2412_18829_gb300 import sharding
 
@@ -519,7 +519,7 @@ class SolidCase(Case):
         self.G, self.X, self.V, self.Wd, self.Tf, self.Ti = (to(a) for a in (w.G, w.X, w.V, Wd, Tf, Ti))
         self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
         self.S = torch.empty_like(self.G)
-        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.h = _kernel_handle(pkg, prec, dev.index or 0)
         _apply_v_shard(self, pkg, w.n)
         self.config = {"workload": w.name, "nk": list(w.nk), "n": w.n, "N": w.N, "n_tau": w.n_tau,
                        "n_omega": self.nO, "beta": w.beta, "precision": prec,
@@ -619,7 +619,7 @@ class DynMoleculeCase(Case):
         self.Tf, self.Ti = to(Tf), to(Ti)
         self.host = (w.G, w.X, w.V, Wd, Tf, Ti)
         self.S = torch.empty_like(self.G)
-        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.h = _kernel_handle(pkg, prec, dev.index or 0)
         _apply_v_shard(self, pkg, w.n)
         self.config = {"workload": self.name, "n": w.n, "N": w.N, "n_tau": w.n_tau, "n_spin": w.n_spin,
                        "n_omega": self.nO, "beta": w.beta, "precision": prec,
@@ -698,7 +698,7 @@ class BatchCase(Case):
         self.dtype = "f16x2+f32acc,f64" if prec == "f16x2" else "f64"
         self.hot = "sox_bcd_tc" if prec == "f16x2" else "sox_bcd"
         self.units = 1.0 / world
-        self.h = pkg.Handle(prec, device=dev.index or 0)
+        self.h = _kernel_handle(pkg, prec, dev.index or 0)
         self.inst = []
         for i in self.mine:
             w = synth.c4_instance(i)
@@ -847,6 +847,16 @@ class BatchCase(Case):
             out["adjoint_split_vs_fp64_max_rel_dX"] = max(rel(e["dX"], e["dX64"]) for e in sub)
             out["adjoint_split_vs_fp64_max_rel_dV"] = max(rel(e["dV"], e["dV64"]) for e in sub)
         return out
+
+
+KERNEL = "auto"   # --kernel: the split path's fused-kernel variant on every handle the bench opens
+
+
+def _kernel_handle(pkg, prec, device):
+    h = pkg.Handle(prec, device=device)
+    if prec == "f16x2" and KERNEL != "auto":
+        pkg.sox_set_kernel_variant(h, KERNEL)
+    return h
 
 
 def make_case(args, torch, pkg, dev, stream, rank, world, dist_mod=None):
@@ -1031,6 +1041,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.precision == "f16x2":
+        line["config"]["fused_kernel"] = KERNEL if KERNEL != "auto" else "autotuned per shape"
     if world == 1 and not args.skip_cpu_baseline:
         if isinstance(case, BatchCase):
             v, dt, desc = batch_oracle_sample()
@@ -1071,7 +1083,7 @@ def profile_case(args):
         p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
         G, X, V = (dev(a) for a in (w.G, w.X, w.V))
         out = torch.empty_like(G)
-        with pkg.Handle(prec) as h:
+        with _kernel_handle(pkg, prec, 0) as h:
             for _ in range(2):
                 pkg.sox_sigma(h, p, G, X, V, out)
             pkg.sox_check_device(h)
@@ -1086,7 +1098,7 @@ def profile_case(args):
         d = torch.ones(1, dtype=torch.float64, device="cuda")
         phi = torch.empty(1, dtype=torch.float64, device="cuda")
         S, dG, dX, out = torch.empty_like(G), torch.empty_like(G), torch.empty_like(X), torch.empty_like(V)
-        with pkg.Handle(prec) as h:
+        with _kernel_handle(pkg, prec, 0) as h:
             for _ in range(2):
                 if kind == "batch":
                     pkg.phi_sox(h, p, G, X, V, tw, phi, S)
@@ -1113,7 +1125,7 @@ def profile_case(args):
         G, X, V, W = (cast(a) for a in (w.G, w.X, w.V, Wd))
         F, I = (dev(np.asarray(a, dtype=complex)) for a in (Tf, Ti))
         out = torch.empty_like(G)
-        with pkg.Handle(prec) as h:
+        with _kernel_handle(pkg, prec, 0) as h:
             pkg.sosex_dynamic_sigma(h, p, G, X, V, W, F, I, 2 * M + 1, out)
             pkg.sox_check_device(h)
     else:   # wdyn
@@ -1154,6 +1166,8 @@ def main():
     ap.add_argument("--mesh", default="3,3,3", help="solid workload: k-mesh (default 3,3,3)")
     ap.add_argument("--rpa-w", action="store_true",
                     help="solid workload: build W_d(i Omega) from G on the GPU inside every step")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "resident", "streamed", "pair"],
+                    help="fused B/C/D kernel variant of the split path (auto: timed per shape)")
     ap.add_argument("--variant", default="sosex", choices=["sosex", "2sosex", "g3w2"],
                     help="screened workload: SOSEX, 2SOSEX or G3W2 with W(0)")
     ap.add_argument("--profile-case", default=None,
@@ -1162,6 +1176,8 @@ def main():
     ap.add_argument("--profile-tau", type=int, default=None, help="tau points of the profile case")
     ap.add_argument("--profile-sizes", default=None, help="profile case sizes n,N (solid, dynmol)")
     args = ap.parse_args()
+    global KERNEL
+    KERNEL = args.kernel
     if args.profile_case:
         profile_case(args)
         return

@@ -205,24 +205,30 @@ struct AdjBcArgs {
 
 __device__ __forceinline__ long long wind_down(long long cap) { return cap > (1LL << 20) ? cap : (1LL << 20); }
 
-// 3 x ks MMAs of one 64-wide K chunk (ks 16-wide steps; the last chunk of the n-long
+// 3 x KS MMAs of one 64-wide K chunk (KS 16-wide steps; the last chunk of the n-long
 // contraction stops at its first all-padding step)
-__device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            bool first, int ks) {
+template <int KS>
+__device__ __forceinline__ void issue_split_ks(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                               uint32_t b_lo, bool first) {
 #pragma unroll
-  for (int k = 0; k < kC / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
 #pragma unroll
-  for (int k = 0; k < kC / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
+}
+__device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+                                            bool first, int ks) {
+  if (ks >= kC / 16) issue_split_ks<kC / 16>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else if (ks == 3) issue_split_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else if (ks == 2) issue_split_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else issue_split_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first);
 }
 
 __device__ __forceinline__ uint32_t pack2(__half a, __half b) {

@@ -87,23 +87,30 @@ __device__ __forceinline__ uint8_t *stage_ptr(uint8_t *smem, int s, int t) {
 // The small cross terms go first: the tensor core truncates every accumulation
 // step to FP32 (round toward zero), and each step into a large accumulator
 // costs up to one ulp, so the large hi*hi steps are kept last and fewest.
-__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first, int ks) {
+template <int KS>
+__device__ __forceinline__ void issue_chunk_ks(uint32_t acc, uint8_t *st, bool first) {
   const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kTileBytes;
   const uint32_t b_hi = a_hi + 2 * kTileBytes, b_lo = a_hi + 3 * kTileBytes;
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
+}
+// one straight-line MMA sequence per step count (a loop with a runtime exit between the
+// MMAs slowed the issuing thread down measurably)
+__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first, int ks) {
+  if (ks >= 4) issue_chunk_ks<4>(acc, st, first);
+  else if (ks == 3) issue_chunk_ks<3>(acc, st, first);
+  else if (ks == 2) issue_chunk_ks<2>(acc, st, first);
+  else issue_chunk_ks<1>(acc, st, first);
 }
 
 // 16-wide K steps of chunk kc when the contraction has K valid elements (the rest of the
@@ -335,22 +342,28 @@ __device__ __forceinline__ uint8_t *res_ptr(uint8_t *res, int op, int part, int 
   return res + (size_t)((op * 2 + part) * 2 + kc) * kTileBytes;
 }
 
-__device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                             uint32_t b_lo, bool first, int ks) {
+template <int KS>
+__device__ __forceinline__ void issue_chunk4_ks(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                                uint32_t b_lo, bool first) {
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
                 (first && k == 0) ? 0u : 1u);
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
   }
+}
+__device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                             uint32_t b_lo, bool first, int ks) {
+  if (ks >= 4) issue_chunk4_ks<4>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else if (ks == 3) issue_chunk4_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else if (ks == 2) issue_chunk4_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first);
+  else issue_chunk4_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first);
 }
 
 __global__ void __launch_bounds__(kBcdThreads, 1)
@@ -532,22 +545,27 @@ struct PairBarriers {
   int abort;
 };
 
-__device__ __forceinline__ void issue_chunk_pair(uint32_t acc, uint32_t st, bool first, int ks) {
+template <int KS>
+__device__ __forceinline__ void issue_chunk_pair_ks(uint32_t acc, uint32_t st, bool first) {
   const uint32_t a_hi = st, a_lo = st + kPATile, b_hi = st + 2 * kPATile, b_lo = b_hi + kPBTile;
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kPairIdesc,
                      (first && k == 0) ? 0u : 1u);
     tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kPairIdesc, 1u);
   }
 #pragma unroll
-  for (int k = 0; k < kChunk / 16; ++k) {
-    if (k >= ks) break;
+  for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
     tc::mma_f16_pair(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kPairIdesc, 1u);
   }
+}
+__device__ __forceinline__ void issue_chunk_pair(uint32_t acc, uint32_t st, bool first, int ks) {
+  if (ks >= 4) issue_chunk_pair_ks<4>(acc, st, first);
+  else if (ks == 3) issue_chunk_pair_ks<3>(acc, st, first);
+  else if (ks == 2) issue_chunk_pair_ks<2>(acc, st, first);
+  else issue_chunk_pair_ks<1>(acc, st, first);
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
