@@ -399,14 +399,6 @@ int sox_create(sox_handle *out, const sox_options *opt) {
     delete h;
     return SOX_ERR_CUDA;
   }
-  if (h->precision == SOX_PREC_F16X2 && !sox::tc_prepare(h).good()) {
-    cudaGetLastError();
-    sox::tc_release(h);
-    cudaFree(h->d_status);
-    delete h;
-    if (prev >= 0 && prev != o.device) cudaSetDevice(prev);
-    return SOX_ERR_CUDA;
-  }
   if (prev >= 0 && prev != o.device) cudaSetDevice(prev);
   *out = h;
   return SOX_OK;
@@ -1088,8 +1080,7 @@ int sox_sigma_batch_plan(sox_handle h, int count, const sox_problem *probs, cons
     }
     if (ec != cudaSuccess) return {SOX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec)};
     plan->graph = g;
-    // node priorities: the fused kernels' CTAs take SMs ahead of the concurrent FP64 blocks
-    SOX_CUDA_TRY(cudaGraphInstantiate(&plan->exec, plan->graph, cudaGraphInstantiateFlagUseNodePriority));
+    SOX_CUDA_TRY(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
     return Status::ok();
   }();
   if (cs) cudaStreamDestroy(cs);

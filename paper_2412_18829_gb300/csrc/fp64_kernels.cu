@@ -76,74 +76,6 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(GemmF64 g) {
   }
 }
 
-// The same GEMM in blocks of 128 threads (64 x 32 tiles) capped at 128 registers a thread:
-// one block fits on an SM beside a fused tensor-core CTA (their registers and shared memory
-// add up to the SM's), so the FP64 projections of one tau chunk run on the FP64 pipes while
-// the previous chunk's tensor-core kernel holds the SMs.
-constexpr int LM = 64, LN = 32, LT = 128;
-
-__device__ __forceinline__ void load_tile_lite(double (*s)[LM + 1], int rows, const double *base, long long rs,
-                                               long long ks, int r0, int k0, int R, int K, int tid) {
-  for (int e = tid; e < rows * TK; e += LT) {
-    int r, k;
-    if (ks == 1) {
-      r = e / TK;
-      k = e % TK;
-    } else {
-      r = e % rows;
-      k = e / rows;
-    }
-    const int gr = r0 + r, gk = k0 + k;
-    s[k][r] = (gr < R && gk < K) ? base[gr * rs + gk * ks] : 0.0;
-  }
-}
-
-__global__ void __launch_bounds__(LT, 4) k_gemm_f64_lite(GemmF64 g) {
-  __shared__ double sa[TK][LM + 1];
-  __shared__ double sb[TK][LM + 1];   // LN rows used
-  const int tid = threadIdx.x;
-  const int tx = tid % 8, ty = tid / 8;
-  const int i0 = blockIdx.y * LM, j0 = blockIdx.x * LN;
-  const long long b = blockIdx.z;
-  if (g.skip && g.skip[b]) return;
-  const double *A = g.A + b * g.sA;
-  const double *B = g.B + b * g.sB;
-  double *C = g.C + b * g.sC;
-  double acc[4][4] = {};
-  for (int k0 = 0; k0 < g.K; k0 += TK) {
-    load_tile_lite(sa, LM, A, g.ai, g.ak, i0, k0, g.M, g.K, tid);
-    load_tile_lite(sb, LN, B, g.bj, g.bk, j0, k0, g.Nc, g.K, tid);
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-      double a[4], bb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sa[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = sb[kk][tx + 8 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gi = i0 + ty + 16 * i;
-    if (gi >= g.M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gj = j0 + tx + 8 * j;
-      if (gj >= g.Nc) continue;
-      double *c = C + gi * g.ci + gj * g.cj;
-      double v = g.alpha * acc[i][j];
-      if (g.beta != 0.0) v = fma(g.beta, *c, v);
-      *c = v;
-    }
-  }
-}
-
 __global__ void k_pair_products(const double *X, double *Y, int N, int n) {
   long long total = (long long)N * n * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -442,12 +374,6 @@ void launch_gemm_f64(const GemmF64 &g, cudaStream_t s) {
   if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return;
   dim3 grid((g.Nc + TN - 1) / TN, (g.M + TM - 1) / TM, g.batch);
   k_gemm_f64<<<grid, NT, 0, s>>>(g);
-}
-
-void launch_gemm_f64_lite(const GemmF64 &g, cudaStream_t s) {
-  if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return;
-  dim3 grid((g.Nc + LN - 1) / LN, (g.M + LM - 1) / LM, g.batch);
-  k_gemm_f64_lite<<<grid, LT, 0, s>>>(g);
 }
 
 void launch_pair_products_f64(const double *X, double *Y, int N, int n, cudaStream_t s) {

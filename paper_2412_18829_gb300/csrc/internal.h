@@ -28,10 +28,6 @@ struct sox_context {
   bool autotune = true;      // time the fused-kernel variants on the first call per shape
   int variant = 0;           // SOX_KERNEL_*: 0 = autotune, else the forced fused-kernel variant
   std::map<std::string, int> tuned;  // shape key -> chosen variant
-  // split path: second stream and events of the tau-chunk pipeline (created on first use)
-  cudaStream_t side = nullptr;
-  cudaEvent_t pipe_ev[6] = {};
-  int prio_high = 0;         // the device's greatest stream priority (fused-kernel launches)
   std::string last_error;
   // launch accounting (sox_profile_enable / sox_profile_read)
   bool prof = false;
@@ -129,8 +125,6 @@ struct GemmF64 {
   const int *skip = nullptr;  // optional per-batch flags: batch b is not computed when skip[b] != 0
 };
 void launch_gemm_f64(const GemmF64 &g, cudaStream_t s);
-// the same in 128-thread blocks that fit beside a fused tensor-core CTA on one SM
-void launch_gemm_f64_lite(const GemmF64 &g, cudaStream_t s);
 
 // Y[Q][q][s] = X[Q][q] * X[Q][s]   (pair products feeding the mixed THC tensor)
 void launch_pair_products_f64(const double *X, double *Y, int N, int n, cudaStream_t s);

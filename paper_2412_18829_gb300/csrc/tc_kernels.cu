@@ -1424,29 +1424,7 @@ cudaError_t pair_capacity(int *pairs) {
   return cudaSuccess;
 }
 
-// <<<>>> launch, or with a scheduling priority (cudaLaunchAttributePriority) when prio != 0
-template <class... KArgs, class... Args>
-cudaError_t launch_prio(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, int prio,
-                        Args... args) {
-  if (prio == 0) {
-    k<<<grid, block, smem, s>>>(args...);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(block, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributePriority;
-  at[0].val.priority = prio;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k, args...);
-}
-
-cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int grid, cudaStream_t s, int variant,
-                              int priority) {
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int grid, cudaStream_t s, int variant) {
   BcdArgs a = args;
   a.v1 = (a.v1 <= 0 || a.v1 > a.n) ? a.n : a.v1;
   a.v0 = a.v0 < 0 ? 0 : (a.v0 > a.v1 ? a.v1 : a.v0);
@@ -1454,8 +1432,9 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     static std::atomic<unsigned long long> rattr{0};
     const cudaError_t e = set_smem_once(k_sox_bcd_tc_res, (int)res_smem_bytes(), rattr);
     if (e != cudaSuccess) return e;
-    return launch_prio(k_sox_bcd_tc_res, grid, kBcdThreads, res_smem_bytes(), s, priority, maps[0], maps[1], maps[2],
-                       maps[3], maps[4], maps[5], maps[6], maps[7], a);
+    k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+                                                               maps[5], maps[6], maps[7], a);
+    return cudaGetLastError();
   }
   if (variant == kBcdPair) {
     static std::atomic<unsigned long long> pattr{0};
@@ -1467,14 +1446,16 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     const int tP = (a.N + kTile - 1) / kTile;
     const long long units = (long long)a.batch * ((tP + 1) / 2) * tP;
     const int g = 2 * (int)std::max<long long>(1, std::min<long long>(units, pairs));
-    return launch_prio(k_sox_bcd_pair, g, kBcdThreads, pair_smem_bytes(), s, priority, maps[0], maps[1], maps[8],
-                       maps[9], maps[4], maps[5], maps[10], maps[11], a);
+    k_sox_bcd_pair<<<g, kBcdThreads, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
+                                                            maps[10], maps[11], a);
+    return cudaGetLastError();
   }
   static std::atomic<unsigned long long> attr{0};
   const cudaError_t e = set_smem_once(k_sox_bcd_tc, (int)tc_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  return launch_prio(k_sox_bcd_tc, grid, kBcdThreads, tc_smem_bytes(), s, priority, maps[0], maps[1], maps[2], maps[3],
-                     maps[4], maps[5], maps[6], maps[7], a);
+  k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+                                                        maps[6], maps[7], a);
+  return cudaGetLastError();
 }
 
 size_t gemm_smem_bytes() { return (size_t)kGStages * kStageBytes + kStageOut + sizeof(Barriers) + 1024; }

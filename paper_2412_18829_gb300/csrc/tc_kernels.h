@@ -74,10 +74,7 @@ bool make_tmap_f32_store3d(CUtensorMap *map, const void *base, uint64_t cols, ui
 // maps: 0/1 A hi/lo, 2/3 G_Rq hi/lo, 4/5 G_wP^T hi/lo, 6/7 U2 hi/lo (boxes 64 x 128); the
 // pair variant reads 8/9 G_Rq hi/lo and 10/11 U2 hi/lo with 64 x 64 boxes instead of 2/3, 6/7.
 enum { kBcdResident = 1, kBcdStreamed = 2, kBcdPair = 3 };
-// priority != 0: launched with that scheduling priority (cudaLaunchAttributePriority), so that
-// its CTAs take SMs ahead of pending blocks of concurrent lower-priority kernels
-cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant,
-                              int priority = 0);
+cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant);
 // maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);
 // rows of batch b come from alt_src instead of src when use_alt[b] != 0 (both optional)

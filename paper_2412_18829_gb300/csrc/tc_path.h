@@ -7,6 +7,4 @@ size_t tc_sigma_bytes(sox_handle h, int n, int N, int T, int S, bool two_slots);
 Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const double *X,
                 const double *U1, const double *U2, double *Sigma, Arena &ar, cudaStream_t s);
 void tc_release(sox_handle h);
-// second stream and events of the tau-chunk pipeline (idempotent)
-Status tc_prepare(sox_handle h);
 }  // namespace sox
