@@ -89,3 +89,30 @@ def test_variant_mid_size_molecule_sampled_tau(env, variant):
         ref = sox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[s, 0], taus=taus, dtype=np.float64)
         err, scale = check(out[s, 0, taus], ref, "f16x2", f"{variant} mid-size spin {s}")
         print(f"{variant} mid-size spin {s}: max|dSigma| {err:.3e} Ha (max|Sigma| {scale:.3e})")
+
+
+def test_sigma_is_bitwise_independent_of_tau_chunking(env):
+    """Every (spin, tau) batch is computed with its own scales, so Sigma is bit-identical for
+    one batch per chunk, the default chunking and a non-default caller stream, and meets the
+    oracle."""
+    torch, pkg, _ = env
+    w = synth.molecule(24, 30, 260, 10, 100.0, n_spin=2)
+    ref = sox.sox_sigma(w.X, w.V, w.G).real
+    outs = []
+    for limit, use_stream in ((0, False), (1, False), (0, True)):
+        with pkg.Handle("f16x2", workspace_limit=limit) as h:
+            pkg.sox_set_kernel_variant(h, "streamed")
+            p = pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta)
+            G, X, V = to_dev(torch, w.G, w.X, w.V)
+            S = torch.full_like(G, float("nan"))
+            if use_stream:
+                st = torch.cuda.Stream()
+                with torch.cuda.stream(st):
+                    pkg.sox_sigma(h, p, G, X, V, S, stream=st.cuda_stream)
+                st.synchronize()
+            else:
+                pkg.sox_sigma(h, p, G, X, V, S)
+            pkg.sox_check_device(h)
+            outs.append(S.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    check(outs[0], ref, "f16x2", "tau chunking", n=w.n, N=w.N)
