@@ -178,7 +178,6 @@ constexpr int kSt = 3;
 constexpr int kProdThreads = 640, kProdEpi = 512;
 constexpr int kRegLaunch = 96, kRegCtl = 56, kRegEpi = 104;
 static_assert(128 * kRegCtl + 512 * kRegEpi <= kProdThreads * kRegLaunch, "register split above the launch total");
-constexpr uint32_t kIdesc = tc::idesc_f16_f32(kT, kT);
 
 struct PBars {
   uint64_t full[kSt];
@@ -209,26 +208,26 @@ __device__ __forceinline__ long long wind_down(long long cap) { return cap > (1L
 // contraction stops at its first all-padding step)
 template <int KS>
 __device__ __forceinline__ void issue_split_ks(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                               uint32_t b_lo, bool first) {
+                                               uint32_t b_lo, bool first, uint32_t idesc) {
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), idesc,
                 (first && k == 0) ? 0u : 1u);
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 }
 __device__ __forceinline__ void issue_split(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            bool first, int ks) {
-  if (ks >= kC / 16) issue_split_ks<kC / 16>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else if (ks == 3) issue_split_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else if (ks == 2) issue_split_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else issue_split_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first);
+                                            bool first, int ks, uint32_t idesc) {
+  if (ks >= kC / 16) issue_split_ks<kC / 16>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else if (ks == 3) issue_split_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else if (ks == 2) issue_split_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else issue_split_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
 }
 
 __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
@@ -418,6 +417,10 @@ __global__ void __launch_bounds__(kProdThreads, 1)
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
+        // N = the R tile's valid width rounded up to 16 (the last tile stops at N)
+        const int R0 = (int)((t % tiles_per_b) % tP) * kT;
+        const int wR = a.N - R0 >= kT ? kT : ((a.N - R0 + 15) & ~15);
+        const uint32_t idesc = tc::idesc_f16_f32(kT, wR);
         for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
               tc::tc_fence_after();
               const uint32_t st = smem_u32(smem + (size_t)s * kStageB);
               issue_split(acc, st, st + kTileB, st + 2 * kTileB, st + 3 * kTileB, kc == 0,
-                          a.n - kc * kC >= kC ? kC / 16 : (a.n - kc * kC + 15) / 16);
+                          a.n - kc * kC >= kC ? kC / 16 : (a.n - kc * kC + 15) / 16, idesc);
               tc::mma_commit(&bar->empty[s]);
             }
           }

@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tM = (a.M + kT - 1) / kT, tN = (a.Ncols + kT - 1) / kT;
   const long long chunks = (long long)a.kc_inner * a.nk_outer;
   const long long items = (long long)a.batch * tM * tN * a.ksplit;
-  const uint32_t idesc = tc::idesc_f16_f32(kT, kT) | ((uint32_t)a.a.mn_major << 15) | ((uint32_t)a.b.mn_major << 16);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -205,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (long long t = blockIdx.x; t < items && ok && !*abort; t += gridDim.x) {
         const Item w = item_of(a, t, tM, tN, chunks);
+        // N = the tile's valid columns rounded up to 16: no MMA over the zero rows of B past Ncols
+        const int wN = a.Ncols - w.j0 >= kT ? kT : ((a.Ncols - w.j0 + 15) & ~15);
+        const uint32_t idesc = tc::idesc_f16_f32(kT, wN) | ((uint32_t)a.a.mn_major << 15) |
+                               ((uint32_t)a.b.mn_major << 16);
         for (long long w0 = w.c0; w0 < w.c1 && ok; w0 += a.window, ++acc_it) {
           const long long w1 = w0 + a.window < w.c1 ? w0 + a.window : w.c1;
           const int buf = (int)(acc_it & 1);

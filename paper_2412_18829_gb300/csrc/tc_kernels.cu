@@ -88,29 +88,38 @@ __device__ __forceinline__ uint8_t *stage_ptr(uint8_t *smem, int s, int t) {
 // step to FP32 (round toward zero), and each step into a large accumulator
 // costs up to one ulp, so the large hi*hi steps are kept last and fewest.
 template <int KS>
-__device__ __forceinline__ void issue_chunk_ks(uint32_t acc, uint8_t *st, bool first) {
+__device__ __forceinline__ void issue_chunk_ks(uint32_t acc, uint8_t *st, bool first, uint32_t idesc) {
   const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kTileBytes;
   const uint32_t b_hi = a_hi + 2 * kTileBytes, b_lo = a_hi + 3 * kTileBytes;
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), idesc,
                 (first && k == 0) ? 0u : 1u);
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 }
 // one straight-line MMA sequence per step count (a loop with a runtime exit between the
 // MMAs slowed the issuing thread down measurably)
-__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first, int ks) {
-  if (ks >= 4) issue_chunk_ks<4>(acc, st, first);
-  else if (ks == 3) issue_chunk_ks<3>(acc, st, first);
-  else if (ks == 2) issue_chunk_ks<2>(acc, st, first);
-  else issue_chunk_ks<1>(acc, st, first);
+__device__ __forceinline__ void issue_chunk(uint32_t acc, uint8_t *st, bool first, int ks,
+                                            uint32_t idesc = kIdesc) {
+  if (ks >= 4) issue_chunk_ks<4>(acc, st, first, idesc);
+  else if (ks == 3) issue_chunk_ks<3>(acc, st, first, idesc);
+  else if (ks == 2) issue_chunk_ks<2>(acc, st, first, idesc);
+  else issue_chunk_ks<1>(acc, st, first, idesc);
+}
+
+// Instruction descriptor of a 128-row tile whose N side holds `cols` valid columns from
+// `c0` on: N = the valid width rounded up to 16 (at most 128), so no MMA runs over the
+// zero rows past the end of the operand
+__device__ __forceinline__ uint32_t idesc_cols(int c0, int cols) {
+  const int w = cols - c0 >= kTile ? kTile : ((cols - c0 + 15) & ~15);
+  return tc::idesc_f16_f32(kTile, w < 16 ? 16 : w);
 }
 
 // 16-wide K steps of chunk kc when the contraction has K valid elements (the rest of the
@@ -279,6 +288,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
+        const uint32_t idesc = idesc_cols((int)((t % tiles_per_b) % tP) * kTile, a.N);   // R side
         for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
               ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
-              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, a.n));
+              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, a.n), idesc);
               tc::mma_commit(&bar->empty[s]);
             }
           }
@@ -344,26 +354,26 @@ __device__ __forceinline__ uint8_t *res_ptr(uint8_t *res, int op, int part, int 
 
 template <int KS>
 __device__ __forceinline__ void issue_chunk4_ks(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                                uint32_t b_lo, bool first) {
+                                                uint32_t b_lo, bool first, uint32_t idesc) {
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), kIdesc,
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), idesc,
                 (first && k == 0) ? 0u : 1u);
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     const uint32_t off = k * 32;
-    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), kIdesc, 1u);
+    tc::mma_f16(acc, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), idesc, 1u);
   }
 }
 __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
-                                             uint32_t b_lo, bool first, int ks) {
-  if (ks >= 4) issue_chunk4_ks<4>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else if (ks == 3) issue_chunk4_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else if (ks == 2) issue_chunk4_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first);
-  else issue_chunk4_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first);
+                                             uint32_t b_lo, bool first, int ks, uint32_t idesc) {
+  if (ks >= 4) issue_chunk4_ks<4>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else if (ks == 3) issue_chunk4_ks<3>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else if (ks == 2) issue_chunk4_ks<2>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
+  else issue_chunk4_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
 }
 
 __global__ void __launch_bounds__(kBcdThreads, 1)
@@ -470,6 +480,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       long long it = 0, acc_it = 0, tt = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++tt) {
+        const uint32_t idesc = idesc_cols((int)((t % tiles_per_b) % tP) * kTile, a.N);   // R side
         ok = tc::mbar_wait(&bar->res_full, (uint32_t)(tt & 1), a.spin_limit, abort, a.status, 32);
         if (!ok) break;
         for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
@@ -489,10 +500,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
               const uint32_t sh = smem_u32(stages + (size_t)s * kRStageBytes), sl = sh + kTileBytes;
               if (half == 0) {   // B_v[P, R] = A_v[P, :] . GR[R, :]
                 issue_chunk4(acc, sh, sl, smem_u32(res_ptr(res, 0, 0, kc)), smem_u32(res_ptr(res, 0, 1, kc)), kc == 0,
-                             chunk_steps(kc, a.n));
+                             chunk_steps(kc, a.n), idesc);
               } else {           // C_v[P, R] = GW[P, :] . U2_v[R, :]
                 issue_chunk4(acc, smem_u32(res_ptr(res, 1, 0, kc)), smem_u32(res_ptr(res, 1, 1, kc)), sh, sl, kc == 0,
-                             chunk_steps(kc, a.n));
+                             chunk_steps(kc, a.n), idesc);
               }
               tc::mma_commit(&bar->empty[s]);
             }
