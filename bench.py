@@ -15,6 +15,12 @@ A step is one full build through the C ABI.  Workloads (``--workload``):
   SOX(W(0), v) per step.
 * c3 dynamically screened SOSEX of a solid (3x3x3 k-mesh, n=26, N=300, 60 tau),
   W_d from a synthetic single-pole form (or the GPU RPA with --rpa-w).
+* c1d dynamically screened SOSEX of the mid-size molecule (c1's shapes, 79
+  bosonic frequencies, W_d from the single-pole form).
+
+``--kernel resident|streamed|pair`` forces the split path's fused B/C/D kernel
+variant (default: timed per shape); ``--shard tau|v|replicas`` chooses how N > 1
+ranks share the work.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead (a bounded sample per step, scaled to builds/s).
@@ -24,8 +30,9 @@ process, one GPU, a few GB on the device): KIND is molecule (sox_sigma twice at
 n=120, N=600, 2 spins), screened (sox_sigma twice at n=250, N=2000), batch
 (phi_sox + phi_sox_grad_G twice at the batch's largest instance, n=298, N=1788),
 adjoint (phi_sox_backward twice at that instance; --profile-sizes n,N for others), solid (sosex_dynamic_sigma at
-the 3x3x3 solid's shapes; --mesh and --profile-sizes n,N change them) or wdyn
-(sox_w_dynamic at the solid's shapes); --profile-tau sets the tau points.
+the 3x3x3 solid's shapes; --mesh and --profile-sizes n,N change them), dynmol
+(sosex_dynamic_sigma at the mid-size molecule's shapes) or wdyn (sox_w_dynamic at
+the solid's shapes); --profile-tau sets the tau points, --kernel the fused variant.
 """
 from __future__ import annotations
 

@@ -143,7 +143,7 @@ __device__ __forceinline__ void load_operand(uint8_t *dst, const CUtensorMap *hi
 }
 
 template <int TN>
-__global__ void __maxnreg__(200)
+__global__ void __maxnreg__(192)
     k_gemm_mn(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
               const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
               const __grid_constant__ CUtensorMap tmC, GemmMnArgs a) {
@@ -287,12 +287,12 @@ __global__ void __maxnreg__(200)
         tc::tc_fence_after();
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * TN + h * HC;
 #pragma unroll
-        for (int c = 0; c < HC; c += 32) {
-          float v[32];
-          tc::tmem_ld_32x32b_x32(base + c, v);
+        for (int c = 0; c < HC; c += 16) {
+          float v[16];
+          tc::tmem_ld_32x32b_x16(base + c, v);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[c + j] += v[j];
+          for (int j = 0; j < 16; ++j) sum[c + j] += v[j];
         }
         tc::tc_fence_before();
         tc::mbar_arrive(&bar->acc_empty[buf]);
