@@ -143,7 +143,7 @@ __device__ __forceinline__ void load_operand(uint8_t *dst, const CUtensorMap *hi
 }
 
 template <int TN>
-__global__ void __maxnreg__(192)
+__global__ void __maxnreg__(168)
     k_gemm_mn(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
               const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
               const __grid_constant__ CUtensorMap tmC, GemmMnArgs a) {
