@@ -24,27 +24,18 @@ using tc::smem_u32;
 
 namespace {
 
-constexpr int kT = 128;                       // tile rows (M)
+constexpr int kT = 128;                       // tile rows / columns
 constexpr int kC = 64;                        // K elements per chunk
-constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of a 128-row operand for one chunk
-constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column quarter of an output tile
+constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of one operand for one chunk
+constexpr int kStageBytes = 4 * kPart;        // A hi, A lo, B hi, B lo
+constexpr int kStages = 3;
+constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column half of an output tile
 constexpr int kThreads = 320;                 // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpi = 256;
-constexpr int kMaxStages = 3;
-
-// Tile geometry by output-tile width TN (128 or 256 columns): a 128 x TN MMA costs the
-// tensor pipe less per flop at TN = 256, at the price of two pipeline stages instead of three.
-template <int TN>
-struct Geo {
-  static constexpr int kBPart = TN * kC * 2;                 // hi (or lo) of the B operand, one chunk
-  static constexpr int kStageBytes = 2 * kPart + 2 * kBPart;   // A hi, A lo, B hi, B lo
-  static constexpr int kStages = TN == 128 ? 3 : 2;
-  static constexpr int kSmem = kStages * kStageBytes + kOutBytes;
-};
 
 struct Bars {
-  uint64_t full[kMaxStages];
-  uint64_t empty[kMaxStages];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
   uint64_t drain;
@@ -108,7 +99,6 @@ struct Item {
 
 // work item t -> (batch, split, tile row, tile column); tile columns run fastest so
 // items in flight together share their A chunks through L2
-template <int TN>
 __device__ __forceinline__ Item item_of(const GemmMnArgs &a, long long t, int tM, int tN, long long total) {
   Item it;
   const long long tiles = (long long)tM * tN;
@@ -118,42 +108,35 @@ __device__ __forceinline__ Item item_of(const GemmMnArgs &a, long long t, int tM
   const long long ks = r / tiles;
   r %= tiles;
   it.i0 = (int)(r / tN) * kT;
-  it.j0 = (int)(r % tN) * TN;
+  it.j0 = (int)(r % tN) * kT;
   it.c0 = ks * a.cps;
   it.c1 = it.c0 + a.cps < total ? it.c0 + a.cps : total;
   return it;
 }
 
-// One operand chunk (hi and lo, `rows` = 128 or 256 rows along MN) into dst: MN-major as 64-row
-// boxes (the MN blocks 8 KB apart), K-major as 128-row boxes
 __device__ __forceinline__ void load_operand(uint8_t *dst, const CUtensorMap *hi, const CUtensorMap *lo, uint64_t *bar,
-                                             int mn, int row0, int k0, int z, int rows) {
-  const int part = rows * kC * 2;
+                                             int mn, int row0, int k0, int z) {
   if (mn) {
-    for (int i = 0; i < rows / 64; ++i) {
-      tc::tma_load_3d(dst + i * (kPart / 2), hi, bar, row0 + 64 * i, k0, z);
-      tc::tma_load_3d(dst + part + i * (kPart / 2), lo, bar, row0 + 64 * i, k0, z);
-    }
+    tc::tma_load_3d(dst, hi, bar, row0, k0, z);
+    tc::tma_load_3d(dst + kPart / 2, hi, bar, row0 + 64, k0, z);
+    tc::tma_load_3d(dst + kPart, lo, bar, row0, k0, z);
+    tc::tma_load_3d(dst + kPart + kPart / 2, lo, bar, row0 + 64, k0, z);
   } else {
-    for (int i = 0; i < rows / 128; ++i) {
-      tc::tma_load_3d(dst + i * kPart, hi, bar, k0, row0 + 128 * i, z);
-      tc::tma_load_3d(dst + part + i * kPart, lo, bar, k0, row0 + 128 * i, z);
-    }
+    tc::tma_load_3d(dst, hi, bar, k0, row0, z);
+    tc::tma_load_3d(dst + kPart, lo, bar, k0, row0, z);
   }
 }
 
-template <int TN>
-__global__ void __maxnreg__(168)
+__global__ void __launch_bounds__(kThreads, 1)
     k_gemm_mn(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
               const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
               const __grid_constant__ CUtensorMap tmC, GemmMnArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int kStages = Geo<TN>::kStages, kStageBytes = Geo<TN>::kStageBytes, kBPart = Geo<TN>::kBPart;
   uint8_t *stage_out = smem + kStages * kStageBytes;
   Bars *bar = reinterpret_cast<Bars *>(stage_out + kOutBytes);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tM = (a.M + kT - 1) / kT, tN = (a.Ncols + TN - 1) / TN;
+  const int tM = (a.M + kT - 1) / kT, tN = (a.Ncols + kT - 1) / kT;
   const long long chunks = (long long)a.kc_inner * a.nk_outer;
   const long long items = (long long)a.batch * tM * tN * a.ksplit;
 
@@ -171,7 +154,7 @@ __global__ void __maxnreg__(168)
     tc::fence_barrier_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(&bar->tmem_base, 2 * TN);
+    tc::tmem_alloc(&bar->tmem_base, 256);
     tc::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
@@ -190,7 +173,7 @@ __global__ void __maxnreg__(168)
     if (lane == 0) {
       long long it = 0;
       for (long long t = blockIdx.x; t < items && !*abort; t += gridDim.x) {
-        const Item w = item_of<TN>(a, t, tM, tN, chunks);
+        const Item w = item_of(a, t, tM, tN, chunks);
         for (long long c = w.c0; c < w.c1 && !*abort; ++c, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
@@ -200,9 +183,9 @@ __global__ void __maxnreg__(168)
           const int k0 = (int)(c % a.kc_inner) * kC;
           uint8_t *st = smem + (size_t)s * kStageBytes;
           load_operand(st, &tmA_hi, &tmA_lo, &bar->full[s], a.a.mn_major, w.i0, k0,
-                       (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk), kT);
+                       (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
           load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, &bar->full[s], a.b.mn_major, w.j0, k0,
-                       (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk), TN);
+                       (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
         }
       }
       for (int s = 0; s < kStages; ++s) {   // every copy issued has landed before the CTA exits
@@ -220,9 +203,9 @@ __global__ void __maxnreg__(168)
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < items && ok && !*abort; t += gridDim.x) {
-        const Item w = item_of<TN>(a, t, tM, tN, chunks);
+        const Item w = item_of(a, t, tM, tN, chunks);
         // N = the tile's valid columns rounded up to 16: no MMA over the zero rows of B past Ncols
-        const int wN = a.Ncols - w.j0 >= TN ? TN : ((a.Ncols - w.j0 + 15) & ~15);
+        const int wN = a.Ncols - w.j0 >= kT ? kT : ((a.Ncols - w.j0 + 15) & ~15);
         const uint32_t idesc = tc::idesc_f16_f32(kT, wN) | ((uint32_t)a.a.mn_major << 15) |
                                ((uint32_t)a.b.mn_major << 16);
         for (long long w0 = w.c0; w0 < w.c1 && ok; w0 += a.window, ++acc_it) {
@@ -232,7 +215,7 @@ __global__ void __maxnreg__(168)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          const uint32_t acc = tmem + buf * TN;
+          const uint32_t acc = tmem + buf * kT;
           for (long long c = w0; c < w1; ++c, ++it) {
             const int s = (int)(it % kStages);
             const uint32_t ph = (uint32_t)((it / kStages) & 1);
@@ -240,7 +223,7 @@ __global__ void __maxnreg__(168)
             if (!ok) break;
             tc::tc_fence_after();
             const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
-            const uint32_t ahi = st, alo = st + kPart, bhi = st + 2 * kPart, blo = bhi + kBPart;
+            const uint32_t ahi = st, alo = st + kPart, bhi = st + 2 * kPart, blo = st + 3 * kPart;
             const bool first = (c == w0);
             // the small cross terms first, the large hi*hi steps last (truncating accumulation)
 #pragma unroll
@@ -262,8 +245,7 @@ __global__ void __maxnreg__(168)
       }
     }
   } else {
-    // ---------------- epilogue: 8 warps, lane quarter q, column half h (TN/2 columns) ----------------
-    constexpr int HC = TN / 2;
+    // ---------------- epilogue: 8 warps, lane quarter q, 64-column half h ----------------
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const int h = (warp - 2) >> 2;
@@ -272,10 +254,10 @@ __global__ void __maxnreg__(168)
     long long acc_it = 0;
     bool live = true;
     for (long long t = blockIdx.x; t < items && live; t += gridDim.x) {
-      const Item w = item_of<TN>(a, t, tM, tN, chunks);
-      float sum[HC];
+      const Item w = item_of(a, t, tM, tN, chunks);
+      float sum[64];
 #pragma unroll
-      for (int j = 0; j < HC; ++j) sum[j] = 0.f;
+      for (int j = 0; j < 64; ++j) sum[j] = 0.f;
       for (long long w0 = w.c0; w0 < w.c1; w0 += a.window, ++acc_it) {
         const int buf = (int)(acc_it & 1);
         const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
@@ -285,38 +267,36 @@ __global__ void __maxnreg__(168)
           break;
         }
         tc::tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * TN + h * HC;
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * kT + h * 64;
 #pragma unroll
-        for (int c = 0; c < HC; c += 16) {
-          float v[16];
-          tc::tmem_ld_32x32b_x16(base + c, v);
+        for (int c = 0; c < 64; c += 32) {
+          float v[32];
+          tc::tmem_ld_32x32b_x32(base + c, v);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sum[c + j] += v[j];
+          for (int j = 0; j < 32; ++j) sum[c + j] += v[j];
         }
         tc::tc_fence_before();
         tc::mbar_arrive(&bar->acc_empty[buf]);
       }
       if (!live) break;
-      // scaled tile -> TMA, one 64-column quarter at a time through the staging buffer (two
-      // 128-byte-swizzled boxes of 128 rows x 32 columns); the warps holding it fill it
+      // scaled tile -> TMA, one 64-column half at a time through the staging buffer (two
+      // 128-byte-swizzled boxes of 128 rows x 32 columns); the half-h warps fill it
       float *tile = reinterpret_cast<float *>(stage_out);
       const bool add = a.accumulate || a.ksplit > 1;
 #pragma unroll
-      for (int qq = 0; qq < TN / 64; ++qq) {
-        if (w.j0 + qq * 64 >= a.Ncols) continue;   // uniform over the epilogue warps
+      for (int half = 0; half < 2; ++half) {
         if (storer) bulk_wait_read();   // the previous stores have read the staging buffer
         epi_sync();
-        if (h == qq / (HC / 64)) {
-          const int c0 = (qq % (HC / 64)) * 64;
+        if (h == half) {
 #pragma unroll
           for (int c = 0; c < 64; c += 32) {
             float *box = tile + (c / 32) * (kT * 32) + row * 32;
 #pragma unroll
             for (int t4 = 0; t4 < 8; ++t4)
               *reinterpret_cast<float4 *>(box + ((t4 ^ (row & 7)) * 4)) =
-                  make_float4(sum[c0 + c + 4 * t4] * alpha, sum[c0 + c + 4 * t4 + 1] * alpha,
-                              sum[c0 + c + 4 * t4 + 2] * alpha, sum[c0 + c + 4 * t4 + 3] * alpha);
+                  make_float4(sum[c + 4 * t4] * alpha, sum[c + 4 * t4 + 1] * alpha, sum[c + 4 * t4 + 2] * alpha,
+                              sum[c + 4 * t4 + 3] * alpha);
           }
         }
         fence_proxy_async_smem();
@@ -324,7 +304,7 @@ __global__ void __maxnreg__(168)
         if (storer) {
 #pragma unroll
           for (int bx = 0; bx < 2; ++bx) {
-            const int x = w.j0 + qq * 64 + 32 * bx;
+            const int x = w.j0 + half * 64 + 32 * bx;
             if (x < a.Ncols) {
               if (add)
                 tma_reduce_add_3d(&tmC, stage_out + (size_t)bx * (kT * 128), x, w.i0, w.b);
@@ -341,7 +321,7 @@ __global__ void __maxnreg__(168)
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 2 * TN);
+    tc::tmem_dealloc(tmem, 256);
   }
 }
 
@@ -445,8 +425,7 @@ int blocks_for_units(long long units) {
 }  // namespace
 
 int plan_gemm_mn(GemmMnArgs &a, int sms, int max_ksplit) {
-  const int TN = a.Ncols > kT ? 2 * kT : kT;   // the wide tile whenever one narrow tile does not hold the row
-  const long long tiles = (long long)a.batch * ((a.M + kT - 1) / kT) * ((a.Ncols + TN - 1) / TN);
+  const long long tiles = (long long)a.batch * ((a.M + kT - 1) / kT) * ((a.Ncols + kT - 1) / kT);
   const long long chunks = (long long)a.kc_inner * a.nk_outer;
   const long long windows = (chunks + a.window - 1) / a.window;
   // Items run in waves of `sms` (one CTA per SM, items strided over the grid); each costs
@@ -473,19 +452,11 @@ int plan_gemm_mn(GemmMnArgs &a, int sms, int max_ksplit) {
 }
 
 cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int grid, cudaStream_t s) {
-  if (a.Ncols > kT) {
-    static std::atomic<unsigned long long> attr{0};
-    const int bytes = Geo<2 * kT>::kSmem + (int)sizeof(Bars) + 1024;
-    const cudaError_t e = set_smem_once(k_gemm_mn<2 * kT>, bytes, attr);
-    if (e != cudaSuccess) return e;
-    k_gemm_mn<2 * kT><<<grid, kThreads, bytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a);
-    return cudaGetLastError();
-  }
   static std::atomic<unsigned long long> attr{0};
-  const int bytes = Geo<kT>::kSmem + (int)sizeof(Bars) + 1024;
-  const cudaError_t e = set_smem_once(k_gemm_mn<kT>, bytes, attr);
+  const int bytes = kStages * kStageBytes + kOutBytes + (int)sizeof(Bars) + 1024;
+  const cudaError_t e = set_smem_once(k_gemm_mn, bytes, attr);
   if (e != cudaSuccess) return e;
-  k_gemm_mn<kT><<<grid, kThreads, bytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a);
+  k_gemm_mn<<<grid, kThreads, bytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a);
   return cudaGetLastError();
 }
 
