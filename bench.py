@@ -723,23 +723,36 @@ class BatchCase(Case):
             self.inst.append(d)
         self.config = {"workload": self.name, "instances": len(sizes), "n": sizes, "N": "6n", "n_tau": 120,
                        "beta": 100.0, "precision": prec, "instances_on_rank0": self.mine if rank == 0 else None,
-                       "step": ("per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept "
-                                "Sigma) + phi_sox_backward (dPhi/dX, dPhi/dV)") if backward else
-                               "per instance: phi_sox (Phi and Sigma) + phi_sox_grad_G (dPhi/dG from the kept Sigma)"}
+                       "step": ("phi_sox_batch (Phi and Sigma of every instance, one persistent fused launch "
+                                "per tau chunk), then per instance phi_sox_grad_G (dPhi/dG from the kept Sigma) + "
+                                "phi_sox_backward (dPhi/dX, dPhi/dV)") if backward else
+                               ("phi_sox_batch (Phi and Sigma of every instance), then per instance "
+                                "phi_sox_grad_G (dPhi/dG from the kept Sigma)")}
 
-    def _one(self, h, d, G, X, V, wt, S, phi, dG, dX=None, dV=None):
-        self.pkg.phi_sox(h, d["p"], G, X, V, wt, phi, S, self.stream)
+    def _forward(self, h, G, X, V, wt, S, phi):
+        """Phi and Sigma of every instance on this rank in one batched call: one persistent
+        fused launch per tau chunk over all instances (split precision)."""
+        self.pkg.phi_sox_batch(h, [d["p"] for d in self.inst], G, X, V, wt, phi, S, self.stream)
+
+    def _rest(self, h, d, G, X, V, wt, S, dG, dX=None, dV=None):
         self.pkg.phi_sox_grad_G(h, d["p"], S, wt, d["dphi"], dG, self.stream)
         if dX is not None:   # dPhi/dX and dPhi/dV by the adjoint of the THC chain
             self.pkg.phi_sox_backward(h, d["p"], G, X, V, wt, d["dphi"], None, dX, dV, self.stream)
 
     def step(self):
-        for d in self.inst:
-            self._one(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["phi"], d["dG"],
-                      d["dX"] if self.backward else None, d["dV"] if self.backward else None)
+        if not self.inst:
+            return
+        ins = self.inst
+        self._forward(self.h, [d["G"] for d in ins], [d["X"] for d in ins], [d["V"] for d in ins],
+                      [d["wt"] for d in ins], [d["S"] for d in ins], [d["phi"] for d in ins])
+        for d in ins:
+            self._rest(self.h, d, d["G"], d["X"], d["V"], d["wt"], d["S"], d["dG"],
+                       d["dX"] if self.backward else None, d["dV"] if self.backward else None)
 
     def e2e_step(self):
         h2d = d2h = 0
+        if not self.inst:
+            return h2d, d2h
         for d in self.inst:
             if "Gh" not in d:
                 pin = lambda a: self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
@@ -749,9 +762,13 @@ class BatchCase(Case):
             if "dXh" not in d:
                 d["dXh"] = self.torch.from_numpy(np.empty_like(d["w"].X)).pin_memory().numpy()
                 d["dVh"] = self.torch.from_numpy(np.empty_like(d["w"].V)).pin_memory().numpy()
-            bw = self.backward
-            self._one(self.h, d, d["Gh"], d["Xh"], d["Vh"], d["wt_h"], d["Sh"], d["phih"], d["dGh"],
-                      d["dXh"] if bw else None, d["dVh"] if bw else None)
+        ins = self.inst
+        self._forward(self.h, [d["Gh"] for d in ins], [d["Xh"] for d in ins], [d["Vh"] for d in ins],
+                      [d["wt_h"] for d in ins], [d["Sh"] for d in ins], [d["phih"] for d in ins])
+        bw = self.backward
+        for d in ins:
+            self._rest(self.h, d, d["Gh"], d["Xh"], d["Vh"], d["wt_h"], d["Sh"], d["dGh"],
+                       d["dXh"] if bw else None, d["dVh"] if bw else None)
             h2d += d["Gh"].nbytes + d["Xh"].nbytes + d["Vh"].nbytes + 2 * d["wt_h"].nbytes + d["Sh"].nbytes
             d2h += d["Sh"].nbytes + d["phih"].nbytes + d["dGh"].nbytes
             if bw:

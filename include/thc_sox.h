@@ -316,12 +316,26 @@ SOX_API int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double
 SOX_API int sox_w_dynamic(sox_handle h, const sox_problem *p, const double *G, const double *X,
                           const double *V, const double *T_fwd, int n_omega, double *Wd, void *stream);
 
-/* Batch of independent bare-SOX problems (uneven sizes allowed), one launch
- * sequence on one stream.  probs, G, X, V, Sigma are HOST arrays of `count`
- * entries; the tensors they point to follow the single-problem rules. */
+/* Batch of independent bare-SOX problems (uneven sizes allowed), Eq. (sox) for each, on one
+ * stream.  probs, G, X, V, Sigma are HOST arrays of `count` entries; the tensors they point
+ * to follow the single-problem rules (device or host memory).  On an SOX_PREC_F16X2 handle a
+ * batch of molecules shares its tau chunks: each instance's chain up to A and after D runs on
+ * its own, and the fused B / C / Hadamard step of one chunk of every instance is ONE
+ * persistent launch over all their (P, R) tiles, largest instances first (at most 24
+ * instances per launch; more take several).  Solids and FP64 handles run the instances in
+ * turn.  The first instance that fails stops the batch (its index in sox_last_error). */
 SOX_API int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs,
                     const double *const *G, const double *const *X, const double *const *V,
                     double *const *Sigma, void *stream);
+
+
+/* phi_sox over a batch of molecules (Sec. II C chain; Phi := 1/4 sum_j w_j Tr[Sigma(tau_j)
+ * G(-tau_j)] per spin), with the batched fused launch of sox_sigma_batch.  w[i] [n_tau],
+ * phi[i] [n_spin] and Sigma[i] (required) are the arrays of phi_sox for instance i.  Solids:
+ * SOX_ERR_UNSUPPORTED. */
+SOX_API int phi_sox_batch(sox_handle h, int count, const sox_problem *probs, const double *const *G,
+                          const double *const *X, const double *const *V, const double *const *w,
+                          double *const *phi, double *const *Sigma, void *stream);
 
 /* Batch plan (graph form of sox_sigma_batch).  The whole launch sequence of
  * `count` independent bare-SOX problems (uneven sizes allowed; molecules,

@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     lib,
     phi_sox,
     phi_sox_backward,
+    phi_sox_batch,
     phi_sox_grad_G,
     problem,
     sosex_dynamic_sigma,

@@ -67,6 +67,7 @@ _SIGS = {
     "sox_w_dynamic": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _I, _P, _P], _I),
     "sox_sigma_batch": ([_P, _I, ctypes.POINTER(sox_problem), ctypes.POINTER(_P), ctypes.POINTER(_P),
                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P], _I),
+    "phi_sox_batch": ([_P, _I, ctypes.POINTER(sox_problem)] + [ctypes.POINTER(_P)] * 6 + [_P], _I),
     "sox_sigma_fp64_noalloc": ([ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
     "g3w2_static_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P], _I),
     "sosex2_static_sigma": ([_P, ctypes.POINTER(sox_problem), _P, _P, _P, _P, _P, _P], _I),
@@ -314,6 +315,16 @@ def sox_sigma_batch(h: Handle, probs, G, X, V, Sigma, stream=None):
     arr = (sox_problem * count)(*probs)
     mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
     h.check(lib().sox_sigma_batch(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(Sigma), _stream(stream)))
+
+
+def phi_sox_batch(h: Handle, probs, G, X, V, w, phi, Sigma, stream=None):
+    """phi_sox for a batch of molecules: lists of per-instance tensors (w [n_tau], phi
+    [n_spin], Sigma as for phi_sox); one persistent fused launch per tau chunk on a
+    split-precision handle."""
+    count = len(probs)
+    arr = (sox_problem * count)(*probs)
+    mk = lambda ts: (_P * count)(*[_ptr(t) for t in ts])  # noqa: E731
+    h.check(lib().phi_sox_batch(h.ptr, count, arr, mk(G), mk(X), mk(V), mk(w), mk(phi), mk(Sigma), _stream(stream)))
 
 
 class SigmaBatchPlan:

@@ -987,20 +987,112 @@ int sosex_dynamic_sigma(sox_handle h, const sox_problem *p, const double *G, con
   return finish(h, st);
 }
 
+// The uneven batch of molecules, with Phi per instance when w and phi are given.  Split
+// precision: every instance's chain up to A and after D runs per instance, and the fused
+// B / C / Hadamard step of one tau chunk of every instance is one persistent launch
+// (tc_sigma_batch).  FP64 (or a single instance): the instances run in turn.
+Status batch_call(sox_handle h, int count, const sox_problem *probs, const double *const *G,
+                  const double *const *X, const double *const *V, const double *const *w, double *const *phi,
+                  double *const *Sigma, void *stream) {
+  if (count < 1 || !probs || !G || !X || !V || !Sigma) return {SOX_ERR_INVALID_ARG, "bad batch arrays"};
+  const bool with_phi = (w != nullptr || phi != nullptr);
+  if (with_phi && (!w || !phi)) return {SOX_ERR_INVALID_ARG, "w and phi go together"};
+  bool solid = false;
+  for (int i = 0; i < count; ++i)
+    solid = solid || probs[i].dtype == SOX_COMPLEX128 || probs[i].nk[0] * probs[i].nk[1] * probs[i].nk[2] != 1;
+  if (solid && !with_phi) {   // solids: each instance through its own chain
+    for (int i = 0; i < count; ++i) {
+      Status st = run_sigma(h, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], stream);
+      if (!st.good()) {
+        st.msg = "instance " + std::to_string(i) + ": " + st.msg;
+        return st;
+      }
+    }
+    return Status::ok();
+  }
+  std::vector<Dims> d(count);
+  for (int i = 0; i < count; ++i) {
+    Status v = validate(&probs[i]);   // molecules (real data, one k point)
+    if (v.good() && (!G[i] || !X[i] || !V[i] || !Sigma[i] || (with_phi && (!w[i] || !phi[i]))))
+      v = {SOX_ERR_INVALID_ARG, "a required tensor pointer is NULL"};
+    if (!v.good()) {
+      v.msg = "instance " + std::to_string(i) + ": " + v.msg;
+      return v;
+    }
+    d[i] = dims_of(&probs[i]);
+  }
+  SOX_TRY(bind_device(h));
+  const bool fused = (h->precision == SOX_PREC_F16X2 && count > 1);
+  std::vector<int> n(count), N(count), T(count), S(count);
+  std::vector<Staged> sG(count), sX(count), sV(count), sw(count), sS(count), sP(count);
+  Call call(h, stream);
+  size_t part_bytes = 0, compute = 0;
+  for (int i = 0; i < count; ++i) {
+    n[i] = d[i].n; N[i] = d[i].N; T[i] = d[i].T; S[i] = d[i].S;
+    const size_t nsig = (size_t)d[i].S * d[i].T * d[i].nn();
+    SOX_TRY(call.input(G[i], nsig, &sG[i]));
+    SOX_TRY(call.input(X[i], (size_t)d[i].N * d[i].n, &sX[i]));
+    SOX_TRY(call.input(V[i], (size_t)d[i].N * d[i].N, &sV[i]));
+    SOX_TRY(call.output(Sigma[i], nsig, &sS[i]));
+    if (with_phi) {
+      SOX_TRY(call.input(w[i], (size_t)d[i].T, &sw[i]));
+      SOX_TRY(call.output(phi[i], (size_t)d[i].S, &sP[i]));
+      part_bytes += sox::aligned_bytes((size_t)d[i].S * d[i].T, 8);
+    }
+    if (!fused) compute = std::max(compute, sigma_bytes(h, d[i], false));
+  }
+  if (fused) compute = sox::tc_sigma_batch_bytes(h, count, n.data(), N.data(), T.data(), S.data());
+  Arena ar;
+  SOX_TRY(call.begin(compute + part_bytes, &ar));
+  cudaStream_t s = call.stream();
+  std::vector<double *> part(count, nullptr);
+  if (with_phi)
+    for (int i = 0; i < count; ++i) part[i] = ar.take<double>((size_t)d[i].S * d[i].T);
+  if (fused) {
+    std::vector<const double *> Gd(count), Xd(count), Vd(count);
+    std::vector<double *> Sd(count);
+    for (int i = 0; i < count; ++i) {
+      Gd[i] = sG[i].in; Xd[i] = sX[i].in; Vd[i] = sV[i].in; Sd[i] = sS[i].out;
+    }
+    Arena a = ar;
+    SOX_TRY(sox::tc_sigma_batch(h, count, n.data(), N.data(), T.data(), S.data(), Gd.data(), Xd.data(), Vd.data(),
+                                Sd.data(), a, s));
+  } else {
+    for (int i = 0; i < count; ++i) {
+      Arena a = ar;
+      Status st = sigma_any(h, d[i], sG[i].in, sX[i].in, sV[i].in, sV[i].in, sS[i].out, a, s);
+      if (!st.good()) {
+        st.msg = "instance " + std::to_string(i) + ": " + st.msg;
+        return st;
+      }
+    }
+  }
+  if (with_phi) {
+    sox::ProfScope ps(h, "phi_trace", s, 2 * count);
+    for (int i = 0; i < count; ++i) {
+      sox::launch_trace_sigma_gminus(sS[i].out, sG[i].in, d[i].n, d[i].T, d[i].S, part[i], s);
+      sox::launch_phi_finish(part[i], sw[i].in, d[i].T, d[i].S, sP[i].out, s);
+    }
+  }
+  return call.end();
+}
+
 int sox_sigma_batch(sox_handle h, int count, const sox_problem *probs, const double *const *G,
                     const double *const *X, const double *const *V, double *const *Sigma,
                     void *stream) {
   if (!h) return SOX_ERR_INVALID_ARG;
-  if (count < 0 || (count > 0 && (!probs || !G || !X || !V || !Sigma)))
-    return finish(h, {SOX_ERR_INVALID_ARG, "bad batch arrays"});
-  for (int i = 0; i < count; ++i) {
-    Status st = run_sigma(h, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], stream);
-    if (!st.good()) {
-      st.msg = "instance " + std::to_string(i) + ": " + st.msg;
-      return finish(h, st);
-    }
-  }
-  return finish(h, Status::ok());
+  if (count < 0) return finish(h, {SOX_ERR_INVALID_ARG, "bad batch arrays"});
+  if (count == 0) return finish(h, Status::ok());
+  return finish(h, batch_call(h, count, probs, G, X, V, nullptr, nullptr, Sigma, stream));
+}
+
+int phi_sox_batch(sox_handle h, int count, const sox_problem *probs, const double *const *G, const double *const *X,
+                  const double *const *V, const double *const *w, double *const *phi, double *const *Sigma,
+                  void *stream) {
+  if (!h) return SOX_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && (!w || !phi))) return finish(h, {SOX_ERR_INVALID_ARG, "bad batch arrays"});
+  if (count == 0) return finish(h, Status::ok());
+  return finish(h, batch_call(h, count, probs, G, X, V, w, phi, Sigma, stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1065,12 +1157,10 @@ int sox_sigma_batch_plan(sox_handle h, int count, const sox_problem *probs, cons
     SOX_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     // eager pass: sizes the plan's workspace for the largest instance and settles the
     // autotuned kernel choices, so that the recorded pass allocates and times nothing
-    for (int i = 0; i < count; ++i) SOX_TRY(run_sigma(plan->ih, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], cs));
+    SOX_TRY(batch_call(plan->ih, count, probs, G, X, V, nullptr, nullptr, Sigma, cs));
     SOX_CUDA_TRY(cudaStreamSynchronize(cs));
     SOX_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    Status rec = Status::ok();
-    for (int i = 0; i < count && rec.good(); ++i)
-      rec = run_sigma(plan->ih, &probs[i], G[i], X[i], V[i], V[i], Sigma[i], cs);
+    Status rec = batch_call(plan->ih, count, probs, G, X, V, nullptr, nullptr, Sigma, cs);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
     if (!rec.good()) {

@@ -326,6 +326,179 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
 }
 
 // ============================================================================
+// The streamed fused kernel over several instances at once (the uneven batch): one
+// persistent grid walks the concatenated tiles of every job; each role (TMA producer, MMA
+// issuer, epilogue) decodes the job of a tile from the table in the kernel parameters and
+// reads that job's maps, shapes and outputs.  Jobs are ordered by cost, largest first, so
+// the grid's last wave holds the cheapest tiles.
+// ============================================================================
+struct MultiTile {
+  int j, b, P0, R0;
+};
+
+__device__ __forceinline__ MultiTile multi_tile(const BcdJobs &jobs, long long t) {
+  int j = 0;
+  while (j + 1 < jobs.count && jobs.job[j + 1].unit0 <= t) ++j;
+  const BcdJob &J = jobs.job[j];
+  const int tP = (J.N + kTile - 1) / kTile;
+  const long long local = t - J.unit0;
+  const int per_b = tP * tP;
+  MultiTile m;
+  m.j = j;
+  m.b = (int)(local / per_b);
+  const int r = (int)(local % per_b);
+  m.P0 = (r / tP) * kTile;
+  m.R0 = (r % tP) * kTile;
+  return m;
+}
+
+__global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_constant__ BcdJobs jobs) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Barriers *bar = reinterpret_cast<Barriers *>(smem + kStages * kStageBytes);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long total = jobs.total;
+  const long long limit = jobs.spin_limit;
+
+  setup_barriers(bar, kEpiThreads);
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = bar->tmem_base;
+  volatile int *abort = &bar->abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      long long it = 0;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+        const MultiTile m = multi_tile(jobs, t);
+        const BcdJob &J = jobs.job[m.j];
+        const int nk = J.Kp / kChunk;
+        for (int v = J.v0; v < J.v1 && !*abort; ++v) {
+          for (int half = 0; half < 2; ++half) {
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kStages);
+              const uint32_t ph = (uint32_t)((it / kStages) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
+              tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+              const int x = kc * kChunk;
+              if (half == 0) {
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[0], &bar->full[s], x, m.P0, m.b * J.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[1], &bar->full[s], x, m.P0, m.b * J.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[2], &bar->full[s], x, m.R0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[3], &bar->full[s], x, m.R0, m.b);
+              } else {
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[4], &bar->full[s], x, m.P0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[5], &bar->full[s], x, m.P0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[6], &bar->full[s], x, m.R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[7], &bar->full[s], x, m.R0, v);
+              }
+            }
+          }
+        }
+      }
+      // wind down: every stage issued must have landed before the CTA exits
+      for (int s = 0; s < kStages; ++s) {
+        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
+        if (last >= 0 && last < it) {
+          const uint32_t ph = (uint32_t)((last / kStages) & 1);
+          for (long long i = 0; i < wind_down_limit(limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
+        const MultiTile m = multi_tile(jobs, t);
+        const BcdJob &J = jobs.job[m.j];
+        const int nk = J.Kp / kChunk;
+        const uint32_t idesc = idesc_cols(m.R0, J.N);
+        for (int v = J.v0; v < J.v1 && ok; ++v, ++acc_it) {
+          const int buf = (int)(acc_it & 1);
+          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, limit, abort, jobs.status, 2);
+          if (!ok) break;
+          tc::tc_fence_after();
+          for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t acc = tmem + buf * 256 + half * 128;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+              const int s = (int)(it % kStages);
+              const uint32_t ph = (uint32_t)((it / kStages) & 1);
+              ok = tc::mbar_wait(&bar->full[s], ph, limit, abort, jobs.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, J.n), idesc);
+              tc::mma_commit(&bar->empty[s]);
+            }
+          }
+          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+        }
+      }
+      tc::mma_commit(&bar->drain);
+      for (long long i = 0; i < wind_down_limit(limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: D[P, R] += B_v * C_v in registers ----------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    long long acc_it = 0;
+    for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      const MultiTile m = multi_tile(jobs, t);
+      const BcdJob &J = jobs.job[m.j];
+      float d[kTile];
+#pragma unroll
+      for (int j = 0; j < kTile; ++j) d[j] = 0.f;
+      bool ok = true;
+      for (int v = J.v0; v < J.v1; ++v, ++acc_it) {
+        const int buf = (int)(acc_it & 1);
+        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        ok = tc::mbar_wait(&bar->acc_full[buf], aph, limit, abort, jobs.status, 8);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * 256;
+#pragma unroll
+        for (int c = 0; c < kTile; c += 16) {
+          float bv[16], cv[16];
+          tc::tmem_ld_32x32b_x16(base + c, bv);
+          tc::tmem_ld_32x32b_x16(base + 128 + c, cv);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[c + j] = fmaf(bv[j], cv[j], d[c + j]);
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bar->acc_empty[buf]);
+      }
+      if (!ok) break;
+      const int P = m.P0 + row;
+      if (P < J.N) {
+        const float rs = J.row_scale[(long long)m.b * J.N + P];
+        float *out = J.Dt + (long long)m.b * J.N * J.ldD + P;
+#pragma unroll
+        for (int j = 0; j < kTile; ++j) {
+          const int R = m.R0 + j;
+          if (R < J.N) out[(long long)R * J.ldD] = d[j] * rs * J.col_scale[(long long)m.b * J.N + R];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// ============================================================================
 // Resident-operand variant of the fused kernel for Kp <= 128.  The per-tile
 // operands G_Rq[R-tile] and G_wP^T[P-tile] (hi/lo, all of K) stay in shared
 // memory for the whole tile (128 KB); only A_v and U2_v stream, one hi/lo chunk
@@ -1466,6 +1639,16 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
   if (e != cudaSuccess) return e;
   k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                                         maps[6], maps[7], a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sox_bcd_multi(const BcdJobs &jobs, int grid, cudaStream_t s) {
+  if (jobs.count <= 0 || jobs.count > kMaxBcdJobs) return cudaErrorInvalidValue;
+  if (jobs.total <= 0) return cudaSuccess;
+  static std::atomic<unsigned long long> attr{0};
+  const cudaError_t e = set_smem_once(k_sox_bcd_multi, (int)tc_smem_bytes(), attr);
+  if (e != cudaSuccess) return e;
+  k_sox_bcd_multi<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,26 @@ struct BcdArgs {
   long long ldD = 0;
 };
 
+// One instance's share of a multi-instance fused launch (launch_sox_bcd_multi): its eight
+// operand maps (as for launch_sox_bcd_tc, 64 x 128 boxes), its shapes and outputs, and the
+// first global work unit (128 x 128 (P, R) tile of one (spin, tau) batch) it owns.
+struct BcdJob {
+  CUtensorMap maps[8];
+  int n = 0, N = 0, Kp = 0, batch = 0, v0 = 0, v1 = 0;
+  const float *row_scale = nullptr, *col_scale = nullptr;
+  float *Dt = nullptr;
+  long long ldD = 0;
+  long long unit0 = 0;
+};
+constexpr int kMaxBcdJobs = 24;   // the table travels as a kernel parameter (< 32 KB)
+struct BcdJobs {
+  BcdJob job[kMaxBcdJobs];
+  int count = 0;
+  long long total = 0;        // work units of all jobs
+  long long spin_limit = 0;
+  int *status = nullptr;
+};
+
 // Output of the split GEMM: FP16 pair tensors [batch][M][n_groups][group] written by
 // TMA stores (maps 4 and 5 of launch_gemm_f16x2, see make_tmap_f16_store4d).
 struct GemmTcArgs {
@@ -75,6 +95,9 @@ bool make_tmap_f32_store3d(CUtensorMap *map, const void *base, uint64_t cols, ui
 // pair variant reads 8/9 G_Rq hi/lo and 10/11 U2 hi/lo with 64 x 64 boxes instead of 2/3, 6/7.
 enum { kBcdResident = 1, kBcdStreamed = 2, kBcdPair = 3 };
 cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &a, int grid, cudaStream_t s, int variant);
+// One persistent launch of the streamed fused kernel over the tiles of several instances of
+// different sizes (jobs.job[j].unit0 ascending; each job's v range already clamped).
+cudaError_t launch_sox_bcd_multi(const BcdJobs &jobs, int grid, cudaStream_t s);
 // maps: A hi/lo, B hi/lo (3-D loads), C hi/lo (4-D stores)
 cudaError_t launch_gemm_f16x2(const CUtensorMap *maps, const GemmTcArgs &a, int grid, cudaStream_t s);
 // rows of batch b come from alt_src instead of src when use_alt[b] != 0 (both optional)

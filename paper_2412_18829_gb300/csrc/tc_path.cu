@@ -9,6 +9,7 @@
 //   Sigma_tr = -sum_PR X_tR D_PR X_rP                   FP32 half-transform, FP64 final sum
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "tc_kernels.h"
 #include "tc_path.h"
@@ -253,6 +254,222 @@ Status tc_sigma(sox_handle h, int n, int N, int T, int S, const double *G, const
       // (a partial v range breaks that symmetry: then every block is computed)
       launch_backproject_sigma(X, Tm, N, n, bc, Sigma + (long long)b0 * n * n, (long long)n * n, s,
                                (two || !v_range_is_full(h, n)) ? nullptr : symf);
+    }
+  }
+  SOX_CUDA_TRY(cudaGetLastError());
+  return Status::ok();
+}
+
+// ---------------------------------------------------------------------------------------
+// The uneven batch (bare SOX of several molecules of different sizes): every instance's
+// chain up to A and after D runs per instance, and the fused B / C / Hadamard step of one tau
+// chunk of every instance runs as one persistent launch (k_sox_bcd_multi).  Instances share
+// the number of tau chunks; each chunk holds ceil(B_i / nc) of instance i's batches.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct BatchGeo {
+  int nc = 1;
+  std::vector<int> Bc;
+  size_t bytes = 0;
+};
+
+BatchGeo batch_geometry(sox_handle h, int count, const int *n, const int *N, const int *T, const int *S) {
+  BatchGeo bg;
+  const size_t budget = chunk_budget(h, kChunkBudget);
+  long long Bmax = 1;
+  for (int i = 0; i < count; ++i) Bmax = std::max<long long>(Bmax, (long long)T[i] * S[i]);
+  for (long long nc = 1;; nc = nc < Bmax ? std::min<long long>(Bmax, nc * 2) : nc) {
+    size_t total = 0;
+    std::vector<int> Bc(count);
+    for (int i = 0; i < count; ++i) {
+      const Geometry g = geometry(nullptr, n[i], N[i], T[i], S[i], false);
+      const long long B = (long long)T[i] * S[i];
+      Bc[i] = (int)((B + nc - 1) / nc);
+      total += g.fixed_bytes + g.per_b_bytes * (size_t)Bc[i] + 64 * 1024;
+    }
+    if (total <= budget || nc >= Bmax) {
+      bg.nc = (int)nc;
+      bg.Bc = Bc;
+      bg.bytes = total;
+      return bg;
+    }
+  }
+}
+
+struct Inst {
+  int n, N, T, S, Kp, NR, RG, Bc;
+  const double *G, *X, *V;
+  double *Sigma;
+  float *Uf, *inv_u1, *inv_u2;
+  __half *U1h, *U1l, *U2h, *U2l;
+  double *GR64, *GW64;
+  __half *GRh, *GRl, *GWh, *GWl, *Gmh, *Gml, *Ah, *Al;
+  float *inv_gr, *inv_gw, *gsc, *osc, *asc, *rowf, *colf, *Dt, *Tm;
+  int *symf;
+  CUtensorMap bcd[8], agemm[6];
+};
+
+}  // namespace
+
+size_t tc_sigma_batch_bytes(sox_handle h, int count, const int *n, const int *N, const int *T, const int *S) {
+  return batch_geometry(h, count, n, N, T, S).bytes + 64 * 1024;
+}
+
+Status tc_sigma_batch(sox_handle h, int count, const int *n, const int *N, const int *T, const int *S,
+                      const double *const *G, const double *const *X, const double *const *V, double *const *Sigma,
+                      Arena &ar, cudaStream_t s) {
+  if (count <= 0) return Status::ok();
+  const BatchGeo bg = batch_geometry(h, count, n, N, T, S);
+  std::vector<Inst> in(count);
+  std::string err;
+  for (int i = 0; i < count; ++i) {
+    Inst &c = in[i];
+    const Geometry g = geometry(nullptr, n[i], N[i], T[i], S[i], false);
+    c.n = n[i]; c.N = N[i]; c.T = T[i]; c.S = S[i];
+    c.Kp = g.Kp; c.NR = g.NR; c.RG = g.RG; c.Bc = bg.Bc[i];
+    c.G = G[i]; c.X = X[i]; c.V = V[i]; c.Sigma = Sigma[i];
+    const int nn = c.n, NN = c.N, Kp = c.Kp, NR = c.NR, RG = c.RG, Bc = c.Bc;
+    const size_t Kp2 = (size_t)Kp * Kp;
+    c.Uf = ar.take<float>((size_t)NN * Kp2);
+    c.U1h = ar.take<__half>((size_t)NR * Kp2); c.U1l = ar.take<__half>((size_t)NR * Kp2);
+    c.inv_u1 = ar.take<float>(NN);
+    c.U2h = ar.take<__half>((size_t)nn * NR * Kp); c.U2l = ar.take<__half>((size_t)nn * NR * Kp);
+    c.inv_u2 = ar.take<float>(NN);
+    c.GR64 = ar.take<double>((size_t)Bc * NN * nn); c.GW64 = ar.take<double>((size_t)Bc * NN * nn);
+    c.GRh = ar.take<__half>((size_t)Bc * NR * Kp); c.GRl = ar.take<__half>((size_t)Bc * NR * Kp);
+    c.GWh = ar.take<__half>((size_t)Bc * NR * Kp); c.GWl = ar.take<__half>((size_t)Bc * NR * Kp);
+    c.inv_gr = ar.take<float>((size_t)Bc * NN); c.inv_gw = ar.take<float>((size_t)Bc * NN);
+    c.Gmh = ar.take<__half>((size_t)Bc * RG * Kp); c.Gml = ar.take<__half>((size_t)Bc * RG * Kp);
+    c.gsc = ar.take<float>(Bc); c.osc = ar.take<float>(Bc);
+    c.asc = ar.take<float>((size_t)Bc * NR);
+    c.Ah = ar.take<__half>((size_t)Bc * nn * NR * Kp); c.Al = ar.take<__half>((size_t)Bc * nn * NR * Kp);
+    c.rowf = ar.take<float>((size_t)Bc * NN); c.colf = ar.take<float>((size_t)Bc * NN);
+    c.Dt = ar.take<float>((size_t)Bc * NN * NN);
+    c.Tm = ar.take<float>((size_t)Bc * NN * nn);
+    c.symf = ar.take<int>((size_t)Bc);
+    if (!c.symf) return {SOX_ERR_OOM, "workspace too small (internal sizing error)"};
+    if (!make_tmap_f16_3d(&c.bcd[0], c.Ah, Kp, NR, (uint64_t)Bc * nn, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[1], c.Al, Kp, NR, (uint64_t)Bc * nn, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[2], c.GRh, Kp, NR, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[3], c.GRl, Kp, NR, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[4], c.GWh, Kp, NR, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[5], c.GWl, Kp, NR, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[6], c.U2h, Kp, NR, nn, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.bcd[7], c.U2l, Kp, NR, nn, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.agemm[0], c.Gmh, Kp, RG, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.agemm[1], c.Gml, Kp, RG, Bc, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.agemm[2], c.U1h, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+        !make_tmap_f16_3d(&c.agemm[3], c.U1l, Kp, (uint64_t)NR * Kp, 1, 64, 128, &err) ||
+        !make_tmap_f16_store4d(&c.agemm[4], c.Ah, Kp, NR, nn, Bc, &err) ||
+        !make_tmap_f16_store4d(&c.agemm[5], c.Al, Kp, NR, nn, Bc, &err))
+      return {SOX_ERR_CUDA, "batch maps: " + err};
+  }
+  const long long limit = h->spin_limit;
+  auto grid_for = [&](long long tiles) { return (int)std::max<long long>(1, std::min<long long>(tiles, h->sm_count)); };
+  // mixed tensors of every instance (Eq. U_contraction at k = 0; one interaction in both slots)
+  {
+    ProfScope ps(h, "mixed_f32", s, 2 * count);
+    for (Inst &c : in) {
+      const size_t Kp2 = (size_t)c.Kp * c.Kp;
+      SOX_CUDA_TRY(cudaMemsetAsync(c.U1h, 0, hb((size_t)c.NR * Kp2), s));
+      SOX_CUDA_TRY(cudaMemsetAsync(c.U1l, 0, hb((size_t)c.NR * Kp2), s));
+      SOX_CUDA_TRY(cudaMemsetAsync(c.U2h, 0, hb((size_t)c.n * c.NR * c.Kp), s));
+      SOX_CUDA_TRY(cudaMemsetAsync(c.U2l, 0, hb((size_t)c.n * c.NR * c.Kp), s));
+      launch_mixed_f32(c.V, c.X, c.N, c.n, c.Kp, c.Uf, s);
+      launch_split_mixed(c.Uf, c.N, c.NR, c.n, c.Kp, c.U1h, c.U1l, c.U2h, c.U2l, c.inv_u1, s);
+      SOX_CUDA_TRY(cudaMemcpyAsync(c.inv_u2, c.inv_u1, 4 * (size_t)c.N, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // instances by cost per tile (n Kp), largest first: the persistent grid ends on cheap tiles
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (long long)in[x].n * in[x].Kp > (long long)in[y].n * in[y].Kp;
+  });
+  for (int k = 0; k < bg.nc; ++k) {
+    // ---- per instance: FP64 projections, row splits, A, the B/C scales ----
+    for (Inst &c : in) {
+      const int B = c.S * c.T, b0 = k * c.Bc, bc = std::min(c.Bc, B - b0);
+      if (bc <= 0) continue;
+      const double *Gc = c.G + (long long)b0 * c.n * c.n;
+      {
+        ProfScope ps(h, "project_f64", s, 5);
+        launch_symmetry_flags(Gc, c.n, bc, c.symf, s);
+        GemmF64 gp;
+        gp.M = c.N; gp.Nc = c.n; gp.K = c.n; gp.batch = bc;
+        gp.A = c.X; gp.ai = c.n; gp.ak = 1;
+        gp.B = Gc; gp.sB = (long long)c.n * c.n; gp.bk = c.n; gp.bj = 1;
+        gp.C = c.GR64; gp.sC = (long long)c.N * c.n; gp.ci = c.n; gp.cj = 1;
+        launch_gemm_f64(gp, s);
+        GemmF64 gw = gp;
+        gw.bk = 1; gw.bj = c.n;
+        gw.C = c.GW64;
+        gw.skip = c.symf;
+        launch_gemm_f64(gw, s);
+        launch_split_rows_f64(c.GR64, c.n, (long long)c.N * c.n, c.N, c.NR, c.n, c.Kp, c.GRh, c.GRl, c.inv_gr, bc, s);
+        launch_split_rows_f64(c.GW64, c.n, (long long)c.N * c.n, c.N, c.NR, c.n, c.Kp, c.GWh, c.GWl, c.inv_gw, bc, s,
+                              c.GR64, c.symf);
+      }
+      {
+        ProfScope ps(h, "A_tc", s, 2);
+        const bool exact_a = (c.Kp <= 128);
+        launch_prep_gminus(c.G, c.n, c.T, bc, c.Kp, c.Gmh, c.Gml, c.gsc, c.osc, b0, c.RG, s);
+        GemmTcArgs ga;
+        ga.M = c.n; ga.Ncols = c.NR * c.Kp; ga.Kp = c.Kp; ga.K = c.n; ga.batch = bc;
+        ga.batchA_shared = 0; ga.batchB_shared = 1;
+        ga.mode = exact_a ? kStoreSplitGroup : kStoreSplit;
+        ga.out_scale = c.osc;
+        ga.group = c.Kp; ga.n_groups = c.NR; ga.group_scale = c.asc;
+        ga.spin_limit = limit; ga.status = h->d_status;
+        const long long tiles = (long long)bc * ((c.n + 127) / 128) * (((long long)c.NR * c.Kp + 127) / 128);
+        SOX_CUDA_TRY(launch_gemm_f16x2(c.agemm, ga, grid_for(tiles), s));
+        launch_bcd_scales(c.inv_u1, c.gsc, c.osc, exact_a ? c.asc : nullptr, c.NR, c.inv_gw, c.inv_gr, c.inv_u2, c.N,
+                          bc, c.rowf, c.colf, s);
+        h->launches += 1;
+      }
+    }
+    // ---- one persistent fused launch over the chunk's tiles of every instance ----
+    {
+      ProfScope ps(h, "sox_bcd_tc", s, 0);
+      BcdJobs jobs;
+      jobs.spin_limit = limit;
+      jobs.status = h->d_status;
+      auto flush = [&]() -> Status {
+        if (jobs.count == 0) return Status::ok();
+        h->launches += 1;
+        SOX_CUDA_TRY(launch_sox_bcd_multi(jobs, grid_for(jobs.total), s));
+        jobs.count = 0;
+        jobs.total = 0;
+        return Status::ok();
+      };
+      for (int oi : order) {
+        Inst &c = in[oi];
+        const int B = c.S * c.T, b0 = k * c.Bc, bc = std::min(c.Bc, B - b0);
+        if (bc <= 0) continue;
+        if (jobs.count == kMaxBcdJobs) SOX_TRY(flush());
+        BcdJob &J = jobs.job[jobs.count++];
+        for (int m = 0; m < 8; ++m) J.maps[m] = c.bcd[m];
+        J.n = c.n; J.N = c.N; J.Kp = c.Kp; J.batch = bc;
+        v_range(h, c.n, &J.v0, &J.v1);
+        J.v1 = (J.v1 <= 0 || J.v1 > c.n) ? c.n : J.v1;
+        J.v0 = J.v0 < 0 ? 0 : std::min(J.v0, J.v1);
+        J.row_scale = c.rowf; J.col_scale = c.colf;
+        J.Dt = c.Dt; J.ldD = c.N;
+        J.unit0 = jobs.total;
+        const long long tP = (c.N + 127) / 128;
+        jobs.total += (long long)bc * tP * tP;
+      }
+      SOX_TRY(flush());
+    }
+    // ---- per instance: back-projection to orbitals ----
+    for (Inst &c : in) {
+      const int B = c.S * c.T, b0 = k * c.Bc, bc = std::min(c.Bc, B - b0);
+      if (bc <= 0) continue;
+      ProfScope ps(h, "backproject", s, 2);
+      launch_backproject_T(c.Dt, c.N, c.X, c.N, c.n, bc, c.Tm, s);
+      launch_backproject_sigma(c.X, c.Tm, c.N, c.n, bc, c.Sigma + (long long)b0 * c.n * c.n, (long long)c.n * c.n, s,
+                               v_range_is_full(h, c.n) ? c.symf : nullptr);
     }
   }
   SOX_CUDA_TRY(cudaGetLastError());

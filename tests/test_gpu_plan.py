@@ -68,3 +68,72 @@ def test_plan_rejects_host_tensors_and_solids(env):
         with pytest.raises(pkg.SoxError) as e:
             pkg.SigmaBatchPlan(h, solid, G[:1], X[:1], V[:1], S[:1])
         assert e.value.code == 3
+
+
+UNEVEN = [(57, 342, 4, 1), (150, 900, 2, 1), (79, 474, 3, 2), (33, 300, 3, 1), (13, 70, 5, 2)]
+
+
+def _uneven(torch, pkg, shapes=UNEVEN):
+    ws = [synth.molecule(80 + i, n, N, T, 100.0, n_spin=s) for i, (n, N, T, s) in enumerate(shapes)]
+    probs = [pkg.problem(w.n, w.N, w.n_tau, w.n_spin, w.beta) for w in ws]
+    dev = [to_dev(torch, w.G, w.X, w.V) for w in ws]
+    return ws, probs, [d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev]
+
+
+@pytest.mark.parametrize("limit", [0, 1])
+def test_batched_fused_launch_equals_the_instances_built_alone(env, limit):
+    """The split path's uneven batch runs the fused step of every tau chunk of every instance
+    as one persistent launch (n from 13 to 150, Kp 64 to 192, one and two spins, odd and even
+    tile counts); with the streamed kernel forced on the single builds, every instance's Sigma
+    is bit-identical to its own build, with the default chunking and with one batch per chunk
+    (limit = 1), and the smallest and largest instances meet the oracle."""
+    torch, pkg = env
+    ws, probs, G, X, V = _uneven(torch, pkg)
+    S = [torch.full_like(g, float("nan")) for g in G]
+    with pkg.Handle("f16x2", workspace_limit=limit) as hb, pkg.Handle("f16x2") as hs:
+        pkg.sox_set_kernel_variant(hs, "streamed")
+        pkg.sox_sigma_batch(hb, probs, G, X, V, S)
+        pkg.sox_check_device(hb)
+        for i, w in enumerate(ws):
+            R = torch.full_like(G[i], float("nan"))
+            pkg.sox_sigma(hs, probs[i], G[i], X[i], V[i], R)
+            pkg.sox_check_device(hs)
+            assert torch.equal(S[i], R), f"instance {i}"
+    for i in (0, 1):   # largest n first in UNEVEN[1], smallest N x n in UNEVEN[4]
+        w = ws[[1, 4][i]]
+        ref = sox.sigma_tau(w.X[0], w.V[0], w.V[0], w.G[0, 0], taus=[0, w.n_tau - 1], dtype=np.float64)
+        got = S[[1, 4][i]].cpu().numpy()[0, 0, [0, w.n_tau - 1]]
+        check(got, ref, "f16x2", f"batched instance n={w.n}", n=w.n, N=w.N)
+
+
+def test_batched_fused_launch_keeps_the_v_range(env):
+    torch, pkg = env
+    ws, probs, G, X, V = _uneven(torch, pkg, UNEVEN[:3])
+    with pkg.Handle("f16x2") as hb, pkg.Handle("f16x2") as hs:
+        pkg.sox_set_kernel_variant(hs, "streamed")
+        for h in (hb, hs):
+            pkg.sox_set_v_range(h, 5, 40)
+        S = [torch.full_like(g, float("nan")) for g in G]
+        pkg.sox_sigma_batch(hb, probs, G, X, V, S)
+        for i in range(len(ws)):
+            R = torch.full_like(G[i], float("nan"))
+            pkg.sox_sigma(hs, probs[i], G[i], X[i], V[i], R)
+            assert torch.equal(S[i], R), f"instance {i}"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x2"])
+def test_phi_sox_batch_matches_phi_sox(env, prec):
+    torch, pkg = env
+    ws, probs, G, X, V = _uneven(torch, pkg, UNEVEN[:3])
+    wts = [torch.from_numpy(np.ascontiguousarray(pkg.sox_tau_grid(w.n_tau, w.beta)[1])).cuda() for w in ws]
+    S = [torch.full_like(g, float("nan")) for g in G]
+    phi = [torch.full((w.n_spin,), float("nan"), dtype=torch.float64, device="cuda") for w in ws]
+    with pkg.Handle(prec) as hb, pkg.Handle(prec) as hs:
+        if prec == "f16x2":
+            pkg.sox_set_kernel_variant(hs, "streamed")
+        pkg.phi_sox_batch(hb, probs, G, X, V, wts, phi, S)
+        for i in range(len(ws)):
+            R = torch.full_like(G[i], float("nan"))
+            p1 = torch.full((ws[i].n_spin,), float("nan"), dtype=torch.float64, device="cuda")
+            pkg.phi_sox(hs, probs[i], G[i], X[i], V[i], wts[i], p1, R)
+            assert torch.equal(S[i], R) and torch.equal(phi[i], p1), f"instance {i}"
