@@ -274,27 +274,42 @@ struct BatchGeo {
   size_t bytes = 0;
 };
 
+constexpr size_t kBatchBudget = size_t(64) << 30;
+
+// Per-instance chunk sizes: every instance starts whole (all its (spin, tau) batches in one
+// chunk); while the batch's buffers exceed the budget, the instance holding the most chunk
+// memory halves its chunk.  Small instances thus finish in the first chunk with large
+// launches of their own, and only the large ones are spread over further chunks.
 BatchGeo batch_geometry(sox_handle h, int count, const int *n, const int *N, const int *T, const int *S) {
   BatchGeo bg;
-  const size_t budget = chunk_budget(h, kChunkBudget);
-  long long Bmax = 1;
-  for (int i = 0; i < count; ++i) Bmax = std::max<long long>(Bmax, (long long)T[i] * S[i]);
-  for (long long nc = 1;; nc = nc < Bmax ? std::min<long long>(Bmax, nc * 2) : nc) {
-    size_t total = 0;
-    std::vector<int> Bc(count);
-    for (int i = 0; i < count; ++i) {
-      const Geometry g = geometry(nullptr, n[i], N[i], T[i], S[i], false);
-      const long long B = (long long)T[i] * S[i];
-      Bc[i] = (int)((B + nc - 1) / nc);
-      total += g.fixed_bytes + g.per_b_bytes * (size_t)Bc[i] + 64 * 1024;
-    }
-    if (total <= budget || nc >= Bmax) {
-      bg.nc = (int)nc;
-      bg.Bc = Bc;
-      bg.bytes = total;
-      return bg;
-    }
+  const size_t budget = chunk_budget(h, kBatchBudget);
+  std::vector<Geometry> g(count);
+  std::vector<long long> B(count);
+  bg.Bc.assign(count, 1);
+  size_t fixed = 0;
+  for (int i = 0; i < count; ++i) {
+    g[i] = geometry(nullptr, n[i], N[i], T[i], S[i], false);
+    B[i] = (long long)T[i] * S[i];
+    bg.Bc[i] = (int)B[i];
+    fixed += g[i].fixed_bytes + 64 * 1024;
   }
+  auto chunk_mem = [&](int i) { return g[i].per_b_bytes * (size_t)bg.Bc[i]; };
+  for (;;) {
+    size_t total = fixed;
+    int hog = -1;
+    for (int i = 0; i < count; ++i) {
+      total += chunk_mem(i);
+      if (bg.Bc[i] > 1 && (hog < 0 || chunk_mem(i) > chunk_mem(hog))) hog = i;
+    }
+    if (total <= budget || hog < 0) {
+      bg.bytes = total;
+      break;
+    }
+    bg.Bc[hog] = (bg.Bc[hog] + 1) / 2;
+  }
+  bg.nc = 1;
+  for (int i = 0; i < count; ++i) bg.nc = std::max<int>(bg.nc, (int)((B[i] + bg.Bc[i] - 1) / bg.Bc[i]));
+  return bg;
 }
 
 struct Inst {
