@@ -274,7 +274,7 @@ struct BatchGeo {
   size_t bytes = 0;
 };
 
-constexpr size_t kBatchBudget = size_t(64) << 30;
+constexpr size_t kBatchBudget = size_t(128) << 30;
 
 // Per-instance chunk sizes: every instance starts whole (all its (spin, tau) batches in one
 // chunk); while the batch's buffers exceed the budget, the instance holding the most chunk
