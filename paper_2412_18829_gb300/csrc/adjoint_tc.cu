@@ -162,8 +162,9 @@ __global__ void k_xbar_factor(AdjScalars *sc) {
 //   B~_v = A~_v GR~^T, C~_v = GWt~ U2~_v^T in TMEM (double-buffered), and in the epilogue
 //   Bbar_v = cg_b E o C~_v, Cbar_v = cg_b E o B~_v -> FP16 pairs [b][v][R][P],
 //   Ebar  += B~_v o C~_v (registers), written em_b * sum at the end of the tile.
-// Warp 0: TMA, warp 1: MMA (one elected thread), warps 4-11: pair writers, warps 12-19:
-// Ebar accumulators (lane quarter warp % 4, column half by warpgroup).
+// Warp 0: TMA, warps 1 and 2: MMA (one thread each: the B_v and the C_v halves), warps 4-11:
+// pair writers, warps 12-19: Ebar accumulators (lane quarter warp % 4, column half by
+// warpgroup).
 // ============================================================================
 constexpr int kT = 128, kC = 64;
 constexpr int kTileB = kT * kC * 2;            // 16 KB: one 64-wide chunk of 128 rows, hi or lo
@@ -342,10 +343,10 @@ __global__ void __launch_bounds__(kProdThreads, 1)
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_full[b], 2);   // one commit per issuing warp
       tc::mbar_init(&bar->acc_empty[b], kProdEpi);
     }
-    tc::mbar_init(&bar->drain, 1);
+    tc::mbar_init(&bar->drain, 2);
     bar->abort = 0;
     tc::fence_barrier_init();
   }
@@ -412,8 +413,11 @@ __global__ void __launch_bounds__(kProdThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 2) {
+    // two MMA issuers, warp 1 the B_v halves and warp 2 the C_v halves (each into its own
+    // accumulators): while one waits for a stage the other keeps the tensor pipe fed
     if (lane == 0) {
+      const int my = warp - 1;
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
@@ -428,6 +432,10 @@ __global__ void __launch_bounds__(kProdThreads, 1)
           if (!ok) break;
           tc::tc_fence_after();
           for (int half = 0; half < 2 && ok; ++half) {
+            if (half != my) {
+              it += nk;
+              continue;
+            }
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kSt);

@@ -30,7 +30,10 @@ constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of one operan
 constexpr int kStageBytes = 4 * kPart;        // A hi, A lo, B hi, B lo
 constexpr int kStages = 3;
 constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column half of an output tile
-constexpr int kThreads = 320;                 // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+// warp 0 TMA, warps 1 and 10 MMA (even and odd accumulation windows: one issuer keeps the
+// tensor pipe fed while the other waits for a stage), warps 2-9 epilogue; eleven warps take
+// the registers of twelve, as ten do
+constexpr int kThreads = 352;
 constexpr int kEpi = 256;
 
 struct Bars {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&bar->acc_full[b], 1);
       tc::mbar_init(&bar->acc_empty[b], kEpi);
     }
-    tc::mbar_init(&bar->drain, 1);
+    tc::mbar_init(&bar->drain, 2);   // one commit per issuing warp
     bar->abort = 0;
     tc::fence_barrier_init();
   }
@@ -197,9 +200,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == 1 || warp == 10) {
+    // ---------------- MMA issuers: warp 1 the even windows, warp 10 the odd ones ----------------
     if (lane == 0) {
+      const long long my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < items && ok && !*abort; t += gridDim.x) {
@@ -210,6 +214,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                ((uint32_t)a.b.mn_major << 16);
         for (long long w0 = w.c0; w0 < w.c1 && ok; w0 += a.window, ++acc_it) {
           const long long w1 = w0 + a.window < w.c1 ? w0 + a.window : w.c1;
+          if ((acc_it & 1) != my) {   // the other issuer's window
+            it += w1 - w0;
+            continue;
+          }
           const int buf = (int)(acc_it & 1);
           const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp <= 9) {
     // ---------------- epilogue: 8 warps, lane quarter q, 64-column half h ----------------
     const int q = warp & 3;
     const int row = q * 32 + lane;

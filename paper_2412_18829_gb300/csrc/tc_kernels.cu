@@ -139,18 +139,25 @@ __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
       tc::mbar_init(&bar->acc_full[b], 1);
       tc::mbar_init(&bar->acc_empty[b], epi_threads);
     }
-    tc::mbar_init(&bar->drain, 1);
+    tc::mbar_init(&bar->drain, 2);   // one commit per issuing warp
     bar->abort = 0;
     tc::fence_barrier_init();
   }
 }
 
-// Fused kernels: warp 0 TMA, warp 1 MMA, warps 2..5 epilogue (one per TMEM
-// lane quarter, 128 columns each).  Measured: the epilogue is not the limit (a
+// Fused kernels: warp 0 TMA, warp 1 MMA (and warp 6, see kBcdThreads2), warps 2..5 epilogue
+// (one per TMEM lane quarter, 128 columns each).  Measured: the epilogue is not the limit (a
 // variant that skips its TMEM loads runs at the same speed), so it stays at
 // four warps with 255 registers available.
 constexpr int kBcdThreads = 192;
 constexpr int kEpiThreads = 128;
+// With two MMA-issuing warps (warp 1: the B_v halves, warp 6: the C_v halves; each into its
+// own accumulators, so every accumulator still receives its MMAs from one thread in order).
+// An issuing thread stalls at each wait for a stage, and the tensor pipe holds few MMAs
+// ahead of it, so one issuer leaves the pipe idle at every wait; with two, one issues while
+// the other waits (the mid-size build's fused kernel: 9.4 -> 7.5 ms).  Seven warps take the
+// same registers as six (registers are granted per four warps).
+constexpr int kBcdThreads2 = 224;
 
 // Epilogue of the fused kernels: D[P, R] += B_v[P, R] * C_v[P, R] over v, in
 // registers; B_v at TMEM columns [buf*256, +128), C_v at [buf*256 + 128, +128).
@@ -210,7 +217,7 @@ __device__ __forceinline__ void bcd_epilogue(Bar *bar, uint32_t tmem, const BcdA
 // (double-buffered), the Hadamard product accumulates in registers, and only
 // D leaves the SM, written transposed and rescaled: Dt[b][R][P].
 // ============================================================================
-__global__ void __launch_bounds__(kBcdThreads, 1)
+__global__ void __launch_bounds__(kBcdThreads2, 1)
     k_sox_bcd_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                  const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                  const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -225,7 +232,19 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
   const long long total = (long long)a.batch * tiles_per_b;
   const int nk = a.Kp / kChunk;
 
-  setup_barriers(bar, kEpiThreads);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 2);   // one commit per issuing warp
+      tc::mbar_init(&bar->acc_empty[b], kEpiThreads);
+    }
+    tc::mbar_init(&bar->drain, 2);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
   if (warp == 1) {
     tc::tmem_alloc(&bar->tmem_base, 512);
     tc::tmem_relinquish();
@@ -282,9 +301,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == 1 || warp == 6) {
+    // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
     if (lane == 0) {
+      const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
@@ -296,6 +316,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           if (!ok) break;
           tc::tc_fence_after();
           for (int half = 0; half < 2 && ok; ++half) {
+            if (half != my) {
+              it += nk;
+              continue;
+            }
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kStages);
@@ -315,7 +339,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp >= 2 && warp <= 5) {
     bcd_epilogue(bar, tmem, a, tP, total, abort, warp, lane);
   }
   __syncthreads();
@@ -352,7 +376,7 @@ __device__ __forceinline__ MultiTile multi_tile(const BcdJobs &jobs, long long t
   return m;
 }
 
-__global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_constant__ BcdJobs jobs) {
+__global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_constant__ BcdJobs jobs) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Barriers *bar = reinterpret_cast<Barriers *>(smem + kStages * kStageBytes);
@@ -360,7 +384,19 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
   const long long total = jobs.total;
   const long long limit = jobs.spin_limit;
 
-  setup_barriers(bar, kEpiThreads);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->acc_full[b], 2);   // one commit per issuing warp
+      tc::mbar_init(&bar->acc_empty[b], kEpiThreads);
+    }
+    tc::mbar_init(&bar->drain, 2);
+    bar->abort = 0;
+    tc::fence_barrier_init();
+  }
   if (warp == 1) {
     tc::tmem_alloc(&bar->tmem_base, 512);
     tc::tmem_relinquish();
@@ -412,9 +448,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == 1 || warp == 6) {
+    // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
     if (lane == 0) {
+      const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
@@ -429,6 +466,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
           if (!ok) break;
           tc::tc_fence_after();
           for (int half = 0; half < 2 && ok; ++half) {
+            if (half != my) {
+              it += nk;
+              continue;
+            }
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kStages);
@@ -447,7 +488,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
       for (long long i = 0; i < wind_down_limit(limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp >= 2 && warp <= 5) {
     // ---------------- epilogue: D[P, R] += B_v * C_v in registers ----------------
     const int q = warp & 3;
     const int row = q * 32 + lane;
@@ -549,7 +590,7 @@ __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32
   else issue_chunk4_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
 }
 
-__global__ void __launch_bounds__(kBcdThreads, 1)
+__global__ void __launch_bounds__(kBcdThreads2, 1)
     k_sox_bcd_tc_res(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                      const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                      const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -572,12 +613,12 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       tc::mbar_init(&bar->empty[s], 1);
     }
     tc::mbar_init(&bar->res_full, 1);
-    tc::mbar_init(&bar->res_empty, 1);
+    tc::mbar_init(&bar->res_empty, 2);   // one commit per issuing warp
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_full[b], 2);
       tc::mbar_init(&bar->acc_empty[b], kEpiThreads);
     }
-    tc::mbar_init(&bar->drain, 1);
+    tc::mbar_init(&bar->drain, 2);
     bar->abort = 0;
     tc::fence_barrier_init();
   }
@@ -648,8 +689,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 6) {
+    // MMA issuers: warp 1 the B halves, warp 6 the C halves
     if (lane == 0) {
+      const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0, tt = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++tt) {
@@ -663,6 +706,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           if (!ok) break;
           tc::tc_fence_after();
           for (int half = 0; half < 2 && ok; ++half) {
+            if (half != my) {
+              it += nk;
+              continue;
+            }
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kRStages);
@@ -689,7 +736,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
       for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp >= 2 && warp <= 5) {
     bcd_epilogue(bar, tmem, a, tP, total, abort, warp, lane);
   }
   __syncthreads();
@@ -962,7 +1009,9 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // The split GEMM runs 8 epilogue warps (two per TMEM lane quarter, one per
 // 64-column half): the epilogue, not the MMA, sets its pace.
-constexpr int kGemmThreads = 320;
+// warp 0 TMA, warps 1 and 10 MMA (even and odd tiles of the CTA, one issuing while the other
+// waits for a stage), warps 2-9 epilogue
+constexpr int kGemmThreads = 352;
 constexpr int kGemmEpi = 256;
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 // the epilogue warps agree on ok (all of them, or none, go on: no warp is left waiting at a
@@ -1073,11 +1122,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 10) {
     if (lane == 0) {
+      const long long my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++acc_it) {
+        if ((acc_it & 1) != my) {   // the other issuer's tile
+          it += nk;
+          continue;
+        }
         const int buf = (int)(acc_it & 1);
         const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
         ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
@@ -1099,7 +1153,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp <= 9) {
     const int q = warp & 3;
     const int row = q * 32 + lane;          // tile row = TMEM lane
     const int h = (warp - 2) >> 2;          // 64-column half of the tile
@@ -1616,7 +1670,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     static std::atomic<unsigned long long> rattr{0};
     const cudaError_t e = set_smem_once(k_sox_bcd_tc_res, (int)res_smem_bytes(), rattr);
     if (e != cudaSuccess) return e;
-    k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+    k_sox_bcd_tc_res<<<grid, kBcdThreads2, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                maps[5], maps[6], maps[7], a);
     return cudaGetLastError();
   }
@@ -1637,7 +1691,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
   static std::atomic<unsigned long long> attr{0};
   const cudaError_t e = set_smem_once(k_sox_bcd_tc, (int)tc_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+  k_sox_bcd_tc<<<grid, kBcdThreads2, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                                         maps[6], maps[7], a);
   return cudaGetLastError();
 }
@@ -1648,7 +1702,7 @@ cudaError_t launch_sox_bcd_multi(const BcdJobs &jobs, int grid, cudaStream_t s) 
   static std::atomic<unsigned long long> attr{0};
   const cudaError_t e = set_smem_once(k_sox_bcd_multi, (int)tc_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  k_sox_bcd_multi<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(jobs);
+  k_sox_bcd_multi<<<grid, kBcdThreads2, tc_smem_bytes(), s>>>(jobs);
   return cudaGetLastError();
 }
 
