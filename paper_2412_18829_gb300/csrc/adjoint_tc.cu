@@ -180,8 +180,10 @@ constexpr int kProdThreads = 640, kProdEpi = 512;
 constexpr int kRegLaunch = 96, kRegCtl = 56, kRegEpi = 104;
 static_assert(128 * kRegCtl + 512 * kRegEpi <= kProdThreads * kRegLaunch, "register split above the launch total");
 
+// full[q][s]: stage s holds a chunk for MMA issuer q (each issuer waits on its own set, so
+// the phases it counts are the ones it consumes)
 struct PBars {
-  uint64_t full[kSt];
+  uint64_t full[2][kSt];
   uint64_t empty[kSt];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
@@ -339,7 +341,8 @@ __global__ void __launch_bounds__(kProdThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSt; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -376,6 +379,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       long long it = 0;
+      tc::RingPhases ring;
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const int b = (int)(t / tiles_per_b);
         const int r = (int)(t % tiles_per_b);
@@ -386,32 +390,28 @@ __global__ void __launch_bounds__(kProdThreads, 1)
               const int s = (int)(it % kSt);
               const uint32_t ph = (uint32_t)((it / kSt) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              tc::mbar_arrive_expect_tx(&bar->full[s], kStageB);
+              uint64_t *fb = &bar->full[half][s];   // the half's issuer
+              ring.take(half, s);
+              tc::mbar_arrive_expect_tx(fb, kStageB);
               uint8_t *st = smem + (size_t)s * kStageB;
               const int x = kc * kC;
               if (half == 0) {   // B_v = A_v GR^T
-                tc::tma_load_3d(st, &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
-                tc::tma_load_3d(st + kTileB, &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
-                tc::tma_load_3d(st + 2 * kTileB, &tmGR_hi, &bar->full[s], x, R0, b);
-                tc::tma_load_3d(st + 3 * kTileB, &tmGR_lo, &bar->full[s], x, R0, b);
+                tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d(st + kTileB, &tmA_lo, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d(st + 2 * kTileB, &tmGR_hi, fb, x, R0, b);
+                tc::tma_load_3d(st + 3 * kTileB, &tmGR_lo, fb, x, R0, b);
               } else {           // C_v = GWt U2_v^T
-                tc::tma_load_3d(st, &tmGW_hi, &bar->full[s], x, P0, b);
-                tc::tma_load_3d(st + kTileB, &tmGW_lo, &bar->full[s], x, P0, b);
-                tc::tma_load_3d(st + 2 * kTileB, &tmU_hi, &bar->full[s], x, R0, v);
-                tc::tma_load_3d(st + 3 * kTileB, &tmU_lo, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(st, &tmGW_hi, fb, x, P0, b);
+                tc::tma_load_3d(st + kTileB, &tmGW_lo, fb, x, P0, b);
+                tc::tma_load_3d(st + 2 * kTileB, &tmU_hi, fb, x, R0, v);
+                tc::tma_load_3d(st + 3 * kTileB, &tmU_lo, fb, x, R0, v);
               }
             }
           }
         }
       }
-      for (int s = 0; s < kSt; ++s) {   // every copy issued has landed before the CTA exits
-        long long last = it - 1 - ((it - 1 - s) % kSt + kSt) % kSt;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kSt) & 1);
-          for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      // every copy issued has landed before the CTA exits
+      tc::ring_wind_down(bar->full, ring, wind_down(a.spin_limit));
     }
   } else if (warp == 1 || warp == 2) {
     // two MMA issuers, warp 1 the B_v halves and warp 2 the C_v halves (each into its own
@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
     if (lane == 0) {
       const int my = warp - 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
         // N = the R tile's valid width rounded up to 16 (the last tile stops at N)
@@ -439,8 +440,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kSt);
-              const uint32_t ph = (uint32_t)((it / kSt) & 1);
-              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
               const uint32_t st = smem_u32(smem + (size_t)s * kStageB);

@@ -36,8 +36,12 @@ constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column h
 constexpr int kThreads = 352;
 constexpr int kEpi = 256;
 
+// full[q][s]: stage s holds a chunk of an accumulation window of issuer q.  Each issuer
+// waits only on its own set, so the phases it counts are the ones it consumes (an issuer
+// that skipped the other's window would otherwise wait on a phase two ahead of the
+// barrier, where the parity test already reads as complete).
 struct Bars {
-  uint64_t full[kStages];
+  uint64_t full[2][kStages];
   uint64_t empty[kStages];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
@@ -145,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -174,37 +179,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      long long it = 0;
+      long long it = 0, acc0 = 0;   // acc0: windows of the previous items
+      tc::RingPhases ring;
       for (long long t = blockIdx.x; t < items && !*abort; t += gridDim.x) {
         const Item w = item_of(a, t, tM, tN, chunks);
         for (long long c = w.c0; c < w.c1 && !*abort; ++c, ++it) {
           const int s = (int)(it % kStages);
           const uint32_t ph = (uint32_t)((it / kStages) & 1);
           if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-          tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+          const int q = (int)((acc0 + (c - w.c0) / a.window) & 1);   // issuer of the chunk's window
+          uint64_t *fb = &bar->full[q][s];
+          ring.take(q, s);
+          tc::mbar_arrive_expect_tx(fb, kStageBytes);
           const long long kz = c / a.kc_inner;
           const int k0 = (int)(c % a.kc_inner) * kC;
           uint8_t *st = smem + (size_t)s * kStageBytes;
-          load_operand(st, &tmA_hi, &tmA_lo, &bar->full[s], a.a.mn_major, w.i0, k0,
+          load_operand(st, &tmA_hi, &tmA_lo, fb, a.a.mn_major, w.i0, k0,
                        (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
-          load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, &bar->full[s], a.b.mn_major, w.j0, k0,
+          load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, fb, a.b.mn_major, w.j0, k0,
                        (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
         }
+        if (w.c1 > w.c0) acc0 += (w.c1 - w.c0 + a.window - 1) / a.window;
       }
-      for (int s = 0; s < kStages; ++s) {   // every copy issued has landed before the CTA exits
-        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kStages) & 1);
-          for (long long i = 0; i < wind_down(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      // every copy issued has landed before the CTA exits
+      tc::ring_wind_down(bar->full, ring, wind_down(a.spin_limit));
     }
   } else if (warp == 1 || warp == 10) {
     // ---------------- MMA issuers: warp 1 the even windows, warp 10 the odd ones ----------------
     if (lane == 0) {
       const long long my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long t = blockIdx.x; t < items && ok && !*abort; t += gridDim.x) {
         const Item w = item_of(a, t, tM, tN, chunks);
@@ -226,8 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t acc = tmem + buf * kT;
           for (long long c = w0; c < w1; ++c, ++it) {
             const int s = (int)(it % kStages);
-            const uint32_t ph = (uint32_t)((it / kStages) & 1);
-            ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+            ok = tc::mbar_wait(&bar->full[my][s], ring.take((int)my, s), a.spin_limit, abort, a.status, 4);
             if (!ok) break;
             tc::tc_fence_after();
             const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);

@@ -60,6 +60,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
   return false;
 }
 
+// Phase bookkeeping for a stage ring whose full barriers come in two sets, one per MMA
+// issuer (full[q][s]), fed by one TMA producer.  Bit 16q + s of `par` is the parity of the
+// next phase the holder expects on full[q][s]; bit 16q + s of `used` marks a barrier the
+// producer has issued on.  Registers only: the set index is a runtime value.
+struct RingPhases {
+  uint32_t par = 0u, used = 0u;
+  __device__ __forceinline__ uint32_t next(int q, int s) const { return (par >> (16 * q + s)) & 1u; }
+  // takes the next phase of full[q][s] and returns its parity
+  __device__ __forceinline__ uint32_t take(int q, int s) {
+    const uint32_t m = 1u << (16 * q + s);
+    const uint32_t ph = (par & m) ? 1u : 0u;
+    par ^= m;
+    used |= m;
+    return ph;
+  }
+};
+
+// Producer wind-down: waits (at most `limit` polls each) until the last phase issued on
+// every barrier of both sets has completed, so no TMA write is in flight when the CTA
+// leaves.
+template <int S>
+__device__ __forceinline__ void ring_wind_down(uint64_t (&full)[2][S], const RingPhases &r, long long limit) {
+  for (int q = 0; q < 2; ++q)
+    for (int s = 0; s < S; ++s)
+      if ((r.used >> (16 * q + s)) & 1u) {
+        const uint32_t ph = r.next(q, s) ^ 1u;
+        for (long long i = 0; i < limit && !mbar_try_wait(&full[q][s], ph); ++i) {
+        }
+      }
+}
+
 // 3-D tiled TMA load into shared memory, completion counted on `bar`.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
                                             int y, int z) {

@@ -62,8 +62,12 @@ constexpr int kStageBytes = 4 * kTileBytes;     // hi/lo of both operands
 constexpr int kStages = 3;
 constexpr uint32_t kIdesc = tc::idesc_f16_f32(kTile, kTile);
 
+// full[q][s]: stage s holds a chunk for MMA issuer q.  Each issuer waits only on its own
+// set, so the phases it counts on a barrier are exactly the ones it consumes: on a ring
+// shared by two issuers, an issuer that skips the other's chunks would otherwise wait on a
+// phase two or more ahead of the barrier, where the parity test reads as complete.
 struct Barriers {
-  uint64_t full[kStages];
+  uint64_t full[2][kStages];
   uint64_t empty[kStages];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
@@ -132,7 +136,8 @@ __device__ __forceinline__ int chunk_steps(int kc, int K) {
 __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -234,7 +239,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -264,6 +270,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       long long it = 0;
+      tc::RingPhases ring;
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const int b = (int)(t / tiles_per_b);
         const int r = (int)(t % tiles_per_b);
@@ -274,38 +281,34 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+              uint64_t *fb = &bar->full[half][s];   // the half's issuer
+              ring.take(half, s);
+              tc::mbar_arrive_expect_tx(fb, kStageBytes);
               const int x = kc * kChunk;
               if (half == 0) {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmGR_hi, &bar->full[s], x, R0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmGR_lo, &bar->full[s], x, R0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmGR_hi, fb, x, R0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmGR_lo, fb, x, R0, b);
               } else {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmGW_hi, &bar->full[s], x, P0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmGW_lo, &bar->full[s], x, P0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmU_hi, &bar->full[s], x, R0, v);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmU_lo, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmGW_hi, fb, x, P0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmGW_lo, fb, x, P0, b);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmU_hi, fb, x, R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmU_lo, fb, x, R0, v);
               }
             }
           }
         }
       }
       // wind down: every stage issued must have landed before the CTA exits
-      for (int s = 0; s < kStages; ++s) {
-        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kStages) & 1);
-          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
     }
   } else if (warp == 1 || warp == 6) {
     // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
         const uint32_t idesc = idesc_cols((int)((t % tiles_per_b) % tP) * kTile, a.N);   // R side
@@ -323,8 +326,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kStages);
-              const uint32_t ph = (uint32_t)((it / kStages) & 1);
-              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
               issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, a.n), idesc);
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -411,6 +414,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       long long it = 0;
+      tc::RingPhases ring;
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const MultiTile m = multi_tile(jobs, t);
         const BcdJob &J = jobs.job[m.j];
@@ -421,38 +425,34 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
-              tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+              uint64_t *fb = &bar->full[half][s];
+              ring.take(half, s);
+              tc::mbar_arrive_expect_tx(fb, kStageBytes);
               const int x = kc * kChunk;
               if (half == 0) {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[0], &bar->full[s], x, m.P0, m.b * J.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[1], &bar->full[s], x, m.P0, m.b * J.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[2], &bar->full[s], x, m.R0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[3], &bar->full[s], x, m.R0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[0], fb, x, m.P0, m.b * J.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[1], fb, x, m.P0, m.b * J.n + v);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[2], fb, x, m.R0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[3], fb, x, m.R0, m.b);
               } else {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[4], &bar->full[s], x, m.P0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[5], &bar->full[s], x, m.P0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[6], &bar->full[s], x, m.R0, v);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[7], &bar->full[s], x, m.R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[4], fb, x, m.P0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[5], fb, x, m.P0, m.b);
+                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[6], fb, x, m.R0, v);
+                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[7], fb, x, m.R0, v);
               }
             }
           }
         }
       }
       // wind down: every stage issued must have landed before the CTA exits
-      for (int s = 0; s < kStages; ++s) {
-        long long last = it - 1 - ((it - 1 - s) % kStages + kStages) % kStages;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kStages) & 1);
-          for (long long i = 0; i < wind_down_limit(limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      tc::ring_wind_down(bar->full, ring, wind_down_limit(limit));
     }
   } else if (warp == 1 || warp == 6) {
     // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x) {
         const MultiTile m = multi_tile(jobs, t);
@@ -473,8 +473,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kStages);
-              const uint32_t ph = (uint32_t)((it / kStages) & 1);
-              ok = tc::mbar_wait(&bar->full[s], ph, limit, abort, jobs.status, 4);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), limit, abort, jobs.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
               issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, J.n), idesc);
@@ -551,7 +550,7 @@ constexpr int kRStageBytes = 2 * kTileBytes;        // hi + lo of one 64-wide ch
 constexpr int kResBytes = 8 * kTileBytes;           // {GR, GW} x {hi, lo} x 2 chunks
 
 struct ResBarriers {
-  uint64_t full[kRStages];
+  uint64_t full[2][kRStages];   // one set per MMA issuer, as in Barriers
   uint64_t empty[kRStages];
   uint64_t res_full, res_empty;
   uint64_t acc_full[2];
@@ -609,7 +608,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     tc::mbar_init(&bar->res_full, 1);
@@ -639,7 +639,9 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      long long it = 0, tt = 0;
+      long long it = 0;
+      tc::RingPhases ring;
+      long long tt = 0;
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++tt) {
         const int b = (int)(t / tiles_per_b);
         const int r = (int)(t % tiles_per_b);
@@ -660,29 +662,24 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
               const int s = (int)(it % kRStages);
               const uint32_t ph = (uint32_t)((it / kRStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              tc::mbar_arrive_expect_tx(&bar->full[s], kRStageBytes);
+              uint64_t *fb = &bar->full[half][s];
+              ring.take(half, s);
+              tc::mbar_arrive_expect_tx(fb, kRStageBytes);
               uint8_t *st = stages + (size_t)s * kRStageBytes;
               const int x = kc * kChunk;
               if (half == 0) {
-                tc::tma_load_3d(st, &tmA_hi, &bar->full[s], x, P0, b * a.n + v);
-                tc::tma_load_3d(st + kTileBytes, &tmA_lo, &bar->full[s], x, P0, b * a.n + v);
+                tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
+                tc::tma_load_3d(st + kTileBytes, &tmA_lo, fb, x, P0, b * a.n + v);
               } else {
-                tc::tma_load_3d(st, &tmU_hi, &bar->full[s], x, R0, v);
-                tc::tma_load_3d(st + kTileBytes, &tmU_lo, &bar->full[s], x, R0, v);
+                tc::tma_load_3d(st, &tmU_hi, fb, x, R0, v);
+                tc::tma_load_3d(st + kTileBytes, &tmU_lo, fb, x, R0, v);
               }
             }
           }
         }
       }
-      // wind down: every copy issued must have landed before the CTA exits
-      for (int s = 0; s < kRStages; ++s) {
-        long long last = it - 1 - ((it - 1 - s) % kRStages + kRStages) % kRStages;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kRStages) & 1);
-          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      // wind down: every stage issued must have landed before the CTA exits
+      tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
       if (tt > 0) {
         const uint32_t ph = (uint32_t)((tt - 1) & 1);
         for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->res_full, ph); ++i) {
@@ -693,7 +690,9 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
     // MMA issuers: warp 1 the B halves, warp 6 the C halves
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
-      long long it = 0, acc_it = 0, tt = 0;
+      long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
+      long long tt = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++tt) {
         const uint32_t idesc = idesc_cols((int)((t % tiles_per_b) % tP) * kTile, a.N);   // R side
@@ -713,8 +712,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kRStages);
-              const uint32_t ph = (uint32_t)((it / kRStages) & 1);
-              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
               const uint32_t sh = smem_u32(stages + (size_t)s * kRStageBytes), sl = sh + kTileBytes;
@@ -767,7 +765,7 @@ constexpr int kPStageBytes = 2 * kPATile + 2 * kPBTile;   // A hi/lo + B-half hi
 constexpr uint32_t kPairIdesc = tc::idesc_f16_f32(2 * kTile, kTile);
 
 struct PairBarriers {
-  uint64_t full[kPStages];    // even CTA: both CTAs' copies of a stage have landed
+  uint64_t full[2][kPStages]; // even CTA: both CTAs' copies of a stage have landed (one set per issuer)
   uint64_t empty[kPStages];   // each CTA: the pair's MMAs are done with its copy of a stage
   uint64_t acc_full[2];       // each CTA: B_v and C_v of an accumulator buffer are complete
   uint64_t acc_empty[2];      // even CTA: the 8 epilogue warps of the pair have read a buffer
@@ -799,7 +797,7 @@ __device__ __forceinline__ void issue_chunk_pair(uint32_t acc, uint32_t st, bool
   else issue_chunk_pair_ks<1>(acc, st, first);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
     k_sox_bcd_pair(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                    const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                    const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -819,14 +817,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPStages; ++s) {
-      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->full[0][s], 1);
+      tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&bar->acc_full[b], 1);
+      tc::mbar_init(&bar->acc_full[b], 2);   // one multicast commit per issuing warp
       tc::mbar_init(&bar->acc_empty[b], 8);
     }
-    tc::mbar_init(&bar->drain, 1);
+    tc::mbar_init(&bar->drain, 2);
     bar->abort = 0;
     tc::fence_barrier_init();
   }
@@ -845,13 +844,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
   tc::tc_fence_after();
   const uint32_t tmem = bar->tmem_base;
   volatile int *abort = &bar->abort;
-  const uint32_t full0 = tc::mapa_shared(tc::smem_u32(&bar->full[0]), 0);
+  const uint32_t full0 = tc::mapa_shared(tc::smem_u32(&bar->full[0][0]), 0);   // full[q][s]: + (q S + s) 8
   const uint32_t acc_empty0 = tc::mapa_shared(tc::smem_u32(&bar->acc_empty[0]), 0);
 
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
       long long it = 0;
+      tc::RingPhases ring;
       for (long long u = pair; u < total && !*abort; u += npairs) {
         const int b = (int)(u / units_per_b);
         const int r = (int)(u % units_per_b);
@@ -863,8 +863,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
               const int s = (int)(it % kPStages);
               const uint32_t ph = (uint32_t)((it / kPStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              if (rank == 0) tc::mbar_arrive_expect_tx(&bar->full[s], 2 * kPStageBytes);
-              const uint32_t fb = full0 + (uint32_t)s * 8u;
+              ring.take(half, s);   // the half's issuer
+              if (rank == 0) tc::mbar_arrive_expect_tx(&bar->full[half][s], 2 * kPStageBytes);
+              const uint32_t fb = full0 + (uint32_t)(half * kPStages + s) * 8u;
               uint8_t *st = smem + (size_t)s * kPStageBytes;
               const int x = kc * kChunk;
               if (half == 0) {   // B_v = A_v . GR^T
@@ -883,21 +884,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
         }
       }
       // wind down (even CTA): every stage issued by either CTA has landed
-      if (rank == 0) {
-        for (int s = 0; s < kPStages; ++s) {
-          long long last = it - 1 - ((it - 1 - s) % kPStages + kPStages) % kPStages;
-          if (last >= 0 && last < it) {
-            const uint32_t ph = (uint32_t)((last / kPStages) & 1);
-            for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-            }
-          }
-        }
-      }
+      if (rank == 0) tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer (even CTA) ----------------
+  } else if (warp == 1 || warp == 6) {
+    // ---------------- MMA issuers (even CTA): warp 1 the B halves, warp 6 the C halves ----------------
     if (lane == 0 && rank == 0) {
+      const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long u = pair; u < total && ok && !*abort; u += npairs) {
         for (int v = a.v0; v < a.v1 && ok; ++v, ++acc_it) {
@@ -907,11 +901,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
           if (!ok) break;
           tc::tc_fence_after();
           for (int half = 0; half < 2 && ok; ++half) {
+            if (half != my) {
+              it += nk;
+              continue;
+            }
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = (int)(it % kPStages);
-              const uint32_t ph = (uint32_t)((it / kPStages) & 1);
-              ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
               issue_chunk_pair(acc, tc::smem_u32(smem + (size_t)s * kPStageBytes), kc == 0, chunk_steps(kc, a.n));
@@ -926,7 +923,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
       for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->drain, 0); ++i) {
       }
     }
-  } else {
+  } else if (warp >= 2 && warp <= 5) {
     // ---------------- epilogue (both CTAs): D[P, R] += B_v * C_v in registers ----------------
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row = q * 32 + lane;          // P offset inside this CTA's tile
@@ -1094,8 +1091,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      long long it = 0;
-      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
+      long long it = 0, tt = 0;
+      tc::RingPhases ring;
+      for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++tt) {
+        const int q = (int)(tt & 1);   // issuer of this tile
         const int b = (int)(t / per_b);
         const long long r = t % per_b;
         const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
@@ -1105,27 +1104,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const int s = (int)(it % kGStages);
           const uint32_t ph = (uint32_t)((it / kGStages) & 1);
           if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-          tc::mbar_arrive_expect_tx(&bar->full[s], kStageBytes);
+          uint64_t *fb = &bar->full[q][s];
+          ring.take(q, s);
+          tc::mbar_arrive_expect_tx(fb, kStageBytes);
           const int x = kc * kChunk;
-          tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, &bar->full[s], x, i0, za);
-          tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, &bar->full[s], x, i0, za);
-          tc::tma_load_3d(stage_ptr(smem, s, 2), &tmB_hi, &bar->full[s], x, j0, zb);
-          tc::tma_load_3d(stage_ptr(smem, s, 3), &tmB_lo, &bar->full[s], x, j0, zb);
+          tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, fb, x, i0, za);
+          tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, fb, x, i0, za);
+          tc::tma_load_3d(stage_ptr(smem, s, 2), &tmB_hi, fb, x, j0, zb);
+          tc::tma_load_3d(stage_ptr(smem, s, 3), &tmB_lo, fb, x, j0, zb);
         }
       }
-      for (int s = 0; s < kGStages; ++s) {
-        long long last = it - 1 - ((it - 1 - s) % kGStages + kGStages) % kGStages;
-        if (last >= 0 && last < it) {
-          const uint32_t ph = (uint32_t)((last / kGStages) & 1);
-          for (long long i = 0; i < wind_down_limit(a.spin_limit) && !tc::mbar_try_wait(&bar->full[s], ph); ++i) {
-          }
-        }
-      }
+      tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
     }
   } else if (warp == 1 || warp == 10) {
     if (lane == 0) {
       const long long my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
+      tc::RingPhases ring;   // this issuer's phases on its set, full[my][.]
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok && !*abort; t += gridDim.x, ++acc_it) {
         if ((acc_it & 1) != my) {   // the other issuer's tile
@@ -1140,8 +1135,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t acc = tmem + buf * 128;
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = (int)(it % kGStages);
-          const uint32_t ph = (uint32_t)((it / kGStages) & 1);
-          ok = tc::mbar_wait(&bar->full[s], ph, a.spin_limit, abort, a.status, 4);
+          ok = tc::mbar_wait(&bar->full[my][s], ring.take((int)my, s), a.spin_limit, abort, a.status, 4);
           if (!ok) break;
           tc::tc_fence_after();
           issue_chunk(acc, stage_ptr(smem, s, 0), kc == 0, chunk_steps(kc, kv));
@@ -1651,7 +1645,7 @@ cudaError_t pair_capacity(int *pairs) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
-  cfg.blockDim = dim3(kBcdThreads, 1, 1);
+  cfg.blockDim = dim3(kBcdThreads2, 1, 1);
   cfg.dynamicSmemBytes = pair_smem_bytes();
   int n = 0;
   e = cudaOccupancyMaxActiveClusters(&n, k_sox_bcd_pair, &cfg);
@@ -1684,7 +1678,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     const int tP = (a.N + kTile - 1) / kTile;
     const long long units = (long long)a.batch * ((tP + 1) / 2) * tP;
     const int g = 2 * (int)std::max<long long>(1, std::min<long long>(units, pairs));
-    k_sox_bcd_pair<<<g, kBcdThreads, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
+    k_sox_bcd_pair<<<g, kBcdThreads2, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
                                                             maps[10], maps[11], a);
     return cudaGetLastError();
   }
