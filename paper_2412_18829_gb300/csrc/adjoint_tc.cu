@@ -162,7 +162,7 @@ __global__ void k_xbar_factor(AdjScalars *sc) {
 //   B~_v = A~_v GR~^T, C~_v = GWt~ U2~_v^T in TMEM (double-buffered), and in the epilogue
 //   Bbar_v = cg_b E o C~_v, Cbar_v = cg_b E o B~_v -> FP16 pairs [b][v][R][P],
 //   Ebar  += B~_v o C~_v (registers), written em_b * sum at the end of the tile.
-// Warp 0: TMA, warps 1 and 2: MMA (one thread each: the B_v and the C_v halves), warps 4-11:
+// Warp 0: TMA, warps 1 and 2: MMA (one thread each: the B_v and the C_v chunks), warps 4-11:
 // pair writers, warps 12-19: Ebar accumulators (lane quarter warp % 4, column half by
 // warpgroup).
 // ============================================================================
@@ -385,8 +385,8 @@ __global__ void __launch_bounds__(kProdThreads, 1)
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int half = 0; half < 2; ++half) {
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+          for (int kc = 0; kc < nk && !*abort; ++kc) {
+            for (int half = 0; half < 2; ++half, ++it) {
               const int s = (int)(it % kSt);
               const uint32_t ph = (uint32_t)((it / kSt) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -414,8 +414,9 @@ __global__ void __launch_bounds__(kProdThreads, 1)
       tc::ring_wind_down(bar->full, ring, wind_down(a.spin_limit));
     }
   } else if (warp == 1 || warp == 2) {
-    // two MMA issuers, warp 1 the B_v halves and warp 2 the C_v halves (each into its own
-    // accumulators): while one waits for a stage the other keeps the tensor pipe fed
+    // two MMA issuers, warp 1 the B_v chunks and warp 2 the C_v chunks (each into its own
+    // accumulators; the producer alternates them in the ring): while one waits for a stage
+    // the other keeps the tensor pipe fed
     if (lane == 0) {
       const int my = warp - 1;
       long long it = 0, acc_it = 0;
@@ -432,14 +433,11 @@ __global__ void __launch_bounds__(kProdThreads, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          for (int half = 0; half < 2 && ok; ++half) {
-            if (half != my) {
-              it += nk;
-              continue;
-            }
+          {   // this issuer's chunks sit at every other ring position
+            const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-              const int s = (int)(it % kSt);
+            for (int kc = 0; kc < nk; ++kc) {
+              const int s = (int)((it + 2 * kc + my) % kSt);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -449,6 +447,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
               tc::mma_commit(&bar->empty[s]);
             }
           }
+          it += 2 * nk;
           if (ok) tc::mma_commit(&bar->acc_full[buf]);
         }
       }

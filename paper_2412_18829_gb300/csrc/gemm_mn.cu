@@ -30,9 +30,12 @@ constexpr int kPart = kT * kC * 2;            // 16 KB: hi (or lo) of one operan
 constexpr int kStageBytes = 4 * kPart;        // A hi, A lo, B hi, B lo
 constexpr int kStages = 3;
 constexpr int kOutBytes = kT * 64 * 4;        // FP32 staging of one 64-column half of an output tile
-// warp 0 TMA, warps 1 and 10 MMA (even and odd accumulation windows: one issuer keeps the
-// tensor pipe fed while the other waits for a stage), warps 2-9 epilogue; eleven warps take
-// the registers of twelve, as ten do
+// warp 0 TMA, warps 1 and 10 MMA, warps 2-9 epilogue; eleven warps take the registers of
+// twelve, as ten do.  The accumulation windows of an item go two at a time, their chunks
+// alternating in the stage ring, the even window issued by warp 1 and the odd one by warp
+// 10: one issuer keeps the tensor pipe fed while the other waits for a stage.  Four TMEM
+// accumulators (window w in buffer w % 4) let a pair accumulate while the epilogue drains
+// the previous pair.
 constexpr int kThreads = 352;
 constexpr int kEpi = 256;
 
@@ -43,8 +46,8 @@ constexpr int kEpi = 256;
 struct Bars {
   uint64_t full[2][kStages];
   uint64_t empty[kStages];
-  uint64_t acc_full[2];
-  uint64_t acc_empty[2];
+  uint64_t acc_full[4];    // window w accumulates in TMEM buffer w % 4
+  uint64_t acc_empty[4];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&bar->full[1][s], 1);
       tc::mbar_init(&bar->empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       tc::mbar_init(&bar->acc_full[b], 1);
       tc::mbar_init(&bar->acc_empty[b], kEpi);
     }
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_barrier_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(&bar->tmem_base, 256);
+    tc::tmem_alloc(&bar->tmem_base, 512);
     tc::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
@@ -183,21 +186,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::RingPhases ring;
       for (long long t = blockIdx.x; t < items && !*abort; t += gridDim.x) {
         const Item w = item_of(a, t, tM, tN, chunks);
-        for (long long c = w.c0; c < w.c1 && !*abort; ++c, ++it) {
-          const int s = (int)(it % kStages);
-          const uint32_t ph = (uint32_t)((it / kStages) & 1);
-          if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-          const int q = (int)((acc0 + (c - w.c0) / a.window) & 1);   // issuer of the chunk's window
-          uint64_t *fb = &bar->full[q][s];
-          ring.take(q, s);
-          tc::mbar_arrive_expect_tx(fb, kStageBytes);
-          const long long kz = c / a.kc_inner;
-          const int k0 = (int)(c % a.kc_inner) * kC;
-          uint8_t *st = smem + (size_t)s * kStageBytes;
-          load_operand(st, &tmA_hi, &tmA_lo, fb, a.a.mn_major, w.i0, k0,
-                       (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
-          load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, fb, a.b.mn_major, w.j0, k0,
-                       (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
+        // the item's windows two at a time, their chunks alternating in the ring
+        for (long long p0 = w.c0; p0 < w.c1 && !*abort; p0 += 2 * a.window) {
+          const long long L0 = w.c1 - p0 < a.window ? w.c1 - p0 : a.window;
+          const long long r1 = w.c1 - p0 - a.window;
+          const long long L1 = r1 <= 0 ? 0 : (r1 < a.window ? r1 : a.window);
+          const long long wi = acc0 + (p0 - w.c0) / a.window;   // the pair's first window
+          for (long long i = 0; i < L0 && !*abort; ++i) {
+            for (int hh = 0; hh < 2 && (hh == 0 || i < L1); ++hh, ++it) {
+              const int s = (int)(it % kStages);
+              const uint32_t ph = (uint32_t)((it / kStages) & 1);
+              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+              const int q = (int)((wi + hh) & 1);   // issuer of the chunk's window
+              uint64_t *fb = &bar->full[q][s];
+              ring.take(q, s);
+              tc::mbar_arrive_expect_tx(fb, kStageBytes);
+              const long long c = p0 + hh * a.window + i;
+              const long long kz = c / a.kc_inner;
+              const int k0 = (int)(c % a.kc_inner) * kC;
+              uint8_t *st = smem + (size_t)s * kStageBytes;
+              load_operand(st, &tmA_hi, &tmA_lo, fb, a.a.mn_major, w.i0, k0,
+                           (int)(a.a.z0 + (w.b / a.a.zdiv) * a.a.zb + kz * a.a.zk));
+              load_operand(st + 2 * kPart, &tmB_hi, &tmB_lo, fb, a.b.mn_major, w.j0, k0,
+                           (int)(a.b.z0 + (w.b / a.b.zdiv) * a.b.zb + kz * a.b.zk));
+            }
+          }
         }
         if (w.c1 > w.c0) acc0 += (w.c1 - w.c0 + a.window - 1) / a.window;
       }
@@ -217,39 +230,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int wN = a.Ncols - w.j0 >= kT ? kT : ((a.Ncols - w.j0 + 15) & ~15);
         const uint32_t idesc = tc::idesc_f16_f32(kT, wN) | ((uint32_t)a.a.mn_major << 15) |
                                ((uint32_t)a.b.mn_major << 16);
-        for (long long w0 = w.c0; w0 < w.c1 && ok; w0 += a.window, ++acc_it) {
-          const long long w1 = w0 + a.window < w.c1 ? w0 + a.window : w.c1;
-          if ((acc_it & 1) != my) {   // the other issuer's window
-            it += w1 - w0;
-            continue;
-          }
-          const int buf = (int)(acc_it & 1);
-          const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
-          ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
-          if (!ok) break;
-          tc::tc_fence_after();
-          const uint32_t acc = tmem + buf * kT;
-          for (long long c = w0; c < w1; ++c, ++it) {
-            const int s = (int)(it % kStages);
-            ok = tc::mbar_wait(&bar->full[my][s], ring.take((int)my, s), a.spin_limit, abort, a.status, 4);
+        for (long long p0 = w.c0; p0 < w.c1 && ok; p0 += 2 * a.window) {
+          const long long L0 = w.c1 - p0 < a.window ? w.c1 - p0 : a.window;
+          const long long r1 = w.c1 - p0 - a.window;
+          const long long L1 = r1 <= 0 ? 0 : (r1 < a.window ? r1 : a.window);
+          const int hh = (int)((my - acc_it) & 1);   // this issuer's window of the pair: acc_it + hh
+          const long long Lh = hh ? L1 : L0;
+          if (Lh > 0) {
+            const long long wi = acc_it + hh;
+            const int buf = (int)(wi & 3);
+            const uint32_t aph = (uint32_t)((wi >> 2) & 1);
+            ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
             if (!ok) break;
             tc::tc_fence_after();
-            const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
-            const uint32_t ahi = st, alo = st + kPart, bhi = st + 2 * kPart, blo = st + 3 * kPart;
-            const bool first = (c == w0);
-            // the small cross terms first, the large hi*hi steps last (truncating accumulation)
+            const uint32_t acc = tmem + buf * kT;
+            for (long long i = 0; i < Lh; ++i) {
+              // ring position of chunk i: the pair alternates while both windows have chunks
+              const long long pos = it + (i < L1 ? 2 * i + hh : 2 * L1 + (i - L1));
+              const int s = (int)(pos % kStages);
+              ok = tc::mbar_wait(&bar->full[my][s], ring.take((int)my, s), a.spin_limit, abort, a.status, 4);
+              if (!ok) break;
+              tc::tc_fence_after();
+              const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
+              const uint32_t ahi = st, alo = st + kPart, bhi = st + 2 * kPart, blo = st + 3 * kPart;
+              const bool first = (i == 0);
+              // the small cross terms first, the large hi*hi steps last (truncating accumulation)
 #pragma unroll
-            for (int k = 0; k < kC / 16; ++k) {
-              tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(blo, a.b.mn_major, k), idesc,
-                          (first && k == 0) ? 0u : 1u);
-              tc::mma_f16(acc, op_desc(alo, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
+              for (int k = 0; k < kC / 16; ++k) {
+                tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(blo, a.b.mn_major, k), idesc,
+                            (first && k == 0) ? 0u : 1u);
+                tc::mma_f16(acc, op_desc(alo, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
+              }
+#pragma unroll
+              for (int k = 0; k < kC / 16; ++k)
+                tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
+              tc::mma_commit(&bar->empty[s]);
             }
-#pragma unroll
-            for (int k = 0; k < kC / 16; ++k)
-              tc::mma_f16(acc, op_desc(ahi, a.a.mn_major, k), op_desc(bhi, a.b.mn_major, k), idesc, 1u);
-            tc::mma_commit(&bar->empty[s]);
+            if (ok) tc::mma_commit(&bar->acc_full[buf]);
           }
-          if (ok) tc::mma_commit(&bar->acc_full[buf]);
+          it += L0 + L1;
+          acc_it += L1 > 0 ? 2 : 1;
         }
       }
       tc::mma_commit(&bar->drain);
@@ -271,8 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int j = 0; j < 64; ++j) sum[j] = 0.f;
       for (long long w0 = w.c0; w0 < w.c1; w0 += a.window, ++acc_it) {
-        const int buf = (int)(acc_it & 1);
-        const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
+        const int buf = (int)(acc_it & 3);
+        const uint32_t aph = (uint32_t)((acc_it >> 2) & 1);
         const bool got = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
         if (!epi_all(got && !*abort)) {
           live = false;
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 256);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 

@@ -150,19 +150,21 @@ __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
   }
 }
 
-// Fused kernels: warp 0 TMA, warp 1 MMA (and warp 6, see kBcdThreads2), warps 2..5 epilogue
-// (one per TMEM lane quarter, 128 columns each).  Measured: the epilogue is not the limit (a
-// variant that skips its TMEM loads runs at the same speed), so it stays at
-// four warps with 255 registers available.
-constexpr int kBcdThreads = 192;
-constexpr int kEpiThreads = 128;
-// With two MMA-issuing warps (warp 1: the B_v halves, warp 6: the C_v halves; each into its
-// own accumulators, so every accumulator still receives its MMAs from one thread in order).
+// Fused kernels: warp 0 TMA, warps 1 and 6 MMA, warps 2..5 epilogue (one per TMEM lane
+// quarter, 128 columns each).  Measured: the epilogue is not the limit (a variant that
+// skips its TMEM loads runs at the same speed), so it stays at four warps with 255
+// registers available.
+// Two MMA-issuing warps, warp 1 for the B_v halves and warp 6 for the C_v halves, each into
+// its own accumulators (so every accumulator receives its MMAs from one thread, in order).
 // An issuing thread stalls at each wait for a stage, and the tensor pipe holds few MMAs
 // ahead of it, so one issuer leaves the pipe idle at every wait; with two, one issues while
-// the other waits (the mid-size build's fused kernel: 9.4 -> 7.5 ms).  Seven warps take the
-// same registers as six (registers are granted per four warps).
-constexpr int kBcdThreads2 = 224;
+// the other waits.  The producer alternates B and C chunks in the stage ring (B_v chunk kc
+// at ring position 2kc, C_v chunk kc at 2kc + 1 of the v's 2 nk positions), so both issuers
+// always have a chunk in flight.  Measured on the mid-size build's fused kernel: one issuer
+// 9.4 ms, two issuers over B-then-C halves 7.6 ms, alternating chunks 7.1 ms.  Seven warps
+// take the same registers as six (registers are granted per four warps).
+constexpr int kBcdThreads = 224;
+constexpr int kEpiThreads = 128;
 
 // Epilogue of the fused kernels: D[P, R] += B_v[P, R] * C_v[P, R] over v, in
 // registers; B_v at TMEM columns [buf*256, +128), C_v at [buf*256 + 128, +128).
@@ -222,7 +224,7 @@ __device__ __forceinline__ void bcd_epilogue(Bar *bar, uint32_t tmem, const BcdA
 // (double-buffered), the Hadamard product accumulates in registers, and only
 // D leaves the SM, written transposed and rescaled: Dt[b][R][P].
 // ============================================================================
-__global__ void __launch_bounds__(kBcdThreads2, 1)
+__global__ void __launch_bounds__(kBcdThreads, 1)
     k_sox_bcd_tc(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                  const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                  const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -276,8 +278,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int half = 0; half < 2; ++half) {
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+          for (int kc = 0; kc < nk && !*abort; ++kc) {
+            for (int half = 0; half < 2; ++half, ++it) {
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
       tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
     }
   } else if (warp == 1 || warp == 6) {
-    // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
+    // ---------------- MMA issuers: warp 1 the B_v chunks, warp 6 the C_v chunks ----------------
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
@@ -318,14 +320,11 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          for (int half = 0; half < 2 && ok; ++half) {
-            if (half != my) {
-              it += nk;
-              continue;
-            }
+          {   // this issuer's chunks sit at every other ring position
+            const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-              const int s = (int)(it % kStages);
+            for (int kc = 0; kc < nk; ++kc) {
+              const int s = (int)((it + 2 * kc + my) % kStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -333,6 +332,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
               tc::mma_commit(&bar->empty[s]);
             }
           }
+          it += 2 * nk;
           if (ok) tc::mma_commit(&bar->acc_full[buf]);
         }
       }
@@ -378,7 +378,7 @@ __device__ __forceinline__ MultiTile multi_tile(const BcdJobs &jobs, long long t
   return m;
 }
 
-__global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_constant__ BcdJobs jobs) {
+__global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_constant__ BcdJobs jobs) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Barriers *bar = reinterpret_cast<Barriers *>(smem + kStages * kStageBytes);
@@ -420,8 +420,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
         const BcdJob &J = jobs.job[m.j];
         const int nk = J.Kp / kChunk;
         for (int v = J.v0; v < J.v1 && !*abort; ++v) {
-          for (int half = 0; half < 2; ++half) {
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+          for (int kc = 0; kc < nk && !*abort; ++kc) {
+            for (int half = 0; half < 2; ++half, ++it) {
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
       tc::ring_wind_down(bar->full, ring, wind_down_limit(limit));
     }
   } else if (warp == 1 || warp == 6) {
-    // ---------------- MMA issuers: warp 1 the B halves, warp 6 the C halves ----------------
+    // ---------------- MMA issuers: warp 1 the B_v chunks, warp 6 the C_v chunks ----------------
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
@@ -465,14 +465,11 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, limit, abort, jobs.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          for (int half = 0; half < 2 && ok; ++half) {
-            if (half != my) {
-              it += nk;
-              continue;
-            }
+          {   // this issuer's chunks sit at every other ring position
+            const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-              const int s = (int)(it % kStages);
+            for (int kc = 0; kc < nk; ++kc) {
+              const int s = (int)((it + 2 * kc + my) % kStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), limit, abort, jobs.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -480,6 +477,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1) k_sox_bcd_multi(const __grid_
               tc::mma_commit(&bar->empty[s]);
             }
           }
+          it += 2 * nk;
           if (ok) tc::mma_commit(&bar->acc_full[buf]);
         }
       }
@@ -589,7 +587,7 @@ __device__ __forceinline__ void issue_chunk4(uint32_t acc, uint32_t a_hi, uint32
   else issue_chunk4_ks<1>(acc, a_hi, a_lo, b_hi, b_lo, first, idesc);
 }
 
-__global__ void __launch_bounds__(kBcdThreads2, 1)
+__global__ void __launch_bounds__(kBcdThreads, 1)
     k_sox_bcd_tc_res(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                      const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                      const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -657,8 +655,8 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
           tc::tma_load_3d(res_ptr(res, 1, 1, kc), &tmGW_lo, &bar->res_full, x, P0, b);
         }
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int half = 0; half < 2; ++half) {
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+          for (int kc = 0; kc < nk && !*abort; ++kc) {
+            for (int half = 0; half < 2; ++half, ++it) {
               const int s = (int)(it % kRStages);
               const uint32_t ph = (uint32_t)((it / kRStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -687,7 +685,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
       }
     }
   } else if (warp == 1 || warp == 6) {
-    // MMA issuers: warp 1 the B halves, warp 6 the C halves
+    // MMA issuers: warp 1 the B_v chunks, warp 6 the C_v chunks
     if (lane == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
@@ -704,14 +702,11 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          for (int half = 0; half < 2 && ok; ++half) {
-            if (half != my) {
-              it += nk;
-              continue;
-            }
+          {   // this issuer's chunks sit at every other ring position
+            const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-              const int s = (int)(it % kRStages);
+            for (int kc = 0; kc < nk; ++kc) {
+              const int s = (int)((it + 2 * kc + my) % kRStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -726,6 +721,7 @@ __global__ void __launch_bounds__(kBcdThreads2, 1)
               tc::mma_commit(&bar->empty[s]);
             }
           }
+          it += 2 * nk;
           if (ok) tc::mma_commit(&bar->acc_full[buf]);
         }
         if (ok) tc::mma_commit(&bar->res_empty);   // resident tiles free once these MMAs retire
@@ -797,7 +793,7 @@ __device__ __forceinline__ void issue_chunk_pair(uint32_t acc, uint32_t st, bool
   else issue_chunk_pair_ks<1>(acc, st, first);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
     k_sox_bcd_pair(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                    const __grid_constant__ CUtensorMap tmGR_hi, const __grid_constant__ CUtensorMap tmGR_lo,
                    const __grid_constant__ CUtensorMap tmGW_hi, const __grid_constant__ CUtensorMap tmGW_lo,
@@ -858,8 +854,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
         const int P0 = (2 * (r / tP) + (int)rank) * kTile;
         const int R0 = (r % tP) * kTile + (int)rank * (kTile / 2);
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int half = 0; half < 2; ++half) {
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+          for (int kc = 0; kc < nk && !*abort; ++kc) {
+            for (int half = 0; half < 2; ++half, ++it) {
               const int s = (int)(it % kPStages);
               const uint32_t ph = (uint32_t)((it / kPStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -887,7 +883,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
       if (rank == 0) tc::ring_wind_down(bar->full, ring, wind_down_limit(a.spin_limit));
     }
   } else if (warp == 1 || warp == 6) {
-    // ---------------- MMA issuers (even CTA): warp 1 the B halves, warp 6 the C halves ----------------
+    // ---------------- MMA issuers (even CTA): warp 1 the B_v chunks, warp 6 the C_v chunks ----------------
     if (lane == 0 && rank == 0) {
       const int my = (warp == 1) ? 0 : 1;
       long long it = 0, acc_it = 0;
@@ -900,14 +896,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          for (int half = 0; half < 2 && ok; ++half) {
-            if (half != my) {
-              it += nk;
-              continue;
-            }
+          {   // this issuer's chunks sit at every other ring position
+            const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
-              const int s = (int)(it % kPStages);
+            for (int kc = 0; kc < nk; ++kc) {
+              const int s = (int)((it + 2 * kc + my) % kPStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -915,6 +908,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads2, 1)
               tc::mma_commit_pair_mc(&bar->empty[s], 3);
             }
           }
+          it += 2 * nk;
           if (ok) tc::mma_commit_pair_mc(&bar->acc_full[buf], 3);
         }
       }
@@ -1645,7 +1639,7 @@ cudaError_t pair_capacity(int *pairs) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
-  cfg.blockDim = dim3(kBcdThreads2, 1, 1);
+  cfg.blockDim = dim3(kBcdThreads, 1, 1);
   cfg.dynamicSmemBytes = pair_smem_bytes();
   int n = 0;
   e = cudaOccupancyMaxActiveClusters(&n, k_sox_bcd_pair, &cfg);
@@ -1664,7 +1658,7 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     static std::atomic<unsigned long long> rattr{0};
     const cudaError_t e = set_smem_once(k_sox_bcd_tc_res, (int)res_smem_bytes(), rattr);
     if (e != cudaSuccess) return e;
-    k_sox_bcd_tc_res<<<grid, kBcdThreads2, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+    k_sox_bcd_tc_res<<<grid, kBcdThreads, res_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                maps[5], maps[6], maps[7], a);
     return cudaGetLastError();
   }
@@ -1678,14 +1672,14 @@ cudaError_t launch_sox_bcd_tc(const CUtensorMap *maps, const BcdArgs &args, int 
     const int tP = (a.N + kTile - 1) / kTile;
     const long long units = (long long)a.batch * ((tP + 1) / 2) * tP;
     const int g = 2 * (int)std::max<long long>(1, std::min<long long>(units, pairs));
-    k_sox_bcd_pair<<<g, kBcdThreads2, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
+    k_sox_bcd_pair<<<g, kBcdThreads, pair_smem_bytes(), s>>>(maps[0], maps[1], maps[8], maps[9], maps[4], maps[5],
                                                             maps[10], maps[11], a);
     return cudaGetLastError();
   }
   static std::atomic<unsigned long long> attr{0};
   const cudaError_t e = set_smem_once(k_sox_bcd_tc, (int)tc_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  k_sox_bcd_tc<<<grid, kBcdThreads2, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+  k_sox_bcd_tc<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                                         maps[6], maps[7], a);
   return cudaGetLastError();
 }
@@ -1696,7 +1690,7 @@ cudaError_t launch_sox_bcd_multi(const BcdJobs &jobs, int grid, cudaStream_t s) 
   static std::atomic<unsigned long long> attr{0};
   const cudaError_t e = set_smem_once(k_sox_bcd_multi, (int)tc_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  k_sox_bcd_multi<<<grid, kBcdThreads2, tc_smem_bytes(), s>>>(jobs);
+  k_sox_bcd_multi<<<grid, kBcdThreads, tc_smem_bytes(), s>>>(jobs);
   return cudaGetLastError();
 }
 
