@@ -84,7 +84,9 @@ typedef struct {
   long long spin_limit; /* iteration cap for device-side waits; 0 = default      */
   long long workspace_limit; /* bytes of chunked intermediates each entry point
                           * sizes its tau / v chunks for; 0 = the library's
-                          * defaults (12-32 GiB per path).  A chunk of one tau
+                          * defaults (12-32 GiB per path; 64 GiB for the
+                          * split-precision adjoint, 128 GiB for the uneven
+                          * batch).  A chunk of one tau
                           * point (or one v) is used even when it exceeds the
                           * limit; fixed-size tensors (mixed tensors, the D
                           * array of the dynamic paths) are not counted.      */

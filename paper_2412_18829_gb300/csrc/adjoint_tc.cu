@@ -548,7 +548,10 @@ AdjGeom adj_geom(sox_handle h, int n, int N, int T, int S) {
   g.Nn = (long long)N * n;
   g.abar_pitch = (g.Nn + 7) & ~7LL;
   const size_t per = per_tau_bytes(g);
-  const size_t budget = chunk_budget(h, size_t(12) << 30);
+  // 64 GB by default: the largest batch instances (about 9 GB per tau at n = 298) then take
+  // several tau points per chunk, so the per-chunk launches fill whole waves of the SMs (one
+  // tau point of n = 298 is 196 fused-producer tiles, 1.3 waves on 152 SMs)
+  const size_t budget = chunk_budget(h, size_t(64) << 30);
   long long c = (long long)(budget / std::max<size_t>(per, 1));
   c = std::max<long long>(1, std::min<long long>({c, (long long)T, 1024}));
   g.Bc = (int)c;

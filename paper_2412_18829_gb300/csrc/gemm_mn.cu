@@ -449,6 +449,77 @@ __global__ void k_split_tensor(const T *src, long long ld0, int rows0, long long
   if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
 }
 
+// FP32 rows with unit column stride, two columns per lane (8-byte loads, 4-byte stores):
+// the same values as the kernels above, for rows whose starts are 8-byte aligned in the
+// source and 4-byte aligned in the outputs.  A unit is 512 consecutive columns.
+constexpr int kUnitCols2 = 512;
+
+__global__ void k_absmax_f32x2(const float *src, long long ld0, int rows0, long long ld1, int rows1, int cols,
+                               float *out) {
+  const long long cpr = (cols + kUnitCols2 - 1) / kUnitCols2;
+  const long long units = (long long)rows1 * rows0 * cpr;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  float m = 0.f;
+  for (long long u = warp0; u < units; u += nwarps) {
+    const long long r = u / cpr;
+    const int c0 = (int)(u % cpr) * kUnitCols2;
+    const long long r1 = r / rows0, r0 = r % rows0;
+    const float *row = src + r1 * ld1 + r0 * ld0;
+#pragma unroll
+    for (int k = 0; k < kUnitCols2 / 64; ++k) {
+      const int c = c0 + 2 * lane + 64 * k;
+      if (c + 1 < cols) {
+        const float2 x = *reinterpret_cast<const float2 *>(row + c);
+        m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+      } else if (c < cols) {
+        m = fmaxf(m, fabsf(row[c]));
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(m));
+}
+
+__global__ void k_split_f32x2(const float *src, long long ld0, int rows0, long long ld1, int rows1, int cols,
+                              long long ldo, long long ldo1, float sign, const float *absmax, const float *scale_in,
+                              __half *hi, __half *lo, float *scale_out) {
+  const float s = scale_in ? *scale_in : big_scale(*absmax);
+  const float sf = sign * s;
+  const long long cpr = (ldo + kUnitCols2 - 1) / kUnitCols2;
+  const long long units = (long long)rows1 * rows0 * cpr;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = warp0; u < units; u += nwarps) {
+    const long long r = u / cpr;
+    const long long c0 = (u % cpr) * kUnitCols2;
+    const long long r1 = r / rows0, r0 = r % rows0;
+    const float *row = src + r1 * ld1 + r0 * ld0;
+    __half *h = hi + r1 * ldo1 + r0 * ldo, *l = lo + r1 * ldo1 + r0 * ldo;
+#pragma unroll
+    for (int k = 0; k < kUnitCols2 / 64; ++k) {
+      const long long c = c0 + 2 * lane + 64 * k;
+      if (c >= ldo) break;   // ldo is even: c + 1 < ldo
+      float2 x = make_float2(0.f, 0.f);
+      if (c + 1 < cols) x = *reinterpret_cast<const float2 *>(row + c);
+      else if (c < cols) x.x = row[c];
+      uint32_t a, b;
+      tc::split_f16x2(x.x * sf, x.y * sf, a, b);
+      *reinterpret_cast<uint32_t *>(h + c) = a;
+      *reinterpret_cast<uint32_t *>(l + c) = b;
+    }
+  }
+  if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
+}
+
+// true when the FP32 two-column kernels apply: unit column stride, even row pitches and
+// 8-byte (source) / 4-byte (outputs) aligned bases
+bool f32x2_ok(const void *src, long long ld0, long long ld1, long long ldc) {
+  return ldc == 1 && (ld0 % 2) == 0 && (ld1 % 2) == 0 && (reinterpret_cast<uintptr_t>(src) % 8) == 0;
+}
+
 // blocks of 256 threads (8 warps) for `units` warp-sized work units, at most 32 per SM
 int blocks_for_units(long long units) {
   return (int)std::max<long long>(1, std::min<long long>((units + 7) / 8, 152 * 32));
@@ -494,6 +565,11 @@ cudaError_t launch_gemm_mn(const CUtensorMap *maps, const GemmMnArgs &a, int gri
 
 void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
                    int cols, float *out, cudaStream_t s) {
+  if (f32 && f32x2_ok(src, ld0, ld1, ldc)) {
+    const int blocks = blocks_for_units((long long)rows1 * rows0 * ((cols + kUnitCols2 - 1) / kUnitCols2));
+    k_absmax_f32x2<<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, cols, out);
+    return;
+  }
   const int blocks = blocks_for_units((long long)rows1 * rows0 * ((cols + kUnitCols - 1) / kUnitCols));
   if (f32)
     k_absmax<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols, out);
@@ -504,6 +580,13 @@ void launch_absmax(const void *src, bool f32, long long ld0, int rows0, long lon
 void launch_split_tensor(const void *src, bool f32, long long ld0, int rows0, long long ld1, int rows1, long long ldc,
                          int cols, long long ldo, long long ldo1, float sign, const float *absmax,
                          const float *scale_in, __half *hi, __half *lo, float *scale_out, cudaStream_t s) {
+  if (f32 && f32x2_ok(src, ld0, ld1, ldc) && (ldo % 2) == 0 && (ldo1 % 2) == 0 &&
+      (reinterpret_cast<uintptr_t>(hi) % 4) == 0 && (reinterpret_cast<uintptr_t>(lo) % 4) == 0) {
+    const int blocks = blocks_for_units((long long)rows1 * rows0 * ((ldo + kUnitCols2 - 1) / kUnitCols2));
+    k_split_f32x2<<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, cols, ldo, ldo1,
+                                         sign, absmax, scale_in, hi, lo, scale_out);
+    return;
+  }
   const int blocks = blocks_for_units((long long)rows1 * rows0 * ((ldo + kUnitCols - 1) / kUnitCols));
   if (f32)
     k_split_tensor<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), ld0, rows0, ld1, rows1, ldc, cols,

@@ -283,6 +283,16 @@ __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo) {
   lo = __float2half_rn(x - __half2float(hi));
 }
 
+// The FP16 pairs of x0 and x1 packed two to a word (x0 in the low half): the same values
+// as split_f16 on each, from two packed conversions instead of four single ones.
+__device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 }  // namespace tc
 
 // ------------------------------ host side ----------------------------------
