@@ -1032,6 +1032,8 @@ def run_ours(args):
     elif case.dtype.startswith("f16x2"):
         roof = _tensor_peak(pk, pk_src, achieved)
         roof["kernel"] = case.hot
+        if isinstance(case, BatchCase):
+            roof["kernel"] = "k_sox_bcd_multi (the fused B/C/D kernel, one persistent launch per tau chunk over all instances)"
         w = getattr(case, "w", None)
         if isinstance(case, MoleculeCase) and (w.n, w.N) == BCD_TRAFFIC["shape"] and hot_n:
             b_launch = case.p.n_tau * w.n_spin / (hot_n / args.steps)

@@ -385,8 +385,10 @@ __global__ void __launch_bounds__(kProdThreads, 1)
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int kc = 0; kc < nk && !*abort; ++kc) {
-            for (int half = 0; half < 2; ++half, ++it) {
+          for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
+            {
+              int kc, half;
+              tc::bc_decode(p, nk, 1, kc, half);
               const int s = (int)(it % kSt);
               const uint32_t ph = (uint32_t)((it / kSt) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
-              const int s = (int)((it + 2 * kc + my) % kSt);
+              const int s = (int)((it + tc::bc_pos(kc, my, nk, 1)) % kSt);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();

@@ -77,6 +77,26 @@ struct RingPhases {
   }
 };
 
+// Order of one v's 2 nk chunks in a fused kernel's stage ring (nk chunks each for the B_v
+// and the C_v products, issued by two MMA threads): groups of g chunks of B_v and g of C_v
+// alternate, so ring positions [2gj, 2gj + g) hold B chunks gj .. gj + g - 1 and the next
+// g positions the same C chunks (the last group may be shorter).  g = 1 alternates single
+// chunks, g = nk runs all of B_v's chunks, then all of C_v's.
+// chunk kc and half h (0: B_v, 1: C_v) at position p of the v's chunks
+__device__ __forceinline__ void bc_decode(int p, int nk, int g, int &kc, int &h) {
+  const int j = p / (2 * g);
+  const int gl = min(g, nk - j * g);
+  const int w = p - 2 * g * j;
+  h = w >= gl ? 1 : 0;
+  kc = j * g + w - h * gl;
+}
+// position of chunk kc of half h
+__device__ __forceinline__ int bc_pos(int kc, int h, int nk, int g) {
+  const int j = kc / g, w = kc - j * g;
+  const int gl = min(g, nk - j * g);
+  return 2 * g * j + h * gl + w;
+}
+
 // Producer wind-down: waits (at most `limit` polls each) until the last phase issued on
 // every barrier of both sets has completed, so no TMA write is in flight when the CTA
 // leaves.

@@ -161,7 +161,8 @@ __device__ __forceinline__ void setup_barriers(Barriers *bar, int epi_threads) {
 // the other waits.  The producer alternates B and C chunks in the stage ring (B_v chunk kc
 // at ring position 2kc, C_v chunk kc at 2kc + 1 of the v's 2 nk positions), so both issuers
 // always have a chunk in flight.  Measured on the mid-size build's fused kernel: one issuer
-// 9.4 ms, two issuers over B-then-C halves 7.6 ms, alternating chunks 7.1 ms.  Seven warps
+// 9.4 ms, two issuers over B-then-C halves 7.6 ms, alternating chunks 7.1 ms (n = 298: 39.4 ->
+// 32.8 ms); the multi-instance kernel keeps the B-then-C order (see there).  Seven warps
 // take the same registers as six (registers are granted per four warps).
 constexpr int kBcdThreads = 224;
 constexpr int kEpiThreads = 128;
@@ -278,8 +279,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         const int r = (int)(t % tiles_per_b);
         const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int kc = 0; kc < nk && !*abort; ++kc) {
-            for (int half = 0; half < 2; ++half, ++it) {
+          for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
+            {
+              int kc, half;
+              tc::bc_decode(p, nk, 1, kc, half);
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
-              const int s = (int)((it + 2 * kc + my) % kStages);
+              const int s = (int)((it + tc::bc_pos(kc, my, nk, 1)) % kStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -415,13 +418,20 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
     if (lane == 0) {
       long long it = 0;
       tc::RingPhases ring;
+      // B_v's chunks, then C_v's (group g = nk): over the uneven batch's long launches, which
+      // run under the power cap, this order measured 3 % faster than alternating single
+      // chunks (1.49 vs 1.53 s of fused kernel per batch forward), although alternating wins
+      // 20 % in a single instance's launch (n = 298, 16 tau) and the same in this kernel
+      // with a batch of one
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x) {
         const MultiTile m = multi_tile(jobs, t);
         const BcdJob &J = jobs.job[m.j];
         const int nk = J.Kp / kChunk;
         for (int v = J.v0; v < J.v1 && !*abort; ++v) {
-          for (int kc = 0; kc < nk && !*abort; ++kc) {
-            for (int half = 0; half < 2; ++half, ++it) {
+          for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
+            {
+              int kc, half;
+              tc::bc_decode(p, nk, nk, kc, half);
               const int s = (int)(it % kStages);
               const uint32_t ph = (uint32_t)((it / kStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
@@ -469,7 +479,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
-              const int s = (int)((it + 2 * kc + my) % kStages);
+              const int s = (int)((it + tc::bc_pos(kc, my, nk, nk)) % kStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), limit, abort, jobs.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -655,8 +665,10 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           tc::tma_load_3d(res_ptr(res, 1, 1, kc), &tmGW_lo, &bar->res_full, x, P0, b);
         }
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int kc = 0; kc < nk && !*abort; ++kc) {
-            for (int half = 0; half < 2; ++half, ++it) {
+          for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
+            {
+              int kc, half;
+              tc::bc_decode(p, nk, 1, kc, half);
               const int s = (int)(it % kRStages);
               const uint32_t ph = (uint32_t)((it / kRStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -706,7 +718,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
-              const int s = (int)((it + 2 * kc + my) % kRStages);
+              const int s = (int)((it + tc::bc_pos(kc, my, nk, 1)) % kRStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
@@ -854,8 +866,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
         const int P0 = (2 * (r / tP) + (int)rank) * kTile;
         const int R0 = (r % tP) * kTile + (int)rank * (kTile / 2);
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
-          for (int kc = 0; kc < nk && !*abort; ++kc) {
-            for (int half = 0; half < 2; ++half, ++it) {
+          for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
+            {
+              int kc, half;
+              tc::bc_decode(p, nk, 1, kc, half);
               const int s = (int)(it % kPStages);
               const uint32_t ph = (uint32_t)((it / kPStages) & 1);
               if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
@@ -900,7 +914,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
-              const int s = (int)((it + 2 * kc + my) % kPStages);
+              const int s = (int)((it + tc::bc_pos(kc, my, nk, 1)) % kPStages);
               ok = tc::mbar_wait(&bar->full[my][s], ring.take(my, s), a.spin_limit, abort, a.status, 4);
               if (!ok) break;
               tc::tc_fence_after();
