@@ -332,8 +332,9 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one fused-kernel launch over 16 (spin, tau) batches at n=120,
 # N=600, from an ncu capture of k_sox_bcd_tc; the U2 operand (36.9 MB) is read once per
 # launch, the rest scales with the batches of a launch
-BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726431744 + 20530944, "shared": 36.9e6,
-               "source": "ncu dram__bytes_read+write of k_sox_bcd_tc on 16 batches, scaled to the launch's batches"}
+BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726826496 + 20508672, "shared": 36.9e6,
+               "source": "ncu dram__bytes_read+write of k_sox_bcd_tc_res (the autotuner's pick at this shape; "
+                         "k_sox_bcd_tc reads the same bytes) on 16 batches, scaled to the launch's batches"}
 # DRAM bytes (read + write) of the B and C GEMM launches of one static (tau, v) pair of the
 # 3x3x3 solid (n=26, N=300), from an ncu capture; compared with the pair's algorithmic bytes
 SOLID_BC_TRAFFIC = {"shape": ((3, 3, 3), 26, 300), "bytes": 64460032 + 467337216 + 117393152 + 464741376,
