@@ -102,6 +102,7 @@ __device__ __forceinline__ int bc_pos(int kc, int h, int nk, int g) {
 // leaves.
 template <int S>
 __device__ __forceinline__ void ring_wind_down(uint64_t (&full)[2][S], const RingPhases &r, long long limit) {
+  static_assert(S <= 16, "RingPhases keeps 16 stages per set");
   for (int q = 0; q < 2; ++q)
     for (int s = 0; s < S; ++s)
       if ((r.used >> (16 * q + s)) & 1u) {
