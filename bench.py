@@ -337,7 +337,7 @@ BCD_TRAFFIC = {"shape": (120, 600), "batches": 16, "bytes": 726826496 + 20508672
                          "k_sox_bcd_tc reads the same bytes) on 16 batches, scaled to the launch's batches"}
 # DRAM bytes (read + write) of the B and C GEMM launches of one static (tau, v) pair of the
 # 3x3x3 solid (n=26, N=300), from an ncu capture; compared with the pair's algorithmic bytes
-SOLID_BC_TRAFFIC = {"shape": ((3, 3, 3), 26, 300), "bytes": 64460032 + 467337216 + 117393152 + 464741376,
+SOLID_BC_TRAFFIC = {"shape": ((3, 3, 3), 26, 300), "bytes": 64837120 + 467264000 + 117595392 + 464676864,
                     "source": "ncu dram__bytes_read+write of the B and C k_gemm_f16x2 launches of one static "
                               "(tau, v) pair (profile_case solid f16x2 4)"}
 
