@@ -1044,18 +1044,45 @@ __device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const 
                "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
                : "memory");
 }
+// Output tile t of a GEMM launch: batch b and the tile's first row i0 and column j0.  When
+// every batch shares one B operand (no index table), the column tiles go slowest, then the
+// batches, then the row tiles, so all the tiles that read one B tile run one after another
+// and B leaves DRAM once per launch (the A GEMM of the chain: U_Pqs of up to 0.7 GB read
+// by every (tau, row tile) pair would otherwise be re-read from DRAM for each); otherwise
+// batches slowest, then rows, then columns.
+struct GemmTile {
+  int b, i0, j0;
+};
+__device__ __forceinline__ GemmTile gemm_tile(const GemmTcArgs &a, long long t, int tM, int tN) {
+  GemmTile g;
+  if (a.batchB_shared && !a.idxB) {
+    const long long per_j = (long long)a.batch * tM;
+    const long long j = t / per_j, r = t % per_j;
+    g.b = (int)(r / tM);
+    g.i0 = (int)(r % tM) * kTile;
+    g.j0 = (int)j * kTile;
+  } else {
+    const long long per_b = (long long)tM * tN;
+    const long long r = t % per_b;
+    g.b = (int)(t / per_b);
+    g.i0 = (int)(r / tN) * kTile;
+    g.j0 = (int)(r % tN) * kTile;
+  }
+  return g;
+}
+
 // kStoreF32 scale of tile t for epilogue thread e: e < 128 the column scale of tile column e,
 // else alpha times the row scale of tile row e - 128
-__device__ __forceinline__ float f32_tile_scale(const GemmTcArgs &a, long long t, int e, int tN, long long per_b) {
-  const int b = (int)(t / per_b);
-  const long long r = t % per_b;
+__device__ __forceinline__ float f32_tile_scale(const GemmTcArgs &a, long long t, int e, int tM, int tN) {
+  const GemmTile g = gemm_tile(a, t, tM, tN);
+  const int b = g.b;
   if (e < kTile) {
-    const int col = (int)(r % tN) * kTile + e;
+    const int col = g.j0 + e;
     if (!a.col_scale || col >= a.Ncols) return 1.f;
     const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
     return a.col_scale[zb * a.cs_b + col];
   }
-  const int row = (int)(r / tN) * kTile + (e - kTile);
+  const int row = g.i0 + (e - kTile);
   if (!a.row_scale || row >= a.M) return a.alpha;
   const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
   return a.alpha * a.row_scale[za * a.rs_b + row];
@@ -1103,9 +1130,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       tc::RingPhases ring;
       for (long long t = blockIdx.x; t < total && !*abort; t += gridDim.x, ++tt) {
         const int q = (int)(tt & 1);   // issuer of this tile
-        const int b = (int)(t / per_b);
-        const long long r = t % per_b;
-        const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
+        const GemmTile gt = gemm_tile(a, t, tM, tN);
+        const int b = gt.b, i0 = gt.i0, j0 = gt.j0;
         const int za = a.idxA ? a.idxA[b] : (a.batchA_shared ? 0 : b);
         const int zb = a.idxB ? a.idxB[b] : (a.batchB_shared ? 0 : b);
         for (int kc = 0; kc < nk; ++kc, ++it) {
@@ -1164,12 +1190,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __shared__ __align__(16) float s_sc[2 * kTile];   // kStoreF32: column scales, then alpha x row scales
     const int ep = (warp - 2) * 32 + lane;
     // the scales of the next tile are loaded one tile ahead (their latency hides behind this one)
-    float pre = (a.mode == kStoreF32 && blockIdx.x < total) ? f32_tile_scale(a, blockIdx.x, ep, tN, per_b) : 0.f;
+    float pre = (a.mode == kStoreF32 && blockIdx.x < total) ? f32_tile_scale(a, blockIdx.x, ep, tM, tN) : 0.f;
     long long acc_it = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x, ++acc_it) {
-      const int b = (int)(t / per_b);
-      const long long r = t % per_b;
-      const int i0 = (int)(r / tN) * kTile, j0 = (int)(r % tN) * kTile;
+      const GemmTile gt = gemm_tile(a, t, tM, tN);
+      const int b = gt.b, i0 = gt.i0, j0 = gt.j0;
       const int buf = (int)(acc_it & 1);
       const uint32_t aph = (uint32_t)((acc_it >> 1) & 1);
       const bool got = tc::mbar_wait(&bar->acc_full[buf], aph, a.spin_limit, abort, a.status, 8);
@@ -1185,7 +1210,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         epi_sync();
         s_sc[ep] = pre;
         epi_sync();
-        if (t + gridDim.x < total) pre = f32_tile_scale(a, t + gridDim.x, ep, tN, per_b);
+        if (t + gridDim.x < total) pre = f32_tile_scale(a, t + gridDim.x, ep, tM, tN);
         const float rsc = s_sc[kTile + row];
         float *tile = reinterpret_cast<float *>(stage_out);
 #pragma unroll
