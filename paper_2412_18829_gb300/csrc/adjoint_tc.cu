@@ -386,28 +386,26 @@ __global__ void __launch_bounds__(kProdThreads, 1)
         const int P0 = (r / tP) * kT, R0 = (r % tP) * kT;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
-            {
-              int kc, half;
-              tc::bc_decode(p, nk, 1, kc, half);
-              const int s = (int)(it % kSt);
-              const uint32_t ph = (uint32_t)((it / kSt) & 1);
-              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              uint64_t *fb = &bar->full[half][s];   // the half's issuer
-              ring.take(half, s);
-              tc::mbar_arrive_expect_tx(fb, kStageB);
-              uint8_t *st = smem + (size_t)s * kStageB;
-              const int x = kc * kC;
-              if (half == 0) {   // B_v = A_v GR^T
-                tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d(st + kTileB, &tmA_lo, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d(st + 2 * kTileB, &tmGR_hi, fb, x, R0, b);
-                tc::tma_load_3d(st + 3 * kTileB, &tmGR_lo, fb, x, R0, b);
-              } else {           // C_v = GWt U2_v^T
-                tc::tma_load_3d(st, &tmGW_hi, fb, x, P0, b);
-                tc::tma_load_3d(st + kTileB, &tmGW_lo, fb, x, P0, b);
-                tc::tma_load_3d(st + 2 * kTileB, &tmU_hi, fb, x, R0, v);
-                tc::tma_load_3d(st + 3 * kTileB, &tmU_lo, fb, x, R0, v);
-              }
+            int kc, half;
+            tc::bc_decode(p, nk, 1, kc, half);
+            const int s = (int)(it % kSt);
+            const uint32_t ph = (uint32_t)((it / kSt) & 1);
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+            uint64_t *fb = &bar->full[half][s];   // the half's issuer
+            ring.take(half, s);
+            tc::mbar_arrive_expect_tx(fb, kStageB);
+            uint8_t *st = smem + (size_t)s * kStageB;
+            const int x = kc * kC;
+            if (half == 0) {   // B_v = A_v GR^T
+              tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d(st + kTileB, &tmA_lo, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d(st + 2 * kTileB, &tmGR_hi, fb, x, R0, b);
+              tc::tma_load_3d(st + 3 * kTileB, &tmGR_lo, fb, x, R0, b);
+            } else {           // C_v = GWt U2_v^T
+              tc::tma_load_3d(st, &tmGW_hi, fb, x, P0, b);
+              tc::tma_load_3d(st + kTileB, &tmGW_lo, fb, x, P0, b);
+              tc::tma_load_3d(st + 2 * kTileB, &tmU_hi, fb, x, R0, v);
+              tc::tma_load_3d(st + 3 * kTileB, &tmU_lo, fb, x, R0, v);
             }
           }
         }
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(kProdThreads, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          {   // this issuer's chunks sit at every other ring position
+          {   // this issuer's chunks, at the ring positions bc_pos gives
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {

@@ -280,27 +280,25 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         const int P0 = (r / tP) * kTile, R0 = (r % tP) * kTile;
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
-            {
-              int kc, half;
-              tc::bc_decode(p, nk, 1, kc, half);
-              const int s = (int)(it % kStages);
-              const uint32_t ph = (uint32_t)((it / kStages) & 1);
-              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              uint64_t *fb = &bar->full[half][s];   // the half's issuer
-              ring.take(half, s);
-              tc::mbar_arrive_expect_tx(fb, kStageBytes);
-              const int x = kc * kChunk;
-              if (half == 0) {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmGR_hi, fb, x, R0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmGR_lo, fb, x, R0, b);
-              } else {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &tmGW_hi, fb, x, P0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &tmGW_lo, fb, x, P0, b);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &tmU_hi, fb, x, R0, v);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &tmU_lo, fb, x, R0, v);
-              }
+            int kc, half;
+            tc::bc_decode(p, nk, 1, kc, half);
+            const int s = (int)(it % kStages);
+            const uint32_t ph = (uint32_t)((it / kStages) & 1);
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+            uint64_t *fb = &bar->full[half][s];   // the half's issuer
+            ring.take(half, s);
+            tc::mbar_arrive_expect_tx(fb, kStageBytes);
+            const int x = kc * kChunk;
+            if (half == 0) {
+              tc::tma_load_3d(stage_ptr(smem, s, 0), &tmA_hi, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d(stage_ptr(smem, s, 1), &tmA_lo, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d(stage_ptr(smem, s, 2), &tmGR_hi, fb, x, R0, b);
+              tc::tma_load_3d(stage_ptr(smem, s, 3), &tmGR_lo, fb, x, R0, b);
+            } else {
+              tc::tma_load_3d(stage_ptr(smem, s, 0), &tmGW_hi, fb, x, P0, b);
+              tc::tma_load_3d(stage_ptr(smem, s, 1), &tmGW_lo, fb, x, P0, b);
+              tc::tma_load_3d(stage_ptr(smem, s, 2), &tmU_hi, fb, x, R0, v);
+              tc::tma_load_3d(stage_ptr(smem, s, 3), &tmU_lo, fb, x, R0, v);
             }
           }
         }
@@ -323,7 +321,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          {   // this issuer's chunks sit at every other ring position
+          {   // this issuer's chunks, at the ring positions bc_pos gives
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
@@ -429,27 +427,25 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
         const int nk = J.Kp / kChunk;
         for (int v = J.v0; v < J.v1 && !*abort; ++v) {
           for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
-            {
-              int kc, half;
-              tc::bc_decode(p, nk, nk, kc, half);
-              const int s = (int)(it % kStages);
-              const uint32_t ph = (uint32_t)((it / kStages) & 1);
-              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
-              uint64_t *fb = &bar->full[half][s];
-              ring.take(half, s);
-              tc::mbar_arrive_expect_tx(fb, kStageBytes);
-              const int x = kc * kChunk;
-              if (half == 0) {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[0], fb, x, m.P0, m.b * J.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[1], fb, x, m.P0, m.b * J.n + v);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[2], fb, x, m.R0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[3], fb, x, m.R0, m.b);
-              } else {
-                tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[4], fb, x, m.P0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[5], fb, x, m.P0, m.b);
-                tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[6], fb, x, m.R0, v);
-                tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[7], fb, x, m.R0, v);
-              }
+            int kc, half;
+            tc::bc_decode(p, nk, nk, kc, half);
+            const int s = (int)(it % kStages);
+            const uint32_t ph = (uint32_t)((it / kStages) & 1);
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, limit, abort, jobs.status, 1)) break;
+            uint64_t *fb = &bar->full[half][s];
+            ring.take(half, s);
+            tc::mbar_arrive_expect_tx(fb, kStageBytes);
+            const int x = kc * kChunk;
+            if (half == 0) {
+              tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[0], fb, x, m.P0, m.b * J.n + v);
+              tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[1], fb, x, m.P0, m.b * J.n + v);
+              tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[2], fb, x, m.R0, m.b);
+              tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[3], fb, x, m.R0, m.b);
+            } else {
+              tc::tma_load_3d(stage_ptr(smem, s, 0), &J.maps[4], fb, x, m.P0, m.b);
+              tc::tma_load_3d(stage_ptr(smem, s, 1), &J.maps[5], fb, x, m.P0, m.b);
+              tc::tma_load_3d(stage_ptr(smem, s, 2), &J.maps[6], fb, x, m.R0, v);
+              tc::tma_load_3d(stage_ptr(smem, s, 3), &J.maps[7], fb, x, m.R0, v);
             }
           }
         }
@@ -475,7 +471,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1) k_sox_bcd_multi(const __grid_c
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, limit, abort, jobs.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          {   // this issuer's chunks sit at every other ring position
+          {   // this issuer's chunks, at the ring positions bc_pos gives
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
@@ -666,24 +662,22 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
         }
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
-            {
-              int kc, half;
-              tc::bc_decode(p, nk, 1, kc, half);
-              const int s = (int)(it % kRStages);
-              const uint32_t ph = (uint32_t)((it / kRStages) & 1);
-              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              uint64_t *fb = &bar->full[half][s];
-              ring.take(half, s);
-              tc::mbar_arrive_expect_tx(fb, kRStageBytes);
-              uint8_t *st = stages + (size_t)s * kRStageBytes;
-              const int x = kc * kChunk;
-              if (half == 0) {
-                tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d(st + kTileBytes, &tmA_lo, fb, x, P0, b * a.n + v);
-              } else {
-                tc::tma_load_3d(st, &tmU_hi, fb, x, R0, v);
-                tc::tma_load_3d(st + kTileBytes, &tmU_lo, fb, x, R0, v);
-              }
+            int kc, half;
+            tc::bc_decode(p, nk, 1, kc, half);
+            const int s = (int)(it % kRStages);
+            const uint32_t ph = (uint32_t)((it / kRStages) & 1);
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+            uint64_t *fb = &bar->full[half][s];
+            ring.take(half, s);
+            tc::mbar_arrive_expect_tx(fb, kRStageBytes);
+            uint8_t *st = stages + (size_t)s * kRStageBytes;
+            const int x = kc * kChunk;
+            if (half == 0) {
+              tc::tma_load_3d(st, &tmA_hi, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d(st + kTileBytes, &tmA_lo, fb, x, P0, b * a.n + v);
+            } else {
+              tc::tma_load_3d(st, &tmU_hi, fb, x, R0, v);
+              tc::tma_load_3d(st + kTileBytes, &tmU_lo, fb, x, R0, v);
             }
           }
         }
@@ -714,7 +708,7 @@ __global__ void __launch_bounds__(kBcdThreads, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          {   // this issuer's chunks sit at every other ring position
+          {   // this issuer's chunks, at the ring positions bc_pos gives
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
@@ -867,28 +861,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
         const int R0 = (r % tP) * kTile + (int)rank * (kTile / 2);
         for (int v = a.v0; v < a.v1 && !*abort; ++v) {
           for (int p = 0; p < 2 * nk && !*abort; ++p, ++it) {
-            {
-              int kc, half;
-              tc::bc_decode(p, nk, 1, kc, half);
-              const int s = (int)(it % kPStages);
-              const uint32_t ph = (uint32_t)((it / kPStages) & 1);
-              if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
-              ring.take(half, s);   // the half's issuer
-              if (rank == 0) tc::mbar_arrive_expect_tx(&bar->full[half][s], 2 * kPStageBytes);
-              const uint32_t fb = full0 + (uint32_t)(half * kPStages + s) * 8u;
-              uint8_t *st = smem + (size_t)s * kPStageBytes;
-              const int x = kc * kChunk;
-              if (half == 0) {   // B_v = A_v . GR^T
-                tc::tma_load_3d_pair(st, &tmA_hi, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d_pair(st + kPATile, &tmA_lo, fb, x, P0, b * a.n + v);
-                tc::tma_load_3d_pair(st + 2 * kPATile, &tmGR_hi, fb, x, R0, b);
-                tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmGR_lo, fb, x, R0, b);
-              } else {           // C_v = G_wP^T . U2_v^T
-                tc::tma_load_3d_pair(st, &tmGW_hi, fb, x, P0, b);
-                tc::tma_load_3d_pair(st + kPATile, &tmGW_lo, fb, x, P0, b);
-                tc::tma_load_3d_pair(st + 2 * kPATile, &tmU_hi, fb, x, R0, v);
-                tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmU_lo, fb, x, R0, v);
-              }
+            int kc, half;
+            tc::bc_decode(p, nk, 1, kc, half);
+            const int s = (int)(it % kPStages);
+            const uint32_t ph = (uint32_t)((it / kPStages) & 1);
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, a.spin_limit, abort, a.status, 1)) break;
+            ring.take(half, s);   // the half's issuer
+            if (rank == 0) tc::mbar_arrive_expect_tx(&bar->full[half][s], 2 * kPStageBytes);
+            const uint32_t fb = full0 + (uint32_t)(half * kPStages + s) * 8u;
+            uint8_t *st = smem + (size_t)s * kPStageBytes;
+            const int x = kc * kChunk;
+            if (half == 0) {   // B_v = A_v . GR^T
+              tc::tma_load_3d_pair(st, &tmA_hi, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d_pair(st + kPATile, &tmA_lo, fb, x, P0, b * a.n + v);
+              tc::tma_load_3d_pair(st + 2 * kPATile, &tmGR_hi, fb, x, R0, b);
+              tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmGR_lo, fb, x, R0, b);
+            } else {           // C_v = G_wP^T . U2_v^T
+              tc::tma_load_3d_pair(st, &tmGW_hi, fb, x, P0, b);
+              tc::tma_load_3d_pair(st + kPATile, &tmGW_lo, fb, x, P0, b);
+              tc::tma_load_3d_pair(st + 2 * kPATile, &tmU_hi, fb, x, R0, v);
+              tc::tma_load_3d_pair(st + 2 * kPATile + kPBTile, &tmU_lo, fb, x, R0, v);
             }
           }
         }
@@ -910,7 +902,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBcdThreads, 1)
           ok = tc::mbar_wait(&bar->acc_empty[buf], aph ^ 1u, a.spin_limit, abort, a.status, 2);
           if (!ok) break;
           tc::tc_fence_after();
-          {   // this issuer's chunks sit at every other ring position
+          {   // this issuer's chunks, at the ring positions bc_pos gives
             const int half = my;
             const uint32_t acc = tmem + buf * 256 + half * 128;
             for (int kc = 0; kc < nk; ++kc) {
